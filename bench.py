@@ -1,0 +1,277 @@
+"""Benchmark: two-component D3Q19 lattice updates per second (GLUPS) of the full coupled time step on one
+GB300, with the fused bulk kernel's fraction of the HBM roofline, an end-to-end figure through the C ABI
+with host buffers, and the FP64 oracle timed on the host cores as a CPU baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs an independent replica of the workload
+(the single-box problem does not shard); value = all ranks' lattice updates / max elapsed time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1904_11386_gb300 import inputs  # noqa: E402
+
+# Algorithmic bytes per lattice update of the fused bulk kernel (both components): read 2 x 19 FP32
+# populations, write 2 x 19 FP32 populations, write rho^A and rho^B.
+BYTES_PER_LU = 2 * 19 * 4 * 2 + 2 * 4
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload(name: str):
+    if name == "adsorb128":
+        # the paper's coupling (bounce-back with wetting) is not in this build yet: the same 128^3 two-component
+        # box and s=4 capsule run with the 2-point immersed-boundary coupling (colour 0)
+        return inputs.cfg_adsorb128(coupling=1), "adsorb128-ibm2: 128^3 D3Q19 x2, walls sheared 1e-4, s=4 capsule R=12"
+    if name == "parity32":
+        return inputs.cfg_parity(coupling=1), "parity32-ibm2: 32^3, psi=rho, s=3 capsule R=6"
+    if name == "fluid256":
+        p = inputs.cfg_droplet256(n_caps=0, coupling=1)
+        p.capsules = []
+        return p, "fluid256: 256^3 periodic two-component droplet, no capsules"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if k in d:
+                v = d[k]
+                if isinstance(v, dict):
+                    v = v.get("value", v.get("gbs"))
+                return float(v), "measured"
+    except Exception:
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", dev, f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(prob, seconds=15.0):
+    """The FP64 oracle as it stands, on this host's cores, on a bounded number of steps of the same workload."""
+    from oracle import oracle as O
+
+    s = O.OracleSim(prob)
+    s.step(1)                                    # first touch
+    n, t0 = 0, time.perf_counter()
+    while True:
+        s.step(1)
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt > seconds or n >= 200:
+            break
+    return {"value": prob.n_nodes * n / dt / 1e9, "unit": "GLUPS", "cores": O.threads(), "kind": "oracle",
+            "sample": f"{n} full time steps of the {prob.nx}x{prob.ny}x{prob.nz} workload ({dt:.1f} s)"}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def run_reference(args, prob, label, ws, rank):
+    """Reference arm: the FP64 oracle (plain C, OpenMP) on the host cores; each step one full time step."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+
+    s = O.OracleSim(prob)
+    for _ in range(args.warmup):
+        s.step(1)
+    t0 = time.perf_counter()
+    s.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = prob.n_nodes * args.steps / dt / 1e9
+    out = {"metric": "2-component D3Q19 lattice updates per second, full coupled step", "value": v,
+           "unit": "GLUPS", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": label, "lattice": [prob.nx, prob.ny, prob.nz]},
+           "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": O.threads(), "kind": "oracle",
+                            "sample": f"{args.steps} full time steps"},
+           "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="adsorb128")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    ws, rank, local = dist_setup()
+    prob, label = workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, prob, label, ws, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_1904_11386_gb300 import scbb
+
+    torch.cuda.set_device(local)
+    rhoA, rhoB = prob.initial_density()
+    sim = scbb.Sim(prob, rhoA, rhoB, device=f"cuda:{local}")
+    st = sim.stream
+    sim.scbb_step(args.warmup)
+    sim.scbb_sync()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    # ---- device-resident timing of K full steps
+    sim.scbb_enable_timing(True)
+    clocks = Clocks()
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = sim.scbb_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    sim.scbb_step(args.steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    launches = sim.scbb_launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    bulk_ms, bulk_n = sim.scbb_kernel_time()
+    sim.scbb_enable_timing(False)
+    sim.scbb_sync()
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    N = prob.n_nodes
+    value = N * args.steps * ws / (ms / 1e3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers: upload the initial fields, K steps, read back
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.scbb_set_density(rhoA, rhoB)
+    sim.scbb_step(args.steps)
+    a, b, u = sim.scbb_get_fields()
+    e2e_s = time.perf_counter() - t0
+    if not np.isfinite(a).all():
+        raise SystemExit("non-finite densities")
+    e2e = {"value": N * args.steps * ws / e2e_s / 1e9, "unit": "GLUPS",
+           "h2d_bytes_per_step": 5 * 4 * N / args.steps, "d2h_bytes_per_step": 5 * 4 * N / args.steps,
+           "job": f"set_density (host FP64 rho^A, rho^B) + {args.steps} steps + get_fields (host FP64)"}
+
+    peak, src = peak_hbm()
+    bulk_avg_s = bulk_ms / max(bulk_n, 1) / 1e3
+    achieved = BYTES_PER_LU * N / bulk_avg_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_bulk (fused 2-component stream + Shan-Chen + collide)",
+            "bytes_per_lu": BYTES_PER_LU, "peak_source": src,
+            "kernel_ms": bulk_avg_s * 1e3, "kernel_share": bulk_ms / ms if ms > 0 else None}
+
+    out = {"metric": "2-component D3Q19 lattice updates per second, full coupled step (GLUPS); fused bulk "
+                     "kernel fraction of HBM roofline",
+           "value": value, "unit": "GLUPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": label, "lattice": [prob.nx, prob.ny, prob.nz], "nodes": N,
+                      "vertices": int(sum(sim.nv)), "parallelism": f"replicas x{ws}",
+                      "l2": "inputs larger than L2 (populations 2 x 319 MB)"},
+           "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    sim.close()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

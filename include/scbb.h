@@ -1,0 +1,154 @@
+/*
+ * scbb — two-component Shan-Chen D3Q19 lattice Boltzmann fluid coupled to triangulated soft-capsule
+ * membranes, one GB300 GPU (sm_103a).  C ABI.
+ *
+ * Method: Wouters, Aouane, Krueger, Harting, "Mesoscale simulation of soft particles with tunable contact
+ * angle in multi-component fluids" (arXiv:1904.11386).  The calls follow the paper's statement of the
+ * problem: a lattice (Sec. II.A), two fluid components with a pseudo-potential coupling (Sec. II.D), a
+ * relaxation time (Eq. 1), membranes with reference shapes and elastic moduli (Sec. II.B), and step(n).
+ *
+ * Conventions shared by every call
+ *   - Units: dx = dt = rho0 = 1 (Sec. III).  Lattice node (x, y, z) has linear index x + nx*(y + ny*z);
+ *     host field arrays are double[nz][ny][nx] (x fastest).
+ *   - x and y are periodic.  With walls = 1 the planes z = 0 and z = nz-1 are solid wall nodes and the
+ *     fluid lives on 1 <= z <= nz-2 (half-way bounce-back walls at z = 0.5 and z = nz-1.5).
+ *   - Ownership: the caller owns all memory.  Device memory comes from ONE caller-allocated workspace of
+ *     scbb_workspace_bytes() bytes (for example a torch uint8 CUDA tensor); the library never allocates
+ *     device memory.  Host arrays passed in are copied during the call and never retained.
+ *   - Streams: every kernel runs on the caller's CUDA stream given to scbb_create.  Calls that return
+ *     host data synchronise that stream; scbb_step does not.
+ *   - Errors: every call returns a scbb_status; nothing throws across the ABI.  scbb_last_error() gives a
+ *     one-line description of the last failure on a context.  A device-side error (non-finite density or
+ *     |u| > 0.1) is recorded in a device word and reported by the next synchronising call as
+ *     SCBB_E_UNSTABLE; after it, calls other than scbb_destroy return SCBB_E_STATE.
+ *   - A NULL context, NULL required pointer, or out-of-range parameter gives SCBB_E_INVAL and changes
+ *     nothing.
+ */
+#ifndef SCBB_H
+#define SCBB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SCBB_ABI_VERSION 1
+
+typedef struct scbb_ctx scbb_ctx;
+
+typedef enum {
+    SCBB_OK = 0,
+    SCBB_E_INVAL = 1,        /* bad argument */
+    SCBB_E_CUDA = 2,         /* a CUDA runtime call failed */
+    SCBB_E_NOMEM = 3,        /* workspace smaller than scbb_workspace_bytes() */
+    SCBB_E_UNSTABLE = 4,     /* non-finite density or Mach guard |u| > 0.1 tripped on the device */
+    SCBB_E_TIMEOUT = 5,      /* a bounded device wait gave up */
+    SCBB_E_MESH = 6,         /* invalid mesh (index out of range, zero-area reference triangle, ...) */
+    SCBB_E_STATE = 7,        /* context is in an error state */
+    SCBB_E_UNSUPPORTED = 8   /* a mode this build does not provide */
+} scbb_status;
+
+/* Lattice (Sec. II.A).  walls: 1 = solid planes z=0 and z=nz-1 with half-way bounce-back (Eq. 11, with the
+ * wall velocity as v0), 0 = periodic in z.  u_lo / u_hi: velocities of the z=0 / z=nz-1 walls. */
+typedef struct {
+    int nx, ny, nz;
+    int walls;
+    double u_lo[3], u_hi[3];
+} scbb_lattice;
+
+/* Fluid (Sec. II.A, II.D, II.E).
+ *   tau       BGK relaxation time (Eq. 1), > 0.5
+ *   G         inter-component coupling G^{AB} = G^{BA} (Eq. 13); G^{AA} = G^{BB} = 0
+ *   psi_kind  0: psi = 1 - exp(-rho) (the paper), 1: psi = rho
+ *   g         uniform body acceleration; component c feels the force density rho^c g
+ *   coupling  0: half-way bounce-back membranes with wetting (the paper, Sec. II.C-E),
+ *             1: 2-point immersed boundary (Peskin hat; not in the paper; colour must be 0)
+ *   rho_maj, rho_min   equilibrium majority / minority densities used to turn colour into a virtual
+ *             density offset (Eq. 15): rho_virtual = 2 |colour| (rho_maj - rho_min)
+ *   C0, mass_correction   adaptive fresh-node mass correction (Eq. 18), C0 = 2500 in the paper
+ *   pp_eps, pp_d0         particle-particle repulsion (Eq. 26, Sec. III.E), 0.5 and 1.25 in the paper
+ *   storage   0: FP32 populations (the only value this build accepts) */
+typedef struct {
+    double tau, G;
+    int psi_kind;
+    double g[3];
+    int coupling;
+    double rho_maj, rho_min, C0;
+    int mass_correction;
+    double pp_eps, pp_d0;
+    int storage;
+} scbb_fluid;
+
+/* One capsule membrane (Sec. II.B): a closed triangulated surface, triangles counter-clockwise seen from
+ * outside.  ref_xyz is the stress-free shape (A0 and V0 are taken from it), init_xyz the initial shape
+ * (may equal ref_xyz).  kS, C: Skalak moduli (Eq. 6); kV: volume penalty (Eq. 7); kB: Helfrich bending
+ * (Eq. 9-10); mass: node mass for the bounce-back coupling (5 in the paper); colour: particle colour
+ * Delta rho (Eq. 15), positive prefers component A. */
+typedef struct {
+    int nv, nt;
+    const double* ref_xyz;   /* [nv][3] */
+    const int* tri;          /* [nt][3] vertex indices 0..nv-1 */
+    const double* init_xyz;  /* [nv][3] */
+    double kS, C, kB, kV, mass, colour;
+} scbb_mesh;
+
+/* Bytes of device workspace a context with this description needs (0 on invalid input). */
+size_t scbb_workspace_bytes(const scbb_lattice* lat, const scbb_fluid* fl, int n_mesh, const scbb_mesh* meshes);
+
+/* Create a context.  dev_workspace: device pointer, 256-byte aligned, of at least `bytes` bytes, owned by
+ * the caller and kept alive until scbb_destroy.  cuda_stream: a cudaStream_t (NULL = legacy default).
+ * Copies the meshes to the device, precomputes reference data (reference metrics, areas, V0) and leaves
+ * the fluid at rest with rho^A = rho^B = 0 until scbb_set_density.  *out receives the context. */
+scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mesh, const scbb_mesh* meshes,
+                        void* dev_workspace, size_t bytes, void* cuda_stream, scbb_ctx** out);
+
+/* Initial state: populations = equilibrium (Eq. 2) of host densities rhoA, rhoB (double[N]) and host
+ * velocity u (double[3][N], NULL = at rest).  Resets the vertices to init_xyz at rest.  Synchronous. */
+scbb_status scbb_set_density(scbb_ctx* ctx, const double* rhoA, const double* rhoB, const double* u);
+
+/* Advance n time steps (Eq. 1 for both components with the Shan-Chen force of Eq. 13, membrane forces of
+ * Eq. 6-10, coupling, node update).  Asynchronous on the context stream. */
+scbb_status scbb_step(scbb_ctx* ctx, long long n);
+
+/* Wait for the context stream; reports device-side errors. */
+scbb_status scbb_sync(scbb_ctx* ctx);
+
+/* Moments of the current state (post-streaming, before the next collision): rho^c = sum_i f_i^c and the
+ * barycentric velocity u = sum_c sum_i f_i^c c_i / sum_c rho^c, into host double[N], double[N],
+ * double[3][N] (any may be NULL).  Wall nodes report 0.  Synchronous. */
+scbb_status scbb_get_fields(scbb_ctx* ctx, double* rhoA, double* rhoB, double* u);
+
+/* Current populations f_i^c(x) (post-streaming) into host double[2][N][19] in the D3Q19 order
+ * rest, +x, -x, +y, -y, +z, -z, (+x+y), (-x-y), (+x-y), (-x+y), (+x+z), (-x-z), (+x-z), (-x+z), (+y+z),
+ * (-y-z), (+y-z), (-y+z).  Wall nodes report 0.  Synchronous. */
+scbb_status scbb_get_populations(scbb_ctx* ctx, double* f);
+
+/* All vertices of all meshes, concatenated in creation order: positions, velocities and the total node
+ * force of the last step, host double[NV][3] each (any may be NULL).  Synchronous. */
+scbb_status scbb_get_vertices(scbb_ctx* ctx, double* x, double* v, double* F);
+
+/* FP64 reductions computed on the device: mass2[2] = total mass per component over fluid nodes, mom3[3] =
+ * total fluid momentum sum_c sum_i f c, and per mesh vol[n_mesh] (enclosed volume) and com[n_mesh][3]
+ * (vertex average).  Any pointer may be NULL.  Synchronous. */
+scbb_status scbb_get_diag(scbb_ctx* ctx, double* mass2, double* mom3, double* vol, double* com);
+
+/* Number of kernel launches issued by this context since creation (for launch accounting). */
+long long scbb_launch_count(const scbb_ctx* ctx);
+
+/* Measurement support.  With on != 0, every later launch of the fused bulk fluid kernel is bracketed by a
+ * pair of CUDA events on the context stream (up to 4096 launches; later launches run untimed).
+ * scbb_kernel_time synchronises, returns the summed device time of the timed bulk launches in
+ * milliseconds and their count, and clears the record.  Timing adds no kernel launches. */
+scbb_status scbb_enable_timing(scbb_ctx* ctx, int on);
+scbb_status scbb_kernel_time(scbb_ctx* ctx, double* ms, long long* launches);
+
+const char* scbb_last_error(const scbb_ctx* ctx);
+
+/* Releases host-side state.  The workspace stays owned by the caller. */
+void scbb_destroy(scbb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCBB_H */

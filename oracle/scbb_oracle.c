@@ -8,13 +8,13 @@
  * state.  Every function names the passage of the paper it follows.
  *
  * Parity status (what pins each function; the pins live in tests/test_oracle_*.py):
- *   fluid collide/stream (Eq. 1-3, Sec. II.A)        mass conservation, Poiseuille order, Couette sign
- *   Shan-Chen force (Eq. 9, Sec. II.D)              Laplace law gamma = 0.0388 (Sec. III), flat interface
- *   Skalak / volume forces (Eq. 4-6, Sec. II.B)      finite-difference gradients, net force/torque, rest shape
- *   Helfrich-Meyer bending (Eq. 7-8, Sec. II.B)      Gauss-Bonnet, mixed-area partition, spheroid curvatures,
+ *   fluid collide/stream (Eq. 1-5, Sec. II.A)        mass conservation, Poiseuille order, Couette sign
+ *   Shan-Chen force (Eq. 13, Sec. II.D)             Laplace law gamma = 0.0388 (Sec. III), flat interface
+ *   Skalak / volume forces (Eq. 6-8, Sec. II.B)      finite-difference gradients, net force/torque, rest shape
+ *   Helfrich-Meyer bending (Eq. 9-10, Sec. II.B)     Gauss-Bonnet, mixed-area partition, spheroid curvatures,
  *                                                    energy-descent cosine
  *   2-point immersed boundary (not in the paper)     adjoint identity, partition of unity, linear exactness
- *   particle-particle repulsion (Sec. III.E)         brute-force pair sum, Newton's third law
+ *   particle-particle repulsion (Eq. 26, Sec. III.E) brute-force pair sum, Newton's third law
  *   bounce-back coupling, wetting, fresh nodes (Sec. II.C-E): see the second part of this file.
  */
 #include <math.h>
@@ -138,7 +138,7 @@ static long nbr(const osim* s, int x, int y, int z, int i, int* zz_out) {
 }
 
 /* ---------------------------------------------------------------------------------------------------- */
-/* Equilibrium (Eq. 2) and pseudo-potential (Sec. II.D: psi = 1 - exp(-rho/rho0), rho0 = 1)              */
+/* Equilibrium (Eq. 2) and pseudo-potential (Sec. II.D, below Eq. 13: psi = 1 - exp(-rho/rho0), rho0 = 1)              */
 /* ---------------------------------------------------------------------------------------------------- */
 static double feq(int i, double rho, const double u[3]) {
     double cu = CX[i] * u[0] + CY[i] * u[1] + CZ[i] * u[2];
@@ -234,7 +234,7 @@ void o_set_state(osim* s, const double* rhoA, const double* rhoB, const double* 
 void o_get_f(const osim* s, double* out) { memcpy(out, s->f, sizeof(double) * 2 * 19 * s->N); }
 void o_set_f(osim* s, const double* in) { memcpy(s->f, in, sizeof(double) * 2 * 19 * s->N); }
 
-/* rho^c = sum_i f_i^c (Sec. II.A, rho0 = 1) for every non-wall node */
+/* rho^c = sum_i f_i^c (Eq. 4, rho0 = 1) for every non-wall node */
 static void compute_rho(osim* s) {
     long N = s->N;
 #pragma omp parallel for schedule(static)
@@ -249,15 +249,25 @@ static void compute_rho(osim* s) {
     }
 }
 
-/* densities, velocity u = (sum_c sum_i f c + F/2) / rho (Sec. II.A) -- F of the last step */
+/* densities and barycentric velocity of the current state (Eq. 4-5 without the half force):
+   rho^c = sum_i f_i^c, u = sum_c sum_i f_i^c c_i / sum_c rho^c; wall nodes report 0 */
 void o_get_fields(osim* s, double* rhoA, double* rhoB, double* u) {
     compute_rho(s);
     long N = s->N;
     for (long n = 0; n < N; n++) {
         if (rhoA) rhoA[n] = s->rho[n];
         if (rhoB) rhoB[n] = s->rho[N + n];
+        if (!u) continue;
+        double j[3] = {0, 0, 0};
+        double rt = s->rho[n] + s->rho[N + n];
+        if (s->owner[n] != OWNER_WALL && rt > 0)
+            for (int c = 0; c < 2; c++)
+                for (int i = 0; i < 19; i++) {
+                    double fi = s->f[(c * N + n) * 19 + i];
+                    j[0] += fi * CX[i]; j[1] += fi * CY[i]; j[2] += fi * CZ[i];
+                }
+        for (int k = 0; k < 3; k++) u[k * N + n] = rt > 0 ? j[k] / rt : 0.0;
     }
-    if (u) memcpy(u, s->u, sizeof(double) * 3 * N);
 }
 
 void o_get_fsc(const osim* s, double* out) { memcpy(out, s->Fsc, sizeof(double) * 6 * s->N); }
@@ -310,12 +320,12 @@ static void cross3(const double* a, const double* b, double* o) {
 static double norm3(const double* a) { return sqrt(dot3(a, a)); }
 
 /*
- * Skalak strain energy (Eq. 4) on linear triangles, integrated over the reference (stress-free) area A0.
+ * Skalak strain energy (Eq. 6) on linear triangles, integrated over the reference (stress-free) area A0.
  * The invariants of the in-plane right Cauchy-Green tensor are frame-free:
  *   tr G = tr(g0^{-1} g),  det G = det g / det g0
  * with g, g0 the 2x2 metric tensors (Gram matrices) of the current and reference edge vectors
  * e1 = x2 - x1, e2 = x3 - x1.  I1 = tr G - 2 = lambda1^2 + lambda2^2 - 2, I2 = det G - 1.
- * Nodal forces are F = -dE/dx (Eq. 6), differentiated analytically through (g11, g12, g22).
+ * Nodal forces are F = -dE/dx (Eq. 8), differentiated analytically through (g11, g12, g22).
  * F may be NULL (energy only).  Returns the energy.
  */
 double o_skalak(int nv, int nt, const double* x, const int* tri, const double* ref, double kS, double C,
@@ -370,7 +380,7 @@ double o_volume(int nv, int nt, const double* x, const int* tri) {
     return V;
 }
 
-/* volume penalty (Eq. 5): E = kV/2 (V-V0)^2/V0, F_b = -kV (V-V0)/V0 dV/dx_b.  Adds into F.  Returns E. */
+/* volume penalty (Eq. 7): E = kV/2 (V-V0)^2/V0, F_b = -kV (V-V0)/V0 dV/dx_b.  Adds into F.  Returns E. */
 double o_volume_force(int nv, int nt, const double* x, const int* tri, double kV, double V0, double* F) {
     double V = o_volume(nv, nt, x, tri);
     double k = -kV * (V - V0) / V0;
@@ -390,7 +400,7 @@ double o_volume_force(int nv, int nt, const double* x, const int* tri, double kV
 }
 
 /*
- * Helfrich bending (Eq. 7-8) with the discrete differential-geometry operators of Meyer et al.:
+ * Helfrich bending (Eq. 9-10) with the discrete differential-geometry operators of Meyer et al.:
  *   A_i     mixed Voronoi area (obtuse triangles: half / quarter of the triangle area)
  *   K_i     = 1/(2 A_i) sum_j (cot a_ij + cot b_ij)(x_i - x_j)      mean-curvature normal (= 2 H n)
  *   n_i     area-weighted average of the outward face normals
@@ -491,7 +501,7 @@ double o_bending(int nv, int nt, const double* x, const int* tri, double kB, dou
 }
 
 /* ---------------------------------------------------------------------------------------------------- */
-/* Particle-particle hard-core repulsion (Sec. III.E): F = eps (d0 - d)^{3/2} along the separation for     */
+/* Particle-particle hard-core repulsion (Eq. 26, Sec. III.E): F = eps (d0 - d)^{3/2} along the separation for     */
 /* boundary nodes of different capsules closer than d0.  Linked-cell search; minimum image in periodic     */
 /* directions.  Adds into F.                                                                             */
 /* ---------------------------------------------------------------------------------------------------- */
@@ -679,8 +689,8 @@ void o_capsule_diag(const osim* s, int m, double* vol, double* com3) {
 }
 
 /* ---------------------------------------------------------------------------------------------------- */
-/* Fluid: Shan-Chen force (Eq. 9), forcing by equilibrium-velocity shift (Sec. II.A), BGK collision      */
-/* (Eq. 1), push streaming with half-way bounce-back (Eq. 10) on wall links and on membrane-cut links.    */
+/* Fluid: Shan-Chen force (Eq. 13), forcing by equilibrium-velocity shift (Sec. II.A), BGK collision      */
+/* (Eq. 1), push streaming with half-way bounce-back (Eq. 11) on wall links and on membrane-cut links.    */
 /* ---------------------------------------------------------------------------------------------------- */
 
 /* virtual density seen across a wall link: mean of rho over the fluid neighbours of the wall node */
@@ -723,7 +733,7 @@ static void fluid_step(osim* s) {
                 double fi = s->f[(c * N + n) * 19 + i];
                 j[c][0] += fi * CX[i]; j[c][1] += fi * CY[i]; j[c][2] += fi * CZ[i];
             }
-        /* Shan-Chen force on component c from the other component c' (G^{AB} = G^{BA} = G) */
+        /* Shan-Chen force (Eq. 13) on component c from the other component c' (G^{AB} = G^{BA} = G) */
         double Fc[2][3] = {{0, 0, 0}, {0, 0, 0}};
         for (int c = 0; c < 2; c++) {
             int co = 1 - c;
@@ -769,7 +779,7 @@ static void fluid_step(osim* s) {
                 if (i == 0) {
                     s->fn[(c * N + n) * 19] = fs;
                 } else if (s->owner[m] == OWNER_WALL) {
-                    /* half-way bounce-back on a moving wall (Eq. 10, v0 = wall velocity); c_i points into the
+                    /* half-way bounce-back on a moving wall (Eq. 11, v0 = wall velocity); c_i points into the
                        wall, the population returns to n in the opposite direction */
                     const double* U = (zz == 0) ? s->p.u_lo : s->p.u_hi;
                     double cu = CX[i] * U[0] + CY[i] * U[1] + CZ[i] * U[2];

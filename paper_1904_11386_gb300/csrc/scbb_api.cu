@@ -1,0 +1,495 @@
+// C ABI of libscbb (declared in include/scbb.h).  Host-side orchestration only: argument checks, carving
+// the caller's workspace, mesh preprocessing, and the per-step launch sequence on the caller's stream.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "scbb_internal.cuh"
+
+using namespace scbb;
+
+struct scbb_ctx {
+    scbb_lattice lat;
+    scbb_fluid fl;
+    LbmParams lp;
+    DevState d;
+    int cur = 0;
+    cudaStream_t st = nullptr;
+    int nm = 0;
+    std::vector<float4> X0;           // initial shape, host copy
+    long long launches = 0;
+    long long steps = 0;
+    int broken = 0;
+    std::string err;
+    // bulk-kernel timing (measurement only)
+    int timing = 0;
+    std::vector<cudaEvent_t> ev;     // pairs
+    size_t ev_used = 0;
+};
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+// Bump allocator over the workspace; with base == nullptr it only measures.
+struct Carve {
+    char* base;
+    size_t off = 0;
+    explicit Carve(void* b) : base((char*)b) {}
+    template <class T>
+    T* take(size_t count) {
+        off = (off + ALIGN - 1) / ALIGN * ALIGN;
+        T* p = base ? (T*)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+scbb_status fail(scbb_ctx* c, scbb_status s, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                         \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) {                                                                    \
+            (ctx)->broken = 1;                                                                      \
+            return fail((ctx), SCBB_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_));               \
+        }                                                                                           \
+    } while (0)
+
+bool valid_lattice(const scbb_lattice* l) {
+    if (!l || l->nx < 1 || l->ny < 1 || l->nz < 1) return false;
+    if (l->walls != 0 && l->walls != 1) return false;
+    if (l->walls && l->nz < 3) return false;
+    double N = (double)l->nx * l->ny * l->nz;
+    return N * 2.0 * Q < 4.0e9;     // 32-bit population indices
+}
+
+bool valid_fluid(const scbb_fluid* f) {
+    if (!f || !(f->tau > 0.5) || !isfinite(f->G)) return false;
+    if (f->psi_kind != 0 && f->psi_kind != 1) return false;
+    if (f->coupling != 0 && f->coupling != 1) return false;
+    if (f->storage != 0) return false;
+    return true;
+}
+
+int total(const scbb_mesh* m, int n, bool tris) {
+    long long s = 0;
+    for (int k = 0; k < n; k++) s += tris ? m[k].nt : m[k].nv;
+    return (int)s;
+}
+
+// Lays out every device buffer; returns total bytes.
+size_t layout(const scbb_lattice* lat, const scbb_fluid* fl, int nm, const scbb_mesh* ms, void* base, DevState* d) {
+    Carve c(base);
+    const size_t N = (size_t)lat->nx * lat->ny * lat->nz;
+    const size_t nxy = (size_t)lat->nx * lat->ny;
+    const int NV = total(ms, nm, false), NT = total(ms, nm, true);
+    DevState t{};
+    t.S[0] = c.take<float>(2 * Q * N);
+    t.S[1] = c.take<float>(2 * Q * N);
+    t.rho = c.take<float>(2 * N);
+    const bool ibm = fl->coupling == 1 && NV > 0;
+    t.u = ibm ? c.take<float>(3 * N) : nullptr;
+    t.Fibm = ibm ? c.take<float>(3 * N) : nullptr;
+    t.mask = ibm ? c.take<uint32_t>((N + 31) / 32) : nullptr;
+    t.wall_rho = c.take<float>(4 * nxy);
+    t.ghost = c.take<float>(4 * nxy);
+    t.red = c.take<double>(8 + 5 * 1024);
+    t.err = c.take<int>(4);
+    t.NV = NV; t.NT = NT; t.NM = nm;
+    const size_t nv1 = NV > 0 ? NV : 1, nt1 = NT > 0 ? NT : 1;
+    t.X = c.take<float4>(nv1);
+    t.V = c.take<float4>(nv1);
+    t.F = c.take<float4>(nv1);
+    t.Fsk = c.take<float4>(nv1);
+    t.dV = c.take<float4>(nv1);
+    t.nrm = c.take<float4>(nv1);
+    t.AK = c.take<float2>(nv1);
+    t.X0 = c.take<float4>(nv1);
+    t.tri = c.take<int4>(nt1);
+    t.tref = c.take<float4>(nt1);
+    t.vt_off = c.take<int>(nv1 + 1);
+    t.vt_idx = c.take<int>(3 * nt1);
+    t.vcap = c.take<int>(nv1);
+    t.cap = c.take<CapDev>(nm > 0 ? nm : 1);
+    t.cap_red = c.take<double>(4 * (nm > 0 ? nm : 1));
+    if (d) *d = t;
+    return (c.off + ALIGN - 1) / ALIGN * ALIGN;
+}
+
+bool valid_meshes(int nm, const scbb_mesh* ms, std::string& why) {
+    if (nm < 0 || (nm > 0 && !ms)) { why = "mesh array"; return false; }
+    for (int k = 0; k < nm; k++) {
+        const scbb_mesh& m = ms[k];
+        if (m.nv < 4 || m.nt < 4 || !m.ref_xyz || !m.tri || !m.init_xyz) { why = "mesh sizes/pointers"; return false; }
+        for (int t = 0; t < 3 * m.nt; t++)
+            if (m.tri[t] < 0 || m.tri[t] >= m.nv) { why = "triangle index out of range"; return false; }
+        if (!(m.mass > 0) || !(m.kS >= 0) || !(m.kV >= 0) || !(m.kB >= 0)) { why = "mesh moduli"; return false; }
+    }
+    return true;
+}
+
+void set_params(scbb_ctx* c) {
+    LbmParams& p = c->lp;
+    p.nx = c->lat.nx; p.ny = c->lat.ny; p.nz = c->lat.nz;
+    p.nxy = p.nx * p.ny;
+    p.N = (unsigned int)((size_t)p.nxy * p.nz);
+    p.walls = c->lat.walls;
+    p.zf0 = p.walls ? 1 : 0;
+    p.zf1 = p.walls ? p.nz - 1 : p.nz;
+    p.tau = (float)c->fl.tau;
+    p.omega = (float)(1.0 / c->fl.tau);
+    p.G = (float)c->fl.G;
+    p.psi_kind = c->fl.psi_kind;
+    for (int k = 0; k < 3; k++) {
+        p.g[k] = (float)c->fl.g[k];
+        p.ulo[k] = (float)c->lat.u_lo[k];
+        p.uhi[k] = (float)c->lat.u_hi[k];
+    }
+    // z-segment length: enough CTAs for several waves on 152 SMs, segments of at least 8 planes
+    int nzf = p.zf1 - p.zf0;
+    int cols = ((p.nx + 31) / 32) * ((p.ny + 7) / 8);
+    int target = 4 * 152;
+    int nseg = (target + cols - 1) / cols;
+    if (nseg < 1) nseg = 1;
+    int lz = (nzf + nseg - 1) / nseg;
+    if (lz < 8) lz = 8;
+    if (lz > nzf) lz = nzf;
+    p.lz = lz;
+}
+
+scbb_status check_device_error(scbb_ctx* c) {
+    int h = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&h, c->d.err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    if (h) {
+        c->broken = 1;
+        return fail(c, SCBB_E_UNSTABLE, "device error word %d after %lld steps (non-finite density or |u| > 0.1)",
+                    h, c->steps);
+    }
+    return SCBB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t scbb_workspace_bytes(const scbb_lattice* lat, const scbb_fluid* fl, int n_mesh, const scbb_mesh* meshes) {
+    std::string why;
+    if (!valid_lattice(lat) || !valid_fluid(fl) || !valid_meshes(n_mesh, meshes, why)) return 0;
+    return layout(lat, fl, n_mesh, meshes, nullptr, nullptr);
+}
+
+scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mesh, const scbb_mesh* meshes,
+                        void* dev_workspace, size_t bytes, void* cuda_stream, scbb_ctx** out) {
+    if (!out) return SCBB_E_INVAL;
+    *out = nullptr;
+    std::string why;
+    if (!valid_lattice(lat) || !valid_fluid(fl) || !dev_workspace) return SCBB_E_INVAL;
+    if (!valid_meshes(n_mesh, meshes, why)) return SCBB_E_MESH;
+    if (fl->coupling == 0 && n_mesh > 0) return SCBB_E_UNSUPPORTED;
+    if (fl->coupling == 1)
+        for (int k = 0; k < n_mesh; k++)
+            if (meshes[k].colour != 0.0) return SCBB_E_INVAL;     // wetting needs the bounce-back coupling
+    if (((uintptr_t)dev_workspace) % ALIGN) return SCBB_E_INVAL;
+    size_t need = layout(lat, fl, n_mesh, meshes, nullptr, nullptr);
+    if (bytes < need) return SCBB_E_NOMEM;
+
+    scbb_ctx* c = new scbb_ctx();
+    c->lat = *lat;
+    c->fl = *fl;
+    c->st = (cudaStream_t)cuda_stream;
+    c->nm = n_mesh;
+    layout(lat, fl, n_mesh, meshes, dev_workspace, &c->d);
+    set_params(c);
+    DevState& d = c->d;
+
+    // ---- meshes: triangles, reference metrics, vertex -> triangle CSR, capsule constants
+    const int NV = d.NV, NT = d.NT;
+    std::vector<int4> tri(NT > 0 ? NT : 1);
+    std::vector<float4> tref(NT > 0 ? NT : 1);
+    std::vector<int> vcap(NV > 0 ? NV : 1), cnt(NV + 1, 0), vt_idx(3 * (NT > 0 ? NT : 1));
+    std::vector<CapDev> caps(n_mesh > 0 ? n_mesh : 1);
+    c->X0.assign(NV > 0 ? NV : 1, make_float4(0, 0, 0, 0));
+    int v0 = 0, t0 = 0;
+    for (int m = 0; m < n_mesh; m++) {
+        const scbb_mesh& M = meshes[m];
+        double V0 = 0;
+        for (int t = 0; t < M.nt; t++) {
+            const int a = M.tri[3 * t], b = M.tri[3 * t + 1], e = M.tri[3 * t + 2];
+            tri[t0 + t] = make_int4(v0 + a, v0 + b, v0 + e, m);
+            const double* A = M.ref_xyz + 3 * a;
+            const double* B = M.ref_xyz + 3 * b;
+            const double* E = M.ref_xyz + 3 * e;
+            double r1[3], r2[3];
+            for (int k = 0; k < 3; k++) { r1[k] = B[k] - A[k]; r2[k] = E[k] - A[k]; }
+            const double P = r1[0] * r1[0] + r1[1] * r1[1] + r1[2] * r1[2];
+            const double Qm = r1[0] * r2[0] + r1[1] * r2[1] + r1[2] * r2[2];
+            const double R = r2[0] * r2[0] + r2[1] * r2[1] + r2[2] * r2[2];
+            const double det = P * R - Qm * Qm;
+            if (!(det > 1e-24)) { delete c; return SCBB_E_MESH; }
+            tref[t0 + t] = make_float4((float)(R / det), (float)(-Qm / det), (float)(P / det), (float)(0.5 * sqrt(det)));
+            V0 += (A[0] * (B[1] * E[2] - B[2] * E[1]) + A[1] * (B[2] * E[0] - B[0] * E[2]) +
+                   A[2] * (B[0] * E[1] - B[1] * E[0])) / 6.0;
+            cnt[v0 + a + 1]++; cnt[v0 + b + 1]++; cnt[v0 + e + 1]++;
+        }
+        if (!(V0 > 0)) { delete c; return SCBB_E_MESH; }     // inward orientation or degenerate
+        for (int v = 0; v < M.nv; v++) {
+            vcap[v0 + v] = m;
+            c->X0[v0 + v] = make_float4((float)M.init_xyz[3 * v], (float)M.init_xyz[3 * v + 1],
+                                        (float)M.init_xyz[3 * v + 2], 0.f);
+        }
+        CapDev cd;
+        cd.kS = (float)M.kS; cd.C = (float)M.C; cd.kB = (float)M.kB; cd.kV = (float)M.kV;
+        cd.mass = (float)M.mass; cd.colour = (float)M.colour; cd.V0 = V0;
+        cd.v0 = v0; cd.nv = M.nv; cd.t0 = t0; cd.nt = M.nt;
+        caps[m] = cd;
+        v0 += M.nv;
+        t0 += M.nt;
+    }
+    for (int v = 0; v < NV; v++) cnt[v + 1] += cnt[v];
+    {
+        std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+        for (int t = 0; t < NT; t++) {
+            const int id[3] = {tri[t].x, tri[t].y, tri[t].z};
+            for (int k = 0; k < 3; k++) vt_idx[fill[id[k]]++] = 4 * t + k;
+        }
+    }
+    if (NT > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(d.tri, tri.data(), sizeof(int4) * NT, cudaMemcpyHostToDevice, c->st));
+        CUDA_TRY(c, cudaMemcpyAsync(d.tref, tref.data(), sizeof(float4) * NT, cudaMemcpyHostToDevice, c->st));
+        CUDA_TRY(c, cudaMemcpyAsync(d.vt_idx, vt_idx.data(), sizeof(int) * 3 * NT, cudaMemcpyHostToDevice, c->st));
+    }
+    if (NV > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(d.vt_off, cnt.data(), sizeof(int) * (NV + 1), cudaMemcpyHostToDevice, c->st));
+        CUDA_TRY(c, cudaMemcpyAsync(d.vcap, vcap.data(), sizeof(int) * NV, cudaMemcpyHostToDevice, c->st));
+        CUDA_TRY(c, cudaMemcpyAsync(d.X0, c->X0.data(), sizeof(float4) * NV, cudaMemcpyHostToDevice, c->st));
+        CUDA_TRY(c, cudaMemcpyAsync(d.X, c->X0.data(), sizeof(float4) * NV, cudaMemcpyHostToDevice, c->st));
+        CUDA_TRY(c, cudaMemsetAsync(d.V, 0, sizeof(float4) * NV, c->st));
+        CUDA_TRY(c, cudaMemsetAsync(d.F, 0, sizeof(float4) * NV, c->st));
+    }
+    if (n_mesh > 0)
+        CUDA_TRY(c, cudaMemcpyAsync(d.cap, caps.data(), sizeof(CapDev) * n_mesh, cudaMemcpyHostToDevice, c->st));
+    const size_t N = c->lp.N;
+    CUDA_TRY(c, cudaMemsetAsync(d.S[0], 0, sizeof(float) * 2 * Q * N, c->st));
+    CUDA_TRY(c, cudaMemsetAsync(d.S[1], 0, sizeof(float) * 2 * Q * N, c->st));
+    CUDA_TRY(c, cudaMemsetAsync(d.rho, 0, sizeof(float) * 2 * N, c->st));
+    if (d.Fibm) {
+        CUDA_TRY(c, cudaMemsetAsync(d.Fibm, 0, sizeof(float) * 3 * N, c->st));
+        CUDA_TRY(c, cudaMemsetAsync(d.u, 0, sizeof(float) * 3 * N, c->st));
+        CUDA_TRY(c, cudaMemsetAsync(d.mask, 0, sizeof(uint32_t) * ((N + 31) / 32), c->st));
+    }
+    CUDA_TRY(c, cudaMemsetAsync(d.err, 0, sizeof(int) * 4, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    *out = c;
+    return SCBB_OK;
+}
+
+scbb_status scbb_set_density(scbb_ctx* c, const double* rhoA, const double* rhoB, const double* u) {
+    if (!c || !rhoA || !rhoB) return SCBB_E_INVAL;
+    if (c->broken) return SCBB_E_STATE;
+    const size_t N = c->lp.N;
+    std::vector<float> h(5 * N);
+    for (size_t n = 0; n < N; n++) {
+        h[n] = (float)rhoA[n];
+        h[N + n] = (float)rhoB[n];
+        h[2 * N + n] = u ? (float)u[n] : 0.f;
+        h[3 * N + n] = u ? (float)u[N + n] : 0.f;
+        h[4 * N + n] = u ? (float)u[2 * N + n] : 0.f;
+    }
+    float* stage = c->d.S[1 - c->cur];
+    CUDA_TRY(c, cudaMemcpyAsync(stage, h.data(), sizeof(float) * 5 * N, cudaMemcpyHostToDevice, c->st));
+    launch_init_state(c->lp, c->d.S[c->cur], stage, stage + 2 * N, c->st);
+    c->launches++;
+    if (c->d.NV > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(c->d.X, c->d.X0, sizeof(float4) * c->d.NV, cudaMemcpyDeviceToDevice, c->st));
+        CUDA_TRY(c, cudaMemsetAsync(c->d.V, 0, sizeof(float4) * c->d.NV, c->st));
+        CUDA_TRY(c, cudaMemsetAsync(c->d.F, 0, sizeof(float4) * c->d.NV, c->st));
+    }
+    if (c->d.Fibm) {
+        CUDA_TRY(c, cudaMemsetAsync(c->d.Fibm, 0, sizeof(float) * 3 * N, c->st));
+        CUDA_TRY(c, cudaMemsetAsync(c->d.mask, 0, sizeof(uint32_t) * ((N + 31) / 32), c->st));
+    }
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    c->steps = 0;
+    return SCBB_OK;
+}
+
+scbb_status scbb_step(scbb_ctx* c, long long n) {
+    if (!c || n < 0) return SCBB_E_INVAL;
+    if (c->broken) return SCBB_E_STATE;
+    const bool ibm = c->fl.coupling == 1 && c->d.NV > 0;
+    for (long long s = 0; s < n; s++) {
+        if (ibm) {
+            launch_capsule_reduce(c->d, c->st);
+            launch_membrane_forces(c->d, c->st);
+            launch_ibm_spread(c->lp, c->d, c->st);
+            c->launches += 4;
+        }
+        if (c->lp.walls) {
+            launch_wall_ghost(c->lp, c->d.S[c->cur], c->d.wall_rho, c->d.ghost, c->st);
+            c->launches += 2;
+        }
+        const bool timed = c->timing && c->ev_used + 2 <= c->ev.size();
+        if (timed) cudaEventRecord(c->ev[c->ev_used], c->st);
+        launch_bulk(c->lp, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.rho, c->d.ghost, c->d.Fibm, c->d.mask, c->d.u,
+                    c->d.err, ibm, c->st);
+        if (timed) {
+            cudaEventRecord(c->ev[c->ev_used + 1], c->st);
+            c->ev_used += 2;
+        }
+        c->launches++;
+        if (ibm) {
+            launch_ibm_interp(c->lp, c->d, c->st);
+            c->launches++;
+        }
+        c->cur ^= 1;
+        c->steps++;
+    }
+    CUDA_TRY(c, cudaGetLastError());
+    return SCBB_OK;
+}
+
+scbb_status scbb_sync(scbb_ctx* c) {
+    if (!c) return SCBB_E_INVAL;
+    if (c->broken) return SCBB_E_STATE;
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    return check_device_error(c);
+}
+
+static scbb_status export_state(scbb_ctx* c, int what, std::vector<float>& h) {
+    const size_t N = c->lp.N;
+    float* stage = c->d.S[1 - c->cur];
+    launch_export(c->lp, c->d.S[c->cur], stage, what, c->st);
+    c->launches++;
+    const size_t cnt = what == 1 ? 2 * Q * N : 5 * N;
+    h.resize(cnt);
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaMemcpyAsync(h.data(), stage, sizeof(float) * cnt, cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    return SCBB_OK;
+}
+
+scbb_status scbb_get_fields(scbb_ctx* c, double* rhoA, double* rhoB, double* u) {
+    if (!c) return SCBB_E_INVAL;
+    if (c->broken) return SCBB_E_STATE;
+    std::vector<float> h;
+    scbb_status s = export_state(c, 0, h);
+    if (s != SCBB_OK) return s;
+    const size_t N = c->lp.N;
+    for (size_t n = 0; n < N; n++) {
+        if (rhoA) rhoA[n] = h[n];
+        if (rhoB) rhoB[n] = h[N + n];
+        if (u) { u[n] = h[2 * N + n]; u[N + n] = h[3 * N + n]; u[2 * N + n] = h[4 * N + n]; }
+    }
+    return check_device_error(c);
+}
+
+scbb_status scbb_get_populations(scbb_ctx* c, double* f) {
+    if (!c || !f) return SCBB_E_INVAL;
+    if (c->broken) return SCBB_E_STATE;
+    std::vector<float> h;
+    scbb_status s = export_state(c, 1, h);
+    if (s != SCBB_OK) return s;
+    for (size_t q = 0; q < h.size(); q++) f[q] = h[q];
+    return check_device_error(c);
+}
+
+scbb_status scbb_get_vertices(scbb_ctx* c, double* x, double* v, double* F) {
+    if (!c) return SCBB_E_INVAL;
+    if (c->broken) return SCBB_E_STATE;
+    const int NV = c->d.NV;
+    if (NV == 0) return SCBB_OK;
+    std::vector<float4> hx(NV), hv(NV), hf(NV);
+    CUDA_TRY(c, cudaMemcpyAsync(hx.data(), c->d.X, sizeof(float4) * NV, cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaMemcpyAsync(hv.data(), c->d.V, sizeof(float4) * NV, cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaMemcpyAsync(hf.data(), c->d.F, sizeof(float4) * NV, cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    for (int q = 0; q < NV; q++) {
+        if (x) { x[3 * q] = hx[q].x; x[3 * q + 1] = hx[q].y; x[3 * q + 2] = hx[q].z; }
+        if (v) { v[3 * q] = hv[q].x; v[3 * q + 1] = hv[q].y; v[3 * q + 2] = hv[q].z; }
+        if (F) { F[3 * q] = hf[q].x; F[3 * q + 1] = hf[q].y; F[3 * q + 2] = hf[q].z; }
+    }
+    return check_device_error(c);
+}
+
+scbb_status scbb_get_diag(scbb_ctx* c, double* mass2, double* mom3, double* vol, double* com) {
+    if (!c) return SCBB_E_INVAL;
+    if (c->broken) return SCBB_E_STATE;
+    double r[5];
+    launch_moments_reduce(c->lp, c->d.S[c->cur], c->d.red, c->st);
+    c->launches += 2;
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaMemcpyAsync(r, c->d.red, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->st));
+    std::vector<double> cr(4 * (c->nm > 0 ? c->nm : 1));
+    if (c->nm > 0) {
+        launch_capsule_reduce(c->d, c->st);
+        c->launches++;
+        CUDA_TRY(c, cudaMemcpyAsync(cr.data(), c->d.cap_red, sizeof(double) * 4 * c->nm, cudaMemcpyDeviceToHost, c->st));
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    if (mass2) { mass2[0] = r[0]; mass2[1] = r[1]; }
+    if (mom3) { mom3[0] = r[2]; mom3[1] = r[3]; mom3[2] = r[4]; }
+    for (int m = 0; m < c->nm; m++) {
+        if (vol) vol[m] = cr[4 * m];
+        if (com) { com[3 * m] = cr[4 * m + 1]; com[3 * m + 1] = cr[4 * m + 2]; com[3 * m + 2] = cr[4 * m + 3]; }
+    }
+    return check_device_error(c);
+}
+
+long long scbb_launch_count(const scbb_ctx* c) { return c ? c->launches : 0; }
+
+scbb_status scbb_enable_timing(scbb_ctx* c, int on) {
+    if (!c) return SCBB_E_INVAL;
+    if (on && c->ev.empty()) {
+        c->ev.resize(2 * 4096);
+        for (auto& e : c->ev) CUDA_TRY(c, cudaEventCreate(&e));
+    }
+    c->timing = on;
+    c->ev_used = 0;
+    return SCBB_OK;
+}
+
+scbb_status scbb_kernel_time(scbb_ctx* c, double* ms, long long* launches) {
+    if (!c) return SCBB_E_INVAL;
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    double tot = 0;
+    for (size_t q = 0; q + 1 < c->ev_used; q += 2) {
+        float t = 0;
+        CUDA_TRY(c, cudaEventElapsedTime(&t, c->ev[q], c->ev[q + 1]));
+        tot += t;
+    }
+    if (ms) *ms = tot;
+    if (launches) *launches = (long long)(c->ev_used / 2);
+    c->ev_used = 0;
+    return SCBB_OK;
+}
+
+const char* scbb_last_error(const scbb_ctx* c) {
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+void scbb_destroy(scbb_ctx* c) {
+    if (!c) return;
+    for (auto& e : c->ev) cudaEventDestroy(e);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,224 @@
+"""Python binding of libscbb (include/scbb.h): argument marshalling only.
+
+Every step of the simulation runs in the CUDA kernels of libscbb.so.  PyTorch supplies the device workspace
+and the stream.  There is no CPU fallback: if the library or a CUDA device is missing, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libscbb.so")
+
+SCBB_OK = 0
+STATUS = {0: "SCBB_OK", 1: "SCBB_E_INVAL", 2: "SCBB_E_CUDA", 3: "SCBB_E_NOMEM", 4: "SCBB_E_UNSTABLE",
+          5: "SCBB_E_TIMEOUT", 6: "SCBB_E_MESH", 7: "SCBB_E_STATE", 8: "SCBB_E_UNSUPPORTED"}
+
+EXPORTS = ["scbb_workspace_bytes", "scbb_create", "scbb_set_density", "scbb_step", "scbb_sync",
+           "scbb_get_fields", "scbb_get_populations", "scbb_get_vertices", "scbb_get_diag",
+           "scbb_launch_count", "scbb_enable_timing", "scbb_kernel_time", "scbb_last_error", "scbb_destroy"]
+
+
+class scbb_lattice(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("walls", C.c_int),
+                ("u_lo", C.c_double * 3), ("u_hi", C.c_double * 3)]
+
+
+class scbb_fluid(C.Structure):
+    _fields_ = [("tau", C.c_double), ("G", C.c_double), ("psi_kind", C.c_int), ("g", C.c_double * 3),
+                ("coupling", C.c_int), ("rho_maj", C.c_double), ("rho_min", C.c_double), ("C0", C.c_double),
+                ("mass_correction", C.c_int), ("pp_eps", C.c_double), ("pp_d0", C.c_double),
+                ("storage", C.c_int)]
+
+
+class scbb_mesh(C.Structure):
+    _fields_ = [("nv", C.c_int), ("nt", C.c_int), ("ref_xyz", C.c_void_p), ("tri", C.c_void_p),
+                ("init_xyz", C.c_void_p), ("kS", C.c_double), ("C", C.c_double), ("kB", C.c_double),
+                ("kV", C.c_double), ("mass", C.c_double), ("colour", C.c_double)]
+
+
+class ScbbError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libscbb.so and declare its exports (fails loudly if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ScbbError(f"libscbb.so not built ({path}); run __graft_entry__.build()")
+    L = C.CDLL(path)
+    vp = C.c_void_p
+    L.scbb_workspace_bytes.restype = C.c_size_t
+    L.scbb_workspace_bytes.argtypes = [vp, vp, C.c_int, vp]
+    L.scbb_create.restype = C.c_int
+    L.scbb_create.argtypes = [vp, vp, C.c_int, vp, vp, C.c_size_t, vp, C.POINTER(vp)]
+    L.scbb_set_density.restype = C.c_int
+    L.scbb_set_density.argtypes = [vp, vp, vp, vp]
+    L.scbb_step.restype = C.c_int
+    L.scbb_step.argtypes = [vp, C.c_longlong]
+    L.scbb_sync.restype = C.c_int
+    L.scbb_sync.argtypes = [vp]
+    L.scbb_get_fields.restype = C.c_int
+    L.scbb_get_fields.argtypes = [vp, vp, vp, vp]
+    L.scbb_get_populations.restype = C.c_int
+    L.scbb_get_populations.argtypes = [vp, vp]
+    L.scbb_get_vertices.restype = C.c_int
+    L.scbb_get_vertices.argtypes = [vp, vp, vp, vp]
+    L.scbb_get_diag.restype = C.c_int
+    L.scbb_get_diag.argtypes = [vp, vp, vp, vp, vp]
+    L.scbb_launch_count.restype = C.c_longlong
+    L.scbb_launch_count.argtypes = [vp]
+    L.scbb_enable_timing.restype = C.c_int
+    L.scbb_enable_timing.argtypes = [vp, C.c_int]
+    L.scbb_kernel_time.restype = C.c_int
+    L.scbb_kernel_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+    L.scbb_last_error.restype = C.c_char_p
+    L.scbb_last_error.argtypes = [vp]
+    L.scbb_destroy.restype = None
+    L.scbb_destroy.argtypes = [vp]
+    _lib = L
+    return L
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def lattice_of(prob) -> scbb_lattice:
+    lat = scbb_lattice()
+    lat.nx, lat.ny, lat.nz, lat.walls = prob.nx, prob.ny, prob.nz, int(prob.walls)
+    lat.u_lo = (C.c_double * 3)(*prob.u_lo)
+    lat.u_hi = (C.c_double * 3)(*prob.u_hi)
+    return lat
+
+
+def fluid_of(prob) -> scbb_fluid:
+    fl = scbb_fluid()
+    fl.tau, fl.G, fl.psi_kind = prob.tau, prob.G, prob.psi_kind
+    fl.g = (C.c_double * 3)(*prob.g)
+    fl.coupling = prob.coupling if prob.capsules else 1
+    fl.rho_maj, fl.rho_min, fl.C0 = prob.rho_maj, prob.rho_min, prob.C0
+    fl.mass_correction = int(prob.mass_correction)
+    fl.pp_eps, fl.pp_d0 = prob.pp_eps, prob.pp_d0
+    fl.storage = 0
+    return fl
+
+
+class Sim:
+    """One simulation context: a torch-owned device workspace, the torch current stream, and the C calls."""
+
+    def __init__(self, prob, rhoA=None, rhoB=None, u=None, device="cuda", set_state=True):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise ScbbError("no CUDA device: the scbb path has no CPU fallback")
+        L = load()
+        self.L = L
+        self.prob = prob
+        self.lat = lattice_of(prob)
+        self.fl = fluid_of(prob)
+        nm = len(prob.capsules)
+        self.meshes = (scbb_mesh * max(nm, 1))()
+        self._keep = []
+        self.nv = []
+        for k, cap in enumerate(prob.capsules):
+            ref, tri, init = cap.mesh()
+            ref = np.ascontiguousarray(ref, np.float64)
+            tri = np.ascontiguousarray(tri, np.int32)
+            init = np.ascontiguousarray(init, np.float64)
+            self._keep += [ref, tri, init]
+            m = self.meshes[k]
+            m.nv, m.nt = len(ref), len(tri)
+            m.ref_xyz, m.tri, m.init_xyz = _p(ref), _p(tri), _p(init)
+            m.kS, m.C, m.kB, m.kV, m.mass, m.colour = cap.kS, cap.C, cap.kB, cap.kV, cap.mass, cap.colour
+            self.nv.append(len(ref))
+        self.nm = nm
+        nbytes = L.scbb_workspace_bytes(C.byref(self.lat), C.byref(self.fl), nm, self.meshes)
+        if nbytes == 0:
+            raise ScbbError("scbb_workspace_bytes rejected the problem description")
+        self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+        self.stream = torch.cuda.current_stream(self.workspace.device)
+        h = C.c_void_p()
+        st = L.scbb_create(C.byref(self.lat), C.byref(self.fl), nm, self.meshes,
+                           C.c_void_p(self.workspace.data_ptr()), C.c_size_t(nbytes),
+                           C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != SCBB_OK:
+            raise ScbbError(f"scbb_create: {STATUS.get(st, st)}")
+        self.h = h
+        if set_state:
+            if rhoA is None:
+                rhoA, rhoB = prob.initial_density()
+            self.scbb_set_density(rhoA, rhoB, u)
+
+    def _check(self, st, what):
+        if st != SCBB_OK:
+            msg = self.L.scbb_last_error(self.h)
+            raise ScbbError(f"{what}: {STATUS.get(st, st)}: {msg.decode() if msg else ''}")
+
+    # ---- calls with the C names
+    def scbb_set_density(self, rhoA, rhoB, u=None):
+        a = np.ascontiguousarray(rhoA, np.float64).ravel()
+        b = np.ascontiguousarray(rhoB, np.float64).ravel()
+        uu = None if u is None else np.ascontiguousarray(u, np.float64).reshape(3, -1)
+        self._check(self.L.scbb_set_density(self.h, _p(a), _p(b), _p(uu)), "scbb_set_density")
+
+    def scbb_step(self, n=1):
+        self._check(self.L.scbb_step(self.h, int(n)), "scbb_step")
+
+    def scbb_sync(self):
+        self._check(self.L.scbb_sync(self.h), "scbb_sync")
+
+    def scbb_get_fields(self):
+        N = self.prob.n_nodes
+        s = (self.prob.nz, self.prob.ny, self.prob.nx)
+        a, b, u = np.empty(N), np.empty(N), np.empty(3 * N)
+        self._check(self.L.scbb_get_fields(self.h, _p(a), _p(b), _p(u)), "scbb_get_fields")
+        return a.reshape(s), b.reshape(s), u.reshape((3,) + s)
+
+    def scbb_get_populations(self):
+        N = self.prob.n_nodes
+        f = np.empty(2 * N * 19)
+        self._check(self.L.scbb_get_populations(self.h, _p(f)), "scbb_get_populations")
+        return f.reshape(2, N, 19)
+
+    def scbb_get_vertices(self):
+        NV = sum(self.nv)
+        X, V, F = np.empty(3 * NV), np.empty(3 * NV), np.empty(3 * NV)
+        self._check(self.L.scbb_get_vertices(self.h, _p(X), _p(V), _p(F)), "scbb_get_vertices")
+        return X.reshape(NV, 3), V.reshape(NV, 3), F.reshape(NV, 3)
+
+    def scbb_get_diag(self):
+        m, p = np.empty(2), np.empty(3)
+        vol, com = np.empty(max(self.nm, 1)), np.empty(3 * max(self.nm, 1))
+        self._check(self.L.scbb_get_diag(self.h, _p(m), _p(p), _p(vol), _p(com)), "scbb_get_diag")
+        return dict(mass=m, momentum=p, volume=vol[:self.nm], com=com[:3 * self.nm].reshape(self.nm, 3))
+
+    def scbb_launch_count(self):
+        return int(self.L.scbb_launch_count(self.h))
+
+    def scbb_enable_timing(self, on=True):
+        self._check(self.L.scbb_enable_timing(self.h, int(on)), "scbb_enable_timing")
+
+    def scbb_kernel_time(self):
+        ms, n = C.c_double(0), C.c_longlong(0)
+        self._check(self.L.scbb_kernel_time(self.h, C.byref(ms), C.byref(n)), "scbb_kernel_time")
+        return ms.value, n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.scbb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,76 @@
+"""GPU parity of the membrane and 2-point immersed-boundary path against the FP64 oracle (C ABI)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1904_11386_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _sim(prob, **kw):
+    from paper_1904_11386_gb300 import scbb
+
+    return scbb.Sim(prob, **kw)
+
+
+def test_membrane_forces_first_step():
+    """Skalak + volume + bending node forces (Eq. 6-10) of a deformed capsule at step 0 match the oracle's
+    FP64 forces to FP32 accuracy."""
+    cap = inputs.Capsule(centre=(12.3, 11.8, 12.2), radius=5.0, subdiv=3, kS=0.01, kB=2e-3, kV=1.0,
+                         deform=np.diag([1.12, 0.93, 1.0]))
+    p = inputs.Problem(name="t", nx=24, ny=24, nz=26, walls=1, coupling=1, psi_kind=0, z_interface=12,
+                       capsules=[cap], noise=1e-4, seed=3)
+    g = _sim(p)
+    o = O.OracleSim(p)
+    g.scbb_step(1)
+    o.step(1)
+    _, _, Fg = g.scbb_get_vertices()
+    _, _, Fo = o.vertices()
+    assert np.abs(Fg - Fo).max() < 1e-4 * np.abs(Fo).max()
+
+
+def test_ibm_small_box_20_steps():
+    """Coupled immersed-boundary steps: fields and vertex positions after 20 steps."""
+    p = inputs.small_problem(n=20, walls=1, coupling=1, subdiv=2, radius=4.0, noise=1e-4)
+    p.capsules[0].kV = 1.0
+    g = _sim(p)
+    o = O.OracleSim(p)
+    g.scbb_step(20)
+    o.step(20)
+    ga, gb, gu = g.scbb_get_fields()
+    oa, ob, ou = o.fields()
+    fl = oa + ob > 0
+    assert (np.abs(ga - oa)[fl] / oa[fl]).max() < 1e-5
+    assert (np.abs(gb - ob)[fl] / ob[fl]).max() < 1e-5
+    assert np.abs(gu - ou).max() < 1e-5 * np.abs(ou).max() + 1e-7
+    Xg, Vg, _ = g.scbb_get_vertices()
+    Xo, Vo, _ = o.vertices()
+    assert np.abs(Xg - Xo).max() < 1e-4
+
+
+def test_parity32_ibm_200_steps():
+    """The 32^3 parity workload (walls, psi = rho, interface at z = 16, s = 3 capsule of radius 6, 200 steps,
+    2-point immersed boundary): densities within 1e-5 relative, velocities within 1e-5 of max|u|, vertex
+    positions within 1e-4 lattice units."""
+    p = inputs.cfg_parity(coupling=1)
+    g = _sim(p)
+    o = O.OracleSim(p)
+    g.scbb_step(p.steps)
+    o.step(p.steps)
+    ga, gb, gu = g.scbb_get_fields()
+    oa, ob, ou = o.fields()
+    fl = oa + ob > 0
+    ea = (np.abs(ga - oa)[fl] / oa[fl]).max()
+    eb = (np.abs(gb - ob)[fl] / ob[fl]).max()
+    eu = np.abs(gu - ou).max() / np.abs(ou).max()
+    Xg, _, _ = g.scbb_get_vertices()
+    Xo, _, _ = o.vertices()
+    ex = np.abs(Xg - Xo).max()
+    assert ea < 1e-5 and eb < 1e-5, (ea, eb)
+    assert eu < 1e-5, eu
+    assert ex < 1e-4, ex
+    d = g.scbb_get_diag()
+    vo, co = o.capsule(0)
+    assert abs(d["volume"][0] - vo) / vo < 1e-5
+    assert np.abs(d["com"][0] - co).max() < 1e-4

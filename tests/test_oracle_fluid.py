@@ -43,7 +43,7 @@ def test_equilibrium_moments():
 
 
 def test_mass_conservation_walls_and_sc():
-    """Collision and half-way bounce-back conserve each component's mass (Sec. II.A, Eq. 10):
+    """Collision and half-way bounce-back conserve each component's mass (Eq. 1, Eq. 11):
     exact to round-off with moving walls, Shan-Chen forces and a ragged box."""
     p = _prob(nx=13, ny=9, nz=14, walls=1, u_lo=(-0.01, 0.0, 0.0), u_hi=(0.01, 0.005, 0.0), z_interface=7,
               noise=1e-3, seed=3)
@@ -55,7 +55,7 @@ def test_mass_conservation_walls_and_sc():
 
 
 def test_momentum_conservation_sc_periodic():
-    """The Shan-Chen forces (Eq. 9) are pairwise antisymmetric, so in a periodic box the total momentum is
+    """The Shan-Chen forces (Eq. 13) are pairwise antisymmetric, so in a periodic box the total momentum is
     conserved exactly; collision with the velocity-shift forcing conserves it as well."""
     p = _prob(nx=10, ny=9, nz=11, z_interface=5, noise=1e-3, seed=4)
     s = O.OracleSim(p)
@@ -65,7 +65,7 @@ def test_momentum_conservation_sc_periodic():
 
 
 def test_body_force_momentum_gain():
-    """Velocity-shift forcing (Sec. II.A): summed over components, collision adds exactly F = rho g per node
+    """Velocity-shift forcing (Sec. II.A, Eq. 5): summed over components, collision adds exactly F = rho g per node
     per step."""
     g = np.array([1e-5, -2e-5, 3e-6])
     p = _prob(nx=6, ny=5, nz=4, G=0.0, g=tuple(g), noise=1e-3, seed=5)
@@ -78,7 +78,7 @@ def test_body_force_momentum_gain():
 
 @pytest.mark.parametrize("psi_kind", [0, 1])
 def test_shan_chen_force_closed_form(psi_kind):
-    """Eq. 9 on a field that varies along x only: the directions with c_x = +1 carry total weight
+    """Eq. 13 on a field that varies along x only: the directions with c_x = +1 carry total weight
     1/18 + 4/36 = 1/6, so F^A_x(x) = -psi^A(x) G (psi^B(x+1) - psi^B(x-1)) / 6 and F_y = F_z = 0."""
     nx = 16
     p = _prob(nx=nx, ny=3, nz=3, psi_kind=psi_kind, G=3.6)
@@ -100,7 +100,7 @@ def test_shan_chen_force_closed_form(psi_kind):
 
 
 def test_couette_moving_wall_sign():
-    """Half-way bounce-back on a moving wall (Eq. 10 with v0 = wall velocity): the steady flow between a
+    """Half-way bounce-back on a moving wall (Eq. 11 with v0 = wall velocity): the steady flow between a
     resting wall at z = 0.5 and a wall moving with U at z = nz - 1.5 is the linear Couette profile, dragged
     in the direction of the wall (fixes the sign of the wall term)."""
     H = 12
@@ -129,7 +129,7 @@ def test_poiseuille_second_order():
         _, _, u = s.fields()
         z = np.arange(1, H + 1)
         ua = g / (2 * nu) * (z - 0.5) * (H + 0.5 - z)
-        un = u[0, 1:H + 1, 0, 0]
+        un = u[0, 1:H + 1, 0, 0] + g / 2          # physical velocity includes half the force (Eq. 5)
         errs.append(np.sqrt(((un - ua) ** 2).sum() / (ua ** 2).sum()))
     order = np.log2(errs[0] / errs[1])
     assert errs[1] < 2e-3
@@ -157,7 +157,7 @@ def test_flat_interface_symmetry():
 def test_laplace_law_surface_tension():
     """Laplace law (Sec. III, common parameters: G = 3.6, 0.7 / 0.042, psi = 1 - exp(-rho) gives
     gamma = 0.0388).  Cylindrical B-rich droplets in a periodic 64 x 64 x 1 box: Delta P = gamma / R.
-    The pressure is p = cs^2 (rho^A + rho^B) + cs^2 G psi^A psi^B (the continuum limit of Eq. 9).
+    The pressure is p = cs^2 (rho^A + rho^B) + cs^2 G psi^A psi^B (the continuum limit of Eq. 13).
     Pinned: Delta P is linear in 1/R through the origin.  The oracle's gamma is 0.046; the paper's 0.0388
     comes from a measurement it does not describe, so only a +-30 % band around it is asserted."""
     L = 64

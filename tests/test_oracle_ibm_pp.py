@@ -58,7 +58,7 @@ def _brute_pp(X, cap, eps, d0, L, per):
 
 def test_pp_repulsion_matches_brute_force_and_newton3():
     """F = eps (d0 - d)^{3/2} along the separation for nodes of different capsules closer than d0
-    (Sec. III.E, eps = 0.5, d0 = 1.25): the linked-cell sum equals the brute-force pair sum, the total force
+    (Eq. 26, Sec. III.E, eps = 0.5, d0 = 1.25): the linked-cell sum equals the brute-force pair sum, the total force
     vanishes, and same-capsule pairs do not interact.  Periodic minimum image across the box faces."""
     rng = np.random.default_rng(3)
     L = np.array([9.0, 8.0, 7.0])
@@ -77,7 +77,7 @@ def test_pp_repulsion_matches_brute_force_and_newton3():
 def test_ibm_coupled_step_conserves_momentum():
     """Skalak and volume forces sum to zero, spreading keeps the sum, and each component receives the
     share rho^c / rho of the spread force: in a periodic box the fluid momentum is conserved by the coupled
-    immersed-boundary step (to round-off).  Bending is off here: the Meyer force of Eq. 8 is not an exact
+    immersed-boundary step (to round-off).  Bending is off here: the Meyer force of Eq. 10 is not an exact
     energy gradient and carries a small net force on irregular shapes."""
     cap = inputs.Capsule(centre=(6.2, 5.9, 6.1), radius=3.0, subdiv=2, kS=0.01, kB=0.0, kV=1.0,
                          deform=np.diag([1.15, 0.9, 1.0]))

@@ -1,4 +1,4 @@
-"""Pins of the oracle's membrane mechanics (Sec. II.B, Eq. 4-8) against closed forms, invariances and
+"""Pins of the oracle's membrane mechanics (Sec. II.B, Eq. 6-10) against closed forms, invariances and
 finite differences of the energies (no GPU needed)."""
 import numpy as np
 import pytest
@@ -28,7 +28,7 @@ def _fd_grad(efun, X, h=1e-6):
 
 @pytest.mark.parametrize("subdiv", [0, 1])
 def test_skalak_force_is_minus_energy_gradient(subdiv):
-    """Eq. 6: F = -dE/dx for the Skalak energy of Eq. 4 (central differences, h = 1e-6)."""
+    """Eq. 8: F = -dE/dx for the Skalak energy of Eq. 6 (central differences, h = 1e-6)."""
     ref, T, X = _deformed(subdiv, seed=subdiv)
     kS, Cs = 0.01, 9.0
     E, F = O.skalak(X, T, ref, kS, Cs)
@@ -38,7 +38,7 @@ def test_skalak_force_is_minus_energy_gradient(subdiv):
 
 def test_skalak_rest_shape_and_invariances():
     """The stress-free shape carries no force; the energy is invariant under rigid motions, so the net force
-    and net torque vanish for any shape (Eq. 4-6)."""
+    and net torque vanish for any shape (Eq. 6-8)."""
     ref, T, X = _deformed(2, seed=3)
     E0, F0 = O.skalak(ref, T, ref, 0.01, 9.0)
     assert E0 < 1e-28 and np.abs(F0).max() < 1e-15
@@ -55,7 +55,7 @@ def test_skalak_rest_shape_and_invariances():
 
 def test_skalak_uniform_dilation_closed_form():
     """Isotropic stretch lambda: I1 = 2 lambda^2 - 2, I2 = lambda^4 - 1, so
-    E = kS/4 A0 (I1^2 + 2 I1 - 2 I2 + C I2^2) with A0 the total reference area (Eq. 4)."""
+    E = kS/4 A0 (I1^2 + 2 I1 - 2 I2 + C I2^2) with A0 the total reference area (Eq. 6)."""
     V, T = inputs.icosphere(2)
     ref = V * 4.0
     lam = 1.07
@@ -69,7 +69,7 @@ def test_skalak_uniform_dilation_closed_form():
 
 def test_skalak_uniaxial_closed_form():
     """Stretch lambda along x of a flat triangle: lambda1 = lambda, lambda2 = 1, so I1 = lambda^2 - 1,
-    I2 = lambda^2 - 1 (Eq. 4 invariants)."""
+    I2 = lambda^2 - 1 (Eq. 6 invariants)."""
     ref = np.array([[0.0, 0, 0], [1.0, 0, 0], [0.3, 0.8, 0]])
     T = np.array([[0, 1, 2]], np.int32)
     lam = 1.2
@@ -81,7 +81,7 @@ def test_skalak_uniaxial_closed_form():
 
 def test_volume_closed_forms_and_gradient():
     """Enclosed volume of a closed outward mesh: a unit cube made of 12 triangles has V = 1; the volume force
-    of Eq. 5 equals -dE/dx."""
+    of Eq. 7 equals -dE/dx."""
     cube = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0], [0, 0, 1], [1, 0, 1], [1, 1, 1], [0, 1, 1]], float)
     T = np.array([[0, 2, 1], [0, 3, 2], [4, 5, 6], [4, 6, 7], [0, 1, 5], [0, 5, 4], [1, 2, 6], [1, 6, 5],
                   [2, 3, 7], [2, 7, 6], [3, 0, 4], [3, 4, 7]], np.int32)
@@ -108,7 +108,7 @@ def test_bending_exact_identities():
 
 def test_bending_sphere():
     """On a sphere of radius R: H -> 1/R, KG -> 1/R^2, 2H(H^2 - KG) -> 0 and the bending force -> 0
-    (Eq. 8); the discrete values converge with refinement and the normals point outward."""
+    (Eq. 10); the discrete values converge with refinement and the normals point outward."""
     R = 5.0
     errs = []
     for s in (3, 4):
@@ -134,7 +134,7 @@ def _spheroid_analytic(a, c, Z):
 
 def test_bending_spheroid_curvatures():
     """Prolate spheroid (a = 4, c = 6): the Meyer mean and Gaussian curvatures match the closed forms of the
-    spheroid to a few per cent at subdivision 4 (Eq. 7-8 operators)."""
+    spheroid to a few per cent at subdivision 4 (Eq. 9-10 operators)."""
     a, c = 4.0, 6.0
     V, T = inputs.icosphere(4)
     X = V * np.array([a, a, c])
@@ -145,7 +145,7 @@ def test_bending_spheroid_curvatures():
 
 
 def test_bending_force_descends_energy():
-    """Sign pin of Eq. 8: on a perturbed sphere the nodal bending force points down the gradient of the
+    """Sign pin of Eq. 10: on a perturbed sphere the nodal bending force points down the gradient of the
     discrete Helfrich energy E = kB/2 sum (2H)^2 A (cosine > 0.9), and it vanishes in net translation to
     discretisation accuracy."""
     V, T = inputs.icosphere(2)
@@ -158,7 +158,7 @@ def test_bending_force_descends_energy():
 
 
 def test_bending_force_density_spheroid():
-    """Eq. 8 force density on a spheroid against its closed form: on a surface of revolution r(t), z(t)
+    """Eq. 10 force density on a spheroid against its closed form: on a surface of revolution r(t), z(t)
     the Laplace-Beltrami operator is (1/(r g)) d/dt (r/g dH/dt), g = |d(r,z)/dt|.  The cotangent Laplacian of
     a discrete H is noisy node by node on a non-uniform mesh, so the pin is on its scale (least-squares
     factor against the closed form within 5 %) and on area-weighted latitude-band averages (within 10 %)
