@@ -18,8 +18,8 @@
  *   - Streams: every kernel runs on the caller's CUDA stream given to scbb_create.  Calls that return
  *     host data synchronise that stream; scbb_step does not.
  *   - Errors: every call returns a scbb_status; nothing throws across the ABI.  scbb_last_error() gives a
- *     one-line description of the last failure on a context.  A device-side error (non-finite density or
- *     |u| > 0.1) is recorded in a device word and reported by the next synchronising call as
+ *     one-line description of the last failure on a context.  A device-side error (non-finite or
+ *     non-positive density, or |u| > 0.3) is recorded in a device word and reported by the next synchronising call as
  *     SCBB_E_UNSTABLE; after it, calls other than scbb_destroy return SCBB_E_STATE.
  *   - A NULL context, NULL required pointer, or out-of-range parameter gives SCBB_E_INVAL and changes
  *     nothing.
@@ -42,7 +42,7 @@ typedef enum {
     SCBB_E_INVAL = 1,        /* bad argument */
     SCBB_E_CUDA = 2,         /* a CUDA runtime call failed */
     SCBB_E_NOMEM = 3,        /* workspace smaller than scbb_workspace_bytes() */
-    SCBB_E_UNSTABLE = 4,     /* non-finite density or Mach guard |u| > 0.1 tripped on the device */
+    SCBB_E_UNSTABLE = 4,     /* non-finite density or Mach guard |u| > 0.3 tripped on the device */
     SCBB_E_TIMEOUT = 5,      /* a bounded device wait gave up */
     SCBB_E_MESH = 6,         /* invalid mesh (index out of range, zero-area reference triangle, ...) */
     SCBB_E_STATE = 7,        /* context is in an error state */

@@ -22,122 +22,153 @@ __device__ __forceinline__ float3 crossf(float3 a, float3 b) {
 
 // ------------------------------------------------------------------------------------------------------
 // FP64 capsule reductions: enclosed volume (relative to the capsule's first vertex, which leaves the closed
-// sum unchanged but keeps the FP32 inputs small) and centre of mass.  One block per capsule, fixed order.
+// sum unchanged but keeps the FP32 triple products small) and centre of mass.  The per-triangle terms are
+// FP32, the sums FP64 (GB300's FP64 rate is low, so only the accumulation is double).  Fixed order.
 // ------------------------------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
 constexpr int CAP_THREADS = 256;
 
-__global__ void __launch_bounds__(CAP_THREADS) k_capsule_reduce(DevState d) {
+// Volume terms come from the triangle pass (tvol), so the reduction is a plain FP64 sum.
+__global__ void __launch_bounds__(CAP_THREADS) k_capsule_reduce(DevState d, int use_tvol) {
+    __shared__ double sh[4 * 32];
     const int m = blockIdx.x;
     const CapDev c = d.cap[m];
-    const float3 r0 = ld3(d.X[c.v0]);
-    double vol = 0, cx = 0, cy = 0, cz = 0;
-    for (int t = threadIdx.x; t < c.nt; t += blockDim.x) {
-        const int4 T = d.tri[c.t0 + t];
-        const float3 a = ld3(d.X[T.x]) - r0, b = ld3(d.X[T.y]) - r0, e = ld3(d.X[T.z]) - r0;
-        const double ax = a.x, ay = a.y, az = a.z, bx = b.x, by = b.y, bz = b.z, ex = e.x, ey = e.y, ez = e.z;
-        vol += (ax * (by * ez - bz * ey) + ay * (bz * ex - bx * ez) + az * (bx * ey - by * ex)) / 6.0;
+    double acc[4] = {0, 0, 0, 0};
+    if (use_tvol) {
+        for (int t = threadIdx.x; t < c.nt; t += blockDim.x) acc[0] += (double)d.tvol[c.t0 + t];
+    } else {
+        const float3 r0 = ld3(d.X[c.v0]);
+        for (int t = threadIdx.x; t < c.nt; t += blockDim.x) {
+            const int4 T = d.tri[c.t0 + t];
+            const float3 a = ld3(d.X[T.x]) - r0, b = ld3(d.X[T.y]) - r0, e = ld3(d.X[T.z]) - r0;
+            acc[0] += (double)(dotf(a, crossf(b, e)) * (1.f / 6.f));
+        }
     }
     for (int v = threadIdx.x; v < c.nv; v += blockDim.x) {
-        const float4 p = d.X[c.v0 + v];
-        cx += p.x; cy += p.y; cz += p.z;
+        const float4 q = d.X[c.v0 + v];
+        acc[1] += q.x; acc[2] += q.y; acc[3] += q.z;
     }
-    __shared__ double sh[4][CAP_THREADS];
-    sh[0][threadIdx.x] = vol; sh[1][threadIdx.x] = cx; sh[2][threadIdx.x] = cy; sh[3][threadIdx.x] = cz;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const double s = warp_sum(acc[k]);
+        if (lane == 0) sh[k * 32 + w] = s;
+    }
     __syncthreads();
-    for (int s = CAP_THREADS / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int q = 0; q < 4; q++) sh[q][threadIdx.x] += sh[q][threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        d.cap_red[4 * m + 0] = sh[0][0];
-        d.cap_red[4 * m + 1] = sh[1][0] / c.nv;
-        d.cap_red[4 * m + 2] = sh[2][0] / c.nv;
-        d.cap_red[4 * m + 3] = sh[3][0] / c.nv;
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const double s = warp_sum(lane < nw ? sh[k * 32 + lane] : 0.0);
+            if (lane == 0) d.cap_red[4 * m + k] = k == 0 ? s : s / c.nv;
+        }
     }
 }
 
 void launch_capsule_reduce(const DevState& d, cudaStream_t st) {
-    if (d.NM > 0) k_capsule_reduce<<<d.NM, CAP_THREADS, 0, st>>>(d);
+    if (d.NM > 0) k_capsule_reduce<<<d.NM, CAP_THREADS, 0, st>>>(d, 0);
 }
 
 // ------------------------------------------------------------------------------------------------------
-// Pass 1 (per vertex): Skalak force, volume gradient, and the Meyer quantities mixed area A, unit normal n,
-// mean curvature H = (K . n)/2 with K = (1/2A) sum (cot a + cot b)(x_i - x_j), Gaussian curvature
-// KG = (2 pi - sum of angles)/A.
+// Membrane forces in three grid-parallel passes plus the FP64 capsule reduction:
+//   triangle pass  Skalak force on each corner (Eq. 6; F = -dE/dx of Eq. 8 through the metric invariants
+//                  tr(g0^-1 g) and det g / det g0), volume gradient (x_j - r0) x (x_l - r0)/6 and volume
+//                  term, Meyer terms: angle, cotangents of the two other angles, mixed-area share, the
+//                  corner's share of the mean-curvature normal, face normal
+//   vertex pass 1  gather the corners of a vertex -> mixed area A, unit normal n, H = (K . n)/2 with
+//                  K = (1/2A) sum (cot a + cot b)(x_i - x_j), Gaussian curvature (2 pi - sum of angles)/A
+//   reduction      capsule volume and centre of mass (FP64)
+//   vertex pass 2  Laplace-Beltrami of H, bending force 2 kB [2H(H^2 - K) + Lap H] A n (Eq. 10), volume
+//                  force -kV (V - V0)/V0 dV/dx (Eq. 7-8), total elastic force
+// The vertex passes gather through a vertex -> corner CSR in a fixed order (no atomics, reproducible) and
+// prefetch a vertex's corner ids before the records, so each gather costs two or three dependent loads.
+// Corner c = 3 t + k of triangle t; cnb[c] holds the global ids of the two other corners (j, l).
 // ------------------------------------------------------------------------------------------------------
-struct Corner {
-    float3 xi, xj, xl;     // this vertex and the next two corners in counter-clockwise order
-    int j, l;
-};
-
-__device__ __forceinline__ Corner corner_of(const DevState& d, int e) {
-    const int t = e >> 2, k = e & 3;
+__global__ void k_mem_tri(DevState d) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= d.NT) return;
     const int4 T = d.tri[t];
-    const int id[3] = {T.x, T.y, T.z};
-    Corner c;
-    const int i = id[k];
-    c.j = id[(k + 1) % 3];
-    c.l = id[(k + 2) % 3];
-    c.xi = ld3(d.X[i]);
-    c.xj = ld3(d.X[c.j]);
-    c.xl = ld3(d.X[c.l]);
-    return c;
+    const CapDev cp = d.cap[T.w];
+    const float3 r0 = ld3(d.X[cp.v0]);
+    const float4 R = d.tref[t];                       // (ia, ib, ic, A0): inverse reference metric, area
+    const float3 P[3] = {ld3(d.X[T.x]), ld3(d.X[T.y]), ld3(d.X[T.z])};
+    const float3 e1 = P[1] - P[0], e2 = P[2] - P[0];
+    const float g11 = dotf(e1, e1), g12 = dotf(e1, e2), g22 = dotf(e2, e2);
+    const float idet0 = R.x * R.z - R.y * R.y;        // 1 / det(g0)
+    const float I1 = R.x * g11 + 2.f * R.y * g12 + R.z * g22 - 2.f;
+    const float I2 = (g11 * g22 - g12 * g12) * idet0 - 1.f;
+    const float pre = 0.25f * cp.kS * R.w;
+    const float d1 = pre * (2.f * I1 + 2.f), d2 = pre * (2.f * cp.C * I2 - 2.f);
+    const float W11 = d1 * R.x + d2 * g22 * idet0;
+    const float W12 = 2.f * d1 * R.y - 2.f * d2 * g12 * idet0;
+    const float W22 = d1 * R.z + d2 * g11 * idet0;
+    const float3 G1 = (2.f * W11) * e1 + W12 * e2;       // dE/de1
+    const float3 G2 = W12 * e1 + (2.f * W22) * e2;       // dE/de2
+    const float3 Fc[3] = {G1 + G2, -1.f * G1, -1.f * G2};
+    const float3 nrm = crossf(e1, e2);                   // 2 * area * outward unit normal
+    const float s2 = sqrtf(dotf(nrm, nrm));
+    const float area = 0.5f * s2;
+    float dots[3], cots[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const float3 a = P[(k + 1) % 3] - P[k], b = P[(k + 2) % 3] - P[k];
+        dots[k] = dotf(a, b);
+        cots[k] = dots[k] / s2;
+    }
+    const int obtuse = dots[0] < 0.f ? 0 : (dots[1] < 0.f ? 1 : (dots[2] < 0.f ? 2 : -1));
+    const float3 pa = P[0] - r0, pb = P[1] - r0, pc = P[2] - r0;
+    d.tvol[t] = dotf(pa, crossf(pb, pc)) * (1.f / 6.f);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const int j = (k + 1) % 3, l = (k + 2) % 3;
+        const float3 aij = P[j] - P[k], ail = P[l] - P[k];
+        // edge (i, j) is opposite corner l, edge (i, l) opposite corner j
+        const float3 K = (-cots[l]) * aij + (-cots[j]) * ail;
+        float Ash;
+        if (obtuse < 0) Ash = 0.125f * (cots[l] * dotf(aij, aij) + cots[j] * dotf(ail, ail));
+        else Ash = (obtuse == k) ? 0.5f * area : 0.25f * area;
+        const float th = atan2f(s2, dots[k]);
+        const float3 dv = (1.f / 6.f) * crossf(P[j] - r0, P[l] - r0);
+        float4* rec = d.corner + 4 * (3 * t + k);
+        rec[0] = make_float4(Fc[k].x, Fc[k].y, Fc[k].z, Ash);
+        rec[1] = make_float4(dv.x, dv.y, dv.z, th);
+        rec[2] = make_float4(K.x, K.y, K.z, 0.f);
+        rec[3] = make_float4(nrm.x, nrm.y, nrm.z, 0.f);
+        d.ccot[3 * t + k] = make_float2(cots[j], cots[l]);
+    }
 }
 
-__global__ void k_membrane_pass1(DevState d) {
+constexpr int GATHER = 8;      // corners fetched per round of a vertex gather
+
+__global__ void k_mem_vert1(DevState d) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.NV) return;
-    const CapDev cp = d.cap[d.vcap[i]];
-    const float3 r0 = ld3(d.X[cp.v0]);
-    float3 Fs = make_float3(0.f, 0.f, 0.f), dv = make_float3(0.f, 0.f, 0.f);
-    float3 K = make_float3(0.f, 0.f, 0.f), nn = make_float3(0.f, 0.f, 0.f);
+    float3 Fs = make_float3(0.f, 0.f, 0.f), dv = make_float3(0.f, 0.f, 0.f), K = make_float3(0.f, 0.f, 0.f);
+    float3 nn = make_float3(0.f, 0.f, 0.f);
     float A = 0.f, ang = 0.f;
-    for (int q = d.vt_off[i]; q < d.vt_off[i + 1]; q++) {
-        const int e = d.vt_idx[q];
-        const int t = e >> 2, k = e & 3;
-        const int4 T = d.tri[t];
-        const float4 R = d.tref[t];                   // (ia, ib, ic, A0): inverse reference metric, area
-        // ---- Skalak (Eq. 6) through the metric invariants; force on this corner = -dE/dx (Eq. 8)
-        const float3 pa = ld3(d.X[T.x]), pb = ld3(d.X[T.y]), pc = ld3(d.X[T.z]);
-        const float3 e1 = pb - pa, e2 = pc - pa;
-        const float g11 = dotf(e1, e1), g12 = dotf(e1, e2), g22 = dotf(e2, e2);
-        const float idet0 = R.x * R.z - R.y * R.y;    // 1 / det(g0)
-        const float I1 = R.x * g11 + 2.f * R.y * g12 + R.z * g22 - 2.f;
-        const float I2 = (g11 * g22 - g12 * g12) * idet0 - 1.f;
-        const float pre = 0.25f * cp.kS * R.w;
-        const float d1 = pre * (2.f * I1 + 2.f), d2 = pre * (2.f * cp.C * I2 - 2.f);
-        const float W11 = d1 * R.x + d2 * g22 * idet0;
-        const float W12 = 2.f * d1 * R.y - 2.f * d2 * g12 * idet0;
-        const float W22 = d1 * R.z + d2 * g11 * idet0;
-        const float3 G1 = (2.f * W11) * e1 + W12 * e2;   // dE/de1
-        const float3 G2 = W12 * e1 + (2.f * W22) * e2;   // dE/de2
-        if (k == 0) Fs = Fs + (G1 + G2);
-        else if (k == 1) Fs = Fs - G1;
-        else Fs = Fs - G2;
-        // ---- volume gradient dV/dx_i = (x_j - r0) x (x_l - r0) / 6
-        const Corner c = corner_of(d, e);
-        dv = dv + (1.f / 6.f) * crossf(c.xj - r0, c.xl - r0);
-        // ---- Meyer operators: angles at the three corners of this triangle
-        const float3 a_ij = c.xj - c.xi, a_il = c.xl - c.xi, a_jl = c.xl - c.xj;
-        const float3 nrm = crossf(a_ij, a_il);          // 2 * area * unit normal (outward)
-        const float s2 = sqrtf(dotf(nrm, nrm));         // |cross| = 2 area, same for every corner
-        const float dot_i = dotf(a_ij, a_il);
-        const float dot_j = -dotf(a_ij, a_jl);          // (x_i - x_j) . (x_l - x_j)
-        const float dot_l = dotf(a_il, a_jl);           // (x_i - x_l) . (x_j - x_l)
-        const float cot_j = dot_j / s2, cot_l = dot_l / s2;
-        const float th_i = atan2f(s2, dot_i);
-        const float area = 0.5f * s2;
-        // edge (i, j) is opposite corner l, edge (i, l) opposite corner j
-        K = K + cot_l * (c.xi - c.xj) + cot_j * (c.xi - c.xl);
-        ang += th_i;
-        nn = nn + nrm;
-        if (dot_i < 0.f) A += 0.5f * area;                       // obtuse at i
-        else if (dot_j < 0.f || dot_l < 0.f) A += 0.25f * area;  // obtuse elsewhere
-        else A += 0.125f * (cot_l * dotf(a_ij, a_ij) + cot_j * dotf(a_il, a_il));
+    const int q0 = d.vt_off[i], q1 = d.vt_off[i + 1];
+    for (int qb = q0; qb < q1; qb += GATHER) {
+        int cid[GATHER];
+#pragma unroll
+        for (int u = 0; u < GATHER; u++) cid[u] = qb + u < q1 ? d.vt_idx[qb + u] : -1;
+#pragma unroll
+        for (int u = 0; u < GATHER; u++) {
+            if (cid[u] < 0) continue;
+            const float4* rec = d.corner + 4 * cid[u];
+            const float4 a = rec[0], b = rec[1], c = rec[2], e = rec[3];
+            Fs = Fs + make_float3(a.x, a.y, a.z);
+            A += a.w;
+            dv = dv + make_float3(b.x, b.y, b.z);
+            ang += b.w;
+            K = K + make_float3(c.x, c.y, c.z);
+            nn = nn + make_float3(e.x, e.y, e.z);
+        }
     }
-    const float inl = rsqrtf(dotf(nn, nn));
-    nn = inl * nn;
+    nn = rsqrtf(dotf(nn, nn)) * nn;
     K = (0.5f / A) * K;
     const float H = 0.5f * dotf(K, nn);
     const float KG = (6.283185307179586f - ang) / A;
@@ -147,11 +178,7 @@ __global__ void k_membrane_pass1(DevState d) {
     d.AK[i] = make_float2(A, KG);
 }
 
-// ------------------------------------------------------------------------------------------------------
-// Pass 2 (per vertex): Laplace-Beltrami of H, bending force 2 kB [2H(H^2 - KG) + Lap H] A n (Eq. 10 times the
-// Voronoi area), volume force -kV (V - V0)/V0 dV/dx (Eq. 7-8), total elastic force.
-// ------------------------------------------------------------------------------------------------------
-__global__ void k_membrane_pass2(DevState d) {
+__global__ void k_mem_vert2(DevState d) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.NV) return;
     const int m = d.vcap[i];
@@ -159,29 +186,36 @@ __global__ void k_membrane_pass2(DevState d) {
     const float4 ni = d.nrm[i];
     const float Hi = ni.w;
     float lap = 0.f;
-    for (int q = d.vt_off[i]; q < d.vt_off[i + 1]; q++) {
-        const int e = d.vt_idx[q];
-        const Corner c = corner_of(d, e);
-        const float3 a_ij = c.xj - c.xi, a_il = c.xl - c.xi, a_jl = c.xl - c.xj;
-        const float3 nrm = crossf(a_ij, a_il);
-        const float s2 = sqrtf(dotf(nrm, nrm));
-        const float cot_j = -dotf(a_ij, a_jl) / s2, cot_l = dotf(a_il, a_jl) / s2;
-        lap += cot_l * (d.nrm[c.j].w - Hi) + cot_j * (d.nrm[c.l].w - Hi);
+    const int q0 = d.vt_off[i], q1 = d.vt_off[i + 1];
+    for (int qb = q0; qb < q1; qb += GATHER) {
+        int cid[GATHER];
+#pragma unroll
+        for (int u = 0; u < GATHER; u++) cid[u] = qb + u < q1 ? d.vt_idx[qb + u] : -1;
+#pragma unroll
+        for (int u = 0; u < GATHER; u++) {
+            if (cid[u] < 0) continue;
+            const int2 nb = d.cnb[cid[u]];
+            const float2 ct = d.ccot[cid[u]];          // (cot at j, cot at l)
+            // edge (i, j) carries the cotangent of the angle at l, edge (i, l) that at j
+            lap += ct.y * (d.nrm[nb.x].w - Hi) + ct.x * (d.nrm[nb.y].w - Hi);
+        }
     }
     const float2 AK = d.AK[i];
     lap *= 0.5f / AK.x;
     const float fb = 2.f * cp.kB * (2.f * Hi * (Hi * Hi - AK.y) + lap) * AK.x;
     const float kv = (float)(-(double)cp.kV * (d.cap_red[4 * m] - cp.V0) / cp.V0);
-    const float4 fs = d.Fsk[i], dv = d.dV[i];
-    d.F[i] = make_float4(fs.x + fb * ni.x + kv * dv.x, fs.y + fb * ni.y + kv * dv.y, fs.z + fb * ni.z + kv * dv.z,
-                         0.f);
+    const float4 fs = d.Fsk[i], dvv = d.dV[i];
+    d.F[i] = make_float4(fs.x + fb * ni.x + kv * dvv.x, fs.y + fb * ni.y + kv * dvv.y,
+                         fs.z + fb * ni.z + kv * dvv.z, 0.f);
 }
 
 void launch_membrane_forces(const DevState& d, cudaStream_t st) {
-    if (d.NV == 0) return;
+    if (d.NM == 0) return;
     const int b = 128;
-    k_membrane_pass1<<<(d.NV + b - 1) / b, b, 0, st>>>(d);
-    k_membrane_pass2<<<(d.NV + b - 1) / b, b, 0, st>>>(d);
+    k_mem_tri<<<(d.NT + b - 1) / b, b, 0, st>>>(d);
+    k_mem_vert1<<<(d.NV + b - 1) / b, b, 0, st>>>(d);
+    k_capsule_reduce<<<d.NM, CAP_THREADS, 0, st>>>(d, 1);
+    k_mem_vert2<<<(d.NV + b - 1) / b, b, 0, st>>>(d);
 }
 
 // ------------------------------------------------------------------------------------------------------

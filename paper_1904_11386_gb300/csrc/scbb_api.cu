@@ -128,6 +128,10 @@ size_t layout(const scbb_lattice* lat, const scbb_fluid* fl, int nm, const scbb_
     t.vcap = c.take<int>(nv1);
     t.cap = c.take<CapDev>(nm > 0 ? nm : 1);
     t.cap_red = c.take<double>(4 * (nm > 0 ? nm : 1));
+    t.corner = c.take<float4>(12 * nt1);
+    t.ccot = c.take<float2>(3 * nt1);
+    t.tvol = c.take<float>(nt1);
+    t.cnb = c.take<int2>(3 * nt1);
     if (d) *d = t;
     return (c.off + ALIGN - 1) / ALIGN * ALIGN;
 }
@@ -179,7 +183,7 @@ scbb_status check_device_error(scbb_ctx* c) {
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
     if (h) {
         c->broken = 1;
-        return fail(c, SCBB_E_UNSTABLE, "device error word %d after %lld steps (non-finite density or |u| > 0.1)",
+        return fail(c, SCBB_E_UNSTABLE, "device error word %d after %lld steps (non-finite density or |u| > 0.3)",
                     h, c->steps);
     }
     return SCBB_OK;
@@ -224,6 +228,7 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
     std::vector<int4> tri(NT > 0 ? NT : 1);
     std::vector<float4> tref(NT > 0 ? NT : 1);
     std::vector<int> vcap(NV > 0 ? NV : 1), cnt(NV + 1, 0), vt_idx(3 * (NT > 0 ? NT : 1));
+    std::vector<int2> cnb(3 * (NT > 0 ? NT : 1));
     std::vector<CapDev> caps(n_mesh > 0 ? n_mesh : 1);
     c->X0.assign(NV > 0 ? NV : 1, make_float4(0, 0, 0, 0));
     int v0 = 0, t0 = 0;
@@ -267,13 +272,17 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
         std::vector<int> fill(cnt.begin(), cnt.end() - 1);
         for (int t = 0; t < NT; t++) {
             const int id[3] = {tri[t].x, tri[t].y, tri[t].z};
-            for (int k = 0; k < 3; k++) vt_idx[fill[id[k]]++] = 4 * t + k;
+            for (int k = 0; k < 3; k++) {
+                vt_idx[fill[id[k]]++] = 3 * t + k;
+                cnb[3 * t + k] = make_int2(id[(k + 1) % 3], id[(k + 2) % 3]);
+            }
         }
     }
     if (NT > 0) {
         CUDA_TRY(c, cudaMemcpyAsync(d.tri, tri.data(), sizeof(int4) * NT, cudaMemcpyHostToDevice, c->st));
         CUDA_TRY(c, cudaMemcpyAsync(d.tref, tref.data(), sizeof(float4) * NT, cudaMemcpyHostToDevice, c->st));
         CUDA_TRY(c, cudaMemcpyAsync(d.vt_idx, vt_idx.data(), sizeof(int) * 3 * NT, cudaMemcpyHostToDevice, c->st));
+        CUDA_TRY(c, cudaMemcpyAsync(d.cnb, cnb.data(), sizeof(int2) * 3 * NT, cudaMemcpyHostToDevice, c->st));
     }
     if (NV > 0) {
         CUDA_TRY(c, cudaMemcpyAsync(d.vt_off, cnt.data(), sizeof(int) * (NV + 1), cudaMemcpyHostToDevice, c->st));
@@ -337,10 +346,9 @@ scbb_status scbb_step(scbb_ctx* c, long long n) {
     const bool ibm = c->fl.coupling == 1 && c->d.NV > 0;
     for (long long s = 0; s < n; s++) {
         if (ibm) {
-            launch_capsule_reduce(c->d, c->st);
             launch_membrane_forces(c->d, c->st);
             launch_ibm_spread(c->lp, c->d, c->st);
-            c->launches += 4;
+            c->launches += 5;
         }
         if (c->lp.walls) {
             launch_wall_ghost(c->lp, c->d.S[c->cur], c->d.wall_rho, c->d.ghost, c->st);

@@ -77,10 +77,14 @@ struct DevState {
     int4* tri;              // [NT] a, b, c, capsule
     float4* tref;           // [NT] inverse reference metric (ia, ib, ic) and reference area A0
     int* vt_off;            // [NV+1] vertex -> incident triangle CSR
-    int* vt_idx;            // [3 NT] entries 4 * t + corner
+    int* vt_idx;            // [3 NT] corner ids 3 * t + k of the triangles around each vertex
     int* vcap;              // [NV] capsule of each vertex
     CapDev* cap;            // [NM]
     double* cap_red;        // [NM][4] volume, centre of mass
+    float4* corner;         // [3 NT][4] per-corner records of the membrane triangle pass (scratch)
+    float2* ccot;           // [3 NT] cotangents of the angles at the two other corners j, l (scratch)
+    float* tvol;            // [NT] volume term of each triangle (scratch)
+    int2* cnb;              // [3 NT] global ids of the two other corners j, l (topology)
     float4* X0;             // [NV] initial shape (for resets)
 };
 

@@ -118,8 +118,8 @@ class Problem:
         """Initial rho^A, rho^B as float64 arrays of shape (nz, ny, nx) (x fastest).
 
         Lower fluid (z < z_interface) is A-rich (rho_maj / rho_min), the upper fluid mirrored; a droplet is
-        B-rich inside; capsule interiors take the lower fluid's composition (paper Sec. III, common
-        parameters).  Wall planes carry the adjacent fluid's composition (never used as fluid).  Noise
+        B-rich inside; under bounce-back coupling capsule interiors take the lower fluid's composition
+        (paper Sec. III, common parameters).  Wall planes carry the adjacent fluid's composition (never used as fluid).  Noise
         U[-noise, noise] per component per node from PCG64(seed).
         """
         nz, ny, nx = self.nz, self.ny, self.nx
@@ -134,7 +134,9 @@ class Problem:
             d = np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2)
             ins = d < R
             a[ins], b[ins] = self.rho_min, self.rho_maj
-        for cap in self.capsules:
+        # Capsule interiors are separate fluid volumes only under bounce-back; an immersed-boundary membrane
+        # is permeable, so there the fluid is left continuous across it.
+        for cap in (self.capsules if self.coupling == 0 else []):
             cx, cy, cz = cap.centre
             d = np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2)
             ins = d < cap.radius
