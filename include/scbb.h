@@ -143,6 +143,24 @@ long long scbb_launch_count(const scbb_ctx* ctx);
 scbb_status scbb_enable_timing(scbb_ctx* ctx, int on);
 scbb_status scbb_kernel_time(scbb_ctx* ctx, double* ms, long long* launches);
 
+/* FP64 mass and momentum of populations already on the device, for callers that cannot allocate device
+ * memory (code running while a CUDA graph is captured, or inside a framework that owns the device
+ * allocator).  The paper has no counterpart; this is a utility of this library.
+ *   dev_f   device pointer, FP32 post-streaming populations in the layout f[c][i][x + nx*(y + ny*z)] (c = 0, 1;
+ *           i in the D3Q19 order of scbb_get_populations), 2*19*nx*ny*nz floats, caller-owned, read only
+ *   walls   1: the planes z = 0 and z = nz-1 are wall nodes and are left out of the sums; 0: all nodes
+ *   out5    host double[5]: mass of component A, mass of component B, total momentum x, y, z
+ * Allocates nothing: its scratch is a fixed file-scope device array of 512 x 5 partial sums plus 5 results
+ * (about 20 KB, held on every GPU that loads the library until exit).  Inputs with more than
+ * SCBB_NOALLOC_MAX_NODES nodes are rejected with SCBB_E_INVAL.  The first call on a device looks up the
+ * array's device address once (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Runs on cuda_stream (NULL = legacy default) and synchronises it.  All calls share the one scratch array
+ * (every call overwrites all of it), so calls that overlap on the GPU, from several streams or threads,
+ * race and must be serialised by the caller. */
+#define SCBB_NOALLOC_MAX_NODES 50000000
+scbb_status scbb_population_moments_noalloc(const float* dev_f, int nx, int ny, int nz, int walls, double* out5,
+                                            void* cuda_stream);
+
 const char* scbb_last_error(const scbb_ctx* ctx);
 
 /* Releases host-side state.  The workspace stays owned by the caller. */

@@ -19,7 +19,8 @@ STATUS = {0: "SCBB_OK", 1: "SCBB_E_INVAL", 2: "SCBB_E_CUDA", 3: "SCBB_E_NOMEM", 
 
 EXPORTS = ["scbb_workspace_bytes", "scbb_create", "scbb_set_density", "scbb_step", "scbb_sync",
            "scbb_get_fields", "scbb_get_populations", "scbb_get_vertices", "scbb_get_diag",
-           "scbb_launch_count", "scbb_enable_timing", "scbb_kernel_time", "scbb_last_error", "scbb_destroy"]
+           "scbb_launch_count", "scbb_enable_timing", "scbb_kernel_time", "scbb_population_moments_noalloc",
+           "scbb_last_error", "scbb_destroy"]
 
 
 class scbb_lattice(C.Structure):
@@ -80,6 +81,8 @@ def load(path: str = LIB_PATH):
     L.scbb_enable_timing.argtypes = [vp, C.c_int]
     L.scbb_kernel_time.restype = C.c_int
     L.scbb_kernel_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+    L.scbb_population_moments_noalloc.restype = C.c_int
+    L.scbb_population_moments_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
     L.scbb_last_error.restype = C.c_char_p
     L.scbb_last_error.argtypes = [vp]
     L.scbb_destroy.restype = None
@@ -110,6 +113,25 @@ def fluid_of(prob) -> scbb_fluid:
     fl.pp_eps, fl.pp_d0 = prob.pp_eps, prob.pp_d0
     fl.storage = 0
     return fl
+
+
+def scbb_population_moments_noalloc(f_dev, nx, ny, nz, walls, stream=None):
+    """FP64 (mass A, mass B, momentum x, y, z) of device populations f[c][i][node] (a float32 CUDA tensor of
+    2*19*nx*ny*nz elements), computed without any device allocation.  Returns a numpy array of 5."""
+    import torch
+
+    if not (f_dev.is_cuda and f_dev.dtype == torch.float32 and f_dev.is_contiguous()):
+        raise ScbbError("f_dev must be a contiguous float32 CUDA tensor")
+    if f_dev.numel() != 2 * 19 * nx * ny * nz:
+        raise ScbbError("f_dev has the wrong size")
+    L = load()
+    out = np.zeros(5)
+    st = (stream or torch.cuda.current_stream(f_dev.device)).cuda_stream
+    rc = L.scbb_population_moments_noalloc(C.c_void_p(f_dev.data_ptr()), nx, ny, nz, int(walls), _p(out),
+                                           C.c_void_p(st))
+    if rc != SCBB_OK:
+        raise ScbbError(f"scbb_population_moments_noalloc: {STATUS.get(rc, rc)}")
+    return out
 
 
 class Sim:
