@@ -86,6 +86,22 @@ def lib():
         L.o_ibm_interp.argtypes = [C.c_void_p, _dp, _dp]
         L.o_feq.restype = C.c_double
         L.o_feq.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double]
+        L.o_fresh_count.restype = C.c_long
+        L.o_fresh_count.argtypes = [C.c_void_p]
+        L.o_fresh_fallbacks.restype = C.c_long
+        L.o_fresh_fallbacks.argtypes = [C.c_void_p]
+        L.o_get_owner_old.argtypes = [C.c_void_p, _u16p]
+        L.o_set_owner.argtypes = [C.c_void_p, _u16p]
+        L.o_crossed_element.restype = C.c_int
+        L.o_crossed_element.argtypes = [C.c_void_p, C.c_int, C.c_long, C.c_int]
+        L.o_inside.restype = C.c_int
+        L.o_inside.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]
+        L.o_classify.argtypes = [C.c_void_p]
+        L.o_get_elem_acc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.o_element_fallbacks.restype = C.c_long
+        L.o_element_fallbacks.argtypes = [C.c_void_p]
+        L.o_boundary_count.restype = C.c_long
+        L.o_boundary_count.argtypes = [C.c_void_p]
         L.o_num_threads.restype = C.c_int
         L.o_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -246,6 +262,24 @@ class OracleSim:
         o = np.zeros(self.N, np.uint16)
         lib().o_get_owner(self.h, o)
         return o.reshape(self.prob.nz, self.prob.ny, self.prob.nx)
+
+    def fresh_count(self):
+        return lib().o_fresh_count(self.h), lib().o_fresh_fallbacks(self.h)
+
+    def boundary_count(self):
+        return lib().o_boundary_count(self.h), lib().o_element_fallbacks(self.h)
+
+    def crossed_element(self, cap, node, i):
+        return lib().o_crossed_element(self.h, cap, node, i)
+
+    def inside(self, cap, x, y, z):
+        return lib().o_inside(self.h, cap, x, y, z)
+
+    def elem_acc(self):
+        NT = sum(len(t) for t in self.tris)
+        now, prev, pend = np.zeros(3 * NT), np.zeros(3 * NT), np.zeros(3 * NT)
+        lib().o_get_elem_acc(self.h, _ptr(now), _ptr(prev), _ptr(pend))
+        return now.reshape(NT, 3), prev.reshape(NT, 3), pend.reshape(NT, 3)
 
     def capsule(self, m):
         v = C.c_double(0)

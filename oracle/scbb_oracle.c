@@ -116,6 +116,12 @@ typedef struct {
     double M0[2];
     double Vsys;
     long n_fresh_total, n_fresh_fallback;
+    /* boundary table rebuilt after each classification: node -> row, row -> crossed element per direction */
+    int* brow;              /* [N] row of a boundary node, -1 otherwise */
+    int* belem;             /* [rows][19] crossed element of each cut membrane link, -1 if not cut */
+    long nb, nb_cap;
+    long n_elem_fallback;
+    double* blink;          /* [rows][19][6] per cut link: exchanged momentum (0..2), SC reaction (3..5) */
     long step;
 } osim;
 
@@ -213,7 +219,7 @@ void o_destroy(osim* s) {
     free(s->f); free(s->fn); free(s->rho); free(s->psi); free(s->u); free(s->Fibm); free(s->Fsc);
     free(s->owner); free(s->owner_old); free(s->mp); free(s->voff); free(s->toff); free(s->tri);
     free(s->X); free(s->Vel); free(s->F); free(s->refX); free(s->V0);
-    free(s->emom_now); free(s->emom_prev); free(s->epend);
+    free(s->emom_now); free(s->emom_prev); free(s->epend); free(s->brow); free(s->belem); free(s->blink);
     free(s);
 }
 
@@ -799,6 +805,8 @@ static void fluid_step(osim* s) {
 /* One time step                                                                                         */
 /* ---------------------------------------------------------------------------------------------------- */
 static void bb_prepare(osim* s);
+static void bb_before_fluid(osim* s);
+static void bb_collect(osim* s);
 static void bb_after_fluid(osim* s);
 
 static void ibm_step(osim* s) {
@@ -830,7 +838,9 @@ void o_init(osim* s) {
 void o_step(osim* s, int n) {
     for (int k = 0; k < n; k++) {
         if (s->p.coupling == 0) {
+            bb_before_fluid(s);
             fluid_step(s);
+            bb_collect(s);
             bb_after_fluid(s);
         } else {
             ibm_step(s);

@@ -1,13 +1,510 @@
-/* Bounce-back coupling part of the oracle (Sec. II.C-II.E).  Included by scbb_oracle.c. */
+/*
+ * Bounce-back coupling part of the FP64 oracle (Sec. II.C-II.E).  Included by scbb_oracle.c.
+ * TEST INFRASTRUCTURE ONLY (see scbb_oracle.c).
+ *
+ * Readings of the paper used here (the paper gives the rules but not every detail):
+ *  - Classification: a lattice node is inside capsule k when a ray from the node in +z crosses capsule k's
+ *    surface an odd number of times.  The ray starts at (x + EPSX, y + EPSY, z + EPSZ) with tiny fixed
+ *    offsets so that no ray passes exactly through a vertex or an edge, and a crossing counts when the
+ *    offset column point lies strictly inside the triangle's xy projection and the triangle's height there
+ *    is above the start point.
+ *  - A link (x, x + c_i) is cut when the two nodes have different owners (Sec. II.C: populations that
+ *    cross a boundary element are bounced back).  Its element is the triangle the segment between the two
+ *    offset points (node + (EPSX, EPSY, EPSZ)) intersects (Moller-Trumbore); with several hits, the one
+ *    nearest to the node of lower linear index; with none (round-off), the triangle whose centroid is
+ *    nearest to the link midpoint; ties go to the lower index.
+ *  - Moving half-way bounce-back (Eq. 11) with the element velocity v0 = mean of its three node velocities
+ *    (Sec. II.C); c_i points from the fluid node into the boundary: f_opp(i)(x, t+1) = f*_i(x, t)
+ *    - 2 w_i rho^c(x) c_i . v0 / cs^2.  Momentum handed to the element (Eq. 12): (f*_i + f_opp(i)) c_i.
+ *    The exchanged momentum is spread over two consecutive steps, half each (Sec. II.C, last paragraph),
+ *    and homogeneously over the element's three nodes.
+ *  - Shan-Chen across a cut link (Eq. 14): the density seen at the node y = x + c_i on the other side is
+ *    the mean of rho over the neighbours of y that lie on x's side (not walls); the particle colour adds
+ *    rho_virtual = 2 |colour| (rho_maj - rho_min) (Eq. 15) to component A if colour > 0, to B if < 0.
+ *    The reaction +psi^c(x) G w_i psi^{c'}(virtual) c_i goes to the crossed element (momentum balance).
+ *  - Fresh nodes (Sec. II.E): nodes whose owner changed.  rho^c = mean over the non-fresh neighbours on
+ *    the new side (Eq. 16), times the mass correction of Eq. 18 with Delta rho^c read as the global mass
+ *    error M^c(t) - M^c(0), V_sys = number of fluid nodes, rho_init^c = M^c(0)/V_sys, clamped to the
+ *    neighbours' min/max; velocity = mean of the nearest element's node velocities (Eq. 17); populations
+ *    = f_eq(rho_fresh, v).  The element gets (removed - created) momentum.  If no non-fresh neighbour is on
+ *    the new side, fresh neighbours are used; with none at all the node keeps its populations.
+ *  - Sub-step order of one time step: fluid (collide, Shan-Chen with virtual densities, stream with
+ *    bounce-back) -> membrane forces at X(t) plus coupling -> node update -> classification at X(t+1) ->
+ *    fresh nodes.
+ *  - Node update (Sec. II.B, "forward Euler"): V(t+1) = V(t) + F(t)/m, then X(t+1) = X(t) + V(t+1).  The
+ *    velocity-first (semi-implicit) order is the one that is stable at the paper's parameters: with
+ *    kappa_V = 20 and node mass 5 the volume mode has omega^2 ~ 1 per step, which the position-first
+ *    order amplifies every step even with the fluid's damping.
+ */
 
+#define EPSX 1.37e-4
+#define EPSY 2.91e-4
+#define EPSZ 3.53e-4
+
+/* ray parity of capsule m at lattice node (x, y, z) */
+static int o_inside_capsule(const osim* s, int m, int x, int y, int z) {
+    const double px = x + EPSX, py = y + EPSY, pz = z + EPSZ;
+    int cnt = 0;
+    for (int t = s->toff[m]; t < s->toff[m + 1]; t++) {
+        const double* a = s->X + 3 * s->tri[3 * t];
+        const double* b = s->X + 3 * s->tri[3 * t + 1];
+        const double* c = s->X + 3 * s->tri[3 * t + 2];
+        /* quick rejection on the xy bounding box */
+        double xmin = fmin(a[0], fmin(b[0], c[0])), xmax = fmax(a[0], fmax(b[0], c[0]));
+        double ymin = fmin(a[1], fmin(b[1], c[1])), ymax = fmax(a[1], fmax(b[1], c[1]));
+        if (px < xmin || px > xmax || py < ymin || py > ymax) continue;
+        /* barycentric coordinates of (px, py) in the projected triangle */
+        double d = (b[0] - a[0]) * (c[1] - a[1]) - (c[0] - a[0]) * (b[1] - a[1]);
+        if (d == 0.0) continue;
+        double l1 = ((px - a[0]) * (c[1] - a[1]) - (c[0] - a[0]) * (py - a[1])) / d;
+        double l2 = ((b[0] - a[0]) * (py - a[1]) - (px - a[0]) * (b[1] - a[1])) / d;
+        double l0 = 1.0 - l1 - l2;
+        if (l0 <= 0.0 || l1 <= 0.0 || l2 <= 0.0) continue;
+        double zt = l0 * a[2] + l1 * b[2] + l2 * c[2];
+        if (zt > pz) cnt++;
+    }
+    return cnt & 1;
+}
+
+/* capsule bounding boxes (lattice index ranges, padded by 2) */
+static void capsule_bbox(const osim* s, int m, int lo[3], int hi[3]) {
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (int v = s->voff[m]; v < s->voff[m + 1]; v++)
+        for (int k = 0; k < 3; k++) {
+            mn[k] = fmin(mn[k], s->X[3 * v + k]);
+            mx[k] = fmax(mx[k], s->X[3 * v + k]);
+        }
+    const int L[3] = {s->p.nx, s->p.ny, s->p.nz};
+    for (int k = 0; k < 3; k++) {
+        lo[k] = (int)floor(fmax(mn[k], -1e6)) - 2;
+        hi[k] = (int)ceil(fmin(mx[k], 1e6)) + 2;
+        if (hi[k] - lo[k] >= L[k]) hi[k] = lo[k] + L[k] - 1;    /* never wider than the box */
+    }
+}
+
+/* heights at which the +z ray of column (xx, yy) crosses capsule m's triangles (same rule as
+   o_inside_capsule, evaluated once per column); returns the count, heights in zs[] (up to cap) */
+static int column_crossings(const osim* s, int m, int xx, int yy, double* zs, int cap) {
+    const double px = xx + EPSX, py = yy + EPSY;
+    int cnt = 0;
+    for (int t = s->toff[m]; t < s->toff[m + 1]; t++) {
+        const double* a = s->X + 3 * s->tri[3 * t];
+        const double* b = s->X + 3 * s->tri[3 * t + 1];
+        const double* c = s->X + 3 * s->tri[3 * t + 2];
+        double xmin = fmin(a[0], fmin(b[0], c[0])), xmax = fmax(a[0], fmax(b[0], c[0]));
+        double ymin = fmin(a[1], fmin(b[1], c[1])), ymax = fmax(a[1], fmax(b[1], c[1]));
+        if (px < xmin || px > xmax || py < ymin || py > ymax) continue;
+        double d = (b[0] - a[0]) * (c[1] - a[1]) - (c[0] - a[0]) * (b[1] - a[1]);
+        if (d == 0.0) continue;
+        double l1 = ((px - a[0]) * (c[1] - a[1]) - (c[0] - a[0]) * (py - a[1])) / d;
+        double l2 = ((b[0] - a[0]) * (py - a[1]) - (px - a[0]) * (b[1] - a[1])) / d;
+        double l0 = 1.0 - l1 - l2;
+        if (l0 <= 0.0 || l1 <= 0.0 || l2 <= 0.0) continue;
+        if (cnt < cap) zs[cnt] = l0 * a[2] + l1 * b[2] + l2 * c[2];
+        cnt++;
+    }
+    return cnt < cap ? cnt : cap;
+}
+
+/* owner field from the current vertex positions; walls keep OWNER_WALL.  Capsules do not overlap. */
+void o_classify(osim* s) {
+    long N = s->N;
+    for (long n = 0; n < N; n++)
+        if (s->owner[n] != OWNER_WALL) s->owner[n] = 0;
+    for (int m = 0; m < s->nm; m++) {
+        int lo[3], hi[3];
+        capsule_bbox(s, m, lo, hi);
+        int wx = hi[0] - lo[0] + 1, wy = hi[1] - lo[1] + 1;
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int col = 0; col < wx * wy; col++) {
+            int xx = lo[0] + col % wx, yy = lo[1] + col / wx;
+            double zs[256];
+            int nc = column_crossings(s, m, xx, yy, zs, 256);
+            if (nc == 0) continue;
+            int x = wrap(xx, s->p.nx), y = wrap(yy, s->p.ny);
+            for (int zz = lo[2]; zz <= hi[2]; zz++) {
+                if (s->p.walls && (zz < 1 || zz > s->p.nz - 2)) continue;
+                const double pz = zz + EPSZ;
+                int above = 0;
+                for (int k = 0; k < nc; k++) above += zs[k] > pz;
+                if (!(above & 1)) continue;
+                int zw = s->p.walls ? zz : wrap(zz, s->p.nz);
+                s->owner[IDX(s, x, y, zw)] = (uint16_t)(m + 1);
+            }
+        }
+    }
+}
+
+static int link_capsule(const osim* s, long n, long m);
+static int crossed_element(osim* s, int cap, long n, int i);
+
+/* boundary table: every fluid node with at least one cut membrane link, and the element each cut link
+   crosses (walls are not membrane links) */
+static void build_boundary_table(osim* s) {
+    long N = s->N;
+    if (!s->brow) s->brow = (int*)malloc(sizeof(int) * N);
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < N; n++) {
+        s->brow[n] = -1;
+        if (s->owner[n] == OWNER_WALL) continue;
+        int z = (int)(n / ((long)s->p.nx * s->p.ny));
+        int rem = (int)(n % ((long)s->p.nx * s->p.ny));
+        int y = rem / s->p.nx, x = rem % s->p.nx;
+        for (int i = 1; i < 19; i++) {
+            int zz;
+            long m = nbr(s, x, y, z, i, &zz);
+            if (m >= 0 && s->owner[m] != OWNER_WALL && s->owner[m] != s->owner[n]) { s->brow[n] = 0; break; }
+        }
+    }
+    s->nb = 0;
+    for (long n = 0; n < N; n++)
+        if (s->brow[n] == 0) s->brow[n] = (int)s->nb++;
+    if (s->nb > s->nb_cap) {
+        s->nb_cap = s->nb + 1024;
+        s->belem = (int*)realloc(s->belem, sizeof(int) * 19 * s->nb_cap);
+        s->blink = (double*)realloc(s->blink, sizeof(double) * 19 * 6 * s->nb_cap);
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long n = 0; n < N; n++) {
+        long r = s->brow[n];
+        if (r < 0) continue;
+        int z = (int)(n / ((long)s->p.nx * s->p.ny));
+        int rem = (int)(n % ((long)s->p.nx * s->p.ny));
+        int y = rem / s->p.nx, x = rem % s->p.nx;
+        for (int i = 0; i < 19; i++) {
+            s->belem[19 * r + i] = -1;
+            if (i == 0) continue;
+            int zz;
+            long m = nbr(s, x, y, z, i, &zz);
+            if (m < 0 || s->owner[m] == OWNER_WALL || s->owner[m] == s->owner[n]) continue;
+            s->belem[19 * r + i] = crossed_element(s, link_capsule(s, n, m), n, i);
+        }
+    }
+}
+
+static int table_element(const osim* s, long n, int i) { return s->belem[19 * (long)s->brow[n] + i]; }
+
+/* vertex average of capsule m (the reference point for choosing periodic images) */
+static void capsule_centroid(const osim* s, int m, double c[3]) {
+    c[0] = c[1] = c[2] = 0;
+    for (int v = s->voff[m]; v < s->voff[m + 1]; v++)
+        for (int k = 0; k < 3; k++) c[k] += s->X[3 * v + k];
+    for (int k = 0; k < 3; k++) c[k] /= (s->voff[m + 1] - s->voff[m]);
+}
+
+/* coordinates of node n in the periodic image nearest to ref (a point inside the capsule) */
+static void node_near(const osim* s, long n, const double* ref, double out[3]) {
+    int z = (int)(n / ((long)s->p.nx * s->p.ny));
+    int rem = (int)(n % ((long)s->p.nx * s->p.ny));
+    int y = rem / s->p.nx, x = rem % s->p.nx;
+    double p[3] = {x, y, z};
+    double L[3] = {s->p.nx, s->p.ny, s->p.nz};
+    int per[3] = {1, 1, !s->p.walls};
+    for (int k = 0; k < 3; k++) {
+        if (per[k]) p[k] -= L[k] * floor((p[k] - ref[k]) / L[k] + 0.5);
+        out[k] = p[k];
+    }
+}
+
+/* the element crossed by the link between nodes n and m = n + c_i (capsule cap) */
+static int crossed_element(osim* s, int cap, long n, int i) {
+    long a = n;
+    /* canonical orientation: from the node of lower linear index */
+    int zz;
+    int z = (int)(n / ((long)s->p.nx * s->p.ny));
+    int rem = (int)(n % ((long)s->p.nx * s->p.ny));
+    int y = rem / s->p.nx, x = rem % s->p.nx;
+    long m = nbr(s, x, y, z, i, &zz);
+    double ref[3];
+    capsule_centroid(s, cap, ref);
+    double P[3], Qp[3];
+    node_near(s, a, ref, P);
+    /* both ends carry the classification ray's offsets, so a cut link always crosses the surface */
+    P[0] += EPSX; P[1] += EPSY; P[2] += EPSZ;
+    for (int k = 0; k < 3; k++) Qp[k] = P[k] + (k == 0 ? CX[i] : (k == 1 ? CY[i] : CZ[i]));
+    if (m < a) {
+        double t3[3];
+        memcpy(t3, P, sizeof t3);
+        memcpy(P, Qp, sizeof t3);
+        memcpy(Qp, t3, sizeof t3);
+    }
+    double D[3] = {Qp[0] - P[0], Qp[1] - P[1], Qp[2] - P[2]};
+    int best = -1;
+    double bt = 1e300;
+    for (int t = s->toff[cap]; t < s->toff[cap + 1]; t++) {
+        const double* v0 = s->X + 3 * s->tri[3 * t];
+        const double* v1 = s->X + 3 * s->tri[3 * t + 1];
+        const double* v2 = s->X + 3 * s->tri[3 * t + 2];
+        int away = 0;          /* the segment's and the triangle's bounding boxes do not overlap */
+        for (int k = 0; k < 3; k++) {
+            double smin = fmin(P[k], Qp[k]), smax = fmax(P[k], Qp[k]);
+            if (fmax(v0[k], fmax(v1[k], v2[k])) < smin || fmin(v0[k], fmin(v1[k], v2[k])) > smax) away = 1;
+        }
+        if (away) continue;
+        double e1[3], e2[3], h[3], sv[3], q[3];
+        sub3(v1, v0, e1); sub3(v2, v0, e2);
+        cross3(D, e2, h);
+        double det = dot3(e1, h);
+        if (fabs(det) < 1e-300) continue;
+        double inv = 1.0 / det;
+        sub3(P, v0, sv);
+        double u = dot3(sv, h) * inv;
+        if (u < 0.0 || u > 1.0) continue;
+        cross3(sv, e1, q);
+        double v = dot3(D, q) * inv;
+        if (v < 0.0 || u + v > 1.0) continue;
+        double tt = dot3(e2, q) * inv;
+        if (tt < 0.0 || tt > 1.0) continue;
+        if (tt < bt) { bt = tt; best = t; }
+    }
+    if (best >= 0) return best;
+#pragma omp atomic
+    s->n_elem_fallback++;
+    /* fallback: nearest centroid to the link midpoint */
+    double mid[3] = {P[0] + 0.5 * D[0], P[1] + 0.5 * D[1], P[2] + 0.5 * D[2]};
+    double bd = 1e300;
+    for (int t = s->toff[cap]; t < s->toff[cap + 1]; t++) {
+        double c[3] = {0, 0, 0};
+        for (int k = 0; k < 3; k++)
+            for (int q = 0; q < 3; q++) c[q] += s->X[3 * s->tri[3 * t + k] + q] / 3.0;
+        double d2 = (c[0] - mid[0]) * (c[0] - mid[0]) + (c[1] - mid[1]) * (c[1] - mid[1]) +
+                    (c[2] - mid[2]) * (c[2] - mid[2]);
+        if (d2 < bd) { bd = d2; best = t; }
+    }
+    return best;
+}
+
+static int link_capsule(const osim* s, long n, long m) {
+    const int a = s->owner[n], b = s->owner[m];
+    return (a != 0 ? a : b) - 1;
+}
+
+static void elem_velocity(const osim* s, int e, double v[3]) {
+    for (int k = 0; k < 3; k++)
+        v[k] = (s->Vel[3 * s->tri[3 * e] + k] + s->Vel[3 * s->tri[3 * e + 1] + k] + s->Vel[3 * s->tri[3 * e + 2] + k]) / 3.0;
+}
+
+/* per-link record of the boundary table (one node's links are written by one thread only) */
+static double* link_rec(osim* s, long n, int i) { return s->blink + 6 * (19 * (long)s->brow[n] + i); }
+
+static void bb_before_fluid(osim* s) {
+    if (s->nb > 0) memset(s->blink, 0, sizeof(double) * 19 * 6 * s->nb);
+}
+
+/* element momenta from the link records, in the fixed order of the boundary table */
+static void bb_collect(osim* s) {
+    for (long r = 0; r < s->nb; r++)
+        for (int i = 1; i < 19; i++) {
+            int e = s->belem[19 * r + i];
+            if (e < 0) continue;
+            const double* q = s->blink + 6 * (19 * r + i);
+            for (int k = 0; k < 3; k++) {
+                s->emom_now[3 * e + k] += q[k];
+                s->epend[3 * e + k] += q[3 + k];
+            }
+        }
+}
+
+/* psi seen across the cut link (n, m = n + c_i) for component c_other; reaction to the element */
 static double bb_virtual_psi(osim* s, long n, int x, int y, int z, int i, long m, int c_other,
                              double* react_elem_out, int* elem_out) {
-    (void)n; (void)x; (void)y; (void)z; (void)i; (void)react_elem_out; (void)elem_out;
-    return psi_of(s, s->rho[c_other * s->N + m]);
+    (void)x; (void)y; (void)z; (void)react_elem_out; (void)elem_out;
+    int side = s->owner[n];
+    int zz;
+    int mz = (int)(m / ((long)s->p.nx * s->p.ny));
+    int mrem = (int)(m % ((long)s->p.nx * s->p.ny));
+    int my = mrem / s->p.nx, mx = mrem % s->p.nx;
+    double sum = 0;
+    int cnt = 0;
+    for (int k = 1; k < 19; k++) {
+        long q = nbr(s, mx, my, mz, k, &zz);
+        if (q < 0 || s->owner[q] == OWNER_WALL || s->owner[q] != side) continue;
+        sum += s->rho[c_other * s->N + q];
+        cnt++;
+    }
+    double rt = cnt ? sum / cnt : s->rho[c_other * s->N + n];
+    int cap = link_capsule(s, n, m);
+    double col = s->mp[cap].colour;
+    double rv = 2.0 * fabs(col) * (s->p.rho_maj - s->p.rho_min);
+    if ((col > 0 && c_other == 0) || (col < 0 && c_other == 1)) rt += rv;
+    double ps = psi_of(s, rt);
+    /* reaction on the element: + psi^c(n) G w_i psi^{c'}(virtual) c_i, c = the other component's partner */
+    int c = 1 - c_other;
+    int e = table_element(s, n, i);
+    (void)e;
+    double* q = link_rec(s, n, i);
+    const double a = s->psi[c * s->N + n] * s->p.G * W[i] * ps;
+    q[3] += a * CX[i]; q[4] += a * CY[i]; q[5] += a * CZ[i];
+    return ps;
 }
+
+/* moving half-way bounce-back on the membrane-cut link (n, m = n + c_i) for component c */
 static void bb_link(osim* s, long n, int x, int y, int z, int i, long m, int c, double fstar, double rho_c) {
-    (void)x; (void)y; (void)z; (void)rho_c; (void)n;
-    s->fn[(c * s->N + m) * 19 + i] = fstar;
+    (void)x; (void)y; (void)z;
+    int e = table_element(s, n, i);
+    double v0[3];
+    elem_velocity(s, e, v0);
+    double cu = CX[i] * v0[0] + CY[i] * v0[1] + CZ[i] * v0[2];
+    double fb = fstar - 2.0 * W[i] * rho_c * cu / CS2;
+    s->fn[(c * s->N + n) * 19 + OPP(i)] = fb;
+    double* q = link_rec(s, n, i);
+    q[0] += (fstar + fb) * CX[i]; q[1] += (fstar + fb) * CY[i]; q[2] += (fstar + fb) * CZ[i];
 }
-static void bb_prepare(osim* s) { (void)s; }
-static void bb_after_fluid(osim* s) { (void)s; }
+
+static void fluid_mass(osim* s, double M[2]) {
+    compute_rho(s);
+    M[0] = M[1] = 0;
+    for (long n = 0; n < s->N; n++)
+        if (s->owner[n] != OWNER_WALL) { M[0] += s->rho[n]; M[1] += s->rho[s->N + n]; }
+}
+
+static void bb_prepare(osim* s) {
+    o_classify(s);
+    build_boundary_table(s);
+    memcpy(s->owner_old, s->owner, sizeof(uint16_t) * s->N);
+    fluid_mass(s, s->M0);
+    s->Vsys = 0;
+    for (long n = 0; n < s->N; n++)
+        if (s->owner[n] != OWNER_WALL) s->Vsys += 1.0;
+    int NT = s->toff[s->nm];
+    memset(s->emom_now, 0, sizeof(double) * 3 * (NT > 0 ? NT : 1));
+    memset(s->emom_prev, 0, sizeof(double) * 3 * (NT > 0 ? NT : 1));
+    memset(s->epend, 0, sizeof(double) * 3 * (NT > 0 ? NT : 1));
+}
+
+/* nearest element (centroid) of capsule cap to node n */
+static int nearest_element(const osim* s, int cap, long n) {
+    double ref[3], p[3];
+    capsule_centroid(s, cap, ref);
+    node_near(s, n, ref, p);
+    int best = -1;
+    double bd = 1e300;
+    for (int t = s->toff[cap]; t < s->toff[cap + 1]; t++) {
+        double c[3] = {0, 0, 0};
+        for (int k = 0; k < 3; k++)
+            for (int q = 0; q < 3; q++) c[q] += s->X[3 * s->tri[3 * t + k] + q] / 3.0;
+        double d2 = (c[0] - p[0]) * (c[0] - p[0]) + (c[1] - p[1]) * (c[1] - p[1]) + (c[2] - p[2]) * (c[2] - p[2]);
+        if (d2 < bd) { bd = d2; best = t; }
+    }
+    return best;
+}
+
+/* after the fluid step: membrane forces with coupling, node update, classification, fresh nodes */
+static void bb_after_fluid(osim* s) {
+    int NV = s->voff[s->nm], NT = s->toff[s->nm];
+    /* ---- membrane forces at X(t) */
+    o_membrane_forces(s, s->F);
+    for (int t = 0; t < NT; t++) {
+        double fe[3];
+        for (int k = 0; k < 3; k++)
+            fe[k] = 0.5 * (s->emom_now[3 * t + k] + s->emom_prev[3 * t + k]) + s->epend[3 * t + k];
+        for (int c = 0; c < 3; c++)
+            for (int k = 0; k < 3; k++) s->F[3 * s->tri[3 * t + c] + k] += fe[k] / 3.0;
+    }
+    memcpy(s->emom_prev, s->emom_now, sizeof(double) * 3 * NT);
+    memset(s->emom_now, 0, sizeof(double) * 3 * NT);
+    memset(s->epend, 0, sizeof(double) * 3 * NT);
+    /* ---- node update: V(t+1) = V + F/m, X(t+1) = X + V(t+1) */
+    for (int m = 0; m < s->nm; m++)
+        for (int v = s->voff[m]; v < s->voff[m + 1]; v++)
+            for (int k = 0; k < 3; k++) {
+                s->Vel[3 * v + k] += s->F[3 * v + k] / s->mp[m].mass;
+                s->X[3 * v + k] += s->Vel[3 * v + k];
+            }
+    (void)NV;
+    /* ---- classification at X(t+1) and fresh nodes */
+    memcpy(s->owner_old, s->owner, sizeof(uint16_t) * s->N);
+    o_classify(s);
+    build_boundary_table(s);
+    double M[2];
+    fluid_mass(s, M);                     /* rho of f(t+1) before the fresh update; also fills s->rho */
+    long N = s->N;
+    uint8_t* fresh = (uint8_t*)calloc((size_t)N, 1);
+    long nf = 0;
+    for (long n = 0; n < N; n++)
+        if (s->owner[n] != OWNER_WALL && s->owner[n] != s->owner_old[n]) { fresh[n] = 1; nf++; }
+    if (nf == 0) { free(fresh); return; }
+    double rinit[2] = {s->M0[0] / s->Vsys, s->M0[1] / s->Vsys};
+    double corr[2];
+    for (int c = 0; c < 2; c++) {
+        double dM = M[c] - s->M0[c];
+        corr[c] = s->p.mass_correction ? 1.0 - s->p.C0 * (rinit[0] + rinit[1]) / rinit[c] * dM / s->Vsys : 1.0;
+    }
+    /* new populations are computed from the unmodified state, then written */
+    double* newf = (double*)calloc((size_t)nf * 38, sizeof(double));
+    long* idx = (long*)calloc((size_t)nf, sizeof(long));
+    int* keep = (int*)calloc((size_t)nf, sizeof(int));
+    long q = 0;
+    for (long n = 0; n < N; n++) {
+        if (!fresh[n]) continue;
+        idx[q] = n;
+        int z = (int)(n / ((long)s->p.nx * s->p.ny));
+        int rem = (int)(n % ((long)s->p.nx * s->p.ny));
+        int y = rem / s->p.nx, x = rem % s->p.nx;
+        int side = s->owner[n];
+        double rf[2];
+        int ok = 0;
+        for (int pass = 0; pass < 2 && !ok; pass++) {
+            double sum[2] = {0, 0}, mn[2] = {1e300, 1e300}, mx[2] = {-1e300, -1e300};
+            int cnt = 0;
+            for (int i = 1; i < 19; i++) {
+                int zz;
+                long m = nbr(s, x, y, z, i, &zz);
+                if (m < 0 || s->owner[m] == OWNER_WALL || s->owner[m] != side) continue;
+                if (pass == 0 && fresh[m]) continue;
+                for (int c = 0; c < 2; c++) {
+                    double r = s->rho[c * N + m];
+                    sum[c] += r; mn[c] = fmin(mn[c], r); mx[c] = fmax(mx[c], r);
+                }
+                cnt++;
+            }
+            if (cnt) {
+                for (int c = 0; c < 2; c++) {
+                    double r = sum[c] / cnt * corr[c];
+                    rf[c] = fmin(fmax(r, mn[c]), mx[c]);
+                }
+                ok = 1;
+            }
+        }
+        if (!ok) { keep[q] = 1; s->n_fresh_fallback++; q++; continue; }
+        int cap = (s->owner[n] != 0 ? s->owner[n] : s->owner_old[n]) - 1;
+        int e = nearest_element(s, cap, n);
+        double v[3];
+        elem_velocity(s, e, v);
+        double removed[3] = {0, 0, 0};
+        for (int c = 0; c < 2; c++)
+            for (int i = 0; i < 19; i++) {
+                double fi = s->f[(c * N + n) * 19 + i];
+                removed[0] += fi * CX[i]; removed[1] += fi * CY[i]; removed[2] += fi * CZ[i];
+                newf[q * 38 + c * 19 + i] = feq(i, rf[c], v);
+            }
+        double dp[3];
+        for (int k = 0; k < 3; k++) dp[k] = removed[k] - (rf[0] + rf[1]) * v[k];
+        for (int k = 0; k < 3; k++) s->epend[3 * e + k] += dp[k];
+        q++;
+    }
+    for (long k = 0; k < nf; k++) {
+        if (keep[k]) continue;
+        long n = idx[k];
+        for (int c = 0; c < 2; c++)
+            for (int i = 0; i < 19; i++) s->f[(c * N + n) * 19 + i] = newf[k * 38 + c * 19 + i];
+    }
+    s->n_fresh_total += nf;
+    free(newf); free(idx); free(keep); free(fresh);
+}
+
+/* diagnostics */
+long o_fresh_count(const osim* s) { return s->n_fresh_total; }
+long o_fresh_fallbacks(const osim* s) { return s->n_fresh_fallback; }
+void o_get_owner_old(const osim* s, uint16_t* out) { memcpy(out, s->owner_old, sizeof(uint16_t) * s->N); }
+void o_set_owner(osim* s, const uint16_t* in) { memcpy(s->owner, in, sizeof(uint16_t) * s->N); }
+int o_crossed_element(osim* s, int cap, long n, int i) { return crossed_element(s, cap, n, i); }
+long o_element_fallbacks(const osim* s) { return s->n_elem_fallback; }
+long o_boundary_count(const osim* s) { return s->nb; }
+int o_inside(const osim* s, int m, int x, int y, int z) { return o_inside_capsule(s, m, x, y, z); }
+void o_get_elem_acc(const osim* s, double* now, double* prev, double* pend) {
+    int NT = s->toff[s->nm];
+    if (now) memcpy(now, s->emom_now, sizeof(double) * 3 * NT);
+    if (prev) memcpy(prev, s->emom_prev, sizeof(double) * 3 * NT);
+    if (pend) memcpy(pend, s->epend, sizeof(double) * 3 * NT);
+}

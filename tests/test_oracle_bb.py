@@ -1,0 +1,136 @@
+"""Pins of the oracle's bounce-back coupling (Sec. II.C-II.E): classification, crossed elements, exact
+conservation laws of the moving half-way bounce-back with momentum exchange, the virtual-density wetting
+sign, and the fresh-node mass correction.  No GPU needed."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1904_11386_gb300 import inputs
+
+
+def _bb(nx=20, ny=20, nz=22, walls=0, caps=None, **kw):
+    base = dict(name="bb", nx=nx, ny=ny, nz=nz, walls=walls, coupling=0, psi_kind=0, noise=1e-3, seed=5,
+                capsules=caps if caps is not None else [])
+    base.update(kw)
+    return inputs.Problem(**base)
+
+
+def test_classification_matches_sphere():
+    """Lattice nodes farther than 0.05 from the sphere of radius R are inside the icosphere (s = 3, chord sag
+    below 0.012) exactly when they are inside the sphere."""
+    cap = inputs.Capsule(centre=(10.3, 9.7, 10.55), radius=6.0, subdiv=3)
+    s = O.OracleSim(_bb(caps=[cap]))
+    own = s.owner()
+    z, y, x = np.meshgrid(np.arange(22), np.arange(20), np.arange(20), indexing="ij")
+    d = np.sqrt((x - 10.3) ** 2 + (y - 9.7) ** 2 + (z - 10.55) ** 2)
+    far = np.abs(d - 6.0) > 0.05
+    assert np.all((own == 1)[far] == (d < 6.0)[far])
+
+
+def test_crossed_elements_are_intersected():
+    """Every cut link's element (Sec. II.C) is a triangle the link crosses (numpy Moller-Trumbore check on the
+    offset segment) and the nearest such crossing; no link needs the fallback."""
+    cap = inputs.Capsule(centre=(10.3, 9.7, 10.55), radius=5.0, subdiv=2)
+    s = O.OracleSim(_bb(caps=[cap]))
+    own = s.owner().ravel()
+    X, _, _ = s.vertices()
+    T = s.tris[0]
+    A, B, C = X[T[:, 0]], X[T[:, 1]], X[T[:, 2]]
+    c, _, _ = O.d3q19()
+    eps = np.array([1.37e-4, 2.91e-4, 3.53e-4])
+    checked = 0
+    for n in np.nonzero(own == 1)[0][::3]:
+        z, r = divmod(int(n), 400)
+        y, x = divmod(r, 20)
+        for i in range(1, 19):
+            m = (x + c[i, 0]) % 20 + 20 * ((y + c[i, 1]) % 20 + 20 * (z + c[i, 2]))
+            if own[m] == 1:
+                continue
+            P = np.array([x, y, z], float) + eps
+            Q = P + c[i]
+            if m < n:
+                P, Q = Q, P
+            D = Q - P
+            e1, e2 = B - A, C - A
+            h = np.cross(D, e2)
+            det = (e1 * h).sum(1)
+            det = np.where(det == 0, 1e-300, det)
+            sv = P - A
+            u = (sv * h).sum(1) / det
+            q = np.cross(sv, e1)
+            v = (q * D).sum(1) / det
+            t = (e2 * q).sum(1) / det
+            ok = (u >= 0) & (u <= 1) & (v >= 0) & (u + v <= 1) & (t >= 0) & (t <= 1)
+            assert ok.any()
+            best = np.nonzero(ok)[0][np.argmin(t[ok])]
+            assert s.crossed_element(0, int(n), i) == best
+            checked += 1
+    assert checked > 50
+    assert s.boundary_count()[1] == 0
+
+
+def test_mass_exact_for_resting_boundary():
+    """Collision and half-way bounce-back on a resting boundary conserve each component's mass exactly
+    (Eq. 1, 11): a capsule of huge node mass stays put, no node changes side, and the masses stay constant
+    to round-off even with different compositions inside and outside.  (A moving boundary carries the term
+    6 w_i (c_i . v0)(rho_in - rho_out) across each cut link, which Sec. II.E's correction handles.)"""
+    cap = inputs.Capsule(centre=(10.2, 10.1, 11.3), radius=5.0, subdiv=2, kS=0.05, kV=20.0, mass=1e12)
+    s = O.OracleSim(_bb(caps=[cap], walls=1, z_interface=11, noise=1e-4))
+    m0 = [s.mass(0), s.mass(1)]
+    s.step(15)
+    assert s.fresh_count()[0] == 0
+    for k in range(2):
+        assert abs(s.mass(k) - m0[k]) / m0[k] < 1e-13
+
+
+def test_momentum_conservation_with_exchange_smoothing_and_wetting():
+    """Total momentum -- fluid, membrane nodes (m V), the half of the last exchanged momentum that the
+    two-step smoothing still holds back, and the fresh-node momenta recorded at the end of the step (applied
+    to the membrane in the next step) -- is conserved to round-off in a periodic box: pins the signs of the
+    bounce-back term (Eq. 11), the exchanged momentum (Eq. 12), the Shan-Chen reaction on the element for
+    the virtual densities with a colour (Eq. 14-15), and the fresh-node momentum balance (Sec. II.E).
+    Bending is off (the Meyer force of Eq. 10 carries a small net force on irregular shapes)."""
+    cap = inputs.Capsule(centre=(10.2, 10.1, 9.6), radius=5.0, subdiv=2, kS=0.01, kB=0.0, kV=2.0, colour=0.3,
+                         deform=np.diag([1.1, 1.0 / 1.1, 1.0]))      # volume-preserving initial strain
+    s = O.OracleSim(_bb(caps=[cap], z_interface=10, noise=1e-3))
+
+    def total():
+        X, V, _ = s.vertices()
+        _, prev, pend = s.elem_acc()
+        return s.momentum() + 5.0 * V.sum(0) + 0.5 * prev.sum(0) + pend.sum(0)
+
+    p0 = total()
+    s.step(40)
+    assert s.fresh_count()[0] > 0
+    assert np.abs(total() - p0).max() < 1e-11
+
+
+def test_wetting_colour_sign():
+    """Eq. 15 and the adsorption behaviour of Sec. III.D: a positive colour adds virtual density to the first
+    component (A, the lower phase), so that capsule sinks further into A than one of negative colour."""
+    zc = []
+    for col in (0.6, 0.0, -0.6):
+        cap = inputs.Capsule(centre=(10.0, 10.0, 12.0), radius=5.0, subdiv=3, kS=0.05, kB=0.0, kV=2.0,
+                             colour=col)
+        p = _bb(nx=20, ny=20, nz=24, walls=1, caps=[cap], z_interface=12, noise=0.0, G=3.6)
+        s = O.OracleSim(p)
+        s.step(120)
+        zc.append(s.capsule(0)[1][2])
+    assert zc[0] < zc[1] - 0.5 and zc[2] > zc[1] + 0.5, zc
+
+
+def test_fresh_node_mass_correction_reduces_drift():
+    """The adaptive correction of Eq. 18 (C0 = 2500) keeps each component's mass closer to its initial value
+    than the plain neighbour average of Eq. 16 (C0 = 0) for a capsule moving through a fluid."""
+    drift = {}
+    for C0 in (0.0, 2500.0):
+        cap = inputs.Capsule(centre=(10.0, 10.0, 10.5), radius=5.0, subdiv=2, kS=0.05, kB=0.0, kV=2.0,
+                             colour=0.3)
+        p = _bb(caps=[cap], z_interface=11, noise=1e-3, C0=C0)
+        s = O.OracleSim(p)
+        m0 = np.array([s.mass(0), s.mass(1)])
+        s.step(120)
+        drift[C0] = np.abs(np.array([s.mass(0), s.mass(1)]) / m0 - 1).max()
+        assert s.fresh_count()[0] > 0
+    assert drift[2500.0] < drift[0.0], drift
+    assert drift[2500.0] < 2e-3
