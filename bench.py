@@ -31,9 +31,12 @@ FALLBACK_HBM_GBS = 6800.0
 
 def workload(name: str):
     if name == "adsorb128":
-        # the paper's coupling (bounce-back with wetting) is not in this build yet: the same 128^3 two-component
-        # box and s=4 capsule run with the 2-point immersed-boundary coupling (colour 0)
-        return inputs.cfg_adsorb128(coupling=1), "adsorb128-ibm2: 128^3 D3Q19 x2, walls sheared 1e-4, s=4 capsule R=12"
+        return inputs.cfg_adsorb128(coupling=0), ("adsorb128: 128^3 D3Q19 x2 Shan-Chen, walls sheared 1e-4, "
+                                                  "s=4 capsule R=12 (2562 vertices), half-way bounce-back, "
+                                                  "colour 0.05, fresh nodes with mass correction")
+    if name == "adsorb128-ibm":
+        return inputs.cfg_adsorb128(coupling=1), ("adsorb128-ibm: same box and capsule with the 2-point "
+                                                  "immersed-boundary coupling (colour 0)")
     if name == "parity32":
         return inputs.cfg_parity(coupling=1), "parity32-ibm2: 32^3, psi=rho, s=3 capsule R=6"
     if name == "fluid256":

@@ -133,6 +133,12 @@ scbb_status scbb_get_vertices(scbb_ctx* ctx, double* x, double* v, double* F);
  * (vertex average).  Any pointer may be NULL.  Synchronous. */
 scbb_status scbb_get_diag(scbb_ctx* ctx, double* mass2, double* mom3, double* vol, double* com);
 
+/* Bounce-back coupling only: the owner of every lattice node (0 = outside all capsules, k+1 = inside mesh k,
+ * 65535 = wall node) as host unsigned short[N] (may be NULL), the number of boundary nodes (nodes with a
+ * link cut by a membrane, Sec. II.C) and of the fresh nodes of the last step (Sec. II.E).  Synchronous.
+ * SCBB_E_UNSUPPORTED for the immersed-boundary coupling. */
+scbb_status scbb_get_owner(scbb_ctx* ctx, unsigned short* owner, int* n_boundary, int* n_fresh);
+
 /* Number of kernel launches issued by this context since creation (for launch accounting). */
 long long scbb_launch_count(const scbb_ctx* ctx);
 

@@ -1,0 +1,789 @@
+// Half-way bounce-back coupling of membranes and fluid (Sec. II.C-II.E), sm_103a.
+//
+//   classification   owner field from z-ray parity per lattice column, updated in place inside each
+//                    capsule's box; nodes that change side are recorded as fresh
+//   boundary list    nodes with a cut membrane link; for each cut link the crossed triangle
+//   boundary kernel  collision of the boundary nodes with Shan-Chen virtual densities and the wetting offset
+//                    (Eq. 14-15), moving half-way bounce-back (Eq. 11) and the exchanged momentum (Eq. 12)
+//   fresh nodes      new density from the non-fresh neighbours on the new side (Eq. 16), adaptive mass
+//                    correction (Eq. 18), velocity of the nearest element (Eq. 17), momentum balance
+//
+// Geometry readings shared with the FP64 oracle: a node is inside capsule k when the +z ray from
+// (x + EPSX, y + EPSY, z + EPSZ) crosses its surface an odd number of times (a crossing counts when the
+// offset point lies strictly inside the triangle's xy projection and the triangle is above it); a link is
+// cut when its two nodes have different owners, and its element is the triangle the offset segment
+// crosses, the crossing nearest to the node of lower linear index (no crossing: nearest centroid to the
+// link midpoint).
+#include <math.h>
+
+#include "scbb_internal.cuh"
+
+namespace scbb {
+
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float3 sub(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ bool wall_z(const LbmParams& p, int z) { return p.walls && (z == 0 || z == p.nz - 1); }
+
+// linear index of unwrapped lattice coordinates (x, y periodic; z periodic without walls), -1 outside
+__device__ __forceinline__ long long node_of(const LbmParams& p, int x, int y, int z) {
+    x = wrapi(x, p.nx);
+    y = wrapi(y, p.ny);
+    if (p.walls) {
+        if (z < 0 || z >= p.nz) return -1;
+    } else {
+        z = wrapi(z, p.nz);
+    }
+    return (long long)x + (long long)p.nx * (y + (long long)p.ny * z);
+}
+
+// coordinate of lattice index q in the periodic image nearest to r (period L; per = periodic)
+__device__ __forceinline__ float near_image(int q, float r, int L, bool per) {
+    float v = (float)q;
+    if (per) v -= L * floorf((v - r) / L + 0.5f);
+    return v;
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Classification
+// ------------------------------------------------------------------------------------------------------
+
+// Per triangle: clear the element accumulators the next step will fill, and append the heights where the
+// triangle crosses the +z rays of the columns inside its xy projection.
+__global__ void k_class_tri(LbmParams p, DevState d, int step) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) { d.cnt[0] = 0; d.cnt[1] = 0; }
+    if (t >= d.NT) return;
+    const int nxt = (step + 1) & 1;
+    d.emom[nxt * d.NT + t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    d.epend[nxt * d.NT + t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int4 T = d.tri[t];
+    const int k = T.w;
+    const int4 lo = d.cbox[2 * k];
+    const float3 a = f3(d.X[T.x]), b = f3(d.X[T.y]), c = f3(d.X[T.z]);
+    // compact record for the element searches of this step
+    d.trec[4 * t + 0] = make_float4(a.x, a.y, a.z, 0.f);
+    d.trec[4 * t + 1] = make_float4(b.x, b.y, b.z, 0.f);
+    d.trec[4 * t + 2] = make_float4(c.x, c.y, c.z, 0.f);
+    d.trec[4 * t + 3] = make_float4((a.x + b.x + c.x) * (1.f / 3.f), (a.y + b.y + c.y) * (1.f / 3.f),
+                                    (a.z + b.z + c.z) * (1.f / 3.f), 0.f);
+    const float xmin = fminf(a.x, fminf(b.x, c.x)), xmax = fmaxf(a.x, fmaxf(b.x, c.x));
+    const float ymin = fminf(a.y, fminf(b.y, c.y)), ymax = fmaxf(a.y, fmaxf(b.y, c.y));
+    if (!(xmax - xmin < (float)d.CW && ymax - ymin < (float)d.CW)) {   // degenerate or non-finite mesh
+        atomicOr(d.cnt + 2, 32);
+        return;
+    }
+    // column cells [xx, xx+1) x [yy, yy+1) overlapped by the xy bounding box: candidate lists for the
+    // element searches
+    for (int yy = (int)floorf(ymin); yy <= (int)floorf(ymax); yy++)
+        for (int xx = (int)floorf(xmin); xx <= (int)floorf(xmax); xx++) {
+            const int cx = xx - lo.x, cy = yy - lo.y;
+            if (cx < 0 || cy < 0 || cx >= d.CW || cy >= d.CW) { atomicOr(d.cnt + 2, 1); continue; }
+            const int col = k * d.CW * d.CW + cy * d.CW + cx;
+            const int slot = atomicAdd(d.tcnt + col, 1);
+            if (slot < BB_MAXT)
+                d.tlst[(size_t)col * BB_MAXT + slot] =
+                    make_int4(t, __float_as_int(fminf(a.z, fminf(b.z, c.z))), __float_as_int(fmaxf(a.z, fmaxf(b.z, c.z))), 0);
+            else atomicOr(d.cnt + 2, 64);
+        }
+    const float det = (b.x - a.x) * (c.y - a.y) - (c.x - a.x) * (b.y - a.y);
+    if (det == 0.f) return;
+    const int x0 = (int)ceilf(xmin - BB_EPSX), x1 = (int)floorf(xmax - BB_EPSX);
+    const int y0 = (int)ceilf(ymin - BB_EPSY), y1 = (int)floorf(ymax - BB_EPSY);
+    for (int yy = y0; yy <= y1; yy++)
+        for (int xx = x0; xx <= x1; xx++) {
+            const float px = xx + BB_EPSX - a.x, py = yy + BB_EPSY - a.y;
+            const float l1 = (px * (c.y - a.y) - (c.x - a.x) * py) / det;
+            const float l2 = ((b.x - a.x) * py - px * (b.y - a.y)) / det;
+            const float l0 = 1.f - l1 - l2;
+            if (l0 <= 0.f || l1 <= 0.f || l2 <= 0.f) continue;
+            const int cx = xx - lo.x, cy = yy - lo.y;
+            if (cx < 0 || cy < 0 || cx >= d.CW || cy >= d.CW) { atomicOr(d.cnt + 2, 1); continue; }
+            const int col = k * d.CW * d.CW + cy * d.CW + cx;
+            const int slot = atomicAdd(d.ccnt + col, 1);
+            if (slot < BB_MAXC) d.czs[(size_t)col * BB_MAXC + slot] = l0 * a.z + l1 * b.z + l2 * c.z;
+            else atomicOr(d.cnt + 2, 2);
+        }
+}
+
+// One thread per node of a capsule's box: parity of the column's crossings above the node; owner updated in
+// place, changed nodes recorded as fresh.
+__global__ void k_class_col(LbmParams p, DevState d, int init) {
+    const int k = blockIdx.y;
+    const int4 lo = d.cbox[2 * k], hi = d.cbox[2 * k + 1];
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = q % (d.CW * d.CW), zo = q / (d.CW * d.CW);
+    if (zo >= d.CW) return;
+    const int cx = c % d.CW, cy = c / d.CW;
+    const int xx = lo.x + cx, yy = lo.y + cy, zz = lo.z + zo;
+    if (xx > hi.x || yy > hi.y || zz > hi.z) return;
+    if (p.walls && (zz < 1 || zz > p.nz - 2)) return;
+    const long long n = node_of(p, xx, yy, zz);
+    if (n < 0) return;
+    const uint16_t old = d.owner[n];
+    if (old == 0xFFFF) return;
+    const int col = k * d.CW * d.CW + c;
+    const int nc = min(d.ccnt[col], BB_MAXC);
+    const float pz = zz + BB_EPSZ;
+    int above = 0;
+    for (int j = 0; j < nc; j++) above += d.czs[(size_t)col * BB_MAXC + j] > pz;
+    const uint16_t me = (uint16_t)(k + 1);
+    uint16_t nw = old;
+    if (above & 1) nw = me;
+    else if (old == me) nw = 0;
+    if (nw == old) return;
+    d.owner[n] = nw;
+    if (init) return;
+    const int f = atomicAdd(d.cnt + 1, 1);
+    if (f < d.maxF) {
+        d.flist[f] = (int)n;
+        d.fold[f] = old;
+        atomicOr(d.fmask + (n >> 5), 1u << (n & 31));
+    } else {
+        atomicOr(d.cnt + 2, 4);
+    }
+}
+
+// Clears the boundary and fresh bits of the previous step's lists and the per-column counters.
+__global__ void k_lists_reset(DevState d) {
+    const int nb = d.cnt[0], nf = d.cnt[1];
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < d.NM * d.CW * d.CW; q += gridDim.x * blockDim.x) {
+        d.ccnt[q] = 0;
+        d.tcnt[q] = 0;
+    }
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < max(nb, nf); q += gridDim.x * blockDim.x) {
+        if (q < nb && q < d.maxB) {
+            const int n = d.blist[q];
+            atomicAnd(d.bmask + (n >> 5), ~(1u << (n & 31)));
+        }
+        if (q < nf && q < d.maxF) {
+            const int n = d.flist[q];
+            atomicAnd(d.fmask + (n >> 5), ~(1u << (n & 31)));
+        }
+    }
+}
+
+// Nodes of each capsule's box (one node wider) with a cut membrane link join the boundary list.
+__global__ void k_boundary_mark(LbmParams p, DevState d) {
+    const int k = blockIdx.y;
+    const int4 lo = d.cbox[2 * k], hi = d.cbox[2 * k + 1];
+    const int wx = hi.x - lo.x + 3, wy = hi.y - lo.y + 3, wz = hi.z - lo.z + 3;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= wx * wy * wz) return;
+    const int xx = lo.x - 1 + q % wx, yy = lo.y - 1 + (q / wx) % wy, zz = lo.z - 1 + q / (wx * wy);
+    const long long n = node_of(p, xx, yy, zz);
+    if (n < 0) return;
+    const uint16_t me = d.owner[n];
+    if (me == 0xFFFF) return;
+    bool cut = false;
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        const long long m = node_of(p, xx + dir_x(i), yy + dir_y(i), zz + dir_z(i));
+        if (m < 0) continue;
+        const uint16_t o = d.owner[m];
+        if (o != 0xFFFF && o != me) cut = true;
+    }
+    if (!cut) return;
+    const uint32_t bit = 1u << (n & 31);
+    const uint32_t prev = atomicOr(d.bmask + (n >> 5), bit);
+    if (prev & bit) return;                           // already listed (boxes of two capsules overlap)
+    const int b = atomicAdd(d.cnt + 0, 1);
+    if (b < d.maxB) d.blist[b] = (int)n;
+    else atomicOr(d.cnt + 2, 8);
+}
+
+// One warp per boundary node: the element each cut link crosses.  Lane i-1 owns direction i.  Candidate
+// triangles come from the 3 x 3 column cells around the node, filtered by their z range; every lane tests
+// its candidates against all cut links of the node, and the nearest crossing per link is kept with a
+// shared-memory atomicMin on (crossing parameter, triangle id) -- the order-independent form of
+// "nearest crossing, lower triangle id on ties".
+constexpr int BE_WARPS = 8;
+
+__global__ void __launch_bounds__(BE_WARPS * 32) k_boundary_elements(LbmParams p, DevState d) {
+    __shared__ unsigned long long best[BE_WARPS][Q - 1];
+    __shared__ float4 segP[BE_WARPS][Q - 1];          // canonical start point of each link's segment
+    __shared__ float4 segD[BE_WARPS][Q - 1];          // and its direction
+    const int wl = threadIdx.x >> 5;
+    const int warp = blockIdx.x * BE_WARPS + wl;
+    const int lane = threadIdx.x & 31;
+    const int nb = min(d.cnt[0], d.maxB);
+    if (warp >= nb) return;
+    const int n = d.blist[warp];
+    const int z = n / p.nxy, r = n - z * p.nxy, y = r / p.nx, x = r - y * p.nx;
+    const uint16_t me = d.owner[n];
+    int my_cap = -1;
+    if (lane < Q - 1) {
+        const int i = lane + 1;
+        const long long m = node_of(p, x + dir_x(i), y + dir_y(i), z + dir_z(i));
+        if (m >= 0) {
+            const uint16_t o = d.owner[m];
+            if (o != 0xFFFF && o != me) my_cap = (me != 0 ? me : o) - 1;
+        }
+        best[wl][lane] = ~0ull;
+    }
+    __syncwarp();
+    const unsigned cutmask = __ballot_sync(0xffffffffu, my_cap >= 0);
+    unsigned todo = cutmask;
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        const int cap = __shfl_sync(0xffffffffu, my_cap, src);
+        const unsigned same = __ballot_sync(0xffffffffu, my_cap == cap) & cutmask;
+        todo &= ~same;
+        const double* cr = d.cap_red + 4 * cap;
+        const float px = near_image(x, (float)cr[1], p.nx, true) + BB_EPSX;
+        const float py = near_image(y, (float)cr[2], p.ny, true) + BB_EPSY;
+        const float pz = near_image(z, (float)cr[3], p.nz, !p.walls) + BB_EPSZ;
+        if (lane < Q - 1 && ((same >> lane) & 1u)) {
+            const int i = lane + 1;
+            const long long m = node_of(p, x + dir_x(i), y + dir_y(i), z + dir_z(i));
+            float3 P = make_float3(px, py, pz);
+            float3 Dv = make_float3((float)dir_x(i), (float)dir_y(i), (float)dir_z(i));
+            if (m < n) {                // canonical orientation: from the node of lower linear index
+                P = make_float3(px + Dv.x, py + Dv.y, pz + Dv.z);
+                Dv = make_float3(-Dv.x, -Dv.y, -Dv.z);
+            }
+            segP[wl][lane] = make_float4(P.x, P.y, P.z, 0.f);
+            segD[wl][lane] = make_float4(Dv.x, Dv.y, Dv.z, 0.f);
+        }
+        __syncwarp();
+        const int4 lo = d.cbox[2 * cap];
+        const int ccx = (int)floorf(px) - lo.x, ccy = (int)floorf(py) - lo.y;
+        for (int j = 0; j < 9; j++) {
+            const int cx = ccx - 1 + j % 3, cy = ccy - 1 + j / 3;
+            if (cx < 0 || cy < 0 || cx >= d.CW || cy >= d.CW) continue;
+            const int col = cap * d.CW * d.CW + cy * d.CW + cx;
+            const int nc = min(d.tcnt[col], BB_MAXT);
+            for (int e = lane; e < nc; e += 32) {
+                const int4 ent = d.tlst[(size_t)col * BB_MAXT + e];
+                if (__int_as_float(ent.z) < pz - 1.f || __int_as_float(ent.y) > pz + 1.f) continue;
+                const int t = ent.x;
+                const float3 v0 = f3(d.trec[4 * t]), v1 = f3(d.trec[4 * t + 1]), v2 = f3(d.trec[4 * t + 2]);
+                const float bx0 = fminf(v0.x, fminf(v1.x, v2.x)), bx1 = fmaxf(v0.x, fmaxf(v1.x, v2.x));
+                const float by0 = fminf(v0.y, fminf(v1.y, v2.y)), by1 = fmaxf(v0.y, fmaxf(v1.y, v2.y));
+                const float bz0 = __int_as_float(ent.y), bz1 = __int_as_float(ent.z);
+                const float3 e1 = sub(v1, v0), e2 = sub(v2, v0);
+                unsigned links = same;
+                while (links) {
+                    const int li = __ffs(links) - 1;
+                    links &= links - 1;
+                    const float4 P4 = segP[wl][li], D4 = segD[wl][li];
+                    // the segment's bounding box must meet the triangle's
+                    if (fmaxf(P4.x, P4.x + D4.x) < bx0 || fminf(P4.x, P4.x + D4.x) > bx1) continue;
+                    if (fmaxf(P4.y, P4.y + D4.y) < by0 || fminf(P4.y, P4.y + D4.y) > by1) continue;
+                    if (fmaxf(P4.z, P4.z + D4.z) < bz0 || fminf(P4.z, P4.z + D4.z) > bz1) continue;
+                    const float3 P = make_float3(P4.x, P4.y, P4.z), Dv = make_float3(D4.x, D4.y, D4.z);
+                    const float3 h = cross(Dv, e2);
+                    const float det = dot(e1, h);
+                    if (fabsf(det) < 1e-30f) continue;
+                    const float inv = 1.f / det;
+                    const float3 sv = sub(P, v0);
+                    const float u = dot(sv, h) * inv;
+                    if (u < 0.f || u > 1.f) continue;
+                    const float3 qv = cross(sv, e1);
+                    const float v = dot(Dv, qv) * inv;
+                    if (v < 0.f || u + v > 1.f) continue;
+                    const float tt = dot(e2, qv) * inv;
+                    if (tt < 0.f || tt > 1.f) continue;
+                    const unsigned long long key =
+                        ((unsigned long long)__float_as_uint(tt) << 32) | (unsigned long long)(unsigned)t;
+                    atomicMin(&best[wl][li], key);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    __syncwarp();
+    int best_e = -1;
+    if (lane < Q - 1 && ((cutmask >> lane) & 1u) && best[wl][lane] != ~0ull)
+        best_e = (int)(unsigned)(best[wl][lane] & 0xffffffffull);
+    // links without a crossing (round-off): nearest centroid to the link midpoint, whole capsule
+    const unsigned miss = __ballot_sync(0xffffffffu, lane < Q - 1 && ((cutmask >> lane) & 1u) && best_e < 0);
+    unsigned mm = miss;
+    while (mm) {
+        const int li = __ffs(mm) - 1;
+        mm &= mm - 1;
+        const int i = li + 1;
+        const int cap = __shfl_sync(0xffffffffu, my_cap, li);
+        const CapDev cp = d.cap[cap];
+        const double* cr = d.cap_red + 4 * cap;
+        const float px = near_image(x, (float)cr[1], p.nx, true) + BB_EPSX;
+        const float py = near_image(y, (float)cr[2], p.ny, true) + BB_EPSY;
+        const float pz = near_image(z, (float)cr[3], p.nz, !p.walls) + BB_EPSZ;
+        const float mx = px + 0.5f * dir_x(i), my = py + 0.5f * dir_y(i), mz = pz + 0.5f * dir_z(i);
+        float bd = 1e30f;
+        int be = -1;
+        for (int tl = lane; tl < cp.nt; tl += 32) {
+            const int t = cp.t0 + tl;
+            const float3 cc = f3(d.trec[4 * t + 3]);
+            const float3 dd = make_float3(cc.x - mx, cc.y - my, cc.z - mz);
+            const float d2 = dot(dd, dd);
+            if (d2 < bd || (d2 == bd && t < be)) { bd = d2; be = t; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float b2 = __shfl_xor_sync(0xffffffffu, bd, o);
+            const int e2 = __shfl_xor_sync(0xffffffffu, be, o);
+            if (e2 >= 0 && (be < 0 || b2 < bd || (b2 == bd && e2 < be))) { bd = b2; be = e2; }
+        }
+        if (lane == li) best_e = be;
+    }
+    if (lane < Q - 1) d.belem[(size_t)warp * (Q - 1) + lane] = ((cutmask >> lane) & 1u) ? best_e : -1;
+}
+
+void launch_bb_classify(const LbmParams& p, const DevState& d, int step, bool init, cudaStream_t st) {
+    if (d.NM == 0) return;
+    k_lists_reset<<<64, 256, 0, st>>>(d);
+    k_class_tri<<<(d.NT + 127) / 128, 128, 0, st>>>(p, d, step);
+    dim3 gc((d.CW * d.CW * d.CW + 127) / 128, d.NM);
+    k_class_col<<<gc, 128, 0, st>>>(p, d, init ? 1 : 0);
+    // boxes are at most CW wide; one node of margin on each side
+    const int w = d.CW + 2;
+    dim3 gm((w * w * w + 127) / 128, d.NM);
+    k_boundary_mark<<<gm, 128, 0, st>>>(p, d);
+    k_boundary_elements<<<(d.maxB + BE_WARPS - 1) / BE_WARPS, BE_WARPS * 32, 0, st>>>(p, d);
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Boundary kernel: collision and streaming of the nodes with cut links
+// ------------------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ float wsum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Every boundary node m: mean density of its neighbours on the other side of the membrane (one warp per
+// node, lane i-1 looks at direction i).  A node x that sees m across a cut link needs the mean over m's
+// neighbours on x's side (Eq. 14); when m borders a single other side that is the same set, so it is
+// computed once per m (otherwise flagged, and recomputed per link).
+__global__ void k_bb_vrho(LbmParams p, DevState d) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nb = min(d.cnt[0], d.maxB);
+    if (b >= nb) return;
+    const int m = d.blist[b];
+    const int z = m / p.nxy, r = m - z * p.nxy, y = r / p.nx, x = r - y * p.nx;
+    const uint16_t me = d.owner[m];
+    float a = 0.f, c = 0.f, cnt = 0.f;
+    int omin = 0x10000, omax = -1;
+    if (lane < Q - 1) {
+        const int i = lane + 1;
+        const long long q = node_of(p, x + dir_x(i), y + dir_y(i), z + dir_z(i));
+        if (q >= 0) {
+            const uint16_t oq = d.owner[q];
+            if (oq != 0xFFFF && oq != me) {
+                a = d.rho[q];
+                c = d.rho[p.N + q];
+                cnt = 1.f;
+                omin = omax = oq;
+            }
+        }
+    }
+    a = wsum(a);
+    c = wsum(c);
+    cnt = wsum(cnt);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        omin = min(omin, __shfl_xor_sync(0xffffffffu, omin, o));
+        omax = max(omax, __shfl_xor_sync(0xffffffffu, omax, o));
+    }
+    if (lane == 0)
+        d.vrho[m] = make_float4(cnt > 0.f ? a / cnt : 0.f, cnt > 0.f ? c / cnt : 0.f, cnt, omin != omax ? 1.f : 0.f);
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Boundary kernel: one warp per boundary node, lane i owns direction i (i = 0..18).  Pull, moments by warp
+// reductions, Shan-Chen force with virtual densities across cut links and the wetting offset
+// (Eq. 13-15; reactions to the crossed element), BGK collision, streaming with moving half-way
+// bounce-back on walls and cut links (Eq. 11) and the exchanged momentum (Eq. 12).
+// ------------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_boundary(LbmParams p, DevState d, const float* __restrict__ S,
+                                                  float* __restrict__ D, const float* __restrict__ ghost,
+                                                  int step, int* err) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nb = min(d.cnt[0], d.maxB);
+    if (b >= nb) return;
+    const int n = d.blist[b];
+    const int z = n / p.nxy, r = n - z * p.nxy, y = r / p.nx, x = r - y * p.nx;
+    const uint16_t me = d.owner[n];
+    const int i = lane < Q ? lane : 0;
+    const bool dl = lane < Q;                         // lanes carrying a direction
+    const int cx = dir_x(i), cy = dir_y(i), cz = dir_z(i);
+    const float wi = dir_w(i);
+    const int pr = step & 1;
+    // ---- pull
+    float fa = 0.f, fb = 0.f;
+    if (dl) {
+        int zs = z - cz;
+        if (!p.walls) zs = wrapi(zs, p.nz);
+        const unsigned int src = (unsigned)wrapi(x - cx, p.nx) + (unsigned)wrapi(y - cy, p.ny) * p.nx + (unsigned)zs * p.nxy;
+        fa = __ldg(S + (size_t)i * p.N + src);
+        fb = __ldg(S + (size_t)(Q + i) * p.N + src);
+    }
+    const float ra = wsum(fa), rb = wsum(fb);
+    const float jx = wsum(cx * (fa + fb)), jy = wsum(cy * (fa + fb)), jz = wsum(cz * (fa + fb));
+    const float pa = psi_fn(ra, p.psi_kind), pb = psi_fn(rb, p.psi_kind);
+    // ---- neighbour along c_i: wall, same side, or across a cut link
+    const int zn = z + cz;
+    const bool wall = dl && lane > 0 && wall_z(p, zn);
+    long long m = -1;
+    uint16_t om = me;
+    int e = -1;
+    float psA = 0.f, psB = 0.f;
+    if (dl && lane > 0) {
+        if (wall) {
+            const int w = zn == 0 ? 0 : 1;
+            const int rr = wrapi(x + cx, p.nx) + wrapi(y + cy, p.ny) * p.nx;
+            psA = psi_fn(ghost[(w * 2 + 0) * p.nxy + rr], p.psi_kind);
+            psB = psi_fn(ghost[(w * 2 + 1) * p.nxy + rr], p.psi_kind);
+        } else {
+            m = node_of(p, x + cx, y + cy, zn);
+            om = d.owner[m];
+            if (om == me) {
+                psA = psi_fn(d.rho[m], p.psi_kind);
+                psB = psi_fn(d.rho[p.N + m], p.psi_kind);
+            } else {
+                e = d.belem[(size_t)b * (Q - 1) + lane - 1];
+                float vA, vB;
+                const float4 vr = d.vrho[m];
+                if (vr.w == 0.f) {
+                    vA = vr.x;
+                    vB = vr.y;
+                } else {
+                    // m borders more than one other side: mean over its neighbours on this node's side
+                    const int mz = (int)(m / p.nxy), mr = (int)(m - (long long)mz * p.nxy), my = mr / p.nx,
+                              mx = mr - my * p.nx;
+                    float sA = 0.f, sB = 0.f;
+                    int cnt = 0;
+                    for (int q = 1; q < Q; q++) {
+                        const long long qq = node_of(p, mx + dir_x(q), my + dir_y(q), mz + dir_z(q));
+                        if (qq < 0) continue;
+                        const uint16_t oq = d.owner[qq];
+                        if (oq == 0xFFFF || oq != me) continue;
+                        sA += d.rho[qq];
+                        sB += d.rho[p.N + qq];
+                        cnt++;
+                    }
+                    vA = cnt ? sA / cnt : ra;
+                    vB = cnt ? sB / cnt : rb;
+                }
+                if (e >= 0) {
+                    const float col = d.cap[d.tri[e].w].colour;
+                    const float rv = 2.f * fabsf(col) * (float)(d.rho_maj - d.rho_min);
+                    if (col > 0.f) vA += rv;
+                    else if (col < 0.f) vB += rv;
+                    psA = psi_fn(vA, p.psi_kind);
+                    psB = psi_fn(vB, p.psi_kind);
+                    // reaction of both components on the element: + psi^c(x) G w_i psi^{c'}(virtual) c_i
+                    const float a = p.G * wi * (pa * psB + pb * psA);
+                    atomicAdd(&d.epend[pr * d.NT + e].x, a * cx);
+                    atomicAdd(&d.epend[pr * d.NT + e].y, a * cy);
+                    atomicAdd(&d.epend[pr * d.NT + e].z, a * cz);
+                } else {
+                    atomicOr(err, 2);      // list out of step with the owner field: never expected
+                }
+            }
+        }
+    }
+    const float qa = wi * psA, qb = wi * psB;
+    const float sa0 = wsum(qa * cx), sa1 = wsum(qa * cy), sa2 = wsum(qa * cz);
+    const float sb0 = wsum(qb * cx), sb1 = wsum(qb * cy), sb2 = wsum(qb * cz);
+    const float FA[3] = {-pa * p.G * sb0 + ra * p.g[0], -pa * p.G * sb1 + ra * p.g[1], -pa * p.G * sb2 + ra * p.g[2]};
+    const float FB[3] = {-pb * p.G * sa0 + rb * p.g[0], -pb * p.G * sa1 + rb * p.g[1], -pb * p.G * sa2 + rb * p.g[2]};
+    const float rt = ra + rb, irt = 1.f / rt;
+    const float ux = jx * irt, uy = jy * irt, uz = jz * irt;
+    if (lane == 0 && (!(rt > 0.f) || !(ux * ux + uy * uy + uz * uz <= 0.09f))) atomicOr(err, 1);
+    const float ta = ra > 0.f ? p.tau / ra : 0.f, tb = rb > 0.f ? p.tau / rb : 0.f;
+    const float uA[3] = {ux + ta * FA[0], uy + ta * FA[1], uz + ta * FA[2]};
+    const float uB[3] = {ux + tb * FB[0], uy + tb * FB[1], uz + tb * FB[2]};
+    // ---- equilibrium (Eq. 2) of this lane's direction; the rest population closes the mass
+    float eA = 0.f, eB = 0.f;
+    if (dl && lane > 0) {
+        const float cuA = cx * uA[0] + cy * uA[1] + cz * uA[2];
+        const float cuB = cx * uB[0] + cy * uB[1] + cz * uB[2];
+        const float uuA = uA[0] * uA[0] + uA[1] * uA[1] + uA[2] * uA[2];
+        const float uuB = uB[0] * uB[0] + uB[1] * uB[1] + uB[2] * uB[2];
+        eA = wi * ra * (1.f + 3.f * cuA + 4.5f * cuA * cuA - 1.5f * uuA);
+        eB = wi * rb * (1.f + 3.f * cuB + 4.5f * cuB * cuB - 1.5f * uuB);
+    }
+    const float sA = wsum(eA), sB = wsum(eB);
+    if (lane == 0) { eA = ra - sA; eB = rb - sB; }
+    const float oA = fa + p.omega * (eA - fa), oB = fb + p.omega * (eB - fb);
+    // ---- streaming
+    double dm[2] = {0.0, 0.0};
+    if (dl) {
+        if (lane == 0) {
+            D[n] = oA;
+            D[(size_t)Q * p.N + n] = oB;
+        } else if (wall) {
+            const float* U = zn == 0 ? p.ulo : p.uhi;
+            const float cU = 6.f * wi * (cx * U[0] + cy * U[1] + cz * U[2]);
+            const unsigned int tgt = (unsigned)(wrapi(x + cx, p.nx) + wrapi(y + cy, p.ny) * p.nx) + (unsigned)zn * p.nxy;
+            D[(size_t)dir_opp(i) * p.N + tgt] = oA - cU * ra;
+            D[(size_t)(Q + dir_opp(i)) * p.N + tgt] = oB - cU * rb;
+        } else if (om == me || e < 0) {
+            D[(size_t)i * p.N + n] = oA;
+            D[(size_t)(Q + i) * p.N + n] = oB;
+        } else {
+            // moving half-way bounce-back (Eq. 11) with the element velocity; exchanged momentum (Eq. 12)
+            const int4 T = d.tri[e];
+            const float4 V0 = d.V[T.x], V1 = d.V[T.y], V2 = d.V[T.z];
+            const float vx = (V0.x + V1.x + V2.x) * (1.f / 3.f), vy = (V0.y + V1.y + V2.y) * (1.f / 3.f),
+                        vz = (V0.z + V1.z + V2.z) * (1.f / 3.f);
+            const float cv = 6.f * wi * (cx * vx + cy * vy + cz * vz);
+            const float bA = oA - cv * ra, bB = oB - cv * rb;
+            D[(size_t)dir_opp(i) * p.N + m] = bA;
+            D[(size_t)(Q + dir_opp(i)) * p.N + m] = bB;
+            const float dp = oA + bA + oB + bB;
+            atomicAdd(&d.emom[pr * d.NT + e].x, dp * cx);
+            atomicAdd(&d.emom[pr * d.NT + e].y, dp * cy);
+            atomicAdd(&d.emom[pr * d.NT + e].z, dp * cz);
+            dm[0] = (double)(bA - oA);
+            dm[1] = (double)(bB - oB);
+        }
+    }
+    const float dmA = wsum((float)dm[0]), dmB = wsum((float)dm[1]);
+    if (lane == 0) {
+        if (dmA != 0.f) atomicAdd(d.mass + 2, (double)dmA);
+        if (dmB != 0.f) atomicAdd(d.mass + 3, (double)dmB);
+    }
+}
+
+void launch_bb_boundary(const LbmParams& p, const DevState& d, const float* S, float* D, const float* ghost,
+                        int step, int* err, cudaStream_t st) {
+    if (d.NM == 0) return;
+    const unsigned blocks = (unsigned)(((size_t)d.maxB * 32 + 255) / 256);
+    k_bb_vrho<<<blocks, 256, 0, st>>>(p, d);
+    k_boundary<<<blocks, 256, 0, st>>>(p, d, S, D, ghost, step, err);
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Fresh nodes
+// ------------------------------------------------------------------------------------------------------
+
+// Mass of the state before the fresh update (bulk-kernel sums of rho(t) plus the bounce-back change of
+// the step) and the correction factors of Eq. 18; resets the bounce-back accumulators.
+__global__ void k_mass_finalize(DevState d, int nblocks, double vsys) {
+    __shared__ double sh[2][256];
+    double a = 0, b = 0;
+    for (int q = threadIdx.x; q < nblocks; q += blockDim.x) { a += d.mpart[2 * q]; b += d.mpart[2 * q + 1]; }
+    sh[0][threadIdx.x] = a;
+    sh[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) { sh[0][threadIdx.x] += sh[0][threadIdx.x + s]; sh[1][threadIdx.x] += sh[1][threadIdx.x + s]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double M[2] = {sh[0][0] + d.mass[2], sh[1][0] + d.mass[3]};
+        const double ri[2] = {d.mass[0] / vsys, d.mass[1] / vsys};
+        for (int c = 0; c < 2; c++) {
+            const double dM = M[c] - d.mass[c];
+            d.mass[4 + c] = d.mass_correction ? 1.0 - d.C0 * (ri[0] + ri[1]) / ri[c] * dM / vsys : 1.0;
+            d.mass[2 + c] = 0.0;
+        }
+    }
+}
+
+// density of node m of the new state (pull from S)
+__device__ __forceinline__ void pulled_rho(const LbmParams& p, const float* __restrict__ S, int m, float& ra, float& rb) {
+    const int z = m / p.nxy, r = m - z * p.nxy, y = r / p.nx, x = r - y * p.nx;
+    Cols k;
+    k.cx[0] = wrapi(x - 1, p.nx); k.cx[1] = x; k.cx[2] = wrapi(x + 1, p.nx);
+    k.ry[0] = wrapi(y - 1, p.ny) * p.nx; k.ry[1] = y * p.nx; k.ry[2] = wrapi(y + 1, p.ny) * p.nx;
+    float f[2 * Q];
+    pull(p, S, k, z, f);
+    ra = rb = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; i++) { ra += f[i]; rb += f[Q + i]; }
+}
+
+// One warp per fresh node: lanes 0-17 pull the densities of the 18 neighbours, then the warp scans the
+// capsule's triangle centroids for the nearest element.
+__global__ void k_fresh_compute(LbmParams p, DevState d, const float* __restrict__ S) {
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nf = min(d.cnt[1], d.maxF);
+    if (q >= nf) return;
+    const int n = d.flist[q];
+    const int z = n / p.nxy, r = n - z * p.nxy, y = r / p.nx, x = r - y * p.nx;
+    const uint16_t side = d.owner[n];
+    // this lane's neighbour (direction lane + 1): same side? fresh? its density
+    bool same = false, fr = false;
+    float a = 0.f, b = 0.f;
+    if (lane < Q - 1) {
+        const int i = lane + 1;
+        const long long m = node_of(p, x + dir_x(i), y + dir_y(i), z + dir_z(i));
+        if (m >= 0 && d.owner[m] == side) {
+            same = true;
+            fr = (d.fmask[m >> 5] >> (m & 31)) & 1u;
+            pulled_rho(p, S, (int)m, a, b);
+        }
+    }
+    float rf[2] = {0.f, 0.f};
+    bool ok = false;
+    for (int pass = 0; pass < 2 && !ok; pass++) {
+        const bool use = same && (pass == 1 || !fr);
+        float sum0 = use ? a : 0.f, sum1 = use ? b : 0.f;
+        float mn0 = use ? a : 1e30f, mn1 = use ? b : 1e30f, mx0 = use ? a : -1e30f, mx1 = use ? b : -1e30f;
+        int cnt = use ? 1 : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sum0 += __shfl_xor_sync(0xffffffffu, sum0, o);
+            sum1 += __shfl_xor_sync(0xffffffffu, sum1, o);
+            mn0 = fminf(mn0, __shfl_xor_sync(0xffffffffu, mn0, o));
+            mn1 = fminf(mn1, __shfl_xor_sync(0xffffffffu, mn1, o));
+            mx0 = fmaxf(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
+            mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        }
+        if (cnt) {
+            rf[0] = fminf(fmaxf(sum0 / cnt * (float)d.mass[4], mn0), mx0);
+            rf[1] = fminf(fmaxf(sum1 / cnt * (float)d.mass[5], mn1), mx1);
+            ok = true;
+        }
+    }
+    if (!ok) {
+        if (lane == 0) d.fnew[2 * q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    // nearest element (centroid) of the capsule that moved over the node
+    const int cap = (side != 0 ? side : d.fold[q]) - 1;
+    const CapDev cp = d.cap[cap];
+    const double* cr = d.cap_red + 4 * cap;
+    const float px = near_image(x, (float)cr[1], p.nx, true), py = near_image(y, (float)cr[2], p.ny, true);
+    const float pz = near_image(z, (float)cr[3], p.nz, !p.walls);
+    float bd = 1e30f;
+    int be = -1;
+    // Candidates from the 5 x 5 column cells around the node: a triangle's centroid lies inside its own
+    // bounding box, so every centroid within distance 2 of the node is listed there.  If the nearest one
+    // found is farther than that, scan the whole capsule.
+    const int4 lo = d.cbox[2 * cap];
+    const int ccx = (int)floorf(px) - lo.x, ccy = (int)floorf(py) - lo.y;
+    for (int j = 0; j < 25; j++) {
+        const int cx = ccx - 2 + j % 5, cy = ccy - 2 + j / 5;
+        if (cx < 0 || cy < 0 || cx >= d.CW || cy >= d.CW) continue;
+        const int col = cap * d.CW * d.CW + cy * d.CW + cx;
+        const int nc = min(d.tcnt[col], BB_MAXT);
+        for (int e = lane; e < nc; e += 32) {
+            const int4 ent = d.tlst[(size_t)col * BB_MAXT + e];
+            if (__int_as_float(ent.z) < pz - 2.f || __int_as_float(ent.y) > pz + 2.f) continue;
+            const int t = ent.x;
+            const float3 c = f3(d.trec[4 * t + 3]);
+            const float dx = c.x - px, dy = c.y - py, dz = c.z - pz;
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 < bd || (d2 == bd && t < be)) { bd = d2; be = t; }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float b2 = __shfl_xor_sync(0xffffffffu, bd, o);
+        const int e2 = __shfl_xor_sync(0xffffffffu, be, o);
+        if (e2 >= 0 && (be < 0 || b2 < bd || (b2 == bd && e2 < be))) { bd = b2; be = e2; }
+    }
+    if (!(bd <= 4.f)) {
+        bd = 1e30f;
+        be = -1;
+        for (int tl = lane; tl < cp.nt; tl += 32) {
+            const int t = cp.t0 + tl;
+            const float3 c = f3(d.trec[4 * t + 3]);
+            const float dx = c.x - px, dy = c.y - py, dz = c.z - pz;
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 < bd) { bd = d2; be = t; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float b2 = __shfl_xor_sync(0xffffffffu, bd, o);
+            const int e2 = __shfl_xor_sync(0xffffffffu, be, o);
+            if (e2 >= 0 && (be < 0 || b2 < bd || (b2 == bd && e2 < be))) { bd = b2; be = e2; }
+        }
+    }
+    if (lane == 0) {
+        const int4 T = d.tri[be];
+        const float3 v = make_float3((d.V[T.x].x + d.V[T.y].x + d.V[T.z].x) * (1.f / 3.f),
+                                     (d.V[T.x].y + d.V[T.y].y + d.V[T.z].y) * (1.f / 3.f),
+                                     (d.V[T.x].z + d.V[T.y].z + d.V[T.z].z) * (1.f / 3.f));
+        d.fnew[2 * q] = make_float4(rf[0], rf[1], 1.f, 0.f);
+        d.fnew[2 * q + 1] = make_float4(v.x, v.y, v.z, __int_as_float(be));
+    }
+}
+
+// Writes f_eq(rho_fresh, v) into the slots the fresh node pulls from (Eq. 2, 16-18) and hands the element
+// the removed minus the created momentum.
+__global__ void k_fresh_apply(LbmParams p, DevState d, float* __restrict__ S, int step) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nf = min(d.cnt[1], d.maxF);
+    if (q >= nf) return;
+    const float4 a = d.fnew[2 * q];
+    if (a.z == 0.f) return;
+    const float4 vv = d.fnew[2 * q + 1];
+    const int e = __float_as_int(vv.w);
+    const int n = d.flist[q];
+    const int z = n / p.nxy, r = n - z * p.nxy, y = r / p.nx, x = r - y * p.nx;
+    Cols k;
+    k.cx[0] = wrapi(x - 1, p.nx); k.cx[1] = x; k.cx[2] = wrapi(x + 1, p.nx);
+    k.ry[0] = wrapi(y - 1, p.ny) * p.nx; k.ry[1] = y * p.nx; k.ry[2] = wrapi(y + 1, p.ny) * p.nx;
+    int zm = z - 1, zp = z + 1;
+    if (!p.walls) { zm = wrapi(zm, p.nz); zp = wrapi(zp, p.nz); }
+    const int pz[3] = {zm * p.nxy, z * p.nxy, zp * p.nxy};
+    const float uu = vv.x * vv.x + vv.y * vv.y + vv.z * vv.z;
+    float rem[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const unsigned int m = k.cx[1 - dir_x(i)] + k.ry[1 - dir_y(i)] + pz[1 - dir_z(i)];
+        const float cu = dir_x(i) * vv.x + dir_y(i) * vv.y + dir_z(i) * vv.z;
+        const float e0 = dir_w(i) * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
+        float* sa = S + (size_t)i * p.N + m;
+        float* sb = S + (size_t)(Q + i) * p.N + m;
+        const float old = *sa + *sb;
+        rem[0] += dir_x(i) * old; rem[1] += dir_y(i) * old; rem[2] += dir_z(i) * old;
+        *sa = e0 * a.x;
+        *sb = e0 * a.y;
+    }
+    const float rt = a.x + a.y;
+    const int nx = (step + 1) & 1;
+    atomicAdd(&d.epend[nx * d.NT + e].x, rem[0] - rt * vv.x);
+    atomicAdd(&d.epend[nx * d.NT + e].y, rem[1] - rt * vv.y);
+    atomicAdd(&d.epend[nx * d.NT + e].z, rem[2] - rt * vv.z);
+}
+
+// Owner field with the wall planes marked, empty lists, zero accumulators, correction factors 1.
+__global__ void k_bb_init(LbmParams p, DevState d) {
+    const unsigned int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < p.N) {
+        const int z = n / p.nxy;
+        d.owner[n] = wall_z(p, z) ? (uint16_t)0xFFFF : (uint16_t)0;
+        if ((n & 31) == 0) { d.bmask[n >> 5] = 0u; d.fmask[n >> 5] = 0u; }
+    }
+    if (n < 2u * d.NT) {
+        d.emom[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+        d.epend[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (n < (unsigned)(d.NM * d.CW * d.CW)) { d.ccnt[n] = 0; d.tcnt[n] = 0; }
+    if (n < 8) d.cnt[n] = 0;
+    if (n < 8) d.mass[n] = (n == 4 || n == 5) ? 1.0 : 0.0;
+}
+
+void launch_bb_init(const LbmParams& p, const DevState& d, cudaStream_t st) {
+    size_t m = p.N;
+    if ((size_t)2 * d.NT > m) m = (size_t)2 * d.NT;
+    if ((size_t)d.NM * d.CW * d.CW > m) m = (size_t)d.NM * d.CW * d.CW;
+    k_bb_init<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(p, d);
+}
+
+void launch_bb_fresh(const LbmParams& p, const DevState& d, float* Snew, int step, int nbulk_blocks,
+                     cudaStream_t st) {
+    if (d.NM == 0) return;
+    double vsys = (double)p.nxy * (p.zf1 - p.zf0);
+    k_mass_finalize<<<1, 256, 0, st>>>(d, nbulk_blocks, vsys);
+    k_fresh_compute<<<(d.maxF * 32 + 255) / 256, 256, 0, st>>>(p, d, Snew);
+    k_fresh_apply<<<(d.maxF + 127) / 128, 128, 0, st>>>(p, d, Snew, step);
+}
+
+}  // namespace scbb

@@ -18,20 +18,6 @@
 
 namespace scbb {
 
-__device__ __forceinline__ int wrapi(int a, int n) {
-    a %= n;
-    return a < 0 ? a + n : a;
-}
-
-__device__ __forceinline__ float psi_fn(float rho, int kind) {
-    // psi = 1 - exp(-rho/rho0) with rho0 = 1 (Sec. II.D), or psi = rho
-    return kind == 1 ? rho : -expm1f(-rho);
-}
-
-__device__ __forceinline__ bool is_wall_plane(const LbmParams& p, int z) {
-    return p.walls && (z == 0 || z == p.nz - 1);
-}
-
 // ------------------------------------------------------------------------------------------------------
 // Initial state: slot (c, i, y) holds the population that node x = y + c_i pulls, f_eq,i(rho^c(x), u(x)).
 // ------------------------------------------------------------------------------------------------------
@@ -60,31 +46,6 @@ __global__ void k_init_state(LbmParams p, float* __restrict__ S, const float* __
         }
         S[(size_t)i * p.N + n] = v0;
         S[(size_t)(Q + i) * p.N + n] = v1;
-    }
-}
-
-// ------------------------------------------------------------------------------------------------------
-// Pull helper: populations arriving at (gx, gy, z) from its 18 neighbours (x, y periodic).
-// ------------------------------------------------------------------------------------------------------
-struct Cols {
-    int cx[3];          // x - 1, x, x + 1 (wrapped)
-    int ry[3];          // (y - 1) nx, y nx, (y + 1) nx (wrapped)
-};
-
-__device__ __forceinline__ void pull(const LbmParams& p, const float* __restrict__ S, const Cols& k, int z,
-                                     float (&f)[2 * Q]) {
-    int zm = z - 1, zp = z + 1;
-    if (!p.walls) {
-        zm = zm < 0 ? zm + p.nz : zm;
-        zp = zp >= p.nz ? zp - p.nz : zp;
-    }
-    const int pz[3] = {zm * p.nxy, z * p.nxy, zp * p.nxy};
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        // source node x - c_i
-        unsigned int m = k.cx[1 - dir_x(i)] + k.ry[1 - dir_y(i)] + pz[1 - dir_z(i)];
-        f[i] = __ldg(S + (size_t)i * p.N + m);
-        f[Q + i] = __ldg(S + (size_t)(Q + i) * p.N + m);
     }
 }
 
@@ -590,11 +551,16 @@ __device__ __forceinline__ void window6(const float* row, int x, int nx, float w
     w[5] = row[x + 4 == nx ? 0 : x + 4];
 }
 
-template <bool TAU1, bool IBM, int NT, int MINB>
+// MODE 0: fluid only, 1: immersed-boundary force at marked nodes, 2: bounce-back membranes (nodes marked in
+// `mask` are the boundary kernel's; this kernel still writes their densities, and every CTA writes the FP64
+// sums of rho^A, rho^B over its nodes to mpart).
+template <bool TAU1, int MODE, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 k_bulk4(LbmParams p, const float* __restrict__ S, float* __restrict__ D, float* __restrict__ rho_out,
         const float* __restrict__ ghost, const float* __restrict__ Fibm, const uint32_t* __restrict__ mask,
-        float* __restrict__ u_out, int* __restrict__ err, int TY) {
+        float* __restrict__ u_out, int* __restrict__ err, int TY, double* __restrict__ mpart) {
+    constexpr bool IBM = MODE == 1;
+    constexpr bool BB = MODE == 2;
     extern __shared__ float ring[];                      // psi [4][2][RR][nx], then moments [2][5][RR][nx]
     const int nx = p.nx;
     const int NQ = nx >> 2;
@@ -619,7 +585,14 @@ k_bulk4(LbmParams p, const float* __restrict__ S, float* __restrict__ D, float* 
     const int nzf = p.zf1 - p.zf0;
     const int zs = p.zf0 + (int)(((long long)blockIdx.y * nzf) / gridDim.y);
     const int ze = p.zf0 + (int)(((long long)(blockIdx.y + 1) * nzf) / gridDim.y);
-    if (zs >= ze) return;
+    if (zs >= ze) {
+        if (BB && threadIdx.x == 0) {
+            mpart[2 * (blockIdx.y * gridDim.x + blockIdx.x)] = 0.0;
+            mpart[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 1] = 0.0;
+        }
+        return;
+    }
+    float msumA = 0.f, msumB = 0.f;    // this thread's density sums (FP32; the block sum is FP64)
     const int dz = (blockIdx.y & 1) ? 1 : -1;
     const int z_first = dz > 0 ? zs : ze - 1;
     const int L = ze - zs;
@@ -726,7 +699,7 @@ k_bulk4(LbmParams p, const float* __restrict__ S, float* __restrict__ D, float* 
 
             const unsigned int n0 = (unsigned)x + (unsigned)gy * nx + (unsigned)z * p.nxy;
             uint32_t bits = 0;
-            if (IBM) bits = (__ldg(mask + (n0 >> 5)) >> (n0 & 31)) & 0xFu;
+            if (IBM || BB) bits = (__ldg(mask + (n0 >> 5)) >> (n0 & 31)) & 0xFu;
             float uA[4][3], uB[4][3], ra[4], rb[4], jxa[4], jya[4], jza[4];
             {
                 const int ms = rel & 1;
@@ -813,7 +786,29 @@ k_bulk4(LbmParams p, const float* __restrict__ S, float* __restrict__ D, float* 
                         oB[k] = FB4[k] + p.omega * (oB[k] - FB4[k]);
                     }
                 }
-                if (dir_z(I) != 0 && wall_next && is_wall_plane(p, z + dir_z(I))) {
+                if (BB && bits) {
+                    // quad holding boundary nodes: store the others one by one
+                    if (dir_z(I) != 0 && wall_next && is_wall_plane(p, z + dir_z(I))) {
+                        const float* U = (z + dir_z(I) == 0) ? p.ulo : p.uhi;
+                        const float cU = 6.f * dir_w(I) * (dir_x(I) * U[0] + dir_y(I) * U[1] + dir_z(I) * U[2]);
+                        const unsigned int drow = (unsigned)ry[1 + dir_y(I)] + (unsigned)(z + dir_z(I)) * p.nxy;
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            if ((bits >> k) & 1u) continue;
+                            int xd = x + k + dir_x(I);
+                            xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
+                            D[(size_t)dir_opp(I) * p.N + drow + xd] = oA[k] - cU * ra[k];
+                            D[(size_t)(Q + dir_opp(I)) * p.N + drow + xd] = oB[k] - cU * rb[k];
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            if ((bits >> k) & 1u) continue;
+                            D[(size_t)I * p.N + n0 + k] = oA[k];
+                            D[(size_t)(Q + I) * p.N + n0 + k] = oB[k];
+                        }
+                    }
+                } else if (dir_z(I) != 0 && wall_next && is_wall_plane(p, z + dir_z(I))) {
                     // half-way bounce-back on a moving wall (Eq. 11), stored where the node pulls opp(I) from
                     const float* U = (z + dir_z(I) == 0) ? p.ulo : p.uhi;
                     const float cU = 6.f * dir_w(I) * (dir_x(I) * U[0] + dir_y(I) * U[1] + dir_z(I) * U[2]);
@@ -844,6 +839,30 @@ k_bulk4(LbmParams p, const float* __restrict__ S, float* __restrict__ D, float* 
             emit(std::integral_constant<int, 0>{});
             *reinterpret_cast<float4*>(rho_out + n0) = make_float4(ra[0], ra[1], ra[2], ra[3]);
             *reinterpret_cast<float4*>(rho_out + p.N + n0) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+            if (BB) {
+                msumA += (ra[0] + ra[1]) + (ra[2] + ra[3]);
+                msumB += (rb[0] + rb[1]) + (rb[2] + rb[3]);
+            }
+        }
+    }
+    if (BB) {
+        // FP64 block sums of the densities (used by the fresh-node mass correction)
+        __shared__ double red[2][32];
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        double dA = msumA, dB = msumB;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            dA += __shfl_down_sync(0xffffffffu, dA, o);
+            dB += __shfl_down_sync(0xffffffffu, dB, o);
+        }
+        __syncthreads();
+        if (lane == 0) { red[0][w] = dA; red[1][w] = dB; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0, b = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); q++) { a += red[0][q]; b += red[1][q]; }
+            mpart[2 * (blockIdx.y * gridDim.x + blockIdx.x)] = a;
+            mpart[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 1] = b;
         }
     }
 }
@@ -920,21 +939,22 @@ static int b4_config() {
     return v;
 }
 
-template <bool TAU1, bool IBM, int NT, int MINB>
+template <bool TAU1, int MODE, int NT, int MINB>
 static void launch_b4(const LbmParams& q, dim3 grid, int threads, size_t smem, int TY, const float* S, float* D,
                       float* rho, const float* ghost, const float* Fibm, const uint32_t* mask, float* u, int* err,
-                      cudaStream_t st) {
+                      double* mpart, cudaStream_t st) {
     static size_t attr = 0;
     if (smem > attr) {
-        cudaFuncSetAttribute(k_bulk4<TAU1, IBM, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_bulk4<TAU1, MODE, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = smem;
     }
-    k_bulk4<TAU1, IBM, NT, MINB><<<grid, threads, smem, st>>>(q, S, D, rho, ghost, Fibm, mask, u, err, TY);
+    k_bulk4<TAU1, MODE, NT, MINB><<<grid, threads, smem, st>>>(q, S, D, rho, ghost, Fibm, mask, u, err, TY, mpart);
 }
 
 template <int NT, int MINB>
 static bool try_b4(const LbmParams& p, const float* S, float* D, float* rho, const float* ghost, const float* Fibm,
-                   const uint32_t* mask, float* u, int* err, bool ibm, cudaStream_t st, int* blocks) {
+                   const uint32_t* mask, float* u, int* err, int mode, double* mpart, cudaStream_t st,
+                   int* blocks) {
     LbmParams q;
     dim3 grid;
     int threads, TY;
@@ -945,24 +965,37 @@ static bool try_b4(const LbmParams& p, const float* S, float* D, float* rho, con
         return true;
     }
     const bool tau1 = p.omega == 1.0f;
-    if (tau1 && ibm) launch_b4<true, true, NT, MINB>(q, grid, threads, smem, TY, S, D, rho, ghost, Fibm, mask, u, err, st);
-    else if (tau1) launch_b4<true, false, NT, MINB>(q, grid, threads, smem, TY, S, D, rho, ghost, Fibm, mask, u, err, st);
-    else if (ibm) launch_b4<false, true, NT, MINB>(q, grid, threads, smem, TY, S, D, rho, ghost, Fibm, mask, u, err, st);
-    else launch_b4<false, false, NT, MINB>(q, grid, threads, smem, TY, S, D, rho, ghost, Fibm, mask, u, err, st);
+#define B4_ARGS q, grid, threads, smem, TY, S, D, rho, ghost, Fibm, mask, u, err, mpart, st
+    if (tau1) {
+        if (mode == 1) launch_b4<true, 1, NT, MINB>(B4_ARGS);
+        else if (mode == 2) launch_b4<true, 2, NT, MINB>(B4_ARGS);
+        else launch_b4<true, 0, NT, MINB>(B4_ARGS);
+    } else {
+        if (mode == 1) launch_b4<false, 1, NT, MINB>(B4_ARGS);
+        else if (mode == 2) launch_b4<false, 2, NT, MINB>(B4_ARGS);
+        else launch_b4<false, 0, NT, MINB>(B4_ARGS);
+    }
+#undef B4_ARGS
     return true;
 }
 
 static bool dispatch_b4(const LbmParams& p, const float* S, float* D, float* rho, const float* ghost,
-                        const float* Fibm, const uint32_t* mask, float* u, int* err, bool ibm, cudaStream_t st,
-                        int* blocks) {
-    if (b4_config() == 2) return try_b4<256, 2>(p, S, D, rho, ghost, Fibm, mask, u, err, ibm, st, blocks);
-    return try_b4<512, 1>(p, S, D, rho, ghost, Fibm, mask, u, err, ibm, st, blocks);
+                        const float* Fibm, const uint32_t* mask, float* u, int* err, int mode, double* mpart,
+                        cudaStream_t st, int* blocks) {
+    if (b4_config() == 2) return try_b4<256, 2>(p, S, D, rho, ghost, Fibm, mask, u, err, mode, mpart, st, blocks);
+    return try_b4<512, 1>(p, S, D, rho, ghost, Fibm, mask, u, err, mode, mpart, st, blocks);
+}
+
+bool bulk_vectorised(const LbmParams& p) {
+    int nb = 0;
+    return bulk_variant() == 4 && dispatch_b4(p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                              nullptr, 0, nullptr, 0, &nb);
 }
 
 int bulk_grid_blocks(const LbmParams& p) {
     int nb = 0;
     if (bulk_variant() == 4 && dispatch_b4(p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                           false, 0, &nb))
+                                           0, nullptr, 0, &nb))
         return nb;
     dim3 g;
     int th;
@@ -971,8 +1004,9 @@ int bulk_grid_blocks(const LbmParams& p) {
 }
 
 void launch_bulk(const LbmParams& p, const float* S, float* D, float* rho, const float* ghost, const float* Fibm,
-                 const uint32_t* mask, float* u, int* err, bool ibm, cudaStream_t st) {
-    if (bulk_variant() == 4 && dispatch_b4(p, S, D, rho, ghost, Fibm, mask, u, err, ibm, st, nullptr)) return;
+                 const uint32_t* mask, float* u, int* err, int mode, double* mpart, cudaStream_t st) {
+    const bool ibm = mode == 1;
+    if (bulk_variant() == 4 && dispatch_b4(p, S, D, rho, ghost, Fibm, mask, u, err, mode, mpart, st, nullptr)) return;
     dim3 grid;
     int threads;
     bulk_geometry(p, grid, threads);

@@ -31,40 +31,84 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-constexpr int CAP_THREADS = 256;
+constexpr int CAP_THREADS = 1024;
 
 // Volume terms come from the triangle pass (tvol), so the reduction is a plain FP64 sum.
 __global__ void __launch_bounds__(CAP_THREADS) k_capsule_reduce(DevState d, int use_tvol) {
     __shared__ double sh[4 * 32];
     const int m = blockIdx.x;
     const CapDev c = d.cap[m];
-    double acc[4] = {0, 0, 0, 0};
+    // per-thread and per-warp partials in FP32 (a few dozen terms each), the block sum in FP64
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
     if (use_tvol) {
-        for (int t = threadIdx.x; t < c.nt; t += blockDim.x) acc[0] += (double)d.tvol[c.t0 + t];
+        for (int t = threadIdx.x; t < c.nt; t += blockDim.x) acc[0] += d.tvol[c.t0 + t];
     } else {
         const float3 r0 = ld3(d.X[c.v0]);
         for (int t = threadIdx.x; t < c.nt; t += blockDim.x) {
             const int4 T = d.tri[c.t0 + t];
             const float3 a = ld3(d.X[T.x]) - r0, b = ld3(d.X[T.y]) - r0, e = ld3(d.X[T.z]) - r0;
-            acc[0] += (double)(dotf(a, crossf(b, e)) * (1.f / 6.f));
+            acc[0] += dotf(a, crossf(b, e)) * (1.f / 6.f);
         }
     }
+    float mn[3] = {1e30f, 1e30f, 1e30f}, mx[3] = {-1e30f, -1e30f, -1e30f};
+    const float4 r0c = d.X[c.v0];       // vertex sums relative to the first vertex (small FP32 terms)
     for (int v = threadIdx.x; v < c.nv; v += blockDim.x) {
         const float4 q = d.X[c.v0 + v];
-        acc[1] += q.x; acc[2] += q.y; acc[3] += q.z;
+        acc[1] += q.x - r0c.x; acc[2] += q.y - r0c.y; acc[3] += q.z - r0c.z;
+        mn[0] = fminf(mn[0], q.x); mn[1] = fminf(mn[1], q.y); mn[2] = fminf(mn[2], q.z);
+        mx[0] = fmaxf(mx[0], q.x); mx[1] = fmaxf(mx[1], q.y); mx[2] = fmaxf(mx[2], q.z);
     }
+    __shared__ float shb[6 * 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        const double s = warp_sum(acc[k]);
-        if (lane == 0) sh[k * 32 + w] = s;
+        float s = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[k * 32 + w] = (double)s;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        float a = mn[k], b = mx[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a = fminf(a, __shfl_down_sync(0xffffffffu, a, o));
+            b = fmaxf(b, __shfl_down_sync(0xffffffffu, b, o));
+        }
+        if (lane == 0) { shb[k * 32 + w] = a; shb[(3 + k) * 32 + w] = b; }
     }
     __syncthreads();
     if (w == 0) {
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             const double s = warp_sum(lane < nw ? sh[k * 32 + lane] : 0.0);
-            if (lane == 0) d.cap_red[4 * m + k] = k == 0 ? s : s / c.nv;
+            const double r0k = k == 1 ? r0c.x : (k == 2 ? r0c.y : r0c.z);
+            if (lane == 0) d.cap_red[4 * m + k] = k == 0 ? s : s / c.nv + r0k;
+        }
+        if (d.cbox) {
+            // classification box: vertex bounds padded by 3 nodes (covers the next step's positions)
+            int lo[3], hi[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                float a = lane < nw ? shb[k * 32 + lane] : 1e30f, b = lane < nw ? shb[(3 + k) * 32 + lane] : -1e30f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    a = fminf(a, __shfl_down_sync(0xffffffffu, a, o));
+                    b = fmaxf(b, __shfl_down_sync(0xffffffffu, b, o));
+                }
+                a = fmaxf(a, -1e6f);
+                b = fminf(b, 1e6f);
+                lo[k] = (int)floorf(a) - 3;
+                hi[k] = (int)ceilf(b) + 3;
+            }
+            if (lane == 0) {
+                bool over = false;
+                for (int k = 0; k < 3; k++)
+                    if (hi[k] - lo[k] + 1 > d.CW) { hi[k] = lo[k] + d.CW - 1; over = true; }
+                if (over) atomicOr(d.cnt + 2, 16);
+                d.cbox[2 * m] = make_int4(lo[0], lo[1], lo[2], 0);
+                d.cbox[2 * m + 1] = make_int4(hi[0], hi[1], hi[2], 0);
+            }
         }
     }
 }
@@ -178,7 +222,10 @@ __global__ void k_mem_vert1(DevState d) {
     d.AK[i] = make_float2(A, KG);
 }
 
-__global__ void k_mem_vert2(DevState d) {
+// bb: add the bounce-back coupling (exchanged momentum smoothed over two steps, Shan-Chen reactions and
+// fresh-node momenta of the crossed elements, one third to each corner) and advance the node
+// (V += F/m, then X += V).
+__global__ void k_mem_vert2(DevState d, int bb, int step) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.NV) return;
     const int m = d.vcap[i];
@@ -205,17 +252,36 @@ __global__ void k_mem_vert2(DevState d) {
     const float fb = 2.f * cp.kB * (2.f * Hi * (Hi * Hi - AK.y) + lap) * AK.x;
     const float kv = (float)(-(double)cp.kV * (d.cap_red[4 * m] - cp.V0) / cp.V0);
     const float4 fs = d.Fsk[i], dvv = d.dV[i];
-    d.F[i] = make_float4(fs.x + fb * ni.x + kv * dvv.x, fs.y + fb * ni.y + kv * dvv.y,
-                         fs.z + fb * ni.z + kv * dvv.z, 0.f);
+    float4 F = make_float4(fs.x + fb * ni.x + kv * dvv.x, fs.y + fb * ni.y + kv * dvv.y,
+                           fs.z + fb * ni.z + kv * dvv.z, 0.f);
+    if (bb) {
+        const int now = step & 1, prev = (step + 1) & 1;
+        float cx = 0.f, cy = 0.f, cz = 0.f;
+        for (int q = q0; q < q1; q++) {
+            const int e = d.vt_idx[q] / 3;
+            const float4 a = d.emom[now * d.NT + e], b = d.emom[prev * d.NT + e], c = d.epend[now * d.NT + e];
+            cx += 0.5f * (a.x + b.x) + c.x;
+            cy += 0.5f * (a.y + b.y) + c.y;
+            cz += 0.5f * (a.z + b.z) + c.z;
+        }
+        F.x += cx * (1.f / 3.f); F.y += cy * (1.f / 3.f); F.z += cz * (1.f / 3.f);
+        float4 V = d.V[i], X = d.X[i];
+        const float im = 1.f / cp.mass;
+        V.x += F.x * im; V.y += F.y * im; V.z += F.z * im;
+        X.x += V.x; X.y += V.y; X.z += V.z;
+        d.V[i] = V;
+        d.X[i] = X;
+    }
+    d.F[i] = F;
 }
 
-void launch_membrane_forces(const DevState& d, cudaStream_t st) {
+void launch_membrane_forces(const DevState& d, bool bb, int step, cudaStream_t st) {
     if (d.NM == 0) return;
     const int b = 128;
     k_mem_tri<<<(d.NT + b - 1) / b, b, 0, st>>>(d);
     k_mem_vert1<<<(d.NV + b - 1) / b, b, 0, st>>>(d);
     k_capsule_reduce<<<d.NM, CAP_THREADS, 0, st>>>(d, 1);
-    k_mem_vert2<<<(d.NV + b - 1) / b, b, 0, st>>>(d);
+    k_mem_vert2<<<(d.NV + b - 1) / b, b, 0, st>>>(d, bb ? 1 : 0, step);
 }
 
 // ------------------------------------------------------------------------------------------------------

@@ -93,6 +93,71 @@ int total(const scbb_mesh* m, int n, bool tris) {
     return (int)s;
 }
 
+LbmParams make_params(const scbb_lattice* lat, const scbb_fluid* fl) {
+    LbmParams p{};
+    p.nx = lat->nx; p.ny = lat->ny; p.nz = lat->nz;
+    p.nxy = p.nx * p.ny;
+    p.N = (unsigned int)((size_t)p.nxy * p.nz);
+    p.walls = lat->walls;
+    p.zf0 = p.walls ? 1 : 0;
+    p.zf1 = p.walls ? p.nz - 1 : p.nz;
+    p.tau = (float)fl->tau;
+    p.omega = (float)(1.0 / fl->tau);
+    p.G = (float)fl->G;
+    p.psi_kind = fl->psi_kind;
+    for (int k = 0; k < 3; k++) {
+        p.g[k] = (float)fl->g[k];
+        p.ulo[k] = (float)lat->u_lo[k];
+        p.uhi[k] = (float)lat->u_hi[k];
+    }
+    // z-segment length of the scalar bulk kernels: several waves on 152 SMs, at least 8 planes
+    int nzf = p.zf1 - p.zf0;
+    int cols = ((p.nx + 31) / 32) * ((p.ny + 7) / 8);
+    int nseg = (4 * 152 + cols - 1) / cols;
+    if (nseg < 1) nseg = 1;
+    int lz = (nzf + nseg - 1) / nseg;
+    if (lz < 8) lz = 8;
+    if (lz > nzf) lz = nzf;
+    p.lz = lz;
+    return p;
+}
+
+void set_params(scbb_ctx* c) { c->lp = make_params(&c->lat, &c->fl); }
+
+// Sizes of the bounce-back lists: boundary and fresh nodes scale with the membrane area (three node layers
+// around each surface, 50 % deformation margin); classification columns cover 1.5 x the largest radius.
+struct BBSizes {
+    int maxB, maxF, CW;
+};
+
+BBSizes bb_sizes(int nm, const scbb_mesh* ms) {
+    BBSizes z{0, 0, 0};
+    double area = 0, rmax = 0;
+    for (int k = 0; k < nm; k++) {
+        const scbb_mesh& m = ms[k];
+        double c[3] = {0, 0, 0};
+        for (int v = 0; v < m.nv; v++)
+            for (int q = 0; q < 3; q++) c[q] += m.ref_xyz[3 * v + q] / m.nv;
+        for (int v = 0; v < m.nv; v++) {
+            double r2 = 0;
+            for (int q = 0; q < 3; q++) r2 += (m.ref_xyz[3 * v + q] - c[q]) * (m.ref_xyz[3 * v + q] - c[q]);
+            rmax = fmax(rmax, sqrt(r2));
+        }
+        for (int t = 0; t < m.nt; t++) {
+            const double* a = m.ref_xyz + 3 * m.tri[3 * t];
+            const double* b = m.ref_xyz + 3 * m.tri[3 * t + 1];
+            const double* e = m.ref_xyz + 3 * m.tri[3 * t + 2];
+            double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, w[3] = {e[0] - a[0], e[1] - a[1], e[2] - a[2]};
+            double x = u[1] * w[2] - u[2] * w[1], y = u[2] * w[0] - u[0] * w[2], zz = u[0] * w[1] - u[1] * w[0];
+            area += 0.5 * sqrt(x * x + y * y + zz * zz);
+        }
+    }
+    z.maxB = (int)(area * 3.0 * 1.5) + 4096;
+    z.maxF = z.maxB / 2 + 1024;
+    z.CW = 2 * (int)ceil(1.5 * rmax) + 10;
+    return z;
+}
+
 // Lays out every device buffer; returns total bytes.
 size_t layout(const scbb_lattice* lat, const scbb_fluid* fl, int nm, const scbb_mesh* ms, void* base, DevState* d) {
     Carve c(base);
@@ -132,6 +197,31 @@ size_t layout(const scbb_lattice* lat, const scbb_fluid* fl, int nm, const scbb_
     t.ccot = c.take<float2>(3 * nt1);
     t.tvol = c.take<float>(nt1);
     t.cnb = c.take<int2>(3 * nt1);
+    if (fl->coupling == 0 && NV > 0) {
+        const BBSizes z = bb_sizes(nm, ms);
+        const LbmParams lp = make_params(lat, fl);
+        t.maxB = z.maxB; t.maxF = z.maxF; t.CW = z.CW;
+        t.owner = c.take<uint16_t>(N);
+        t.bmask = c.take<uint32_t>((N + 31) / 32);
+        t.fmask = c.take<uint32_t>((N + 31) / 32);
+        t.blist = c.take<int>(z.maxB);
+        t.belem = c.take<int>((size_t)z.maxB * (Q - 1));
+        t.flist = c.take<int>(z.maxF);
+        t.fold = c.take<int>(z.maxF);
+        t.fnew = c.take<float4>((size_t)2 * z.maxF);
+        t.cnt = c.take<int>(8);
+        t.emom = c.take<float4>(2 * nt1);
+        t.epend = c.take<float4>(2 * nt1);
+        t.cbox = c.take<int4>(2 * (nm > 0 ? nm : 1));
+        t.ccnt = c.take<int>((size_t)nm * z.CW * z.CW);
+        t.czs = c.take<float>((size_t)nm * z.CW * z.CW * BB_MAXC);
+        t.mpart = c.take<double>((size_t)2 * (bulk_grid_blocks(lp) + 1));
+        t.mass = c.take<double>(8);
+        t.trec = c.take<float4>((size_t)4 * nt1);
+        t.tcnt = c.take<int>((size_t)nm * z.CW * z.CW);
+        t.tlst = c.take<int4>((size_t)nm * z.CW * z.CW * BB_MAXT);
+        t.vrho = c.take<float4>(N);
+    }
     if (d) *d = t;
     return (c.off + ALIGN - 1) / ALIGN * ALIGN;
 }
@@ -148,33 +238,18 @@ bool valid_meshes(int nm, const scbb_mesh* ms, std::string& why) {
     return true;
 }
 
-void set_params(scbb_ctx* c) {
-    LbmParams& p = c->lp;
-    p.nx = c->lat.nx; p.ny = c->lat.ny; p.nz = c->lat.nz;
-    p.nxy = p.nx * p.ny;
-    p.N = (unsigned int)((size_t)p.nxy * p.nz);
-    p.walls = c->lat.walls;
-    p.zf0 = p.walls ? 1 : 0;
-    p.zf1 = p.walls ? p.nz - 1 : p.nz;
-    p.tau = (float)c->fl.tau;
-    p.omega = (float)(1.0 / c->fl.tau);
-    p.G = (float)c->fl.G;
-    p.psi_kind = c->fl.psi_kind;
-    for (int k = 0; k < 3; k++) {
-        p.g[k] = (float)c->fl.g[k];
-        p.ulo[k] = (float)c->lat.u_lo[k];
-        p.uhi[k] = (float)c->lat.u_hi[k];
+scbb_status check_bb_flags(scbb_ctx* c) {
+    if (!c->d.owner) return SCBB_OK;
+    int h[3] = {0, 0, 0};
+    CUDA_TRY(c, cudaMemcpyAsync(h, c->d.cnt, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    if (h[2]) {
+        c->broken = 1;
+        return fail(c, SCBB_E_UNSTABLE,
+                    "bounce-back list overflow (flags %d: 1/16 capsule box, 2 column crossings, 4 fresh list, "
+                    "8 boundary list)", h[2]);
     }
-    // z-segment length: enough CTAs for several waves on 152 SMs, segments of at least 8 planes
-    int nzf = p.zf1 - p.zf0;
-    int cols = ((p.nx + 31) / 32) * ((p.ny + 7) / 8);
-    int target = 4 * 152;
-    int nseg = (target + cols - 1) / cols;
-    if (nseg < 1) nseg = 1;
-    int lz = (nzf + nseg - 1) / nseg;
-    if (lz < 8) lz = 8;
-    if (lz > nzf) lz = nzf;
-    p.lz = lz;
+    return SCBB_OK;
 }
 
 scbb_status check_device_error(scbb_ctx* c) {
@@ -206,7 +281,12 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
     std::string why;
     if (!valid_lattice(lat) || !valid_fluid(fl) || !dev_workspace) return SCBB_E_INVAL;
     if (!valid_meshes(n_mesh, meshes, why)) return SCBB_E_MESH;
-    if (fl->coupling == 0 && n_mesh > 0) return SCBB_E_UNSUPPORTED;
+    if (fl->coupling == 0 && n_mesh > 0) {
+        // bounce-back membranes run with the row-vectorised bulk kernel (nx a multiple of 4, nx/4 a power of
+        // two up to 32 or a multiple of 32)
+        LbmParams lp = make_params(lat, fl);
+        if (!bulk_vectorised(lp)) return SCBB_E_UNSUPPORTED;
+    }
     if (fl->coupling == 1)
         for (int k = 0; k < n_mesh; k++)
             if (meshes[k].colour != 0.0) return SCBB_E_INVAL;     // wetting needs the bounce-back coupling
@@ -222,6 +302,10 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
     layout(lat, fl, n_mesh, meshes, dev_workspace, &c->d);
     set_params(c);
     DevState& d = c->d;
+    d.rho_maj = fl->rho_maj;
+    d.rho_min = fl->rho_min;
+    d.C0 = fl->C0;
+    d.mass_correction = fl->mass_correction;
 
     // ---- meshes: triangles, reference metrics, vertex -> triangle CSR, capsule constants
     const int NV = d.NV, NT = d.NT;
@@ -334,19 +418,32 @@ scbb_status scbb_set_density(scbb_ctx* c, const double* rhoA, const double* rhoB
         CUDA_TRY(c, cudaMemsetAsync(c->d.Fibm, 0, sizeof(float) * 3 * N, c->st));
         CUDA_TRY(c, cudaMemsetAsync(c->d.mask, 0, sizeof(uint32_t) * ((N + 31) / 32), c->st));
     }
+    if (c->d.owner) {
+        // bounce-back: classification of the initial shape, boundary list, initial masses M(0)
+        launch_bb_init(c->lp, c->d, c->st);
+        launch_capsule_reduce(c->d, c->st);
+        launch_bb_classify(c->lp, c->d, -1, true, c->st);
+        launch_moments_reduce(c->lp, c->d.S[c->cur], c->d.red, c->st);
+        CUDA_TRY(c, cudaMemcpyAsync(c->d.mass, c->d.red, 2 * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        c->launches += 9;
+    }
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
     c->steps = 0;
-    return SCBB_OK;
+    return check_bb_flags(c);
 }
 
 scbb_status scbb_step(scbb_ctx* c, long long n) {
     if (!c || n < 0) return SCBB_E_INVAL;
     if (c->broken) return SCBB_E_STATE;
     const bool ibm = c->fl.coupling == 1 && c->d.NV > 0;
+    const bool bb = c->d.owner != nullptr;
+    const int mode = ibm ? 1 : (bb ? 2 : 0);
     for (long long s = 0; s < n; s++) {
+        const int step = (int)(c->steps & 0x7fffffff);
         if (ibm) {
-            launch_membrane_forces(c->d, c->st);
+            // membrane forces at X(t), spread onto the lattice (2-point immersed boundary)
+            launch_membrane_forces(c->d, false, step, c->st);
             launch_ibm_spread(c->lp, c->d, c->st);
             c->launches += 5;
         }
@@ -356,8 +453,8 @@ scbb_status scbb_step(scbb_ctx* c, long long n) {
         }
         const bool timed = c->timing && c->ev_used + 2 <= c->ev.size();
         if (timed) cudaEventRecord(c->ev[c->ev_used], c->st);
-        launch_bulk(c->lp, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.rho, c->d.ghost, c->d.Fibm, c->d.mask, c->d.u,
-                    c->d.err, ibm, c->st);
+        launch_bulk(c->lp, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.rho, c->d.ghost, c->d.Fibm,
+                    bb ? c->d.bmask : c->d.mask, c->d.u, c->d.err, mode, c->d.mpart, c->st);
         if (timed) {
             cudaEventRecord(c->ev[c->ev_used + 1], c->st);
             c->ev_used += 2;
@@ -366,6 +463,15 @@ scbb_status scbb_step(scbb_ctx* c, long long n) {
         if (ibm) {
             launch_ibm_interp(c->lp, c->d, c->st);
             c->launches++;
+        }
+        if (bb) {
+            // boundary nodes (bounce-back, wetting) -> membrane forces with coupling, node update ->
+            // classification at X(t+1), boundary list -> fresh nodes
+            launch_bb_boundary(c->lp, c->d, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.ghost, step, c->d.err, c->st);
+            launch_membrane_forces(c->d, true, step, c->st);
+            launch_bb_classify(c->lp, c->d, step, false, c->st);
+            launch_bb_fresh(c->lp, c->d, c->d.S[1 - c->cur], step, bulk_grid_blocks(c->lp), c->st);
+            c->launches += 14;
         }
         c->cur ^= 1;
         c->steps++;
@@ -378,6 +484,8 @@ scbb_status scbb_sync(scbb_ctx* c) {
     if (!c) return SCBB_E_INVAL;
     if (c->broken) return SCBB_E_STATE;
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    scbb_status e = check_bb_flags(c);
+    if (e != SCBB_OK) return e;
     return check_device_error(c);
 }
 
@@ -458,6 +566,20 @@ scbb_status scbb_get_diag(scbb_ctx* c, double* mass2, double* mom3, double* vol,
         if (vol) vol[m] = cr[4 * m];
         if (com) { com[3 * m] = cr[4 * m + 1]; com[3 * m + 1] = cr[4 * m + 2]; com[3 * m + 2] = cr[4 * m + 3]; }
     }
+    return check_device_error(c);
+}
+
+scbb_status scbb_get_owner(scbb_ctx* c, unsigned short* owner, int* n_boundary, int* n_fresh) {
+    if (!c) return SCBB_E_INVAL;
+    if (c->broken) return SCBB_E_STATE;
+    if (!c->d.owner) return SCBB_E_UNSUPPORTED;
+    int h[2] = {0, 0};
+    CUDA_TRY(c, cudaMemcpyAsync(h, c->d.cnt, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+    if (owner)
+        CUDA_TRY(c, cudaMemcpyAsync(owner, c->d.owner, sizeof(uint16_t) * c->lp.N, cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    if (n_boundary) *n_boundary = h[0];
+    if (n_fresh) *n_fresh = h[1];
     return check_device_error(c);
 }
 

@@ -86,22 +86,105 @@ struct DevState {
     float* tvol;            // [NT] volume term of each triangle (scratch)
     int2* cnb;              // [3 NT] global ids of the two other corners j, l (topology)
     float4* X0;             // [NV] initial shape (for resets)
+    // ---- bounce-back coupling (coupling == 0)
+    uint16_t* owner;        // [N] 0 outside every capsule, k+1 inside capsule k, 0xFFFF wall node
+    uint32_t* bmask;        // [ceil(N/32)] boundary-node bits (nodes with a cut membrane link)
+    uint32_t* fmask;        // [ceil(N/32)] fresh-node bits of the current step
+    int* blist;             // [maxB] boundary nodes
+    int* belem;             // [maxB][18] element crossed by the link along direction i (slot i-1), -1 if uncut
+    int* flist;             // [maxF] fresh nodes
+    int* fold;              // [maxF] their owner before the change
+    float4* fnew;           // [maxF][2] new (rhoA, rhoB, ok, -) and (vx, vy, vz, element)
+    int* cnt;               // [8] 0: boundary nodes, 1: fresh nodes, 2: overflow flags
+    float4* emom;           // [2][NT] exchanged momentum (Eq. 12) by step parity
+    float4* epend;          // [2][NT] Shan-Chen reactions and fresh-node momenta by step parity
+    int4* cbox;             // [NM][2] classification box (lo, hi), unwrapped lattice coordinates
+    int* ccnt;              // [NM][CW*CW] crossings per column
+    float* czs;             // [NM][CW*CW][MAXC] crossing heights
+    double* mpart;          // [bulk blocks][2] per-CTA mass sums of the bulk kernel
+    float4* trec;           // [NT][4] vertex positions and centroid of every triangle at X(t+1)
+    int* tcnt;              // [NM][CW*CW] triangles whose xy bounding box overlaps each column cell
+    int4* tlst;             // [NM][CW*CW][BB_MAXT] their ids and z ranges (t, zmin bits, zmax bits, 0)
+    float4* vrho;           // [N] at boundary nodes: mean rho^A, rho^B over neighbours on the other side,
+                            //     count, 1 if those neighbours lie on more than one other side
+    double* mass;           // [8] 0-1: M(0), 2-3: bounce-back mass change of the step, 4-5: correction factor
+    int maxB, maxF, CW;
+    double rho_maj, rho_min, C0;
+    int mass_correction;
 };
+
+constexpr int BB_MAXC = 16;             // crossings stored per classification column
+constexpr int BB_MAXT = 96;             // triangles listed per column cell
+constexpr float BB_EPSX = 1.37e-4f;     // offsets of the classification rays / link segments
+constexpr float BB_EPSY = 2.91e-4f;
+constexpr float BB_EPSZ = 3.53e-4f;
+
+// ---- device helpers shared by the kernels ----
+__device__ __forceinline__ int wrapi(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+__device__ __forceinline__ float psi_fn(float rho, int kind) {
+    // psi = 1 - exp(-rho/rho0) with rho0 = 1 (Sec. II.D), or psi = rho
+    return kind == 1 ? rho : -expm1f(-rho);
+}
+
+__device__ __forceinline__ bool is_wall_plane(const LbmParams& p, int z) {
+    return p.walls && (z == 0 || z == p.nz - 1);
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Pull helper: populations arriving at (gx, gy, z) from its 18 neighbours (x, y periodic).
+// ------------------------------------------------------------------------------------------------------
+struct Cols {
+    int cx[3];          // x - 1, x, x + 1 (wrapped)
+    int ry[3];          // (y - 1) nx, y nx, (y + 1) nx (wrapped)
+};
+
+__device__ __forceinline__ void pull(const LbmParams& p, const float* __restrict__ S, const Cols& k, int z,
+                                     float (&f)[2 * Q]) {
+    int zm = z - 1, zp = z + 1;
+    if (!p.walls) {
+        zm = zm < 0 ? zm + p.nz : zm;
+        zp = zp >= p.nz ? zp - p.nz : zp;
+    }
+    const int pz[3] = {zm * p.nxy, z * p.nxy, zp * p.nxy};
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        // source node x - c_i
+        unsigned int m = k.cx[1 - dir_x(i)] + k.ry[1 - dir_y(i)] + pz[1 - dir_z(i)];
+        f[i] = __ldg(S + (size_t)i * p.N + m);
+        f[Q + i] = __ldg(S + (size_t)(Q + i) * p.N + m);
+    }
+}
 
 // ---- launches (lbm_kernels.cu) ----
 void launch_init_state(const LbmParams& p, float* S, const float* rho_st, const float* u_st, cudaStream_t st);
 void launch_wall_ghost(const LbmParams& p, const float* S, float* wall_rho, float* ghost, cudaStream_t st);
+// mode 0: fluid only, 1: immersed boundary (mask = IBM stencil bits), 2: bounce-back (mask = boundary-node
+// bits, mpart receives per-CTA FP64 density sums; needs the row-vectorised geometry)
 void launch_bulk(const LbmParams& p, const float* S, float* D, float* rho, const float* ghost,
-                 const float* Fibm, const uint32_t* mask, float* u, int* err, bool ibm, cudaStream_t st);
+                 const float* Fibm, const uint32_t* mask, float* u, int* err, int mode, double* mpart,
+                 cudaStream_t st);
+bool bulk_vectorised(const LbmParams& p);
 void launch_export(const LbmParams& p, const float* S, float* out, int what, cudaStream_t st);
 void launch_moments_reduce(const LbmParams& p, const float* S, double* red, cudaStream_t st);
 int bulk_grid_blocks(const LbmParams& p);
 
 // ---- launches (membrane_kernels.cu) ----
 void launch_capsule_reduce(const DevState& d, cudaStream_t st);
-void launch_membrane_forces(const DevState& d, cudaStream_t st);
+void launch_membrane_forces(const DevState& d, bool bb, int step, cudaStream_t st);
 void launch_ibm_spread(const LbmParams& p, const DevState& d, cudaStream_t st);
 void launch_ibm_interp(const LbmParams& p, const DevState& d, cudaStream_t st);
 void launch_pp_forces(const LbmParams& p, const DevState& d, float eps, float d0, cudaStream_t st);
+
+// ---- launches (bb_kernels.cu) ----
+void launch_bb_init(const LbmParams& p, const DevState& d, cudaStream_t st);
+void launch_bb_classify(const LbmParams& p, const DevState& d, int step, bool init, cudaStream_t st);
+void launch_bb_boundary(const LbmParams& p, const DevState& d, const float* S, float* D, const float* ghost,
+                        int step, int* err, cudaStream_t st);
+void launch_bb_fresh(const LbmParams& p, const DevState& d, float* Snew, int step, int nbulk_blocks,
+                     cudaStream_t st);
 
 }  // namespace scbb

@@ -18,7 +18,7 @@ STATUS = {0: "SCBB_OK", 1: "SCBB_E_INVAL", 2: "SCBB_E_CUDA", 3: "SCBB_E_NOMEM", 
           5: "SCBB_E_TIMEOUT", 6: "SCBB_E_MESH", 7: "SCBB_E_STATE", 8: "SCBB_E_UNSUPPORTED"}
 
 EXPORTS = ["scbb_workspace_bytes", "scbb_create", "scbb_set_density", "scbb_step", "scbb_sync",
-           "scbb_get_fields", "scbb_get_populations", "scbb_get_vertices", "scbb_get_diag",
+           "scbb_get_fields", "scbb_get_populations", "scbb_get_vertices", "scbb_get_diag", "scbb_get_owner",
            "scbb_launch_count", "scbb_enable_timing", "scbb_kernel_time", "scbb_population_moments_noalloc",
            "scbb_last_error", "scbb_destroy"]
 
@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH):
     L.scbb_get_vertices.argtypes = [vp, vp, vp, vp]
     L.scbb_get_diag.restype = C.c_int
     L.scbb_get_diag.argtypes = [vp, vp, vp, vp, vp]
+    L.scbb_get_owner.restype = C.c_int
+    L.scbb_get_owner.argtypes = [vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.scbb_launch_count.restype = C.c_longlong
     L.scbb_launch_count.argtypes = [vp]
     L.scbb_enable_timing.restype = C.c_int
@@ -222,6 +224,13 @@ class Sim:
         vol, com = np.empty(max(self.nm, 1)), np.empty(3 * max(self.nm, 1))
         self._check(self.L.scbb_get_diag(self.h, _p(m), _p(p), _p(vol), _p(com)), "scbb_get_diag")
         return dict(mass=m, momentum=p, volume=vol[:self.nm], com=com[:3 * self.nm].reshape(self.nm, 3))
+
+    def scbb_get_owner(self):
+        """(owner[nz, ny, nx] uint16, boundary-node count, fresh-node count of the last step)."""
+        o = np.empty(self.prob.n_nodes, np.uint16)
+        nb, nf = C.c_int(0), C.c_int(0)
+        self._check(self.L.scbb_get_owner(self.h, _p(o), C.byref(nb), C.byref(nf)), "scbb_get_owner")
+        return o.reshape(self.prob.nz, self.prob.ny, self.prob.nx), nb.value, nf.value
 
     def scbb_launch_count(self):
         return int(self.L.scbb_launch_count(self.h))

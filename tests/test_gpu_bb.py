@@ -1,0 +1,95 @@
+"""GPU parity of the half-way bounce-back coupling (Sec. II.C-II.E) against the FP64 oracle, through the C
+ABI: classification, boundary collision with wetting, membrane coupling, fresh nodes."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1904_11386_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _sim(prob, **kw):
+    from paper_1904_11386_gb300 import scbb
+
+    return scbb.Sim(prob, **kw)
+
+
+def _small(colour=0.3, walls=1, seed=13, steps_noise=1e-4):
+    cap = inputs.Capsule(centre=(15.3, 11.8, 12.6), radius=6.0, subdiv=3, kS=0.02, kB=1e-3, kV=2.0, colour=colour)
+    return inputs.Problem(name="bbs", nx=32, ny=24, nz=26, walls=walls, coupling=0, psi_kind=0, z_interface=13,
+                          capsules=[cap], noise=steps_noise, seed=seed, u_lo=(-0.002, 0, 0), u_hi=(0.002, 0, 0))
+
+
+def _cmp_rho(g, o, tol=1e-5):
+    ga, gb, _ = g
+    oa, ob, _ = o
+    fl = oa + ob > 0
+    return max((np.abs(ga - oa)[fl] / oa[fl]).max(), (np.abs(gb - ob)[fl] / ob[fl]).max())
+
+
+def test_bb_classification_matches_oracle():
+    """Owner field and boundary-node count of the initial shapes equal the oracle's exactly."""
+    for prob in (_small(), inputs.cfg_parity(coupling=0)):
+        g = _sim(prob)
+        o = O.OracleSim(prob)
+        og, nb, _ = g.scbb_get_owner()
+        assert np.array_equal(og, o.owner())
+        assert nb == o.boundary_count()[0]
+
+
+def test_bb_one_step_populations():
+    """One step with bounce-back, virtual-density wetting and moving walls: every post-streaming population
+    matches the oracle to FP32 accuracy, except at fresh nodes.  Their densities come from Eq. 18, which
+    multiplies the global mass error by C0 = 2500 and by sum(rho_init)/rho_init^c (about 17 for the
+    minority component): an FP32 mass sum uncertain by ~1e-6 of the total then moves a fresh density by
+    ~1e-5 relative, so fresh nodes are held to 1e-4 relative."""
+    p = _small()
+    g = _sim(p)
+    o = O.OracleSim(p)
+    own0 = o.owner().ravel().copy()
+    g.scbb_step(1)
+    o.step(1)
+    fresh = (o.owner().ravel() != own0)
+    assert fresh.any()
+    fg = g.scbb_get_populations()
+    fo = o.populations()
+    fluid = np.ones((p.nz, p.ny, p.nx), bool)
+    fluid[[0, -1]] = False
+    fluid = fluid.ravel()
+    keep = fluid & ~fresh
+    assert np.abs(fg[:, keep] - fo[:, keep]).max() < 2e-6 * np.abs(fo).max()
+    assert (np.abs(fg[:, fresh] - fo[:, fresh]) / np.abs(fo[:, fresh])).max() < 1e-4
+
+
+def test_bb_small_box_20_steps():
+    """20 coupled steps (membrane forces with exchanged momenta, node update, re-classification, fresh nodes):
+    densities within 1e-5 relative, vertex positions within 1e-4, identical owner fields."""
+    p = _small()
+    g = _sim(p)
+    o = O.OracleSim(p)
+    g.scbb_step(20)
+    o.step(20)
+    og, _, _ = g.scbb_get_owner()
+    assert np.array_equal(og, o.owner())
+    assert _cmp_rho(g.scbb_get_fields(), o.fields()) < 1e-5
+    Xg, _, _ = g.scbb_get_vertices()
+    Xo, _, _ = o.vertices()
+    assert np.abs(Xg - Xo).max() < 1e-4
+    assert o.fresh_count()[0] > 0
+
+
+def test_bb_adsorb128_full_size():
+    """The 128^3 bounce-back workload of the benchmark (walls sheared at 1e-4, exponential psi, s = 4 capsule
+    of colour 0.05), launch configuration as timed: 3 steps against the oracle, every node."""
+    p = inputs.cfg_adsorb128(coupling=0)
+    g = _sim(p)
+    o = O.OracleSim(p)
+    og, _, _ = g.scbb_get_owner()
+    assert np.array_equal(og, o.owner())
+    g.scbb_step(3)
+    o.step(3)
+    assert _cmp_rho(g.scbb_get_fields(), o.fields()) < 1e-5
+    Xg, _, _ = g.scbb_get_vertices()
+    Xo, _, _ = o.vertices()
+    assert np.abs(Xg - Xo).max() < 1e-4
