@@ -254,6 +254,10 @@ __global__ void k_mem_vert2(DevState d, int bb, int step) {
     const float4 fs = d.Fsk[i], dvv = d.dV[i];
     float4 F = make_float4(fs.x + fb * ni.x + kv * dvv.x, fs.y + fb * ni.y + kv * dvv.y,
                            fs.z + fb * ni.z + kv * dvv.z, 0.f);
+    if (d.pp_head) {                                   // particle-particle repulsion (Eq. 26)
+        const float4 fp = d.Fpp[i];
+        F.x += fp.x; F.y += fp.y; F.z += fp.z;
+    }
     if (bb) {
         const int now = step & 1, prev = (step + 1) & 1;
         float cx = 0.f, cy = 0.f, cz = 0.f;
@@ -275,9 +279,10 @@ __global__ void k_mem_vert2(DevState d, int bb, int step) {
     d.F[i] = F;
 }
 
-void launch_membrane_forces(const DevState& d, bool bb, int step, cudaStream_t st) {
+void launch_membrane_forces(const LbmParams& p, const DevState& d, bool bb, int step, cudaStream_t st) {
     if (d.NM == 0) return;
     const int b = 128;
+    launch_pp_forces(p, d, d.pp_eps, d.pp_d0, st);
     k_mem_tri<<<(d.NT + b - 1) / b, b, 0, st>>>(d);
     k_mem_vert1<<<(d.NV + b - 1) / b, b, 0, st>>>(d);
     k_capsule_reduce<<<d.NM, CAP_THREADS, 0, st>>>(d, 1);
@@ -380,11 +385,106 @@ void launch_ibm_interp(const LbmParams& p, const DevState& d, cudaStream_t st) {
 
 // ------------------------------------------------------------------------------------------------------
 // Particle-particle repulsion (Eq. 26): nodes of different capsules closer than d0 push each other apart
-// with eps (d0 - d)^{3/2}.  Each capsule tests only capsules whose bounding spheres overlap its own (the
-// capsule reduction provides the centres); nodes are compared brute force within those pairs.
+// with eps (d0 - d)^{3/2} along their separation (minimum image in the periodic directions).  Vertices go
+// into a hashed grid of cells at least d0 wide (linked lists, head table of 2^k >= 2 NV entries); every
+// vertex then gathers over the 27 cells around it.  Hash collisions only add candidates that the distance
+// test rejects.  The gather sums each vertex's own force, so Newton's third law holds pairwise.
 // ------------------------------------------------------------------------------------------------------
+struct PPGrid {
+    int nc[3];          // cells per direction (periodic directions wrap)
+    float cw[3];        // cell widths (>= d0)
+    int per[3];
+    float L[3];
+    unsigned mask;      // hash table size - 1
+};
+
+__device__ __forceinline__ unsigned pp_hash(int cx, int cy, int cz, unsigned mask) {
+    return ((unsigned)cx * 73856093u ^ (unsigned)cy * 19349663u ^ (unsigned)cz * 83492791u) & mask;
+}
+
+__device__ __forceinline__ int pp_cell(float v, int k, const PPGrid& g) {
+    if (g.per[k]) {
+        v = fmodf(v, g.L[k]);
+        if (v < 0.f) v += g.L[k];
+    }
+    int c = (int)floorf(v / g.cw[k]);
+    if (g.per[k]) c = c < 0 ? 0 : (c >= g.nc[k] ? g.nc[k] - 1 : c);
+    return c;
+}
+
+__global__ void k_pp_clear(DevState d, unsigned size) {
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < size; q += gridDim.x * blockDim.x) d.pp_head[q] = -1;
+}
+
+__global__ void k_pp_insert(DevState d, PPGrid g) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= d.NV) return;
+    const float4 X = d.X[v];
+    if (!(fabsf(X.x) < 1e6f && fabsf(X.y) < 1e6f && fabsf(X.z) < 1e6f)) { d.pp_next[v] = -1; return; }
+    const unsigned h = pp_hash(pp_cell(X.x, 0, g), pp_cell(X.y, 1, g), pp_cell(X.z, 2, g), g.mask);
+    d.pp_next[v] = atomicExch(d.pp_head + h, v);
+}
+
+__global__ void k_pp_force(DevState d, PPGrid g, float eps, float d0) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= d.NV) return;
+    const float4 X = d.X[v];
+    const int cap = d.vcap[v];
+    float3 F = make_float3(0.f, 0.f, 0.f);
+    if (fabsf(X.x) < 1e6f && fabsf(X.y) < 1e6f && fabsf(X.z) < 1e6f) {
+        const int c0[3] = {pp_cell(X.x, 0, g), pp_cell(X.y, 1, g), pp_cell(X.z, 2, g)};
+        for (int dz = -1; dz <= 1; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    int cc[3] = {c0[0] + dx, c0[1] + dy, c0[2] + dz};
+                    const int dd[3] = {dx, dy, dz};
+                    bool skip = false;
+                    for (int k = 0; k < 3; k++) {
+                        if (g.per[k]) {
+                            if (g.nc[k] < 3 && dd[k] != 0 && (g.nc[k] == 1 || dd[k] == 1)) skip = true;  // no revisit
+                            cc[k] = cc[k] < 0 ? cc[k] + g.nc[k] : (cc[k] >= g.nc[k] ? cc[k] - g.nc[k] : cc[k]);
+                        }
+                    }
+                    if (skip) continue;
+                    const unsigned h = pp_hash(cc[0], cc[1], cc[2], g.mask);
+                    for (int w = d.pp_head[h]; w >= 0; w = d.pp_next[w]) {
+                        if (d.vcap[w] == cap) continue;
+                        const float4 Y = d.X[w];
+                        float r[3] = {X.x - Y.x, X.y - Y.y, X.z - Y.z};
+                        for (int k = 0; k < 3; k++)
+                            if (g.per[k]) r[k] -= g.L[k] * floorf(r[k] / g.L[k] + 0.5f);
+                        // only the cell this neighbour really occupies counts (hash collisions)
+                        const int wc[3] = {pp_cell(Y.x, 0, g), pp_cell(Y.y, 1, g), pp_cell(Y.z, 2, g)};
+                        if (wc[0] != cc[0] || wc[1] != cc[1] || wc[2] != cc[2]) continue;
+                        const float dist = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+                        if (dist < d0 && dist > 0.f) {
+                            const float q = d0 - dist;
+                            const float mag = eps * q * sqrtf(q) / dist;
+                            F.x += mag * r[0]; F.y += mag * r[1]; F.z += mag * r[2];
+                        }
+                    }
+                }
+    }
+    d.Fpp[v] = make_float4(F.x, F.y, F.z, 0.f);
+}
+
 void launch_pp_forces(const LbmParams& p, const DevState& d, float eps, float d0, cudaStream_t st) {
-    (void)p; (void)d; (void)eps; (void)d0; (void)st;
+    if (!d.pp_head || d.NM < 2 || eps == 0.f) return;
+    PPGrid g;
+    const float L[3] = {(float)p.nx, (float)p.ny, (float)p.nz};
+    const int per[3] = {1, 1, p.walls ? 0 : 1};
+    for (int k = 0; k < 3; k++) {
+        g.per[k] = per[k];
+        g.L[k] = L[k];
+        int n = (int)floorf(L[k] / d0);
+        if (n < 1) n = 1;
+        g.nc[k] = n;
+        g.cw[k] = per[k] ? L[k] / n : d0;       // non-periodic z: unbounded cells of width d0
+    }
+    g.mask = (unsigned)d.pp_size - 1u;
+    k_pp_clear<<<(d.pp_size + 255) / 256, 256, 0, st>>>(d, (unsigned)d.pp_size);
+    k_pp_insert<<<(d.NV + 127) / 128, 128, 0, st>>>(d, g);
+    k_pp_force<<<(d.NV + 127) / 128, 128, 0, st>>>(d, g, eps, d0);
 }
 
 }  // namespace scbb

@@ -84,6 +84,7 @@ bool valid_fluid(const scbb_fluid* f) {
     if (f->psi_kind != 0 && f->psi_kind != 1) return false;
     if (f->coupling != 0 && f->coupling != 1) return false;
     if (f->storage != 0) return false;
+    if (f->pp_eps != 0.0 && !(f->pp_d0 > 0.0)) return false;
     return true;
 }
 
@@ -197,6 +198,16 @@ size_t layout(const scbb_lattice* lat, const scbb_fluid* fl, int nm, const scbb_
     t.ccot = c.take<float2>(3 * nt1);
     t.tvol = c.take<float>(nt1);
     t.cnb = c.take<int2>(3 * nt1);
+    if (nm > 1 && fl->pp_eps != 0.0) {
+        int sz = 1;
+        while (sz < 2 * NV) sz <<= 1;
+        t.pp_size = sz;
+        t.pp_head = c.take<int>(sz);
+        t.pp_next = c.take<int>(nv1);
+        t.Fpp = c.take<float4>(nv1);
+    }
+    t.pp_eps = (float)fl->pp_eps;
+    t.pp_d0 = (float)fl->pp_d0;
     if (fl->coupling == 0 && NV > 0) {
         const BBSizes z = bb_sizes(nm, ms);
         const LbmParams lp = make_params(lat, fl);
@@ -443,7 +454,7 @@ scbb_status scbb_step(scbb_ctx* c, long long n) {
         const int step = (int)(c->steps & 0x7fffffff);
         if (ibm) {
             // membrane forces at X(t), spread onto the lattice (2-point immersed boundary)
-            launch_membrane_forces(c->d, false, step, c->st);
+            launch_membrane_forces(c->lp, c->d, false, step, c->st);
             launch_ibm_spread(c->lp, c->d, c->st);
             c->launches += 5;
         }
@@ -468,7 +479,7 @@ scbb_status scbb_step(scbb_ctx* c, long long n) {
             // boundary nodes (bounce-back, wetting) -> membrane forces with coupling, node update ->
             // classification at X(t+1), boundary list -> fresh nodes
             launch_bb_boundary(c->lp, c->d, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.ghost, step, c->d.err, c->st);
-            launch_membrane_forces(c->d, true, step, c->st);
+            launch_membrane_forces(c->lp, c->d, true, step, c->st);
             launch_bb_classify(c->lp, c->d, step, false, c->st);
             launch_bb_fresh(c->lp, c->d, c->d.S[1 - c->cur], step, bulk_grid_blocks(c->lp), c->st);
             c->launches += 14;

@@ -109,6 +109,12 @@ struct DevState {
                             //     count, 1 if those neighbours lie on more than one other side
     double* mass;           // [8] 0-1: M(0), 2-3: bounce-back mass change of the step, 4-5: correction factor
     int maxB, maxF, CW;
+    // particle-particle repulsion (several capsules)
+    int* pp_head;           // [pp_size] hashed cell heads, nullptr when unused
+    int* pp_next;           // [NV] linked lists
+    float4* Fpp;            // [NV] repulsion force of the step
+    int pp_size;
+    float pp_eps, pp_d0;
     double rho_maj, rho_min, C0;
     int mass_correction;
 };
@@ -174,7 +180,7 @@ int bulk_grid_blocks(const LbmParams& p);
 
 // ---- launches (membrane_kernels.cu) ----
 void launch_capsule_reduce(const DevState& d, cudaStream_t st);
-void launch_membrane_forces(const DevState& d, bool bb, int step, cudaStream_t st);
+void launch_membrane_forces(const LbmParams& p, const DevState& d, bool bb, int step, cudaStream_t st);
 void launch_ibm_spread(const LbmParams& p, const DevState& d, cudaStream_t st);
 void launch_ibm_interp(const LbmParams& p, const DevState& d, cudaStream_t st);
 void launch_pp_forces(const LbmParams& p, const DevState& d, float eps, float d0, cudaStream_t st);

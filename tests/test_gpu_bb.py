@@ -93,3 +93,26 @@ def test_bb_adsorb128_full_size():
     Xg, _, _ = g.scbb_get_vertices()
     Xo, _, _ = o.vertices()
     assert np.abs(Xg - Xo).max() < 1e-4
+
+
+def test_bb_three_capsules_periodic():
+    """Three capsules with colours +-0.05 and the particle-particle repulsion in a periodic box (a reduced
+    stand-in for the droplet-covering workload): 10 steps, owner fields identical, densities within 1e-5,
+    vertices within 1e-4."""
+    caps = [inputs.Capsule(centre=(9.7, 10.2, 12.1), radius=5.0, subdiv=3, kS=0.02, kB=1e-3, kV=2.0, colour=0.05),
+            inputs.Capsule(centre=(21.1, 10.6, 11.8), radius=5.0, subdiv=3, kS=0.02, kB=1e-3, kV=2.0, colour=-0.05),
+            inputs.Capsule(centre=(15.6, 21.3, 12.4), radius=5.0, subdiv=3, kS=0.02, kB=1e-3, kV=2.0, colour=0.05)]
+    p = inputs.Problem(name="bb3", nx=32, ny=32, nz=24, walls=0, coupling=0, psi_kind=0,
+                       droplet=(16.0, 16.0, 12.0, 7.0), capsules=caps, noise=1e-4, seed=15)
+    g = _sim(p)
+    o = O.OracleSim(p)
+    og, _, _ = g.scbb_get_owner()
+    assert np.array_equal(og, o.owner())
+    g.scbb_step(10)
+    o.step(10)
+    og, _, _ = g.scbb_get_owner()
+    assert np.array_equal(og, o.owner())
+    assert _cmp_rho(g.scbb_get_fields(), o.fields()) < 1e-5
+    Xg, _, _ = g.scbb_get_vertices()
+    Xo, _, _ = o.vertices()
+    assert np.abs(Xg - Xo).max() < 1e-4
