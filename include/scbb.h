@@ -142,12 +142,27 @@ scbb_status scbb_get_owner(scbb_ctx* ctx, unsigned short* owner, int* n_boundary
 /* Number of kernel launches issued by this context since creation (for launch accounting). */
 long long scbb_launch_count(const scbb_ctx* ctx);
 
-/* Measurement support.  With on != 0, every later launch of the fused bulk fluid kernel is bracketed by a
- * pair of CUDA events on the context stream (up to 4096 launches; later launches run untimed).
+/* Measurement support.  With on = 1 or 2, every later launch of the fused bulk fluid kernel is bracketed by
+ * a pair of CUDA events on the context stream (up to 4096 launches; later launches run untimed).
  * scbb_kernel_time synchronises, returns the summed device time of the timed bulk launches in
- * milliseconds and their count, and clears the record.  Timing adds no kernel launches. */
+ * milliseconds and their count, and clears the record.  With on = 2 every step (up to 1024) also records
+ * events between its phases; scbb_phase_times synchronises, writes the summed milliseconds of each phase
+ * to ms[SCBB_PHASES] (indices below; a phase the coupling does not have reads 0) and the number of steps,
+ * and clears the record.  on = 0 stops timing; other values give SCBB_E_INVAL.  Timing adds no kernel
+ * launches, but the events between phases add a little time to the steps they time. */
+#define SCBB_PHASES 7
+enum {
+    SCBB_PHASE_IBM_SPREAD = 0,   /* membrane forces and spreading (immersed boundary) */
+    SCBB_PHASE_WALLS = 1,        /* wall-plane densities and ghost densities */
+    SCBB_PHASE_BULK = 2,         /* fused stream + Shan-Chen + collide */
+    SCBB_PHASE_BOUNDARY = 3,     /* interpolation (immersed boundary) or boundary-node collision (bounce-back) */
+    SCBB_PHASE_MEMBRANE = 4,     /* bounce-back: membrane forces with the coupling and node update */
+    SCBB_PHASE_CLASSIFY = 5,     /* bounce-back: owner field, boundary list and crossed elements */
+    SCBB_PHASE_FRESH = 6         /* bounce-back: mass correction factors and fresh nodes */
+};
 scbb_status scbb_enable_timing(scbb_ctx* ctx, int on);
 scbb_status scbb_kernel_time(scbb_ctx* ctx, double* ms, long long* launches);
+scbb_status scbb_phase_times(scbb_ctx* ctx, double* ms, long long* steps);
 
 /* FP64 mass and momentum of populations already on the device, for callers that cannot allocate device
  * memory (code running while a CUDA graph is captured, or inside a framework that owns the device

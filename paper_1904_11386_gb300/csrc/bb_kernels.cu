@@ -14,6 +14,7 @@
 // cut when its two nodes have different owners, and its element is the triangle the offset segment
 // crosses, the crossing nearest to the node of lower linear index (no crossing: nearest centroid to the
 // link midpoint).
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "scbb_internal.cuh"
@@ -46,6 +47,108 @@ __device__ __forceinline__ float near_image(int q, float r, int L, bool per) {
     float v = (float)q;
     if (per) v -= L * floorf((v - r) / L + 0.5f);
     return v;
+}
+
+// A bounding-box interval [lo, hi] in one int as two FP16 values rounded outwards (lo down, hi up), so the
+// packed box always contains the exact one: a filter on it keeps every triangle the exact box keeps.
+__device__ __forceinline__ int pack_range(float lo, float hi) {
+    const unsigned a = __half_as_ushort(__float2half_rd(lo)), b = __half_as_ushort(__float2half_ru(hi));
+    return (int)(a | (b << 16));
+}
+__device__ __forceinline__ bool range_meets(int r, float lo, float hi) {
+    const float a = __half2float(__ushort_as_half((unsigned short)(r & 0xffff)));
+    const float b = __half2float(__ushort_as_half((unsigned short)((unsigned)r >> 16)));
+    return !(b < lo || a > hi);
+}
+// list entry (t, z range, x range, y range) against the query box [q0, q1]
+__device__ __forceinline__ bool entry_meets(int4 e, float3 q0, float3 q1) {
+    return range_meets(e.y, q0.z, q1.z) && range_meets(e.z, q0.x, q1.x) && range_meets(e.w, q0.y, q1.y);
+}
+
+// The triangle lists of a w x w block of column cells of one capsule, read by a warp as one flat list:
+// lane j (j < w*w) holds cell j's column and the inclusive end of its entries, so that every lane loads
+// its count in parallel and the warp then strides over all entries together.
+struct CellScan {
+    int col;      // column index of this lane's cell, -1 outside the capsule's cell grid
+    int end;      // inclusive prefix sum of the entry counts up to this lane's cell
+    int total;    // entries of all w*w cells
+};
+
+__device__ __forceinline__ CellScan cell_scan(const DevState& d, int cap, int cx0, int cy0, int w, int lane) {
+    CellScan s;
+    s.col = -1;
+    int c = 0;
+    if (lane < w * w) {
+        const int cx = cx0 + lane % w, cy = cy0 + lane / w;
+        if (cx >= 0 && cy >= 0 && cx < d.CW && cy < d.CW) {
+            s.col = cap * d.CW * d.CW + cy * d.CW + cx;
+            c = min(d.tcnt[s.col], BB_MAXT);
+        }
+    }
+    s.end = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, s.end, o);
+        if (lane >= o) s.end += v;
+    }
+    s.total = __shfl_sync(0xffffffffu, s.end, 31);
+    return s;
+}
+
+// Position in the triangle list of entry k < total of the flat list (warp-convergent call; any k).
+__device__ __forceinline__ size_t cell_entry(const CellScan& s, int k) {
+    int j = 0;                    // cell of entry k: the number of cells whose entries end at or before k
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        if (__shfl_sync(0xffffffffu, s.end, j + o - 1) <= k) j += o;
+    // every lane takes part in the shuffles with its own j; a cell outside the grid holds no entries, so
+    // only k >= total can land on one
+    const int col = __shfl_sync(0xffffffffu, s.col, j);
+    const int prev = __shfl_sync(0xffffffffu, s.end, j > 0 ? j - 1 : 0);
+    const int start = j > 0 ? prev : 0;
+    return col < 0 ? 0 : (size_t)col * BB_MAXT + (size_t)(k - start);
+}
+
+// Streams the entries of a CellScan whose boxes meet the query box [q0, q1] through a per-warp queue of
+// 64 ids in shared memory, so that the per-candidate work runs on full warps: fn(t) is called by the whole
+// warp, each lane with a candidate triangle t or with -1.  A triangle listed in several cells may come
+// more than once.
+constexpr int CAND_Q = 64;
+
+template <class Fn>
+__device__ __forceinline__ void for_candidates(const DevState& d, const CellScan& cs, float3 q0, float3 q1,
+                                               int* queue, int lane, Fn&& fn) {
+    int qn = 0;                                   // warp-uniform queue length
+    for (int base = 0; base < cs.total; base += 32) {
+        const int k = base + lane;
+        const size_t at = cell_entry(cs, k);
+        bool keep = false;
+        int t = -1;
+        if (k < cs.total) {
+            const int4 e = d.tlst[at];
+            keep = entry_meets(e, q0, q1);
+            t = e.x;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) queue[qn + __popc(bal & ((1u << lane) - 1u))] = t;
+        qn += __popc(bal);
+        __syncwarp();
+        if (qn >= 32) {
+            const int tt = queue[lane];
+            __syncwarp();
+            if (lane < qn - 32) queue[lane] = queue[32 + lane];
+            __syncwarp();
+            qn -= 32;
+            fn(tt);
+            __syncwarp();
+        }
+    }
+    if (qn > 0) {
+        const int tt = lane < qn ? queue[lane] : -1;
+        __syncwarp();
+        fn(tt);
+        __syncwarp();
+    }
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -87,7 +190,8 @@ __global__ void k_class_tri(LbmParams p, DevState d, int step) {
             const int slot = atomicAdd(d.tcnt + col, 1);
             if (slot < BB_MAXT)
                 d.tlst[(size_t)col * BB_MAXT + slot] =
-                    make_int4(t, __float_as_int(fminf(a.z, fminf(b.z, c.z))), __float_as_int(fmaxf(a.z, fmaxf(b.z, c.z))), 0);
+                    make_int4(t, pack_range(fminf(a.z, fminf(b.z, c.z)), fmaxf(a.z, fmaxf(b.z, c.z))),
+                              pack_range(xmin, xmax), pack_range(ymin, ymax));
             else atomicOr(d.cnt + 2, 64);
         }
     const float det = (b.x - a.x) * (c.y - a.y) - (c.x - a.x) * (b.y - a.y);
@@ -151,6 +255,7 @@ __global__ void k_class_col(LbmParams p, DevState d, int init) {
 // Clears the boundary and fresh bits of the previous step's lists and the per-column counters.
 __global__ void k_lists_reset(DevState d) {
     const int nb = d.cnt[0], nf = d.cnt[1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt[3] = nb;     // list the boundary kernel of this step used
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < d.NM * d.CW * d.CW; q += gridDim.x * blockDim.x) {
         d.ccnt[q] = 0;
         d.tcnt[q] = 0;
@@ -207,6 +312,7 @@ __global__ void __launch_bounds__(BE_WARPS * 32) k_boundary_elements(LbmParams p
     __shared__ unsigned long long best[BE_WARPS][Q - 1];
     __shared__ float4 segP[BE_WARPS][Q - 1];          // canonical start point of each link's segment
     __shared__ float4 segD[BE_WARPS][Q - 1];          // and its direction
+    __shared__ int queue[BE_WARPS][CAND_Q];
     const int wl = threadIdx.x >> 5;
     const int warp = blockIdx.x * BE_WARPS + wl;
     const int lane = threadIdx.x & 31;
@@ -252,48 +358,58 @@ __global__ void __launch_bounds__(BE_WARPS * 32) k_boundary_elements(LbmParams p
         __syncwarp();
         const int4 lo = d.cbox[2 * cap];
         const int ccx = (int)floorf(px) - lo.x, ccy = (int)floorf(py) - lo.y;
-        for (int j = 0; j < 9; j++) {
-            const int cx = ccx - 1 + j % 3, cy = ccy - 1 + j / 3;
-            if (cx < 0 || cy < 0 || cx >= d.CW || cy >= d.CW) continue;
-            const int col = cap * d.CW * d.CW + cy * d.CW + cx;
-            const int nc = min(d.tcnt[col], BB_MAXT);
-            for (int e = lane; e < nc; e += 32) {
-                const int4 ent = d.tlst[(size_t)col * BB_MAXT + e];
-                if (__int_as_float(ent.z) < pz - 1.f || __int_as_float(ent.y) > pz + 1.f) continue;
-                const int t = ent.x;
-                const float3 v0 = f3(d.trec[4 * t]), v1 = f3(d.trec[4 * t + 1]), v2 = f3(d.trec[4 * t + 2]);
-                const float bx0 = fminf(v0.x, fminf(v1.x, v2.x)), bx1 = fmaxf(v0.x, fmaxf(v1.x, v2.x));
-                const float by0 = fminf(v0.y, fminf(v1.y, v2.y)), by1 = fmaxf(v0.y, fmaxf(v1.y, v2.y));
-                const float bz0 = __int_as_float(ent.y), bz1 = __int_as_float(ent.z);
-                const float3 e1 = sub(v1, v0), e2 = sub(v2, v0);
-                unsigned links = same;
-                while (links) {
-                    const int li = __ffs(links) - 1;
-                    links &= links - 1;
-                    const float4 P4 = segP[wl][li], D4 = segD[wl][li];
-                    // the segment's bounding box must meet the triangle's
-                    if (fmaxf(P4.x, P4.x + D4.x) < bx0 || fminf(P4.x, P4.x + D4.x) > bx1) continue;
-                    if (fmaxf(P4.y, P4.y + D4.y) < by0 || fminf(P4.y, P4.y + D4.y) > by1) continue;
-                    if (fmaxf(P4.z, P4.z + D4.z) < bz0 || fminf(P4.z, P4.z + D4.z) > bz1) continue;
-                    const float3 P = make_float3(P4.x, P4.y, P4.z), Dv = make_float3(D4.x, D4.y, D4.z);
-                    const float3 h = cross(Dv, e2);
-                    const float det = dot(e1, h);
-                    if (fabsf(det) < 1e-30f) continue;
-                    const float inv = 1.f / det;
-                    const float3 sv = sub(P, v0);
-                    const float u = dot(sv, h) * inv;
-                    if (u < 0.f || u > 1.f) continue;
-                    const float3 qv = cross(sv, e1);
-                    const float v = dot(Dv, qv) * inv;
-                    if (v < 0.f || u + v > 1.f) continue;
-                    const float tt = dot(e2, qv) * inv;
-                    if (tt < 0.f || tt > 1.f) continue;
-                    const unsigned long long key =
-                        ((unsigned long long)__float_as_uint(tt) << 32) | (unsigned long long)(unsigned)t;
-                    atomicMin(&best[wl][li], key);
-                }
-            }
+        // box around the cut links of this capsule: a triangle crossing one of them meets it
+        float b0x = 1e30f, b0y = 1e30f, b0z = 1e30f, b1x = -1e30f, b1y = -1e30f, b1z = -1e30f;
+        if (lane < Q - 1 && ((same >> lane) & 1u)) {
+            const float4 P4 = segP[wl][lane], D4 = segD[wl][lane];
+            b0x = fminf(P4.x, P4.x + D4.x); b1x = fmaxf(P4.x, P4.x + D4.x);
+            b0y = fminf(P4.y, P4.y + D4.y); b1y = fmaxf(P4.y, P4.y + D4.y);
+            b0z = fminf(P4.z, P4.z + D4.z); b1z = fmaxf(P4.z, P4.z + D4.z);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            b0x = fminf(b0x, __shfl_xor_sync(0xffffffffu, b0x, o));
+            b0y = fminf(b0y, __shfl_xor_sync(0xffffffffu, b0y, o));
+            b0z = fminf(b0z, __shfl_xor_sync(0xffffffffu, b0z, o));
+            b1x = fmaxf(b1x, __shfl_xor_sync(0xffffffffu, b1x, o));
+            b1y = fmaxf(b1y, __shfl_xor_sync(0xffffffffu, b1y, o));
+            b1z = fmaxf(b1z, __shfl_xor_sync(0xffffffffu, b1z, o));
+        }
+        const CellScan cs = cell_scan(d, cap, ccx - 1, ccy - 1, 3, lane);
+        for_candidates(d, cs, make_float3(b0x, b0y, b0z), make_float3(b1x, b1y, b1z), queue[wl], lane, [&](int t) {
+            if (t < 0) return;
+            const float3 v0 = f3(d.trec[4 * t]), v1 = f3(d.trec[4 * t + 1]), v2 = f3(d.trec[4 * t + 2]);
+            const float bx0 = fminf(v0.x, fminf(v1.x, v2.x)), bx1 = fmaxf(v0.x, fmaxf(v1.x, v2.x));
+            const float by0 = fminf(v0.y, fminf(v1.y, v2.y)), by1 = fmaxf(v0.y, fmaxf(v1.y, v2.y));
+            const float bz0 = fminf(v0.z, fminf(v1.z, v2.z)), bz1 = fmaxf(v0.z, fmaxf(v1.z, v2.z));
+            const float3 e1 = sub(v1, v0), e2 = sub(v2, v0);
+            unsigned links = same;
+            while (links) {
+                const int li = __ffs(links) - 1;
+                links &= links - 1;
+                const float4 P4 = segP[wl][li], D4 = segD[wl][li];
+                // the segment's bounding box must meet the triangle's
+                if (fmaxf(P4.x, P4.x + D4.x) < bx0 || fminf(P4.x, P4.x + D4.x) > bx1) continue;
+                if (fmaxf(P4.y, P4.y + D4.y) < by0 || fminf(P4.y, P4.y + D4.y) > by1) continue;
+                if (fmaxf(P4.z, P4.z + D4.z) < bz0 || fminf(P4.z, P4.z + D4.z) > bz1) continue;
+                const float3 P = make_float3(P4.x, P4.y, P4.z), Dv = make_float3(D4.x, D4.y, D4.z);
+                const float3 h = cross(Dv, e2);
+                const float det = dot(e1, h);
+                if (fabsf(det) < 1e-30f) continue;
+                const float inv = 1.f / det;
+                const float3 sv = sub(P, v0);
+                const float u = dot(sv, h) * inv;
+                if (u < 0.f || u > 1.f) continue;
+                const float3 qv = cross(sv, e1);
+                const float v = dot(Dv, qv) * inv;
+                if (v < 0.f || u + v > 1.f) continue;
+                const float tt = dot(e2, qv) * inv;
+                if (tt < 0.f || tt > 1.f) continue;
+                const unsigned long long key =
+                    ((unsigned long long)__float_as_uint(tt) << 32) | (unsigned long long)(unsigned)t;
+                atomicMin(&best[wl][li], key);
+            }
+        });
         __syncwarp();
     }
     __syncwarp();
@@ -549,10 +665,7 @@ __global__ void __launch_bounds__(256) k_boundary(LbmParams p, DevState d, const
         }
     }
     const float dmA = wsum((float)dm[0]), dmB = wsum((float)dm[1]);
-    if (lane == 0) {
-        if (dmA != 0.f) atomicAdd(d.mass + 2, (double)dmA);
-        if (dmB != 0.f) atomicAdd(d.mass + 3, (double)dmB);
-    }
+    if (lane == 0) d.bdm[b] = make_float2(dmA, dmB);
 }
 
 void launch_bb_boundary(const LbmParams& p, const DevState& d, const float* S, float* D, const float* ghost,
@@ -568,11 +681,17 @@ void launch_bb_boundary(const LbmParams& p, const DevState& d, const float* S, f
 // ------------------------------------------------------------------------------------------------------
 
 // Mass of the state before the fresh update (bulk-kernel sums of rho(t) plus the bounce-back change of
-// the step) and the correction factors of Eq. 18; resets the bounce-back accumulators.
+// the step, summed in a fixed order) and the correction factors of Eq. 18.
 __global__ void k_mass_finalize(DevState d, int nblocks, double vsys) {
     __shared__ double sh[2][256];
     double a = 0, b = 0;
     for (int q = threadIdx.x; q < nblocks; q += blockDim.x) { a += d.mpart[2 * q]; b += d.mpart[2 * q + 1]; }
+    const int nb = min(d.cnt[3], d.maxB);            // boundary list of this step, saved before re-listing
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) {
+        const float2 v = d.bdm[q];
+        a += (double)v.x;
+        b += (double)v.y;
+    }
     sh[0][threadIdx.x] = a;
     sh[1][threadIdx.x] = b;
     __syncthreads();
@@ -581,12 +700,11 @@ __global__ void k_mass_finalize(DevState d, int nblocks, double vsys) {
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double M[2] = {sh[0][0] + d.mass[2], sh[1][0] + d.mass[3]};
+        const double M[2] = {sh[0][0], sh[1][0]};
         const double ri[2] = {d.mass[0] / vsys, d.mass[1] / vsys};
         for (int c = 0; c < 2; c++) {
             const double dM = M[c] - d.mass[c];
             d.mass[4 + c] = d.mass_correction ? 1.0 - d.C0 * (ri[0] + ri[1]) / ri[c] * dM / vsys : 1.0;
-            d.mass[2 + c] = 0.0;
         }
     }
 }
@@ -606,7 +724,8 @@ __device__ __forceinline__ void pulled_rho(const LbmParams& p, const float* __re
 
 // One warp per fresh node: lanes 0-17 pull the densities of the 18 neighbours, then the warp scans the
 // capsule's triangle centroids for the nearest element.
-__global__ void k_fresh_compute(LbmParams p, DevState d, const float* __restrict__ S) {
+__global__ void __launch_bounds__(256) k_fresh_compute(LbmParams p, DevState d, const float* __restrict__ S) {
+    __shared__ int queue[8][CAND_Q];
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int nf = min(d.cnt[1], d.maxF);
@@ -661,31 +780,31 @@ __global__ void k_fresh_compute(LbmParams p, DevState d, const float* __restrict
     const float pz = near_image(z, (float)cr[3], p.nz, !p.walls);
     float bd = 1e30f;
     int be = -1;
-    // Candidates from the 5 x 5 column cells around the node: a triangle's centroid lies inside its own
-    // bounding box, so every centroid within distance 2 of the node is listed there.  If the nearest one
-    // found is farther than that, scan the whole capsule.
+    // Candidates within distance r of the node, r = 1 then 2: a triangle's centroid lies inside its own
+    // bounding box, so every centroid within r is listed in the (2r+1) x (2r+1) column cells around the
+    // node and its box meets the cube of half-width r around the node.  A nearest centroid found within r
+    // is therefore the nearest of the whole capsule (ties included); a node the membrane has just swept
+    // over almost always has one within 1.  Otherwise scan the whole capsule.
     const int4 lo = d.cbox[2 * cap];
     const int ccx = (int)floorf(px) - lo.x, ccy = (int)floorf(py) - lo.y;
-    for (int j = 0; j < 25; j++) {
-        const int cx = ccx - 2 + j % 5, cy = ccy - 2 + j / 5;
-        if (cx < 0 || cy < 0 || cx >= d.CW || cy >= d.CW) continue;
-        const int col = cap * d.CW * d.CW + cy * d.CW + cx;
-        const int nc = min(d.tcnt[col], BB_MAXT);
-        for (int e = lane; e < nc; e += 32) {
-            const int4 ent = d.tlst[(size_t)col * BB_MAXT + e];
-            if (__int_as_float(ent.z) < pz - 2.f || __int_as_float(ent.y) > pz + 2.f) continue;
-            const int t = ent.x;
-            const float3 c = f3(d.trec[4 * t + 3]);
-            const float dx = c.x - px, dy = c.y - py, dz = c.z - pz;
-            const float d2 = dx * dx + dy * dy + dz * dz;
-            if (d2 < bd || (d2 == bd && t < be)) { bd = d2; be = t; }
-        }
-    }
+    for (int r = 1; r <= 2; r++) {
+        const float fr = (float)r;
+        const CellScan cs = cell_scan(d, cap, ccx - r, ccy - r, 2 * r + 1, lane);
+        for_candidates(d, cs, make_float3(px - fr, py - fr, pz - fr), make_float3(px + fr, py + fr, pz + fr),
+                       queue[threadIdx.x >> 5], lane, [&](int t) {
+                           if (t < 0) return;
+                           const float3 c = f3(d.trec[4 * t + 3]);
+                           const float dx = c.x - px, dy = c.y - py, dz = c.z - pz;
+                           const float d2 = dx * dx + dy * dy + dz * dz;
+                           if (d2 < bd || (d2 == bd && t < be)) { bd = d2; be = t; }
+                       });
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float b2 = __shfl_xor_sync(0xffffffffu, bd, o);
-        const int e2 = __shfl_xor_sync(0xffffffffu, be, o);
-        if (e2 >= 0 && (be < 0 || b2 < bd || (b2 == bd && e2 < be))) { bd = b2; be = e2; }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float b2 = __shfl_xor_sync(0xffffffffu, bd, o);
+            const int e2 = __shfl_xor_sync(0xffffffffu, be, o);
+            if (e2 >= 0 && (be < 0 || b2 < bd || (b2 == bd && e2 < be))) { bd = b2; be = e2; }
+        }
+        if (bd <= fr * fr) break;
     }
     if (!(bd <= 4.f)) {
         bd = 1e30f;

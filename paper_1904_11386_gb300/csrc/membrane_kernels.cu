@@ -233,6 +233,8 @@ __global__ void k_mem_vert2(DevState d, int bb, int step) {
     const float4 ni = d.nrm[i];
     const float Hi = ni.w;
     float lap = 0.f;
+    float cx = 0.f, cy = 0.f, cz = 0.f;                // bounce-back coupling of the adjacent elements
+    const int now = step & 1, prev = (step + 1) & 1;
     const int q0 = d.vt_off[i], q1 = d.vt_off[i + 1];
     for (int qb = q0; qb < q1; qb += GATHER) {
         int cid[GATHER];
@@ -245,6 +247,13 @@ __global__ void k_mem_vert2(DevState d, int bb, int step) {
             const float2 ct = d.ccot[cid[u]];          // (cot at j, cot at l)
             // edge (i, j) carries the cotangent of the angle at l, edge (i, l) that at j
             lap += ct.y * (d.nrm[nb.x].w - Hi) + ct.x * (d.nrm[nb.y].w - Hi);
+            if (bb) {
+                const int e = cid[u] / 3;
+                const float4 a = d.emom[now * d.NT + e], b = d.emom[prev * d.NT + e], c = d.epend[now * d.NT + e];
+                cx += 0.5f * (a.x + b.x) + c.x;
+                cy += 0.5f * (a.y + b.y) + c.y;
+                cz += 0.5f * (a.z + b.z) + c.z;
+            }
         }
     }
     const float2 AK = d.AK[i];
@@ -259,15 +268,6 @@ __global__ void k_mem_vert2(DevState d, int bb, int step) {
         F.x += fp.x; F.y += fp.y; F.z += fp.z;
     }
     if (bb) {
-        const int now = step & 1, prev = (step + 1) & 1;
-        float cx = 0.f, cy = 0.f, cz = 0.f;
-        for (int q = q0; q < q1; q++) {
-            const int e = d.vt_idx[q] / 3;
-            const float4 a = d.emom[now * d.NT + e], b = d.emom[prev * d.NT + e], c = d.epend[now * d.NT + e];
-            cx += 0.5f * (a.x + b.x) + c.x;
-            cy += 0.5f * (a.y + b.y) + c.y;
-            cz += 0.5f * (a.z + b.z) + c.z;
-        }
         F.x += cx * (1.f / 3.f); F.y += cy * (1.f / 3.f); F.z += cz * (1.f / 3.f);
         float4 V = d.V[i], X = d.X[i];
         const float im = 1.f / cp.mass;
@@ -279,14 +279,15 @@ __global__ void k_mem_vert2(DevState d, int bb, int step) {
     d.F[i] = F;
 }
 
-void launch_membrane_forces(const LbmParams& p, const DevState& d, bool bb, int step, cudaStream_t st) {
-    if (d.NM == 0) return;
+int launch_membrane_forces(const LbmParams& p, const DevState& d, bool bb, int step, cudaStream_t st) {
+    if (d.NM == 0) return 0;
     const int b = 128;
-    launch_pp_forces(p, d, d.pp_eps, d.pp_d0, st);
+    const int npp = launch_pp_forces(p, d, d.pp_eps, d.pp_d0, st);
     k_mem_tri<<<(d.NT + b - 1) / b, b, 0, st>>>(d);
     k_mem_vert1<<<(d.NV + b - 1) / b, b, 0, st>>>(d);
     k_capsule_reduce<<<d.NM, CAP_THREADS, 0, st>>>(d, 1);
     k_mem_vert2<<<(d.NV + b - 1) / b, b, 0, st>>>(d, bb ? 1 : 0, step);
+    return 4 + npp;
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -468,8 +469,8 @@ __global__ void k_pp_force(DevState d, PPGrid g, float eps, float d0) {
     d.Fpp[v] = make_float4(F.x, F.y, F.z, 0.f);
 }
 
-void launch_pp_forces(const LbmParams& p, const DevState& d, float eps, float d0, cudaStream_t st) {
-    if (!d.pp_head || d.NM < 2 || eps == 0.f) return;
+int launch_pp_forces(const LbmParams& p, const DevState& d, float eps, float d0, cudaStream_t st) {
+    if (!d.pp_head || d.NM < 2 || eps == 0.f) return 0;
     PPGrid g;
     const float L[3] = {(float)p.nx, (float)p.ny, (float)p.nz};
     const int per[3] = {1, 1, p.walls ? 0 : 1};
@@ -485,6 +486,7 @@ void launch_pp_forces(const LbmParams& p, const DevState& d, float eps, float d0
     k_pp_clear<<<(d.pp_size + 255) / 256, 256, 0, st>>>(d, (unsigned)d.pp_size);
     k_pp_insert<<<(d.NV + 127) / 128, 128, 0, st>>>(d, g);
     k_pp_force<<<(d.NV + 127) / 128, 128, 0, st>>>(d, g, eps, d0);
+    return 3;
 }
 
 }  // namespace scbb

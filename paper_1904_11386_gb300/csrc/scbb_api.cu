@@ -30,6 +30,13 @@ struct scbb_ctx {
     int timing = 0;
     std::vector<cudaEvent_t> ev;     // pairs
     size_t ev_used = 0;
+    // per-phase timing (timing mode 2): PHASES + 1 events per step
+    std::vector<cudaEvent_t> pev;
+    size_t pev_steps = 0;
+    void mark(int k) {
+        if (timing == 2 && (pev_steps + 1) * (SCBB_PHASES + 1) <= pev.size())
+            cudaEventRecord(pev[pev_steps * (SCBB_PHASES + 1) + k], st);
+    }
 };
 
 namespace {
@@ -216,6 +223,7 @@ size_t layout(const scbb_lattice* lat, const scbb_fluid* fl, int nm, const scbb_
         t.bmask = c.take<uint32_t>((N + 31) / 32);
         t.fmask = c.take<uint32_t>((N + 31) / 32);
         t.blist = c.take<int>(z.maxB);
+        t.bdm = c.take<float2>(z.maxB);
         t.belem = c.take<int>((size_t)z.maxB * (Q - 1));
         t.flist = c.take<int>(z.maxF);
         t.fold = c.take<int>(z.maxF);
@@ -452,16 +460,19 @@ scbb_status scbb_step(scbb_ctx* c, long long n) {
     const int mode = ibm ? 1 : (bb ? 2 : 0);
     for (long long s = 0; s < n; s++) {
         const int step = (int)(c->steps & 0x7fffffff);
+        c->mark(0);
         if (ibm) {
             // membrane forces at X(t), spread onto the lattice (2-point immersed boundary)
-            launch_membrane_forces(c->lp, c->d, false, step, c->st);
+            c->launches += launch_membrane_forces(c->lp, c->d, false, step, c->st);
             launch_ibm_spread(c->lp, c->d, c->st);
-            c->launches += 5;
+            c->launches += 1;
         }
+        c->mark(1);
         if (c->lp.walls) {
             launch_wall_ghost(c->lp, c->d.S[c->cur], c->d.wall_rho, c->d.ghost, c->st);
             c->launches += 2;
         }
+        c->mark(2);
         const bool timed = c->timing && c->ev_used + 2 <= c->ev.size();
         if (timed) cudaEventRecord(c->ev[c->ev_used], c->st);
         launch_bulk(c->lp, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.rho, c->d.ghost, c->d.Fibm,
@@ -471,6 +482,7 @@ scbb_status scbb_step(scbb_ctx* c, long long n) {
             c->ev_used += 2;
         }
         c->launches++;
+        c->mark(3);
         if (ibm) {
             launch_ibm_interp(c->lp, c->d, c->st);
             c->launches++;
@@ -479,11 +491,22 @@ scbb_status scbb_step(scbb_ctx* c, long long n) {
             // boundary nodes (bounce-back, wetting) -> membrane forces with coupling, node update ->
             // classification at X(t+1), boundary list -> fresh nodes
             launch_bb_boundary(c->lp, c->d, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.ghost, step, c->d.err, c->st);
-            launch_membrane_forces(c->lp, c->d, true, step, c->st);
+            c->launches += 2;
+            c->mark(4);
+            c->launches += launch_membrane_forces(c->lp, c->d, true, step, c->st);
+            c->mark(5);
             launch_bb_classify(c->lp, c->d, step, false, c->st);
+            c->launches += 5;
+            c->mark(6);
             launch_bb_fresh(c->lp, c->d, c->d.S[1 - c->cur], step, bulk_grid_blocks(c->lp), c->st);
-            c->launches += 14;
+            c->launches += 3;
+        } else {
+            c->mark(4);
+            c->mark(5);
+            c->mark(6);
         }
+        c->mark(7);
+        if (c->timing == 2 && (c->pev_steps + 1) * (SCBB_PHASES + 1) <= c->pev.size()) c->pev_steps++;
         c->cur ^= 1;
         c->steps++;
     }
@@ -597,13 +620,35 @@ scbb_status scbb_get_owner(scbb_ctx* c, unsigned short* owner, int* n_boundary, 
 long long scbb_launch_count(const scbb_ctx* c) { return c ? c->launches : 0; }
 
 scbb_status scbb_enable_timing(scbb_ctx* c, int on) {
-    if (!c) return SCBB_E_INVAL;
+    if (!c || on < 0 || on > 2) return SCBB_E_INVAL;
     if (on && c->ev.empty()) {
         c->ev.resize(2 * 4096);
         for (auto& e : c->ev) CUDA_TRY(c, cudaEventCreate(&e));
     }
+    if (on == 2 && c->pev.empty()) {
+        c->pev.resize((size_t)(SCBB_PHASES + 1) * 1024);
+        for (auto& e : c->pev) CUDA_TRY(c, cudaEventCreate(&e));
+    }
     c->timing = on;
     c->ev_used = 0;
+    c->pev_steps = 0;
+    return SCBB_OK;
+}
+
+scbb_status scbb_phase_times(scbb_ctx* c, double* ms, long long* steps) {
+    if (!c || !ms) return SCBB_E_INVAL;
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    for (int k = 0; k < SCBB_PHASES; k++) ms[k] = 0.0;
+    for (size_t q = 0; q < c->pev_steps; q++) {
+        const cudaEvent_t* e = c->pev.data() + q * (SCBB_PHASES + 1);
+        for (int k = 0; k < SCBB_PHASES; k++) {
+            float t = 0;
+            CUDA_TRY(c, cudaEventElapsedTime(&t, e[k], e[k + 1]));
+            ms[k] += t;
+        }
+    }
+    if (steps) *steps = (long long)c->pev_steps;
+    c->pev_steps = 0;
     return SCBB_OK;
 }
 

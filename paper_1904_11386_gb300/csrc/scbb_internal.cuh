@@ -91,11 +91,13 @@ struct DevState {
     uint32_t* bmask;        // [ceil(N/32)] boundary-node bits (nodes with a cut membrane link)
     uint32_t* fmask;        // [ceil(N/32)] fresh-node bits of the current step
     int* blist;             // [maxB] boundary nodes
+    float2* bdm;            // [maxB] mass change of each boundary node's bounce-back links (A, B)
     int* belem;             // [maxB][18] element crossed by the link along direction i (slot i-1), -1 if uncut
     int* flist;             // [maxF] fresh nodes
     int* fold;              // [maxF] their owner before the change
     float4* fnew;           // [maxF][2] new (rhoA, rhoB, ok, -) and (vx, vy, vz, element)
-    int* cnt;               // [8] 0: boundary nodes, 1: fresh nodes, 2: overflow flags
+    int* cnt;               // [8] 0: boundary nodes, 1: fresh nodes, 2: overflow flags, 3: boundary nodes of
+                            //     the step's boundary kernel (saved before re-listing)
     float4* emom;           // [2][NT] exchanged momentum (Eq. 12) by step parity
     float4* epend;          // [2][NT] Shan-Chen reactions and fresh-node momenta by step parity
     int4* cbox;             // [NM][2] classification box (lo, hi), unwrapped lattice coordinates
@@ -180,10 +182,11 @@ int bulk_grid_blocks(const LbmParams& p);
 
 // ---- launches (membrane_kernels.cu) ----
 void launch_capsule_reduce(const DevState& d, cudaStream_t st);
-void launch_membrane_forces(const LbmParams& p, const DevState& d, bool bb, int step, cudaStream_t st);
+// returns the number of kernels launched
+int launch_membrane_forces(const LbmParams& p, const DevState& d, bool bb, int step, cudaStream_t st);
 void launch_ibm_spread(const LbmParams& p, const DevState& d, cudaStream_t st);
 void launch_ibm_interp(const LbmParams& p, const DevState& d, cudaStream_t st);
-void launch_pp_forces(const LbmParams& p, const DevState& d, float eps, float d0, cudaStream_t st);
+int launch_pp_forces(const LbmParams& p, const DevState& d, float eps, float d0, cudaStream_t st);
 
 // ---- launches (bb_kernels.cu) ----
 void launch_bb_init(const LbmParams& p, const DevState& d, cudaStream_t st);

@@ -19,7 +19,8 @@ STATUS = {0: "SCBB_OK", 1: "SCBB_E_INVAL", 2: "SCBB_E_CUDA", 3: "SCBB_E_NOMEM", 
 
 EXPORTS = ["scbb_workspace_bytes", "scbb_create", "scbb_set_density", "scbb_step", "scbb_sync",
            "scbb_get_fields", "scbb_get_populations", "scbb_get_vertices", "scbb_get_diag", "scbb_get_owner",
-           "scbb_launch_count", "scbb_enable_timing", "scbb_kernel_time", "scbb_population_moments_noalloc",
+           "scbb_launch_count", "scbb_enable_timing", "scbb_kernel_time", "scbb_phase_times",
+           "scbb_population_moments_noalloc",
            "scbb_last_error", "scbb_destroy"]
 
 
@@ -83,6 +84,8 @@ def load(path: str = LIB_PATH):
     L.scbb_enable_timing.argtypes = [vp, C.c_int]
     L.scbb_kernel_time.restype = C.c_int
     L.scbb_kernel_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+    L.scbb_phase_times.restype = C.c_int
+    L.scbb_phase_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
     L.scbb_population_moments_noalloc.restype = C.c_int
     L.scbb_population_moments_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
     L.scbb_last_error.restype = C.c_char_p
@@ -236,12 +239,22 @@ class Sim:
         return int(self.L.scbb_launch_count(self.h))
 
     def scbb_enable_timing(self, on=True):
+        """on: False/0 off, True/1 bulk-kernel events, 2 bulk-kernel and per-phase events."""
         self._check(self.L.scbb_enable_timing(self.h, int(on)), "scbb_enable_timing")
 
     def scbb_kernel_time(self):
         ms, n = C.c_double(0), C.c_longlong(0)
         self._check(self.L.scbb_kernel_time(self.h, C.byref(ms), C.byref(n)), "scbb_kernel_time")
         return ms.value, n.value
+
+    PHASES = ("ibm_spread", "walls", "bulk", "boundary", "membrane", "classify", "fresh")
+
+    def scbb_phase_times(self):
+        """Summed milliseconds per phase of the steps timed with timing mode 2, and their count."""
+        ms = (C.c_double * len(self.PHASES))()
+        n = C.c_longlong(0)
+        self._check(self.L.scbb_phase_times(self.h, ms, C.byref(n)), "scbb_phase_times")
+        return dict(zip(self.PHASES, list(ms))), n.value
 
     def close(self):
         if getattr(self, "h", None):
