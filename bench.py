@@ -113,6 +113,53 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def replica_max(x: float, ws: int, device: str = "cpu") -> float:
+    """Max over all ranks of one rank's elapsed time (every rank calls it; ws = 1 returns x)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_glups(nodes: int, steps: int, ws: int, seconds: float) -> float:
+    """Whole-job lattice updates per second: every rank runs one replica of `nodes` nodes for `steps` steps."""
+    return nodes * steps * ws / seconds / 1e9
+
+
+KERNEL_SOURCES = ("paper_1904_11386_gb300/csrc/lbm_kernels.cu", "paper_1904_11386_gb300/csrc/scbb_internal.cuh")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(workload_name: str):
+    """DRAM bytes (read + write) per launch of the bulk kernel from the committed ncu summary of this
+    workload, or None when there is none or the kernel source changed since it was taken."""
+    import re
+
+    path = os.path.join(ROOT, "profiles", f"k_bulk4_{workload_name}.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", txt)
+    if not m_hash or not m_tr or m_hash.group(1) != kernel_source_hash():
+        return None
+    return int(m_tr.group(1))
+
+
 def cpu_baseline(prob, seconds=15.0):
     """The FP64 oracle as it stands, on this host's cores, on a bounded number of steps of the same workload."""
     from oracle import oracle as O
@@ -185,6 +232,10 @@ def main():
     prob, label = workload(args.workload)
     if args.impl == "reference":
         run_reference(args, prob, label, ws, rank)
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
         return
 
     import numpy as np
@@ -225,14 +276,9 @@ def main():
     bulk_ms, bulk_n = sim.scbb_kernel_time()
     sim.scbb_enable_timing(False)
     sim.scbb_sync()
-    if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replica_max(ms, ws, f"cuda:{local}")
     N = prob.n_nodes
-    value = N * args.steps * ws / (ms / 1e3) / 1e9
+    value = aggregate_glups(N, args.steps, ws, ms / 1e3)
 
     # ---- end to end through the C ABI with host buffers: upload the initial fields, K steps, read back
     barrier()
@@ -241,19 +287,21 @@ def main():
     sim.scbb_set_density(rhoA, rhoB)
     sim.scbb_step(args.steps)
     a, b, u = sim.scbb_get_fields()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = replica_max(time.perf_counter() - t0, ws, f"cuda:{local}")
     if not np.isfinite(a).all():
         raise SystemExit("non-finite densities")
-    e2e = {"value": N * args.steps * ws / e2e_s / 1e9, "unit": "GLUPS",
+    e2e = {"value": aggregate_glups(N, args.steps, ws, e2e_s), "unit": "GLUPS",
            "h2d_bytes_per_step": 5 * 4 * N / args.steps, "d2h_bytes_per_step": 5 * 4 * N / args.steps,
            "job": f"set_density (host FP64 rho^A, rho^B) + {args.steps} steps + get_fields (host FP64)"}
 
     peak, src = peak_hbm()
     bulk_avg_s = bulk_ms / max(bulk_n, 1) / 1e3
-    achieved = BYTES_PER_LU * N / bulk_avg_s / 1e9
+    n_upd = prob.nx * prob.ny * (prob.nz - 2 * prob.walls)    # nodes one bulk launch updates (no wall planes)
+    achieved = BYTES_PER_LU * n_upd / bulk_avg_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_bulk (fused 2-component stream + Shan-Chen + collide)",
-            "bytes_per_lu": BYTES_PER_LU, "peak_source": src,
+            "traffic": recorded_traffic(args.workload),
+            "kernel": "k_bulk4 (fused 2-component stream + Shan-Chen + collide)",
+            "bytes_per_lu": BYTES_PER_LU, "units_per_launch": n_upd, "peak_source": src,
             "kernel_ms": bulk_avg_s * 1e3, "kernel_share": bulk_ms / ms if ms > 0 else None}
 
     out = {"metric": "2-component D3Q19 lattice updates per second, full coupled step (GLUPS); fused bulk "

@@ -682,23 +682,37 @@ void launch_bb_boundary(const LbmParams& p, const DevState& d, const float* S, f
 
 // Mass of the state before the fresh update (bulk-kernel sums of rho(t) plus the bounce-back change of
 // the step, summed in a fixed order) and the correction factors of Eq. 18.
-__global__ void k_mass_finalize(DevState d, int nblocks, double vsys) {
-    __shared__ double sh[2][256];
+__global__ void __launch_bounds__(1024) k_mass_finalize(DevState d, int nblocks, double vsys) {
+    __shared__ double sh[2][32];
     double a = 0, b = 0;
+#pragma unroll 4
     for (int q = threadIdx.x; q < nblocks; q += blockDim.x) { a += d.mpart[2 * q]; b += d.mpart[2 * q + 1]; }
     const int nb = min(d.cnt[3], d.maxB);            // boundary list of this step, saved before re-listing
+#pragma unroll 4
     for (int q = threadIdx.x; q < nb; q += blockDim.x) {
         const float2 v = d.bdm[q];
         a += (double)v.x;
         b += (double)v.y;
     }
-    sh[0][threadIdx.x] = a;
-    sh[1][threadIdx.x] = b;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (threadIdx.x < s) { sh[0][threadIdx.x] += sh[0][threadIdx.x + s]; sh[1][threadIdx.x] += sh[1][threadIdx.x + s]; }
-        __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
     }
+    if (lane == 0) { sh[0][w] = a; sh[1][w] = b; }
+    __syncthreads();
+    if (w == 0) {
+        a = lane < (int)(blockDim.x >> 5) ? sh[0][lane] : 0.0;
+        b = lane < (int)(blockDim.x >> 5) ? sh[1][lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) { sh[0][0] = a; sh[1][0] = b; }
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         const double M[2] = {sh[0][0], sh[1][0]};
         const double ri[2] = {d.mass[0] / vsys, d.mass[1] / vsys};
@@ -900,7 +914,7 @@ void launch_bb_fresh(const LbmParams& p, const DevState& d, float* Snew, int ste
                      cudaStream_t st) {
     if (d.NM == 0) return;
     double vsys = (double)p.nxy * (p.zf1 - p.zf0);
-    k_mass_finalize<<<1, 256, 0, st>>>(d, nbulk_blocks, vsys);
+    k_mass_finalize<<<1, 1024, 0, st>>>(d, nbulk_blocks, vsys);
     k_fresh_compute<<<(d.maxF * 32 + 255) / 256, 256, 0, st>>>(p, d, Snew);
     k_fresh_apply<<<(d.maxF + 127) / 128, 128, 0, st>>>(p, d, Snew, step);
 }
