@@ -108,7 +108,10 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
 scbb_status scbb_set_density(scbb_ctx* ctx, const double* rhoA, const double* rhoB, const double* u);
 
 /* Advance n time steps (Eq. 1 for both components with the Shan-Chen force of Eq. 13, membrane forces of
- * Eq. 6-10, coupling, node update).  Asynchronous on the context stream. */
+ * Eq. 6-10, coupling, node update).  Asynchronous on the context stream.  After the context's first step,
+ * pairs of steps are replayed from a CUDA graph captured on that stream (not while timing is enabled, and
+ * never on the legacy default stream, where capture is not allowed: there every step launches its kernels
+ * one by one; environment SCBB_GRAPHS=0 does the same everywhere).  The results do not depend on it. */
 scbb_status scbb_step(scbb_ctx* ctx, long long n);
 
 /* Wait for the context stream; reports device-side errors. */

@@ -49,20 +49,35 @@ __device__ __forceinline__ float near_image(int q, float r, int L, bool per) {
     return v;
 }
 
-// A bounding-box interval [lo, hi] in one int as two FP16 values rounded outwards (lo down, hi up), so the
-// packed box always contains the exact one: a filter on it keeps every triangle the exact box keeps.
+// A bounding-box interval [lo, hi] in one int as the FP16 pair (lo rounded down, -hi rounded up in
+// magnitude), so the packed box always contains the exact one: a filter on it keeps every triangle the exact
+// box keeps.  A query interval [q0, q1] is packed as (q1 rounded up, -q0 with q0 rounded down); the two
+// intervals meet exactly when lo <= q1 and -hi <= -q0, one paired FP16 comparison.
 __device__ __forceinline__ int pack_range(float lo, float hi) {
-    const unsigned a = __half_as_ushort(__float2half_rd(lo)), b = __half_as_ushort(__float2half_ru(hi));
+    const unsigned a = __half_as_ushort(__float2half_rd(lo));
+    const unsigned b = __half_as_ushort(__hneg(__float2half_ru(hi)));
     return (int)(a | (b << 16));
 }
-__device__ __forceinline__ bool range_meets(int r, float lo, float hi) {
-    const float a = __half2float(__ushort_as_half((unsigned short)(r & 0xffff)));
-    const float b = __half2float(__ushort_as_half((unsigned short)((unsigned)r >> 16)));
-    return !(b < lo || a > hi);
+__device__ __forceinline__ __half2 as_half2(int v) {
+    return __halves2half2(__ushort_as_half((unsigned short)(v & 0xffff)),
+                          __ushort_as_half((unsigned short)((unsigned)v >> 16)));
 }
-// list entry (t, z range, x range, y range) against the query box [q0, q1]
-__device__ __forceinline__ bool entry_meets(int4 e, float3 q0, float3 q1) {
-    return range_meets(e.y, q0.z, q1.z) && range_meets(e.z, q0.x, q1.x) && range_meets(e.w, q0.y, q1.y);
+__device__ __forceinline__ __half2 query_range(float q0, float q1) {
+    return __halves2half2(__float2half_ru(q1), __hneg(__float2half_rd(q0)));
+}
+struct QueryBox {
+    __half2 z, x, y;
+};
+__device__ __forceinline__ QueryBox query_box(float3 q0, float3 q1) {
+    QueryBox b;
+    b.z = query_range(q0.z, q1.z);
+    b.x = query_range(q0.x, q1.x);
+    b.y = query_range(q0.y, q1.y);
+    return b;
+}
+// list entry (t, z range, x range, y range) against the query box
+__device__ __forceinline__ bool entry_meets(int4 e, const QueryBox& b) {
+    return __hble2(as_half2(e.y), b.z) && __hble2(as_half2(e.z), b.x) && __hble2(as_half2(e.w), b.y);
 }
 
 // The triangle lists of a w x w block of column cells of one capsule, read by a warp as one flat list:
@@ -110,33 +125,35 @@ __device__ __forceinline__ size_t cell_entry(const CellScan& s, int k) {
 }
 
 // Streams the entries of a CellScan whose boxes meet the query box [q0, q1] through a per-warp queue of
-// 64 ids in shared memory, so that the per-candidate work runs on full warps: fn(t) is called by the whole
-// warp, each lane with a candidate triangle t or with -1.  A triangle listed in several cells may come
-// more than once.
-constexpr int CAND_Q = 64;
+// CAND_Q ids in shared memory, so that the per-candidate work runs on full warps: fn(t) is called by the
+// whole warp, each lane with a candidate triangle t or with -1.  Two entries per lane are loaded per round
+// (independent loads in flight).  A triangle listed in several cells may come more than once.
+constexpr int CAND_Q = 96;
 
 template <class Fn>
 __device__ __forceinline__ void for_candidates(const DevState& d, const CellScan& cs, float3 q0, float3 q1,
                                                int* queue, int lane, Fn&& fn) {
+    const QueryBox qb = query_box(q0, q1);
     int qn = 0;                                   // warp-uniform queue length
-    for (int base = 0; base < cs.total; base += 32) {
-        const int k = base + lane;
-        const size_t at = cell_entry(cs, k);
-        bool keep = false;
-        int t = -1;
-        if (k < cs.total) {
-            const int4 e = d.tlst[at];
-            keep = entry_meets(e, q0, q1);
-            t = e.x;
-        }
+    auto enqueue = [&](bool keep, int t) {
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (keep) queue[qn + __popc(bal & ((1u << lane) - 1u))] = t;
         qn += __popc(bal);
+    };
+    for (int base = 0; base < cs.total; base += 64) {
+        const int k0 = base + lane, k1 = base + 32 + lane;
+        const size_t a0 = cell_entry(cs, k0), a1 = cell_entry(cs, k1);
+        int4 e0 = make_int4(-1, 0, 0, 0), e1 = make_int4(-1, 0, 0, 0);
+        if (k0 < cs.total) e0 = d.tlst[a0];
+        if (k1 < cs.total) e1 = d.tlst[a1];
+        enqueue(k0 < cs.total && entry_meets(e0, qb), e0.x);
+        enqueue(k1 < cs.total && entry_meets(e1, qb), e1.x);
         __syncwarp();
-        if (qn >= 32) {
+        while (qn >= 32) {
             const int tt = queue[lane];
             __syncwarp();
             if (lane < qn - 32) queue[lane] = queue[32 + lane];
+            if (lane + 32 < qn - 32) queue[lane + 32] = queue[64 + lane];
             __syncwarp();
             qn -= 32;
             fn(tt);
@@ -308,7 +325,7 @@ __global__ void k_boundary_mark(LbmParams p, DevState d) {
 // "nearest crossing, lower triangle id on ties".
 constexpr int BE_WARPS = 8;
 
-__global__ void __launch_bounds__(BE_WARPS * 32) k_boundary_elements(LbmParams p, DevState d) {
+__global__ void __launch_bounds__(BE_WARPS * 32, 4) k_boundary_elements(LbmParams p, DevState d) {
     __shared__ unsigned long long best[BE_WARPS][Q - 1];
     __shared__ float4 segP[BE_WARPS][Q - 1];          // canonical start point of each link's segment
     __shared__ float4 segD[BE_WARPS][Q - 1];          // and its direction
@@ -632,7 +649,7 @@ __global__ void __launch_bounds__(256) k_boundary(LbmParams p, DevState d, const
     if (lane == 0) { eA = ra - sA; eB = rb - sB; }
     const float oA = fa + p.omega * (eA - fa), oB = fb + p.omega * (eB - fb);
     // ---- streaming
-    double dm[2] = {0.0, 0.0};
+    float dm[2] = {0.f, 0.f};
     if (dl) {
         if (lane == 0) {
             D[n] = oA;
@@ -660,11 +677,11 @@ __global__ void __launch_bounds__(256) k_boundary(LbmParams p, DevState d, const
             atomicAdd(&d.emom[pr * d.NT + e].x, dp * cx);
             atomicAdd(&d.emom[pr * d.NT + e].y, dp * cy);
             atomicAdd(&d.emom[pr * d.NT + e].z, dp * cz);
-            dm[0] = (double)(bA - oA);
-            dm[1] = (double)(bB - oB);
+            dm[0] = bA - oA;
+            dm[1] = bB - oB;
         }
     }
-    const float dmA = wsum((float)dm[0]), dmB = wsum((float)dm[1]);
+    const float dmA = wsum(dm[0]), dmB = wsum(dm[1]);
     if (lane == 0) d.bdm[b] = make_float2(dmA, dmB);
 }
 
@@ -683,28 +700,30 @@ void launch_bb_boundary(const LbmParams& p, const DevState& d, const float* S, f
 // Mass of the state before the fresh update (bulk-kernel sums of rho(t) plus the bounce-back change of
 // the step, summed in a fixed order) and the correction factors of Eq. 18.
 __global__ void __launch_bounds__(1024) k_mass_finalize(DevState d, int nblocks, double vsys) {
-    __shared__ double sh[2][32];
-    double a = 0, b = 0;
-#pragma unroll 4
-    for (int q = threadIdx.x; q < nblocks; q += blockDim.x) { a += d.mpart[2 * q]; b += d.mpart[2 * q + 1]; }
+    // The bounce-back mass changes are small: FP32 partials per thread and per warp.  FP64 (slow on this
+    // part) only in warp 0, for the bulk partials and the 32 warp sums.
+    __shared__ float shf[2][32];
+    __shared__ double sh[2][1];
+    float fa = 0.f, fb = 0.f;
     const int nb = min(d.cnt[3], d.maxB);            // boundary list of this step, saved before re-listing
 #pragma unroll 4
     for (int q = threadIdx.x; q < nb; q += blockDim.x) {
         const float2 v = d.bdm[q];
-        a += (double)v.x;
-        b += (double)v.y;
+        fa += v.x;
+        fb += v.y;
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
+        fa += __shfl_xor_sync(0xffffffffu, fa, o);
+        fb += __shfl_xor_sync(0xffffffffu, fb, o);
     }
-    if (lane == 0) { sh[0][w] = a; sh[1][w] = b; }
+    if (lane == 0) { shf[0][w] = fa; shf[1][w] = fb; }
     __syncthreads();
     if (w == 0) {
-        a = lane < (int)(blockDim.x >> 5) ? sh[0][lane] : 0.0;
-        b = lane < (int)(blockDim.x >> 5) ? sh[1][lane] : 0.0;
+        double a = lane < (int)(blockDim.x >> 5) ? (double)shf[0][lane] : 0.0;
+        double b = lane < (int)(blockDim.x >> 5) ? (double)shf[1][lane] : 0.0;
+        for (int q = lane; q < nblocks; q += 32) { a += d.mpart[2 * q]; b += d.mpart[2 * q + 1]; }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             a += __shfl_xor_sync(0xffffffffu, a, o);

@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(CAP_THREADS) k_capsule_reduce(DevState d, int 
     // per-thread and per-warp partials in FP32 (a few dozen terms each), the block sum in FP64
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     if (use_tvol) {
+#pragma unroll 4
         for (int t = threadIdx.x; t < c.nt; t += blockDim.x) acc[0] += d.tvol[c.t0 + t];
     } else {
         const float3 r0 = ld3(d.X[c.v0]);
@@ -52,6 +53,7 @@ __global__ void __launch_bounds__(CAP_THREADS) k_capsule_reduce(DevState d, int 
     }
     float mn[3] = {1e30f, 1e30f, 1e30f}, mx[3] = {-1e30f, -1e30f, -1e30f};
     const float4 r0c = d.X[c.v0];       // vertex sums relative to the first vertex (small FP32 terms)
+#pragma unroll 4
     for (int v = threadIdx.x; v < c.nv; v += blockDim.x) {
         const float4 q = d.X[c.v0 + v];
         acc[1] += q.x - r0c.x; acc[2] += q.y - r0c.y; acc[3] += q.z - r0c.z;

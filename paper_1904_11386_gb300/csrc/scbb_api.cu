@@ -30,6 +30,12 @@ struct scbb_ctx {
     int timing = 0;
     std::vector<cudaEvent_t> ev;     // pairs
     size_t ev_used = 0;
+    // replay of a captured pair of steps
+    cudaGraphExec_t gexec = nullptr;
+    int gkey = -1;                    // (cur << 1) | step parity at the capture
+    long long gpair_launches = 0;
+    int graph_off = 0;                // capture failed: launch one by one
+    long long eager_steps = 0;
     // per-phase timing (timing mode 2): PHASES + 1 events per step
     std::vector<cudaEvent_t> pev;
     size_t pev_steps = 0;
@@ -416,6 +422,7 @@ scbb_status scbb_set_density(scbb_ctx* c, const double* rhoA, const double* rhoB
     if (!c || !rhoA || !rhoB) return SCBB_E_INVAL;
     if (c->broken) return SCBB_E_STATE;
     const size_t N = c->lp.N;
+    c->cur = 0;                       // state in lattice 0 at step 0 (the captured step pairs stay valid)
     std::vector<float> h(5 * N);
     for (size_t n = 0; n < N; n++) {
         h[n] = (float)rhoA[n];
@@ -452,63 +459,132 @@ scbb_status scbb_set_density(scbb_ctx* c, const double* rhoA, const double* rhoB
     return check_bb_flags(c);
 }
 
-scbb_status scbb_step(scbb_ctx* c, long long n) {
-    if (!c || n < 0) return SCBB_E_INVAL;
-    if (c->broken) return SCBB_E_STATE;
+// One time step on the context stream (kernel launches only), advancing cur, steps and the launch count.
+static void enqueue_step(scbb_ctx* c) {
     const bool ibm = c->fl.coupling == 1 && c->d.NV > 0;
     const bool bb = c->d.owner != nullptr;
     const int mode = ibm ? 1 : (bb ? 2 : 0);
-    for (long long s = 0; s < n; s++) {
-        const int step = (int)(c->steps & 0x7fffffff);
-        c->mark(0);
-        if (ibm) {
-            // membrane forces at X(t), spread onto the lattice (2-point immersed boundary)
-            c->launches += launch_membrane_forces(c->lp, c->d, false, step, c->st);
-            launch_ibm_spread(c->lp, c->d, c->st);
-            c->launches += 1;
-        }
-        c->mark(1);
-        if (c->lp.walls) {
-            launch_wall_ghost(c->lp, c->d.S[c->cur], c->d.wall_rho, c->d.ghost, c->st);
-            c->launches += 2;
-        }
-        c->mark(2);
-        const bool timed = c->timing && c->ev_used + 2 <= c->ev.size();
-        if (timed) cudaEventRecord(c->ev[c->ev_used], c->st);
-        launch_bulk(c->lp, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.rho, c->d.ghost, c->d.Fibm,
-                    bb ? c->d.bmask : c->d.mask, c->d.u, c->d.err, mode, c->d.mpart, c->st);
-        if (timed) {
-            cudaEventRecord(c->ev[c->ev_used + 1], c->st);
-            c->ev_used += 2;
-        }
+    const int step = (int)(c->steps & 0x7fffffff);     // the kernels use its parity only
+    c->mark(0);
+    if (ibm) {
+        // membrane forces at X(t), spread onto the lattice (2-point immersed boundary)
+        c->launches += launch_membrane_forces(c->lp, c->d, false, step, c->st);
+        launch_ibm_spread(c->lp, c->d, c->st);
+        c->launches += 1;
+    }
+    c->mark(1);
+    if (c->lp.walls) {
+        launch_wall_ghost(c->lp, c->d.S[c->cur], c->d.wall_rho, c->d.ghost, c->st);
+        c->launches += 2;
+    }
+    c->mark(2);
+    const bool timed = c->timing && c->ev_used + 2 <= c->ev.size();
+    if (timed) cudaEventRecord(c->ev[c->ev_used], c->st);
+    launch_bulk(c->lp, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.rho, c->d.ghost, c->d.Fibm,
+                bb ? c->d.bmask : c->d.mask, c->d.u, c->d.err, mode, c->d.mpart, c->st);
+    if (timed) {
+        cudaEventRecord(c->ev[c->ev_used + 1], c->st);
+        c->ev_used += 2;
+    }
+    c->launches++;
+    c->mark(3);
+    if (ibm) {
+        launch_ibm_interp(c->lp, c->d, c->st);
         c->launches++;
-        c->mark(3);
-        if (ibm) {
-            launch_ibm_interp(c->lp, c->d, c->st);
-            c->launches++;
+    }
+    if (bb) {
+        // boundary nodes (bounce-back, wetting) -> membrane forces with coupling, node update ->
+        // classification at X(t+1), boundary list -> fresh nodes
+        launch_bb_boundary(c->lp, c->d, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.ghost, step, c->d.err, c->st);
+        c->launches += 2;
+        c->mark(4);
+        c->launches += launch_membrane_forces(c->lp, c->d, true, step, c->st);
+        c->mark(5);
+        launch_bb_classify(c->lp, c->d, step, false, c->st);
+        c->launches += 5;
+        c->mark(6);
+        launch_bb_fresh(c->lp, c->d, c->d.S[1 - c->cur], step, bulk_grid_blocks(c->lp), c->st);
+        c->launches += 3;
+    } else {
+        c->mark(4);
+        c->mark(5);
+        c->mark(6);
+    }
+    c->mark(7);
+    if (c->timing == 2 && (c->pev_steps + 1) * (SCBB_PHASES + 1) <= c->pev.size()) c->pev_steps++;
+    c->cur ^= 1;
+    c->steps++;
+}
+
+static bool graphs_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("SCBB_GRAPHS");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
+// Records two consecutive steps, starting from the current lattice and step parity, into a CUDA graph.
+// The kernels take the step number for its parity only and every other argument is fixed for the life of
+// the context, so the pair can be replayed whenever the lattice and the parity are back where the capture
+// started.  Nothing runs during the capture; the host counters are restored afterwards.  If capturing or
+// instantiating fails the context keeps launching the same kernels one by one.
+static void capture_pair(scbb_ctx* c) {
+    const int cur0 = c->cur;
+    const long long steps0 = c->steps, launches0 = c->launches;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        c->graph_off = 1;
+        return;
+    }
+    enqueue_step(c);
+    enqueue_step(c);
+    const cudaError_t e = cudaStreamEndCapture(c->st, &g);
+    const long long per_pair = c->launches - launches0;
+    c->cur = cur0;
+    c->steps = steps0;
+    c->launches = launches0;
+    if (e != cudaSuccess || !g) {
+        cudaGetLastError();
+        c->graph_off = 1;
+        return;
+    }
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    if (cudaGraphInstantiate(&c->gexec, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        c->gexec = nullptr;
+        c->graph_off = 1;
+    }
+    cudaGraphDestroy(g);
+    c->gkey = (cur0 << 1) | (int)(steps0 & 1);
+    c->gpair_launches = per_pair;
+}
+
+scbb_status scbb_step(scbb_ctx* c, long long n) {
+    if (!c || n < 0) return SCBB_E_INVAL;
+    if (c->broken) return SCBB_E_STATE;
+    long long left = n;
+    while (left > 0) {
+        // pairs of steps replay a captured graph (not while timing, which needs per-launch events, and not
+        // before one step has run eagerly, which sets the kernels' launch attributes)
+        if (left >= 2 && graphs_enabled() && !c->graph_off && c->timing == 0 && c->eager_steps > 0) {
+            const int key = (c->cur << 1) | (int)(c->steps & 1);
+            if (!c->gexec || ((key ^ c->gkey) != 0 && (key ^ c->gkey) != 3)) capture_pair(c);
+            if (c->gexec && key == c->gkey) {
+                for (; left >= 2; left -= 2) {
+                    CUDA_TRY(c, cudaGraphLaunch(c->gexec, c->st));
+                    c->steps += 2;
+                    c->launches += c->gpair_launches;
+                }
+                continue;
+            }
         }
-        if (bb) {
-            // boundary nodes (bounce-back, wetting) -> membrane forces with coupling, node update ->
-            // classification at X(t+1), boundary list -> fresh nodes
-            launch_bb_boundary(c->lp, c->d, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.ghost, step, c->d.err, c->st);
-            c->launches += 2;
-            c->mark(4);
-            c->launches += launch_membrane_forces(c->lp, c->d, true, step, c->st);
-            c->mark(5);
-            launch_bb_classify(c->lp, c->d, step, false, c->st);
-            c->launches += 5;
-            c->mark(6);
-            launch_bb_fresh(c->lp, c->d, c->d.S[1 - c->cur], step, bulk_grid_blocks(c->lp), c->st);
-            c->launches += 3;
-        } else {
-            c->mark(4);
-            c->mark(5);
-            c->mark(6);
-        }
-        c->mark(7);
-        if (c->timing == 2 && (c->pev_steps + 1) * (SCBB_PHASES + 1) <= c->pev.size()) c->pev_steps++;
-        c->cur ^= 1;
-        c->steps++;
+        enqueue_step(c);            // one step launched kernel by kernel
+        c->eager_steps++;
+        left--;
     }
     CUDA_TRY(c, cudaGetLastError());
     return SCBB_OK;
@@ -674,7 +750,9 @@ const char* scbb_last_error(const scbb_ctx* c) {
 
 void scbb_destroy(scbb_ctx* c) {
     if (!c) return;
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
     for (auto& e : c->ev) cudaEventDestroy(e);
+    for (auto& e : c->pev) cudaEventDestroy(e);
     delete c;
 }
 

@@ -140,9 +140,12 @@ def scbb_population_moments_noalloc(f_dev, nx, ny, nz, walls, stream=None):
 
 
 class Sim:
-    """One simulation context: a torch-owned device workspace, the torch current stream, and the C calls."""
+    """One simulation context: a torch-owned device workspace, a CUDA stream and the C calls.
 
-    def __init__(self, prob, rhoA=None, rhoB=None, u=None, device="cuda", set_state=True):
+    stream: the torch stream the context runs on; by default a stream of its own (steps are replayed as CUDA
+    graphs, which cannot be captured on the legacy default stream)."""
+
+    def __init__(self, prob, rhoA=None, rhoB=None, u=None, device="cuda", set_state=True, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -172,7 +175,7 @@ class Sim:
         if nbytes == 0:
             raise ScbbError("scbb_workspace_bytes rejected the problem description")
         self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
-        self.stream = torch.cuda.current_stream(self.workspace.device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.workspace.device)
         h = C.c_void_p()
         st = L.scbb_create(C.byref(self.lat), C.byref(self.fl), nm, self.meshes,
                            C.c_void_p(self.workspace.data_ptr()), C.c_size_t(nbytes),

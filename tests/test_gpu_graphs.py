@@ -1,0 +1,46 @@
+"""Steps replayed from a captured CUDA graph (pairs of steps) give the state of the same steps launched one
+by one: bit-exact for the fluid (no atomics on that path), and for the bounce-back coupling identical owner
+fields with populations and vertices within 1e-5: its element momenta are float atomics whose summation
+order is free, and the fresh-node mass correction multiplies that round-off by C0 (2500) times
+sum(rho_init)/rho_init^c; a replay from the wrong lattice or step parity would differ at O(1)."""
+import numpy as np
+import pytest
+
+from paper_1904_11386_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _pair(prob, n):
+    from paper_1904_11386_gb300 import scbb
+
+    a = scbb.Sim(prob)
+    b = scbb.Sim(prob)
+    a.scbb_step(1)               # the first step of a context always runs launch by launch
+    b.scbb_step(1)
+    for _ in range(n):           # single steps: never replayed
+        a.scbb_step(1)
+    b.scbb_step(n)               # pairs replayed from the graph
+    assert a.scbb_launch_count() == b.scbb_launch_count()
+    return a, b
+
+
+def test_graph_replay_fluid_bit_exact():
+    p = inputs.small_problem(n=32, walls=1, coupling=1, capsule=False, noise=1e-3)
+    a, b = _pair(p, 12)
+    assert np.array_equal(a.scbb_get_populations(), b.scbb_get_populations())
+
+
+def test_graph_replay_bounce_back():
+    cap = inputs.Capsule(centre=(15.3, 11.8, 12.6), radius=6.0, subdiv=3, kS=0.02, kB=1e-3, kV=2.0, colour=0.3)
+    p = inputs.Problem(name="g", nx=32, ny=24, nz=26, walls=1, coupling=0, psi_kind=0, z_interface=13,
+                       capsules=[cap], noise=1e-4, seed=13, u_lo=(-0.002, 0, 0), u_hi=(0.002, 0, 0))
+    a, b = _pair(p, 13)
+    oa, _, _ = a.scbb_get_owner()
+    ob, _, _ = b.scbb_get_owner()
+    assert np.array_equal(oa, ob)
+    fa, fb = a.scbb_get_populations(), b.scbb_get_populations()
+    assert np.abs(fa - fb).max() < 1e-5 * np.abs(fa).max()
+    Xa, _, _ = a.scbb_get_vertices()
+    Xb, _, _ = b.scbb_get_vertices()
+    assert np.abs(Xa - Xb).max() < 1e-5
