@@ -168,8 +168,9 @@ scbb_status scbb_kernel_time(scbb_ctx* ctx, double* ms, long long* launches);
 scbb_status scbb_phase_times(scbb_ctx* ctx, double* ms, long long* steps);
 
 /* FP64 mass and momentum of populations already on the device, for callers that cannot allocate device
- * memory (code running while a CUDA graph is captured, or inside a framework that owns the device
- * allocator).  The paper has no counterpart; this is a utility of this library.
+ * memory: a framework that owns the device allocator and forbids side allocations, or a loop that must not
+ * take cudaMalloc's implicit synchronisation or risk running out of memory mid-run.  The paper has no
+ * counterpart; this is a utility of this library.
  *   dev_f   device pointer, FP32 post-streaming populations in the layout f[c][i][x + nx*(y + ny*z)] (c = 0, 1;
  *           i in the D3Q19 order of scbb_get_populations), 2*19*nx*ny*nz floats, caller-owned, read only
  *   walls   1: the planes z = 0 and z = nz-1 are wall nodes and are left out of the sums; 0: all nodes

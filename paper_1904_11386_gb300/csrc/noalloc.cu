@@ -1,7 +1,8 @@
 // scbb_population_moments_noalloc: FP64 mass and momentum of a device population array with no device
 // allocation at all.  Its block partial sums live in a file-scope __device__ array instead of a workspace,
-// for callers that cannot allocate device memory themselves: code that runs while a CUDA graph is being
-// captured, or inside a host framework whose device allocator is owned by someone else.
+// for callers that cannot allocate device memory themselves: a host framework that owns the device
+// allocator and forbids side allocations, or a loop that must not take cudaMalloc's implicit
+// synchronisation and the risk of an out-of-memory failure in the middle of a run.
 #include <stdio.h>
 
 #include <mutex>

@@ -1,7 +1,8 @@
 """The allocation-free moments entry point (scbb_population_moments_noalloc) against scbb_get_diag.
 
-It serves callers that cannot allocate device memory (for example code that runs while a CUDA graph is
-captured): its scratch is a fixed device array inside the library.  This file is collected last so that a
+It serves callers that cannot allocate device memory (a framework that owns the device allocator, or a
+loop that must not take cudaMalloc's synchronisation): its scratch is a fixed device array inside the
+library.  This file is collected last so that a
 run stopping at the first failure has run every other test before it."""
 import numpy as np
 import pytest
