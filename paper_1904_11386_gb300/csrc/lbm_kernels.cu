@@ -551,9 +551,12 @@ __device__ __forceinline__ void window6(const float* row, int x, int nx, float w
     w[5] = row[x + 4 == nx ? 0 : x + 4];
 }
 
-// MODE 0: fluid only, 1: immersed-boundary force at marked nodes, 2: bounce-back membranes (nodes marked in
-// `mask` are the boundary kernel's; this kernel still writes their densities, and every CTA writes the FP64
-// sums of rho^A, rho^B over its nodes to mpart).
+// MODE 0: fluid only, 1: immersed-boundary force at marked nodes, 2: bounce-back membranes.  In mode 2 every
+// quad is stored whole, boundary nodes included: the boundary kernel, which runs next, rewrites every slot
+// of a boundary node that is read later (its own rest and uncut directions; across a cut link the node on
+// the other side, itself a boundary node, bounces into the slot; the slot towards a wall node is never
+// read), so a uniform vector store is both correct and cheapest.  The kernel writes the densities of all
+// nodes, and every CTA the FP64 sums of rho^A, rho^B over its nodes to mpart.
 template <bool TAU1, int MODE, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 k_bulk4(LbmParams p, const float* __restrict__ S, float* __restrict__ D, float* __restrict__ rho_out,
@@ -699,7 +702,7 @@ k_bulk4(LbmParams p, const float* __restrict__ S, float* __restrict__ D, float* 
 
             const unsigned int n0 = (unsigned)x + (unsigned)gy * nx + (unsigned)z * p.nxy;
             uint32_t bits = 0;
-            if (IBM || BB) bits = (__ldg(mask + (n0 >> 5)) >> (n0 & 31)) & 0xFu;
+            if (IBM) bits = (__ldg(mask + (n0 >> 5)) >> (n0 & 31)) & 0xFu;
             float uA[4][3], uB[4][3], ra[4], rb[4], jxa[4], jya[4], jza[4];
             {
                 const int ms = rel & 1;
@@ -786,29 +789,7 @@ k_bulk4(LbmParams p, const float* __restrict__ S, float* __restrict__ D, float* 
                         oB[k] = FB4[k] + p.omega * (oB[k] - FB4[k]);
                     }
                 }
-                if (BB && bits) {
-                    // quad holding boundary nodes: store the others one by one
-                    if (dir_z(I) != 0 && wall_next && is_wall_plane(p, z + dir_z(I))) {
-                        const float* U = (z + dir_z(I) == 0) ? p.ulo : p.uhi;
-                        const float cU = 6.f * dir_w(I) * (dir_x(I) * U[0] + dir_y(I) * U[1] + dir_z(I) * U[2]);
-                        const unsigned int drow = (unsigned)ry[1 + dir_y(I)] + (unsigned)(z + dir_z(I)) * p.nxy;
-#pragma unroll
-                        for (int k = 0; k < 4; k++) {
-                            if ((bits >> k) & 1u) continue;
-                            int xd = x + k + dir_x(I);
-                            xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
-                            D[(size_t)dir_opp(I) * p.N + drow + xd] = oA[k] - cU * ra[k];
-                            D[(size_t)(Q + dir_opp(I)) * p.N + drow + xd] = oB[k] - cU * rb[k];
-                        }
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < 4; k++) {
-                            if ((bits >> k) & 1u) continue;
-                            D[(size_t)I * p.N + n0 + k] = oA[k];
-                            D[(size_t)(Q + I) * p.N + n0 + k] = oB[k];
-                        }
-                    }
-                } else if (dir_z(I) != 0 && wall_next && is_wall_plane(p, z + dir_z(I))) {
+                if (dir_z(I) != 0 && wall_next && is_wall_plane(p, z + dir_z(I))) {
                     // half-way bounce-back on a moving wall (Eq. 11), stored where the node pulls opp(I) from
                     const float* U = (z + dir_z(I) == 0) ? p.ulo : p.uhi;
                     const float cU = 6.f * dir_w(I) * (dir_x(I) * U[0] + dir_y(I) * U[1] + dir_z(I) * U[2]);
