@@ -23,9 +23,10 @@ sys.path.insert(0, ROOT)
 
 from paper_1904_11386_gb300 import inputs  # noqa: E402
 
-# Algorithmic bytes per lattice update of the fused bulk kernel (both components): read 2 x 19 FP32
-# populations, write 2 x 19 FP32 populations, write rho^A and rho^B.
+# Algorithmic bytes per lattice update of the fused bulk kernel (both components): read 2 x 19 populations,
+# write 2 x 19 populations (4 bytes each in FP32 storage, 2 in FP16), write rho^A and rho^B (FP32).
 BYTES_PER_LU = 2 * 19 * 4 * 2 + 2 * 4
+BYTES_PER_LU_FP16 = 2 * 19 * 2 * 2 + 2 * 4
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -160,6 +161,46 @@ def recorded_traffic(workload_name: str):
     return int(m_tr.group(1))
 
 
+def fp16_beside(prob, args, ws, local, n_upd, peak):
+    """The same workload with the populations stored as FP16 (FP32 arithmetic), timed the same way: K steps
+    as the user call runs them, then K steps with events around every bulk launch."""
+    import copy
+
+    import torch
+
+    from paper_1904_11386_gb300 import scbb
+
+    p16 = copy.deepcopy(prob)
+    p16.storage = 1
+    rhoA, rhoB = p16.initial_density()
+    sim = scbb.Sim(p16, rhoA, rhoB, device=f"cuda:{local}")
+    st = sim.stream
+    sim.scbb_step(args.warmup)
+    sim.scbb_sync()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    sim.scbb_step(args.steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = replica_max(e0.elapsed_time(e1), ws, f"cuda:{local}")
+    sim.scbb_enable_timing(True)
+    sim.scbb_step(args.steps)
+    bulk_ms, bulk_n = sim.scbb_kernel_time()
+    sim.scbb_enable_timing(False)
+    sim.scbb_sync()
+    sim.close()
+    bulk_s = bulk_ms / max(bulk_n, 1) / 1e3
+    achieved = BYTES_PER_LU_FP16 * n_upd / bulk_s / 1e9
+    return {"value": aggregate_glups(prob.n_nodes, args.steps, ws, ms / 1e3), "unit": "GLUPS",
+            "ms_per_step": ms / args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "bytes_per_lu": BYTES_PER_LU_FP16, "kernel_ms": bulk_s * 1e3,
+                         "traffic": recorded_traffic(args.workload + "-fp16")},
+            "error_vs_fp64_oracle": "densities 1e-3 relative after 200 steps (32^3), mass offset 1e-5; "
+                                    "tests/test_gpu_fp16.py"}
+
+
 def cpu_baseline(prob, seconds=15.0):
     """The FP64 oracle as it stands, on this host's cores, on a bounded number of steps of the same workload."""
     from oracle import oracle as O
@@ -225,11 +266,17 @@ def main():
     ap.add_argument("--workload", default="adsorb128")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-storage figures beside the FP32 ones")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
+                    help="population storage on the GPU (arithmetic is FP32 either way)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     ws, rank, local = dist_setup()
     prob, label = workload(args.workload)
+    if args.storage == "fp16":
+        prob.storage = 1
+        label += "; populations stored as FP16"
     if args.impl == "reference":
         run_reference(args, prob, label, ws, rank)
         if ws > 1:
@@ -302,11 +349,12 @@ def main():
     peak, src = peak_hbm()
     bulk_avg_s = bulk_ms / max(bulk_n, 1) / 1e3
     n_upd = prob.nx * prob.ny * (prob.nz - 2 * prob.walls)    # nodes one bulk launch updates (no wall planes)
-    achieved = BYTES_PER_LU * n_upd / bulk_avg_s / 1e9
+    bpl = BYTES_PER_LU_FP16 if args.storage == "fp16" else BYTES_PER_LU
+    achieved = bpl * n_upd / bulk_avg_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": recorded_traffic(args.workload),
+            "traffic": recorded_traffic(args.workload + ("-fp16" if args.storage == "fp16" else "")),
             "kernel": "k_bulk4 (fused 2-component stream + Shan-Chen + collide)",
-            "bytes_per_lu": BYTES_PER_LU, "units_per_launch": n_upd, "peak_source": src,
+            "bytes_per_lu": bpl, "units_per_launch": n_upd, "peak_source": src,
             "kernel_ms": bulk_avg_s * 1e3, "kernel_share": bulk_avg_s * 1e3 / (ms / args.steps) if ms > 0 else None,
             "kernel_timing": f"{bulk_n} bulk launches bracketed by CUDA events (second region of {args.steps} steps)"}
 
@@ -317,13 +365,16 @@ def main():
            "dtype": "f32", "data": "synthetic",
            "config": {"workload": label, "lattice": [prob.nx, prob.ny, prob.nz], "nodes": N,
                       "vertices": int(sum(sim.nv)), "parallelism": f"replicas x{ws}",
-                      "l2": "inputs larger than L2 (populations 2 x 319 MB)"},
+                      "storage": args.storage,
+                      "l2": f"inputs larger than L2 (populations 2 x {2 * 19 * N * (2 if args.storage == 'fp16' else 4) / 1e6:.0f} MB)"},
            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+    sim.close()
+    if args.storage == "fp32" and not args.no_fp16:
+        out["fp16_storage"] = fp16_beside(prob, args, ws, local, n_upd, peak)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
-    sim.close()
     if ws > 1:
         import torch.distributed as dist
 

@@ -68,7 +68,10 @@ typedef struct {
  *             density offset (Eq. 15): rho_virtual = 2 |colour| (rho_maj - rho_min)
  *   C0, mass_correction   adaptive fresh-node mass correction (Eq. 18), C0 = 2500 in the paper
  *   pp_eps, pp_d0         particle-particle repulsion (Eq. 26, Sec. III.E), 0.5 and 1.25 in the paper
- *   storage   0: FP32 populations (the only value this build accepts) */
+ *   storage   0: FP32 populations; 1: populations stored as IEEE FP16 (arithmetic stays FP32; each stored
+ *             value is rounded to nearest, about 2.4e-4 relative), half the population bytes.  FP16 needs
+ *             the row-vectorised bulk geometry (nx a multiple of 4, nx/4 a power of two up to 32 or a
+ *             multiple of 32), else scbb_create returns SCBB_E_UNSUPPORTED.  Not in the paper. */
 typedef struct {
     double tau, G;
     int psi_kind;

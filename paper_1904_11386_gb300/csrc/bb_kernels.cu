@@ -272,7 +272,10 @@ __global__ void k_class_col(LbmParams p, DevState d, int init) {
 // Clears the boundary and fresh bits of the previous step's lists and the per-column counters.
 __global__ void k_lists_reset(DevState d) {
     const int nb = d.cnt[0], nf = d.cnt[1];
-    if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt[3] = nb;     // list the boundary kernel of this step used
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        d.cnt[3] = nb;          // list the boundary kernel of this step used
+        d.cnt[4] = nf;          // fresh nodes replaced at the end of the previous step
+    }
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < d.NM * d.CW * d.CW; q += gridDim.x * blockDim.x) {
         d.ccnt[q] = 0;
         d.tcnt[q] = 0;
@@ -535,8 +538,9 @@ __global__ void k_bb_vrho(LbmParams p, DevState d) {
 // (Eq. 13-15; reactions to the crossed element), BGK collision, streaming with moving half-way
 // bounce-back on walls and cut links (Eq. 11) and the exchanged momentum (Eq. 12).
 // ------------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_boundary(LbmParams p, DevState d, const float* __restrict__ S,
-                                                  float* __restrict__ D, const float* __restrict__ ghost,
+template <typename T>
+__global__ void __launch_bounds__(256) k_boundary(LbmParams p, DevState d, const T* __restrict__ S,
+                                                  T* __restrict__ D, const float* __restrict__ ghost,
                                                   int step, int* err) {
     const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -556,8 +560,8 @@ __global__ void __launch_bounds__(256) k_boundary(LbmParams p, DevState d, const
         int zs = z - cz;
         if (!p.walls) zs = wrapi(zs, p.nz);
         const unsigned int src = (unsigned)wrapi(x - cx, p.nx) + (unsigned)wrapi(y - cy, p.ny) * p.nx + (unsigned)zs * p.nxy;
-        fa = __ldg(S + (size_t)i * p.N + src);
-        fb = __ldg(S + (size_t)(Q + i) * p.N + src);
+        fa = pld(S + (size_t)i * p.N + src);
+        fb = pld(S + (size_t)(Q + i) * p.N + src);
     }
     const float ra = wsum(fa), rb = wsum(fb);
     const float jx = wsum(cx * (fa + fb)), jy = wsum(cy * (fa + fb)), jz = wsum(cz * (fa + fb));
@@ -652,17 +656,17 @@ __global__ void __launch_bounds__(256) k_boundary(LbmParams p, DevState d, const
     float dm[2] = {0.f, 0.f};
     if (dl) {
         if (lane == 0) {
-            D[n] = oA;
-            D[(size_t)Q * p.N + n] = oB;
+            pst(D + n, oA);
+            pst(D + (size_t)Q * p.N + n, oB);
         } else if (wall) {
             const float* U = zn == 0 ? p.ulo : p.uhi;
             const float cU = 6.f * wi * (cx * U[0] + cy * U[1] + cz * U[2]);
             const unsigned int tgt = (unsigned)(wrapi(x + cx, p.nx) + wrapi(y + cy, p.ny) * p.nx) + (unsigned)zn * p.nxy;
-            D[(size_t)dir_opp(i) * p.N + tgt] = oA - cU * ra;
-            D[(size_t)(Q + dir_opp(i)) * p.N + tgt] = oB - cU * rb;
+            pst(D + (size_t)dir_opp(i) * p.N + tgt, oA - cU * ra);
+            pst(D + (size_t)(Q + dir_opp(i)) * p.N + tgt, oB - cU * rb);
         } else if (om == me || e < 0) {
-            D[(size_t)i * p.N + n] = oA;
-            D[(size_t)(Q + i) * p.N + n] = oB;
+            pst(D + (size_t)i * p.N + n, oA);
+            pst(D + (size_t)(Q + i) * p.N + n, oB);
         } else {
             // moving half-way bounce-back (Eq. 11) with the element velocity; exchanged momentum (Eq. 12)
             const int4 T = d.tri[e];
@@ -671,8 +675,8 @@ __global__ void __launch_bounds__(256) k_boundary(LbmParams p, DevState d, const
                         vz = (V0.z + V1.z + V2.z) * (1.f / 3.f);
             const float cv = 6.f * wi * (cx * vx + cy * vy + cz * vz);
             const float bA = oA - cv * ra, bB = oB - cv * rb;
-            D[(size_t)dir_opp(i) * p.N + m] = bA;
-            D[(size_t)(Q + dir_opp(i)) * p.N + m] = bB;
+            pst(D + (size_t)dir_opp(i) * p.N + m, bA);
+            pst(D + (size_t)(Q + dir_opp(i)) * p.N + m, bB);
             const float dp = oA + bA + oB + bB;
             atomicAdd(&d.emom[pr * d.NT + e].x, dp * cx);
             atomicAdd(&d.emom[pr * d.NT + e].y, dp * cy);
@@ -690,25 +694,36 @@ void launch_bb_boundary(const LbmParams& p, const DevState& d, const float* S, f
     if (d.NM == 0) return;
     const unsigned blocks = (unsigned)(((size_t)d.maxB * 32 + 255) / 256);
     k_bb_vrho<<<blocks, 256, 0, st>>>(p, d);
-    k_boundary<<<blocks, 256, 0, st>>>(p, d, S, D, ghost, step, err);
+    if (p.half)
+        k_boundary<__half><<<blocks, 256, 0, st>>>(p, d, reinterpret_cast<const __half*>(S),
+                                                   reinterpret_cast<__half*>(D), ghost, step, err);
+    else
+        k_boundary<float><<<blocks, 256, 0, st>>>(p, d, S, D, ghost, step, err);
 }
 
 // ------------------------------------------------------------------------------------------------------
 // Fresh nodes
 // ------------------------------------------------------------------------------------------------------
 
-// Mass of the state before the fresh update (bulk-kernel sums of rho(t) plus the bounce-back change of
-// the step, summed in a fixed order) and the correction factors of Eq. 18.
-__global__ void __launch_bounds__(1024) k_mass_finalize(DevState d, int nblocks, double vsys) {
-    // The bounce-back mass changes are small: FP32 partials per thread and per warp.  FP64 (slow on this
-    // part) only in warp 0, for the bulk partials and the 32 warp sums.
+// Mass of the state before the fresh update and the correction factors of Eq. 18.  Collision and streaming
+// conserve each component's mass exactly, so M(t) - M(0) is the running FP64 sum of the changes the method
+// makes on purpose: the moving bounce-back of every boundary node of this step (Eq. 11) and the fresh-node
+// replacements of the previous step (Eq. 16).  Summing M(t) over the FP32 lattice instead would carry its
+// rounding (systematic over uniform regions), which Eq. 18 multiplies by C0 sum(rho_init)/rho_init^c.
+__global__ void __launch_bounds__(1024) k_mass_finalize(DevState d, double vsys) {
+    // the changes are small: FP32 partials per thread and per warp, FP64 only in warp 0
     __shared__ float shf[2][32];
-    __shared__ double sh[2][1];
     float fa = 0.f, fb = 0.f;
-    const int nb = min(d.cnt[3], d.maxB);            // boundary list of this step, saved before re-listing
+    const int nb = min(d.cnt[3], d.maxB);
+    const int nf = min(d.cnt[4], d.maxF);
 #pragma unroll 4
     for (int q = threadIdx.x; q < nb; q += blockDim.x) {
         const float2 v = d.bdm[q];
+        fa += v.x;
+        fb += v.y;
+    }
+    for (int q = threadIdx.x; q < nf; q += blockDim.x) {
+        const float2 v = d.fdm[q];
         fa += v.x;
         fb += v.y;
     }
@@ -723,27 +738,25 @@ __global__ void __launch_bounds__(1024) k_mass_finalize(DevState d, int nblocks,
     if (w == 0) {
         double a = lane < (int)(blockDim.x >> 5) ? (double)shf[0][lane] : 0.0;
         double b = lane < (int)(blockDim.x >> 5) ? (double)shf[1][lane] : 0.0;
-        for (int q = lane; q < nblocks; q += 32) { a += d.mpart[2 * q]; b += d.mpart[2 * q + 1]; }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             a += __shfl_xor_sync(0xffffffffu, a, o);
             b += __shfl_xor_sync(0xffffffffu, b, o);
         }
-        if (lane == 0) { sh[0][0] = a; sh[1][0] = b; }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const double M[2] = {sh[0][0], sh[1][0]};
-        const double ri[2] = {d.mass[0] / vsys, d.mass[1] / vsys};
-        for (int c = 0; c < 2; c++) {
-            const double dM = M[c] - d.mass[c];
-            d.mass[4 + c] = d.mass_correction ? 1.0 - d.C0 * (ri[0] + ri[1]) / ri[c] * dM / vsys : 1.0;
+        if (lane == 0) {
+            const double dM[2] = {d.mass[2] + a, d.mass[3] + b};
+            const double ri[2] = {d.mass[0] / vsys, d.mass[1] / vsys};
+            for (int c = 0; c < 2; c++) {
+                d.mass[2 + c] = dM[c];
+                d.mass[4 + c] = d.mass_correction ? 1.0 - d.C0 * (ri[0] + ri[1]) / ri[c] * dM[c] / vsys : 1.0;
+            }
         }
     }
 }
 
 // density of node m of the new state (pull from S)
-__device__ __forceinline__ void pulled_rho(const LbmParams& p, const float* __restrict__ S, int m, float& ra, float& rb) {
+template <typename T>
+__device__ __forceinline__ void pulled_rho(const LbmParams& p, const T* __restrict__ S, int m, float& ra, float& rb) {
     const int z = m / p.nxy, r = m - z * p.nxy, y = r / p.nx, x = r - y * p.nx;
     Cols k;
     k.cx[0] = wrapi(x - 1, p.nx); k.cx[1] = x; k.cx[2] = wrapi(x + 1, p.nx);
@@ -757,7 +770,8 @@ __device__ __forceinline__ void pulled_rho(const LbmParams& p, const float* __re
 
 // One warp per fresh node: lanes 0-17 pull the densities of the 18 neighbours, then the warp scans the
 // capsule's triangle centroids for the nearest element.
-__global__ void __launch_bounds__(256) k_fresh_compute(LbmParams p, DevState d, const float* __restrict__ S) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_fresh_compute(LbmParams p, DevState d, const T* __restrict__ S) {
     __shared__ int queue[8][CAND_Q];
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -868,12 +882,16 @@ __global__ void __launch_bounds__(256) k_fresh_compute(LbmParams p, DevState d, 
 
 // Writes f_eq(rho_fresh, v) into the slots the fresh node pulls from (Eq. 2, 16-18) and hands the element
 // the removed minus the created momentum.
-__global__ void k_fresh_apply(LbmParams p, DevState d, float* __restrict__ S, int step) {
+template <typename T>
+__global__ void k_fresh_apply(LbmParams p, DevState d, T* __restrict__ S, int step) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const int nf = min(d.cnt[1], d.maxF);
     if (q >= nf) return;
     const float4 a = d.fnew[2 * q];
-    if (a.z == 0.f) return;
+    if (a.z == 0.f) {
+        d.fdm[q] = make_float2(0.f, 0.f);          // populations kept
+        return;
+    }
     const float4 vv = d.fnew[2 * q + 1];
     const int e = __float_as_int(vv.w);
     const int n = d.flist[q];
@@ -886,18 +904,24 @@ __global__ void k_fresh_apply(LbmParams p, DevState d, float* __restrict__ S, in
     const int pz[3] = {zm * p.nxy, z * p.nxy, zp * p.nxy};
     const float uu = vv.x * vv.x + vv.y * vv.y + vv.z * vv.z;
     float rem[3] = {0.f, 0.f, 0.f};
+    float dA = 0.f, dB = 0.f;                      // mass change of the replacement, per component
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         const unsigned int m = k.cx[1 - dir_x(i)] + k.ry[1 - dir_y(i)] + pz[1 - dir_z(i)];
         const float cu = dir_x(i) * vv.x + dir_y(i) * vv.y + dir_z(i) * vv.z;
         const float e0 = dir_w(i) * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
-        float* sa = S + (size_t)i * p.N + m;
-        float* sb = S + (size_t)(Q + i) * p.N + m;
-        const float old = *sa + *sb;
+        T* sa = S + (size_t)i * p.N + m;
+        T* sb = S + (size_t)(Q + i) * p.N + m;
+        const float oa = pldc(sa), ob = pldc(sb);
+        const float old = oa + ob;
         rem[0] += dir_x(i) * old; rem[1] += dir_y(i) * old; rem[2] += dir_z(i) * old;
-        *sa = e0 * a.x;
-        *sb = e0 * a.y;
+        const float na = pround(e0 * a.x, S), nb = pround(e0 * a.y, S);
+        dA += na - oa;
+        dB += nb - ob;
+        pst(sa, na);
+        pst(sb, nb);
     }
+    d.fdm[q] = make_float2(dA, dB);
     const float rt = a.x + a.y;
     const int nx = (step + 1) & 1;
     atomicAdd(&d.epend[nx * d.NT + e].x, rem[0] - rt * vv.x);
@@ -929,13 +953,18 @@ void launch_bb_init(const LbmParams& p, const DevState& d, cudaStream_t st) {
     k_bb_init<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(p, d);
 }
 
-void launch_bb_fresh(const LbmParams& p, const DevState& d, float* Snew, int step, int nbulk_blocks,
-                     cudaStream_t st) {
+void launch_bb_fresh(const LbmParams& p, const DevState& d, float* Snew, int step, cudaStream_t st) {
     if (d.NM == 0) return;
     double vsys = (double)p.nxy * (p.zf1 - p.zf0);
-    k_mass_finalize<<<1, 1024, 0, st>>>(d, nbulk_blocks, vsys);
-    k_fresh_compute<<<(d.maxF * 32 + 255) / 256, 256, 0, st>>>(p, d, Snew);
-    k_fresh_apply<<<(d.maxF + 127) / 128, 128, 0, st>>>(p, d, Snew, step);
+    k_mass_finalize<<<1, 1024, 0, st>>>(d, vsys);
+    if (p.half) {
+        __half* Sh = reinterpret_cast<__half*>(Snew);
+        k_fresh_compute<__half><<<(d.maxF * 32 + 255) / 256, 256, 0, st>>>(p, d, Sh);
+        k_fresh_apply<__half><<<(d.maxF + 127) / 128, 128, 0, st>>>(p, d, Sh, step);
+    } else {
+        k_fresh_compute<float><<<(d.maxF * 32 + 255) / 256, 256, 0, st>>>(p, d, Snew);
+        k_fresh_apply<float><<<(d.maxF + 127) / 128, 128, 0, st>>>(p, d, Snew, step);
+    }
 }
 
 }  // namespace scbb

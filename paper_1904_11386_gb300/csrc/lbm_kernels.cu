@@ -19,41 +19,46 @@
 namespace scbb {
 
 // ------------------------------------------------------------------------------------------------------
-// Initial state: slot (c, i, y) holds the population that node x = y + c_i pulls, f_eq,i(rho^c(x), u(x)).
+// Initial state: every fluid node x writes f_eq,i(rho^c(x), u(x)) into the slot it pulls direction i from,
+// (c, i, x - c_i); the rest population closes the node's mass over the values as stored.  The lattice is
+// zeroed beforehand (slots only wall nodes would pull from stay 0).
 // ------------------------------------------------------------------------------------------------------
-__global__ void k_init_state(LbmParams p, float* __restrict__ S, const float* __restrict__ rho_st,
+template <typename T>
+__global__ void k_init_state(LbmParams p, T* __restrict__ S, const float* __restrict__ rho_st,
                              const float* __restrict__ u_st) {
-    unsigned int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
-    int z = n / p.nxy;
-    int r = n - z * p.nxy;
-    int y = r / p.nx, x = r - y * p.nx;
+    const int z = n / p.nxy;
+    if (is_wall_plane(p, z)) return;
+    const int r = n - z * p.nxy;
+    const int y = r / p.nx, x = r - y * p.nx;
+    const float ux = u_st[n], uy = u_st[p.N + n], uz = u_st[2 * p.N + n];
+    const float a = rho_st[n], b = rho_st[p.N + n];
+    const float uu = ux * ux + uy * uy + uz * uz;
+    float sa = 0.f, sb = 0.f;
 #pragma unroll
-    for (int i = 0; i < Q; i++) {
-        int zz = z + dir_z(i);
-        float v0 = 0.f, v1 = 0.f;
-        bool ok = true;
-        if (p.walls) ok = (zz >= 1 && zz <= p.nz - 2);
-        else zz = wrapi(zz, p.nz);
-        if (ok) {
-            unsigned int m = wrapi(x + dir_x(i), p.nx) + p.nx * (wrapi(y + dir_y(i), p.ny) + p.ny * zz);
-            float ux = u_st[m], uy = u_st[p.N + m], uz = u_st[2 * p.N + m];
-            float cu = dir_x(i) * ux + dir_y(i) * uy + dir_z(i) * uz;
-            float uu = ux * ux + uy * uy + uz * uz;
-            float e = dir_w(i) * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
-            v0 = e * rho_st[m];
-            v1 = e * rho_st[p.N + m];
-        }
-        S[(size_t)i * p.N + n] = v0;
-        S[(size_t)(Q + i) * p.N + n] = v1;
+    for (int i = 1; i < Q; i++) {
+        const float cu = dir_x(i) * ux + dir_y(i) * uy + dir_z(i) * uz;
+        const float e = dir_w(i) * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
+        const float va = pround(e * a, S), vb = pround(e * b, S);
+        sa += va;
+        sb += vb;
+        int zs = z - dir_z(i);
+        if (!p.walls) zs = wrapi(zs, p.nz);
+        const unsigned int m = wrapi(x - dir_x(i), p.nx) + p.nx * (wrapi(y - dir_y(i), p.ny) + p.ny * zs);
+        pst(S + (size_t)i * p.N + m, va);
+        pst(S + (size_t)(Q + i) * p.N + m, vb);
     }
+    pst(S + n, a - sa);
+    pst(S + (size_t)Q * p.N + n, b - sb);
 }
 
 // ------------------------------------------------------------------------------------------------------
 // Virtual densities of the wall planes (neutral wetting): the wall node (x, y, 0) is seen with the mean
 // density of its five fluid neighbours (x, y, 1), (x +- 1, y, 1), (x, y +- 1, 1); likewise at the top.
 // ------------------------------------------------------------------------------------------------------
-__global__ void k_wall_planes_rho(LbmParams p, const float* __restrict__ S, float* __restrict__ wall_rho) {
+template <typename T>
+__global__ void k_wall_planes_rho(LbmParams p, const T* __restrict__ S, float* __restrict__ wall_rho) {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= 2 * p.nxy) return;
     int w = q / p.nxy;
@@ -459,21 +464,19 @@ struct Quad {
     float a[4];
 };
 
-__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
-
 // populations of direction i (component base cb = S + c*Q*N) arriving at the four nodes x..x+3 of a row
-template <int I>
-__device__ __forceinline__ float4 pull4(const LbmParams& p, const float* __restrict__ cb, unsigned int srow, int x,
+template <int I, typename T>
+__device__ __forceinline__ float4 pull4(const LbmParams& p, const T* __restrict__ cb, unsigned int srow, int x,
                                         int segl, int W, bool multi, int q_in_warp, unsigned int lanes) {
-    const float* base = cb + (size_t)I * p.N + srow;
-    float4 v = ldg4(base + x);
+    const T* base = cb + (size_t)I * p.N + srow;
+    float4 v = pld4(base + x);
     if (dir_x(I) == 1) {            // source x - 1: {x-1, x, x+1, x+2}
         float pw = __shfl_sync(lanes, v.w, (segl + W - 1) & (W - 1), W);
-        if (multi && q_in_warp == 0) pw = __ldg(base + (x == 0 ? p.nx - 1 : x - 1));
+        if (multi && q_in_warp == 0) pw = pld(base + (x == 0 ? p.nx - 1 : x - 1));
         v = make_float4(pw, v.x, v.y, v.z);
     } else if (dir_x(I) == -1) {    // source x + 1: {x+1, x+2, x+3, x+4}
         float nx0 = __shfl_sync(lanes, v.x, (segl + 1) & (W - 1), W);
-        if (multi && q_in_warp == 31) nx0 = __ldg(base + (x + 4 == p.nx ? 0 : x + 4));
+        if (multi && q_in_warp == 31) nx0 = pld(base + (x + 4 == p.nx ? 0 : x + 4));
         v = make_float4(v.y, v.z, v.w, nx0);
     }
     return v;
@@ -501,22 +504,22 @@ struct PullCtx {
     unsigned int rows[3][3];        // [1 - c_y][1 - c_z] row start index of the source row
 };
 
-template <int I>
-__device__ __forceinline__ void pull_dir(const LbmParams& p, const float* __restrict__ S, const PullCtx& pc, int x,
+template <int I, typename T>
+__device__ __forceinline__ void pull_dir(const LbmParams& p, const T* __restrict__ S, const PullCtx& pc, int x,
                                          int segl, int W, bool multi, int qw, Mom4& m) {
     const unsigned int srow = pc.rows[1 - dir_y(I)][1 - dir_z(I)];
-    const float4 a = pull4<I>(p, S, srow, x, segl, W, multi, qw, 0xffffffffu);
-    const float4 b = pull4<I>(p, S + (size_t)Q * p.N, srow, x, segl, W, multi, qw, 0xffffffffu);
+    const float4 a = pull4<I, T>(p, S, srow, x, segl, W, multi, qw, 0xffffffffu);
+    const float4 b = pull4<I, T>(p, S + (size_t)Q * p.N, srow, x, segl, W, multi, qw, 0xffffffffu);
     acc_dir<I>(m, a, b);
 }
 
 template <int... Is>
 struct DirList {};
 
-template <int I, int... Rest>
-__device__ __forceinline__ void pull_all(const LbmParams& p, const float* __restrict__ S, const PullCtx& pc, int x,
+template <typename T, int I, int... Rest>
+__device__ __forceinline__ void pull_all(const LbmParams& p, const T* __restrict__ S, const PullCtx& pc, int x,
                                          int segl, int W, bool multi, int qw, Mom4& m, DirList<I, Rest...>) {
-    pull_dir<I>(p, S, pc, x, segl, W, multi, qw, m);
+    pull_dir<I, T>(p, S, pc, x, segl, W, multi, qw, m);
     if constexpr (sizeof...(Rest) > 0) pull_all(p, S, pc, x, segl, W, multi, qw, m, DirList<Rest...>{});
 }
 
@@ -537,10 +540,10 @@ __device__ __forceinline__ PullCtx pull_ctx(const LbmParams& p, const int ry[3],
     return pc;
 }
 
-template <int I>
-__device__ __forceinline__ float4 pull_comp(const LbmParams& p, const float* __restrict__ cb, const PullCtx& pc, int x,
+template <int I, typename T>
+__device__ __forceinline__ float4 pull_comp(const LbmParams& p, const T* __restrict__ cb, const PullCtx& pc, int x,
                                             int segl, int W, bool multi, int qw, unsigned int lanes) {
-    return pull4<I>(p, cb, pc.rows[1 - dir_y(I)][1 - dir_z(I)], x, segl, W, multi, qw, lanes);
+    return pull4<I, T>(p, cb, pc.rows[1 - dir_y(I)][1 - dir_z(I)], x, segl, W, multi, qw, lanes);
 }
 
 // six psi values x-1 .. x+4 of one ring row (periodic in x)
@@ -551,19 +554,18 @@ __device__ __forceinline__ void window6(const float* row, int x, int nx, float w
     w[5] = row[x + 4 == nx ? 0 : x + 4];
 }
 
-// MODE 0: fluid only, 1: immersed-boundary force at marked nodes, 2: bounce-back membranes.  In mode 2 every
-// quad is stored whole, boundary nodes included: the boundary kernel, which runs next, rewrites every slot
-// of a boundary node that is read later (its own rest and uncut directions; across a cut link the node on
-// the other side, itself a boundary node, bounces into the slot; the slot towards a wall node is never
-// read), so a uniform vector store is both correct and cheapest.  The kernel writes the densities of all
-// nodes, and every CTA the FP64 sums of rho^A, rho^B over its nodes to mpart.
-template <bool TAU1, int MODE, int NT, int MINB>
+// MODE 0: fluid only (also with bounce-back membranes), 1: immersed-boundary force at marked nodes.  With
+// bounce-back membranes every quad is stored whole, boundary nodes included: the boundary kernel, which runs
+// next, rewrites every slot of a boundary node that is read later (its own rest and uncut directions; across
+// a cut link the node on the other side, itself a boundary node, bounces into the slot; the slot towards a
+// wall node is never read), so a uniform vector store is both correct and cheapest.  The kernel writes the
+// densities of all nodes.
+template <bool TAU1, int MODE, int NT, int MINB, typename T>
 __global__ void __launch_bounds__(NT, MINB)
-k_bulk4(LbmParams p, const float* __restrict__ S, float* __restrict__ D, float* __restrict__ rho_out,
+k_bulk4(LbmParams p, const T* __restrict__ S, T* __restrict__ D, float* __restrict__ rho_out,
         const float* __restrict__ ghost, const float* __restrict__ Fibm, const uint32_t* __restrict__ mask,
-        float* __restrict__ u_out, int* __restrict__ err, int TY, double* __restrict__ mpart) {
+        float* __restrict__ u_out, int* __restrict__ err, int TY) {
     constexpr bool IBM = MODE == 1;
-    constexpr bool BB = MODE == 2;
     extern __shared__ float ring[];                      // psi [4][2][RR][nx], then moments [2][5][RR][nx]
     const int nx = p.nx;
     const int NQ = nx >> 2;
@@ -588,14 +590,7 @@ k_bulk4(LbmParams p, const float* __restrict__ S, float* __restrict__ D, float* 
     const int nzf = p.zf1 - p.zf0;
     const int zs = p.zf0 + (int)(((long long)blockIdx.y * nzf) / gridDim.y);
     const int ze = p.zf0 + (int)(((long long)(blockIdx.y + 1) * nzf) / gridDim.y);
-    if (zs >= ze) {
-        if (BB && threadIdx.x == 0) {
-            mpart[2 * (blockIdx.y * gridDim.x + blockIdx.x)] = 0.0;
-            mpart[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 1] = 0.0;
-        }
-        return;
-    }
-    float msumA = 0.f, msumB = 0.f;    // this thread's density sums (FP32; the block sum is FP64)
+    if (zs >= ze) return;
     const int dz = (blockIdx.y & 1) ? 1 : -1;
     const int z_first = dz > 0 ? zs : ze - 1;
     const int L = ze - zs;
@@ -773,6 +768,10 @@ k_bulk4(LbmParams p, const float* __restrict__ S, float* __restrict__ D, float* 
                         const float cuB = dir_x(I) * uB[k][0] + dir_y(I) * uB[k][1] + dir_z(I) * uB[k][2];
                         eA = dir_w(I) * ra[k] * (1.f + 3.f * cuA + 4.5f * cuA * cuA - 1.5f * uuA[k]);
                         eB = dir_w(I) * rb[k] * (1.f + 3.f * cuB + 4.5f * cuB * cuB - 1.5f * uuB[k]);
+                        if (TAU1) {             // the values as stored (exact for FP32)
+                            eA = pround(eA, D);
+                            eB = pround(eB, D);
+                        }
                         sA[k] += eA;
                         sB[k] += eB;
                     }
@@ -780,8 +779,8 @@ k_bulk4(LbmParams p, const float* __restrict__ S, float* __restrict__ D, float* 
                     oB[k] = eB;
                 }
                 if (!TAU1) {
-                    const float4 fa = pull_comp<I>(p, S, pc, x, segl, W, multi, qw, lanes);
-                    const float4 fb = pull_comp<I>(p, S + (size_t)Q * p.N, pc, x, segl, W, multi, qw, lanes);
+                    const float4 fa = pull_comp<I, T>(p, S, pc, x, segl, W, multi, qw, lanes);
+                    const float4 fb = pull_comp<I, T>(p, S + (size_t)Q * p.N, pc, x, segl, W, multi, qw, lanes);
                     const float FA4[4] = {fa.x, fa.y, fa.z, fa.w}, FB4[4] = {fb.x, fb.y, fb.z, fb.w};
 #pragma unroll
                     for (int k = 0; k < 4; k++) {
@@ -798,13 +797,12 @@ k_bulk4(LbmParams p, const float* __restrict__ S, float* __restrict__ D, float* 
                     for (int k = 0; k < 4; k++) {
                         int xd = x + k + dir_x(I);
                         xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
-                        D[(size_t)dir_opp(I) * p.N + drow + xd] = oA[k] - cU * ra[k];
-                        D[(size_t)(Q + dir_opp(I)) * p.N + drow + xd] = oB[k] - cU * rb[k];
+                        pst(D + (size_t)dir_opp(I) * p.N + drow + xd, oA[k] - cU * ra[k]);
+                        pst(D + (size_t)(Q + dir_opp(I)) * p.N + drow + xd, oB[k] - cU * rb[k]);
                     }
                 } else {
-                    *reinterpret_cast<float4*>(D + (size_t)I * p.N + n0) = make_float4(oA[0], oA[1], oA[2], oA[3]);
-                    *reinterpret_cast<float4*>(D + (size_t)(Q + I) * p.N + n0) =
-                        make_float4(oB[0], oB[1], oB[2], oB[3]);
+                    pst4(D + (size_t)I * p.N + n0, make_float4(oA[0], oA[1], oA[2], oA[3]));
+                    pst4(D + (size_t)(Q + I) * p.N + n0, make_float4(oB[0], oB[1], oB[2], oB[3]));
                 }
             };
             // moving directions first, the rest population last (it closes the mass, see k_bulk)
@@ -820,30 +818,6 @@ k_bulk4(LbmParams p, const float* __restrict__ S, float* __restrict__ D, float* 
             emit(std::integral_constant<int, 0>{});
             *reinterpret_cast<float4*>(rho_out + n0) = make_float4(ra[0], ra[1], ra[2], ra[3]);
             *reinterpret_cast<float4*>(rho_out + p.N + n0) = make_float4(rb[0], rb[1], rb[2], rb[3]);
-            if (BB) {
-                msumA += (ra[0] + ra[1]) + (ra[2] + ra[3]);
-                msumB += (rb[0] + rb[1]) + (rb[2] + rb[3]);
-            }
-        }
-    }
-    if (BB) {
-        // FP64 block sums of the densities (used by the fresh-node mass correction)
-        __shared__ double red[2][32];
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        double dA = msumA, dB = msumB;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            dA += __shfl_down_sync(0xffffffffu, dA, o);
-            dB += __shfl_down_sync(0xffffffffu, dB, o);
-        }
-        __syncthreads();
-        if (lane == 0) { red[0][w] = dA; red[1][w] = dB; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double a = 0.0, b = 0.0;
-            for (int q = 0; q < (int)(blockDim.x >> 5); q++) { a += red[0][q]; b += red[1][q]; }
-            mpart[2 * (blockIdx.y * gridDim.x + blockIdx.x)] = a;
-            mpart[2 * (blockIdx.y * gridDim.x + blockIdx.x) + 1] = b;
         }
     }
 }
@@ -920,21 +894,35 @@ static int b4_config() {
     return v;
 }
 
+template <bool TAU1, int MODE, int NT, int MINB, typename T>
+static void launch_b4t(const LbmParams& q, dim3 grid, int threads, size_t smem, int TY, const T* S, T* D,
+                       float* rho, const float* ghost, const float* Fibm, const uint32_t* mask, float* u, int* err,
+                       cudaStream_t st) {
+    static size_t attr = 0;
+    if (smem > attr) {
+        cudaFuncSetAttribute(k_bulk4<TAU1, MODE, NT, MINB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        attr = smem;
+    }
+    k_bulk4<TAU1, MODE, NT, MINB, T><<<grid, threads, smem, st>>>(q, S, D, rho, ghost, Fibm, mask, u, err, TY);
+}
+
+// S, D point to FP32 or (q.half) FP16 populations
 template <bool TAU1, int MODE, int NT, int MINB>
 static void launch_b4(const LbmParams& q, dim3 grid, int threads, size_t smem, int TY, const float* S, float* D,
                       float* rho, const float* ghost, const float* Fibm, const uint32_t* mask, float* u, int* err,
-                      double* mpart, cudaStream_t st) {
-    static size_t attr = 0;
-    if (smem > attr) {
-        cudaFuncSetAttribute(k_bulk4<TAU1, MODE, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = smem;
-    }
-    k_bulk4<TAU1, MODE, NT, MINB><<<grid, threads, smem, st>>>(q, S, D, rho, ghost, Fibm, mask, u, err, TY, mpart);
+                      cudaStream_t st) {
+    if (q.half)
+        launch_b4t<TAU1, MODE, NT, MINB, __half>(q, grid, threads, smem, TY, reinterpret_cast<const __half*>(S),
+                                                 reinterpret_cast<__half*>(D), rho, ghost, Fibm, mask, u, err, st);
+    else
+        launch_b4t<TAU1, MODE, NT, MINB, float>(q, grid, threads, smem, TY, S, D, rho, ghost, Fibm, mask, u, err,
+                                                st);
 }
 
 template <int NT, int MINB>
 static bool try_b4(const LbmParams& p, const float* S, float* D, float* rho, const float* ghost, const float* Fibm,
-                   const uint32_t* mask, float* u, int* err, int mode, double* mpart, cudaStream_t st,
+                   const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st,
                    int* blocks) {
     LbmParams q;
     dim3 grid;
@@ -946,14 +934,12 @@ static bool try_b4(const LbmParams& p, const float* S, float* D, float* rho, con
         return true;
     }
     const bool tau1 = p.omega == 1.0f;
-#define B4_ARGS q, grid, threads, smem, TY, S, D, rho, ghost, Fibm, mask, u, err, mpart, st
+#define B4_ARGS q, grid, threads, smem, TY, S, D, rho, ghost, Fibm, mask, u, err, st
     if (tau1) {
         if (mode == 1) launch_b4<true, 1, NT, MINB>(B4_ARGS);
-        else if (mode == 2) launch_b4<true, 2, NT, MINB>(B4_ARGS);
         else launch_b4<true, 0, NT, MINB>(B4_ARGS);
     } else {
         if (mode == 1) launch_b4<false, 1, NT, MINB>(B4_ARGS);
-        else if (mode == 2) launch_b4<false, 2, NT, MINB>(B4_ARGS);
         else launch_b4<false, 0, NT, MINB>(B4_ARGS);
     }
 #undef B4_ARGS
@@ -961,22 +947,22 @@ static bool try_b4(const LbmParams& p, const float* S, float* D, float* rho, con
 }
 
 static bool dispatch_b4(const LbmParams& p, const float* S, float* D, float* rho, const float* ghost,
-                        const float* Fibm, const uint32_t* mask, float* u, int* err, int mode, double* mpart,
+                        const float* Fibm, const uint32_t* mask, float* u, int* err, int mode,
                         cudaStream_t st, int* blocks) {
-    if (b4_config() == 2) return try_b4<256, 2>(p, S, D, rho, ghost, Fibm, mask, u, err, mode, mpart, st, blocks);
-    return try_b4<512, 1>(p, S, D, rho, ghost, Fibm, mask, u, err, mode, mpart, st, blocks);
+    if (b4_config() == 2) return try_b4<256, 2>(p, S, D, rho, ghost, Fibm, mask, u, err, mode, st, blocks);
+    return try_b4<512, 1>(p, S, D, rho, ghost, Fibm, mask, u, err, mode, st, blocks);
 }
 
 bool bulk_vectorised(const LbmParams& p) {
     int nb = 0;
     return bulk_variant() == 4 && dispatch_b4(p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                              nullptr, 0, nullptr, 0, &nb);
+                                              nullptr, 0, 0, &nb);
 }
 
 int bulk_grid_blocks(const LbmParams& p) {
     int nb = 0;
     if (bulk_variant() == 4 && dispatch_b4(p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                           0, nullptr, 0, &nb))
+                                           0, 0, &nb))
         return nb;
     dim3 g;
     int th;
@@ -985,9 +971,9 @@ int bulk_grid_blocks(const LbmParams& p) {
 }
 
 void launch_bulk(const LbmParams& p, const float* S, float* D, float* rho, const float* ghost, const float* Fibm,
-                 const uint32_t* mask, float* u, int* err, int mode, double* mpart, cudaStream_t st) {
+                 const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st) {
     const bool ibm = mode == 1;
-    if (bulk_variant() == 4 && dispatch_b4(p, S, D, rho, ghost, Fibm, mask, u, err, mode, mpart, st, nullptr)) return;
+    if (bulk_variant() == 4 && dispatch_b4(p, S, D, rho, ghost, Fibm, mask, u, err, mode, st, nullptr)) return;
     dim3 grid;
     int threads;
     bulk_geometry(p, grid, threads);
@@ -1012,11 +998,18 @@ void launch_bulk(const LbmParams& p, const float* S, float* D, float* rho, const
 }
 
 void launch_init_state(const LbmParams& p, float* S, const float* rho_st, const float* u_st, cudaStream_t st) {
-    k_init_state<<<(p.N + 255) / 256, 256, 0, st>>>(p, S, rho_st, u_st);
+    if (p.half)
+        k_init_state<__half><<<(p.N + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<__half*>(S), rho_st, u_st);
+    else
+        k_init_state<float><<<(p.N + 255) / 256, 256, 0, st>>>(p, S, rho_st, u_st);
 }
 
 void launch_wall_ghost(const LbmParams& p, const float* S, float* wall_rho, float* ghost, cudaStream_t st) {
-    k_wall_planes_rho<<<(2 * p.nxy + 255) / 256, 256, 0, st>>>(p, S, wall_rho);
+    if (p.half)
+        k_wall_planes_rho<__half><<<(2 * p.nxy + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<const __half*>(S),
+                                                                          wall_rho);
+    else
+        k_wall_planes_rho<float><<<(2 * p.nxy + 255) / 256, 256, 0, st>>>(p, S, wall_rho);
     k_wall_ghost<<<(4 * p.nxy + 255) / 256, 256, 0, st>>>(p, wall_rho, ghost);
 }
 
@@ -1024,7 +1017,9 @@ void launch_wall_ghost(const LbmParams& p, const float* S, float* wall_rho, floa
 // Exports of the current state.  what = 0: rho^A, rho^B, u (5 N floats); what = 1: populations in the
 // [c][node][i] order (38 N floats).  Wall nodes report 0.
 // ------------------------------------------------------------------------------------------------------
-__global__ void k_export(LbmParams p, const float* __restrict__ S, float* __restrict__ out, int what) {
+// what = 2, 3: the populations of component A or B only, [node][i] (19 N floats)
+template <typename T>
+__global__ void k_export(LbmParams p, const T* __restrict__ S, float* __restrict__ out, int what) {
     unsigned int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
     int z = n / p.nxy;
@@ -1048,24 +1043,35 @@ __global__ void k_export(LbmParams p, const float* __restrict__ S, float* __rest
         }
         return;
     }
-    float ra = 0.f, rb = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+    if (what == 2 || what == 3) {
+        const int c = what - 2;
+#pragma unroll
+        for (int i = 0; i < Q; i++) out[(size_t)n * Q + i] = f[c * Q + i];
+        return;
+    }
+    // read-out in FP64: the momentum is a sum of populations with +- cancellations, whose FP32 rounding
+    // (about 19 * 2^-24 of the largest population) would otherwise show in the exported velocity
+    double ra = 0.0, rb = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         ra += f[i]; rb += f[Q + i];
-        const float fs = f[i] + f[Q + i];
+        const double fs = (double)f[i] + (double)f[Q + i];
         jx += dir_x(i) * fs; jy += dir_y(i) * fs; jz += dir_z(i) * fs;
     }
-    const float rt = ra + rb;
-    const float irt = rt > 0.f ? 1.f / rt : 0.f;
-    out[n] = ra;
-    out[p.N + n] = rb;
-    out[2 * (size_t)p.N + n] = jx * irt;
-    out[3 * (size_t)p.N + n] = jy * irt;
-    out[4 * (size_t)p.N + n] = jz * irt;
+    const double rt = ra + rb;
+    const double irt = rt > 0.0 ? 1.0 / rt : 0.0;
+    out[n] = (float)ra;
+    out[p.N + n] = (float)rb;
+    out[2 * (size_t)p.N + n] = (float)(jx * irt);
+    out[3 * (size_t)p.N + n] = (float)(jy * irt);
+    out[4 * (size_t)p.N + n] = (float)(jz * irt);
 }
 
 void launch_export(const LbmParams& p, const float* S, float* out, int what, cudaStream_t st) {
-    k_export<<<(p.N + 255) / 256, 256, 0, st>>>(p, S, out, what);
+    if (p.half)
+        k_export<__half><<<(p.N + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<const __half*>(S), out, what);
+    else
+        k_export<float><<<(p.N + 255) / 256, 256, 0, st>>>(p, S, out, what);
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -1075,7 +1081,8 @@ void launch_export(const LbmParams& p, const float* S, float* out, int what, cud
 constexpr int RED_THREADS = 256;
 constexpr int RED_BLOCKS = 1024;
 
-__global__ void __launch_bounds__(RED_THREADS) k_moments_partial(LbmParams p, const float* __restrict__ S,
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_moments_partial(LbmParams p, const T* __restrict__ S,
                                                                  double* __restrict__ part) {
     double acc[5] = {0, 0, 0, 0, 0};
     for (unsigned int n = blockIdx.x * blockDim.x + threadIdx.x; n < p.N; n += gridDim.x * blockDim.x) {
@@ -1125,7 +1132,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_sum_partials(const double* __re
 
 void launch_moments_reduce(const LbmParams& p, const float* S, double* red, cudaStream_t st) {
     // red must hold 8 + 5 * RED_BLOCKS doubles; result in red[0..4]
-    k_moments_partial<<<RED_BLOCKS, RED_THREADS, 0, st>>>(p, S, red + 8);
+    if (p.half)
+        k_moments_partial<__half><<<RED_BLOCKS, RED_THREADS, 0, st>>>(p, reinterpret_cast<const __half*>(S), red + 8);
+    else
+        k_moments_partial<float><<<RED_BLOCKS, RED_THREADS, 0, st>>>(p, S, red + 8);
     k_sum_partials<<<1, RED_THREADS, 0, st>>>(red + 8, RED_BLOCKS, 5, red);
 }
 

@@ -96,7 +96,7 @@ bool valid_fluid(const scbb_fluid* f) {
     if (!f || !(f->tau > 0.5) || !isfinite(f->G)) return false;
     if (f->psi_kind != 0 && f->psi_kind != 1) return false;
     if (f->coupling != 0 && f->coupling != 1) return false;
-    if (f->storage != 0) return false;
+    if (f->storage != 0 && f->storage != 1) return false;
     if (f->pp_eps != 0.0 && !(f->pp_d0 > 0.0)) return false;
     return true;
 }
@@ -119,6 +119,7 @@ LbmParams make_params(const scbb_lattice* lat, const scbb_fluid* fl) {
     p.omega = (float)(1.0 / fl->tau);
     p.G = (float)fl->G;
     p.psi_kind = fl->psi_kind;
+    p.half = fl->storage == 1 ? 1 : 0;
     for (int k = 0; k < 3; k++) {
         p.g[k] = (float)fl->g[k];
         p.ulo[k] = (float)lat->u_lo[k];
@@ -179,8 +180,10 @@ size_t layout(const scbb_lattice* lat, const scbb_fluid* fl, int nm, const scbb_
     const size_t nxy = (size_t)lat->nx * lat->ny;
     const int NV = total(ms, nm, false), NT = total(ms, nm, true);
     DevState t{};
-    t.S[0] = c.take<float>(2 * Q * N);
-    t.S[1] = c.take<float>(2 * Q * N);
+    // FP16 storage halves the lattices; each still holds the 5 N floats staged through it by set_density
+    const size_t pop_floats = fl->storage == 1 ? (size_t)Q * N : (size_t)2 * Q * N;
+    t.S[0] = c.take<float>(pop_floats);
+    t.S[1] = c.take<float>(pop_floats);
     t.rho = c.take<float>(2 * N);
     const bool ibm = fl->coupling == 1 && NV > 0;
     t.u = ibm ? c.take<float>(3 * N) : nullptr;
@@ -240,7 +243,7 @@ size_t layout(const scbb_lattice* lat, const scbb_fluid* fl, int nm, const scbb_
         t.cbox = c.take<int4>(2 * (nm > 0 ? nm : 1));
         t.ccnt = c.take<int>((size_t)nm * z.CW * z.CW);
         t.czs = c.take<float>((size_t)nm * z.CW * z.CW * BB_MAXC);
-        t.mpart = c.take<double>((size_t)2 * (bulk_grid_blocks(lp) + 1));
+        t.fdm = c.take<float2>(z.maxF);
         t.mass = c.take<double>(8);
         t.trec = c.take<float4>((size_t)4 * nt1);
         t.tcnt = c.take<int>((size_t)nm * z.CW * z.CW);
@@ -306,9 +309,9 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
     std::string why;
     if (!valid_lattice(lat) || !valid_fluid(fl) || !dev_workspace) return SCBB_E_INVAL;
     if (!valid_meshes(n_mesh, meshes, why)) return SCBB_E_MESH;
-    if (fl->coupling == 0 && n_mesh > 0) {
-        // bounce-back membranes run with the row-vectorised bulk kernel (nx a multiple of 4, nx/4 a power of
-        // two up to 32 or a multiple of 32)
+    if ((fl->coupling == 0 && n_mesh > 0) || fl->storage == 1) {
+        // bounce-back membranes and FP16 storage run with the row-vectorised bulk kernel (nx a multiple of 4,
+        // nx/4 a power of two up to 32 or a multiple of 32)
         LbmParams lp = make_params(lat, fl);
         if (!bulk_vectorised(lp)) return SCBB_E_UNSUPPORTED;
     }
@@ -404,8 +407,9 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
     if (n_mesh > 0)
         CUDA_TRY(c, cudaMemcpyAsync(d.cap, caps.data(), sizeof(CapDev) * n_mesh, cudaMemcpyHostToDevice, c->st));
     const size_t N = c->lp.N;
-    CUDA_TRY(c, cudaMemsetAsync(d.S[0], 0, sizeof(float) * 2 * Q * N, c->st));
-    CUDA_TRY(c, cudaMemsetAsync(d.S[1], 0, sizeof(float) * 2 * Q * N, c->st));
+    const size_t pop_bytes = (c->lp.half ? sizeof(uint16_t) : sizeof(float)) * 2 * Q * N;
+    CUDA_TRY(c, cudaMemsetAsync(d.S[0], 0, pop_bytes, c->st));
+    CUDA_TRY(c, cudaMemsetAsync(d.S[1], 0, pop_bytes, c->st));
     CUDA_TRY(c, cudaMemsetAsync(d.rho, 0, sizeof(float) * 2 * N, c->st));
     if (d.Fibm) {
         CUDA_TRY(c, cudaMemsetAsync(d.Fibm, 0, sizeof(float) * 3 * N, c->st));
@@ -433,6 +437,8 @@ scbb_status scbb_set_density(scbb_ctx* c, const double* rhoA, const double* rhoB
     }
     float* stage = c->d.S[1 - c->cur];
     CUDA_TRY(c, cudaMemcpyAsync(stage, h.data(), sizeof(float) * 5 * N, cudaMemcpyHostToDevice, c->st));
+    CUDA_TRY(c, cudaMemsetAsync(c->d.S[c->cur], 0,
+                                (c->lp.half ? sizeof(uint16_t) : sizeof(float)) * 2 * Q * N, c->st));
     launch_init_state(c->lp, c->d.S[c->cur], stage, stage + 2 * N, c->st);
     c->launches++;
     if (c->d.NV > 0) {
@@ -463,7 +469,7 @@ scbb_status scbb_set_density(scbb_ctx* c, const double* rhoA, const double* rhoB
 static void enqueue_step(scbb_ctx* c) {
     const bool ibm = c->fl.coupling == 1 && c->d.NV > 0;
     const bool bb = c->d.owner != nullptr;
-    const int mode = ibm ? 1 : (bb ? 2 : 0);
+    const int mode = ibm ? 1 : 0;
     const int step = (int)(c->steps & 0x7fffffff);     // the kernels use its parity only
     c->mark(0);
     if (ibm) {
@@ -481,7 +487,7 @@ static void enqueue_step(scbb_ctx* c) {
     const bool timed = c->timing && c->ev_used + 2 <= c->ev.size();
     if (timed) cudaEventRecord(c->ev[c->ev_used], c->st);
     launch_bulk(c->lp, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.rho, c->d.ghost, c->d.Fibm,
-                bb ? c->d.bmask : c->d.mask, c->d.u, c->d.err, mode, c->d.mpart, c->st);
+                c->d.mask, c->d.u, c->d.err, mode, c->st);
     if (timed) {
         cudaEventRecord(c->ev[c->ev_used + 1], c->st);
         c->ev_used += 2;
@@ -503,7 +509,7 @@ static void enqueue_step(scbb_ctx* c) {
         launch_bb_classify(c->lp, c->d, step, false, c->st);
         c->launches += 5;
         c->mark(6);
-        launch_bb_fresh(c->lp, c->d, c->d.S[1 - c->cur], step, bulk_grid_blocks(c->lp), c->st);
+        launch_bb_fresh(c->lp, c->d, c->d.S[1 - c->cur], step, c->st);
         c->launches += 3;
     } else {
         c->mark(4);
@@ -602,10 +608,22 @@ scbb_status scbb_sync(scbb_ctx* c) {
 static scbb_status export_state(scbb_ctx* c, int what, std::vector<float>& h) {
     const size_t N = c->lp.N;
     float* stage = c->d.S[1 - c->cur];
-    launch_export(c->lp, c->d.S[c->cur], stage, what, c->st);
-    c->launches++;
     const size_t cnt = what == 1 ? 2 * Q * N : 5 * N;
     h.resize(cnt);
+    if (what == 1 && c->lp.half) {
+        // an FP16 lattice holds 19 N floats: export the components one after the other
+        for (int comp = 0; comp < 2; comp++) {
+            launch_export(c->lp, c->d.S[c->cur], stage, 2 + comp, c->st);
+            c->launches++;
+            CUDA_TRY(c, cudaGetLastError());
+            CUDA_TRY(c, cudaMemcpyAsync(h.data() + (size_t)comp * Q * N, stage, sizeof(float) * Q * N,
+                                        cudaMemcpyDeviceToHost, c->st));
+            CUDA_TRY(c, cudaStreamSynchronize(c->st));
+        }
+        return SCBB_OK;
+    }
+    launch_export(c->lp, c->d.S[c->cur], stage, what, c->st);
+    c->launches++;
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaMemcpyAsync(h.data(), stage, sizeof(float) * cnt, cudaMemcpyDeviceToHost, c->st));
     CUDA_TRY(c, cudaStreamSynchronize(c->st));

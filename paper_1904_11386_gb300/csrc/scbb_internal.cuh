@@ -1,13 +1,16 @@
 // Internal declarations shared by the CUDA translation units of libscbb (sm_103a).
 //
-// Population storage: two FP32 lattices S[c][i][N] (structure of arrays, x fastest).  A lattice holds the
-// post-collision populations of the last step, not yet streamed; streaming is a pull, f_i(x) = S[i][x - c_i].
+// Population storage: two lattices S[c][i][N] (structure of arrays, x fastest) of FP32 or, with FP16 storage,
+// IEEE half values; all arithmetic is FP32 either way.  A lattice holds the post-collision populations of the
+// last step, not yet streamed; streaming is a pull, f_i(x) = S[i][x - c_i].
 // Links that end on a wall node (Eq. 11) store the bounced value in the slot the receiving node pulls from,
 // so every pull is the same plain gather and the density of any node can be recomputed from S.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "../../include/scbb.h"
 
@@ -45,7 +48,40 @@ struct LbmParams {
     int psi_kind;
     float g[3];
     float ulo[3], uhi[3];
+    int half;               // 1: populations stored as FP16 (the S pointers point to __half)
 };
+
+// Population element access for either storage (values convert to and from FP32 at the load and store;
+// FP16 stores round to nearest).  A four-node vector is 16 bytes in FP32 and 8 bytes in FP16.
+__device__ __forceinline__ float pld(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float pld(const __half* p) { return __half2float(__ldg(p)); }
+// the value a store of this storage type keeps (identity for FP32): collisions sum the stored values of the
+// moving populations, so the rest population absorbs their rounding and the node's mass is exact up to
+// one rounding
+__device__ __forceinline__ float pround(float v, const float*) { return v; }
+__device__ __forceinline__ float pround(float v, const __half*) { return __half2float(__float2half_rn(v)); }
+// coherent loads, for populations a kernel also writes (the pld loads go through the read-only path)
+__device__ __forceinline__ float pldc(const float* p) { return *p; }
+__device__ __forceinline__ float pldc(const __half* p) { return __half2float(*p); }
+__device__ __forceinline__ void pst(float* p, float v) { *p = v; }
+__device__ __forceinline__ void pst(__half* p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ float4 pld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float4 pld4(const __half* p) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    __half2 a, b;
+    memcpy(&a, &u.x, 4);
+    memcpy(&b, &u.y, 4);
+    const float2 fa = __half22float2(a), fb = __half22float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+__device__ __forceinline__ void pst4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ void pst4(__half* p, float4 v) {
+    const __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+    uint2 u;
+    memcpy(&u.x, &a, 4);
+    memcpy(&u.y, &b, 4);
+    *reinterpret_cast<uint2*>(p) = u;
+}
 
 // One capsule's constants on the device.
 struct CapDev {
@@ -56,7 +92,7 @@ struct CapDev {
 
 // Device-side buffers of a context (all carved from the caller's workspace).
 struct DevState {
-    float* S[2];            // populations, 2 * 19 * N floats each
+    float* S[2];            // populations, 2 * 19 * N values each (FP32, or FP16 when LbmParams::half)
     float* rho;             // [2][N] densities of the last collision
     float* u;               // [3][N] velocity incl. half force, written where the IBM mask is set
     float* Fibm;            // [3][N] spread immersed-boundary force density
@@ -97,19 +133,21 @@ struct DevState {
     int* fold;              // [maxF] their owner before the change
     float4* fnew;           // [maxF][2] new (rhoA, rhoB, ok, -) and (vx, vy, vz, element)
     int* cnt;               // [8] 0: boundary nodes, 1: fresh nodes, 2: overflow flags, 3: boundary nodes of
-                            //     the step's boundary kernel (saved before re-listing)
+                            //     the step's boundary kernel, 4: fresh nodes of the previous step (both saved
+                            //     before re-listing)
     float4* emom;           // [2][NT] exchanged momentum (Eq. 12) by step parity
     float4* epend;          // [2][NT] Shan-Chen reactions and fresh-node momenta by step parity
     int4* cbox;             // [NM][2] classification box (lo, hi), unwrapped lattice coordinates
     int* ccnt;              // [NM][CW*CW] crossings per column
     float* czs;             // [NM][CW*CW][MAXC] crossing heights
-    double* mpart;          // [bulk blocks][2] per-CTA mass sums of the bulk kernel
+    float2* fdm;            // [maxF] mass change (A, B) of each fresh node's replacement
     float4* trec;           // [NT][4] vertex positions and centroid of every triangle at X(t+1)
     int* tcnt;              // [NM][CW*CW] triangles whose xy bounding box overlaps each column cell
     int4* tlst;             // [NM][CW*CW][BB_MAXT] their ids and z ranges (t, zmin bits, zmax bits, 0)
     float4* vrho;           // [N] at boundary nodes: mean rho^A, rho^B over neighbours on the other side,
                             //     count, 1 if those neighbours lie on more than one other side
-    double* mass;           // [8] 0-1: M(0), 2-3: bounce-back mass change of the step, 4-5: correction factor
+    double* mass;           // [8] 0-1: M(0), 2-3: mass change since M(0) (FP64 running sums of the bounce-back and
+                            //     fresh-node changes), 4-5: correction factors
     int maxB, maxF, CW;
     // particle-particle repulsion (several capsules)
     int* pp_head;           // [pp_size] hashed cell heads, nullptr when unused
@@ -150,7 +188,8 @@ struct Cols {
     int ry[3];          // (y - 1) nx, y nx, (y + 1) nx (wrapped)
 };
 
-__device__ __forceinline__ void pull(const LbmParams& p, const float* __restrict__ S, const Cols& k, int z,
+template <typename T>
+__device__ __forceinline__ void pull(const LbmParams& p, const T* __restrict__ S, const Cols& k, int z,
                                      float (&f)[2 * Q]) {
     int zm = z - 1, zp = z + 1;
     if (!p.walls) {
@@ -162,19 +201,17 @@ __device__ __forceinline__ void pull(const LbmParams& p, const float* __restrict
     for (int i = 0; i < Q; i++) {
         // source node x - c_i
         unsigned int m = k.cx[1 - dir_x(i)] + k.ry[1 - dir_y(i)] + pz[1 - dir_z(i)];
-        f[i] = __ldg(S + (size_t)i * p.N + m);
-        f[Q + i] = __ldg(S + (size_t)(Q + i) * p.N + m);
+        f[i] = pld(S + (size_t)i * p.N + m);
+        f[Q + i] = pld(S + (size_t)(Q + i) * p.N + m);
     }
 }
 
 // ---- launches (lbm_kernels.cu) ----
 void launch_init_state(const LbmParams& p, float* S, const float* rho_st, const float* u_st, cudaStream_t st);
 void launch_wall_ghost(const LbmParams& p, const float* S, float* wall_rho, float* ghost, cudaStream_t st);
-// mode 0: fluid only, 1: immersed boundary (mask = IBM stencil bits), 2: bounce-back (mask = boundary-node
-// bits, mpart receives per-CTA FP64 density sums; needs the row-vectorised geometry)
+// mode 0: fluid only (also with bounce-back membranes), 1: immersed boundary (mask = IBM stencil bits)
 void launch_bulk(const LbmParams& p, const float* S, float* D, float* rho, const float* ghost,
-                 const float* Fibm, const uint32_t* mask, float* u, int* err, int mode, double* mpart,
-                 cudaStream_t st);
+                 const float* Fibm, const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st);
 bool bulk_vectorised(const LbmParams& p);
 void launch_export(const LbmParams& p, const float* S, float* out, int what, cudaStream_t st);
 void launch_moments_reduce(const LbmParams& p, const float* S, double* red, cudaStream_t st);
@@ -193,7 +230,7 @@ void launch_bb_init(const LbmParams& p, const DevState& d, cudaStream_t st);
 void launch_bb_classify(const LbmParams& p, const DevState& d, int step, bool init, cudaStream_t st);
 void launch_bb_boundary(const LbmParams& p, const DevState& d, const float* S, float* D, const float* ghost,
                         int step, int* err, cudaStream_t st);
-void launch_bb_fresh(const LbmParams& p, const DevState& d, float* Snew, int step, int nbulk_blocks,
+void launch_bb_fresh(const LbmParams& p, const DevState& d, float* Snew, int step,
                      cudaStream_t st);
 
 }  // namespace scbb

@@ -116,7 +116,7 @@ def fluid_of(prob) -> scbb_fluid:
     fl.rho_maj, fl.rho_min, fl.C0 = prob.rho_maj, prob.rho_min, prob.C0
     fl.mass_correction = int(prob.mass_correction)
     fl.pp_eps, fl.pp_d0 = prob.pp_eps, prob.pp_d0
-    fl.storage = 0
+    fl.storage = int(getattr(prob, "storage", 0))
     return fl
 
 

@@ -49,31 +49,44 @@ def test_ibm_small_box_20_steps():
     assert np.abs(Xg - Xo).max() < 1e-4
 
 
-def test_parity32_ibm_200_steps():
-    """The 32^3 parity workload (walls, psi = rho, interface at z = 16, s = 3 capsule of radius 6, 200 steps,
-    2-point immersed boundary): densities within 1e-5 relative, velocities within 1e-5 of max|u|, vertex
-    positions within 1e-4 lattice units."""
+def test_parity32_ibm_1000_steps():
+    """The 32^3 parity workload (walls, psi = rho, interface at z = 16, s = 3 capsule of radius 6, 2-point
+    immersed boundary).  After 200 steps: densities within 1e-5 relative, velocities within 1e-5 of max|u|,
+    vertex positions within 1e-4 lattice units, FP64 volume and centre of mass.  After 1000 steps: densities
+    within 1e-5 and vertices within 1e-4 still; velocities within 1e-4 of max|u| (measured 3.6e-5): with
+    psi = rho the velocity is dominated by the spurious currents at the interface (|u| ~ 0.07), a difference
+    of large Shan-Chen terms that magnifies the FP32 state's round-off."""
     p = inputs.cfg_parity(coupling=1)
     g = _sim(p)
     o = O.OracleSim(p)
-    g.scbb_step(p.steps)
-    o.step(p.steps)
-    ga, gb, gu = g.scbb_get_fields()
-    oa, ob, ou = o.fields()
-    fl = oa + ob > 0
-    ea = (np.abs(ga - oa)[fl] / oa[fl]).max()
-    eb = (np.abs(gb - ob)[fl] / ob[fl]).max()
-    eu = np.abs(gu - ou).max() / np.abs(ou).max()
-    Xg, _, _ = g.scbb_get_vertices()
-    Xo, _, _ = o.vertices()
-    ex = np.abs(Xg - Xo).max()
-    assert ea < 1e-5 and eb < 1e-5, (ea, eb)
+
+    def errors():
+        ga, gb, gu = g.scbb_get_fields()
+        oa, ob, ou = o.fields()
+        fl = oa + ob > 0
+        ea = (np.abs(ga - oa)[fl] / oa[fl]).max()
+        eb = (np.abs(gb - ob)[fl] / ob[fl]).max()
+        eu = np.abs(gu - ou).max() / np.abs(ou).max()
+        Xg, _, _ = g.scbb_get_vertices()
+        Xo, _, _ = o.vertices()
+        return max(ea, eb), eu, np.abs(Xg - Xo).max()
+
+    g.scbb_step(200)
+    o.step(200)
+    er, eu, ex = errors()
+    assert er < 1e-5, er
     assert eu < 1e-5, eu
     assert ex < 1e-4, ex
     d = g.scbb_get_diag()
     vo, co = o.capsule(0)
     assert abs(d["volume"][0] - vo) / vo < 1e-5
     assert np.abs(d["com"][0] - co).max() < 1e-4
+    g.scbb_step(800)
+    o.step(800)
+    er, eu, ex = errors()
+    assert er < 1e-5, er
+    assert eu < 1e-4, eu
+    assert ex < 1e-4, ex
 
 
 def test_pp_repulsion_two_capsules():
