@@ -40,6 +40,10 @@ def workload(name: str):
                                                   "immersed-boundary coupling (colour 0)")
     if name == "parity32":
         return inputs.cfg_parity(coupling=1), "parity32-ibm2: 32^3, psi=rho, s=3 capsule R=6"
+    if name == "batch48":
+        return inputs.cfg_batch48(), ("batch48: 48 independent cubes with edges 40-72 (multiples of 4), each a flat "
+                                      "interface with one s=3 capsule R=6 (642 vertices), colours over [-0.1, 0.1] "
+                                      "x shear moduli {0.001, 0.003, 0.01, 0.03}, half-way bounce-back")
     if name == "fluid256":
         p = inputs.cfg_droplet256(n_caps=0, coupling=1)
         p.capsules = []
@@ -201,6 +205,85 @@ def fp16_beside(prob, args, ws, local, n_upd, peak):
                                     "tests/test_gpu_fp16.py"}
 
 
+def run_batch(args, probs, label, ws, rank, local):
+    """The sweep of independent boxes: steps of all boxes together (one CUDA graph with a branch per box),
+    against the same boxes stepped one after another on one stream, kernel by kernel (looping single
+    launches).  value = lattice updates of all boxes per second of the batched run."""
+    import numpy as np
+    import torch
+
+    from paper_1904_11386_gb300 import scbb
+
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    nodes = sum(p.n_nodes for p in probs)
+    n_upd = sum(p.nx * p.ny * (p.nz - 2 * p.walls) for p in probs)
+    sims = [scbb.Sim(p, device=dev) for p in probs]
+    batch = scbb.Batch(sims)
+    bst = batch.stream
+    batch.scbb_batch_step(args.warmup)
+    torch.cuda.synchronize()
+    clocks = Clocks()
+    clocks.start()
+    time.sleep(0.3)
+    l0 = sum(s.scbb_launch_count() for s in sims)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(bst)
+    batch.scbb_batch_step(args.steps)
+    e1.record(bst)
+    torch.cuda.synchronize()
+    launches = sum(s.scbb_launch_count() for s in sims) - l0
+    ms = replica_max(e0.elapsed_time(e1), ws, dev)
+    clk = clocks.stop()
+    for s in sims:
+        s.scbb_sync()
+    batch.close()
+    # looping single launches: all boxes on one stream, one box after another, one step per call
+    one = torch.cuda.Stream(device=dev)
+    loop_sims = [scbb.Sim(p, device=dev, stream=one) for p in probs]
+    for s in loop_sims:
+        s.scbb_step(args.warmup)
+    torch.cuda.synchronize()
+    k_loop = min(args.steps, 20)
+    e0.record(one)
+    for _ in range(k_loop):
+        for s in loop_sims:
+            s.scbb_step(1)
+    e1.record(one)
+    torch.cuda.synchronize()
+    ms_loop = replica_max(e0.elapsed_time(e1), ws, dev)
+    for s in loop_sims:
+        s.scbb_sync()
+        s.close()
+    for s in sims:
+        s.close()
+    peak, src = peak_hbm()
+    # the boxes' bulk kernels overlap each other and the other kernels of the step, so per-launch events do not
+    # give a kernel duration here: the bulk kernels' algorithmic bytes per batched step over the whole step
+    # time bound their throughput from below
+    achieved = BYTES_PER_LU * n_upd / (ms / args.steps / 1e3) / 1e9
+    out = {"metric": "2-component D3Q19 lattice updates per second, full coupled step (GLUPS); batched sweep",
+           "value": aggregate_glups(nodes, args.steps, ws, ms / 1e3), "unit": "GLUPS", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": label, "boxes": len(probs), "nodes": nodes, "parallelism": f"replicas x{ws}",
+                      "l2": f"inputs larger than L2 (populations 2 x {2 * 19 * 4 * nodes / 1e6:.0f} MB)"},
+           "looped_single_launches": {"value": aggregate_glups(nodes, k_loop, ws, ms_loop / 1e3), "unit": "GLUPS",
+                                      "steps": k_loop,
+                                      "how": "all boxes on one stream, box after box, one step per call"},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": None,
+                        "kernel": "k_bulk4 of all boxes: algorithmic bytes per batched step / whole step time "
+                                  "(a lower bound; the step also runs the bookkeeping kernels)",
+                        "bytes_per_lu": BYTES_PER_LU, "units_per_step": n_upd, "peak_source": src},
+           "gpu_launches": launches, "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(probs[0], args.cpu_seconds)
+        out["cpu_baseline"]["sample"] += " (box 0 of the sweep)"
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def cpu_baseline(prob, seconds=15.0):
     """The FP64 oracle as it stands, on this host's cores, on a bounded number of steps of the same workload."""
     from oracle import oracle as O
@@ -231,6 +314,32 @@ def dist_setup():
             torch.cuda.set_device(local)
         dist.init_process_group(backend)
     return ws, rank, local
+
+
+def run_reference_batch(args, probs, label, rank):
+    """Reference arm of the sweep: the FP64 oracle steps every box in turn on the host cores."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+
+    sims = [O.OracleSim(p) for p in probs]
+    for s in sims:
+        s.step(args.warmup)
+    t0 = time.perf_counter()
+    for s in sims:
+        s.step(args.steps)
+    dt = time.perf_counter() - t0
+    nodes = sum(p.n_nodes for p in probs)
+    v = nodes * args.steps / dt / 1e9
+    print(json.dumps({"metric": "2-component D3Q19 lattice updates per second, full coupled step (GLUPS); batched sweep",
+                      "value": v, "unit": "GLUPS", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                      "config": {"workload": label, "boxes": len(probs), "nodes": nodes},
+                      "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": O.threads(), "kind": "oracle",
+                                       "sample": f"{args.steps} full time steps of every box"},
+                      "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
 
 
 def run_reference(args, prob, label, ws, rank):
@@ -274,6 +383,16 @@ def main():
 
     ws, rank, local = dist_setup()
     prob, label = workload(args.workload)
+    if args.workload == "batch48":
+        if args.impl == "reference":
+            run_reference_batch(args, prob, label, rank)
+        else:
+            run_batch(args, prob, label, ws, rank, local)
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return
     if args.storage == "fp16":
         prob.storage = 1
         label += "; populations stored as FP16"

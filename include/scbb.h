@@ -69,9 +69,11 @@ typedef struct {
  *   C0, mass_correction   adaptive fresh-node mass correction (Eq. 18), C0 = 2500 in the paper
  *   pp_eps, pp_d0         particle-particle repulsion (Eq. 26, Sec. III.E), 0.5 and 1.25 in the paper
  *   storage   0: FP32 populations; 1: populations stored as IEEE FP16 (arithmetic stays FP32; each stored
- *             value is rounded to nearest, about 2.4e-4 relative), half the population bytes.  FP16 needs
- *             the row-vectorised bulk geometry (nx a multiple of 4, nx/4 a power of two up to 32 or a
- *             multiple of 32), else scbb_create returns SCBB_E_UNSUPPORTED.  Not in the paper. */
+ *             value is rounded to nearest, about 2.4e-4 relative), half the population bytes.  Not in the
+ *             paper.
+ * FP16 storage and the bounce-back coupling with meshes run on the row-vectorised bulk kernel, which needs nx
+ * a multiple of 4 (and, for tau != 1, nx/4 a power of two up to 32 or a multiple of 32); otherwise
+ * scbb_create returns SCBB_E_UNSUPPORTED. */
 typedef struct {
     double tau, G;
     int psi_kind;
@@ -188,6 +190,21 @@ scbb_status scbb_phase_times(scbb_ctx* ctx, double* ms, long long* steps);
 #define SCBB_NOALLOC_MAX_NODES 50000000
 scbb_status scbb_population_moments_noalloc(const float* dev_f, int nx, int ny, int nz, int walls, double* out5,
                                             void* cuda_stream);
+
+/* Batches (not in the paper): step several independent contexts together, for example a sweep of boxes of
+ * different sizes and parameters.  ctxs: n distinct contexts, kept alive by the caller until
+ * scbb_batch_destroy; each must run on a stream of its own (not the legacy default).  cuda_stream: the
+ * batch's own stream (not the legacy default, not a context's stream).  scbb_batch_step(b, n) advances
+ * every context by n steps, asynchronously: the batch stream first waits for the work already queued on
+ * every context stream, and afterwards every context stream waits for the batch, so single-context calls
+ * before and after stay ordered.  After each context has run one step, pairs of steps of all contexts are
+ * replayed from one CUDA graph with a branch per context, so small boxes run side by side on the GPU; the
+ * results equal those of stepping each context alone.  Errors: SCBB_E_INVAL for bad arguments,
+ * SCBB_E_STATE if a context has failed, SCBB_E_CUDA. */
+typedef struct scbb_batch scbb_batch;
+scbb_status scbb_batch_create(scbb_ctx* const* ctxs, int n, void* cuda_stream, scbb_batch** out);
+scbb_status scbb_batch_step(scbb_batch* batch, long long n);
+void scbb_batch_destroy(scbb_batch* batch);
 
 const char* scbb_last_error(const scbb_ctx* ctx);
 

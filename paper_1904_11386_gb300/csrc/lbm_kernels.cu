@@ -444,8 +444,8 @@ k_bulk2(LbmParams p, const float* __restrict__ S, float* __restrict__ D, float* 
 }
 
 // ------------------------------------------------------------------------------------------------------
-// Bulk kernel, row-vectorised variant (the fast path when nx is a multiple of 4 and nx/4 is a power of two
-// up to 32 or a multiple of 32).
+// Bulk kernel, row-vectorised variant (the fast path when nx is a multiple of 4; with tau != 1 nx/4 must also
+// be a power of two up to 32 or a multiple of 32).
 //
 // A CTA owns whole x-rows: TY rows of the tile plus the rows y0-1 and y0+TY, marching through a z-segment.
 // Each thread owns four consecutive nodes of a row and moves them with 16-byte loads and stores.  The pull
@@ -465,18 +465,20 @@ struct Quad {
 };
 
 // populations of direction i (component base cb = S + c*Q*N) arriving at the four nodes x..x+3 of a row
+// edge bit 0: the element at x - 1 is not in the lane below (row start or warp edge) and is loaded directly;
+// bit 1: likewise for x + 4 and the lane above.
 template <int I, typename T>
 __device__ __forceinline__ float4 pull4(const LbmParams& p, const T* __restrict__ cb, unsigned int srow, int x,
-                                        int segl, int W, bool multi, int q_in_warp, unsigned int lanes) {
+                                        int segl, int W, int edge, unsigned int lanes) {
     const T* base = cb + (size_t)I * p.N + srow;
     float4 v = pld4(base + x);
     if (dir_x(I) == 1) {            // source x - 1: {x-1, x, x+1, x+2}
         float pw = __shfl_sync(lanes, v.w, (segl + W - 1) & (W - 1), W);
-        if (multi && q_in_warp == 0) pw = pld(base + (x == 0 ? p.nx - 1 : x - 1));
+        if (edge & 1) pw = pld(base + (x == 0 ? p.nx - 1 : x - 1));
         v = make_float4(pw, v.x, v.y, v.z);
     } else if (dir_x(I) == -1) {    // source x + 1: {x+1, x+2, x+3, x+4}
         float nx0 = __shfl_sync(lanes, v.x, (segl + 1) & (W - 1), W);
-        if (multi && q_in_warp == 31) nx0 = pld(base + (x + 4 == p.nx ? 0 : x + 4));
+        if (edge & 2) nx0 = pld(base + (x + 4 == p.nx ? 0 : x + 4));
         v = make_float4(v.y, v.z, v.w, nx0);
     }
     return v;
@@ -506,10 +508,10 @@ struct PullCtx {
 
 template <int I, typename T>
 __device__ __forceinline__ void pull_dir(const LbmParams& p, const T* __restrict__ S, const PullCtx& pc, int x,
-                                         int segl, int W, bool multi, int qw, Mom4& m) {
+                                         int segl, int W, int edge, Mom4& m) {
     const unsigned int srow = pc.rows[1 - dir_y(I)][1 - dir_z(I)];
-    const float4 a = pull4<I, T>(p, S, srow, x, segl, W, multi, qw, 0xffffffffu);
-    const float4 b = pull4<I, T>(p, S + (size_t)Q * p.N, srow, x, segl, W, multi, qw, 0xffffffffu);
+    const float4 a = pull4<I, T>(p, S, srow, x, segl, W, edge, 0xffffffffu);
+    const float4 b = pull4<I, T>(p, S + (size_t)Q * p.N, srow, x, segl, W, edge, 0xffffffffu);
     acc_dir<I>(m, a, b);
 }
 
@@ -518,9 +520,9 @@ struct DirList {};
 
 template <typename T, int I, int... Rest>
 __device__ __forceinline__ void pull_all(const LbmParams& p, const T* __restrict__ S, const PullCtx& pc, int x,
-                                         int segl, int W, bool multi, int qw, Mom4& m, DirList<I, Rest...>) {
-    pull_dir<I, T>(p, S, pc, x, segl, W, multi, qw, m);
-    if constexpr (sizeof...(Rest) > 0) pull_all(p, S, pc, x, segl, W, multi, qw, m, DirList<Rest...>{});
+                                         int segl, int W, int edge, Mom4& m, DirList<I, Rest...>) {
+    pull_dir<I, T>(p, S, pc, x, segl, W, edge, m);
+    if constexpr (sizeof...(Rest) > 0) pull_all(p, S, pc, x, segl, W, edge, m, DirList<Rest...>{});
 }
 
 using AllDirs = DirList<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18>;
@@ -542,8 +544,8 @@ __device__ __forceinline__ PullCtx pull_ctx(const LbmParams& p, const int ry[3],
 
 template <int I, typename T>
 __device__ __forceinline__ float4 pull_comp(const LbmParams& p, const T* __restrict__ cb, const PullCtx& pc, int x,
-                                            int segl, int W, bool multi, int qw, unsigned int lanes) {
-    return pull4<I, T>(p, cb, pc.rows[1 - dir_y(I)][1 - dir_z(I)], x, segl, W, multi, qw, lanes);
+                                            int segl, int W, int edge, unsigned int lanes) {
+    return pull4<I, T>(p, cb, pc.rows[1 - dir_y(I)][1 - dir_z(I)], x, segl, W, edge, lanes);
 }
 
 // six psi values x-1 .. x+4 of one ring row (periodic in x)
@@ -571,16 +573,24 @@ k_bulk4(LbmParams p, const T* __restrict__ S, T* __restrict__ D, float* __restri
     const int NQ = nx >> 2;
     const int RR = TY + 2;
     const int t = threadIdx.x;
-    const int r = t / NQ;                                // ring row: 0 <-> y0 - 1
-    const int q = t - r * NQ;
+    // threads past the rows (the last warp of rows whose width does not divide 32 lanes) shadow the last
+    // real thread: their loads and shuffles are valid, and they write nothing
+    const int nreal = NQ * RR;
+    const bool phantom = t >= nreal;
+    const int tr = phantom ? nreal - 1 : t;
+    const int r = tr / NQ;                               // ring row: 0 <-> y0 - 1
+    const int q = tr - r * NQ;
     const int x = 4 * q;
-    const int W = NQ < 32 ? NQ : 32;
-    const bool multi = NQ > 32;
-    const int segl = q & (W - 1);                        // lane within the row segment
-    const int qw = q & 31;
+    // x-shift of the pull: rows of a power-of-two number of quads up to 32 shuffle within their own lane
+    // segment (its wrap is the periodic boundary); any other row shuffles across the warp, and a lane whose
+    // neighbour quad is in another warp or across the periodic wrap loads that element directly
+    const bool seg_rows = NQ <= 32 && (NQ & (NQ - 1)) == 0;
+    const int W = seg_rows ? NQ : 32;
+    const int segl = seg_rows ? (q & (W - 1)) : (t & 31);
+    const int edge = seg_rows ? 0 : (((q == 0 || (t & 31) == 0) ? 1 : 0) | ((q == NQ - 1 || (t & 31) == 31) ? 2 : 0));
     const int y0 = blockIdx.x * TY;
     const int gy = wrapi(y0 - 1 + r, p.ny);
-    const bool active = r >= 1 && r <= TY && (y0 + r - 1) < p.ny;
+    const bool active = !phantom && r >= 1 && r <= TY && (y0 + r - 1) < p.ny;
     const int ry[3] = {wrapi(gy - 1, p.ny) * nx, gy * nx, wrapi(gy + 1, p.ny) * nx};
     const int plane_sz = RR * nx;
 
@@ -605,6 +615,7 @@ k_bulk4(LbmParams p, const T* __restrict__ S, T* __restrict__ D, float* __restri
         float* rA = ring + (size_t)(slot * 2 + 0) * plane_sz + r * nx + x;
         float* rB = ring + (size_t)(slot * 2 + 1) * plane_sz + r * nx + x;
         if (is_wall_plane(p, z)) {
+            if (phantom) return;
             const int w = z == 0 ? 0 : 1;
             const float4 ga = *reinterpret_cast<const float4*>(ghost + (w * 2 + 0) * p.nxy + gy * nx + x);
             const float4 gb = *reinterpret_cast<const float4*>(ghost + (w * 2 + 1) * p.nxy + gy * nx + x);
@@ -618,7 +629,8 @@ k_bulk4(LbmParams p, const T* __restrict__ S, T* __restrict__ D, float* __restri
 #pragma unroll
         for (int k = 0; k < 4; k++) m.ra[k] = m.rb[k] = m.jx[k] = m.jy[k] = m.jz[k] = 0.f;
         const PullCtx pc = pull_ctx(p, ry, z);
-        pull_all(p, S, pc, x, segl, W, multi, qw, m, AllDirs{});
+        pull_all(p, S, pc, x, segl, W, edge, m, AllDirs{});
+        if (phantom) return;                             // its pulls only fed the shuffles
         *reinterpret_cast<float4*>(rA) = make_float4(psi_fn(m.ra[0], p.psi_kind), psi_fn(m.ra[1], p.psi_kind),
                                                      psi_fn(m.ra[2], p.psi_kind), psi_fn(m.ra[3], p.psi_kind));
         *reinterpret_cast<float4*>(rB) = make_float4(psi_fn(m.rb[0], p.psi_kind), psi_fn(m.rb[1], p.psi_kind),
@@ -779,8 +791,8 @@ k_bulk4(LbmParams p, const T* __restrict__ S, T* __restrict__ D, float* __restri
                     oB[k] = eB;
                 }
                 if (!TAU1) {
-                    const float4 fa = pull_comp<I, T>(p, S, pc, x, segl, W, multi, qw, lanes);
-                    const float4 fb = pull_comp<I, T>(p, S + (size_t)Q * p.N, pc, x, segl, W, multi, qw, lanes);
+                    const float4 fa = pull_comp<I, T>(p, S, pc, x, segl, W, edge, lanes);
+                    const float4 fb = pull_comp<I, T>(p, S + (size_t)Q * p.N, pc, x, segl, W, edge, lanes);
                     const float FA4[4] = {fa.x, fa.y, fa.z, fa.w}, FB4[4] = {fb.x, fb.y, fb.z, fb.w};
 #pragma unroll
                     for (int k = 0; k < 4; k++) {
@@ -827,11 +839,18 @@ static int bulk4_rows(const LbmParams& p, int nthreads) {
     if (p.nx % 4) return 0;
     const int NQ = p.nx / 4;
     const bool pow2 = (NQ & (NQ - 1)) == 0;
-    if (!((NQ <= 32 && pow2) || NQ % 32 == 0)) return 0;
+    const bool aligned = (NQ <= 32 && pow2) || NQ % 32 == 0;
+    // rows of any other width shuffle across whole warps, which the collision's re-pull of tau != 1 (with
+    // only the colliding rows' lanes) cannot do
+    if (!aligned && p.omega != 1.0f) return 0;
     if (NQ > nthreads / 3) return 0;                   // need at least one tile row plus two halo rows
     int RR = nthreads / NQ;
-    while (RR > 3 && (RR * NQ) % 32) RR--;
-    if ((RR * NQ) % 32) return 0;
+    if (aligned) {
+        while (RR > 3 && (RR * NQ) % 32) RR--;
+        if ((RR * NQ) % 32) return 0;
+    } else {
+        while (RR > 3 && (RR * NQ + 31) / 32 * 32 > nthreads) RR--;    // the last warp may carry phantoms
+    }
     int TY = RR - 2;
     if (TY > p.ny) TY = p.ny;
     return TY;
@@ -861,8 +880,13 @@ static bool bulk4_geometry(const LbmParams& p, int nthreads, int cps, LbmParams&
     TY = bulk4_rows(p, nthreads);
     if (TY <= 0) return false;
     const int NQ = p.nx / 4;
-    while ((NQ * (TY + 2)) % 32) TY++;
-    threads = NQ * (TY + 2);
+    const bool aligned = (NQ <= 32 && (NQ & (NQ - 1)) == 0) || NQ % 32 == 0;
+    if (aligned) {
+        while ((NQ * (TY + 2)) % 32) TY++;
+        threads = NQ * (TY + 2);
+    } else {
+        threads = (NQ * (TY + 2) + 31) / 32 * 32;     // rows, then phantom threads up to a whole warp
+    }
     if (threads > nthreads) return false;
     const int cols = (p.ny + TY - 1) / TY;
     const int nzf = p.zf1 - p.zf0;

@@ -310,8 +310,8 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
     if (!valid_lattice(lat) || !valid_fluid(fl) || !dev_workspace) return SCBB_E_INVAL;
     if (!valid_meshes(n_mesh, meshes, why)) return SCBB_E_MESH;
     if ((fl->coupling == 0 && n_mesh > 0) || fl->storage == 1) {
-        // bounce-back membranes and FP16 storage run with the row-vectorised bulk kernel (nx a multiple of 4,
-        // nx/4 a power of two up to 32 or a multiple of 32)
+        // bounce-back membranes and FP16 storage run with the row-vectorised bulk kernel (nx a multiple of 4;
+        // for tau != 1 also nx/4 a power of two up to 32 or a multiple of 32)
         LbmParams lp = make_params(lat, fl);
         if (!bulk_vectorised(lp)) return SCBB_E_UNSUPPORTED;
     }
@@ -596,6 +596,84 @@ scbb_status scbb_step(scbb_ctx* c, long long n) {
     return SCBB_OK;
 }
 
+// ------------------------------------------------------------------------------------------------------
+// Batches of independent contexts (for example a sweep of boxes with different sizes and parameters).
+// ------------------------------------------------------------------------------------------------------
+struct scbb_batch {
+    std::vector<scbb_ctx*> ctx;
+    cudaStream_t st = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<int> keys;                // (cur << 1) | step parity of every context at the capture
+    std::vector<long long> pair_launches;
+    std::vector<cudaEvent_t> ev;          // [0]: fork, [1 + k]: join of context k
+    int graph_off = 0;
+};
+
+static int ctx_key(const scbb_ctx* c) { return (c->cur << 1) | (int)(c->steps & 1); }
+
+// every context stream waits for the batch stream (fork), or the batch stream for every context (join)
+static cudaError_t batch_fork(scbb_batch* b) {
+    cudaError_t e = cudaEventRecord(b->ev[0], b->st);
+    for (size_t k = 0; k < b->ctx.size() && e == cudaSuccess; k++) e = cudaStreamWaitEvent(b->ctx[k]->st, b->ev[0], 0);
+    return e;
+}
+static cudaError_t batch_join(scbb_batch* b) {
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < b->ctx.size() && e == cudaSuccess; k++) {
+        e = cudaEventRecord(b->ev[1 + k], b->ctx[k]->st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->ev[1 + k], 0);
+    }
+    return e;
+}
+
+// One graph with a branch per context, each branch two steps of that context on its own stream.
+static void batch_capture(scbb_batch* b) {
+    const size_t n = b->ctx.size();
+    std::vector<int> cur0(n);
+    std::vector<long long> steps0(n), launches0(n);
+    for (size_t k = 0; k < n; k++) {
+        cur0[k] = b->ctx[k]->cur;
+        steps0[k] = b->ctx[k]->steps;
+        launches0[k] = b->ctx[k]->launches;
+    }
+    if (cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        b->graph_off = 1;
+        return;
+    }
+    cudaError_t e = batch_fork(b);
+    for (size_t k = 0; k < n && e == cudaSuccess; k++) {
+        enqueue_step(b->ctx[k]);
+        enqueue_step(b->ctx[k]);
+    }
+    if (e == cudaSuccess) e = batch_join(b);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
+    b->keys.assign(n, 0);
+    b->pair_launches.assign(n, 0);
+    for (size_t k = 0; k < n; k++) {
+        b->pair_launches[k] = b->ctx[k]->launches - launches0[k];
+        b->ctx[k]->cur = cur0[k];
+        b->ctx[k]->steps = steps0[k];
+        b->ctx[k]->launches = launches0[k];
+        b->keys[k] = ctx_key(b->ctx[k]);
+    }
+    if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        b->graph_off = 1;
+        return;
+    }
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    if (cudaGraphInstantiate(&b->gexec, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        b->gexec = nullptr;
+        b->graph_off = 1;
+    }
+    cudaGraphDestroy(g);
+}
+
 scbb_status scbb_sync(scbb_ctx* c) {
     if (!c) return SCBB_E_INVAL;
     if (c->broken) return SCBB_E_STATE;
@@ -759,6 +837,90 @@ scbb_status scbb_kernel_time(scbb_ctx* c, double* ms, long long* launches) {
     if (launches) *launches = (long long)(c->ev_used / 2);
     c->ev_used = 0;
     return SCBB_OK;
+}
+
+scbb_status scbb_batch_create(scbb_ctx* const* ctxs, int n, void* cuda_stream, scbb_batch** out) {
+    if (!out) return SCBB_E_INVAL;
+    *out = nullptr;
+    if (!ctxs || n < 1) return SCBB_E_INVAL;
+    scbb_batch* b = new scbb_batch();
+    b->st = (cudaStream_t)cuda_stream;
+    for (int k = 0; k < n; k++) {
+        if (!ctxs[k]) {
+            delete b;
+            return SCBB_E_INVAL;
+        }
+        for (int j = 0; j < k; j++)
+            if (ctxs[j] == ctxs[k]) {
+                delete b;
+                return SCBB_E_INVAL;
+            }
+        b->ctx.push_back(ctxs[k]);
+    }
+    b->ev.resize(1 + (size_t)n, nullptr);
+    for (auto& e : b->ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            for (auto& f : b->ev)
+                if (f) cudaEventDestroy(f);
+            delete b;
+            return SCBB_E_CUDA;
+        }
+    *out = b;
+    return SCBB_OK;
+}
+
+scbb_status scbb_batch_step(scbb_batch* b, long long n) {
+    if (!b || n < 0) return SCBB_E_INVAL;
+    for (auto* c : b->ctx)
+        if (c->broken) return SCBB_E_STATE;
+    const size_t nc = b->ctx.size();
+    if (batch_join(b) != cudaSuccess) return SCBB_E_CUDA;      // earlier work of every context first
+    long long left = n;
+    while (left > 0) {
+        bool warm = graphs_enabled() && !b->graph_off;
+        for (auto* c : b->ctx) warm = warm && c->eager_steps > 0 && c->timing == 0;
+        if (left >= 2 && warm) {
+            bool same = b->gexec != nullptr, shifted = b->gexec != nullptr;
+            for (size_t k = 0; k < nc && b->gexec; k++) {
+                const int d = ctx_key(b->ctx[k]) ^ b->keys[k];
+                same = same && d == 0;
+                shifted = shifted && d == 3;
+            }
+            if (!same && !shifted) batch_capture(b);
+            same = b->gexec != nullptr;
+            for (size_t k = 0; k < nc && same; k++) same = ctx_key(b->ctx[k]) == b->keys[k];
+            if (same) {
+                for (; left >= 2; left -= 2) {
+                    if (cudaGraphLaunch(b->gexec, b->st) != cudaSuccess) return SCBB_E_CUDA;
+                    for (size_t k = 0; k < nc; k++) {
+                        b->ctx[k]->steps += 2;
+                        b->ctx[k]->launches += b->pair_launches[k];
+                    }
+                }
+                continue;
+            }
+        }
+        // one step of every context, launched kernel by kernel on the contexts' own streams
+        if (batch_fork(b) != cudaSuccess) return SCBB_E_CUDA;
+        for (auto* c : b->ctx) {
+            enqueue_step(c);
+            c->eager_steps++;
+        }
+        if (batch_join(b) != cudaSuccess) return SCBB_E_CUDA;
+        left--;
+    }
+    if (batch_fork(b) != cudaSuccess) return SCBB_E_CUDA;      // later calls on a context wait for the batch
+    if (cudaGetLastError() != cudaSuccess) return SCBB_E_CUDA;
+    return SCBB_OK;
+}
+
+void scbb_batch_destroy(scbb_batch* b) {
+    if (!b) return;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (auto& e : b->ev)
+        if (e) cudaEventDestroy(e);
+    delete b;
 }
 
 const char* scbb_last_error(const scbb_ctx* c) {

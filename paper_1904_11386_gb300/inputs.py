@@ -219,6 +219,26 @@ def cfg_droplet256(n_caps: int = 300, coupling: int = 0, n: int = 256, R_drop: f
                    steps=20000)
 
 
+def cfg_batch48(n_boxes: int = 48, seed: int = 3) -> List[Problem]:
+    """A sweep of independent boxes of uneven size: cubes with edges drawn from PCG64(seed) among the multiples
+    of 4 in [40, 72], walls at both z ends, a flat interface at mid height, one s = 3 capsule of radius 6 (642
+    vertices) penetrating it by 1; box k takes colour index k mod 11 over [-0.1, 0.1] and shear modulus index
+    (k div 11) mod 4 over {0.001, 0.003, 0.01, 0.03}, kB = 0.01 kS R^2, kV = 2 (coarse mesh), exponential psi."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    colours = np.linspace(-0.1, 0.1, 11)
+    moduli = (0.001, 0.003, 0.01, 0.03)
+    R = 6.0
+    out = []
+    for k in range(n_boxes):
+        L = 4 * int(rng.integers(10, 19))
+        kS = moduli[(k // 11) % 4]
+        cap = Capsule(centre=(L / 2 + 0.3, L / 2 - 0.2, L / 2 - R + 1.0), radius=R, subdiv=3, kS=kS,
+                      kB=0.01 * kS * R * R, kV=2.0, colour=float(colours[k % 11]))
+        out.append(Problem(name=f"batch{k}", nx=L, ny=L, nz=L, walls=1, psi_kind=0, coupling=0,
+                           z_interface=L // 2, capsules=[cap], noise=1e-4, seed=100 + k, steps=5000))
+    return out
+
+
 def small_problem(n=16, walls=1, coupling=1, capsule=True, psi_kind=0, seed=7, subdiv=2, radius=4.0,
                   noise=1e-3, nx=None, ny=None, nz=None) -> Problem:
     """A small seeded case for quick parity checks (several tiles plus a ragged tail when sizes are odd)."""

@@ -20,7 +20,7 @@ STATUS = {0: "SCBB_OK", 1: "SCBB_E_INVAL", 2: "SCBB_E_CUDA", 3: "SCBB_E_NOMEM", 
 EXPORTS = ["scbb_workspace_bytes", "scbb_create", "scbb_set_density", "scbb_step", "scbb_sync",
            "scbb_get_fields", "scbb_get_populations", "scbb_get_vertices", "scbb_get_diag", "scbb_get_owner",
            "scbb_launch_count", "scbb_enable_timing", "scbb_kernel_time", "scbb_phase_times",
-           "scbb_population_moments_noalloc",
+           "scbb_population_moments_noalloc", "scbb_batch_create", "scbb_batch_step", "scbb_batch_destroy",
            "scbb_last_error", "scbb_destroy"]
 
 
@@ -92,6 +92,12 @@ def load(path: str = LIB_PATH):
     L.scbb_last_error.argtypes = [vp]
     L.scbb_destroy.restype = None
     L.scbb_destroy.argtypes = [vp]
+    L.scbb_batch_create.restype = C.c_int
+    L.scbb_batch_create.argtypes = [C.POINTER(vp), C.c_int, vp, C.POINTER(vp)]
+    L.scbb_batch_step.restype = C.c_int
+    L.scbb_batch_step.argtypes = [vp, C.c_longlong]
+    L.scbb_batch_destroy.restype = None
+    L.scbb_batch_destroy.argtypes = [vp]
     _lib = L
     return L
 
@@ -269,3 +275,45 @@ class Sim:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Several independent Sim contexts stepped together (scbb_batch_*): each context keeps its own stream, the
+    batch runs on a stream of its own, and pairs of steps of all contexts replay from one CUDA graph."""
+
+    def __init__(self, sims, stream=None):
+        import torch
+
+        self.sims = list(sims)
+        self.L = self.sims[0].L
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.sims[0].workspace.device)
+        arr = (C.c_void_p * len(self.sims))(*[s.h.value for s in self.sims])
+        h = C.c_void_p()
+        st = self.L.scbb_batch_create(arr, len(self.sims), C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != SCBB_OK:
+            raise ScbbError(f"scbb_batch_create: {STATUS.get(st, st)}")
+        self.h = h
+
+    @classmethod
+    def scbb_batch_create(cls, sims, stream=None):
+        return cls(sims, stream)
+
+    def scbb_batch_destroy(self):
+        self.close()
+
+    def scbb_batch_step(self, n=1):
+        st = self.L.scbb_batch_step(self.h, int(n))
+        if st != SCBB_OK:
+            raise ScbbError(f"scbb_batch_step: {STATUS.get(st, st)}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.scbb_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

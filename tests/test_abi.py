@@ -40,7 +40,7 @@ def test_binding_names_match_header():
     for n in _declared():
         if n in ("scbb_create", "scbb_workspace_bytes", "scbb_destroy", "scbb_last_error"):
             continue
-        assert hasattr(scbb.Sim, n) or hasattr(scbb, n), n
+        assert hasattr(scbb.Sim, n) or hasattr(scbb.Batch, n) or hasattr(scbb, n), n
 
 
 def test_workspace_sizing_and_argument_checks():

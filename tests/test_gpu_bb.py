@@ -116,3 +116,22 @@ def test_bb_three_capsules_periodic():
     Xg, _, _ = g.scbb_get_vertices()
     Xo, _, _ = o.vertices()
     assert np.abs(Xg - Xo).max() < 1e-4
+
+
+def test_bb_uneven_box_rows_across_warps():
+    """A box whose rows are not a power-of-two number of four-node quads (nx = 44: 11 quads, rows straddle
+    warps, the x-shift falls back to direct loads at warp edges and at the periodic wrap): 20 coupled steps,
+    owners identical, densities within 1e-5, vertices within 1e-4."""
+    cap = inputs.Capsule(centre=(21.3, 17.8, 19.6), radius=6.0, subdiv=3, kS=0.02, kB=1e-3, kV=2.0, colour=-0.2)
+    p = inputs.Problem(name="uneven", nx=44, ny=36, nz=40, walls=1, coupling=0, psi_kind=0, z_interface=20,
+                       capsules=[cap], noise=1e-4, seed=17, u_lo=(-0.001, 0, 0), u_hi=(0.001, 0, 0))
+    g = _sim(p)
+    o = O.OracleSim(p)
+    g.scbb_step(20)
+    o.step(20)
+    og, _, _ = g.scbb_get_owner()
+    assert np.array_equal(og, o.owner())
+    assert _cmp_rho(g.scbb_get_fields(), o.fields()) < 1e-5
+    Xg, _, _ = g.scbb_get_vertices()
+    Xo, _, _ = o.vertices()
+    assert np.abs(Xg - Xo).max() < 1e-4
