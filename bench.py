@@ -44,6 +44,10 @@ def workload(name: str):
         return inputs.cfg_batch48(), ("batch48: 48 independent cubes with edges 40-72 (multiples of 4), each a flat "
                                       "interface with one s=3 capsule R=6 (642 vertices), colours over [-0.1, 0.1] "
                                       "x shear moduli {0.001, 0.003, 0.01, 0.03}, half-way bounce-back")
+    if name == "droplet256":
+        p = inputs.cfg_droplet256(n_caps=300, coupling=0)
+        return p, (f"droplet256: 256^3 periodic two-component box, B droplet R=70 covered by {len(p.capsules)} s=3 "
+                   "capsules R=8 (642 vertices each) with colours +-0.05, half-way bounce-back, repulsion")
     if name == "fluid256":
         p = inputs.cfg_droplet256(n_caps=0, coupling=1)
         p.capsules = []
