@@ -42,6 +42,30 @@ __device__ __forceinline__ long long node_of(const LbmParams& p, int x, int y, i
     return (long long)x + (long long)p.nx * (y + (long long)p.ny * z);
 }
 
+// Grid-stride launches over the boundary and fresh lists: the lists' lengths live on the device, so the
+// grid fills every SM at the kernel's occupancy (at most the blocks the list capacity needs) and each warp
+// or thread strides over the entries.
+static int sm_count() {
+    static const int n = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
+            v = 152;
+        return v;
+    }();
+    return n;
+}
+static int occupancy(const void* kernel, int threads) {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, 0) != cudaSuccess || v < 1) v = 1;
+    return v;
+}
+static unsigned fill_grid(int per_sm, size_t need) {
+    size_t g = (size_t)per_sm * sm_count();
+    if (need < g) g = need;
+    return (unsigned)(g > 0 ? g : 1);
+}
+
 // coordinate of lattice index q in the periodic image nearest to r (period L; per = periodic)
 __device__ __forceinline__ float near_image(int q, float r, int L, bool per) {
     float v = (float)q;
@@ -272,10 +296,7 @@ __global__ void k_class_col(LbmParams p, DevState d, int init) {
 // Clears the boundary and fresh bits of the previous step's lists and the per-column counters.
 __global__ void k_lists_reset(DevState d) {
     const int nb = d.cnt[0], nf = d.cnt[1];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        d.cnt[3] = nb;          // list the boundary kernel of this step used
-        d.cnt[4] = nf;          // fresh nodes replaced at the end of the previous step
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt[4] = nf;     // fresh nodes replaced at the end of the previous step
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < d.NM * d.CW * d.CW; q += gridDim.x * blockDim.x) {
         d.ccnt[q] = 0;
         d.tcnt[q] = 0;
@@ -328,16 +349,9 @@ __global__ void k_boundary_mark(LbmParams p, DevState d) {
 // "nearest crossing, lower triangle id on ties".
 constexpr int BE_WARPS = 8;
 
-__global__ void __launch_bounds__(BE_WARPS * 32, 4) k_boundary_elements(LbmParams p, DevState d) {
-    __shared__ unsigned long long best[BE_WARPS][Q - 1];
-    __shared__ float4 segP[BE_WARPS][Q - 1];          // canonical start point of each link's segment
-    __shared__ float4 segD[BE_WARPS][Q - 1];          // and its direction
-    __shared__ int queue[BE_WARPS][CAND_Q];
-    const int wl = threadIdx.x >> 5;
-    const int warp = blockIdx.x * BE_WARPS + wl;
-    const int lane = threadIdx.x & 31;
-    const int nb = min(d.cnt[0], d.maxB);
-    if (warp >= nb) return;
+__device__ __forceinline__ void node_elements(const LbmParams& p, const DevState& d, const int warp, const int wl,
+                                              const int lane, unsigned long long (*best)[Q - 1],
+                                              float4 (*segP)[Q - 1], float4 (*segD)[Q - 1], int (*queue)[CAND_Q]) {
     const int n = d.blist[warp];
     const int z = n / p.nxy, r = n - z * p.nxy, y = r / p.nx, x = r - y * p.nx;
     const uint16_t me = d.owner[n];
@@ -470,6 +484,19 @@ __global__ void __launch_bounds__(BE_WARPS * 32, 4) k_boundary_elements(LbmParam
     if (lane < Q - 1) d.belem[(size_t)warp * (Q - 1) + lane] = ((cutmask >> lane) & 1u) ? best_e : -1;
 }
 
+__global__ void __launch_bounds__(BE_WARPS * 32, 4) k_boundary_elements(LbmParams p, DevState d) {
+    __shared__ unsigned long long best[BE_WARPS][Q - 1];
+    __shared__ float4 segP[BE_WARPS][Q - 1];          // canonical start point of each link's segment
+    __shared__ float4 segD[BE_WARPS][Q - 1];          // and its direction
+    __shared__ int queue[BE_WARPS][CAND_Q];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nb = min(d.cnt[0], d.maxB);
+    for (int w = blockIdx.x * BE_WARPS + wl; w < nb; w += gridDim.x * BE_WARPS) {
+        node_elements(p, d, w, wl, lane, best, segP, segD, queue);
+        __syncwarp();
+    }
+}
+
 void launch_bb_classify(const LbmParams& p, const DevState& d, int step, bool init, cudaStream_t st) {
     if (d.NM == 0) return;
     k_lists_reset<<<64, 256, 0, st>>>(d);
@@ -480,7 +507,9 @@ void launch_bb_classify(const LbmParams& p, const DevState& d, int step, bool in
     const int w = d.CW + 2;
     dim3 gm((w * w * w + 127) / 128, d.NM);
     k_boundary_mark<<<gm, 128, 0, st>>>(p, d);
-    k_boundary_elements<<<(d.maxB + BE_WARPS - 1) / BE_WARPS, BE_WARPS * 32, 0, st>>>(p, d);
+    static const int per_sm = occupancy((const void*)k_boundary_elements, BE_WARPS * 32);
+    k_boundary_elements<<<fill_grid(per_sm, ((size_t)d.maxB + BE_WARPS - 1) / BE_WARPS), BE_WARPS * 32, 0, st>>>(p,
+                                                                                                             d);
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -497,11 +526,7 @@ __device__ __forceinline__ float wsum(float v) {
 // node, lane i-1 looks at direction i).  A node x that sees m across a cut link needs the mean over m's
 // neighbours on x's side (Eq. 14); when m borders a single other side that is the same set, so it is
 // computed once per m (otherwise flagged, and recomputed per link).
-__global__ void k_bb_vrho(LbmParams p, DevState d) {
-    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    const int nb = min(d.cnt[0], d.maxB);
-    if (b >= nb) return;
+__device__ __forceinline__ void node_vrho(const LbmParams& p, const DevState& d, const int b, const int lane) {
     const int m = d.blist[b];
     const int z = m / p.nxy, r = m - z * p.nxy, y = r / p.nx, x = r - y * p.nx;
     const uint16_t me = d.owner[m];
@@ -532,20 +557,23 @@ __global__ void k_bb_vrho(LbmParams p, DevState d) {
         d.vrho[m] = make_float4(cnt > 0.f ? a / cnt : 0.f, cnt > 0.f ? c / cnt : 0.f, cnt, omin != omax ? 1.f : 0.f);
 }
 
+__global__ void __launch_bounds__(256) k_bb_vrho(LbmParams p, DevState d) {
+    const int nb = min(d.cnt[0], d.maxB);
+    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += (gridDim.x * blockDim.x) >> 5)
+        node_vrho(p, d, b, threadIdx.x & 31);
+}
+
 // ------------------------------------------------------------------------------------------------------
 // Boundary kernel: one warp per boundary node, lane i owns direction i (i = 0..18).  Pull, moments by warp
 // reductions, Shan-Chen force with virtual densities across cut links and the wetting offset
 // (Eq. 13-15; reactions to the crossed element), BGK collision, streaming with moving half-way
 // bounce-back on walls and cut links (Eq. 11) and the exchanged momentum (Eq. 12).
 // ------------------------------------------------------------------------------------------------------
+// Returns the mass change (A, B) of the node's moving bounce-back links (Eq. 11), in every lane.
 template <typename T>
-__global__ void __launch_bounds__(256) k_boundary(LbmParams p, DevState d, const T* __restrict__ S,
-                                                  T* __restrict__ D, const float* __restrict__ ghost,
-                                                  int step, int* err) {
-    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    const int nb = min(d.cnt[0], d.maxB);
-    if (b >= nb) return;
+__device__ __forceinline__ float2 boundary_node(const LbmParams& p, const DevState& d, const T* __restrict__ S,
+                                                T* __restrict__ D, const float* __restrict__ ghost, const int step,
+                                                int* err, const int b, const int lane) {
     const int n = d.blist[b];
     const int z = n / p.nxy, r = n - z * p.nxy, y = r / p.nx, x = r - y * p.nx;
     const uint16_t me = d.owner[n];
@@ -619,9 +647,7 @@ __global__ void __launch_bounds__(256) k_boundary(LbmParams p, DevState d, const
                     psB = psi_fn(vB, p.psi_kind);
                     // reaction of both components on the element: + psi^c(x) G w_i psi^{c'}(virtual) c_i
                     const float a = p.G * wi * (pa * psB + pb * psA);
-                    atomicAdd(&d.epend[pr * d.NT + e].x, a * cx);
-                    atomicAdd(&d.epend[pr * d.NT + e].y, a * cy);
-                    atomicAdd(&d.epend[pr * d.NT + e].z, a * cz);
+                    atomicAdd(&d.epend[pr * d.NT + e], make_float4(a * cx, a * cy, a * cz, 0.f));
                 } else {
                     atomicOr(err, 2);      // list out of step with the owner field: never expected
                 }
@@ -678,27 +704,53 @@ __global__ void __launch_bounds__(256) k_boundary(LbmParams p, DevState d, const
             pst(D + (size_t)dir_opp(i) * p.N + m, bA);
             pst(D + (size_t)(Q + dir_opp(i)) * p.N + m, bB);
             const float dp = oA + bA + oB + bB;
-            atomicAdd(&d.emom[pr * d.NT + e].x, dp * cx);
-            atomicAdd(&d.emom[pr * d.NT + e].y, dp * cy);
-            atomicAdd(&d.emom[pr * d.NT + e].z, dp * cz);
+            atomicAdd(&d.emom[pr * d.NT + e], make_float4(dp * cx, dp * cy, dp * cz, 0.f));
             dm[0] = bA - oA;
             dm[1] = bB - oB;
         }
     }
-    const float dmA = wsum(dm[0]), dmB = wsum(dm[1]);
-    if (lane == 0) d.bdm[b] = make_float2(dmA, dmB);
+    return make_float2(wsum(dm[0]), wsum(dm[1]));
+}
+
+// Grid-stride over the boundary list, 8 warps per block; each block writes the sum of its nodes' mass
+// changes, in a fixed order, to bdm[blockIdx.x] and block 0 records the number of partials.
+template <typename T>
+__global__ void __launch_bounds__(256) k_boundary(LbmParams p, DevState d, const T* __restrict__ S,
+                                                  T* __restrict__ D, const float* __restrict__ ghost,
+                                                  int step, int* err) {
+    __shared__ float2 part[8];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nb = min(d.cnt[0], d.maxB);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int b = blockIdx.x * 8 + wl; b < nb; b += gridDim.x * 8) {
+        const float2 v = boundary_node<T>(p, d, S, D, ghost, step, err, b, lane);
+        acc.x += v.x;
+        acc.y += v.y;
+    }
+    if (lane == 0) part[wl] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float2 t = part[0];
+        for (int w = 1; w < 8; w++) { t.x += part[w].x; t.y += part[w].y; }
+        d.bdm[blockIdx.x] = t;
+        if (blockIdx.x == 0) d.cnt[5] = (int)gridDim.x;
+    }
 }
 
 void launch_bb_boundary(const LbmParams& p, const DevState& d, const float* S, float* D, const float* ghost,
                         int step, int* err, cudaStream_t st) {
     if (d.NM == 0) return;
-    const unsigned blocks = (unsigned)(((size_t)d.maxB * 32 + 255) / 256);
-    k_bb_vrho<<<blocks, 256, 0, st>>>(p, d);
-    if (p.half)
-        k_boundary<__half><<<blocks, 256, 0, st>>>(p, d, reinterpret_cast<const __half*>(S),
-                                                   reinterpret_cast<__half*>(D), ghost, step, err);
-    else
-        k_boundary<float><<<blocks, 256, 0, st>>>(p, d, S, D, ghost, step, err);
+    const size_t need = ((size_t)d.maxB + 7) / 8;   // 8 warps per block; the partials fit in bdm[maxB]
+    static const int per_v = occupancy((const void*)k_bb_vrho, 256);
+    k_bb_vrho<<<fill_grid(per_v, need), 256, 0, st>>>(p, d);
+    if (p.half) {
+        static const int per_h = occupancy((const void*)k_boundary<__half>, 256);
+        k_boundary<__half><<<fill_grid(per_h, need), 256, 0, st>>>(p, d, reinterpret_cast<const __half*>(S),
+                                                                   reinterpret_cast<__half*>(D), ghost, step, err);
+    } else {
+        static const int per_f = occupancy((const void*)k_boundary<float>, 256);
+        k_boundary<float><<<fill_grid(per_f, need), 256, 0, st>>>(p, d, S, D, ghost, step, err);
+    }
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -714,7 +766,7 @@ __global__ void __launch_bounds__(1024) k_mass_finalize(DevState d, double vsys)
     // the changes are small: FP32 partials per thread and per warp, FP64 only in warp 0
     __shared__ float shf[2][32];
     float fa = 0.f, fb = 0.f;
-    const int nb = min(d.cnt[3], d.maxB);
+    const int nb = min(d.cnt[5], d.maxB);            // block partials of this step's boundary kernel
     const int nf = min(d.cnt[4], d.maxF);
 #pragma unroll 4
     for (int q = threadIdx.x; q < nb; q += blockDim.x) {
@@ -771,12 +823,8 @@ __device__ __forceinline__ void pulled_rho(const LbmParams& p, const T* __restri
 // One warp per fresh node: lanes 0-17 pull the densities of the 18 neighbours, then the warp scans the
 // capsule's triangle centroids for the nearest element.
 template <typename T>
-__global__ void __launch_bounds__(256) k_fresh_compute(LbmParams p, DevState d, const T* __restrict__ S) {
-    __shared__ int queue[8][CAND_Q];
-    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    const int nf = min(d.cnt[1], d.maxF);
-    if (q >= nf) return;
+__device__ __forceinline__ void fresh_node(const LbmParams& p, const DevState& d, const T* __restrict__ S, const int q,
+                                           const int lane, int* queue) {
     const int n = d.flist[q];
     const int z = n / p.nxy, r = n - z * p.nxy, y = r / p.nx, x = r - y * p.nx;
     const uint16_t side = d.owner[n];
@@ -838,7 +886,7 @@ __global__ void __launch_bounds__(256) k_fresh_compute(LbmParams p, DevState d, 
         const float fr = (float)r;
         const CellScan cs = cell_scan(d, cap, ccx - r, ccy - r, 2 * r + 1, lane);
         for_candidates(d, cs, make_float3(px - fr, py - fr, pz - fr), make_float3(px + fr, py + fr, pz + fr),
-                       queue[threadIdx.x >> 5], lane, [&](int t) {
+                       queue, lane, [&](int t) {
                            if (t < 0) return;
                            const float3 c = f3(d.trec[4 * t + 3]);
                            const float dx = c.x - px, dy = c.y - py, dz = c.z - pz;
@@ -880,13 +928,21 @@ __global__ void __launch_bounds__(256) k_fresh_compute(LbmParams p, DevState d, 
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_fresh_compute(LbmParams p, DevState d, const T* __restrict__ S) {
+    __shared__ int queue[8][CAND_Q];
+    const int nf = min(d.cnt[1], d.maxF);
+    for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nf; q += (gridDim.x * blockDim.x) >> 5) {
+        fresh_node<T>(p, d, S, q, threadIdx.x & 31, queue[threadIdx.x >> 5]);
+        __syncwarp();
+    }
+}
+
 // Writes f_eq(rho_fresh, v) into the slots the fresh node pulls from (Eq. 2, 16-18) and hands the element
 // the removed minus the created momentum.
 template <typename T>
-__global__ void k_fresh_apply(LbmParams p, DevState d, T* __restrict__ S, int step) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nf = min(d.cnt[1], d.maxF);
-    if (q >= nf) return;
+__device__ __forceinline__ void fresh_apply_node(const LbmParams& p, const DevState& d, T* __restrict__ S,
+                                                 const int step, const int q) {
     const float4 a = d.fnew[2 * q];
     if (a.z == 0.f) {
         d.fdm[q] = make_float2(0.f, 0.f);          // populations kept
@@ -924,9 +980,14 @@ __global__ void k_fresh_apply(LbmParams p, DevState d, T* __restrict__ S, int st
     d.fdm[q] = make_float2(dA, dB);
     const float rt = a.x + a.y;
     const int nx = (step + 1) & 1;
-    atomicAdd(&d.epend[nx * d.NT + e].x, rem[0] - rt * vv.x);
-    atomicAdd(&d.epend[nx * d.NT + e].y, rem[1] - rt * vv.y);
-    atomicAdd(&d.epend[nx * d.NT + e].z, rem[2] - rt * vv.z);
+    atomicAdd(&d.epend[nx * d.NT + e], make_float4(rem[0] - rt * vv.x, rem[1] - rt * vv.y, rem[2] - rt * vv.z, 0.f));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_fresh_apply(LbmParams p, DevState d, T* __restrict__ S, int step) {
+    const int nf = min(d.cnt[1], d.maxF);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nf; q += gridDim.x * blockDim.x)
+        fresh_apply_node<T>(p, d, S, step, q);
 }
 
 // Owner field with the wall planes marked, empty lists, zero accumulators, correction factors 1.
@@ -957,13 +1018,18 @@ void launch_bb_fresh(const LbmParams& p, const DevState& d, float* Snew, int ste
     if (d.NM == 0) return;
     double vsys = (double)p.nxy * (p.zf1 - p.zf0);
     k_mass_finalize<<<1, 1024, 0, st>>>(d, vsys);
+    const size_t need_c = ((size_t)d.maxF + 7) / 8, need_a = ((size_t)d.maxF + 127) / 128;
     if (p.half) {
         __half* Sh = reinterpret_cast<__half*>(Snew);
-        k_fresh_compute<__half><<<(d.maxF * 32 + 255) / 256, 256, 0, st>>>(p, d, Sh);
-        k_fresh_apply<__half><<<(d.maxF + 127) / 128, 128, 0, st>>>(p, d, Sh, step);
+        static const int per_c = occupancy((const void*)k_fresh_compute<__half>, 256);
+        static const int per_a = occupancy((const void*)k_fresh_apply<__half>, 128);
+        k_fresh_compute<__half><<<fill_grid(per_c, need_c), 256, 0, st>>>(p, d, Sh);
+        k_fresh_apply<__half><<<fill_grid(per_a, need_a), 128, 0, st>>>(p, d, Sh, step);
     } else {
-        k_fresh_compute<float><<<(d.maxF * 32 + 255) / 256, 256, 0, st>>>(p, d, Snew);
-        k_fresh_apply<float><<<(d.maxF + 127) / 128, 128, 0, st>>>(p, d, Snew, step);
+        static const int per_c = occupancy((const void*)k_fresh_compute<float>, 256);
+        static const int per_a = occupancy((const void*)k_fresh_apply<float>, 128);
+        k_fresh_compute<float><<<fill_grid(per_c, need_c), 256, 0, st>>>(p, d, Snew);
+        k_fresh_apply<float><<<fill_grid(per_a, need_a), 128, 0, st>>>(p, d, Snew, step);
     }
 }
 

@@ -127,14 +127,14 @@ struct DevState {
     uint32_t* bmask;        // [ceil(N/32)] boundary-node bits (nodes with a cut membrane link)
     uint32_t* fmask;        // [ceil(N/32)] fresh-node bits of the current step
     int* blist;             // [maxB] boundary nodes
-    float2* bdm;            // [maxB] mass change of each boundary node's bounce-back links (A, B)
+    float2* bdm;            // [maxB] mass change (A, B) of the bounce-back links, one partial per block of the
+                            //     boundary kernel (cnt[5] partials)
     int* belem;             // [maxB][18] element crossed by the link along direction i (slot i-1), -1 if uncut
     int* flist;             // [maxF] fresh nodes
     int* fold;              // [maxF] their owner before the change
     float4* fnew;           // [maxF][2] new (rhoA, rhoB, ok, -) and (vx, vy, vz, element)
-    int* cnt;               // [8] 0: boundary nodes, 1: fresh nodes, 2: overflow flags, 3: boundary nodes of
-                            //     the step's boundary kernel, 4: fresh nodes of the previous step (both saved
-                            //     before re-listing)
+    int* cnt;               // [8] 0: boundary nodes, 1: fresh nodes, 2: overflow flags, 4: fresh nodes of the
+                            //     previous step (saved before re-listing), 5: partials in bdm
     float4* emom;           // [2][NT] exchanged momentum (Eq. 12) by step parity
     float4* epend;          // [2][NT] Shan-Chen reactions and fresh-node momenta by step parity
     int4* cbox;             // [NM][2] classification box (lo, hi), unwrapped lattice coordinates
