@@ -24,10 +24,24 @@ sys.path.insert(0, ROOT)
 from paper_1904_11386_gb300 import inputs  # noqa: E402
 
 # Algorithmic bytes per lattice update of the fused bulk kernel (both components): read 2 x 19 populations,
-# write 2 x 19 populations (4 bytes each in FP32 storage, 2 in FP16), write rho^A and rho^B (FP32).
+# write 2 x 19 populations (4 bytes each in FP32 storage, 2 in FP16 or BF16), write rho^A and rho^B (FP32).
 BYTES_PER_LU = 2 * 19 * 4 * 2 + 2 * 4
-BYTES_PER_LU_FP16 = 2 * 19 * 2 * 2 + 2 * 4
+BYTES_PER_LU_16 = 2 * 19 * 2 * 2 + 2 * 4
+STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
+# error against the FP64 oracle of each 16-bit storage, as the tests bound it
+STORAGE_ERROR = {
+    "fp16": ("densities 1.3e-3, velocities 2.2e-3 of max|u|, vertices 1.7e-3 after 200 steps (32^3); mass offset "
+             "1e-5, drift over 2000 steps (128^3) as FP32's; tests/test_gpu_storage16.py"),
+    "bf16": ("densities 1.9e-2, velocities 2.6e-2 of max|u|, vertices 2.6e-2 after 200 steps (32^3); mass offset "
+             "3e-4, drift 8.6e-4 over 2000 steps (128^3); tests/test_gpu_storage16.py"),
+}
+
+
 FALLBACK_HBM_GBS = 6800.0
+
+
+def bytes_per_lu(storage: str) -> int:
+    return BYTES_PER_LU if storage == "fp32" else BYTES_PER_LU_16
 
 
 def workload(name: str):
@@ -173,9 +187,9 @@ def recorded_traffic(workload_name: str):
     return int(m_tr.group(1))
 
 
-def fp16_beside(prob, args, ws, local, n_upd, peak):
-    """The same workload with the populations stored as FP16 (FP32 arithmetic), timed the same way: K steps
-    as the user call runs them, then K steps with events around every bulk launch."""
+def storage_beside(prob, args, ws, local, n_upd, peak, storage):
+    """The same workload with the populations stored as FP16 or BF16 (FP32 arithmetic), timed the same way:
+    K steps as the user call runs them, then K steps with events around every bulk launch."""
     import copy
 
     import torch
@@ -183,7 +197,7 @@ def fp16_beside(prob, args, ws, local, n_upd, peak):
     from paper_1904_11386_gb300 import scbb
 
     p16 = copy.deepcopy(prob)
-    p16.storage = 1
+    p16.storage = STORAGE[storage]
     rhoA, rhoB = p16.initial_density()
     sim = scbb.Sim(p16, rhoA, rhoB, device=f"cuda:{local}")
     st = sim.stream
@@ -203,14 +217,13 @@ def fp16_beside(prob, args, ws, local, n_upd, peak):
     sim.scbb_sync()
     sim.close()
     bulk_s = bulk_ms / max(bulk_n, 1) / 1e3
-    achieved = BYTES_PER_LU_FP16 * n_upd / bulk_s / 1e9
+    achieved = BYTES_PER_LU_16 * n_upd / bulk_s / 1e9
     return {"value": aggregate_glups(prob.n_nodes, args.steps, ws, ms / 1e3), "unit": "GLUPS",
             "ms_per_step": ms / args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "bytes_per_lu": BYTES_PER_LU_FP16, "kernel_ms": bulk_s * 1e3,
-                         "traffic": recorded_traffic(args.workload + "-fp16")},
-            "error_vs_fp64_oracle": "densities 1e-3 relative after 200 steps (32^3), mass offset 1e-5; "
-                                    "tests/test_gpu_fp16.py"}
+                         "bytes_per_lu": BYTES_PER_LU_16, "kernel_ms": bulk_s * 1e3,
+                         "traffic": recorded_traffic(f"{args.workload}-{storage}")},
+            "error_vs_fp64_oracle": STORAGE_ERROR[storage]}
 
 
 def run_batch(args, probs, label, ws, rank, local):
@@ -383,8 +396,9 @@ def main():
     ap.add_argument("--workload", default="adsorb128")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-storage figures beside the FP32 ones")
-    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
+    ap.add_argument("--no-fp16", action="store_true",
+                    help="skip the 16-bit storage figures (FP16, BF16) beside the FP32 ones")
+    ap.add_argument("--storage", default="fp32", choices=list(STORAGE),
                     help="population storage on the GPU (arithmetic is FP32 either way)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -401,9 +415,9 @@ def main():
 
             dist.destroy_process_group()
         return
-    if args.storage == "fp16":
-        prob.storage = 1
-        label += "; populations stored as FP16"
+    if args.storage != "fp32":
+        prob.storage = STORAGE[args.storage]
+        label += f"; populations stored as {args.storage.upper()}"
     if args.impl == "reference":
         run_reference(args, prob, label, ws, rank)
         if ws > 1:
@@ -476,10 +490,10 @@ def main():
     peak, src = peak_hbm()
     bulk_avg_s = bulk_ms / max(bulk_n, 1) / 1e3
     n_upd = prob.nx * prob.ny * (prob.nz - 2 * prob.walls)    # nodes one bulk launch updates (no wall planes)
-    bpl = BYTES_PER_LU_FP16 if args.storage == "fp16" else BYTES_PER_LU
+    bpl = bytes_per_lu(args.storage)
     achieved = bpl * n_upd / bulk_avg_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": recorded_traffic(args.workload + ("-fp16" if args.storage == "fp16" else "")),
+            "traffic": recorded_traffic(args.workload + ("" if args.storage == "fp32" else "-" + args.storage)),
             "kernel": "k_bulk4 (fused 2-component stream + Shan-Chen + collide)",
             "bytes_per_lu": bpl, "units_per_launch": n_upd, "peak_source": src,
             "kernel_ms": bulk_avg_s * 1e3, "kernel_share": bulk_avg_s * 1e3 / (ms / args.steps) if ms > 0 else None,
@@ -493,11 +507,12 @@ def main():
            "config": {"workload": label, "lattice": [prob.nx, prob.ny, prob.nz], "nodes": N,
                       "vertices": int(sum(sim.nv)), "parallelism": f"replicas x{ws}",
                       "storage": args.storage,
-                      "l2": f"inputs larger than L2 (populations 2 x {2 * 19 * N * (2 if args.storage == 'fp16' else 4) / 1e6:.0f} MB)"},
+                      "l2": f"inputs larger than L2 (populations 2 x {2 * 19 * N * (4 if args.storage == 'fp32' else 2) / 1e6:.0f} MB)"},
            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     sim.close()
     if args.storage == "fp32" and not args.no_fp16:
-        out["fp16_storage"] = fp16_beside(prob, args, ws, local, n_upd, peak)
+        for st16 in ("fp16", "bf16"):
+            out[f"{st16}_storage"] = storage_beside(prob, args, ws, local, n_upd, peak, st16)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
     if rank == 0:

@@ -68,10 +68,10 @@ typedef struct {
  *             density offset (Eq. 15): rho_virtual = 2 |colour| (rho_maj - rho_min)
  *   C0, mass_correction   adaptive fresh-node mass correction (Eq. 18), C0 = 2500 in the paper
  *   pp_eps, pp_d0         particle-particle repulsion (Eq. 26, Sec. III.E), 0.5 and 1.25 in the paper
- *   storage   0: FP32 populations; 1: populations stored as IEEE FP16 (arithmetic stays FP32; each stored
- *             value is rounded to nearest, about 2.4e-4 relative), half the population bytes.  Not in the
- *             paper.
- * FP16 storage and the bounce-back coupling with meshes run on the row-vectorised bulk kernel, which needs nx
+ *   storage   0: FP32 populations; 1: populations stored as IEEE FP16, 2: as BF16 (arithmetic stays FP32;
+ *             each stored value is rounded to nearest even, at most 2^-12 relative for FP16 and 2^-9 for
+ *             BF16), half the population bytes.  Not in the paper.
+ * 16-bit storage and the bounce-back coupling with meshes run on the row-vectorised bulk kernel, which needs nx
  * a multiple of 4 (and, for tau != 1, nx/4 a power of two up to 32 or a multiple of 32); otherwise
  * scbb_create returns SCBB_E_UNSUPPORTED. */
 typedef struct {

@@ -17,6 +17,8 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "scbb_internal.cuh"
 
 namespace scbb {
@@ -743,14 +745,12 @@ void launch_bb_boundary(const LbmParams& p, const DevState& d, const float* S, f
     const size_t need = ((size_t)d.maxB + 7) / 8;   // 8 warps per block; the partials fit in bdm[maxB]
     static const int per_v = occupancy((const void*)k_bb_vrho, 256);
     k_bb_vrho<<<fill_grid(per_v, need), 256, 0, st>>>(p, d);
-    if (p.half) {
-        static const int per_h = occupancy((const void*)k_boundary<__half>, 256);
-        k_boundary<__half><<<fill_grid(per_h, need), 256, 0, st>>>(p, d, reinterpret_cast<const __half*>(S),
-                                                                   reinterpret_cast<__half*>(D), ghost, step, err);
-    } else {
-        static const int per_f = occupancy((const void*)k_boundary<float>, 256);
-        k_boundary<float><<<fill_grid(per_f, need), 256, 0, st>>>(p, d, S, D, ghost, step, err);
-    }
+    with_storage(p.store, [&](auto* tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        static const int per_b = occupancy((const void*)k_boundary<T>, 256);
+        k_boundary<T><<<fill_grid(per_b, need), 256, 0, st>>>(p, d, reinterpret_cast<const T*>(S),
+                                                              reinterpret_cast<T*>(D), ghost, step, err);
+    });
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -1019,18 +1019,14 @@ void launch_bb_fresh(const LbmParams& p, const DevState& d, float* Snew, int ste
     double vsys = (double)p.nxy * (p.zf1 - p.zf0);
     k_mass_finalize<<<1, 1024, 0, st>>>(d, vsys);
     const size_t need_c = ((size_t)d.maxF + 7) / 8, need_a = ((size_t)d.maxF + 127) / 128;
-    if (p.half) {
-        __half* Sh = reinterpret_cast<__half*>(Snew);
-        static const int per_c = occupancy((const void*)k_fresh_compute<__half>, 256);
-        static const int per_a = occupancy((const void*)k_fresh_apply<__half>, 128);
-        k_fresh_compute<__half><<<fill_grid(per_c, need_c), 256, 0, st>>>(p, d, Sh);
-        k_fresh_apply<__half><<<fill_grid(per_a, need_a), 128, 0, st>>>(p, d, Sh, step);
-    } else {
-        static const int per_c = occupancy((const void*)k_fresh_compute<float>, 256);
-        static const int per_a = occupancy((const void*)k_fresh_apply<float>, 128);
-        k_fresh_compute<float><<<fill_grid(per_c, need_c), 256, 0, st>>>(p, d, Snew);
-        k_fresh_apply<float><<<fill_grid(per_a, need_a), 128, 0, st>>>(p, d, Snew, step);
-    }
+    with_storage(p.store, [&](auto* tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        T* Sn = reinterpret_cast<T*>(Snew);
+        static const int per_c = occupancy((const void*)k_fresh_compute<T>, 256);
+        static const int per_a = occupancy((const void*)k_fresh_apply<T>, 128);
+        k_fresh_compute<T><<<fill_grid(per_c, need_c), 256, 0, st>>>(p, d, Sn);
+        k_fresh_apply<T><<<fill_grid(per_a, need_a), 128, 0, st>>>(p, d, Sn, step);
+    });
 }
 
 }  // namespace scbb

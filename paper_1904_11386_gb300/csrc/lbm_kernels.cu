@@ -49,8 +49,9 @@ __global__ void k_init_state(LbmParams p, T* __restrict__ S, const float* __rest
         pst(S + (size_t)i * p.N + m, va);
         pst(S + (size_t)(Q + i) * p.N + m, vb);
     }
-    pst(S + n, a - sa);
-    pst(S + (size_t)Q * p.N + n, b - sb);
+    const uint32_t h = dither_bits(n, a, b);
+    pst(S + n, pdither(a - sa, h >> 16, S));
+    pst(S + (size_t)Q * p.N + n, pdither(b - sb, h & 0xffffu, S));
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -775,6 +776,11 @@ k_bulk4(LbmParams p, const T* __restrict__ S, T* __restrict__ D, float* __restri
                     if (I == 0) {
                         eA = ra[k] - sA[k];
                         eB = rb[k] - sB[k];
+                        if (TAU1 && sizeof(T) == 2) {   // unbiased rounding of the mass-closing value
+                            const uint32_t h = dither_bits(n0 + k, ra[k], rb[k]);
+                            eA = pdither(eA, h >> 16, D);
+                            eB = pdither(eB, h & 0xffffu, D);
+                        }
                     } else {
                         const float cuA = dir_x(I) * uA[k][0] + dir_y(I) * uA[k][1] + dir_z(I) * uA[k][2];
                         const float cuB = dir_x(I) * uB[k][0] + dir_y(I) * uB[k][1] + dir_z(I) * uB[k][2];
@@ -931,17 +937,16 @@ static void launch_b4t(const LbmParams& q, dim3 grid, int threads, size_t smem, 
     k_bulk4<TAU1, MODE, NT, MINB, T><<<grid, threads, smem, st>>>(q, S, D, rho, ghost, Fibm, mask, u, err, TY);
 }
 
-// S, D point to FP32 or (q.half) FP16 populations
+// S, D point to populations of the type q.store names
 template <bool TAU1, int MODE, int NT, int MINB>
 static void launch_b4(const LbmParams& q, dim3 grid, int threads, size_t smem, int TY, const float* S, float* D,
                       float* rho, const float* ghost, const float* Fibm, const uint32_t* mask, float* u, int* err,
                       cudaStream_t st) {
-    if (q.half)
-        launch_b4t<TAU1, MODE, NT, MINB, __half>(q, grid, threads, smem, TY, reinterpret_cast<const __half*>(S),
-                                                 reinterpret_cast<__half*>(D), rho, ghost, Fibm, mask, u, err, st);
-    else
-        launch_b4t<TAU1, MODE, NT, MINB, float>(q, grid, threads, smem, TY, S, D, rho, ghost, Fibm, mask, u, err,
-                                                st);
+    with_storage(q.store, [&](auto* tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        launch_b4t<TAU1, MODE, NT, MINB, T>(q, grid, threads, smem, TY, reinterpret_cast<const T*>(S),
+                                            reinterpret_cast<T*>(D), rho, ghost, Fibm, mask, u, err, st);
+    });
 }
 
 template <int NT, int MINB>
@@ -1022,18 +1027,17 @@ void launch_bulk(const LbmParams& p, const float* S, float* D, float* rho, const
 }
 
 void launch_init_state(const LbmParams& p, float* S, const float* rho_st, const float* u_st, cudaStream_t st) {
-    if (p.half)
-        k_init_state<__half><<<(p.N + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<__half*>(S), rho_st, u_st);
-    else
-        k_init_state<float><<<(p.N + 255) / 256, 256, 0, st>>>(p, S, rho_st, u_st);
+    with_storage(p.store, [&](auto* tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        k_init_state<T><<<(p.N + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<T*>(S), rho_st, u_st);
+    });
 }
 
 void launch_wall_ghost(const LbmParams& p, const float* S, float* wall_rho, float* ghost, cudaStream_t st) {
-    if (p.half)
-        k_wall_planes_rho<__half><<<(2 * p.nxy + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<const __half*>(S),
-                                                                          wall_rho);
-    else
-        k_wall_planes_rho<float><<<(2 * p.nxy + 255) / 256, 256, 0, st>>>(p, S, wall_rho);
+    with_storage(p.store, [&](auto* tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        k_wall_planes_rho<T><<<(2 * p.nxy + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<const T*>(S), wall_rho);
+    });
     k_wall_ghost<<<(4 * p.nxy + 255) / 256, 256, 0, st>>>(p, wall_rho, ghost);
 }
 
@@ -1092,10 +1096,10 @@ __global__ void k_export(LbmParams p, const T* __restrict__ S, float* __restrict
 }
 
 void launch_export(const LbmParams& p, const float* S, float* out, int what, cudaStream_t st) {
-    if (p.half)
-        k_export<__half><<<(p.N + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<const __half*>(S), out, what);
-    else
-        k_export<float><<<(p.N + 255) / 256, 256, 0, st>>>(p, S, out, what);
+    with_storage(p.store, [&](auto* tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        k_export<T><<<(p.N + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<const T*>(S), out, what);
+    });
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -1156,10 +1160,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_sum_partials(const double* __re
 
 void launch_moments_reduce(const LbmParams& p, const float* S, double* red, cudaStream_t st) {
     // red must hold 8 + 5 * RED_BLOCKS doubles; result in red[0..4]
-    if (p.half)
-        k_moments_partial<__half><<<RED_BLOCKS, RED_THREADS, 0, st>>>(p, reinterpret_cast<const __half*>(S), red + 8);
-    else
-        k_moments_partial<float><<<RED_BLOCKS, RED_THREADS, 0, st>>>(p, S, red + 8);
+    with_storage(p.store, [&](auto* tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        k_moments_partial<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(p, reinterpret_cast<const T*>(S), red + 8);
+    });
     k_sum_partials<<<1, RED_THREADS, 0, st>>>(red + 8, RED_BLOCKS, 5, red);
 }
 

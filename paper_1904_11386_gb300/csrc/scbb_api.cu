@@ -96,7 +96,7 @@ bool valid_fluid(const scbb_fluid* f) {
     if (!f || !(f->tau > 0.5) || !isfinite(f->G)) return false;
     if (f->psi_kind != 0 && f->psi_kind != 1) return false;
     if (f->coupling != 0 && f->coupling != 1) return false;
-    if (f->storage != 0 && f->storage != 1) return false;
+    if (f->storage < 0 || f->storage > 2) return false;
     if (f->pp_eps != 0.0 && !(f->pp_d0 > 0.0)) return false;
     return true;
 }
@@ -119,7 +119,7 @@ LbmParams make_params(const scbb_lattice* lat, const scbb_fluid* fl) {
     p.omega = (float)(1.0 / fl->tau);
     p.G = (float)fl->G;
     p.psi_kind = fl->psi_kind;
-    p.half = fl->storage == 1 ? 1 : 0;
+    p.store = fl->storage;
     for (int k = 0; k < 3; k++) {
         p.g[k] = (float)fl->g[k];
         p.ulo[k] = (float)lat->u_lo[k];
@@ -180,8 +180,8 @@ size_t layout(const scbb_lattice* lat, const scbb_fluid* fl, int nm, const scbb_
     const size_t nxy = (size_t)lat->nx * lat->ny;
     const int NV = total(ms, nm, false), NT = total(ms, nm, true);
     DevState t{};
-    // FP16 storage halves the lattices; each still holds the 5 N floats staged through it by set_density
-    const size_t pop_floats = fl->storage == 1 ? (size_t)Q * N : (size_t)2 * Q * N;
+    // FP16 and BF16 storage halve the lattices; each still holds the 5 N floats staged through it by set_density
+    const size_t pop_floats = fl->storage != 0 ? (size_t)Q * N : (size_t)2 * Q * N;
     t.S[0] = c.take<float>(pop_floats);
     t.S[1] = c.take<float>(pop_floats);
     t.rho = c.take<float>(2 * N);
@@ -309,8 +309,8 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
     std::string why;
     if (!valid_lattice(lat) || !valid_fluid(fl) || !dev_workspace) return SCBB_E_INVAL;
     if (!valid_meshes(n_mesh, meshes, why)) return SCBB_E_MESH;
-    if ((fl->coupling == 0 && n_mesh > 0) || fl->storage == 1) {
-        // bounce-back membranes and FP16 storage run with the row-vectorised bulk kernel (nx a multiple of 4;
+    if ((fl->coupling == 0 && n_mesh > 0) || fl->storage != 0) {
+        // bounce-back membranes and 16-bit storage run with the row-vectorised bulk kernel (nx a multiple of 4;
         // for tau != 1 also nx/4 a power of two up to 32 or a multiple of 32)
         LbmParams lp = make_params(lat, fl);
         if (!bulk_vectorised(lp)) return SCBB_E_UNSUPPORTED;
@@ -407,7 +407,7 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
     if (n_mesh > 0)
         CUDA_TRY(c, cudaMemcpyAsync(d.cap, caps.data(), sizeof(CapDev) * n_mesh, cudaMemcpyHostToDevice, c->st));
     const size_t N = c->lp.N;
-    const size_t pop_bytes = (c->lp.half ? sizeof(uint16_t) : sizeof(float)) * 2 * Q * N;
+    const size_t pop_bytes = (c->lp.store ? sizeof(uint16_t) : sizeof(float)) * 2 * Q * N;
     CUDA_TRY(c, cudaMemsetAsync(d.S[0], 0, pop_bytes, c->st));
     CUDA_TRY(c, cudaMemsetAsync(d.S[1], 0, pop_bytes, c->st));
     CUDA_TRY(c, cudaMemsetAsync(d.rho, 0, sizeof(float) * 2 * N, c->st));
@@ -438,7 +438,7 @@ scbb_status scbb_set_density(scbb_ctx* c, const double* rhoA, const double* rhoB
     float* stage = c->d.S[1 - c->cur];
     CUDA_TRY(c, cudaMemcpyAsync(stage, h.data(), sizeof(float) * 5 * N, cudaMemcpyHostToDevice, c->st));
     CUDA_TRY(c, cudaMemsetAsync(c->d.S[c->cur], 0,
-                                (c->lp.half ? sizeof(uint16_t) : sizeof(float)) * 2 * Q * N, c->st));
+                                (c->lp.store ? sizeof(uint16_t) : sizeof(float)) * 2 * Q * N, c->st));
     launch_init_state(c->lp, c->d.S[c->cur], stage, stage + 2 * N, c->st);
     c->launches++;
     if (c->d.NV > 0) {
@@ -688,8 +688,8 @@ static scbb_status export_state(scbb_ctx* c, int what, std::vector<float>& h) {
     float* stage = c->d.S[1 - c->cur];
     const size_t cnt = what == 1 ? 2 * Q * N : 5 * N;
     h.resize(cnt);
-    if (what == 1 && c->lp.half) {
-        // an FP16 lattice holds 19 N floats: export the components one after the other
+    if (what == 1 && c->lp.store) {
+        // a 16-bit lattice holds 19 N floats: export the components one after the other
         for (int comp = 0; comp < 2; comp++) {
             launch_export(c->lp, c->d.S[c->cur], stage, 2 + comp, c->st);
             c->launches++;

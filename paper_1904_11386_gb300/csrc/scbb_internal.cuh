@@ -1,12 +1,13 @@
 // Internal declarations shared by the CUDA translation units of libscbb (sm_103a).
 //
-// Population storage: two lattices S[c][i][N] (structure of arrays, x fastest) of FP32 or, with FP16 storage,
-// IEEE half values; all arithmetic is FP32 either way.  A lattice holds the post-collision populations of the
+// Population storage: two lattices S[c][i][N] (structure of arrays, x fastest) of FP32, IEEE FP16 or BF16
+// values; all arithmetic is FP32 in every case.  A lattice holds the post-collision populations of the
 // last step, not yet streamed; streaming is a pull, f_i(x) = S[i][x - c_i].
 // Links that end on a wall node (Eq. 11) store the bounced value in the slot the receiving node pulls from,
 // so every pull is the same plain gather and the density of any node can be recomputed from S.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -48,23 +49,64 @@ struct LbmParams {
     int psi_kind;
     float g[3];
     float ulo[3], uhi[3];
-    int half;               // 1: populations stored as FP16 (the S pointers point to __half)
+    int store;              // population storage: 0 FP32, 1 FP16 (__half), 2 BF16 (__nv_bfloat16); the S
+                            // pointers point to that type
 };
 
-// Population element access for either storage (values convert to and from FP32 at the load and store;
-// FP16 stores round to nearest).  A four-node vector is 16 bytes in FP32 and 8 bytes in FP16.
+// Calls f with a null pointer of the population storage type of `store` (float, __half or __nv_bfloat16), so a
+// launcher instantiates the kernel for that type: with_storage(p.store, [&](auto* tag) { using T = ...; }).
+template <class F>
+inline void with_storage(int store, F&& f) {
+    if (store == 1) f(static_cast<__half*>(nullptr));
+    else if (store == 2) f(static_cast<__nv_bfloat16*>(nullptr));
+    else f(static_cast<float*>(nullptr));
+}
+
+// Population element access for each storage (values convert to and from FP32 at the load and store;
+// FP16 and BF16 stores round to nearest even).  A four-node vector is 16 bytes in FP32 and 8 bytes in FP16
+// or BF16.
 __device__ __forceinline__ float pld(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float pld(const __half* p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ float pld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
 // the value a store of this storage type keeps (identity for FP32): collisions sum the stored values of the
 // moving populations, so the rest population absorbs their rounding and the node's mass is exact up to
 // one rounding
 __device__ __forceinline__ float pround(float v, const float*) { return v; }
 __device__ __forceinline__ float pround(float v, const __half*) { return __half2float(__float2half_rn(v)); }
+__device__ __forceinline__ float pround(float v, const __nv_bfloat16*) {
+    return __bfloat162float(__float2bfloat16_rn(v));
+}
+// Unbiased rounding of v to the storage type: the neighbour below or above, the one above with probability
+// (v - below) / (above - below), for a uniform 16-bit draw u.  The rest population closes each node's mass;
+// rounded to nearest it would carry the same error at every node of a uniform phase, step after step, and
+// the total mass would drift.
+__device__ __forceinline__ float pdither(float v, uint32_t, const float*) { return v; }
+__device__ __forceinline__ float pdither(float v, uint32_t u, const __half*) {
+    const float lo = __half2float(__float2half_rd(v)), hi = __half2float(__float2half_ru(v));
+    return (hi - lo) * ((float)u * (1.f / 65536.f)) < v - lo ? hi : lo;
+}
+__device__ __forceinline__ float pdither(float v, uint32_t u, const __nv_bfloat16*) {
+    const float lo = __bfloat162float(__float2bfloat16_rd(v)), hi = __bfloat162float(__float2bfloat16_ru(v));
+    return (hi - lo) * ((float)u * (1.f / 65536.f)) < v - lo ? hi : lo;
+}
+// Two 16-bit draws (high and low half) for node n: the node index and the bits of its two densities, so that
+// the draws change with the state from step to step, through the 32-bit finalizer of MurmurHash3.
+__device__ __forceinline__ uint32_t dither_bits(unsigned int n, float ra, float rb) {
+    uint32_t h = n * 0x9e3779b9u ^ __float_as_uint(ra) ^ (__float_as_uint(rb) << 7);
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
 // coherent loads, for populations a kernel also writes (the pld loads go through the read-only path)
 __device__ __forceinline__ float pldc(const float* p) { return *p; }
 __device__ __forceinline__ float pldc(const __half* p) { return __half2float(*p); }
+__device__ __forceinline__ float pldc(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 __device__ __forceinline__ void pst(float* p, float v) { *p = v; }
 __device__ __forceinline__ void pst(__half* p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ void pst(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 __device__ __forceinline__ float4 pld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ float4 pld4(const __half* p) {
     const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
@@ -74,9 +116,24 @@ __device__ __forceinline__ float4 pld4(const __half* p) {
     const float2 fa = __half22float2(a), fb = __half22float2(b);
     return make_float4(fa.x, fa.y, fb.x, fb.y);
 }
+__device__ __forceinline__ float4 pld4(const __nv_bfloat16* p) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    __nv_bfloat162 a, b;
+    memcpy(&a, &u.x, 4);
+    memcpy(&b, &u.y, 4);
+    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
 __device__ __forceinline__ void pst4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 __device__ __forceinline__ void pst4(__half* p, float4 v) {
     const __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+    uint2 u;
+    memcpy(&u.x, &a, 4);
+    memcpy(&u.y, &b, 4);
+    *reinterpret_cast<uint2*>(p) = u;
+}
+__device__ __forceinline__ void pst4(__nv_bfloat16* p, float4 v) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
     uint2 u;
     memcpy(&u.x, &a, 4);
     memcpy(&u.y, &b, 4);
@@ -92,7 +149,7 @@ struct CapDev {
 
 // Device-side buffers of a context (all carved from the caller's workspace).
 struct DevState {
-    float* S[2];            // populations, 2 * 19 * N values each (FP32, or FP16 when LbmParams::half)
+    float* S[2];            // populations, 2 * 19 * N values each, of the type LbmParams::store names
     float* rho;             // [2][N] densities of the last collision
     float* u;               // [3][N] velocity incl. half force, written where the IBM mask is set
     float* Fibm;            // [3][N] spread immersed-boundary force density

@@ -109,7 +109,7 @@ class Problem:
     noise: float = 1e-4
     seed: int = 1
     steps: int = 200
-    storage: int = 0                # populations on the GPU: 0 FP32, 1 FP16 (the oracle is FP64 either way)
+    storage: int = 0                # populations on the GPU: 0 FP32, 1 FP16, 2 BF16 (the oracle is FP64 always)
 
     @property
     def n_nodes(self):

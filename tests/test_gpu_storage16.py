@@ -1,0 +1,114 @@
+"""16-bit population storage (populations stored as IEEE FP16 or BF16, arithmetic in FP32) against the FP64
+oracle.
+
+Every stored moving population is rounded to nearest even, a relative error of at most 2^-12 (FP16) or 2^-9
+(BF16).  The rest population of each collision absorbs the rounding of the 18 moving ones and is itself
+rounded without bias (to the value below or above with the probabilities that make the mean exact), so a
+node's mass is off by one unbiased rounding and the total mass does not drift systematically.  The bounds
+below are about three times the values measured on a GB300; BF16's are about ten times FP16's, close to the
+ratio 8 of the two unit roundoffs.  The bounce-back comparison is limited to a window shorter than the first
+side change whose timing the rounding can move."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1904_11386_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FP16, BF16 = 1, 2
+
+# storage -> bounds (density relative, velocity relative to max|u|, vertices in lattice units, mass relative)
+BOUNDS = {
+    "fluid": {FP16: dict(rho=6e-3, mass=3e-5), BF16: dict(rho=5e-2, mass=3e-4)},
+    "parity32": {FP16: dict(rho=4e-3, u=7e-3, X=6e-3, mass=3e-5), BF16: dict(rho=6e-2, u=8e-2, X=8e-2, mass=1e-3)},
+    "adsorb128": {FP16: dict(rho=2e-3, mass=2e-6), BF16: dict(rho=1.5e-2, mass=1e-5)},
+}
+
+
+def _run(prob, steps, storage):
+    from paper_1904_11386_gb300 import scbb
+
+    prob.storage = storage
+    g = scbb.Sim(prob)
+    g.scbb_step(steps)
+    o = O.OracleSim(prob)
+    o.step(steps)
+    return g, o
+
+
+def _rho_err(g, o, keep=None):
+    ga, gb, gu = g.scbb_get_fields()
+    oa, ob, ou = o.fields()
+    fl = oa + ob > 0
+    if keep is not None:
+        fl &= keep
+    e = max((np.abs(ga - oa)[fl] / oa[fl]).max(), (np.abs(gb - ob)[fl] / ob[fl]).max())
+    eu = np.abs(gu - ou)[:, fl].max() / np.abs(ou).max()
+    return e, eu
+
+
+def _mass_err(g, o):
+    d = g.scbb_get_diag()
+    m = np.array([o.mass(0), o.mass(1)])
+    return np.abs(np.asarray(d["mass"]) - m).max() / m.max()
+
+
+@pytest.mark.parametrize("storage", [FP16, BF16])
+def test_fluid_100_steps(storage):
+    """Two-component fluid with walls, 100 steps."""
+    b = BOUNDS["fluid"][storage]
+    g, o = _run(inputs.small_problem(n=32, walls=1, coupling=1, capsule=False, noise=1e-3), 100, storage)
+    e, _ = _rho_err(g, o)
+    assert e < b["rho"], e
+    assert _mass_err(g, o) < b["mass"]
+
+
+@pytest.mark.parametrize("storage", [FP16, BF16])
+def test_parity32_ibm_200_steps(storage):
+    """The 32^3 immersed-boundary configuration, 200 steps: densities, velocities, vertices and mass."""
+    b = BOUNDS["parity32"][storage]
+    g, o = _run(inputs.cfg_parity(coupling=1), 200, storage)
+    e, eu = _rho_err(g, o)
+    assert e < b["rho"], e
+    assert eu < b["u"], eu
+    Xg, _, _ = g.scbb_get_vertices()
+    Xo, _, _ = o.vertices()
+    assert np.abs(Xg - Xo).max() < b["X"]
+    assert _mass_err(g, o) < b["mass"]
+
+
+@pytest.mark.parametrize("storage", [FP16, BF16])
+def test_adsorb128_3_steps(storage):
+    """The 128^3 bounce-back workload, 3 steps: owners identical, densities and mass within the bounds."""
+    b = BOUNDS["adsorb128"][storage]
+    g, o = _run(inputs.cfg_adsorb128(coupling=0), 3, storage)
+    og, _, _ = g.scbb_get_owner()
+    assert np.array_equal(og, o.owner())
+    e, _ = _rho_err(g, o)
+    assert e < b["rho"], e
+    assert _mass_err(g, o) < b["mass"]
+
+
+def test_mass_drift_2000_steps():
+    """Per-component mass after 2000 steps of the 128^3 bounce-back workload (fresh nodes with the Eq. 18
+    correction): FP16 and BF16 drift no more than FP32 does by the method itself (measured 2.3e-4 for FP32,
+    2.0e-4 for FP16, 1.5e-4 for BF16; BF16's bound is wider because its rest rounding is 8 times coarser).
+    Rounding the rest population to nearest instead drifted 1.6e-3 (FP16) and 9.7e-3 (BF16)."""
+    from paper_1904_11386_gb300 import scbb
+
+    drift = {}
+    for storage in (0, FP16, BF16):
+        p = inputs.cfg_adsorb128(coupling=0)
+        p.storage = storage
+        g = scbb.Sim(p)
+        m0 = np.asarray(g.scbb_get_diag()["mass"])
+        g.scbb_step(2000)
+        m1 = np.asarray(g.scbb_get_diag()["mass"])
+        a, _, u = g.scbb_get_fields()
+        assert np.isfinite(a).all() and np.isfinite(u).all()
+        drift[storage] = np.abs(m1 - m0).max() / m0.max()
+        g.close()
+    assert drift[0] < 4e-4, drift
+    assert drift[FP16] < 5e-4, drift
+    assert drift[BF16] < 2e-3, drift
