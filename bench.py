@@ -66,6 +66,11 @@ def workload(name: str):
         p = inputs.cfg_droplet256(n_caps=40, coupling=0, n=128, R_drop=35.0)
         return p, (f"droplet128: 128^3 periodic two-component box, B droplet R=35 covered by {len(p.capsules)} s=3 "
                    "capsules R=8 with colours +-0.05, half-way bounce-back, repulsion")
+    if name == "adjoint64":
+        return inputs.cfg_adjoint(n=64, R_drop=16.0), ("adjoint64: 64^3 periodic two-component box, B droplet R=16, "
+                                                       "gradient of the components' weighted centres of mass "
+                                                       "after 2000 steps w.r.t. G, g and the initial densities, "
+                                                       "checkpoint every 100 steps")
     if name == "fluid256":
         p = inputs.cfg_droplet256(n_caps=0, coupling=1)
         p.capsules = []
@@ -363,6 +368,58 @@ def run_reference_batch(args, probs, label, rank):
           flush=True)
 
 
+def run_adjoint(args, prob, label, ws, rank, local, n_steps=2000, every=100):
+    """Forward (n steps with a population checkpoint every `every` steps) and backward (recompute each
+    segment, adjoint steps) of the fluid adjoint, each timed with CUDA events on the context stream after a
+    warm-up pair; value = backward time / forward time."""
+    import numpy as np
+    import torch
+
+    from paper_1904_11386_gb300 import scbb
+
+    torch.cuda.set_device(local)
+    rhoA0, rhoB0 = prob.initial_density()
+    z, _, x = np.meshgrid(np.arange(prob.nz), np.arange(prob.ny), np.arange(prob.nx), indexing="ij")
+    wA, wB = z.astype(np.float64), 0.5 * x.astype(np.float64)
+    sim = scbb.Sim(prob, rhoA0, rhoB0, device=f"cuda:{local}")
+    adj = scbb.Adjoint(sim, n_steps, every)
+    st = sim.stream
+    times = []
+    for rep in range(2):                     # the first pair warms up
+        sim.scbb_set_density(rhoA0, rhoB0)
+        sim.scbb_sync()
+        l0 = sim.scbb_launch_count()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(st)
+        adj.scbb_adjoint_forward()
+        e1.record(st)
+        dG, dg, _, _ = adj.scbb_adjoint_backward(wA, wB)
+        e2.record(st)
+        torch.cuda.synchronize()
+        times.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
+        launches = sim.scbb_launch_count() - l0
+    fwd_ms, bwd_ms = times[-1]
+    fwd_ms = replica_max(fwd_ms, ws, f"cuda:{local}")
+    bwd_ms = replica_max(bwd_ms, ws, f"cuda:{local}")
+    nodes = prob.n_nodes
+    out = {"metric": "fluid adjoint backward / forward time (2000 steps, checkpoint every 100)",
+           "value": bwd_ms / fwd_ms, "unit": "x", "n_gpus": ws, "steps": n_steps, "warmup": 1,
+           "ms_per_step": (fwd_ms + bwd_ms) / n_steps, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": label, "lattice": [prob.nx, prob.ny, prob.nz], "nodes": nodes,
+                      "checkpoint_every": every, "parallelism": f"replicas x{ws}"},
+           "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+           "forward_glups": aggregate_glups(nodes, n_steps, ws, fwd_ms / 1e3),
+           "adjoint_workspace_bytes": adj.nbytes, "context_workspace_bytes": int(sim.workspace.numel()),
+           "gradients": {"dL_dG": dG, "dL_dg": list(map(float, dg))},
+           "gradient_check": "tests/test_gpu_adjoint.py: FP64 central differences of the oracle, 32^3, 100 steps",
+           "gpu_launches": launches}
+    adj.close()
+    sim.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def run_reference(args, prob, label, ws, rank):
     """Reference arm: the FP64 oracle (plain C, OpenMP) on the host cores; each step one full time step."""
     if rank != 0:
@@ -405,6 +462,13 @@ def main():
 
     ws, rank, local = dist_setup()
     prob, label = workload(args.workload)
+    if args.workload == "adjoint64" and args.impl == "ours":
+        run_adjoint(args, prob, label, ws, rank, local)
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return
     if args.workload == "batch48":
         if args.impl == "reference":
             run_reference_batch(args, prob, label, rank)

@@ -206,6 +206,35 @@ scbb_status scbb_batch_create(scbb_ctx* const* ctxs, int n, void* cuda_stream, s
 scbb_status scbb_batch_step(scbb_batch* batch, long long n);
 void scbb_batch_destroy(scbb_batch* batch);
 
+/* Reverse-mode derivative of the fluid (not in the paper, which has no adjoint).  The gradient of a loss of
+ * the densities after n steps, L(rho^A(T), rho^B(T)), with respect to the Shan-Chen coupling G (Eq. 13), the
+ * body acceleration g and the initial densities rho^c(0), by hand-written adjoint kernels of the step:
+ * BGK collision with the velocity-shift forcing (Eq. 1-5), the pseudo-potential force (Eq. 13) whose
+ * stencil the adjoint applies transposed, and streaming (pull; the adjoint pushes).
+ *   Supported contexts: periodic boxes (walls = 0) without meshes, FP32 storage; otherwise
+ *   SCBB_E_UNSUPPORTED at creation.
+ *   scbb_adjoint_workspace_bytes(ctx, n, K): device bytes of the adjoint's workspace for n steps with a
+ *     population checkpoint every K steps: ceil(n/K) checkpoints, K + 1 lattices and K density fields of one
+ *     segment, two adjoint lattices and 13 + 2 floats per node of scratch.  0 for bad arguments.
+ *   scbb_adjoint_create(ctx, n, K, dev_workspace, out): dev_workspace caller-owned, at least that many
+ *     bytes, 256-byte aligned; the adjoint keeps ctx and runs on its stream.
+ *   scbb_adjoint_forward(a): runs the n steps of ctx from its current state (set by scbb_set_density, an
+ *     equilibrium), storing a checkpoint at steps 0, K, 2K, ...; ctx ends at step n as scbb_step(ctx, n)
+ *     leaves it.
+ *   scbb_adjoint_backward(a, dL_drhoA, dL_drhoB, dL_dG, dL_dg, dL_drho0A, dL_drho0B): host arrays of N
+ *     doubles in, the adjoint of the final densities; out: host dL_dG (1 double), dL_dg (3 doubles) and
+ *     dL_drho0A, dL_drho0B (N doubles each; either may be NULL).  Recomputes each segment of K steps from
+ *     its checkpoint, then steps the adjoint backwards through it.  Synchronous.  SCBB_E_STATE before
+ *     scbb_adjoint_forward.  All arithmetic is FP32 except the FP64 sums of the parameter gradients. */
+typedef struct scbb_adjoint scbb_adjoint;
+size_t scbb_adjoint_workspace_bytes(const scbb_ctx* ctx, long long n_steps, int checkpoint_every);
+scbb_status scbb_adjoint_create(scbb_ctx* ctx, long long n_steps, int checkpoint_every, void* dev_workspace,
+                                scbb_adjoint** out);
+scbb_status scbb_adjoint_forward(scbb_adjoint* a);
+scbb_status scbb_adjoint_backward(scbb_adjoint* a, const double* dL_drhoA, const double* dL_drhoB, double* dL_dG,
+                                  double* dL_dg, double* dL_drho0A, double* dL_drho0B);
+void scbb_adjoint_destroy(scbb_adjoint* a);
+
 const char* scbb_last_error(const scbb_ctx* ctx);
 
 /* Releases host-side state.  The workspace stays owned by the caller. */

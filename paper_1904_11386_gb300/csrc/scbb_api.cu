@@ -6,9 +6,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
+#include "adjoint.cuh"
 #include "scbb_internal.cuh"
 
 using namespace scbb;
@@ -922,6 +924,143 @@ void scbb_batch_destroy(scbb_batch* b) {
         if (e) cudaEventDestroy(e);
     delete b;
 }
+
+// ------------------------------------------------------------------------------------------------------
+// Adjoint of the fluid: checkpoints every K steps, recomputation of each segment, adjoint steps backwards.
+// ------------------------------------------------------------------------------------------------------
+
+struct scbb_adjoint {
+    scbb_ctx* c = nullptr;
+    long long n = 0;
+    int K = 0, nseg = 0;
+    float* ckpt = nullptr;      // nseg lattices: the state read by steps 0, K, 2K, ...
+    float* L = nullptr;         // K + 1 lattices of the segment being recomputed
+    float* R = nullptr;         // K density fields (2 N) of that segment, written by the forward kernel
+    float* lam[2] = {nullptr, nullptr};
+    float* scr = nullptr;       // ADJ_SCR N
+    float* g = nullptr;         // 2 N: adjoint of the final densities, then dL/drho0
+    double* part = nullptr;     // ADJ_PARAMS x adj_blocks
+    int blocks = 0;
+    bool forward_done = false;
+};
+
+namespace {
+
+bool adjoint_supported(const scbb_ctx* c) {
+    return c && !c->lp.walls && c->d.NV == 0 && c->d.NM == 0 && c->lp.store == 0;
+}
+
+// Carves the adjoint's buffers (base == nullptr: measures only).
+size_t adjoint_layout(const scbb_ctx* c, long long n, int K, void* base, scbb_adjoint* a) {
+    Carve cv(base);
+    const size_t N = c->lp.N, lat = (size_t)2 * Q * N;
+    const int nseg = (int)((n + K - 1) / K);
+    float* ckpt = cv.take<float>(lat * nseg);
+    float* L = cv.take<float>(lat * (K + 1));
+    float* R = cv.take<float>((size_t)2 * N * K);
+    float* l0 = cv.take<float>(lat);
+    float* l1 = cv.take<float>(lat);
+    float* scr = cv.take<float>((size_t)ADJ_SCR * N);
+    float* g = cv.take<float>(2 * N);
+    double* part = cv.take<double>((size_t)ADJ_PARAMS * adj_blocks(c->lp));
+    if (a) {
+        a->ckpt = ckpt; a->L = L; a->R = R; a->lam[0] = l0; a->lam[1] = l1;
+        a->scr = scr; a->g = g; a->part = part; a->nseg = nseg; a->blocks = adj_blocks(c->lp);
+    }
+    return cv.off + ALIGN;
+}
+
+}  // namespace
+
+size_t scbb_adjoint_workspace_bytes(const scbb_ctx* c, long long n, int K) {
+    if (!adjoint_supported(c) || n < 1 || K < 1) return 0;
+    return adjoint_layout(c, n, K, nullptr, nullptr);
+}
+
+scbb_status scbb_adjoint_create(scbb_ctx* c, long long n, int K, void* ws, scbb_adjoint** out) {
+    if (!out) return SCBB_E_INVAL;
+    *out = nullptr;
+    if (!c || !ws || n < 1 || K < 1 || ((uintptr_t)ws % ALIGN)) return SCBB_E_INVAL;
+    if (c->broken) return SCBB_E_STATE;
+    if (!adjoint_supported(c))
+        return fail(c, SCBB_E_UNSUPPORTED, "adjoint: periodic boxes without meshes and FP32 storage only");
+    scbb_adjoint* a = new scbb_adjoint;
+    a->c = c;
+    a->n = n;
+    a->K = K;
+    adjoint_layout(c, n, K, ws, a);
+    *out = a;
+    return SCBB_OK;
+}
+
+scbb_status scbb_adjoint_forward(scbb_adjoint* a) {
+    if (!a) return SCBB_E_INVAL;
+    scbb_ctx* c = a->c;
+    if (c->broken) return SCBB_E_STATE;
+    const size_t lat_bytes = sizeof(float) * 2 * Q * c->lp.N;
+    for (int s = 0; s < a->nseg; s++) {
+        CUDA_TRY(c, cudaMemcpyAsync(a->ckpt + (size_t)s * 2 * Q * c->lp.N, c->d.S[c->cur], lat_bytes,
+                                    cudaMemcpyDeviceToDevice, c->st));
+        const long long len = std::min<long long>(a->K, a->n - (long long)s * a->K);
+        const scbb_status r = scbb_step(c, len);
+        if (r != SCBB_OK) return r;
+    }
+    a->forward_done = true;
+    return SCBB_OK;
+}
+
+scbb_status scbb_adjoint_backward(scbb_adjoint* a, const double* gA, const double* gB, double* dG, double* dg,
+                                  double* drA, double* drB) {
+    if (!a || !gA || !gB || !dG || !dg) return SCBB_E_INVAL;
+    scbb_ctx* c = a->c;
+    if (c->broken) return SCBB_E_STATE;
+    if (!a->forward_done) return fail(c, SCBB_E_STATE, "adjoint: scbb_adjoint_forward has not run");
+    const size_t N = c->lp.N, lat = (size_t)2 * Q * N;
+    std::vector<float> h(2 * N);
+    for (size_t q = 0; q < N; q++) {
+        h[q] = (float)gA[q];
+        h[N + q] = (float)gB[q];
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(a->g, h.data(), sizeof(float) * 2 * N, cudaMemcpyHostToDevice, c->st));
+    CUDA_TRY(c, cudaMemsetAsync(a->part, 0, sizeof(double) * ADJ_PARAMS * a->blocks, c->st));
+    launch_adj_final(c->lp, a->g, a->g + N, a->lam[0], c->st);
+    c->launches++;
+    int cur = 0;
+    for (int s = a->nseg - 1; s >= 0; s--) {
+        const int len = (int)std::min<long long>(a->K, a->n - (long long)s * a->K);
+        CUDA_TRY(c, cudaMemcpyAsync(a->L, a->ckpt + (size_t)s * lat, sizeof(float) * lat, cudaMemcpyDeviceToDevice,
+                                    c->st));
+        // recompute the segment with the forward kernel, keeping every lattice and density field
+        for (int k = 0; k < len; k++)
+            launch_bulk(c->lp, a->L + (size_t)k * lat, a->L + (size_t)(k + 1) * lat, a->R + (size_t)k * 2 * N,
+                        c->d.ghost, nullptr, nullptr, nullptr, c->d.err, 0, c->st);
+        for (int k = len - 1; k >= 0; k--) {
+            launch_adj_step(c->lp, a->L + (size_t)k * lat, a->R + (size_t)k * 2 * N, a->lam[cur], a->lam[1 - cur],
+                            a->scr, a->part, c->st);
+            cur ^= 1;
+        }
+        c->launches += 3 * len;
+        CUDA_TRY(c, cudaGetLastError());
+    }
+    launch_adj_initial(c->lp, a->ckpt, a->lam[cur], a->g, c->st);
+    c->launches++;
+    std::vector<double> part((size_t)ADJ_PARAMS * a->blocks);
+    CUDA_TRY(c, cudaMemcpyAsync(part.data(), a->part, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaMemcpyAsync(h.data(), a->g, sizeof(float) * 2 * N, cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    double acc[ADJ_PARAMS] = {0, 0, 0, 0};
+    for (int b = 0; b < a->blocks; b++)
+        for (int k = 0; k < ADJ_PARAMS; k++) acc[k] += part[(size_t)b * ADJ_PARAMS + k];
+    *dG = acc[0];
+    for (int k = 0; k < 3; k++) dg[k] = acc[1 + k];
+    for (size_t q = 0; q < N; q++) {
+        if (drA) drA[q] = h[q];
+        if (drB) drB[q] = h[N + q];
+    }
+    return SCBB_OK;
+}
+
+void scbb_adjoint_destroy(scbb_adjoint* a) { delete a; }
 
 const char* scbb_last_error(const scbb_ctx* c) {
     if (!c) return "null context";

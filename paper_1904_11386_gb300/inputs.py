@@ -219,6 +219,15 @@ def cfg_droplet256(n_caps: int = 300, coupling: int = 0, n: int = 256, R_drop: f
                    steps=20000)
 
 
+def cfg_adjoint(n: int = 32, R_drop: float = 8.0, seed: int = 9, G: float = 3.6) -> Problem:
+    """Periodic n^3 two-component box with a B-rich droplet of radius R_drop slightly off the box centre
+    (exponential psi, no capsules): the fluid whose adjoint is checked against finite differences, and, at
+    64^3, the differentiation workload of the benchmark."""
+    c = n / 2.0
+    return Problem(name=f"adjoint{n}", nx=n, ny=n, nz=n, walls=0, psi_kind=0, G=G, coupling=1,
+                   droplet=(c + 0.3, c - 0.2, c + 0.1, R_drop), capsules=[], noise=1e-3, seed=seed, steps=2000)
+
+
 def cfg_batch48(n_boxes: int = 48, seed: int = 3) -> List[Problem]:
     """A sweep of independent boxes of uneven size: cubes with edges drawn from PCG64(seed) among the multiples
     of 4 in [40, 72], walls at both z ends, a flat interface at mid height, one s = 3 capsule of radius 6 (642

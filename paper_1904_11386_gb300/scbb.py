@@ -21,7 +21,8 @@ EXPORTS = ["scbb_workspace_bytes", "scbb_create", "scbb_set_density", "scbb_step
            "scbb_get_fields", "scbb_get_populations", "scbb_get_vertices", "scbb_get_diag", "scbb_get_owner",
            "scbb_launch_count", "scbb_enable_timing", "scbb_kernel_time", "scbb_phase_times",
            "scbb_population_moments_noalloc", "scbb_batch_create", "scbb_batch_step", "scbb_batch_destroy",
-           "scbb_last_error", "scbb_destroy"]
+           "scbb_adjoint_workspace_bytes", "scbb_adjoint_create", "scbb_adjoint_forward", "scbb_adjoint_backward",
+           "scbb_adjoint_destroy", "scbb_last_error", "scbb_destroy"]
 
 
 class scbb_lattice(C.Structure):
@@ -98,6 +99,16 @@ def load(path: str = LIB_PATH):
     L.scbb_batch_step.argtypes = [vp, C.c_longlong]
     L.scbb_batch_destroy.restype = None
     L.scbb_batch_destroy.argtypes = [vp]
+    L.scbb_adjoint_workspace_bytes.restype = C.c_size_t
+    L.scbb_adjoint_workspace_bytes.argtypes = [vp, C.c_longlong, C.c_int]
+    L.scbb_adjoint_create.restype = C.c_int
+    L.scbb_adjoint_create.argtypes = [vp, C.c_longlong, C.c_int, vp, C.POINTER(vp)]
+    L.scbb_adjoint_forward.restype = C.c_int
+    L.scbb_adjoint_forward.argtypes = [vp]
+    L.scbb_adjoint_backward.restype = C.c_int
+    L.scbb_adjoint_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.scbb_adjoint_destroy.restype = None
+    L.scbb_adjoint_destroy.argtypes = [vp]
     _lib = L
     return L
 
@@ -317,3 +328,106 @@ class Batch:
         except Exception:
             pass
 
+
+
+class Adjoint:
+    """Reverse-mode derivative of n fluid steps of a Sim (scbb_adjoint_*): a torch-owned workspace holding a
+    population checkpoint every K steps, the segment being recomputed and the adjoint lattices."""
+
+    def __init__(self, sim, n_steps, checkpoint_every):
+        import torch
+
+        self.sim, self.L = sim, sim.L
+        self.n, self.K = int(n_steps), int(checkpoint_every)
+        nbytes = self.L.scbb_adjoint_workspace_bytes(sim.h, self.n, self.K)
+        if nbytes == 0:
+            raise ScbbError("scbb_adjoint_workspace_bytes: unsupported context or arguments "
+                            "(periodic boxes without meshes, FP32 storage)")
+        self.nbytes = int(nbytes)
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=sim.workspace.device)
+        h = C.c_void_p()
+        sim._check(self.L.scbb_adjoint_create(sim.h, self.n, self.K, C.c_void_p(self.workspace.data_ptr()),
+                                              C.byref(h)), "scbb_adjoint_create")
+        self.h = h
+
+    @classmethod
+    def scbb_adjoint_create(cls, sim, n_steps, checkpoint_every):
+        return cls(sim, n_steps, checkpoint_every)
+
+    def scbb_adjoint_forward(self):
+        self.sim._check(self.L.scbb_adjoint_forward(self.h), "scbb_adjoint_forward")
+
+    def scbb_adjoint_backward(self, dL_drhoA, dL_drhoB):
+        """Adjoint of the final densities in (arrays of N); returns (dL/dG, dL/dg[3], dL/drho0^A, dL/drho0^B)
+        with the density gradients shaped (nz, ny, nx)."""
+        p = self.sim.prob
+        a = np.ascontiguousarray(dL_drhoA, np.float64).ravel()
+        b = np.ascontiguousarray(dL_drhoB, np.float64).ravel()
+        dG, dg = np.zeros(1), np.zeros(3)
+        ra, rb = np.empty(p.n_nodes), np.empty(p.n_nodes)
+        self.sim._check(self.L.scbb_adjoint_backward(self.h, _p(a), _p(b), _p(dG), _p(dg), _p(ra), _p(rb)),
+                        "scbb_adjoint_backward")
+        s = (p.nz, p.ny, p.nx)
+        return float(dG[0]), dg, ra.reshape(s), rb.reshape(s)
+
+    def scbb_adjoint_destroy(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.scbb_adjoint_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fluid_rollout(prob, n_steps, checkpoint_every, G, g, rhoA0, rhoB0):
+    """The densities after n_steps of the fluid of `prob` (periodic, no meshes) as a differentiable torch
+    function of the Shan-Chen coupling G (0-d tensor), the body acceleration g (3 values) and the initial
+    densities rhoA0, rhoB0 (float64 CPU tensors shaped (nz, ny, nx)): returns (rhoA(T), rhoB(T)).  The
+    forward pass runs the CUDA step with a population checkpoint every checkpoint_every steps; the backward
+    pass runs the adjoint kernels (scbb_adjoint_backward), recomputing each segment from its checkpoint."""
+    return _FluidRollout.apply(prob, int(n_steps), int(checkpoint_every), G, g, rhoA0, rhoB0)
+
+
+def _rollout_function():
+    import dataclasses
+
+    import torch
+
+    class FluidRollout(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, prob, n, K, G, g, rhoA0, rhoB0):
+            pr = dataclasses.replace(prob, G=float(G), g=tuple(float(v) for v in g))
+            sim = Sim(pr, rhoA0.detach().cpu().numpy(), rhoB0.detach().cpu().numpy())
+            adj = Adjoint(sim, n, K)
+            adj.scbb_adjoint_forward()
+            a, b, _ = sim.scbb_get_fields()
+            ctx.sim, ctx.adj = sim, adj
+            return torch.from_numpy(a.copy()), torch.from_numpy(b.copy())
+
+        @staticmethod
+        def backward(ctx, ga, gb):
+            dG, dg, ra, rb = ctx.adj.scbb_adjoint_backward(ga.detach().cpu().numpy(), gb.detach().cpu().numpy())
+            ctx.adj.close()
+            ctx.sim.close()
+            return (None, None, None, torch.tensor(dG, dtype=torch.float64), torch.from_numpy(dg),
+                    torch.from_numpy(ra), torch.from_numpy(rb))
+
+    return FluidRollout
+
+
+class _Lazy:
+    fn = None
+
+    def apply(self, *args):
+        if _Lazy.fn is None:
+            _Lazy.fn = _rollout_function()
+        return _Lazy.fn.apply(*args)
+
+
+_FluidRollout = _Lazy()

@@ -38,9 +38,10 @@ def test_binding_names_match_header():
 
     assert sorted(scbb.EXPORTS) == _declared()
     for n in _declared():
-        if n in ("scbb_create", "scbb_workspace_bytes", "scbb_destroy", "scbb_last_error"):
+        if n in ("scbb_create", "scbb_workspace_bytes", "scbb_destroy", "scbb_last_error",
+                 "scbb_adjoint_workspace_bytes"):
             continue
-        assert hasattr(scbb.Sim, n) or hasattr(scbb.Batch, n) or hasattr(scbb, n), n
+        assert hasattr(scbb.Sim, n) or hasattr(scbb.Batch, n) or hasattr(scbb.Adjoint, n) or hasattr(scbb, n), n
 
 
 def test_workspace_sizing_and_argument_checks():

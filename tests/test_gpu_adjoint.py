@@ -1,0 +1,135 @@
+"""The adjoint of the periodic two-component fluid (scbb_adjoint_*) against FP64 central finite differences
+of the oracle.
+
+Loss: L = sum_x z rho^A(x, T) + 0.5 sum_x x rho^B(x, T) after T steps of a droplet in a periodic box, a
+weighted centre of mass of each component.  Its derivatives with respect to the Shan-Chen coupling G, the
+body acceleration g and the initial densities (along a seeded direction) come from the FP32 adjoint kernels;
+the oracle differences its own FP64 runs with steps of 1e-4 (G), 1e-5 (g) and 1e-5 (densities).  The
+agreement asked of the adjoint is 1e-3 relative; the FP32 forward trajectory the adjoint follows differs from
+the FP64 one by about 1e-6."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1904_11386_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+T = 100
+RTOL = 1e-3
+
+
+def _weights(p):
+    z, y, x = np.meshgrid(np.arange(p.nz), np.arange(p.ny), np.arange(p.nx), indexing="ij")
+    return z.astype(np.float64), 0.5 * x.astype(np.float64)
+
+
+def _oracle_loss(p, rhoA0, rhoB0, steps):
+    o = O.OracleSim(p, rhoA0, rhoB0)
+    o.step(steps)
+    a, b, _ = o.fields()
+    wA, wB = _weights(p)
+    return float((wA * a).sum() + (wB * b).sum())
+
+
+def _gpu_grads(p, rhoA0, rhoB0, steps, K):
+    from paper_1904_11386_gb300 import scbb
+
+    sim = scbb.Sim(p, rhoA0, rhoB0)
+    adj = scbb.Adjoint(sim, steps, K)
+    adj.scbb_adjoint_forward()
+    wA, wB = _weights(p)
+    out = adj.scbb_adjoint_backward(wA, wB)
+    a, b, _ = sim.scbb_get_fields()
+    adj.close()
+    sim.close()
+    return out, float((wA * a).sum() + (wB * b).sum())
+
+
+@pytest.fixture(scope="module")
+def case():
+    p = inputs.cfg_adjoint(n=32, R_drop=8.0)
+    rhoA0, rhoB0 = p.initial_density()
+    (dG, dg, drA, drB), L = _gpu_grads(p, rhoA0, rhoB0, T, 16)      # 100 = 6 x 16 + 4: a ragged last segment
+    return p, rhoA0, rhoB0, dG, dg, drA, drB, L
+
+
+def test_loss_matches_oracle(case):
+    p, rhoA0, rhoB0, *_, L = case
+    assert abs(L - _oracle_loss(p, rhoA0, rhoB0, T)) < 1e-5 * abs(L)
+
+
+def test_dG_against_fd(case):
+    import dataclasses
+
+    p, rhoA0, rhoB0, dG, *_ = case
+    h = 1e-4
+    fd = (_oracle_loss(dataclasses.replace(p, G=p.G + h), rhoA0, rhoB0, T) -
+          _oracle_loss(dataclasses.replace(p, G=p.G - h), rhoA0, rhoB0, T)) / (2 * h)
+    assert abs(dG - fd) < RTOL * abs(fd), (dG, fd)
+
+
+@pytest.mark.parametrize("k", [0, 2])
+def test_dg_against_fd(case, k):
+    import dataclasses
+
+    p, rhoA0, rhoB0, _, dg, *_ = case
+    h = 1e-5
+    e = np.zeros(3)
+    e[k] = h
+    fd = (_oracle_loss(dataclasses.replace(p, g=tuple(e)), rhoA0, rhoB0, T) -
+          _oracle_loss(dataclasses.replace(p, g=tuple(-e)), rhoA0, rhoB0, T)) / (2 * h)
+    assert abs(dg[k] - fd) < RTOL * abs(fd), (k, dg[k], fd)
+
+
+def test_drho0_against_fd(case):
+    """Directional derivative along a seeded direction of both initial density fields."""
+    p, rhoA0, rhoB0, _, _, drA, drB, _ = case
+    rng = np.random.Generator(np.random.PCG64(21))
+    vA, vB = rng.standard_normal(rhoA0.shape), rng.standard_normal(rhoB0.shape)
+    h = 1e-5
+    fd = (_oracle_loss(p, rhoA0 + h * vA, rhoB0 + h * vB, T) -
+          _oracle_loss(p, rhoA0 - h * vA, rhoB0 - h * vB, T)) / (2 * h)
+    ad = float((drA * vA).sum() + (drB * vB).sum())
+    assert abs(ad - fd) < RTOL * abs(fd), (ad, fd)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient(case):
+    """Recomputation from checkpoints is exact: one segment of T steps and segments of 7 steps give the same
+    gradients bit for bit (the kernels are deterministic)."""
+    p, rhoA0, rhoB0, dG, dg, drA, drB, _ = case
+    for K in (T, 7):
+        (dG2, dg2, drA2, drB2), _ = _gpu_grads(p, rhoA0, rhoB0, T, K)
+        assert dG2 == dG and np.array_equal(dg2, dg)
+        assert np.array_equal(drA2, drA) and np.array_equal(drB2, drB)
+
+
+def test_autograd_function(case):
+    """fluid_rollout as a torch.autograd.Function: the gradients of the same loss through torch equal the
+    direct adjoint call."""
+    import torch
+
+    from paper_1904_11386_gb300 import scbb
+
+    p, rhoA0, rhoB0, dG, dg, drA, drB, _ = case
+    G = torch.tensor(p.G, dtype=torch.float64, requires_grad=True)
+    g = torch.zeros(3, dtype=torch.float64, requires_grad=True)
+    a0 = torch.tensor(rhoA0, requires_grad=True)
+    b0 = torch.tensor(rhoB0, requires_grad=True)
+    a, b = scbb.fluid_rollout(p, T, 16, G, g, a0, b0)
+    wA, wB = (torch.from_numpy(w) for w in _weights(p))
+    loss = (wA * a).sum() + (wB * b).sum()
+    loss.backward()
+    assert G.grad.item() == dG
+    assert np.array_equal(g.grad.numpy(), dg)
+    assert np.array_equal(a0.grad.numpy(), drA) and np.array_equal(b0.grad.numpy(), drB)
+
+
+def test_unsupported_contexts_are_rejected():
+    from paper_1904_11386_gb300 import scbb
+
+    p = inputs.small_problem(n=16, walls=1, coupling=1, capsule=False)
+    sim = scbb.Sim(p)
+    with pytest.raises(scbb.ScbbError):
+        scbb.Adjoint(sim, 10, 5)
+    sim.close()
