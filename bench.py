@@ -382,6 +382,7 @@ def run_adjoint(args, prob, label, ws, rank, local, n_steps=2000, every=100):
     z, _, x = np.meshgrid(np.arange(prob.nz), np.arange(prob.ny), np.arange(prob.nx), indexing="ij")
     wA, wB = z.astype(np.float64), 0.5 * x.astype(np.float64)
     sim = scbb.Sim(prob, rhoA0, rhoB0, device=f"cuda:{local}")
+    shape = sim.scbb_autotune()              # a single 64^3 box fills the GPU only with short z-segments
     adj = scbb.Adjoint(sim, n_steps, every)
     st = sim.stream
     times = []
@@ -407,7 +408,7 @@ def run_adjoint(args, prob, label, ws, rank, local, n_steps=2000, every=100):
            "ms_per_step": (fwd_ms + bwd_ms) / n_steps, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": label, "lattice": [prob.nx, prob.ny, prob.nz], "nodes": nodes,
-                      "checkpoint_every": every, "parallelism": f"replicas x{ws}"},
+                      "checkpoint_every": every, "bulk_shape": shape, "parallelism": f"replicas x{ws}"},
            "forward_ms": fwd_ms, "backward_ms": bwd_ms,
            "forward_glups": aggregate_glups(nodes, n_steps, ws, fwd_ms / 1e3),
            "adjoint_workspace_bytes": adj.nbytes, "context_workspace_bytes": int(sim.workspace.numel()),

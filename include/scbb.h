@@ -191,6 +191,16 @@ scbb_status scbb_phase_times(scbb_ctx* ctx, double* ms, long long* steps);
 scbb_status scbb_population_moments_noalloc(const float* dev_f, int nx, int ny, int nz, int walls, double* out5,
                                             void* cuda_stream);
 
+/* Autotuner of the bulk kernel's block shape (not in the paper).  The row-vectorised bulk kernel can run with
+ * 512 threads per CTA (one CTA per SM) or 256 (two per SM), and with z-segments of at least 6 or at least 3
+ * planes; which is fastest depends on the box.  scbb_autotune times the bulk kernel of the context's current
+ * state in every shape that fits the box (one untimed launch, then reps launches between CUDA events, into the
+ * spare lattice, which the next step rewrites) and keeps the fastest for the context's later steps.  The
+ * results of a step do not depend on the shape.  chosen (may be NULL): the shape kept, 0 .. 3, or -1 when the
+ * context runs the general bulk kernel (nx not a multiple of 4), which has no shapes.  Synchronous; call it
+ * between steps, not while a batch holds the context. */
+scbb_status scbb_autotune(scbb_ctx* ctx, int reps, int* chosen);
+
 /* Batches (not in the paper): step several independent contexts together, for example a sweep of boxes of
  * different sizes and parameters.  ctxs: n distinct contexts, kept alive by the caller until
  * scbb_batch_destroy; each must run on a stream of its own (not the legacy default).  cuda_stream: the

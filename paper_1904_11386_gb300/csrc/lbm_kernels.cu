@@ -880,9 +880,10 @@ static void bulk_geometry(const LbmParams& p, dim3& grid, int& threads) {
 }
 
 // Row-vectorised geometry: TY tile rows (+2 halo rows) per CTA of nthreads threads, z split into
-// segments so that the grid fills the 152 SMs (cps CTAs resident per SM) in as few waves as possible.
-static bool bulk4_geometry(const LbmParams& p, int nthreads, int cps, LbmParams& q, dim3& grid, int& threads,
-                           int& TY, size_t& smem) {
+// segments of at least min_planes planes so that the grid fills the 152 SMs (cps CTAs resident per SM) in as
+// few waves as possible.
+static bool bulk4_geometry(const LbmParams& p, int nthreads, int cps, int min_planes, LbmParams& q, dim3& grid,
+                           int& threads, int& TY, size_t& smem) {
     TY = bulk4_rows(p, nthreads);
     if (TY <= 0) return false;
     const int NQ = p.nx / 4;
@@ -902,7 +903,7 @@ static bool bulk4_geometry(const LbmParams& p, int nthreads, int cps, LbmParams&
     for (int w = 1; w <= 4; w++) {
         int ns = (slots * w) / cols;
         if (ns < 1) ns = 1;
-        if (ns > nzf / 6) ns = nzf / 6 > 0 ? nzf / 6 : 1;
+        if (ns > nzf / min_planes) ns = nzf / min_planes > 0 ? nzf / min_planes : 1;
         const int nb = cols * ns;
         const int waves = (nb + slots - 1) / slots;
         const double eff = (double)nb / ((double)slots * waves) - 0.02 * waves;
@@ -913,15 +914,6 @@ static bool bulk4_geometry(const LbmParams& p, int nthreads, int cps, LbmParams&
     grid = dim3(cols, nseg, 1);
     smem = (size_t)(4 * 2 + 2 * 5) * (TY + 2) * p.nx * sizeof(float);
     return true;
-}
-
-static int b4_config() {
-    static int v = -1;
-    if (v < 0) {
-        const char* e = getenv("SCBB_B4_CFG");
-        v = e ? atoi(e) : 0;
-    }
-    return v;
 }
 
 template <bool TAU1, int MODE, int NT, int MINB, typename T>
@@ -950,14 +942,14 @@ static void launch_b4(const LbmParams& q, dim3 grid, int threads, size_t smem, i
 }
 
 template <int NT, int MINB>
-static bool try_b4(const LbmParams& p, const float* S, float* D, float* rho, const float* ghost, const float* Fibm,
-                   const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st,
+static bool try_b4(const LbmParams& p, int min_planes, const float* S, float* D, float* rho, const float* ghost,
+                   const float* Fibm, const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st,
                    int* blocks) {
     LbmParams q;
     dim3 grid;
     int threads, TY;
     size_t smem;
-    if (!bulk4_geometry(p, NT, MINB, q, grid, threads, TY, smem)) return false;
+    if (!bulk4_geometry(p, NT, MINB, min_planes, q, grid, threads, TY, smem)) return false;
     if (blocks) {
         *blocks = (int)(grid.x * grid.y);
         return true;
@@ -978,8 +970,12 @@ static bool try_b4(const LbmParams& p, const float* S, float* D, float* rho, con
 static bool dispatch_b4(const LbmParams& p, const float* S, float* D, float* rho, const float* ghost,
                         const float* Fibm, const uint32_t* mask, float* u, int* err, int mode,
                         cudaStream_t st, int* blocks) {
-    if (b4_config() == 2) return try_b4<256, 2>(p, S, D, rho, ghost, Fibm, mask, u, err, mode, st, blocks);
-    return try_b4<512, 1>(p, S, D, rho, ghost, Fibm, mask, u, err, mode, st, blocks);
+    switch (p.b4cfg) {
+        case 1: return try_b4<256, 2>(p, 6, S, D, rho, ghost, Fibm, mask, u, err, mode, st, blocks);
+        case 2: return try_b4<512, 1>(p, 3, S, D, rho, ghost, Fibm, mask, u, err, mode, st, blocks);
+        case 3: return try_b4<256, 2>(p, 3, S, D, rho, ghost, Fibm, mask, u, err, mode, st, blocks);
+        default: return try_b4<512, 1>(p, 6, S, D, rho, ghost, Fibm, mask, u, err, mode, st, blocks);
+    }
 }
 
 bool bulk_vectorised(const LbmParams& p) {

@@ -793,6 +793,51 @@ scbb_status scbb_get_owner(scbb_ctx* c, unsigned short* owner, int* n_boundary, 
 
 long long scbb_launch_count(const scbb_ctx* c) { return c ? c->launches : 0; }
 
+scbb_status scbb_autotune(scbb_ctx* c, int reps, int* chosen) {
+    if (!c || reps < 1) return SCBB_E_INVAL;
+    if (c->broken) return SCBB_E_STATE;
+    if (chosen) *chosen = -1;
+    LbmParams q = c->lp;
+    q.b4cfg = 0;
+    if (!bulk_vectorised(q)) return SCBB_OK;      // the general bulk kernel has no shapes to choose from
+    const int mode = (c->fl.coupling == 1 && c->d.NV > 0) ? 1 : 0;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(c, cudaEventCreate(&e0));
+    CUDA_TRY(c, cudaEventCreate(&e1));
+    float best = 0.f;
+    int best_k = -1;
+    // Each shape runs the bulk kernel from the current state into the spare lattice (scratch between
+    // steps; the next step rewrites it and the density field), once untimed, then reps times between events.
+    for (int k = 0; k < B4_CONFIGS; k++) {
+        q.b4cfg = k;
+        if (!bulk_vectorised(q)) continue;
+        for (int r = 0; r <= reps; r++) {
+            if (r == 1) CUDA_TRY(c, cudaEventRecord(e0, c->st));
+            launch_bulk(q, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.rho, c->d.ghost, c->d.Fibm, c->d.mask, c->d.u,
+                        c->d.err, mode, c->st);
+            c->launches++;
+        }
+        CUDA_TRY(c, cudaEventRecord(e1, c->st));
+        CUDA_TRY(c, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CUDA_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
+        if (best_k < 0 || ms < best) {
+            best = ms;
+            best_k = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->lp.b4cfg = best_k;
+    // the captured step pairs hold the old shape
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->gkey = -1;
+    c->eager_steps = 0;
+    if (chosen) *chosen = best_k;
+    return SCBB_OK;
+}
+
 scbb_status scbb_enable_timing(scbb_ctx* c, int on) {
     if (!c || on < 0 || on > 2) return SCBB_E_INVAL;
     if (on && c->ev.empty()) {

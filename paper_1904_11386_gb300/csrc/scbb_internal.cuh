@@ -51,7 +51,12 @@ struct LbmParams {
     float ulo[3], uhi[3];
     int store;              // population storage: 0 FP32, 1 FP16 (__half), 2 BF16 (__nv_bfloat16); the S
                             // pointers point to that type
+    int b4cfg;              // shape of the row-vectorised bulk kernel, 0 .. B4_CONFIGS - 1 (scbb_autotune)
 };
+
+// Shapes of the row-vectorised bulk kernel: (threads per CTA, CTAs per SM, fewest planes per z-segment) =
+// 0: (512, 1, 6), 1: (256, 2, 6), 2: (512, 1, 3), 3: (256, 2, 3).
+constexpr int B4_CONFIGS = 4;
 
 // Calls f with a null pointer of the population storage type of `store` (float, __half or __nv_bfloat16), so a
 // launcher instantiates the kernel for that type: with_storage(p.store, [&](auto* tag) { using T = ...; }).

@@ -19,7 +19,7 @@ STATUS = {0: "SCBB_OK", 1: "SCBB_E_INVAL", 2: "SCBB_E_CUDA", 3: "SCBB_E_NOMEM", 
 
 EXPORTS = ["scbb_workspace_bytes", "scbb_create", "scbb_set_density", "scbb_step", "scbb_sync",
            "scbb_get_fields", "scbb_get_populations", "scbb_get_vertices", "scbb_get_diag", "scbb_get_owner",
-           "scbb_launch_count", "scbb_enable_timing", "scbb_kernel_time", "scbb_phase_times",
+           "scbb_launch_count", "scbb_enable_timing", "scbb_kernel_time", "scbb_phase_times", "scbb_autotune",
            "scbb_population_moments_noalloc", "scbb_batch_create", "scbb_batch_step", "scbb_batch_destroy",
            "scbb_adjoint_workspace_bytes", "scbb_adjoint_create", "scbb_adjoint_forward", "scbb_adjoint_backward",
            "scbb_adjoint_destroy", "scbb_last_error", "scbb_destroy"]
@@ -85,6 +85,8 @@ def load(path: str = LIB_PATH):
     L.scbb_enable_timing.argtypes = [vp, C.c_int]
     L.scbb_kernel_time.restype = C.c_int
     L.scbb_kernel_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+    L.scbb_autotune.restype = C.c_int
+    L.scbb_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
     L.scbb_phase_times.restype = C.c_int
     L.scbb_phase_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
     L.scbb_population_moments_noalloc.restype = C.c_int
@@ -267,6 +269,13 @@ class Sim:
         self._check(self.L.scbb_kernel_time(self.h, C.byref(ms), C.byref(n)), "scbb_kernel_time")
         return ms.value, n.value
 
+    def scbb_autotune(self, reps=5):
+        """Times the bulk kernel in each block shape that fits the box and keeps the fastest; returns the shape
+        kept (0..3), or -1 for boxes on the general bulk kernel."""
+        k = C.c_int(-1)
+        self._check(self.L.scbb_autotune(self.h, int(reps), C.byref(k)), "scbb_autotune")
+        return k.value
+
     PHASES = ("ibm_spread", "walls", "bulk", "boundary", "membrane", "classify", "fresh")
 
     def scbb_phase_times(self):
@@ -292,10 +301,13 @@ class Batch:
     """Several independent Sim contexts stepped together (scbb_batch_*): each context keeps its own stream, the
     batch runs on a stream of its own, and pairs of steps of all contexts replay from one CUDA graph."""
 
-    def __init__(self, sims, stream=None):
+    def __init__(self, sims, stream=None, autotune=False):
         import torch
 
         self.sims = list(sims)
+        if autotune:                                 # each box picks its bulk-kernel shape before the batch
+            for sim in self.sims:
+                sim.scbb_autotune()
         self.L = self.sims[0].L
         self.stream = stream if stream is not None else torch.cuda.Stream(device=self.sims[0].workspace.device)
         arr = (C.c_void_p * len(self.sims))(*[s.h.value for s in self.sims])
