@@ -61,7 +61,8 @@ def workload(name: str):
     if name == "droplet256":
         p = inputs.cfg_droplet256(n_caps=300, coupling=0)
         return p, (f"droplet256: 256^3 periodic two-component box, B droplet R=70 covered by {len(p.capsules)} s=3 "
-                   "capsules R=8 (642 vertices each) with colours +-0.05, half-way bounce-back, repulsion")
+                   "capsules R=8 (642 vertices each, softness beta=100) with colours +-0.05, half-way bounce-back, "
+                   "repulsion")
     if name == "droplet128":
         p = inputs.cfg_droplet256(n_caps=40, coupling=0, n=128, R_drop=35.0)
         return p, (f"droplet128: 128^3 periodic two-component box, B droplet R=35 covered by {len(p.capsules)} s=3 "

@@ -219,7 +219,11 @@ __global__ void k_class_tri(LbmParams p, DevState d, int step) {
                                     (a.z + b.z + c.z) * (1.f / 3.f), 0.f);
     const float xmin = fminf(a.x, fminf(b.x, c.x)), xmax = fmaxf(a.x, fmaxf(b.x, c.x));
     const float ymin = fminf(a.y, fminf(b.y, c.y)), ymax = fmaxf(a.y, fmaxf(b.y, c.y));
-    if (!(xmax - xmin < (float)d.CW && ymax - ymin < (float)d.CW)) {   // degenerate or non-finite mesh
+    // a triangle wider than a column grid or outside its capsule's grid (a degenerate mesh, runaway or
+    // non-finite vertices) is flagged and skipped, so that the loops below visit at most CW + 3 columns of
+    // bounded coordinates
+    if (!(xmax - xmin < (float)d.CW && ymax - ymin < (float)d.CW && xmin >= (float)(lo.x - 2) &&
+          xmax <= (float)(lo.x + d.CW + 2) && ymin >= (float)(lo.y - 2) && ymax <= (float)(lo.y + d.CW + 2))) {
         atomicOr(d.cnt + 2, 32);
         return;
     }
@@ -917,6 +921,13 @@ __device__ __forceinline__ void fresh_node(const LbmParams& p, const DevState& d
             const int e2 = __shfl_xor_sync(0xffffffffu, be, o);
             if (e2 >= 0 && (be < 0 || b2 < bd || (b2 == bd && e2 < be))) { bd = b2; be = e2; }
         }
+    }
+    if (be < 0) {                                  // no finite distance (non-finite geometry): keep the node
+        if (lane == 0) {
+            d.fnew[2 * q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            atomicOr(d.cnt + 2, 128);
+        }
+        return;
     }
     if (lane == 0) {
         const int4 T = d.tri[be];

@@ -276,8 +276,9 @@ scbb_status check_bb_flags(scbb_ctx* c) {
     if (h[2]) {
         c->broken = 1;
         return fail(c, SCBB_E_UNSTABLE,
-                    "bounce-back list overflow (flags %d: 1/16 capsule box, 2 column crossings, 4 fresh list, "
-                    "8 boundary list)", h[2]);
+                    "bounce-back geometry or list overflow (flags %d: 1/16 capsule box, 2 column crossings, "
+                    "4 fresh list, 8 boundary list, 32 triangle outside its column grid, 64 column triangle list, "
+                    "128 fresh node without a finite nearest element)", h[2]);
     }
     return SCBB_OK;
 }

@@ -193,9 +193,14 @@ def cfg_adjoint64(coupling: int = 0) -> Problem:
 
 
 def cfg_droplet256(n_caps: int = 300, coupling: int = 0, n: int = 256, R_drop: float = 70.0,
-                   R_cap: float = 8.0, seed: int = 5) -> Problem:
+                   R_cap: float = 8.0, seed: int = 5, penetration: float = 1.5, shell: float = 20.0,
+                   kS: float = 0.0388) -> Problem:
     """256^3 periodic box, B-rich droplet of radius 70 at the centre, n_caps s=3 capsules of radius 8 at
-    seeded non-overlapping positions in a shell around the droplet, colours alternating +/-0.05."""
+    seeded non-overlapping positions around it, colours alternating +/-0.05.  The centres lie in a shell
+    from R_drop + R_cap - penetration (a capsule that slightly penetrates the droplet, as in the paper's
+    droplet covering) to that radius + shell: the capsules' A-rich interiors stay in the A-rich phase.
+    Softness as in the paper's droplet covering: beta = R^2 gamma / kB = 100 with B = kB / (kS R^2) = 0.01,
+    i.e. kS = gamma = 0.0388, the interface tension of these fluids."""
     rng = np.random.Generator(np.random.PCG64(seed))
     c0 = np.array([n / 2.0] * 3)
     centres = []
@@ -204,13 +209,12 @@ def cfg_droplet256(n_caps: int = 300, coupling: int = 0, n: int = 256, R_drop: f
         tries += 1
         d = rng.normal(size=3)
         d /= np.linalg.norm(d)
-        r = R_drop + rng.uniform(-R_cap + 1.0, R_cap + 4.0)
+        r = R_drop + R_cap - penetration + rng.uniform(0.0, shell)
         p = c0 + r * d
         if np.any(p < R_cap + 2) or np.any(p > n - R_cap - 2):
             continue
         if all(np.linalg.norm(p - q) >= 2 * R_cap + 2 for q in centres):
             centres.append(p)
-    kS = 0.002
     caps = [Capsule(centre=tuple(p), radius=R_cap, subdiv=3, kS=kS, kB=0.01 * kS * R_cap ** 2,
                     colour=(0.05 if k % 2 == 0 else -0.05) if coupling == 0 else 0.0)
             for k, p in enumerate(centres)]
