@@ -7,6 +7,7 @@
 // recomputed by each of its three vertices, which costs nothing measurable at these mesh sizes.
 #include <math.h>
 
+#include "membrane.cuh"
 #include "scbb_internal.cuh"
 
 namespace scbb {
@@ -281,15 +282,25 @@ __global__ void k_mem_vert2(DevState d, int bb, int step) {
     d.F[i] = F;
 }
 
-int launch_membrane_forces(const LbmParams& p, const DevState& d, bool bb, int step, cudaStream_t st) {
+int launch_membrane_elastic(const LbmParams& p, const DevState& d, cudaStream_t st) {
     if (d.NM == 0) return 0;
     const int b = 128;
     const int npp = launch_pp_forces(p, d, d.pp_eps, d.pp_d0, st);
     k_mem_tri<<<(d.NT + b - 1) / b, b, 0, st>>>(d);
     k_mem_vert1<<<(d.NV + b - 1) / b, b, 0, st>>>(d);
     k_capsule_reduce<<<d.NM, CAP_THREADS, 0, st>>>(d, 1);
+    return 3 + npp;
+}
+
+int launch_membrane_update(const LbmParams& p, const DevState& d, bool bb, int step, cudaStream_t st) {
+    if (d.NM == 0) return 0;
+    const int b = 128;
     k_mem_vert2<<<(d.NV + b - 1) / b, b, 0, st>>>(d, bb ? 1 : 0, step);
-    return 4 + npp;
+    return 1;
+}
+
+int launch_membrane_forces(const LbmParams& p, const DevState& d, bool bb, int step, cudaStream_t st) {
+    return launch_membrane_elastic(p, d, st) + launch_membrane_update(p, d, bb, step, st);
 }
 
 // ------------------------------------------------------------------------------------------------------

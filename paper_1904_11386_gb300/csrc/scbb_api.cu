@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "adjoint.cuh"
+#include "membrane.cuh"
 #include "scbb_internal.cuh"
 
 using namespace scbb;
@@ -22,6 +23,9 @@ struct scbb_ctx {
     DevState d;
     int cur = 0;
     cudaStream_t st = nullptr;
+    // bounce-back contexts: a second stream for the elastic membrane forces, which run beside the fluid kernels
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int nm = 0;
     std::vector<float4> X0;           // initial shape, host copy
     long long launches = 0;
@@ -330,6 +334,11 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
     c->fl = *fl;
     c->st = (cudaStream_t)cuda_stream;
     c->nm = n_mesh;
+    if (n_mesh > 0 && fl->coupling == 0) {
+        CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+        CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    }
     layout(lat, fl, n_mesh, meshes, dev_workspace, &c->d);
     set_params(c);
     DevState& d = c->d;
@@ -468,13 +477,32 @@ scbb_status scbb_set_density(scbb_ctx* c, const double* rhoA, const double* rhoB
     return check_bb_flags(c);
 }
 
+static bool overlap_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("SCBB_OVERLAP");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
 // One time step on the context stream (kernel launches only), advancing cur, steps and the launch count.
 static void enqueue_step(scbb_ctx* c) {
     const bool ibm = c->fl.coupling == 1 && c->d.NV > 0;
     const bool bb = c->d.owner != nullptr;
     const int mode = ibm ? 1 : 0;
     const int step = (int)(c->steps & 0x7fffffff);     // the kernels use its parity only
+    // Under bounce-back the elastic membrane forces read X(t) alone, and nothing up to the boundary kernel reads
+    // what they write: they run on the second stream beside the fluid kernels (the bulk kernel leaves SMs to
+    // them) and join before the vertex update.  Not while the phases are timed one after another.
+    const bool side = bb && c->side && overlap_enabled() && c->timing != 2;
     c->mark(0);
+    if (side) {
+        cudaEventRecord(c->ev_fork, c->st);
+        cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+        c->launches += launch_membrane_elastic(c->lp, c->d, c->side);
+        cudaEventRecord(c->ev_join, c->side);
+    }
     if (ibm) {
         // membrane forces at X(t), spread onto the lattice (2-point immersed boundary)
         c->launches += launch_membrane_forces(c->lp, c->d, false, step, c->st);
@@ -507,7 +535,9 @@ static void enqueue_step(scbb_ctx* c) {
         launch_bb_boundary(c->lp, c->d, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.ghost, step, c->d.err, c->st);
         c->launches += 2;
         c->mark(4);
-        c->launches += launch_membrane_forces(c->lp, c->d, true, step, c->st);
+        if (side) cudaStreamWaitEvent(c->st, c->ev_join, 0);
+        else c->launches += launch_membrane_elastic(c->lp, c->d, c->st);
+        c->launches += launch_membrane_update(c->lp, c->d, true, step, c->st);
         c->mark(5);
         launch_bb_classify(c->lp, c->d, step, false, c->st);
         c->launches += 5;
@@ -1116,6 +1146,12 @@ const char* scbb_last_error(const scbb_ctx* c) {
 void scbb_destroy(scbb_ctx* c) {
     if (!c) return;
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     for (auto& e : c->ev) cudaEventDestroy(e);
     for (auto& e : c->pev) cudaEventDestroy(e);
     delete c;
