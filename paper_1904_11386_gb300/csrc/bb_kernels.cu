@@ -19,6 +19,7 @@
 
 #include <type_traits>
 
+#include "bb.cuh"
 #include "scbb_internal.cuh"
 
 namespace scbb {
@@ -503,9 +504,18 @@ __global__ void __launch_bounds__(BE_WARPS * 32, 4) k_boundary_elements(LbmParam
     }
 }
 
-void launch_bb_classify(const LbmParams& p, const DevState& d, int step, bool init, cudaStream_t st) {
+void launch_bb_lists_reset(const DevState& d, cudaStream_t st) {
     if (d.NM == 0) return;
     k_lists_reset<<<64, 256, 0, st>>>(d);
+}
+
+void launch_bb_classify(const LbmParams& p, const DevState& d, int step, bool init, cudaStream_t st) {
+    launch_bb_lists_reset(d, st);
+    launch_bb_classify_lists(p, d, step, init, st);
+}
+
+void launch_bb_classify_lists(const LbmParams& p, const DevState& d, int step, bool init, cudaStream_t st) {
+    if (d.NM == 0) return;
     k_class_tri<<<(d.NT + 127) / 128, 128, 0, st>>>(p, d, step);
     dim3 gc((d.CW * d.CW * d.CW + 127) / 128, d.NM);
     k_class_col<<<gc, 128, 0, st>>>(p, d, init ? 1 : 0);
@@ -1025,10 +1035,19 @@ void launch_bb_init(const LbmParams& p, const DevState& d, cudaStream_t st) {
     k_bb_init<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(p, d);
 }
 
-void launch_bb_fresh(const LbmParams& p, const DevState& d, float* Snew, int step, cudaStream_t st) {
+void launch_bb_mass(const LbmParams& p, const DevState& d, cudaStream_t st) {
     if (d.NM == 0) return;
-    double vsys = (double)p.nxy * (p.zf1 - p.zf0);
+    const double vsys = (double)p.nxy * (p.zf1 - p.zf0);
     k_mass_finalize<<<1, 1024, 0, st>>>(d, vsys);
+}
+
+void launch_bb_fresh(const LbmParams& p, const DevState& d, float* Snew, int step, cudaStream_t st) {
+    launch_bb_mass(p, d, st);
+    launch_bb_fresh_nodes(p, d, Snew, step, st);
+}
+
+void launch_bb_fresh_nodes(const LbmParams& p, const DevState& d, float* Snew, int step, cudaStream_t st) {
+    if (d.NM == 0) return;
     const size_t need_c = ((size_t)d.maxF + 7) / 8, need_a = ((size_t)d.maxF + 127) / 128;
     with_storage(p.store, [&](auto* tag) {
         using T = std::remove_pointer_t<decltype(tag)>;

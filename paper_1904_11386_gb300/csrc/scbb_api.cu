@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "adjoint.cuh"
+#include "bb.cuh"
 #include "membrane.cuh"
 #include "scbb_internal.cuh"
 
@@ -25,7 +26,7 @@ struct scbb_ctx {
     cudaStream_t st = nullptr;
     // bounce-back contexts: a second stream for the elastic membrane forces, which run beside the fluid kernels
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
     int nm = 0;
     std::vector<float4> X0;           // initial shape, host copy
     long long launches = 0;
@@ -338,6 +339,8 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
         CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
         CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
         CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+        CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork2, cudaEventDisableTiming));
+        CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming));
     }
     layout(lat, fl, n_mesh, meshes, dev_workspace, &c->d);
     set_params(c);
@@ -492,14 +495,20 @@ static void enqueue_step(scbb_ctx* c) {
     const bool bb = c->d.owner != nullptr;
     const int mode = ibm ? 1 : 0;
     const int step = (int)(c->steps & 0x7fffffff);     // the kernels use its parity only
-    // Under bounce-back the elastic membrane forces read X(t) alone, and nothing up to the boundary kernel reads
-    // what they write: they run on the second stream beside the fluid kernels (the bulk kernel leaves SMs to
-    // them) and join before the vertex update.  Not while the phases are timed one after another.
+    // Under bounce-back, kernels whose inputs are ready early run on the second stream (the bulk kernel
+    // leaves SMs to them) and join where their results are needed; not while the phases are timed one after
+    // another:
+    //   at the start of the step, the reset of the previous lists (nothing up to the boundary kernel reads the
+    //   bits and counters it clears) and the elastic membrane forces (they read X(t) alone, and nothing up to
+    //   the boundary kernel reads what they write), joined before the vertex update;
+    //   after the boundary kernel, the mass bookkeeping of Eq. 18 (its partial sums and the previous fresh
+    //   nodes' changes), joined before the fresh nodes.
     const bool side = bb && c->side && overlap_enabled() && c->timing != 2;
     c->mark(0);
     if (side) {
         cudaEventRecord(c->ev_fork, c->st);
         cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+        launch_bb_lists_reset(c->d, c->side);          // counted with the classification below
         c->launches += launch_membrane_elastic(c->lp, c->d, c->side);
         cudaEventRecord(c->ev_join, c->side);
     }
@@ -534,15 +543,24 @@ static void enqueue_step(scbb_ctx* c) {
         // classification at X(t+1), boundary list -> fresh nodes
         launch_bb_boundary(c->lp, c->d, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.ghost, step, c->d.err, c->st);
         c->launches += 2;
+        if (side) {
+            cudaEventRecord(c->ev_fork2, c->st);
+            cudaStreamWaitEvent(c->side, c->ev_fork2, 0);
+            launch_bb_mass(c->lp, c->d, c->side);
+            cudaEventRecord(c->ev_join2, c->side);
+        }
         c->mark(4);
         if (side) cudaStreamWaitEvent(c->st, c->ev_join, 0);
         else c->launches += launch_membrane_elastic(c->lp, c->d, c->st);
         c->launches += launch_membrane_update(c->lp, c->d, true, step, c->st);
         c->mark(5);
-        launch_bb_classify(c->lp, c->d, step, false, c->st);
+        if (!side) launch_bb_lists_reset(c->d, c->st);
+        launch_bb_classify_lists(c->lp, c->d, step, false, c->st);
         c->launches += 5;
         c->mark(6);
-        launch_bb_fresh(c->lp, c->d, c->d.S[1 - c->cur], step, c->st);
+        if (side) cudaStreamWaitEvent(c->st, c->ev_join2, 0);
+        else launch_bb_mass(c->lp, c->d, c->st);
+        launch_bb_fresh_nodes(c->lp, c->d, c->d.S[1 - c->cur], step, c->st);
         c->launches += 3;
     } else {
         c->mark(4);
@@ -1152,6 +1170,8 @@ void scbb_destroy(scbb_ctx* c) {
     }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_fork2) cudaEventDestroy(c->ev_fork2);
+    if (c->ev_join2) cudaEventDestroy(c->ev_join2);
     for (auto& e : c->ev) cudaEventDestroy(e);
     for (auto& e : c->pev) cudaEventDestroy(e);
     delete c;
