@@ -24,7 +24,7 @@ struct scbb_ctx {
     DevState d;
     int cur = 0;
     cudaStream_t st = nullptr;
-    // bounce-back contexts: a second stream for the elastic membrane forces, which run beside the fluid kernels
+    // contexts with meshes: a second stream for kernels that run beside the critical path of the step
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
     int nm = 0;
@@ -335,7 +335,7 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
     c->fl = *fl;
     c->st = (cudaStream_t)cuda_stream;
     c->nm = n_mesh;
-    if (n_mesh > 0 && fl->coupling == 0) {
+    if (n_mesh > 0) {
         CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
         CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
         CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
@@ -503,8 +503,17 @@ static void enqueue_step(scbb_ctx* c) {
     //   the boundary kernel reads what they write), joined before the vertex update;
     //   after the boundary kernel, the mass bookkeeping of Eq. 18 (its partial sums and the previous fresh
     //   nodes' changes), joined before the fresh nodes.
+    // With the immersed boundary, the wall ghosts (they read the populations alone) run there beside the
+    // membrane forces and the spreading (they read the vertices alone), joined before the bulk kernel.
     const bool side = bb && c->side && overlap_enabled() && c->timing != 2;
+    const bool side_walls = ibm && c->lp.walls && c->side && overlap_enabled() && c->timing != 2;
     c->mark(0);
+    if (side_walls) {
+        cudaEventRecord(c->ev_fork, c->st);
+        cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+        launch_wall_ghost(c->lp, c->d.S[c->cur], c->d.wall_rho, c->d.ghost, c->side);
+        cudaEventRecord(c->ev_join, c->side);
+    }
     if (side) {
         cudaEventRecord(c->ev_fork, c->st);
         cudaStreamWaitEvent(c->side, c->ev_fork, 0);
@@ -520,7 +529,8 @@ static void enqueue_step(scbb_ctx* c) {
     }
     c->mark(1);
     if (c->lp.walls) {
-        launch_wall_ghost(c->lp, c->d.S[c->cur], c->d.wall_rho, c->d.ghost, c->st);
+        if (side_walls) cudaStreamWaitEvent(c->st, c->ev_join, 0);
+        else launch_wall_ghost(c->lp, c->d.S[c->cur], c->d.wall_rho, c->d.ghost, c->st);
         c->launches += 2;
     }
     c->mark(2);
