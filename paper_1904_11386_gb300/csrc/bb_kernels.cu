@@ -515,10 +515,19 @@ void launch_bb_classify(const LbmParams& p, const DevState& d, int step, bool in
 }
 
 void launch_bb_classify_lists(const LbmParams& p, const DevState& d, int step, bool init, cudaStream_t st) {
+    launch_bb_owner(p, d, step, init, st);
+    launch_bb_boundary_list(p, d, st);
+}
+
+void launch_bb_owner(const LbmParams& p, const DevState& d, int step, bool init, cudaStream_t st) {
     if (d.NM == 0) return;
     k_class_tri<<<(d.NT + 127) / 128, 128, 0, st>>>(p, d, step);
     dim3 gc((d.CW * d.CW * d.CW + 127) / 128, d.NM);
     k_class_col<<<gc, 128, 0, st>>>(p, d, init ? 1 : 0);
+}
+
+void launch_bb_boundary_list(const LbmParams& p, const DevState& d, cudaStream_t st) {
+    if (d.NM == 0) return;
     // boxes are at most CW wide; one node of margin on each side
     const int w = d.CW + 2;
     dim3 gm((w * w * w + 127) / 128, d.NM);

@@ -26,7 +26,7 @@ struct scbb_ctx {
     cudaStream_t st = nullptr;
     // contexts with meshes: a second stream for kernels that run beside the critical path of the step
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_fork3 = nullptr, ev_join3 = nullptr;
     int nm = 0;
     std::vector<float4> X0;           // initial shape, host copy
     long long launches = 0;
@@ -340,7 +340,8 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
         CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
         CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
         CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork2, cudaEventDisableTiming));
-        CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming));
+        CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork3, cudaEventDisableTiming));
+        CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join3, cudaEventDisableTiming));
     }
     layout(lat, fl, n_mesh, meshes, dev_workspace, &c->d);
     set_params(c);
@@ -490,7 +491,9 @@ static bool overlap_enabled() {
 }
 
 // One time step on the context stream (kernel launches only), advancing cur, steps and the launch count.
-static void enqueue_step(scbb_ctx* c) {
+// allow_side: false inside a batch, whose graph already runs the contexts side by side (a second stream per
+// context there cost more than it gained: 7.49 -> 7.36 GLUPS on the 48-box sweep).
+static void enqueue_step(scbb_ctx* c, bool allow_side = true) {
     const bool ibm = c->fl.coupling == 1 && c->d.NV > 0;
     const bool bb = c->d.owner != nullptr;
     const int mode = ibm ? 1 : 0;
@@ -502,11 +505,14 @@ static void enqueue_step(scbb_ctx* c) {
     //   bits and counters it clears) and the elastic membrane forces (they read X(t) alone, and nothing up to
     //   the boundary kernel reads what they write), joined before the vertex update;
     //   after the boundary kernel, the mass bookkeeping of Eq. 18 (its partial sums and the previous fresh
-    //   nodes' changes), joined before the fresh nodes.
+    //   nodes' changes);
+    //   after the owner field, the fresh nodes (they need the owner field, the column lists, the vertex
+    //   velocities and the mass factors, not the boundary list, and the boundary-list kernels read nothing they
+    //   write), joined at the end of the step.
     // With the immersed boundary, the wall ghosts (they read the populations alone) run there beside the
     // membrane forces and the spreading (they read the vertices alone), joined before the bulk kernel.
-    const bool side = bb && c->side && overlap_enabled() && c->timing != 2;
-    const bool side_walls = ibm && c->lp.walls && c->side && overlap_enabled() && c->timing != 2;
+    const bool side = allow_side && bb && c->side && overlap_enabled() && c->timing != 2;
+    const bool side_walls = allow_side && ibm && c->lp.walls && c->side && overlap_enabled() && c->timing != 2;
     c->mark(0);
     if (side_walls) {
         cudaEventRecord(c->ev_fork, c->st);
@@ -557,21 +563,28 @@ static void enqueue_step(scbb_ctx* c) {
             cudaEventRecord(c->ev_fork2, c->st);
             cudaStreamWaitEvent(c->side, c->ev_fork2, 0);
             launch_bb_mass(c->lp, c->d, c->side);
-            cudaEventRecord(c->ev_join2, c->side);
         }
         c->mark(4);
         if (side) cudaStreamWaitEvent(c->st, c->ev_join, 0);
         else c->launches += launch_membrane_elastic(c->lp, c->d, c->st);
         c->launches += launch_membrane_update(c->lp, c->d, true, step, c->st);
         c->mark(5);
-        if (!side) launch_bb_lists_reset(c->d, c->st);
-        launch_bb_classify_lists(c->lp, c->d, step, false, c->st);
-        c->launches += 5;
-        c->mark(6);
-        if (side) cudaStreamWaitEvent(c->st, c->ev_join2, 0);
-        else launch_bb_mass(c->lp, c->d, c->st);
-        launch_bb_fresh_nodes(c->lp, c->d, c->d.S[1 - c->cur], step, c->st);
-        c->launches += 3;
+        if (side) {
+            launch_bb_owner(c->lp, c->d, step, false, c->st);
+            cudaEventRecord(c->ev_fork3, c->st);
+            cudaStreamWaitEvent(c->side, c->ev_fork3, 0);
+            launch_bb_fresh_nodes(c->lp, c->d, c->d.S[1 - c->cur], step, c->side);
+            cudaEventRecord(c->ev_join3, c->side);
+            launch_bb_boundary_list(c->lp, c->d, c->st);
+            cudaStreamWaitEvent(c->st, c->ev_join3, 0);
+        } else {
+            launch_bb_lists_reset(c->d, c->st);
+            launch_bb_classify_lists(c->lp, c->d, step, false, c->st);
+            c->mark(6);
+            launch_bb_mass(c->lp, c->d, c->st);
+            launch_bb_fresh_nodes(c->lp, c->d, c->d.S[1 - c->cur], step, c->st);
+        }
+        c->launches += 5 + 3;
     } else {
         c->mark(4);
         c->mark(5);
@@ -704,8 +717,8 @@ static void batch_capture(scbb_batch* b) {
     }
     cudaError_t e = batch_fork(b);
     for (size_t k = 0; k < n && e == cudaSuccess; k++) {
-        enqueue_step(b->ctx[k]);
-        enqueue_step(b->ctx[k]);
+        enqueue_step(b->ctx[k], false);
+        enqueue_step(b->ctx[k], false);
     }
     if (e == cudaSuccess) e = batch_join(b);
     cudaGraph_t g = nullptr;
@@ -1010,7 +1023,7 @@ scbb_status scbb_batch_step(scbb_batch* b, long long n) {
         // one step of every context, launched kernel by kernel on the contexts' own streams
         if (batch_fork(b) != cudaSuccess) return SCBB_E_CUDA;
         for (auto* c : b->ctx) {
-            enqueue_step(c);
+            enqueue_step(c, false);
             c->eager_steps++;
         }
         if (batch_join(b) != cudaSuccess) return SCBB_E_CUDA;
@@ -1181,7 +1194,8 @@ void scbb_destroy(scbb_ctx* c) {
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_fork2) cudaEventDestroy(c->ev_fork2);
-    if (c->ev_join2) cudaEventDestroy(c->ev_join2);
+    if (c->ev_fork3) cudaEventDestroy(c->ev_fork3);
+    if (c->ev_join3) cudaEventDestroy(c->ev_join3);
     for (auto& e : c->ev) cudaEventDestroy(e);
     for (auto& e : c->pev) cudaEventDestroy(e);
     delete c;
