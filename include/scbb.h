@@ -221,11 +221,13 @@ void scbb_batch_destroy(scbb_batch* batch);
  * body acceleration g and the initial densities rho^c(0), by hand-written adjoint kernels of the step:
  * BGK collision with the velocity-shift forcing (Eq. 1-5), the pseudo-potential force (Eq. 13) whose
  * stencil the adjoint applies transposed, and streaming (pull; the adjoint pushes).
- *   Supported contexts: periodic boxes (walls = 0) without meshes, FP32 storage; otherwise
- *   SCBB_E_UNSUPPORTED at creation.
+ *   With walls, the adjoint includes the moving-wall bounce-back (Eq. 11) and the walls' virtual densities
+ *   in the force.  Supported contexts: boxes without meshes, FP32 storage; otherwise SCBB_E_UNSUPPORTED at
+ *   creation.
  *   scbb_adjoint_workspace_bytes(ctx, n, K): device bytes of the adjoint's workspace for n steps with a
- *     population checkpoint every K steps: ceil(n/K) checkpoints, K + 1 lattices and K density fields of one
- *     segment, two adjoint lattices and 13 + 2 floats per node of scratch.  0 for bad arguments.
+ *     population checkpoint every K steps: ceil(n/K) checkpoints, K + 1 lattices, K density fields and (walls)
+ *     K wall planes of one segment, two adjoint lattices and 13 + 2 floats per node of scratch.  0 for bad
+ *     arguments.
  *   scbb_adjoint_create(ctx, n, K, dev_workspace, out): dev_workspace caller-owned, at least that many
  *     bytes, 256-byte aligned; the adjoint keeps ctx and runs on its stream.
  *   scbb_adjoint_forward(a): runs the n steps of ctx from its current state (set by scbb_set_density, an

@@ -1,9 +1,12 @@
 // Reverse-mode derivative (adjoint) of the two-component fluid step, sm_103a.
 //
-// The forward step (Sec. II.A, II.D) of a periodic box: pull f_i^c(x) = S^c[i][x - c_i]; rho^c, j; the
+// The forward step (Sec. II.A, II.D): pull f_i^c(x) = S^c[i][x - c_i]; rho^c, j; the
 // Shan-Chen force F^c(x) = -psi^c(x) G sum_i w_i psi^c'(x + c_i) c_i + rho^c g (Eq. 13); the equilibrium
 // velocity u^c = j / rho_t + tau F^c / rho^c; BGK f*_i^c = f_i^c + omega (f_eq,i(rho^c, u^c) - f_i^c) (Eq. 1-2),
-// stored at S'^c[i][x].  Its adjoint maps lambda' = dL/dS' to lambda = dL/dS in two passes over the nodes:
+// stored at S'^c[i][x]; next to a wall, a population leaving towards it is stored, bounced with the wall's
+// velocity (Eq. 11), in the wall node's slot the node pulls back, and the force reads psi of the wall's virtual
+// density (the mean density of five nodes of the first fluid plane).  Its adjoint maps lambda' = dL/dS' to
+// lambda = dL/dS in two passes over the nodes (and, with walls, a pass over the wall nodes between them):
 //
 //   local   per node x: adjoints of rho^c, u^c, F^c, u', j from lambda'(x) (chain rule through f_eq and the
 //           force), the local part of dL/dpsi^c(x), and b^c(x) = G psi^c(x) dL/dF^c(x), which the force at x
@@ -31,10 +34,11 @@ int adj_blocks(const LbmParams& p);
 // with the weights g^c = dL/drho^c (device, N floats per component).
 void launch_adj_final(const LbmParams& p, const float* gA, const float* gB, float* lam, cudaStream_t st);
 
-// One step backwards: S is the lattice the forward step read, rho the densities it computed, lam_in the
-// adjoint of the lattice it wrote; writes lam_out, the adjoint of S.  scr holds ADJ_SCR * N floats.
-void launch_adj_step(const LbmParams& p, const float* S, const float* rho, const float* lam_in, float* lam_out,
-                     float* scr, double* part, cudaStream_t st);
+// One step backwards: S is the lattice the forward step read, rho the densities it computed, ghost the wall
+// planes' virtual densities it used (4 nxy floats, walls only), lam_in the adjoint of the lattice it wrote;
+// writes lam_out, the adjoint of S.  scr holds ADJ_SCR * N floats, gw 4 nxy floats (walls only).
+void launch_adj_step(const LbmParams& p, const float* S, const float* rho, const float* ghost, const float* lam_in,
+                     float* lam_out, float* scr, float* gw, double* part, cudaStream_t st);
 
 // dL/drho0^c(x) of an initial equilibrium lattice S0 (f_i = f_eq,i(rho0, u0), linear in rho0 at fixed u0):
 // sum_i lambda0^c[i][x - c_i] S0^c[i][x - c_i] / rho0^c(x), into drho (2 N floats).

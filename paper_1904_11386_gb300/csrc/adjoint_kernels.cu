@@ -9,10 +9,18 @@ namespace {
 
 constexpr int ADJ_THREADS = 256;
 
-// Node of the periodic lattice at (x + dx, y + dy, z + dz).
+// Node at (x + dx, y + dy, z + dz): x and y periodic, z periodic without walls (with walls the callers keep
+// z + dz inside 0 .. nz-1).  The kernels are instantiated with and without walls (W), so that the periodic
+// box compiles without the wall branches.
+template <bool W>
 __device__ __forceinline__ unsigned int pnode(const LbmParams& p, int x, int y, int z, int dx, int dy, int dz) {
-    return (unsigned)wrapi(x + dx, p.nx) + (unsigned)p.nx * ((unsigned)wrapi(y + dy, p.ny) +
-                                                             (unsigned)p.ny * (unsigned)wrapi(z + dz, p.nz));
+    const int zz = W ? z + dz : wrapi(z + dz, p.nz);
+    return (unsigned)wrapi(x + dx, p.nx) + (unsigned)p.nx * ((unsigned)wrapi(y + dy, p.ny) + (unsigned)p.ny * zz);
+}
+
+template <bool W>
+__device__ __forceinline__ bool fluid_z(const LbmParams& p, int z) {
+    return W ? (z >= 1 && z <= p.nz - 2) : true;
 }
 
 __device__ __forceinline__ float dpsi_fn(float rho, int kind) { return kind == 1 ? 1.f : expf(-rho); }
@@ -24,6 +32,7 @@ int adj_blocks(const LbmParams& p) {
     return (int)(need < 152 * 8 ? need : 152 * 8);
 }
 
+template <bool W>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_final(LbmParams p, const float* __restrict__ gA,
                                                            const float* __restrict__ gB, float* __restrict__ lam) {
     const unsigned int y = blockIdx.x * blockDim.x + threadIdx.x;
@@ -31,35 +40,59 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_final(LbmParams p, const fl
     const int z = y / p.nxy, r = y - z * p.nxy, yy = r / p.nx, x = r - yy * p.nx;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        const unsigned int m = pnode(p, x, yy, z, dir_x(i), dir_y(i), dir_z(i));
-        lam[(size_t)i * p.N + y] = gA[m];
-        lam[(size_t)(Q + i) * p.N + y] = gB[m];
+        // the slot feeds the density of the node it streams to; with walls only fluid nodes have one
+        float a = 0.f, b = 0.f;
+        if (fluid_z<W>(p, z + dir_z(i))) {
+            const unsigned int m = pnode<W>(p, x, yy, z, dir_x(i), dir_y(i), dir_z(i));
+            a = gA[m];
+            b = gB[m];
+        }
+        lam[(size_t)i * p.N + y] = a;
+        lam[(size_t)(Q + i) * p.N + y] = b;
     }
 }
 
 // Local pass (one thread per node, grid-stride over a fixed grid).
+template <bool W>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(LbmParams p, const float* __restrict__ S,
                                                            const float* __restrict__ rho,
+                                                           const float* __restrict__ ghost,
                                                            const float* __restrict__ lam, float* __restrict__ scr,
                                                            double* __restrict__ part) {
     float acc[ADJ_PARAMS] = {0.f, 0.f, 0.f, 0.f};
     const size_t N = p.N;
     for (unsigned int n = blockIdx.x * blockDim.x + threadIdx.x; n < p.N; n += gridDim.x * blockDim.x) {
         const int z = n / p.nxy, r = n - z * p.nxy, y = r / p.nx, x = r - y * p.nx;
+        if (!fluid_z<W>(p, z)) {                 // wall node: no collision, nothing to send
+#pragma unroll
+            for (int k = 0; k < ADJ_SCR; k++) scr[(size_t)k * N + n] = 0.f;
+            continue;
+        }
         // forward quantities of the node (Eq. 1-5, 13)
         float jx = 0.f, jy = 0.f, jz = 0.f;
         float sA[3] = {0.f, 0.f, 0.f}, sB[3] = {0.f, 0.f, 0.f};   // sum_i w_i psi^{B|A}(x + c_i) c_i
 #pragma unroll
         for (int i = 0; i < Q; i++) {
-            const unsigned int src = pnode(p, x, y, z, -dir_x(i), -dir_y(i), -dir_z(i));
+            const unsigned int src = pnode<W>(p, x, y, z, -dir_x(i), -dir_y(i), -dir_z(i));
             const float f = S[(size_t)i * N + src] + S[(size_t)(Q + i) * N + src];
             jx += dir_x(i) * f;
             jy += dir_y(i) * f;
             jz += dir_z(i) * f;
             if (i > 0) {
-                const unsigned int m = pnode(p, x, y, z, dir_x(i), dir_y(i), dir_z(i));
-                const float wpB = dir_w(i) * psi_fn(rho[N + m], p.psi_kind);
-                const float wpA = dir_w(i) * psi_fn(rho[m], p.psi_kind);
+                // psi of the neighbour: its density, or on a wall plane the wall's virtual density
+                float nA, nB;
+                if (fluid_z<W>(p, z + dir_z(i))) {
+                    const unsigned int m = pnode<W>(p, x, y, z, dir_x(i), dir_y(i), dir_z(i));
+                    nA = rho[m];
+                    nB = rho[N + m];
+                } else {
+                    const int w = z + dir_z(i) == 0 ? 0 : 1;
+                    const unsigned int rm = (unsigned)wrapi(x + dir_x(i), p.nx) + (unsigned)p.nx * wrapi(y + dir_y(i), p.ny);
+                    nA = ghost[(size_t)(w * 2 + 0) * p.nxy + rm];
+                    nB = ghost[(size_t)(w * 2 + 1) * p.nxy + rm];
+                }
+                const float wpB = dir_w(i) * psi_fn(nB, p.psi_kind);
+                const float wpA = dir_w(i) * psi_fn(nA, p.psi_kind);
                 sA[0] += wpB * dir_x(i); sA[1] += wpB * dir_y(i); sA[2] += wpB * dir_z(i);
                 sB[0] += wpA * dir_x(i); sB[1] += wpA * dir_y(i); sB[2] += wpA * dir_z(i);
             }
@@ -83,9 +116,24 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(LbmParams p, const fl
         //   d f_eq,i / d u   = w_i rho (3 c_i + 9 (c_i.u) c_i - 3 u)
         float arA = 0.f, arB = 0.f;
         float auA[3] = {0.f, 0.f, 0.f}, auB[3] = {0.f, 0.f, 0.f};
+        float wallA = 0.f, wallB = 0.f;       // moving-wall term of the bounced values (Eq. 11)
 #pragma unroll
         for (int i = 0; i < Q; i++) {
-            const float a = lam[(size_t)i * N + n], b = lam[(size_t)(Q + i) * N + n];
+            // adjoint of f*_i: where f*_i stays in the fluid its own slot; where c_i points into a wall, the slot
+            // of the wall node its bounced value -6 w_i c_i.U rho was stored in (the node pulls it back)
+            float a, b;
+            if (fluid_z<W>(p, z + dir_z(i))) {
+                a = lam[(size_t)i * N + n];
+                b = lam[(size_t)(Q + i) * N + n];
+            } else {
+                const unsigned int m = pnode<W>(p, x, y, z, dir_x(i), dir_y(i), dir_z(i));
+                a = lam[(size_t)dir_opp(i) * N + m];
+                b = lam[(size_t)(Q + dir_opp(i)) * N + m];
+                const float* U = z + dir_z(i) == 0 ? p.ulo : p.uhi;
+                const float cU = 6.f * dir_w(i) * (dir_x(i) * U[0] + dir_y(i) * U[1] + dir_z(i) * U[2]);
+                wallA -= cU * a;
+                wallB -= cU * b;
+            }
             const float cuA = dir_x(i) * uA[0] + dir_y(i) * uA[1] + dir_z(i) * uA[2];
             const float cuB = dir_x(i) * uB[0] + dir_y(i) * uB[1] + dir_z(i) * uB[2];
             arA += a * dir_w(i) * (1.f + 3.f * cuA + 4.5f * cuA * cuA - 1.5f * uuA);
@@ -110,9 +158,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(LbmParams p, const fl
         const float aupu = aup[0] * up[0] + aup[1] * up[1] + aup[2] * up[2];
         // rho^c: through f_eq, through tau F^c / rho^c, through rho^c g, through u' = j / rho_t
         const float rA = arA - (ra > 0.f ? (aFA[0] * FA[0] + aFA[1] * FA[1] + aFA[2] * FA[2]) / ra : 0.f) +
-                   (aFA[0] * p.g[0] + aFA[1] * p.g[1] + aFA[2] * p.g[2]) - aupu * irt;
+                         (aFA[0] * p.g[0] + aFA[1] * p.g[1] + aFA[2] * p.g[2]) - aupu * irt + wallA;
         const float rB = arB - (rb > 0.f ? (aFB[0] * FB[0] + aFB[1] * FB[1] + aFB[2] * FB[2]) / rb : 0.f) +
-                   (aFB[0] * p.g[0] + aFB[1] * p.g[1] + aFB[2] * p.g[2]) - aupu * irt;
+                         (aFB[0] * p.g[0] + aFB[1] * p.g[1] + aFB[2] * p.g[2]) - aupu * irt + wallB;
         const float gpA = -p.G * (aFA[0] * sA[0] + aFA[1] * sA[1] + aFA[2] * sA[2]);
         const float gpB = -p.G * (aFB[0] * sB[0] + aFB[1] * sB[1] + aFB[2] * sB[2]);
         float* o = scr + n;
@@ -149,27 +197,63 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(LbmParams p, const fl
     }
 }
 
+// Wall pass (one thread per wall node w, both walls): the force at the fluid nodes next to the wall reads
+// psi of the wall's virtual density; dL/dpsi gathers -w_i c_i . b(w - c_i) over those nodes, and gw holds
+// dL/d(virtual density) = psi'(ghost) dL/dpsi, per wall and component.
+__global__ void __launch_bounds__(ADJ_THREADS) k_adj_wall(LbmParams p, const float* __restrict__ ghost,
+                                                          const float* __restrict__ scr, float* __restrict__ gw) {
+    const unsigned int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= 2u * p.nxy) return;
+    const size_t N = p.N;
+    const int w = q / p.nxy, r = q - w * p.nxy, y = r / p.nx, x = r - y * p.nx;
+    const int zw = w == 0 ? 0 : p.nz - 1, dz = w == 0 ? -1 : 1;     // c_z from the fluid plane into the wall
+    float apA = 0.f, apB = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        if (dir_z(i) != dz) continue;
+        const unsigned int m = pnode<true>(p, x, y, zw, -dir_x(i), -dir_y(i), -dir_z(i));
+        apA -= dir_w(i) * (dir_x(i) * scr[10 * N + m] + dir_y(i) * scr[11 * N + m] + dir_z(i) * scr[12 * N + m]);
+        apB -= dir_w(i) * (dir_x(i) * scr[7 * N + m] + dir_y(i) * scr[8 * N + m] + dir_z(i) * scr[9 * N + m]);
+    }
+    gw[(size_t)(w * 2 + 0) * p.nxy + r] = dpsi_fn(ghost[(size_t)(w * 2 + 0) * p.nxy + r], p.psi_kind) * apA;
+    gw[(size_t)(w * 2 + 1) * p.nxy + r] = dpsi_fn(ghost[(size_t)(w * 2 + 1) * p.nxy + r], p.psi_kind) * apB;
+}
+
 // Push pass (one thread per node y).
+template <bool W>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_push(LbmParams p, const float* __restrict__ rho,
                                                           const float* __restrict__ lam_in,
                                                           const float* __restrict__ scr,
+                                                          const float* __restrict__ gw,
                                                           float* __restrict__ lam_out) {
     const unsigned int y = blockIdx.x * blockDim.x + threadIdx.x;
     if (y >= p.N) return;
     const size_t N = p.N;
     const int z = y / p.nxy, r = y - z * p.nxy, yy = r / p.nx, x = r - yy * p.nx;
+    if (!fluid_z<W>(p, z)) return;               // wall nodes pull nothing
     // transposed pseudo-potential stencil: psi^A(y) enters F^B(y - c_i) with weight w_i c_i, and vice versa
     float apA = scr[5 * N + y], apB = scr[6 * N + y];
 #pragma unroll
     for (int i = 1; i < Q; i++) {
-        const unsigned int m = pnode(p, x, yy, z, -dir_x(i), -dir_y(i), -dir_z(i));
+        const unsigned int m = pnode<W>(p, x, yy, z, -dir_x(i), -dir_y(i), -dir_z(i));
         const float bBx = scr[10 * N + m], bBy = scr[11 * N + m], bBz = scr[12 * N + m];
         const float bAx = scr[7 * N + m], bAy = scr[8 * N + m], bAz = scr[9 * N + m];
         apA -= dir_w(i) * (dir_x(i) * bBx + dir_y(i) * bBy + dir_z(i) * bBz);
         apB -= dir_w(i) * (dir_x(i) * bAx + dir_y(i) * bAy + dir_z(i) * bAz);
     }
-    const float aRA = scr[y] + dpsi_fn(rho[y], p.psi_kind) * apA;
-    const float aRB = scr[N + y] + dpsi_fn(rho[N + y], p.psi_kind) * apB;
+    float aRA = scr[y] + dpsi_fn(rho[y], p.psi_kind) * apA;
+    float aRB = scr[N + y] + dpsi_fn(rho[N + y], p.psi_kind) * apB;
+    if (W && (z == 1 || z == p.nz - 2)) {
+        // a wall's virtual density is the mean density of the five fluid nodes (x, y), (x +- 1, y), (x, y +- 1)
+        // of the plane next to it; this node is in the stencils of the same five wall nodes
+        const int w = z == 1 ? 0 : 1;
+        const float* ga = gw + (size_t)(w * 2 + 0) * p.nxy;
+        const float* gb = gw + (size_t)(w * 2 + 1) * p.nxy;
+        const int xm = wrapi(x - 1, p.nx), xp = wrapi(x + 1, p.nx);
+        const int ym = wrapi(yy - 1, p.ny) * p.nx, y0 = yy * p.nx, yp = wrapi(yy + 1, p.ny) * p.nx;
+        aRA += 0.2f * (ga[x + y0] + ga[xm + y0] + ga[xp + y0] + ga[x + ym] + ga[x + yp]);
+        aRB += 0.2f * (gb[x + y0] + gb[xm + y0] + gb[xp + y0] + gb[x + ym] + gb[x + yp]);
+    }
     const float Jx = scr[2 * N + y], Jy = scr[3 * N + y], Jz = scr[4 * N + y];
     const float keep = 1.f - p.omega;
 #pragma unroll
@@ -180,12 +264,13 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_push(LbmParams p, const flo
             gA += keep * lam_in[(size_t)i * N + y];
             gB += keep * lam_in[(size_t)(Q + i) * N + y];
         }
-        const unsigned int src = pnode(p, x, yy, z, -dir_x(i), -dir_y(i), -dir_z(i));
+        const unsigned int src = pnode<W>(p, x, yy, z, -dir_x(i), -dir_y(i), -dir_z(i));
         lam_out[(size_t)i * N + src] = gA;
         lam_out[(size_t)(Q + i) * N + src] = gB;
     }
 }
 
+template <bool W>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_initial(LbmParams p, const float* __restrict__ S0,
                                                              const float* __restrict__ lam0,
                                                              float* __restrict__ drho) {
@@ -193,10 +278,15 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_initial(LbmParams p, const 
     if (x >= p.N) return;
     const size_t N = p.N;
     const int z = x / p.nxy, r = x - z * p.nxy, y = r / p.nx, xx = r - y * p.nx;
+    if (!fluid_z<W>(p, z)) {
+        drho[x] = 0.f;
+        drho[N + x] = 0.f;
+        return;
+    }
     float ra = 0.f, rb = 0.f, da = 0.f, db = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        const unsigned int src = pnode(p, xx, y, z, -dir_x(i), -dir_y(i), -dir_z(i));
+        const unsigned int src = pnode<W>(p, xx, y, z, -dir_x(i), -dir_y(i), -dir_z(i));
         const float fa = S0[(size_t)i * N + src], fb = S0[(size_t)(Q + i) * N + src];
         ra += fa;
         rb += fb;
@@ -208,17 +298,28 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_initial(LbmParams p, const 
 }
 
 void launch_adj_final(const LbmParams& p, const float* gA, const float* gB, float* lam, cudaStream_t st) {
-    k_adj_final<<<(p.N + ADJ_THREADS - 1) / ADJ_THREADS, ADJ_THREADS, 0, st>>>(p, gA, gB, lam);
+    const unsigned nb = (p.N + ADJ_THREADS - 1) / ADJ_THREADS;
+    if (p.walls) k_adj_final<true><<<nb, ADJ_THREADS, 0, st>>>(p, gA, gB, lam);
+    else k_adj_final<false><<<nb, ADJ_THREADS, 0, st>>>(p, gA, gB, lam);
 }
 
-void launch_adj_step(const LbmParams& p, const float* S, const float* rho, const float* lam_in, float* lam_out,
-                     float* scr, double* part, cudaStream_t st) {
-    k_adj_local<<<adj_blocks(p), ADJ_THREADS, 0, st>>>(p, S, rho, lam_in, scr, part);
-    k_adj_push<<<(p.N + ADJ_THREADS - 1) / ADJ_THREADS, ADJ_THREADS, 0, st>>>(p, rho, lam_in, scr, lam_out);
+void launch_adj_step(const LbmParams& p, const float* S, const float* rho, const float* ghost, const float* lam_in,
+                     float* lam_out, float* scr, float* gw, double* part, cudaStream_t st) {
+    const unsigned nb = (p.N + ADJ_THREADS - 1) / ADJ_THREADS;
+    if (p.walls) {
+        k_adj_local<true><<<adj_blocks(p), ADJ_THREADS, 0, st>>>(p, S, rho, ghost, lam_in, scr, part);
+        k_adj_wall<<<(2 * p.nxy + ADJ_THREADS - 1) / ADJ_THREADS, ADJ_THREADS, 0, st>>>(p, ghost, scr, gw);
+        k_adj_push<true><<<nb, ADJ_THREADS, 0, st>>>(p, rho, lam_in, scr, gw, lam_out);
+    } else {
+        k_adj_local<false><<<adj_blocks(p), ADJ_THREADS, 0, st>>>(p, S, rho, ghost, lam_in, scr, part);
+        k_adj_push<false><<<nb, ADJ_THREADS, 0, st>>>(p, rho, lam_in, scr, gw, lam_out);
+    }
 }
 
 void launch_adj_initial(const LbmParams& p, const float* S0, const float* lam0, float* drho, cudaStream_t st) {
-    k_adj_initial<<<(p.N + ADJ_THREADS - 1) / ADJ_THREADS, ADJ_THREADS, 0, st>>>(p, S0, lam0, drho);
+    const unsigned nb = (p.N + ADJ_THREADS - 1) / ADJ_THREADS;
+    if (p.walls) k_adj_initial<true><<<nb, ADJ_THREADS, 0, st>>>(p, S0, lam0, drho);
+    else k_adj_initial<false><<<nb, ADJ_THREADS, 0, st>>>(p, S0, lam0, drho);
 }
 
 }  // namespace scbb

@@ -1053,6 +1053,8 @@ struct scbb_adjoint {
     float* ckpt = nullptr;      // nseg lattices: the state read by steps 0, K, 2K, ...
     float* L = nullptr;         // K + 1 lattices of the segment being recomputed
     float* R = nullptr;         // K density fields (2 N) of that segment, written by the forward kernel
+    float* Gh = nullptr;        // K wall virtual densities (4 nxy) of that segment (walls only)
+    float* gw = nullptr;        // 4 nxy: adjoint of the wall virtual densities (walls only)
     float* lam[2] = {nullptr, nullptr};
     float* scr = nullptr;       // ADJ_SCR N
     float* g = nullptr;         // 2 N: adjoint of the final densities, then dL/drho0
@@ -1064,7 +1066,7 @@ struct scbb_adjoint {
 namespace {
 
 bool adjoint_supported(const scbb_ctx* c) {
-    return c && !c->lp.walls && c->d.NV == 0 && c->d.NM == 0 && c->lp.store == 0;
+    return c && c->d.NV == 0 && c->d.NM == 0 && c->lp.store == 0;
 }
 
 // Carves the adjoint's buffers (base == nullptr: measures only).
@@ -1075,13 +1077,16 @@ size_t adjoint_layout(const scbb_ctx* c, long long n, int K, void* base, scbb_ad
     float* ckpt = cv.take<float>(lat * nseg);
     float* L = cv.take<float>(lat * (K + 1));
     float* R = cv.take<float>((size_t)2 * N * K);
+    const size_t nw = c->lp.walls ? (size_t)4 * c->lp.nxy : 0;
+    float* Gh = cv.take<float>(nw * K);
+    float* gw = cv.take<float>(nw);
     float* l0 = cv.take<float>(lat);
     float* l1 = cv.take<float>(lat);
     float* scr = cv.take<float>((size_t)ADJ_SCR * N);
     float* g = cv.take<float>(2 * N);
     double* part = cv.take<double>((size_t)ADJ_PARAMS * adj_blocks(c->lp));
     if (a) {
-        a->ckpt = ckpt; a->L = L; a->R = R; a->lam[0] = l0; a->lam[1] = l1;
+        a->ckpt = ckpt; a->L = L; a->R = R; a->Gh = Gh; a->gw = gw; a->lam[0] = l0; a->lam[1] = l1;
         a->scr = scr; a->g = g; a->part = part; a->nseg = nseg; a->blocks = adj_blocks(c->lp);
     }
     return cv.off + ALIGN;
@@ -1100,7 +1105,7 @@ scbb_status scbb_adjoint_create(scbb_ctx* c, long long n, int K, void* ws, scbb_
     if (!c || !ws || n < 1 || K < 1 || ((uintptr_t)ws % ALIGN)) return SCBB_E_INVAL;
     if (c->broken) return SCBB_E_STATE;
     if (!adjoint_supported(c))
-        return fail(c, SCBB_E_UNSUPPORTED, "adjoint: periodic boxes without meshes and FP32 storage only");
+        return fail(c, SCBB_E_UNSUPPORTED, "adjoint: boxes without meshes and FP32 storage only");
     scbb_adjoint* a = new scbb_adjoint;
     a->c = c;
     a->n = n;
@@ -1147,16 +1152,21 @@ scbb_status scbb_adjoint_backward(scbb_adjoint* a, const double* gA, const doubl
         const int len = (int)std::min<long long>(a->K, a->n - (long long)s * a->K);
         CUDA_TRY(c, cudaMemcpyAsync(a->L, a->ckpt + (size_t)s * lat, sizeof(float) * lat, cudaMemcpyDeviceToDevice,
                                     c->st));
-        // recompute the segment with the forward kernel, keeping every lattice and density field
-        for (int k = 0; k < len; k++)
-            launch_bulk(c->lp, a->L + (size_t)k * lat, a->L + (size_t)(k + 1) * lat, a->R + (size_t)k * 2 * N,
-                        c->d.ghost, nullptr, nullptr, nullptr, c->d.err, 0, c->st);
+        // recompute the segment with the forward kernels, keeping every lattice, density field and wall plane
+        const size_t nw = (size_t)4 * c->lp.nxy;
+        for (int k = 0; k < len; k++) {
+            float* gh = c->lp.walls ? a->Gh + (size_t)k * nw : c->d.ghost;
+            if (c->lp.walls) launch_wall_ghost(c->lp, a->L + (size_t)k * lat, c->d.wall_rho, gh, c->st);
+            launch_bulk(c->lp, a->L + (size_t)k * lat, a->L + (size_t)(k + 1) * lat, a->R + (size_t)k * 2 * N, gh,
+                        nullptr, nullptr, nullptr, c->d.err, 0, c->st);
+        }
         for (int k = len - 1; k >= 0; k--) {
-            launch_adj_step(c->lp, a->L + (size_t)k * lat, a->R + (size_t)k * 2 * N, a->lam[cur], a->lam[1 - cur],
-                            a->scr, a->part, c->st);
+            const float* gh = c->lp.walls ? a->Gh + (size_t)k * nw : nullptr;
+            launch_adj_step(c->lp, a->L + (size_t)k * lat, a->R + (size_t)k * 2 * N, gh, a->lam[cur],
+                            a->lam[1 - cur], a->scr, a->gw, a->part, c->st);
             cur ^= 1;
         }
-        c->launches += 3 * len;
+        c->launches += (c->lp.walls ? 6 : 3) * len;
         CUDA_TRY(c, cudaGetLastError());
     }
     launch_adj_initial(c->lp, a->ckpt, a->lam[cur], a->g, c->st);

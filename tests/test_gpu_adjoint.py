@@ -1,12 +1,14 @@
-"""The adjoint of the periodic two-component fluid (scbb_adjoint_*) against FP64 central finite differences
-of the oracle.
+"""The adjoint of the two-component fluid (scbb_adjoint_*) against FP64 central finite differences of the
+oracle.
 
-Loss: L = sum_x z rho^A(x, T) + 0.5 sum_x x rho^B(x, T) after T steps of a droplet in a periodic box, a
-weighted centre of mass of each component.  Its derivatives with respect to the Shan-Chen coupling G, the
-body acceleration g and the initial densities (along a seeded direction) come from the FP32 adjoint kernels;
-the oracle differences its own FP64 runs with steps of 1e-4 (G), 1e-5 (g) and 1e-5 (densities).  The
-agreement asked of the adjoint is 1e-3 relative; the FP32 forward trajectory the adjoint follows differs from
-the FP64 one by about 1e-6."""
+Loss: L = sum_x z rho^A(x, T) + 0.5 sum_x x rho^B(x, T) after T steps, a weighted centre of mass of each
+component.  Two boxes: a droplet in a periodic 32^3 box (100 steps, exponential psi), and the 32^3 parity
+fluid between walls moving at -+0.005 along x (200 steps, psi = rho; the moving-wall bounce-back and the walls'
+virtual densities enter the adjoint).  The derivatives with respect to the Shan-Chen coupling G, the body
+acceleration g and the initial densities (along a seeded direction) come from the FP32 adjoint kernels; the
+oracle differences its own FP64 runs with steps of 1e-4 (G), 1e-5 (g) and 1e-5 (densities).  The agreement
+asked of the adjoint is 1e-3 relative; the FP32 forward trajectory the adjoint follows differs from the FP64
+one by about 1e-6."""
 import numpy as np
 import pytest
 
@@ -15,7 +17,6 @@ from paper_1904_11386_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-T = 100
 RTOL = 1e-3
 
 
@@ -46,45 +47,61 @@ def _gpu_grads(p, rhoA0, rhoB0, steps, K):
     return out, float((wA * a).sum() + (wB * b).sum())
 
 
-@pytest.fixture(scope="module")
-def case():
-    p = inputs.cfg_adjoint(n=32, R_drop=8.0)
+def _walls_problem():
+    import dataclasses
+
+    p = inputs.cfg_parity(coupling=1)
+    return dataclasses.replace(p, capsules=[], u_lo=(-0.005, 0.0, 0.0), u_hi=(0.005, 0.0, 0.0))
+
+
+CASES = {"periodic": (lambda: inputs.cfg_adjoint(n=32, R_drop=8.0), 100),
+         "walls": (_walls_problem, 200)}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    make, steps = CASES[request.param]
+    p = make()
     rhoA0, rhoB0 = p.initial_density()
-    (dG, dg, drA, drB), L = _gpu_grads(p, rhoA0, rhoB0, T, 16)      # 100 = 6 x 16 + 4: a ragged last segment
-    return p, rhoA0, rhoB0, dG, dg, drA, drB, L
+    (dG, dg, drA, drB), L = _gpu_grads(p, rhoA0, rhoB0, steps, 16)   # a ragged last segment (100 and 200 steps)
+    return p, rhoA0, rhoB0, dG, dg, drA, drB, L, steps
 
 
 def test_loss_matches_oracle(case):
-    p, rhoA0, rhoB0, *_, L = case
+    p, rhoA0, rhoB0, *_, L, T = case
     assert abs(L - _oracle_loss(p, rhoA0, rhoB0, T)) < 1e-5 * abs(L)
 
 
 def test_dG_against_fd(case):
     import dataclasses
 
-    p, rhoA0, rhoB0, dG, *_ = case
+    p, rhoA0, rhoB0, dG, *_, T = case
     h = 1e-4
     fd = (_oracle_loss(dataclasses.replace(p, G=p.G + h), rhoA0, rhoB0, T) -
           _oracle_loss(dataclasses.replace(p, G=p.G - h), rhoA0, rhoB0, T)) / (2 * h)
     assert abs(dG - fd) < RTOL * abs(fd), (dG, fd)
 
 
-@pytest.mark.parametrize("k", [0, 2])
-def test_dg_against_fd(case, k):
+def test_dg_against_fd(case):
+    """The gradient vector dL/dg against its three central differences, relative to its norm: a component that
+    the box's symmetry makes nearly zero (for example across a shear flow) carries the absolute FP32 error of the
+    whole vector, a few units against about 1e6 here, and is not held to 1e-3 of itself."""
     import dataclasses
 
-    p, rhoA0, rhoB0, _, dg, *_ = case
+    p, rhoA0, rhoB0, _, dg, *_, T = case
     h = 1e-5
-    e = np.zeros(3)
-    e[k] = h
-    fd = (_oracle_loss(dataclasses.replace(p, g=tuple(e)), rhoA0, rhoB0, T) -
-          _oracle_loss(dataclasses.replace(p, g=tuple(-e)), rhoA0, rhoB0, T)) / (2 * h)
-    assert abs(dg[k] - fd) < RTOL * abs(fd), (k, dg[k], fd)
+    fd = np.zeros(3)
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        fd[k] = (_oracle_loss(dataclasses.replace(p, g=tuple(e)), rhoA0, rhoB0, T) -
+                 _oracle_loss(dataclasses.replace(p, g=tuple(-e)), rhoA0, rhoB0, T)) / (2 * h)
+    assert np.linalg.norm(dg - fd) < RTOL * np.linalg.norm(fd), (dg, fd)
 
 
 def test_drho0_against_fd(case):
     """Directional derivative along a seeded direction of both initial density fields."""
-    p, rhoA0, rhoB0, _, _, drA, drB, _ = case
+    p, rhoA0, rhoB0, _, _, drA, drB, _, T = case
     rng = np.random.Generator(np.random.PCG64(21))
     vA, vB = rng.standard_normal(rhoA0.shape), rng.standard_normal(rhoB0.shape)
     h = 1e-5
@@ -97,7 +114,7 @@ def test_drho0_against_fd(case):
 def test_checkpoint_interval_does_not_change_the_gradient(case):
     """Recomputation from checkpoints is exact: one segment of T steps and segments of 7 steps give the same
     gradients bit for bit (the kernels are deterministic)."""
-    p, rhoA0, rhoB0, dG, dg, drA, drB, _ = case
+    p, rhoA0, rhoB0, dG, dg, drA, drB, _, T = case
     for K in (T, 7):
         (dG2, dg2, drA2, drB2), _ = _gpu_grads(p, rhoA0, rhoB0, T, K)
         assert dG2 == dG and np.array_equal(dg2, dg)
@@ -111,7 +128,7 @@ def test_autograd_function(case):
 
     from paper_1904_11386_gb300 import scbb
 
-    p, rhoA0, rhoB0, dG, dg, drA, drB, _ = case
+    p, rhoA0, rhoB0, dG, dg, drA, drB, _, T = case
     G = torch.tensor(p.G, dtype=torch.float64, requires_grad=True)
     g = torch.zeros(3, dtype=torch.float64, requires_grad=True)
     a0 = torch.tensor(rhoA0, requires_grad=True)
@@ -126,10 +143,14 @@ def test_autograd_function(case):
 
 
 def test_unsupported_contexts_are_rejected():
+    """Meshes and 16-bit storage are outside the adjoint."""
     from paper_1904_11386_gb300 import scbb
 
-    p = inputs.small_problem(n=16, walls=1, coupling=1, capsule=False)
-    sim = scbb.Sim(p)
-    with pytest.raises(scbb.ScbbError):
-        scbb.Adjoint(sim, 10, 5)
-    sim.close()
+    for p in (inputs.small_problem(n=16, walls=1, coupling=1, capsule=True),
+              inputs.small_problem(n=16, walls=1, coupling=1, capsule=False)):
+        if not p.capsules:
+            p.storage = 1
+        sim = scbb.Sim(p)
+        with pytest.raises(scbb.ScbbError):
+            scbb.Adjoint(sim, 10, 5)
+        sim.close()
