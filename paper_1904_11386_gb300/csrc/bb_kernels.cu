@@ -33,14 +33,17 @@ __device__ __forceinline__ float3 cross(float3 a, float3 b) {
 
 __device__ __forceinline__ bool wall_z(const LbmParams& p, int z) { return p.walls && (z == 0 || z == p.nz - 1); }
 
+// a wrapped into 0 .. n-1; coordinates already in range (almost all) skip the integer modulo
+__device__ __forceinline__ int wrapf(int a, int n) { return (unsigned)a < (unsigned)n ? a : wrapi(a, n); }
+
 // linear index of unwrapped lattice coordinates (x, y periodic; z periodic without walls), -1 outside
 __device__ __forceinline__ long long node_of(const LbmParams& p, int x, int y, int z) {
-    x = wrapi(x, p.nx);
-    y = wrapi(y, p.ny);
+    x = wrapf(x, p.nx);
+    y = wrapf(y, p.ny);
     if (p.walls) {
         if (z < 0 || z >= p.nz) return -1;
     } else {
-        z = wrapi(z, p.nz);
+        z = wrapf(z, p.nz);
     }
     return (long long)x + (long long)p.nx * (y + (long long)p.ny * z);
 }
@@ -611,8 +614,8 @@ __device__ __forceinline__ float2 boundary_node(const LbmParams& p, const DevSta
     float fa = 0.f, fb = 0.f;
     if (dl) {
         int zs = z - cz;
-        if (!p.walls) zs = wrapi(zs, p.nz);
-        const unsigned int src = (unsigned)wrapi(x - cx, p.nx) + (unsigned)wrapi(y - cy, p.ny) * p.nx + (unsigned)zs * p.nxy;
+        if (!p.walls) zs = wrapf(zs, p.nz);
+        const unsigned int src = (unsigned)wrapf(x - cx, p.nx) + (unsigned)wrapf(y - cy, p.ny) * p.nx + (unsigned)zs * p.nxy;
         fa = pld(S + (size_t)i * p.N + src);
         fb = pld(S + (size_t)(Q + i) * p.N + src);
     }
@@ -629,7 +632,7 @@ __device__ __forceinline__ float2 boundary_node(const LbmParams& p, const DevSta
     if (dl && lane > 0) {
         if (wall) {
             const int w = zn == 0 ? 0 : 1;
-            const int rr = wrapi(x + cx, p.nx) + wrapi(y + cy, p.ny) * p.nx;
+            const int rr = wrapf(x + cx, p.nx) + wrapf(y + cy, p.ny) * p.nx;
             psA = psi_fn(ghost[(w * 2 + 0) * p.nxy + rr], p.psi_kind);
             psB = psi_fn(ghost[(w * 2 + 1) * p.nxy + rr], p.psi_kind);
         } else {
@@ -712,7 +715,7 @@ __device__ __forceinline__ float2 boundary_node(const LbmParams& p, const DevSta
         } else if (wall) {
             const float* U = zn == 0 ? p.ulo : p.uhi;
             const float cU = 6.f * wi * (cx * U[0] + cy * U[1] + cz * U[2]);
-            const unsigned int tgt = (unsigned)(wrapi(x + cx, p.nx) + wrapi(y + cy, p.ny) * p.nx) + (unsigned)zn * p.nxy;
+            const unsigned int tgt = (unsigned)(wrapf(x + cx, p.nx) + wrapf(y + cy, p.ny) * p.nx) + (unsigned)zn * p.nxy;
             pst(D + (size_t)dir_opp(i) * p.N + tgt, oA - cU * ra);
             pst(D + (size_t)(Q + dir_opp(i)) * p.N + tgt, oB - cU * rb);
         } else if (om == me || e < 0) {
@@ -834,8 +837,8 @@ template <typename T>
 __device__ __forceinline__ void pulled_rho(const LbmParams& p, const T* __restrict__ S, int m, float& ra, float& rb) {
     const int z = m / p.nxy, r = m - z * p.nxy, y = r / p.nx, x = r - y * p.nx;
     Cols k;
-    k.cx[0] = wrapi(x - 1, p.nx); k.cx[1] = x; k.cx[2] = wrapi(x + 1, p.nx);
-    k.ry[0] = wrapi(y - 1, p.ny) * p.nx; k.ry[1] = y * p.nx; k.ry[2] = wrapi(y + 1, p.ny) * p.nx;
+    k.cx[0] = wrapf(x - 1, p.nx); k.cx[1] = x; k.cx[2] = wrapf(x + 1, p.nx);
+    k.ry[0] = wrapf(y - 1, p.ny) * p.nx; k.ry[1] = y * p.nx; k.ry[2] = wrapf(y + 1, p.ny) * p.nx;
     float f[2 * Q];
     pull(p, S, k, z, f);
     ra = rb = 0.f;
@@ -983,10 +986,10 @@ __device__ __forceinline__ void fresh_apply_node(const LbmParams& p, const DevSt
     const int n = d.flist[q];
     const int z = n / p.nxy, r = n - z * p.nxy, y = r / p.nx, x = r - y * p.nx;
     Cols k;
-    k.cx[0] = wrapi(x - 1, p.nx); k.cx[1] = x; k.cx[2] = wrapi(x + 1, p.nx);
-    k.ry[0] = wrapi(y - 1, p.ny) * p.nx; k.ry[1] = y * p.nx; k.ry[2] = wrapi(y + 1, p.ny) * p.nx;
+    k.cx[0] = wrapf(x - 1, p.nx); k.cx[1] = x; k.cx[2] = wrapf(x + 1, p.nx);
+    k.ry[0] = wrapf(y - 1, p.ny) * p.nx; k.ry[1] = y * p.nx; k.ry[2] = wrapf(y + 1, p.ny) * p.nx;
     int zm = z - 1, zp = z + 1;
-    if (!p.walls) { zm = wrapi(zm, p.nz); zp = wrapi(zp, p.nz); }
+    if (!p.walls) { zm = wrapf(zm, p.nz); zp = wrapf(zp, p.nz); }
     const int pz[3] = {zm * p.nxy, z * p.nxy, zp * p.nxy};
     const float uu = vv.x * vv.x + vv.y * vv.y + vv.z * vv.z;
     float rem[3] = {0.f, 0.f, 0.f};

@@ -317,6 +317,7 @@ struct Stencil {
 };
 
 __device__ __forceinline__ int wrap_dev(int a, int n) {
+    if ((unsigned)a < (unsigned)n) return a;        // in range: no integer modulo
     a %= n;
     return a < 0 ? a + n : a;
 }
