@@ -407,7 +407,7 @@ def run_adjoint(args, prob, label, ws, rank, local, n_steps=2000, every=100):
     fwd_ms = replica_max(fwd_ms, ws, f"cuda:{local}")
     bwd_ms = replica_max(bwd_ms, ws, f"cuda:{local}")
     nodes = prob.n_nodes
-    out = {"metric": "fluid adjoint backward / forward time (2000 steps, checkpoint every 100)",
+    out = {"metric": f"fluid adjoint backward / forward time ({n_steps} steps, checkpoint every {every})",
            "value": bwd_ms / fwd_ms, "unit": "x", "n_gpus": ws, "steps": n_steps, "warmup": 1,
            "ms_per_step": (fwd_ms + bwd_ms) / n_steps, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -460,6 +460,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp16", action="store_true",
                     help="skip the 16-bit storage figures (FP16, BF16) beside the FP32 ones")
+    ap.add_argument("--adj-steps", type=int, default=2000, help="adjoint64: steps differentiated")
+    ap.add_argument("--adj-every", type=int, default=100, help="adjoint64: steps between checkpoints")
     ap.add_argument("--storage", default="fp32", choices=list(STORAGE),
                     help="population storage on the GPU (arithmetic is FP32 either way)")
     args = ap.parse_args()
@@ -468,7 +470,7 @@ def main():
     ws, rank, local = dist_setup()
     prob, label = workload(args.workload)
     if args.workload == "adjoint64" and args.impl == "ours":
-        run_adjoint(args, prob, label, ws, rank, local)
+        run_adjoint(args, prob, label, ws, rank, local, n_steps=args.adj_steps, every=args.adj_every)
         if ws > 1:
             import torch.distributed as dist
 
