@@ -579,6 +579,10 @@ def main():
                       "storage": args.storage,
                       "l2": f"inputs larger than L2 (populations 2 x {2 * 19 * N * (4 if args.storage == 'fp32' else 2) / 1e6:.0f} MB)"},
            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+    nv = int(sum(sim.nv))
+    if nv:
+        # membrane vertices moved per second by the whole job (the same timed region as value)
+        out["vertex_updates_per_s"] = nv * args.steps * ws / (ms / 1e3)
     sim.close()
     if args.storage == "fp32" and not args.no_fp16:
         for st16 in ("fp16", "bf16"):

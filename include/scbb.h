@@ -247,6 +247,18 @@ scbb_status scbb_adjoint_backward(scbb_adjoint* a, const double* dL_drhoA, const
                                   double* dL_dg, double* dL_drho0A, double* dL_drho0B);
 void scbb_adjoint_destroy(scbb_adjoint* a);
 
+/* State save and load (checkpoint and resume; not in the paper).  scbb_state_bytes: the size of a saved state,
+ * a header (shape, current lattice, step count) followed by the context's whole workspace (populations,
+ * densities, vertices and velocities, element accumulators, lists and counters, mass bookkeeping).
+ * scbb_save copies the state into host_buf (caller-owned, at least scbb_state_bytes); synchronous.
+ * scbb_load restores a state saved from a context of the same shape (lattice, walls, meshes, storage) and
+ * clears a failed context's error state; SCBB_E_INVAL for a buffer of another shape.  Steps after a load
+ * continue exactly as they would have from the saved state (for the bounce-back coupling up to the order of
+ * float atomic additions). */
+size_t scbb_state_bytes(const scbb_ctx* ctx);
+scbb_status scbb_save(scbb_ctx* ctx, void* host_buf, size_t bytes);
+scbb_status scbb_load(scbb_ctx* ctx, const void* host_buf, size_t bytes);
+
 const char* scbb_last_error(const scbb_ctx* ctx);
 
 /* Releases host-side state.  The workspace stays owned by the caller. */

@@ -29,6 +29,8 @@ struct scbb_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_fork3 = nullptr, ev_join3 = nullptr;
     int nm = 0;
     std::vector<float4> X0;           // initial shape, host copy
+    void* ws = nullptr;               // the caller's workspace: every piece of device state lives in it
+    size_t ws_bytes = 0;
     long long launches = 0;
     long long steps = 0;
     int broken = 0;
@@ -344,6 +346,8 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
         CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join3, cudaEventDisableTiming));
     }
     layout(lat, fl, n_mesh, meshes, dev_workspace, &c->d);
+    c->ws = dev_workspace;
+    c->ws_bytes = need;
     set_params(c);
     DevState& d = c->d;
     d.rho_maj = fl->rho_maj;
@@ -1188,6 +1192,68 @@ scbb_status scbb_adjoint_backward(scbb_adjoint* a, const double* gA, const doubl
 }
 
 void scbb_adjoint_destroy(scbb_adjoint* a) { delete a; }
+
+// ------------------------------------------------------------------------------------------------------
+// State save and load: a header, then the whole workspace (populations, densities, vertices, element
+// accumulators, lists, counters, mass bookkeeping); the host keeps the current lattice and the step count.
+// ------------------------------------------------------------------------------------------------------
+
+namespace {
+
+struct StateHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t cur;
+    long long steps;
+    unsigned long long ws_bytes;
+    int nx, ny, nz, walls, nv, nt, nm, store;
+};
+
+void fill_header(const scbb_ctx* c, StateHeader* h) {
+    memset(h, 0, sizeof(*h));
+    memcpy(h->magic, "SCBBSTAT", 8);
+    h->version = 1;
+    h->cur = (uint32_t)c->cur;
+    h->steps = c->steps;
+    h->ws_bytes = c->ws_bytes;
+    h->nx = c->lp.nx; h->ny = c->lp.ny; h->nz = c->lp.nz; h->walls = c->lp.walls;
+    h->nv = c->d.NV; h->nt = c->d.NT; h->nm = c->d.NM; h->store = c->lp.store;
+}
+
+}  // namespace
+
+size_t scbb_state_bytes(const scbb_ctx* c) { return c ? sizeof(StateHeader) + c->ws_bytes : 0; }
+
+scbb_status scbb_save(scbb_ctx* c, void* buf, size_t bytes) {
+    if (!c || !buf || bytes < scbb_state_bytes(c)) return SCBB_E_INVAL;
+    if (c->broken) return SCBB_E_STATE;
+    StateHeader h;
+    fill_header(c, &h);
+    memcpy(buf, &h, sizeof(h));
+    CUDA_TRY(c, cudaMemcpyAsync((char*)buf + sizeof(h), c->ws, c->ws_bytes, cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    return SCBB_OK;
+}
+
+scbb_status scbb_load(scbb_ctx* c, const void* buf, size_t bytes) {
+    if (!c || !buf || bytes < sizeof(StateHeader)) return SCBB_E_INVAL;
+    StateHeader h, mine;
+    memcpy(&h, buf, sizeof(h));
+    fill_header(c, &mine);
+    mine.cur = h.cur;
+    mine.steps = h.steps;
+    if (memcmp(&h, &mine, sizeof(h)) != 0 || h.cur > 1 || h.steps < 0 || bytes < scbb_state_bytes(c))
+        return fail(c, SCBB_E_INVAL, "scbb_load: the state was saved from a context of another shape");
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    if (c->side) CUDA_TRY(c, cudaStreamSynchronize(c->side));
+    CUDA_TRY(c, cudaMemcpyAsync(c->ws, (const char*)buf + sizeof(h), c->ws_bytes, cudaMemcpyHostToDevice, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    c->cur = (int)h.cur;
+    c->steps = h.steps;
+    c->broken = 0;
+    c->err.clear();
+    return SCBB_OK;
+}
 
 const char* scbb_last_error(const scbb_ctx* c) {
     if (!c) return "null context";

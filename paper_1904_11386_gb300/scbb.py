@@ -22,7 +22,7 @@ EXPORTS = ["scbb_workspace_bytes", "scbb_create", "scbb_set_density", "scbb_step
            "scbb_launch_count", "scbb_enable_timing", "scbb_kernel_time", "scbb_phase_times", "scbb_autotune",
            "scbb_population_moments_noalloc", "scbb_batch_create", "scbb_batch_step", "scbb_batch_destroy",
            "scbb_adjoint_workspace_bytes", "scbb_adjoint_create", "scbb_adjoint_forward", "scbb_adjoint_backward",
-           "scbb_adjoint_destroy", "scbb_last_error", "scbb_destroy"]
+           "scbb_adjoint_destroy", "scbb_state_bytes", "scbb_save", "scbb_load", "scbb_last_error", "scbb_destroy"]
 
 
 class scbb_lattice(C.Structure):
@@ -85,6 +85,12 @@ def load(path: str = LIB_PATH):
     L.scbb_enable_timing.argtypes = [vp, C.c_int]
     L.scbb_kernel_time.restype = C.c_int
     L.scbb_kernel_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+    L.scbb_state_bytes.restype = C.c_size_t
+    L.scbb_state_bytes.argtypes = [vp]
+    L.scbb_save.restype = C.c_int
+    L.scbb_save.argtypes = [vp, vp, C.c_size_t]
+    L.scbb_load.restype = C.c_int
+    L.scbb_load.argtypes = [vp, vp, C.c_size_t]
     L.scbb_autotune.restype = C.c_int
     L.scbb_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
     L.scbb_phase_times.restype = C.c_int
@@ -275,6 +281,20 @@ class Sim:
         k = C.c_int(-1)
         self._check(self.L.scbb_autotune(self.h, int(reps), C.byref(k)), "scbb_autotune")
         return k.value
+
+    def scbb_state_bytes(self):
+        return int(self.L.scbb_state_bytes(self.h))
+
+    def scbb_save(self):
+        """The whole state (header and workspace) as a numpy uint8 array on the host."""
+        buf = np.empty(self.scbb_state_bytes(), np.uint8)
+        self._check(self.L.scbb_save(self.h, _p(buf), C.c_size_t(buf.size)), "scbb_save")
+        return buf
+
+    def scbb_load(self, buf):
+        """Restores a state saved by scbb_save from a context of the same shape."""
+        b = np.ascontiguousarray(buf, np.uint8)
+        self._check(self.L.scbb_load(self.h, _p(b), C.c_size_t(b.size)), "scbb_load")
 
     PHASES = ("ibm_spread", "walls", "bulk", "boundary", "membrane", "classify", "fresh")
 
