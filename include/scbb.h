@@ -89,13 +89,15 @@ typedef struct {
  * outside.  ref_xyz is the stress-free shape (A0 and V0 are taken from it), init_xyz the initial shape
  * (may equal ref_xyz).  kS, C: Skalak moduli (Eq. 6); kV: volume penalty (Eq. 7); kB: Helfrich bending
  * (Eq. 9-10); mass: node mass for the bounce-back coupling (5 in the paper); colour: particle colour
- * Delta rho (Eq. 15), positive prefers component A. */
+ * Delta rho (Eq. 15), positive prefers component A.  elem_colour: NULL, or the colour of each triangle (nt
+ * values, a Janus particle; Sec. V names it as a direct extension), which then replaces colour. */
 typedef struct {
     int nv, nt;
     const double* ref_xyz;   /* [nv][3] */
     const int* tri;          /* [nt][3] vertex indices 0..nv-1 */
     const double* init_xyz;  /* [nv][3] */
     double kS, C, kB, kV, mass, colour;
+    const double* elem_colour;  /* [nt] or NULL */
 } scbb_mesh;
 
 /* Bytes of device workspace a context with this description needs (0 on invalid input). */

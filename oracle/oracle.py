@@ -70,6 +70,8 @@ def lib():
         L.o_momentum.argtypes = [C.c_void_p, _dp]
         L.o_get_vertices.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.o_set_vertices.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.o_set_elem_colour.restype = None
+        L.o_set_elem_colour.argtypes = [C.c_void_p, _dp]
         L.o_get_owner.argtypes = [C.c_void_p, _u16p]
         L.o_capsule_diag.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_double), _dp]
         L.o_skalak.restype = C.c_double
@@ -202,6 +204,12 @@ class OracleSim:
         init_all = np.ascontiguousarray(np.concatenate(inits) if inits else np.zeros((1, 3)), np.float64)
         self._keep = (mps, tri_all, ref_all, init_all)
         self.h = L.o_create(C.byref(p), nm, mps, _ptr(tri_all), _ptr(ref_all), _ptr(init_all))
+        if any(getattr(cap, "elem_colour", None) is not None for cap in prob.capsules):
+            # per-element colours (Sec. V), a capsule without them keeps its uniform colour on every element
+            ecol = np.concatenate([np.full(len(t), cap.colour) if cap.elem_colour is None
+                                   else np.asarray(cap.elem_colour, np.float64) for cap, t in zip(prob.capsules, tris)])
+            self._ecol = np.ascontiguousarray(ecol, np.float64)
+            L.o_set_elem_colour(self.h, self._ecol)
         if rhoA is None:
             rhoA, rhoB = prob.initial_density()
         L.o_set_state(self.h, np.ascontiguousarray(rhoA.ravel(), np.float64),

@@ -101,6 +101,7 @@ typedef struct {
     /* capsules */
     int nm;
     o_mesh_params* mp;
+    double* ecol;           /* [T] colour of each element (NULL: the capsule's colour on every element) */
     int* voff;              /* vertex offset per capsule (nm+1) */
     int* toff;              /* triangle offset per capsule (nm+1) */
     int* tri;               /* global vertex ids [T][3] */
@@ -220,7 +221,19 @@ void o_destroy(osim* s) {
     free(s->owner); free(s->owner_old); free(s->mp); free(s->voff); free(s->toff); free(s->tri);
     free(s->X); free(s->Vel); free(s->F); free(s->refX); free(s->V0);
     free(s->emom_now); free(s->emom_prev); free(s->epend); free(s->brow); free(s->belem); free(s->blink);
+    free(s->ecol);
     free(s);
+}
+
+/* Colour of each element (Sec. V: an individually coloured particle surface, a Janus particle), T values in the
+   global triangle order; NULL restores the capsules' uniform colours. */
+void o_set_elem_colour(osim* s, const double* col) {
+    free(s->ecol);
+    s->ecol = NULL;
+    if (!col || s->nm == 0) return;
+    const int T = s->toff[s->nm];
+    s->ecol = (double*)malloc(sizeof(double) * (size_t)(T > 0 ? T : 1));
+    memcpy(s->ecol, col, sizeof(double) * (size_t)T);
 }
 
 /* populations f = f_eq(rho^c, u) on every node (wall nodes included; they are never used as fluid) */

@@ -324,14 +324,14 @@ static double bb_virtual_psi(osim* s, long n, int x, int y, int z, int i, long m
     }
     double rt = cnt ? sum / cnt : s->rho[c_other * s->N + n];
     int cap = link_capsule(s, n, m);
-    double col = s->mp[cap].colour;
+    int e = table_element(s, n, i);
+    /* the colour of the crossed element (Sec. V's per-element colour), else of its capsule */
+    double col = (s->ecol && e >= 0) ? s->ecol[e] : s->mp[cap].colour;
     double rv = 2.0 * fabs(col) * (s->p.rho_maj - s->p.rho_min);
     if ((col > 0 && c_other == 0) || (col < 0 && c_other == 1)) rt += rv;
     double ps = psi_of(s, rt);
     /* reaction on the element: + psi^c(n) G w_i psi^{c'}(virtual) c_i, c = the other component's partner */
     int c = 1 - c_other;
-    int e = table_element(s, n, i);
-    (void)e;
     double* q = link_rec(s, n, i);
     const double a = s->psi[c * s->N + n] * s->p.G * W[i] * ps;
     q[3] += a * CX[i]; q[4] += a * CY[i]; q[5] += a * CZ[i];

@@ -667,7 +667,7 @@ __device__ __forceinline__ float2 boundary_node(const LbmParams& p, const DevSta
                     vB = cnt ? sB / cnt : rb;
                 }
                 if (e >= 0) {
-                    const float col = d.cap[d.tri[e].w].colour;
+                    const float col = d.tcol[e];     // the crossed element's colour (per capsule or per element)
                     const float rv = 2.f * fabsf(col) * (float)(d.rho_maj - d.rho_min);
                     if (col > 0.f) vA += rv;
                     else if (col < 0.f) vB += rv;

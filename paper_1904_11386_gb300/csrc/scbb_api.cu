@@ -213,6 +213,7 @@ size_t layout(const scbb_lattice* lat, const scbb_fluid* fl, int nm, const scbb_
     t.AK = c.take<float2>(nv1);
     t.X0 = c.take<float4>(nv1);
     t.tri = c.take<int4>(nt1);
+    t.tcol = c.take<float>(nt1);
     t.tref = c.take<float4>(nt1);
     t.vt_off = c.take<int>(nv1 + 1);
     t.vt_idx = c.take<int>(3 * nt1);
@@ -325,9 +326,13 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
         LbmParams lp = make_params(lat, fl);
         if (!bulk_vectorised(lp)) return SCBB_E_UNSUPPORTED;
     }
-    if (fl->coupling == 1)
-        for (int k = 0; k < n_mesh; k++)
-            if (meshes[k].colour != 0.0) return SCBB_E_INVAL;     // wetting needs the bounce-back coupling
+    for (int k = 0; k < n_mesh; k++) {
+        if (fl->coupling == 1 && (meshes[k].colour != 0.0 || meshes[k].elem_colour))
+            return SCBB_E_INVAL;                                      // wetting needs the bounce-back coupling
+        if (meshes[k].elem_colour)
+            for (int t = 0; t < meshes[k].nt; t++)
+                if (!isfinite(meshes[k].elem_colour[t])) return SCBB_E_INVAL;
+    }
     if (((uintptr_t)dev_workspace) % ALIGN) return SCBB_E_INVAL;
     size_t need = layout(lat, fl, n_mesh, meshes, nullptr, nullptr);
     if (bytes < need) return SCBB_E_NOMEM;
@@ -358,6 +363,7 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
     // ---- meshes: triangles, reference metrics, vertex -> triangle CSR, capsule constants
     const int NV = d.NV, NT = d.NT;
     std::vector<int4> tri(NT > 0 ? NT : 1);
+    std::vector<float> tcol(NT > 0 ? NT : 1);
     std::vector<float4> tref(NT > 0 ? NT : 1);
     std::vector<int> vcap(NV > 0 ? NV : 1), cnt(NV + 1, 0), vt_idx(3 * (NT > 0 ? NT : 1));
     std::vector<int2> cnb(3 * (NT > 0 ? NT : 1));
@@ -370,6 +376,7 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
         for (int t = 0; t < M.nt; t++) {
             const int a = M.tri[3 * t], b = M.tri[3 * t + 1], e = M.tri[3 * t + 2];
             tri[t0 + t] = make_int4(v0 + a, v0 + b, v0 + e, m);
+            tcol[t0 + t] = (float)(M.elem_colour ? M.elem_colour[t] : M.colour);
             const double* A = M.ref_xyz + 3 * a;
             const double* B = M.ref_xyz + 3 * b;
             const double* E = M.ref_xyz + 3 * e;
@@ -412,6 +419,7 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
     }
     if (NT > 0) {
         CUDA_TRY(c, cudaMemcpyAsync(d.tri, tri.data(), sizeof(int4) * NT, cudaMemcpyHostToDevice, c->st));
+        CUDA_TRY(c, cudaMemcpyAsync(d.tcol, tcol.data(), sizeof(float) * NT, cudaMemcpyHostToDevice, c->st));
         CUDA_TRY(c, cudaMemcpyAsync(d.tref, tref.data(), sizeof(float4) * NT, cudaMemcpyHostToDevice, c->st));
         CUDA_TRY(c, cudaMemcpyAsync(d.vt_idx, vt_idx.data(), sizeof(int) * 3 * NT, cudaMemcpyHostToDevice, c->st));
         CUDA_TRY(c, cudaMemcpyAsync(d.cnb, cnb.data(), sizeof(int2) * 3 * NT, cudaMemcpyHostToDevice, c->st));

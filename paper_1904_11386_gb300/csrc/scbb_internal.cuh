@@ -173,6 +173,7 @@ struct DevState {
     float4* nrm;            // [NV] unit normal (xyz) and H (w)
     float2* AK;             // [NV] mixed area, Gaussian curvature
     int4* tri;              // [NT] a, b, c, capsule
+    float* tcol;            // [NT] colour of each element (its capsule's, or the mesh's per-element colour)
     float4* tref;           // [NT] inverse reference metric (ia, ib, ic) and reference area A0
     int* vt_off;            // [NV+1] vertex -> incident triangle CSR
     int* vt_idx;            // [3 NT] corner ids 3 * t + k of the triangles around each vertex

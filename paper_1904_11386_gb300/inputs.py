@@ -73,6 +73,7 @@ class Capsule:
     mass: float = 5.0
     colour: float = 0.0
     deform: Optional[np.ndarray] = None      # optional 3x3 affine map applied to the initial (not reference) shape
+    elem_colour: Optional[np.ndarray] = None  # optional colour of each triangle (a Janus particle); else `colour`
 
     def mesh(self):
         V, F = icosphere(self.subdiv)
@@ -221,6 +222,14 @@ def cfg_droplet256(n_caps: int = 300, coupling: int = 0, n: int = 256, R_drop: f
     return Problem(name="droplet256", nx=n, ny=n, nz=n, walls=0, psi_kind=0, coupling=coupling,
                    droplet=(n / 2.0, n / 2.0, n / 2.0, R_drop), capsules=caps, noise=1e-4, seed=seed,
                    steps=20000)
+
+
+def janus_colours(cap: "Capsule", top: float, bottom: float) -> np.ndarray:
+    """Per-triangle colours of a Janus capsule: `top` on the triangles whose centroid lies above the capsule's
+    centre (+z), `bottom` below."""
+    ref, tri, _ = cap.mesh()
+    cz = ref[tri].mean(axis=1)[:, 2]
+    return np.where(cz >= cap.centre[2], top, bottom).astype(np.float64)
 
 
 def cfg_adjoint(n: int = 32, R_drop: float = 8.0, seed: int = 9, G: float = 3.6) -> Problem:

@@ -40,7 +40,7 @@ class scbb_fluid(C.Structure):
 class scbb_mesh(C.Structure):
     _fields_ = [("nv", C.c_int), ("nt", C.c_int), ("ref_xyz", C.c_void_p), ("tri", C.c_void_p),
                 ("init_xyz", C.c_void_p), ("kS", C.c_double), ("C", C.c_double), ("kB", C.c_double),
-                ("kV", C.c_double), ("mass", C.c_double), ("colour", C.c_double)]
+                ("kV", C.c_double), ("mass", C.c_double), ("colour", C.c_double), ("elem_colour", C.c_void_p)]
 
 
 class ScbbError(RuntimeError):
@@ -194,6 +194,12 @@ class Sim:
             m.nv, m.nt = len(ref), len(tri)
             m.ref_xyz, m.tri, m.init_xyz = _p(ref), _p(tri), _p(init)
             m.kS, m.C, m.kB, m.kV, m.mass, m.colour = cap.kS, cap.C, cap.kB, cap.kV, cap.mass, cap.colour
+            if getattr(cap, "elem_colour", None) is not None:
+                ec = np.ascontiguousarray(cap.elem_colour, np.float64)
+                if ec.shape != (len(tri),):
+                    raise ScbbError("elem_colour needs one value per triangle")
+                self._keep.append(ec)
+                m.elem_colour = _p(ec)
             self.nv.append(len(ref))
         self.nm = nm
         nbytes = L.scbb_workspace_bytes(C.byref(self.lat), C.byref(self.fl), nm, self.meshes)

@@ -135,3 +135,23 @@ def test_bb_uneven_box_rows_across_warps():
     Xg, _, _ = g.scbb_get_vertices()
     Xo, _, _ = o.vertices()
     assert np.abs(Xg - Xo).max() < 1e-4
+
+
+def test_bb_janus_capsule_20_steps():
+    """Per-element colour (a Janus capsule: +0.3 on its upper half, -0.3 on its lower half), 20 coupled steps:
+    identical owner fields, densities within 1e-5 relative, vertex positions within 1e-4."""
+    import dataclasses
+
+    p = _small()
+    cap = p.capsules[0]
+    p.capsules = [dataclasses.replace(cap, elem_colour=inputs.janus_colours(cap, 0.3, -0.3))]
+    g = _sim(p)
+    o = O.OracleSim(p)
+    g.scbb_step(20)
+    o.step(20)
+    og, _, _ = g.scbb_get_owner()
+    assert np.array_equal(og, o.owner())
+    assert _cmp_rho(g.scbb_get_fields(), o.fields()) < 1e-5
+    Xg, _, _ = g.scbb_get_vertices()
+    Xo, _, _ = o.vertices()
+    assert np.abs(Xg - Xo).max() < 1e-4

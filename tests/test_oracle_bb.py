@@ -134,3 +134,27 @@ def test_fresh_node_mass_correction_reduces_drift():
         assert s.fresh_count()[0] > 0
     assert drift[2500.0] < drift[0.0], drift
     assert drift[2500.0] < 2e-3
+
+
+def test_janus_colour_per_element():
+    """Sec. V's per-element colour: every element given the capsule's colour reproduces the uniform capsule
+    exactly; a Janus colouring (+0.6 on the upper half, -0.6 on the lower) changes the wetting forces, and the
+    capsule's two halves feel opposite virtual densities, so it ends between the two uniform capsules."""
+    import dataclasses
+
+    def run(cap):
+        p = _bb(nx=20, ny=20, nz=24, walls=1, caps=[cap], z_interface=12, noise=0.0, G=3.6)
+        s = O.OracleSim(p)
+        s.step(60)
+        return s.populations(), s.capsule(0)[1][2]
+
+    base = inputs.Capsule(centre=(10.0, 10.0, 12.0), radius=5.0, subdiv=3, kS=0.05, kB=0.0, kV=2.0, colour=0.6)
+    f_uni, z_uni = run(base)
+    nt = len(base.mesh()[1])
+    f_same, _ = run(dataclasses.replace(base, elem_colour=np.full(nt, 0.6)))
+    assert np.array_equal(f_uni, f_same)
+    janus = dataclasses.replace(base, elem_colour=inputs.janus_colours(base, 0.6, -0.6))
+    f_jan, z_jan = run(janus)
+    assert not np.array_equal(f_uni, f_jan)
+    _, z_neg = run(dataclasses.replace(base, colour=-0.6))
+    assert min(z_uni, z_neg) - 1e-3 < z_jan < max(z_uni, z_neg) + 1e-3, (z_uni, z_jan, z_neg)
