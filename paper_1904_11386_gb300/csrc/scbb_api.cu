@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -337,7 +338,9 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
     size_t need = layout(lat, fl, n_mesh, meshes, nullptr, nullptr);
     if (bytes < need) return SCBB_E_NOMEM;
 
-    scbb_ctx* c = new scbb_ctx();
+    // released (streams, events, graphs) by scbb_destroy on every failure below
+    std::unique_ptr<scbb_ctx, void (*)(scbb_ctx*)> guard(new scbb_ctx(), scbb_destroy);
+    scbb_ctx* c = guard.get();
     c->lat = *lat;
     c->fl = *fl;
     c->st = (cudaStream_t)cuda_stream;
@@ -446,7 +449,7 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
     }
     CUDA_TRY(c, cudaMemsetAsync(d.err, 0, sizeof(int) * 4, c->st));
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
-    *out = c;
+    *out = guard.release();
     return SCBB_OK;
 }
 
