@@ -58,6 +58,42 @@ def icosphere(subdiv: int):
     return V, F
 
 
+def geodesic_sphere(freq: int):
+    """Class-I geodesic sphere: every face of the icosahedron split into freq^2 triangles, the points projected
+    onto the unit sphere.  Returns (vertices[nv,3], triangles[nt,3] int32) with nv = 10 freq^2 + 2 and
+    nt = 20 freq^2, triangles counter-clockwise seen from outside; freq = 12 gives the paper's 1442 nodes and
+    2880 elements (recursive halving only reaches the frequencies 2^s)."""
+    V0, F0 = icosphere(0)
+    index, pts = {}, []
+
+    def vid(a, b, c, i, j, k):
+        # the point (i A + j B + k C) / freq of face (A, B, C); a point on an edge or a corner is keyed by the
+        # icosahedron vertices it mixes, so the faces sharing it share one vertex
+        key = tuple(sorted((v, w) for v, w in ((a, i), (b, j), (c, k)) if w > 0))
+        if key not in index:
+            q = (i * V0[a] + j * V0[b] + k * V0[c]) / freq
+            pts.append(q / np.linalg.norm(q))
+            index[key] = len(pts) - 1
+        return index[key]
+
+    tris = []
+    for a, b, c in F0:
+        for i in range(freq):
+            for j in range(freq - i):
+                p00 = vid(a, b, c, freq - i - j, i, j)
+                p10 = vid(a, b, c, freq - i - j - 1, i + 1, j)
+                p01 = vid(a, b, c, freq - i - j - 1, i, j + 1)
+                tris.append((p00, p10, p01))
+                if i + j < freq - 1:
+                    tris.append((p10, vid(a, b, c, freq - i - j - 2, i + 1, j + 1), p01))
+    V = np.array(pts, dtype=np.float64)
+    F = np.array(tris, dtype=np.int32)
+    a, b, c = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    flip = np.einsum("ij,ij->i", np.cross(b - a, c - a), (a + b + c) / 3.0) < 0
+    F[flip] = F[flip][:, [0, 2, 1]]
+    return V, F
+
+
 # ----------------------------------------------------------------------------------------------------------
 # Problem description (plain data).  Units: dx = dt = rho0 = 1.
 # ----------------------------------------------------------------------------------------------------------
@@ -74,9 +110,10 @@ class Capsule:
     colour: float = 0.0
     deform: Optional[np.ndarray] = None      # optional 3x3 affine map applied to the initial (not reference) shape
     elem_colour: Optional[np.ndarray] = None  # optional colour of each triangle (a Janus particle); else `colour`
+    geodesic: int = 0                        # > 0: a frequency-`geodesic` geodesic sphere instead of subdiv
 
     def mesh(self):
-        V, F = icosphere(self.subdiv)
+        V, F = geodesic_sphere(self.geodesic) if self.geodesic else icosphere(self.subdiv)
         ref = V * self.radius + np.asarray(self.centre, dtype=np.float64)
         init = ref.copy()
         if self.deform is not None:

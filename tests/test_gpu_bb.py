@@ -155,3 +155,24 @@ def test_bb_janus_capsule_20_steps():
     Xg, _, _ = g.scbb_get_vertices()
     Xo, _, _ = o.vertices()
     assert np.abs(Xg - Xo).max() < 1e-4
+
+
+def test_bb_paper_mesh_capsule():
+    """The paper's particle: a frequency-12 geodesic sphere (1442 nodes, 2880 elements) of radius 10
+    penetrating the interface by 1 in a 40^3 box between sheared walls, colour 0.05: 10 coupled steps,
+    owners identical, densities within 1e-5, vertices within 1e-4."""
+    cap = inputs.Capsule(centre=(20.2, 19.7, 20.0 - 10.0 + 1.0), radius=10.0, geodesic=12, kS=0.005,
+                         kB=0.01 * 0.005 * 100.0, kV=20.0, colour=0.05)
+    assert len(cap.mesh()[0]) == 1442
+    p = inputs.Problem(name="paper-mesh", nx=40, ny=40, nz=40, walls=1, coupling=0, psi_kind=0, z_interface=20,
+                       capsules=[cap], noise=1e-4, seed=19, u_lo=(-0.002, 0, 0), u_hi=(0.002, 0, 0))
+    g = _sim(p)
+    o = O.OracleSim(p)
+    g.scbb_step(10)
+    o.step(10)
+    og, _, _ = g.scbb_get_owner()
+    assert np.array_equal(og, o.owner())
+    assert _cmp_rho(g.scbb_get_fields(), o.fields()) < 1e-5
+    Xg, _, _ = g.scbb_get_vertices()
+    Xo, _, _ = o.vertices()
+    assert np.abs(Xg - Xo).max() < 1e-4

@@ -1,6 +1,7 @@
 """The seeded synthetic workloads (paper_1904_11386_gb300/inputs.py): shapes and placement rules the
 benchmark and the tests rely on.  No GPU needed."""
 import numpy as np
+import pytest
 
 from paper_1904_11386_gb300 import inputs
 
@@ -47,3 +48,27 @@ def test_batch_sweep_boxes():
         {round(v, 12) for v in np.linspace(-0.1, 0.1, 11)})
     assert {p.capsules[0].kS for p in probs} == {0.001, 0.003, 0.01, 0.03}
     assert [p.seed for p in probs] == [100 + k for k in range(48)]
+
+
+@pytest.mark.parametrize("freq", [1, 2, 3, 12])
+def test_geodesic_sphere(freq):
+    """The class-I geodesic sphere: 10 f^2 + 2 vertices and 20 f^2 triangles (f = 12: the paper's 1442 nodes
+    and 2880 elements), every vertex on the unit sphere, a closed surface whose directed edges each appear once
+    with their reverse once (consistent orientation, Euler characteristic 2), normals outward, and the
+    discrete Gauss-Bonnet identity sum K_G A = 4 pi of the oracle's Meyer operators."""
+    from oracle import oracle as O
+
+    V, F = inputs.geodesic_sphere(freq)
+    assert V.shape == (10 * freq * freq + 2, 3) and F.shape == (20 * freq * freq, 3)
+    assert np.allclose(np.linalg.norm(V, axis=1), 1.0, atol=1e-14)
+    directed = {}
+    for t in F:
+        for a, b in ((t[0], t[1]), (t[1], t[2]), (t[2], t[0])):
+            directed[(a, b)] = directed.get((a, b), 0) + 1
+    assert all(n == 1 for n in directed.values())
+    assert all((b, a) in directed for a, b in directed)
+    assert len(V) - len(directed) // 2 + len(F) == 2
+    a, b, c = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    assert np.all(np.einsum("ij,ij->i", np.cross(b - a, c - a), a + b + c) > 0)
+    bend = O.bending(V * 7.0, F, 1.0)
+    assert np.isclose((bend["KG"] * bend["A"]).sum(), 4 * np.pi, rtol=1e-12)
