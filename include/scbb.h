@@ -46,7 +46,7 @@ typedef enum {
     SCBB_E_TIMEOUT = 5,      /* a bounded device wait gave up */
     SCBB_E_MESH = 6,         /* invalid mesh (index out of range, zero-area reference triangle, ...) */
     SCBB_E_STATE = 7,        /* context is in an error state */
-    SCBB_E_UNSUPPORTED = 8   /* a mode this build does not provide */
+    SCBB_E_UNSUPPORTED = 8   /* a mode the library does not provide for these arguments */
 } scbb_status;
 
 /* Lattice (Sec. II.A).  walls: 1 = solid planes z=0 and z=nz-1 with half-way bounce-back (Eq. 11, with the
