@@ -118,7 +118,9 @@ scbb_status scbb_set_density(scbb_ctx* ctx, const double* rhoA, const double* rh
  * Eq. 6-10, coupling, node update).  Asynchronous on the context stream.  After the context's first step,
  * pairs of steps are replayed from a CUDA graph captured on that stream (not while timing is enabled, and
  * never on the legacy default stream, where capture is not allowed: there every step launches its kernels
- * one by one; environment SCBB_GRAPHS=0 does the same everywhere).  The results do not depend on it. */
+ * one by one; environment SCBB_GRAPHS=0 does the same everywhere).  In a context with meshes, kernels whose
+ * inputs are ready early run on a second stream the context creates and joins back within the step
+ * (environment SCBB_OVERLAP=0 keeps them on the context stream).  The results do not depend on either. */
 scbb_status scbb_step(scbb_ctx* ctx, long long n);
 
 /* Wait for the context stream; reports device-side errors. */
