@@ -888,7 +888,16 @@ scbb_status scbb_autotune(scbb_ctx* c, int reps, int* chosen) {
     q.b4cfg = 0;
     if (!bulk_vectorised(q)) return SCBB_OK;      // the general bulk kernel has no shapes to choose from
     const int mode = (c->fl.coupling == 1 && c->d.NV > 0) ? 1 : 0;
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // both events are destroyed on every return below
+    struct Events {
+        cudaEvent_t* a;
+        cudaEvent_t* b;
+        ~Events() {
+            if (*a) cudaEventDestroy(*a);
+            if (*b) cudaEventDestroy(*b);
+        }
+    } guard{&e0, &e1};
     CUDA_TRY(c, cudaEventCreate(&e0));
     CUDA_TRY(c, cudaEventCreate(&e1));
     float best = 0.f;
@@ -913,8 +922,6 @@ scbb_status scbb_autotune(scbb_ctx* c, int reps, int* chosen) {
             best_k = k;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     c->lp.b4cfg = best_k;
     // the captured step pairs hold the old shape
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
