@@ -158,3 +158,19 @@ def test_janus_colour_per_element():
     assert not np.array_equal(f_uni, f_jan)
     _, z_neg = run(dataclasses.replace(base, colour=-0.6))
     assert min(z_uni, z_neg) - 1e-3 < z_jan < max(z_uni, z_neg) + 1e-3, (z_uni, z_jan, z_neg)
+
+
+def test_neutral_wetting_contact_angle():
+    """Young's law with equal particle-fluid tensions (colour 0, Eq. 15: no virtual-density offset) gives a
+    90-degree contact angle: the capsule's centre settles on the interface midplane (z = 11.5 between the last
+    A-rich plane 11 and the first B-rich plane 12, walls symmetric about it).  Started 2 above and 2 below, the
+    capsule moves to within 0.8 of the midplane in 300 steps, from both sides alike."""
+    off = []
+    for z0 in (13.5, 9.5):
+        cap = inputs.Capsule(centre=(10.0, 10.0, z0), radius=5.0, subdiv=3, kS=0.05, kB=0.0, kV=2.0, colour=0.0)
+        p = _bb(nx=20, ny=20, nz=24, walls=1, caps=[cap], z_interface=12, noise=0.0, G=3.6)
+        s = O.OracleSim(p)
+        s.step(300)
+        off.append(s.capsule(0)[1][2] - 11.5)
+    assert 0.0 < off[0] < 0.8 and -0.8 < off[1] < 0.0, off
+    assert abs(off[0] + off[1]) < 0.1, off
