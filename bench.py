@@ -1,5 +1,5 @@
 """Benchmark: two-component D3Q19 lattice updates per second (GLUPS) of the full coupled time step on one
-GB300, with the fused bulk kernel's fraction of the HBM roofline, an end-to-end figure through the C ABI
+GB300, with the bulk stream + collide phase's fraction of the HBM roofline, an end-to-end figure through the C ABI
 with host buffers, and the FP64 oracle timed on the host cores as a CPU baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
@@ -23,10 +23,11 @@ sys.path.insert(0, ROOT)
 
 from paper_1904_11386_gb300 import inputs  # noqa: E402
 
-# Algorithmic bytes per lattice update of the fused bulk kernel (both components): read 2 x 19 populations,
-# write 2 x 19 populations (4 bytes each in FP32 storage, 2 in FP16 or BF16), write rho^A and rho^B (FP32).
-BYTES_PER_LU = 2 * 19 * 4 * 2 + 2 * 4
-BYTES_PER_LU_16 = 2 * 19 * 2 * 2 + 2 * 4
+# Algorithmic bytes per lattice update (both components): read and write 2 x 19 populations (4 bytes each in
+# FP32 storage, 2 in FP16 or BF16), write rho^A and rho^B (FP32) and read them back (the Shan-Chen force needs
+# the neighbours' densities of the same time level): 320 B, or 168 B with 16-bit populations.
+BYTES_PER_LU = 2 * 19 * 4 * 2 + 2 * 4 + 2 * 4
+BYTES_PER_LU_16 = 2 * 19 * 2 * 2 + 2 * 4 + 2 * 4
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 # error against the FP64 oracle of each 16-bit storage, as the tests bound it
 STORAGE_ERROR = {
@@ -39,8 +40,8 @@ STORAGE_ERROR = {
 
 FALLBACK_HBM_GBS = 6800.0
 # the headline metric, the same string on both arms (the oracle's line carries it too)
-METRIC = ("2-component D3Q19 lattice updates per second, full coupled step (GLUPS); fused bulk kernel fraction of "
-          "HBM roofline")
+METRIC = ("2-component D3Q19 lattice updates per second, full coupled step (GLUPS); bulk stream+collide phase "
+          "fraction of HBM roofline")
 
 
 def bytes_per_lu(storage: str) -> int:
@@ -184,7 +185,7 @@ def recorded_traffic(workload_name: str):
     workload, or None when there is none or the kernel source changed since it was taken."""
     import re
 
-    path = os.path.join(ROOT, "profiles", f"k_bulk4_{workload_name}.md")
+    path = os.path.join(ROOT, "profiles", f"bulk_{workload_name}.md")
     try:
         txt = open(path).read()
     except OSError:
@@ -565,7 +566,7 @@ def main():
     achieved = bpl * n_upd / bulk_avg_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": recorded_traffic(args.workload + ("" if args.storage == "fp32" else "-" + args.storage)),
-            "kernel": "k_bulk4 (fused 2-component stream + Shan-Chen + collide)",
+            "kernel": "bulk phase: k_moments4 (stream, moments) + k_collide4 (Shan-Chen force, collide)",
             "bytes_per_lu": bpl, "units_per_launch": n_upd, "peak_source": src,
             "kernel_ms": bulk_avg_s * 1e3, "kernel_share": bulk_avg_s * 1e3 / (ms / args.steps) if ms > 0 else None,
             "kernel_timing": f"{bulk_n} bulk launches bracketed by CUDA events (second region of {args.steps} steps)"}

@@ -840,6 +840,314 @@ k_bulk4(LbmParams p, const T* __restrict__ S, T* __restrict__ D, float* __restri
     }
 }
 
+// ------------------------------------------------------------------------------------------------------
+// Bulk phase in two kernels (tau = 1, nx a multiple of 4): stream + moments, then force + collide.
+//
+// With tau = 1 the BGK update (Eq. 1) gives f* = f_eq(rho^c, u_eq^c) exactly, so the collision of a node needs
+// nothing of its populations beyond the five moments rho^A, rho^B, j.  The first kernel pulls every node's
+// populations once (Eq. 4, the stream) and writes those moments; it has no halo and no barrier, so it is a
+// plain streaming read at full occupancy.  The second reads the moments and stages psi of its tile's y-halo
+// rows and z-halo planes from the density field (8 bytes per node, L2 hits) instead of pulling 152 bytes
+// of populations for them, forms the Shan-Chen force (Eq. 13) and writes f_eq (Eq. 2) of every node.  The
+// moments make one round trip through L2 (20 bytes per node).
+// ------------------------------------------------------------------------------------------------------
+
+// Kernel A: one thread per four consecutive nodes of a row (float4 loads; the x-shifts of the pull are warp
+// shuffles, see pull4), every fluid node of the lattice once.  Writes rho^c to rho[c][n] and j to J[d][n],
+// summed over the directions in the same order as the fused kernel, so both give the same bits.
+template <typename T>
+__global__ void __launch_bounds__(256) k_moments4(LbmParams p, const T* __restrict__ S, float* __restrict__ rho,
+                                                  float* __restrict__ J) {
+    const int NQ = p.nx >> 2;
+    const unsigned int total = (unsigned)NQ * (unsigned)p.ny * (unsigned)(p.zf1 - p.zf0);
+    const unsigned int g0 = blockIdx.x * blockDim.x + threadIdx.x;
+    // a warp wholly past the end has nothing to do (it is never a shuffle partner of a live lane)
+    if (blockIdx.x * blockDim.x + (threadIdx.x & ~31u) >= total) return;
+    const bool live = g0 < total;
+    const unsigned int g = live ? g0 : total - 1;       // the tail of the last warp shadows the last quad
+    const unsigned int row = g / (unsigned)NQ;
+    const int q = (int)(g - row * (unsigned)NQ);
+    const int y = (int)(row % (unsigned)p.ny);
+    const int z = p.zf0 + (int)(row / (unsigned)p.ny);
+    const int x = 4 * q;
+    const int lane = threadIdx.x & 31;
+    // rows of a power-of-two number of quads up to 32 fill whole lane segments (their shuffle wrap is the
+    // periodic boundary); any other row shuffles across the warp and loads the element beyond a warp edge or
+    // the periodic wrap directly.  Live rows are whole, so a live lane's shuffle partner is live or loads.
+    const bool seg_rows = NQ <= 32 && (NQ & (NQ - 1)) == 0;
+    const int W = seg_rows ? NQ : 32;
+    const int segl = seg_rows ? (q & (W - 1)) : lane;
+    const int edge = seg_rows ? 0 : (((q == 0 || lane == 0) ? 1 : 0) | ((q == NQ - 1 || lane == 31) ? 2 : 0));
+    const int ry[3] = {(y == 0 ? p.ny - 1 : y - 1) * p.nx, y * p.nx, (y == p.ny - 1 ? 0 : y + 1) * p.nx};
+    Mom4 m;
+#pragma unroll
+    for (int k = 0; k < 4; k++) m.ra[k] = m.rb[k] = m.jx[k] = m.jy[k] = m.jz[k] = 0.f;
+    const PullCtx pc = pull_ctx(p, ry, z);
+    pull_all(p, S, pc, x, segl, W, edge, m, AllDirs{});
+    if (!live) return;
+    const unsigned int n0 = (unsigned)x + (unsigned)ry[1] + (unsigned)z * p.nxy;
+    *reinterpret_cast<float4*>(rho + n0) = make_float4(m.ra[0], m.ra[1], m.ra[2], m.ra[3]);
+    *reinterpret_cast<float4*>(rho + p.N + n0) = make_float4(m.rb[0], m.rb[1], m.rb[2], m.rb[3]);
+    *reinterpret_cast<float4*>(J + n0) = make_float4(m.jx[0], m.jx[1], m.jx[2], m.jx[3]);
+    *reinterpret_cast<float4*>(J + p.N + n0) = make_float4(m.jy[0], m.jy[1], m.jy[2], m.jy[3]);
+    *reinterpret_cast<float4*>(J + 2 * (size_t)p.N + n0) = make_float4(m.jz[0], m.jz[1], m.jz[2], m.jz[3]);
+}
+
+// Virtual densities of the four wall nodes (x .. x+3, yy) of wall plane z (neutral wetting of the walls):
+// the mean of the densities of the five nodes (x', yy, za), (x' +- 1, yy, za), (x', yy +- 1, za) of the
+// adjacent fluid plane za, summed in that order.
+__device__ __forceinline__ float4 wall_ghost4(const LbmParams& p, const float* __restrict__ a, int x, int yy,
+                                              int za) {
+    const float* row = a + (size_t)za * p.nxy + yy * p.nx;
+    const float* rm = a + (size_t)za * p.nxy + (yy == 0 ? p.ny - 1 : yy - 1) * p.nx;
+    const float* rp = a + (size_t)za * p.nxy + (yy == p.ny - 1 ? 0 : yy + 1) * p.nx;
+    const float4 c = *reinterpret_cast<const float4*>(row + x);
+    const float4 m = *reinterpret_cast<const float4*>(rm + x);
+    const float4 pl = *reinterpret_cast<const float4*>(rp + x);
+    const float left = row[x == 0 ? p.nx - 1 : x - 1], right = row[x + 4 == p.nx ? 0 : x + 4];
+    float4 g;
+    g.x = (c.x + left + c.y + m.x + pl.x) * 0.2f;
+    g.y = (c.y + c.x + c.z + m.y + pl.y) * 0.2f;
+    g.z = (c.z + c.y + c.w + m.z + pl.z) * 0.2f;
+    g.w = (c.w + c.z + right + m.w + pl.w) * 0.2f;
+    return g;
+}
+
+// Kernel B: a CTA owns TY whole rows and marches through a z-segment like the fused kernel; one thread per
+// quad of a tile row.  psi of the tile rows and the two halo rows, for the planes z - 1 .. z + 1, sits in a
+// four-plane shared ring filled from the density field (wall planes: the ghost densities, computed here from
+// the adjacent fluid plane and written out for the boundary kernel by the CTA that owns the rows).
+template <int MODE, int NT, int MINB, typename T>
+__global__ void __launch_bounds__(NT, MINB)
+k_collide4(LbmParams p, T* __restrict__ D, const float* __restrict__ rho, const float* __restrict__ J,
+           float* __restrict__ ghost, const float* __restrict__ Fibm, const uint32_t* __restrict__ mask,
+           float* __restrict__ u_out, int* __restrict__ err, int TY) {
+    constexpr bool IBM = MODE == 1;
+    extern __shared__ float ring[];                      // psi [4][2][RR][nx]
+    const int nx = p.nx;
+    const int NQ = nx >> 2;
+    const int RR = TY + 2;
+    const int t = threadIdx.x;
+    const int nreal = NQ * TY;
+    const int tr = t < nreal ? t : nreal - 1;
+    const int r = tr / NQ + 1;                           // ring row 1 .. TY (0 and TY + 1 are the halo rows)
+    const int q = tr - (r - 1) * NQ;
+    const int x = 4 * q;
+    const int y0 = blockIdx.x * TY;
+    const int gy = y0 + r - 1;
+    const bool active = t < nreal && gy < p.ny;
+    const int plane_sz = RR * nx;
+    const int ry[3] = {(gy == 0 ? p.ny - 1 : gy - 1) * nx, gy * nx, (gy + 1 >= p.ny ? 0 : gy + 1) * nx};
+
+    const int nzf = p.zf1 - p.zf0;
+    const int zs = p.zf0 + (int)(((long long)blockIdx.y * nzf) / gridDim.y);
+    const int ze = p.zf0 + (int)(((long long)(blockIdx.y + 1) * nzf) / gridDim.y);
+    if (zs >= ze) return;
+    const int dz = (blockIdx.y & 1) ? 1 : -1;
+    const int z_first = dz > 0 ? zs : ze - 1;
+    const int L = ze - zs;
+    auto zwrap = [&](int z) { return p.walls ? z : (z < 0 ? z + p.nz : (z >= p.nz ? z - p.nz : z)); };
+
+    // psi of plane z, all RR rows, into ring slot `slot`
+    auto fill = [&](int z, int slot) {
+        float* base = ring + (size_t)slot * 2 * plane_sz;
+        const bool wall = is_wall_plane(p, z);
+        const int w = z == 0 ? 0 : 1;
+        const int za = z == 0 ? 1 : p.nz - 2;
+        for (int idx = t; idx < RR * NQ; idx += blockDim.x) {
+            const int rr = idx / NQ, qq = idx - rr * NQ;
+            int yy = y0 - 1 + rr;
+            yy = yy < 0 ? yy + p.ny : (yy >= p.ny ? yy - p.ny : yy);
+            float4 a, b;
+            if (wall) {
+                a = wall_ghost4(p, rho, 4 * qq, yy, za);
+                b = wall_ghost4(p, rho + p.N, 4 * qq, yy, za);
+                if (rr >= 1 && rr <= TY && y0 + rr - 1 < p.ny) {
+                    *reinterpret_cast<float4*>(ghost + (w * 2 + 0) * p.nxy + yy * nx + 4 * qq) = a;
+                    *reinterpret_cast<float4*>(ghost + (w * 2 + 1) * p.nxy + yy * nx + 4 * qq) = b;
+                }
+            } else {
+                const size_t n = (size_t)z * p.nxy + yy * nx + 4 * qq;
+                a = *reinterpret_cast<const float4*>(rho + n);
+                b = *reinterpret_cast<const float4*>(rho + p.N + n);
+            }
+            *reinterpret_cast<float4*>(base + rr * nx + 4 * qq) =
+                make_float4(psi_fn(a.x, p.psi_kind), psi_fn(a.y, p.psi_kind), psi_fn(a.z, p.psi_kind),
+                            psi_fn(a.w, p.psi_kind));
+            *reinterpret_cast<float4*>(base + plane_sz + rr * nx + 4 * qq) =
+                make_float4(psi_fn(b.x, p.psi_kind), psi_fn(b.y, p.psi_kind), psi_fn(b.z, p.psi_kind),
+                            psi_fn(b.w, p.psi_kind));
+        }
+    };
+
+    fill(zwrap(z_first - dz), 0);
+    fill(z_first, 1);
+
+    for (int rel = 0; rel < L; rel++) {
+        const int z = z_first + rel * dz;
+        fill(zwrap(z + dz), (rel + 2) & 3);
+        // the node's own moments (issued before the barrier)
+        const unsigned int n0 = (unsigned)x + (unsigned)ry[1] + (unsigned)z * p.nxy;
+        float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f), b4 = a4, jx4 = a4, jy4 = a4, jz4 = a4;
+        if (active) {
+            a4 = *reinterpret_cast<const float4*>(rho + n0);
+            b4 = *reinterpret_cast<const float4*>(rho + p.N + n0);
+            jx4 = *reinterpret_cast<const float4*>(J + n0);
+            jy4 = *reinterpret_cast<const float4*>(J + p.N + n0);
+            jz4 = *reinterpret_cast<const float4*>(J + 2 * (size_t)p.N + n0);
+        }
+        __syncthreads();
+        if (!active) continue;
+        // ---- Shan-Chen force (Eq. 13) for the four nodes from the psi ring
+        float sa[3][4], sb[3][4];                       // sum_i w_i psi^A(x+c_i) c_i, same with psi^B
+#pragma unroll
+        for (int d = 0; d < 3; d++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) sa[d][k] = sb[d][k] = 0.f;
+        const int s_back = rel & 3, s_ahead = (rel + 2) & 3;
+        const float* slots[3] = {ring + (size_t)(dz > 0 ? s_back : s_ahead) * 2 * plane_sz,
+                                 ring + (size_t)((rel + 1) & 3) * 2 * plane_sz,
+                                 ring + (size_t)(dz > 0 ? s_ahead : s_back) * 2 * plane_sz};
+#pragma unroll
+        for (int cz = -1; cz <= 1; cz++)
+#pragma unroll
+            for (int cy = -1; cy <= 1; cy++) {
+                if (cy != 0 && cz != 0) {
+                    const float w = 1.f / 36.f;
+#pragma unroll
+                    for (int c = 0; c < 2; c++) {
+                        const float4 v = *reinterpret_cast<const float4*>(slots[1 + cz] + c * plane_sz +
+                                                                          (r + cy) * nx + x);
+                        const float V[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            if (c == 0) { sa[1][k] += w * cy * V[k]; sa[2][k] += w * cz * V[k]; }
+                            else { sb[1][k] += w * cy * V[k]; sb[2][k] += w * cz * V[k]; }
+                        }
+                    }
+                    continue;
+                }
+                const bool centre = cy == 0 && cz == 0;
+                const float wc = centre ? 0.f : 1.f / 18.f;
+                const float wx = centre ? 1.f / 18.f : 1.f / 36.f;
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    float w6[6];
+                    window6(slots[1 + cz] + c * plane_sz + (r + cy) * nx, x, nx, w6);
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        const float vm = w6[k], v0 = w6[k + 1], vp = w6[k + 2];
+                        const float fx = wx * (vp - vm);
+                        const float sum3 = wx * (vp + vm) + wc * v0;
+                        if (c == 0) {
+                            sa[0][k] += fx; sa[1][k] += cy * sum3; sa[2][k] += cz * sum3;
+                        } else {
+                            sb[0][k] += fx; sb[1][k] += cy * sum3; sb[2][k] += cz * sum3;
+                        }
+                    }
+                }
+            }
+
+        uint32_t bits = 0;
+        if (IBM) bits = (__ldg(mask + (n0 >> 5)) >> (n0 & 31)) & 0xFu;
+        const float ra[4] = {a4.x, a4.y, a4.z, a4.w}, rb[4] = {b4.x, b4.y, b4.z, b4.w};
+        const float jxa[4] = {jx4.x, jx4.y, jx4.z, jx4.w}, jya[4] = {jy4.x, jy4.y, jy4.z, jy4.w},
+                    jza[4] = {jz4.x, jz4.y, jz4.z, jz4.w};
+        float uA[4][3], uB[4][3];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float pa = psi_fn(ra[k], p.psi_kind), pb = psi_fn(rb[k], p.psi_kind);
+            const float rt = ra[k] + rb[k];
+            const float irt = 1.f / rt;
+            float FA[3], FB[3];
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                FA[d] = -pa * p.G * sb[d][k] + ra[k] * p.g[d];
+                FB[d] = -pb * p.G * sa[d][k] + rb[k] * p.g[d];
+            }
+            if (IBM && ((bits >> k) & 1u)) {
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    const float fi = Fibm[(size_t)d * p.N + n0 + k];
+                    FA[d] += ra[k] * irt * fi;
+                    FB[d] += rb[k] * irt * fi;
+                }
+            }
+            const float ux = jxa[k] * irt, uy = jya[k] * irt, uz = jza[k] * irt;
+            if (!(rt > 0.f) || !(ux * ux + uy * uy + uz * uz <= 0.09f)) atomicOr(err, 1);
+            const float ta = ra[k] > 0.f ? p.tau / ra[k] : 0.f, tb = rb[k] > 0.f ? p.tau / rb[k] : 0.f;
+            uA[k][0] = ux + ta * FA[0]; uA[k][1] = uy + ta * FA[1]; uA[k][2] = uz + ta * FA[2];
+            uB[k][0] = ux + tb * FB[0]; uB[k][1] = uy + tb * FB[1]; uB[k][2] = uz + tb * FB[2];
+            if (IBM && ((bits >> k) & 1u)) {
+                u_out[n0 + k] = (jxa[k] + 0.5f * (FA[0] + FB[0])) * irt;
+                u_out[(size_t)p.N + n0 + k] = (jya[k] + 0.5f * (FA[1] + FB[1])) * irt;
+                u_out[(size_t)2 * p.N + n0 + k] = (jza[k] + 0.5f * (FA[2] + FB[2])) * irt;
+            }
+        }
+        // ---- equilibrium (Eq. 2) = the post-collision populations, direction by direction, float4 stores
+        const bool wall_next = p.walls && (z == 1 || z == p.nz - 2);
+        float uuA[4], uuB[4], sA[4], sB[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            uuA[k] = uA[k][0] * uA[k][0] + uA[k][1] * uA[k][1] + uA[k][2] * uA[k][2];
+            uuB[k] = uB[k][0] * uB[k][0] + uB[k][1] * uB[k][1] + uB[k][2] * uB[k][2];
+            sA[k] = sB[k] = 0.f;
+        }
+        auto emit = [&](auto Ic) {
+            constexpr int I = decltype(Ic)::value;
+            float oA[4], oB[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                float eA, eB;
+                if (I == 0) {
+                    eA = ra[k] - sA[k];
+                    eB = rb[k] - sB[k];
+                    if (sizeof(T) == 2) {       // unbiased rounding of the mass-closing value
+                        const uint32_t h = dither_bits(n0 + k, ra[k], rb[k]);
+                        eA = pdither(eA, h >> 16, D);
+                        eB = pdither(eB, h & 0xffffu, D);
+                    }
+                } else {
+                    const float cuA = dir_x(I) * uA[k][0] + dir_y(I) * uA[k][1] + dir_z(I) * uA[k][2];
+                    const float cuB = dir_x(I) * uB[k][0] + dir_y(I) * uB[k][1] + dir_z(I) * uB[k][2];
+                    eA = pround(dir_w(I) * ra[k] * (1.f + 3.f * cuA + 4.5f * cuA * cuA - 1.5f * uuA[k]), D);
+                    eB = pround(dir_w(I) * rb[k] * (1.f + 3.f * cuB + 4.5f * cuB * cuB - 1.5f * uuB[k]), D);
+                    sA[k] += eA;
+                    sB[k] += eB;
+                }
+                oA[k] = eA;
+                oB[k] = eB;
+            }
+            if (dir_z(I) != 0 && wall_next && is_wall_plane(p, z + dir_z(I))) {
+                // half-way bounce-back on a moving wall (Eq. 11), stored where the node pulls opp(I) from
+                const float* U = (z + dir_z(I) == 0) ? p.ulo : p.uhi;
+                const float cU = 6.f * dir_w(I) * (dir_x(I) * U[0] + dir_y(I) * U[1] + dir_z(I) * U[2]);
+                const unsigned int drow = (unsigned)ry[1 + dir_y(I)] + (unsigned)(z + dir_z(I)) * p.nxy;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    int xd = x + k + dir_x(I);
+                    xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
+                    pst(D + (size_t)dir_opp(I) * p.N + drow + xd, oA[k] - cU * ra[k]);
+                    pst(D + (size_t)(Q + dir_opp(I)) * p.N + drow + xd, oB[k] - cU * rb[k]);
+                }
+            } else {
+                pst4(D + (size_t)I * p.N + n0, make_float4(oA[0], oA[1], oA[2], oA[3]));
+                pst4(D + (size_t)(Q + I) * p.N + n0, make_float4(oB[0], oB[1], oB[2], oB[3]));
+            }
+        };
+        emit(std::integral_constant<int, 1>{});  emit(std::integral_constant<int, 2>{});
+        emit(std::integral_constant<int, 3>{});  emit(std::integral_constant<int, 4>{});
+        emit(std::integral_constant<int, 5>{});  emit(std::integral_constant<int, 6>{});
+        emit(std::integral_constant<int, 7>{});  emit(std::integral_constant<int, 8>{});
+        emit(std::integral_constant<int, 9>{});  emit(std::integral_constant<int, 10>{});
+        emit(std::integral_constant<int, 11>{}); emit(std::integral_constant<int, 12>{});
+        emit(std::integral_constant<int, 13>{}); emit(std::integral_constant<int, 14>{});
+        emit(std::integral_constant<int, 15>{}); emit(std::integral_constant<int, 16>{});
+        emit(std::integral_constant<int, 17>{}); emit(std::integral_constant<int, 18>{});
+        emit(std::integral_constant<int, 0>{});
+    }
+}
+
 // Tile height (rows per CTA) of the row-vectorised kernel with nthreads threads, or 0 if it does not fit.
 static int bulk4_rows(const LbmParams& p, int nthreads) {
     if (p.nx % 4) return 0;
@@ -864,11 +1172,13 @@ static int bulk4_rows(const LbmParams& p, int nthreads) {
 
 constexpr int BTX = 32, BTY = 8;
 
+// SCBB_BULK_VARIANT: unset -> the two-kernel bulk phase where it applies (tau = 1, nx a multiple of 4), else
+// the fused row-vectorised kernel; "4": always the fused row-vectorised kernel; "1", "2": the tile kernels.
 static int bulk_variant() {
     static int v = -1;
     if (v < 0) {
         const char* e = getenv("SCBB_BULK_VARIANT");
-        v = (e && (e[0] == '1' || e[0] == '2')) ? e[0] - '0' : 4;
+        v = (e && (e[0] == '1' || e[0] == '2' || e[0] == '4')) ? e[0] - '0' : 5;
     }
     return v;
 }
@@ -978,15 +1288,113 @@ static bool dispatch_b4(const LbmParams& p, const float* S, float* D, float* rho
     }
 }
 
+// ---- the two-kernel bulk phase (tau = 1, nx a multiple of 4)
+
+// Shapes of kernel B: (threads per CTA, CTAs per SM, fewest planes per z-segment), chosen by b4cfg.
+struct SplitShape {
+    int nt, cps, min_planes;
+};
+static SplitShape split_shape(int cfg) {
+    switch (cfg) {
+        case 1: return {512, 1, 4};
+        case 2: return {256, 2, 8};
+        case 3: return {128, 4, 4};
+        default: return {256, 2, 4};
+    }
+}
+
+bool bulk_split(const LbmParams& p) {
+    if (bulk_variant() != 5) return false;
+    if (p.omega != 1.0f || p.nx % 4) return false;
+    const SplitShape sh = split_shape(p.b4cfg);
+    return p.nx / 4 <= sh.nt;
+}
+
+static bool split_geometry(const LbmParams& p, dim3& grid, int& threads, int& TY, size_t& smem) {
+    const SplitShape sh = split_shape(p.b4cfg);
+    const int NQ = p.nx / 4;
+    if (NQ > sh.nt) return false;
+    TY = sh.nt / NQ;
+    if (TY > p.ny) TY = p.ny;
+    threads = (NQ * TY + 31) / 32 * 32;
+    const int cols = (p.ny + TY - 1) / TY;
+    const int nzf = p.zf1 - p.zf0;
+    const int slots = 152 * sh.cps;
+    int nseg = 1;
+    double best = -1.0;
+    for (int w = 1; w <= 4; w++) {
+        int ns = (slots * w) / cols;
+        if (ns < 1) ns = 1;
+        const int cap = nzf / sh.min_planes > 0 ? nzf / sh.min_planes : 1;
+        if (ns > cap) ns = cap;
+        const int nb = cols * ns;
+        const int waves = (nb + slots - 1) / slots;
+        const double eff = (double)nb / ((double)slots * waves) - 0.02 * waves;
+        if (eff > best + 1e-9) { best = eff; nseg = ns; }
+    }
+    grid = dim3(cols, nseg, 1);
+    smem = (size_t)4 * 2 * (TY + 2) * p.nx * sizeof(float);
+    return true;
+}
+
+template <int MODE, int NT, int MINB, typename T>
+static void launch_c4t(const LbmParams& p, dim3 grid, int threads, size_t smem, int TY, T* D, const float* rho,
+                       const float* J, float* ghost, const float* Fibm, const uint32_t* mask, float* u, int* err,
+                       cudaStream_t st) {
+    static size_t attr = 0;
+    if (smem > attr) {
+        cudaFuncSetAttribute(k_collide4<MODE, NT, MINB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = smem;
+    }
+    k_collide4<MODE, NT, MINB, T><<<grid, threads, smem, st>>>(p, D, rho, J, ghost, Fibm, mask, u, err, TY);
+}
+
+template <int NT, int MINB, typename T>
+static void launch_c4m(int mode, const LbmParams& p, dim3 grid, int threads, size_t smem, int TY, T* D,
+                       const float* rho, const float* J, float* ghost, const float* Fibm, const uint32_t* mask,
+                       float* u, int* err, cudaStream_t st) {
+    if (mode == 1) launch_c4t<1, NT, MINB, T>(p, grid, threads, smem, TY, D, rho, J, ghost, Fibm, mask, u, err, st);
+    else launch_c4t<0, NT, MINB, T>(p, grid, threads, smem, TY, D, rho, J, ghost, Fibm, mask, u, err, st);
+}
+
+static void launch_split(const LbmParams& p, const float* S, float* D, float* rho, float* J, float* ghost,
+                         const float* Fibm, const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st) {
+    dim3 grid;
+    int threads, TY;
+    size_t smem;
+    split_geometry(p, grid, threads, TY, smem);
+    const unsigned int quads = (unsigned)(p.nx / 4) * p.ny * (p.zf1 - p.zf0);
+    with_storage(p.store, [&](auto* tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        k_moments4<T><<<(quads + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<const T*>(S), rho, J);
+        T* Dt = reinterpret_cast<T*>(D);
+        switch (p.b4cfg) {
+            case 1: launch_c4m<512, 1, T>(mode, p, grid, threads, smem, TY, Dt, rho, J, ghost, Fibm, mask, u, err, st); break;
+            case 3: launch_c4m<128, 4, T>(mode, p, grid, threads, smem, TY, Dt, rho, J, ghost, Fibm, mask, u, err, st); break;
+            default: launch_c4m<256, 2, T>(mode, p, grid, threads, smem, TY, Dt, rho, J, ghost, Fibm, mask, u, err, st); break;
+        }
+    });
+}
+
 bool bulk_vectorised(const LbmParams& p) {
+    if (bulk_split(p)) return true;
     int nb = 0;
-    return bulk_variant() == 4 && dispatch_b4(p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+    return bulk_variant() >= 4 && dispatch_b4(p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                                               nullptr, 0, 0, &nb);
 }
 
+bool bulk_writes_ghost(const LbmParams& p) { return bulk_split(p); }
+
 int bulk_grid_blocks(const LbmParams& p) {
     int nb = 0;
-    if (bulk_variant() == 4 && dispatch_b4(p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+    if (bulk_split(p)) {
+        dim3 g;
+        int th, ty;
+        size_t sm;
+        split_geometry(p, g, th, ty, sm);
+        return (int)(g.x * g.y);
+    }
+    if (bulk_variant() >= 4 && dispatch_b4(p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                                            0, 0, &nb))
         return nb;
     dim3 g;
@@ -995,10 +1403,14 @@ int bulk_grid_blocks(const LbmParams& p) {
     return (int)(g.x * g.y * g.z);
 }
 
-void launch_bulk(const LbmParams& p, const float* S, float* D, float* rho, const float* ghost, const float* Fibm,
+void launch_bulk(const LbmParams& p, const float* S, float* D, float* rho, float* J, float* ghost, const float* Fibm,
                  const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st) {
     const bool ibm = mode == 1;
-    if (bulk_variant() == 4 && dispatch_b4(p, S, D, rho, ghost, Fibm, mask, u, err, mode, st, nullptr)) return;
+    if (J && bulk_split(p)) {
+        launch_split(p, S, D, rho, J, ghost, Fibm, mask, u, err, mode, st);
+        return;
+    }
+    if (bulk_variant() >= 4 && dispatch_b4(p, S, D, rho, ghost, Fibm, mask, u, err, mode, st, nullptr)) return;
     dim3 grid;
     int threads;
     bulk_geometry(p, grid, threads);

@@ -195,6 +195,7 @@ size_t layout(const scbb_lattice* lat, const scbb_fluid* fl, int nm, const scbb_
     t.S[0] = c.take<float>(pop_floats);
     t.S[1] = c.take<float>(pop_floats);
     t.rho = c.take<float>(2 * N);
+    t.J = c.take<float>(3 * N);
     const bool ibm = fl->coupling == 1 && NV > 0;
     t.u = ibm ? c.take<float>(3 * N) : nullptr;
     t.Fibm = ibm ? c.take<float>(3 * N) : nullptr;
@@ -527,7 +528,9 @@ static void enqueue_step(scbb_ctx* c, bool allow_side = true) {
     // With the immersed boundary, the wall ghosts (they read the populations alone) run there beside the
     // membrane forces and the spreading (they read the vertices alone), joined before the bulk kernel.
     const bool side = allow_side && bb && c->side && overlap_enabled() && c->timing != 2;
-    const bool side_walls = allow_side && ibm && c->lp.walls && c->side && overlap_enabled() && c->timing != 2;
+    // the two-kernel bulk phase computes the wall ghost densities itself
+    const bool ghost_pass = c->lp.walls && !bulk_writes_ghost(c->lp);
+    const bool side_walls = allow_side && ibm && ghost_pass && c->side && overlap_enabled() && c->timing != 2;
     c->mark(0);
     if (side_walls) {
         cudaEventRecord(c->ev_fork, c->st);
@@ -549,7 +552,7 @@ static void enqueue_step(scbb_ctx* c, bool allow_side = true) {
         c->launches += 1;
     }
     c->mark(1);
-    if (c->lp.walls) {
+    if (ghost_pass) {
         if (side_walls) cudaStreamWaitEvent(c->st, c->ev_join, 0);
         else launch_wall_ghost(c->lp, c->d.S[c->cur], c->d.wall_rho, c->d.ghost, c->st);
         c->launches += 2;
@@ -557,13 +560,13 @@ static void enqueue_step(scbb_ctx* c, bool allow_side = true) {
     c->mark(2);
     const bool timed = c->timing && c->ev_used + 2 <= c->ev.size();
     if (timed) cudaEventRecord(c->ev[c->ev_used], c->st);
-    launch_bulk(c->lp, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.rho, c->d.ghost, c->d.Fibm,
+    launch_bulk(c->lp, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.rho, c->d.J, c->d.ghost, c->d.Fibm,
                 c->d.mask, c->d.u, c->d.err, mode, c->st);
     if (timed) {
         cudaEventRecord(c->ev[c->ev_used + 1], c->st);
         c->ev_used += 2;
     }
-    c->launches++;
+    c->launches += bulk_split(c->lp) ? 2 : 1;
     c->mark(3);
     if (ibm) {
         launch_ibm_interp(c->lp, c->d, c->st);
@@ -909,7 +912,7 @@ scbb_status scbb_autotune(scbb_ctx* c, int reps, int* chosen) {
         if (!bulk_vectorised(q)) continue;
         for (int r = 0; r <= reps; r++) {
             if (r == 1) CUDA_TRY(c, cudaEventRecord(e0, c->st));
-            launch_bulk(q, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.rho, c->d.ghost, c->d.Fibm, c->d.mask, c->d.u,
+            launch_bulk(q, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.rho, c->d.J, c->d.ghost, c->d.Fibm, c->d.mask, c->d.u,
                         c->d.err, mode, c->st);
             c->launches++;
         }
@@ -1178,8 +1181,9 @@ scbb_status scbb_adjoint_backward(scbb_adjoint* a, const double* gA, const doubl
         const size_t nw = (size_t)4 * c->lp.nxy;
         for (int k = 0; k < len; k++) {
             float* gh = c->lp.walls ? a->Gh + (size_t)k * nw : c->d.ghost;
-            if (c->lp.walls) launch_wall_ghost(c->lp, a->L + (size_t)k * lat, c->d.wall_rho, gh, c->st);
-            launch_bulk(c->lp, a->L + (size_t)k * lat, a->L + (size_t)(k + 1) * lat, a->R + (size_t)k * 2 * N, gh,
+            if (c->lp.walls && !bulk_writes_ghost(c->lp))
+                launch_wall_ghost(c->lp, a->L + (size_t)k * lat, c->d.wall_rho, gh, c->st);
+            launch_bulk(c->lp, a->L + (size_t)k * lat, a->L + (size_t)(k + 1) * lat, a->R + (size_t)k * 2 * N, c->d.J, gh,
                         nullptr, nullptr, nullptr, c->d.err, 0, c->st);
         }
         for (int k = len - 1; k >= 0; k--) {
@@ -1188,7 +1192,8 @@ scbb_status scbb_adjoint_backward(scbb_adjoint* a, const double* gA, const doubl
                             a->lam[1 - cur], a->scr, a->gw, a->part, c->st);
             cur ^= 1;
         }
-        c->launches += (c->lp.walls ? 6 : 3) * len;
+        c->launches += ((c->lp.walls ? 5 : 2) + (bulk_split(c->lp) ? 2 : 1) -
+                        (c->lp.walls && bulk_writes_ghost(c->lp) ? 2 : 0)) * len;
         CUDA_TRY(c, cudaGetLastError());
     }
     launch_adj_initial(c->lp, a->ckpt, a->lam[cur], a->g, c->st);

@@ -156,6 +156,7 @@ struct CapDev {
 struct DevState {
     float* S[2];            // populations, 2 * 19 * N values each, of the type LbmParams::store names
     float* rho;             // [2][N] densities of the last collision
+    float* J;               // [3][N] momentum of the last stream (two-kernel bulk phase)
     float* u;               // [3][N] velocity incl. half force, written where the IBM mask is set
     float* Fibm;            // [3][N] spread immersed-boundary force density
     uint32_t* mask;         // [ceil(N/32)] IBM stencil bits
@@ -273,9 +274,13 @@ __device__ __forceinline__ void pull(const LbmParams& p, const T* __restrict__ S
 void launch_init_state(const LbmParams& p, float* S, const float* rho_st, const float* u_st, cudaStream_t st);
 void launch_wall_ghost(const LbmParams& p, const float* S, float* wall_rho, float* ghost, cudaStream_t st);
 // mode 0: fluid only (also with bounce-back membranes), 1: immersed boundary (mask = IBM stencil bits)
-void launch_bulk(const LbmParams& p, const float* S, float* D, float* rho, const float* ghost,
+// J: [3][N] momentum scratch of the two-kernel bulk phase (tau = 1, nx a multiple of 4), which also writes the
+// wall ghost densities itself (bulk_writes_ghost); with J null the fused kernels run
+void launch_bulk(const LbmParams& p, const float* S, float* D, float* rho, float* J, float* ghost,
                  const float* Fibm, const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st);
 bool bulk_vectorised(const LbmParams& p);
+bool bulk_split(const LbmParams& p);
+bool bulk_writes_ghost(const LbmParams& p);
 void launch_export(const LbmParams& p, const float* S, float* out, int what, cudaStream_t st);
 void launch_moments_reduce(const LbmParams& p, const float* S, double* red, cudaStream_t st);
 int bulk_grid_blocks(const LbmParams& p);
