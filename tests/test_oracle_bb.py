@@ -174,3 +174,65 @@ def test_neutral_wetting_contact_angle():
         off.append(s.capsule(0)[1][2] - 11.5)
     assert 0.0 < off[0] < 0.8 and -0.8 < off[1] < 0.0, off
     assert abs(off[0] + off[1]) < 0.1, off
+
+
+@pytest.mark.parametrize("eta, regime", [(2e-3, "inside"), (0.08, "min"), (-0.08, "max")])
+def test_fresh_node_density_eq18_closed_form(eta, regime):
+    """Eq. 16 and Eq. 18 (Sec. II.E) on a state built so that every input of the fresh-node density is known:
+    a resting capsule (no wetting, G = 0) in a periodic box whose densities carry a smooth designed pattern
+    scaled by (1 + eps) after the initial mass M0 was taken.  Collision, streaming and resting bounce-back
+    conserve each component's mass exactly, so M^c(t) - M^c(0) = eps M0^c, and the factor of Eq. 18 is
+    1 - C0 (rho_init^A + rho_init^B) / rho_init^c * eps M0^c / V_sys = 1 - C0 eps (M0^A + M0^B) / V_sys = 1 - eta
+    for both components.  The capsule is then displaced by a fixed vector (zero velocity), so the
+    classification at the end of the step makes the nodes between the old and the new surface fresh.  Each
+    fresh node must carry the mean density of its non-fresh neighbours on its new side times (1 - eta),
+    clamped to their range: unclamped for eta = 2e-3, at the neighbours' minimum for eta = 0.08 (an excess of
+    mass lowers the fresh densities) and at their maximum for eta = -0.08."""
+    n, C0 = 24, 2500.0
+    cap = inputs.Capsule(centre=(11.6, 12.2, 11.9), radius=6.0, subdiv=3, kS=0.05, kB=0.0, kV=2.0, colour=0.0)
+    p = _bb(nx=n, ny=n, nz=n, walls=0, caps=[cap], G=0.0, noise=0.0, C0=C0)
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    A0 = 0.7 * (1 + 0.05 * np.cos(2 * np.pi * x / n) + 0.03 * np.sin(2 * np.pi * (y + 2 * z) / n))
+    B0 = 0.042 * (1 + 0.04 * np.sin(2 * np.pi * (x + y) / n) + 0.05 * np.cos(2 * np.pi * z / n))
+    s = O.OracleSim(p, A0, B0)
+    N = n ** 3
+    M0 = np.array([A0.sum(), B0.sum()])
+    eps = eta / (C0 * M0.sum() / N)
+    # the state at rest with densities (1 + eps) rho0: f_i = w_i (1 + eps) rho0 (Eq. 2 with u = 0)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    f = np.empty((2, N, 19))
+    f[0] = (1 + eps) * A0.ravel()[:, None] * w[None, :]
+    f[1] = (1 + eps) * B0.ravel()[:, None] * w[None, :]
+    s.set_populations(f)
+    own0 = s.owner().copy()
+    X, _, _ = s.vertices()
+    s.set_vertices(X + np.array([0.45, -0.3, 0.2]), np.zeros_like(X))
+    s.step(1)
+    own1 = s.owner()
+    a, b, _ = s.fields()
+    fresh = (own1 != own0)
+    assert fresh.sum() >= 50
+    c, _, _ = O.d3q19()
+    checked = clamped = 0
+    for zz, yy, xx in zip(*np.nonzero(fresh)):
+        side = own1[zz, yy, xx]
+        nb = [((zz + c[i, 2]) % n, (yy + c[i, 1]) % n, (xx + c[i, 0]) % n) for i in range(1, 19)]
+        nb = [m for m in nb if own1[m] == side and not fresh[m]]
+        if not nb:
+            continue
+        checked += 1
+        for rho, fr in ((a, a[zz, yy, xx]), (b, b[zz, yy, xx])):
+            v = np.array([rho[m] for m in nb])
+            raw = v.mean() * (1 - eta)
+            exp = min(max(raw, v.min()), v.max())
+            clamped += raw != exp
+            # M(t) - M(0) is a difference of two FP64 sums over N nodes (rounding ~ N 2^-53 M, a few 1e-15 of M
+            # here), which Eq. 18 multiplies by C0 sum(rho_init) / rho_init^c / V_sys (up to ~3 for B)
+            assert abs(fr - exp) < 1e-10 * exp, (regime, fr, exp)
+            if regime == "min":
+                assert exp == v.min()
+            elif regime == "max":
+                assert exp == v.max()
+    assert checked >= 0.9 * fresh.sum()
+    if regime == "inside":
+        assert clamped < 0.5 * 2 * checked, (clamped, checked)
