@@ -913,6 +913,24 @@ __device__ __forceinline__ float4 wall_ghost4(const LbmParams& p, const float* _
     return g;
 }
 
+// c_i . v for direction I with only the nonzero terms (a product by a zero component is not folded away
+// under IEEE rules)
+template <int I>
+__device__ __forceinline__ float cdot(float vx, float vy, float vz) {
+    float r = 0.f;
+    bool first = true;
+    auto add = [&](int c, float v) {
+        if (c == 0) return;
+        const float t = c > 0 ? v : -v;
+        r = first ? t : r + t;
+        first = false;
+    };
+    add(dir_x(I), vx);
+    add(dir_y(I), vy);
+    add(dir_z(I), vz);
+    return r;
+}
+
 // Kernel B: a CTA owns TY whole rows and marches through a z-segment like the fused kernel; one thread per
 // quad of a tile row.  psi of the tile rows and the two halo rows, for the planes z - 1 .. z + 1, sits in a
 // four-plane shared ring filled from the density field (wall planes: the ghost densities, computed here from
@@ -948,122 +966,148 @@ k_collide4(LbmParams p, T* __restrict__ D, const float* __restrict__ rho, const 
     const int L = ze - zs;
     auto zwrap = [&](int z) { return p.walls ? z : (z < 0 ? z + p.nz : (z >= p.nz ? z - p.nz : z)); };
 
-    // psi of plane z, all RR rows, into ring slot `slot`
-    auto fill = [&](int z, int slot) {
-        float* base = ring + (size_t)slot * 2 * plane_sz;
-        const bool wall = is_wall_plane(p, z);
-        const int w = z == 0 ? 0 : 1;
-        const int za = z == 0 ? 1 : p.nz - 2;
-        for (int idx = t; idx < RR * NQ; idx += blockDim.x) {
-            const int rr = idx / NQ, qq = idx - rr * NQ;
-            int yy = y0 - 1 + rr;
-            yy = yy < 0 ? yy + p.ny : (yy >= p.ny ? yy - p.ny : yy);
-            float4 a, b;
-            if (wall) {
-                a = wall_ghost4(p, rho, 4 * qq, yy, za);
-                b = wall_ghost4(p, rho + p.N, 4 * qq, yy, za);
-                if (rr >= 1 && rr <= TY && y0 + rr - 1 < p.ny) {
-                    *reinterpret_cast<float4*>(ghost + (w * 2 + 0) * p.nxy + yy * nx + 4 * qq) = a;
-                    *reinterpret_cast<float4*>(ghost + (w * 2 + 1) * p.nxy + yy * nx + 4 * qq) = b;
-                }
-            } else {
-                const size_t n = (size_t)z * p.nxy + yy * nx + 4 * qq;
-                a = *reinterpret_cast<const float4*>(rho + n);
-                b = *reinterpret_cast<const float4*>(rho + p.N + n);
-            }
-            *reinterpret_cast<float4*>(base + rr * nx + 4 * qq) =
-                make_float4(psi_fn(a.x, p.psi_kind), psi_fn(a.y, p.psi_kind), psi_fn(a.z, p.psi_kind),
-                            psi_fn(a.w, p.psi_kind));
-            *reinterpret_cast<float4*>(base + plane_sz + rr * nx + 4 * qq) =
-                make_float4(psi_fn(b.x, p.psi_kind), psi_fn(b.y, p.psi_kind), psi_fn(b.z, p.psi_kind),
-                            psi_fn(b.w, p.psi_kind));
+    // Ring fill, software-pipelined: thread t fills the quad of its own tile row (t < nreal) and, for t < 2 NQ,
+    // one quad of the halo row below (t < NQ) or above.  The densities of plane z + 2 are loaded before plane z's
+    // barrier and written into the ring one plane later, so their latency hides behind the collision.  A thread's own densities come from its fill.  Wall planes hold the ghost densities,
+    // computed here from the adjacent fluid plane; the CTA that owns the rows writes them out for the boundary
+    // kernel.
+    struct Fill {
+        float4 a, b;
+    };
+    const bool own_q = t < nreal;
+    const bool halo_q = t < 2 * NQ;
+    const int hr = t < NQ ? 0 : TY + 1;                  // ring row of the halo quad
+    const int hx = 4 * (t < NQ ? t : t - NQ);
+    int hy = hr == 0 ? y0 - 1 : y0 + TY;
+    hy = hy < 0 ? hy + p.ny : (hy >= p.ny ? hy - p.ny : hy);
+    const int gyw = gy >= p.ny ? gy - p.ny : gy;          // rows past ny (last tile) wrap, and are not collided
+    // densities (ghost densities on a wall plane) of plane z at the quad (xq, yq)
+    auto load_q = [&](int z, int xq, int yq, float4& a, float4& b) {
+        if (is_wall_plane(p, z)) {
+            const int za = z == 0 ? 1 : p.nz - 2;
+            a = wall_ghost4(p, rho, xq, yq, za);
+            b = wall_ghost4(p, rho + p.N, xq, yq, za);
+        } else {
+            const size_t n = (size_t)z * p.nxy + yq * nx + xq;
+            a = *reinterpret_cast<const float4*>(rho + n);
+            b = *reinterpret_cast<const float4*>(rho + p.N + n);
         }
     };
+    auto load = [&](int z) {
+        Fill f;
+        f.a = f.b = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (own_q) load_q(z, x, gyw, f.a, f.b);
+        return f;
+    };
+    auto psi4 = [&](float4 v) {
+        return make_float4(psi_fn(v.x, p.psi_kind), psi_fn(v.y, p.psi_kind), psi_fn(v.z, p.psi_kind),
+                           psi_fn(v.w, p.psi_kind));
+    };
+    auto store = [&](int z, int slot, const Fill& f) {
+        float* base = ring + (size_t)slot * 2 * plane_sz;
+        if (own_q) {
+            *reinterpret_cast<float4*>(base + r * nx + x) = psi4(f.a);
+            *reinterpret_cast<float4*>(base + plane_sz + r * nx + x) = psi4(f.b);
+            if (active && is_wall_plane(p, z)) {
+                const int w = z == 0 ? 0 : 1;
+                *reinterpret_cast<float4*>(ghost + (w * 2 + 0) * p.nxy + gy * nx + x) = f.a;
+                *reinterpret_cast<float4*>(ghost + (w * 2 + 1) * p.nxy + gy * nx + x) = f.b;
+            }
+        }
+        if (halo_q) {
+            float4 ha, hb;
+            load_q(z, hx, hy, ha, hb);
+            *reinterpret_cast<float4*>(base + hr * nx + hx) = psi4(ha);
+            *reinterpret_cast<float4*>(base + plane_sz + hr * nx + hx) = psi4(hb);
+        }
+    };
+    auto load_j = [&](int z, float4& jx, float4& jy, float4& jz) {
+        const size_t n = (size_t)x + (size_t)ry[1] + (size_t)z * p.nxy;
+        jx = *reinterpret_cast<const float4*>(J + n);
+        jy = *reinterpret_cast<const float4*>(J + p.N + n);
+        jz = *reinterpret_cast<const float4*>(J + 2 * (size_t)p.N + n);
+    };
 
-    fill(zwrap(z_first - dz), 0);
-    fill(z_first, 1);
+    float4 a4, b4, jx4, jy4, jz4;                        // densities and momentum of the plane being collided
+    jx4 = jy4 = jz4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    {
+        const int zb = zwrap(z_first - dz);
+        store(zb, 0, load(zb));
+        const Fill f1 = load(z_first);
+        store(z_first, 1, f1);
+        a4 = f1.a;
+        b4 = f1.b;
+        if (active) load_j(z_first, jx4, jy4, jz4);
+    }
+    Fill fn = load(zwrap(z_first + dz));
 
     for (int rel = 0; rel < L; rel++) {
         const int z = z_first + rel * dz;
-        fill(zwrap(z + dz), (rel + 2) & 3);
-        // the node's own moments (issued before the barrier)
+        store(zwrap(z + dz), (rel + 2) & 3, fn);
+        const float4 an = fn.a, bn = fn.b;               // own densities of plane z + 1
+        if (rel + 1 < L) fn = load(zwrap(z + 2 * dz));
+        if (active && rel > 0) load_j(z, jx4, jy4, jz4);
         const unsigned int n0 = (unsigned)x + (unsigned)ry[1] + (unsigned)z * p.nxy;
-        float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f), b4 = a4, jx4 = a4, jy4 = a4, jz4 = a4;
-        if (active) {
-            a4 = *reinterpret_cast<const float4*>(rho + n0);
-            b4 = *reinterpret_cast<const float4*>(rho + p.N + n0);
-            jx4 = *reinterpret_cast<const float4*>(J + n0);
-            jy4 = *reinterpret_cast<const float4*>(J + p.N + n0);
-            jz4 = *reinterpret_cast<const float4*>(J + 2 * (size_t)p.N + n0);
-        }
         __syncthreads();
-        if (!active) continue;
-        // ---- Shan-Chen force (Eq. 13) for the four nodes from the psi ring
-        float sa[3][4], sb[3][4];                       // sum_i w_i psi^A(x+c_i) c_i, same with psi^B
-#pragma unroll
-        for (int d = 0; d < 3; d++)
-#pragma unroll
-            for (int k = 0; k < 4; k++) sa[d][k] = sb[d][k] = 0.f;
+        if (active) {
+        // ---- Shan-Chen force (Eq. 13) for the four nodes from the psi ring.  Per component, with the ring
+        // rows R = (c_y, c_z) of the planes z - 1 .. z + 1: S_x = (1/18) D(0,0) + (1/36) sum of D over the four
+        // edge rows, D = psi(x+1) - psi(x-1); S_y and S_z from the centre values C and the x-pair sums T of the
+        // rows above and below (weights 1/18 for the axis rows, 1/36 for the edge and corner rows)
         const int s_back = rel & 3, s_ahead = (rel + 2) & 3;
-        const float* slots[3] = {ring + (size_t)(dz > 0 ? s_back : s_ahead) * 2 * plane_sz,
-                                 ring + (size_t)((rel + 1) & 3) * 2 * plane_sz,
-                                 ring + (size_t)(dz > 0 ? s_ahead : s_back) * 2 * plane_sz};
+        const float* pm = ring + (size_t)(dz > 0 ? s_back : s_ahead) * 2 * plane_sz;   // plane z - 1
+        const float* p0 = ring + (size_t)((rel + 1) & 3) * 2 * plane_sz;               // plane z
+        const float* pp = ring + (size_t)(dz > 0 ? s_ahead : s_back) * 2 * plane_sz;   // plane z + 1
+        float SA[3][4], SB[3][4], psA[4], psB[4];
 #pragma unroll
-        for (int cz = -1; cz <= 1; cz++)
+        for (int c = 0; c < 2; c++) {
+            const int co = c * plane_sz;
+            float w00[6], wyp[6], wym[6], wzp[6], wzm[6];
+            window6(p0 + co + r * nx, x, nx, w00);
+            window6(p0 + co + (r + 1) * nx, x, nx, wyp);
+            window6(p0 + co + (r - 1) * nx, x, nx, wym);
+            window6(pp + co + r * nx, x, nx, wzp);
+            window6(pm + co + r * nx, x, nx, wzm);
+            const float4 cpp = *reinterpret_cast<const float4*>(pp + co + (r + 1) * nx + x);   // (+y, +z)
+            const float4 cmp = *reinterpret_cast<const float4*>(pp + co + (r - 1) * nx + x);   // (-y, +z)
+            const float4 cpm = *reinterpret_cast<const float4*>(pm + co + (r + 1) * nx + x);   // (+y, -z)
+            const float4 cmm = *reinterpret_cast<const float4*>(pm + co + (r - 1) * nx + x);   // (-y, -z)
+            const float Cpp[4] = {cpp.x, cpp.y, cpp.z, cpp.w}, Cmp[4] = {cmp.x, cmp.y, cmp.z, cmp.w};
+            const float Cpm[4] = {cpm.x, cpm.y, cpm.z, cpm.w}, Cmm[4] = {cmm.x, cmm.y, cmm.z, cmm.w};
+            float(&S)[3][4] = c == 0 ? SA : SB;
 #pragma unroll
-            for (int cy = -1; cy <= 1; cy++) {
-                if (cy != 0 && cz != 0) {
-                    const float w = 1.f / 36.f;
-#pragma unroll
-                    for (int c = 0; c < 2; c++) {
-                        const float4 v = *reinterpret_cast<const float4*>(slots[1 + cz] + c * plane_sz +
-                                                                          (r + cy) * nx + x);
-                        const float V[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                        for (int k = 0; k < 4; k++) {
-                            if (c == 0) { sa[1][k] += w * cy * V[k]; sa[2][k] += w * cz * V[k]; }
-                            else { sb[1][k] += w * cy * V[k]; sb[2][k] += w * cz * V[k]; }
-                        }
-                    }
-                    continue;
-                }
-                const bool centre = cy == 0 && cz == 0;
-                const float wc = centre ? 0.f : 1.f / 18.f;
-                const float wx = centre ? 1.f / 18.f : 1.f / 36.f;
-#pragma unroll
-                for (int c = 0; c < 2; c++) {
-                    float w6[6];
-                    window6(slots[1 + cz] + c * plane_sz + (r + cy) * nx, x, nx, w6);
-#pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        const float vm = w6[k], v0 = w6[k + 1], vp = w6[k + 2];
-                        const float fx = wx * (vp - vm);
-                        const float sum3 = wx * (vp + vm) + wc * v0;
-                        if (c == 0) {
-                            sa[0][k] += fx; sa[1][k] += cy * sum3; sa[2][k] += cz * sum3;
-                        } else {
-                            sb[0][k] += fx; sb[1][k] += cy * sum3; sb[2][k] += cz * sum3;
-                        }
-                    }
-                }
+            for (int k = 0; k < 4; k++) {
+                const float dx = (w00[k + 2] - w00[k]) * (1.f / 18.f) +
+                                 ((wyp[k + 2] - wyp[k]) + (wym[k + 2] - wym[k]) + (wzp[k + 2] - wzp[k]) +
+                                  (wzm[k + 2] - wzm[k])) * (1.f / 36.f);
+                const float ty = (wyp[k + 2] + wyp[k]) - (wym[k + 2] + wym[k]);
+                const float tz = (wzp[k + 2] + wzp[k]) - (wzm[k + 2] + wzm[k]);
+                const float dy = (wyp[k + 1] - wym[k + 1]) * (1.f / 18.f) +
+                                 (ty + ((Cpp[k] + Cpm[k]) - (Cmp[k] + Cmm[k]))) * (1.f / 36.f);
+                const float dzv = (wzp[k + 1] - wzm[k + 1]) * (1.f / 18.f) +
+                                  (tz + ((Cpp[k] + Cmp[k]) - (Cpm[k] + Cmm[k]))) * (1.f / 36.f);
+                S[0][k] = dx; S[1][k] = dy; S[2][k] = dzv;
+                if (c == 0) psA[k] = w00[k + 1]; else psB[k] = w00[k + 1];
             }
+        }
 
         uint32_t bits = 0;
         if (IBM) bits = (__ldg(mask + (n0 >> 5)) >> (n0 & 31)) & 0xFu;
         const float ra[4] = {a4.x, a4.y, a4.z, a4.w}, rb[4] = {b4.x, b4.y, b4.z, b4.w};
         const float jxa[4] = {jx4.x, jx4.y, jx4.z, jx4.w}, jya[4] = {jy4.x, jy4.y, jy4.z, jy4.w},
                     jza[4] = {jz4.x, jz4.y, jz4.z, jz4.w};
-        float uA[4][3], uB[4][3];
+        // per node and component: 3 u_eq (the c_i . u of Eq. 2 scaled by 1/cs^2 = 3), a = 1 - 1.5 u.u, and the
+        // weighted densities w rho for the axis (1/18) and diagonal (1/36) directions
+        float vA[4][3], vB[4][3], aA[4], aB[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            const float pa = psi_fn(ra[k], p.psi_kind), pb = psi_fn(rb[k], p.psi_kind);
             const float rt = ra[k] + rb[k];
             const float irt = 1.f / rt;
             float FA[3], FB[3];
 #pragma unroll
             for (int d = 0; d < 3; d++) {
-                FA[d] = -pa * p.G * sb[d][k] + ra[k] * p.g[d];
-                FB[d] = -pb * p.G * sa[d][k] + rb[k] * p.g[d];
+                FA[d] = -psA[k] * p.G * SB[d][k] + ra[k] * p.g[d];
+                FB[d] = -psB[k] * p.G * SA[d][k] + rb[k] * p.g[d];
             }
             if (IBM && ((bits >> k) & 1u)) {
 #pragma unroll
@@ -1076,48 +1120,26 @@ k_collide4(LbmParams p, T* __restrict__ D, const float* __restrict__ rho, const 
             const float ux = jxa[k] * irt, uy = jya[k] * irt, uz = jza[k] * irt;
             if (!(rt > 0.f) || !(ux * ux + uy * uy + uz * uz <= 0.09f)) atomicOr(err, 1);
             const float ta = ra[k] > 0.f ? p.tau / ra[k] : 0.f, tb = rb[k] > 0.f ? p.tau / rb[k] : 0.f;
-            uA[k][0] = ux + ta * FA[0]; uA[k][1] = uy + ta * FA[1]; uA[k][2] = uz + ta * FA[2];
-            uB[k][0] = ux + tb * FB[0]; uB[k][1] = uy + tb * FB[1]; uB[k][2] = uz + tb * FB[2];
+            const float uA0 = ux + ta * FA[0], uA1 = uy + ta * FA[1], uA2 = uz + ta * FA[2];
+            const float uB0 = ux + tb * FB[0], uB1 = uy + tb * FB[1], uB2 = uz + tb * FB[2];
+            aA[k] = 1.f - 1.5f * (uA0 * uA0 + uA1 * uA1 + uA2 * uA2);
+            aB[k] = 1.f - 1.5f * (uB0 * uB0 + uB1 * uB1 + uB2 * uB2);
+            vA[k][0] = 3.f * uA0; vA[k][1] = 3.f * uA1; vA[k][2] = 3.f * uA2;
+            vB[k][0] = 3.f * uB0; vB[k][1] = 3.f * uB1; vB[k][2] = 3.f * uB2;
             if (IBM && ((bits >> k) & 1u)) {
                 u_out[n0 + k] = (jxa[k] + 0.5f * (FA[0] + FB[0])) * irt;
                 u_out[(size_t)p.N + n0 + k] = (jya[k] + 0.5f * (FA[1] + FB[1])) * irt;
                 u_out[(size_t)2 * p.N + n0 + k] = (jza[k] + 0.5f * (FA[2] + FB[2])) * irt;
             }
         }
-        // ---- equilibrium (Eq. 2) = the post-collision populations, direction by direction, float4 stores
+        // ---- equilibrium (Eq. 2) = the post-collision populations.  For a direction pair i, opp(i) with
+        // q = 3 c_i.u: f_eq = w rho (a + q + q^2 / 2) and w rho (a - q + q^2 / 2), so the pair shares h = a + q^2/2.
         const bool wall_next = p.walls && (z == 1 || z == p.nz - 2);
-        float uuA[4], uuB[4], sA[4], sB[4];
+        float sA[4], sB[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            uuA[k] = uA[k][0] * uA[k][0] + uA[k][1] * uA[k][1] + uA[k][2] * uA[k][2];
-            uuB[k] = uB[k][0] * uB[k][0] + uB[k][1] * uB[k][1] + uB[k][2] * uB[k][2];
-            sA[k] = sB[k] = 0.f;
-        }
-        auto emit = [&](auto Ic) {
+        for (int k = 0; k < 4; k++) sA[k] = sB[k] = 0.f;
+        auto store_dir = [&](auto Ic, const float (&oA)[4], const float (&oB)[4]) {
             constexpr int I = decltype(Ic)::value;
-            float oA[4], oB[4];
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                float eA, eB;
-                if (I == 0) {
-                    eA = ra[k] - sA[k];
-                    eB = rb[k] - sB[k];
-                    if (sizeof(T) == 2) {       // unbiased rounding of the mass-closing value
-                        const uint32_t h = dither_bits(n0 + k, ra[k], rb[k]);
-                        eA = pdither(eA, h >> 16, D);
-                        eB = pdither(eB, h & 0xffffu, D);
-                    }
-                } else {
-                    const float cuA = dir_x(I) * uA[k][0] + dir_y(I) * uA[k][1] + dir_z(I) * uA[k][2];
-                    const float cuB = dir_x(I) * uB[k][0] + dir_y(I) * uB[k][1] + dir_z(I) * uB[k][2];
-                    eA = pround(dir_w(I) * ra[k] * (1.f + 3.f * cuA + 4.5f * cuA * cuA - 1.5f * uuA[k]), D);
-                    eB = pround(dir_w(I) * rb[k] * (1.f + 3.f * cuB + 4.5f * cuB * cuB - 1.5f * uuB[k]), D);
-                    sA[k] += eA;
-                    sB[k] += eB;
-                }
-                oA[k] = eA;
-                oB[k] = eB;
-            }
             if (dir_z(I) != 0 && wall_next && is_wall_plane(p, z + dir_z(I))) {
                 // half-way bounce-back on a moving wall (Eq. 11), stored where the node pulls opp(I) from
                 const float* U = (z + dir_z(I) == 0) ? p.ulo : p.uhi;
@@ -1135,16 +1157,49 @@ k_collide4(LbmParams p, T* __restrict__ D, const float* __restrict__ rho, const 
                 pst4(D + (size_t)(Q + I) * p.N + n0, make_float4(oB[0], oB[1], oB[2], oB[3]));
             }
         };
-        emit(std::integral_constant<int, 1>{});  emit(std::integral_constant<int, 2>{});
-        emit(std::integral_constant<int, 3>{});  emit(std::integral_constant<int, 4>{});
-        emit(std::integral_constant<int, 5>{});  emit(std::integral_constant<int, 6>{});
-        emit(std::integral_constant<int, 7>{});  emit(std::integral_constant<int, 8>{});
-        emit(std::integral_constant<int, 9>{});  emit(std::integral_constant<int, 10>{});
-        emit(std::integral_constant<int, 11>{}); emit(std::integral_constant<int, 12>{});
-        emit(std::integral_constant<int, 13>{}); emit(std::integral_constant<int, 14>{});
-        emit(std::integral_constant<int, 15>{}); emit(std::integral_constant<int, 16>{});
-        emit(std::integral_constant<int, 17>{}); emit(std::integral_constant<int, 18>{});
-        emit(std::integral_constant<int, 0>{});
+        auto emit_pair = [&](auto Ic) {
+            constexpr int I = decltype(Ic)::value;             // odd: I and I + 1 = opp(I)
+            constexpr float W = dir_w(I);
+            float oA[4], oB[4], qA4[4], qB4[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const float qA = cdot<I>(vA[k][0], vA[k][1], vA[k][2]);
+                const float qB = cdot<I>(vB[k][0], vB[k][1], vB[k][2]);
+                const float hA = fmaf(0.5f * qA, qA, aA[k]), hB = fmaf(0.5f * qB, qB, aB[k]);
+                const float wA = W * ra[k], wB = W * rb[k];
+                oA[k] = pround(wA * (hA + qA), D);
+                oB[k] = pround(wB * (hB + qB), D);
+                qA4[k] = pround(wA * (hA - qA), D);
+                qB4[k] = pround(wB * (hB - qB), D);
+                sA[k] += oA[k] + qA4[k];
+                sB[k] += oB[k] + qB4[k];
+            }
+            store_dir(std::integral_constant<int, I>{}, oA, oB);
+            store_dir(std::integral_constant<int, I + 1>{}, qA4, qB4);
+        };
+        emit_pair(std::integral_constant<int, 1>{});  emit_pair(std::integral_constant<int, 3>{});
+        emit_pair(std::integral_constant<int, 5>{});  emit_pair(std::integral_constant<int, 7>{});
+        emit_pair(std::integral_constant<int, 9>{});  emit_pair(std::integral_constant<int, 11>{});
+        emit_pair(std::integral_constant<int, 13>{}); emit_pair(std::integral_constant<int, 15>{});
+        emit_pair(std::integral_constant<int, 17>{});
+        {
+            // the rest population closes each node's mass over the values as stored
+            float oA[4], oB[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                oA[k] = ra[k] - sA[k];
+                oB[k] = rb[k] - sB[k];
+                if (sizeof(T) == 2) {       // unbiased rounding of the mass-closing value
+                    const uint32_t h = dither_bits(n0 + k, ra[k], rb[k]);
+                    oA[k] = pdither(oA[k], h >> 16, D);
+                    oB[k] = pdither(oB[k], h & 0xffffu, D);
+                }
+            }
+            store_dir(std::integral_constant<int, 0>{}, oA, oB);
+        }
+        }
+        a4 = an;
+        b4 = bn;
     }
 }
 
@@ -1367,12 +1422,10 @@ static void launch_split(const LbmParams& p, const float* S, float* D, float* rh
     with_storage(p.store, [&](auto* tag) {
         using T = std::remove_pointer_t<decltype(tag)>;
         k_moments4<T><<<(quads + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<const T*>(S), rho, J);
-        T* Dt = reinterpret_cast<T*>(D);
-        switch (p.b4cfg) {
-            case 1: launch_c4m<512, 1, T>(mode, p, grid, threads, smem, TY, Dt, rho, J, ghost, Fibm, mask, u, err, st); break;
-            case 3: launch_c4m<128, 4, T>(mode, p, grid, threads, smem, TY, Dt, rho, J, ghost, Fibm, mask, u, err, st); break;
-            default: launch_c4m<256, 2, T>(mode, p, grid, threads, smem, TY, Dt, rho, J, ghost, Fibm, mask, u, err, st); break;
-        }
+        // one compiled kernel serves every shape (at most 512 threads, 128 registers: two 256-thread CTAs or
+        // four 128-thread CTAs share an SM), so the per-node arithmetic, and the results, do not depend on it
+        launch_c4m<512, 1, T>(mode, p, grid, threads, smem, TY, reinterpret_cast<T*>(D), rho, J, ghost, Fibm, mask,
+                              u, err, st);
     });
 }
 

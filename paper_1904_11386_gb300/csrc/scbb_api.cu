@@ -107,6 +107,7 @@ bool valid_fluid(const scbb_fluid* f) {
     if (f->psi_kind != 0 && f->psi_kind != 1) return false;
     if (f->coupling != 0 && f->coupling != 1) return false;
     if (f->storage < 0 || f->storage > 2) return false;
+    if (f->max_boundary < 0) return false;
     if (f->pp_eps != 0.0 && !(f->pp_d0 > 0.0)) return false;
     return true;
 }
@@ -144,6 +145,10 @@ LbmParams make_params(const scbb_lattice* lat, const scbb_fluid* fl) {
     if (lz < 8) lz = 8;
     if (lz > nzf) lz = nzf;
     p.lz = lz;
+    // SCBB_BULK_SHAPE=0..3 starts every context with that shape of the bulk kernel (scbb_autotune still
+    // replaces it); results do not depend on the shape
+    const char* e = getenv("SCBB_BULK_SHAPE");
+    if (e && e[0] >= '0' && e[0] < '0' + B4_CONFIGS && e[1] == 0) p.b4cfg = e[0] - '0';
     return p;
 }
 
@@ -155,7 +160,7 @@ struct BBSizes {
     int maxB, maxF, CW;
 };
 
-BBSizes bb_sizes(int nm, const scbb_mesh* ms) {
+BBSizes bb_sizes(int nm, const scbb_mesh* ms, int max_boundary) {
     BBSizes z{0, 0, 0};
     double area = 0, rmax = 0;
     for (int k = 0; k < nm; k++) {
@@ -177,7 +182,7 @@ BBSizes bb_sizes(int nm, const scbb_mesh* ms) {
             area += 0.5 * sqrt(x * x + y * y + zz * zz);
         }
     }
-    z.maxB = (int)(area * 3.0 * 1.5) + 4096;
+    z.maxB = max_boundary > 0 ? max_boundary : (int)(area * 3.0 * 1.5) + 4096;
     z.maxF = z.maxB / 2 + 1024;
     z.CW = 2 * (int)ceil(1.5 * rmax) + 10;
     return z;
@@ -237,7 +242,7 @@ size_t layout(const scbb_lattice* lat, const scbb_fluid* fl, int nm, const scbb_
     t.pp_eps = (float)fl->pp_eps;
     t.pp_d0 = (float)fl->pp_d0;
     if (fl->coupling == 0 && NV > 0) {
-        const BBSizes z = bb_sizes(nm, ms);
+        const BBSizes z = bb_sizes(nm, ms, fl->max_boundary);
         const LbmParams lp = make_params(lat, fl);
         t.maxB = z.maxB; t.maxF = z.maxF; t.CW = z.CW;
         t.owner = c.take<uint16_t>(N);
