@@ -36,7 +36,8 @@ class o_params(C.Structure):
                 ("tau", C.c_double), ("G", C.c_double), ("psi_kind", C.c_int),
                 ("g", C.c_double * 3), ("coupling", C.c_int),
                 ("rho_maj", C.c_double), ("rho_min", C.c_double), ("C0", C.c_double),
-                ("mass_correction", C.c_int), ("pp_eps", C.c_double), ("pp_d0", C.c_double)]
+                ("mass_correction", C.c_int), ("pp_eps", C.c_double), ("pp_d0", C.c_double),
+                ("wall_kind", C.c_int)]
 
 
 class o_mesh_params(C.Structure):
@@ -186,6 +187,7 @@ class OracleSim:
         p.rho_maj, p.rho_min, p.C0 = prob.rho_maj, prob.rho_min, prob.C0
         p.mass_correction = int(prob.mass_correction)
         p.pp_eps, p.pp_d0 = prob.pp_eps, prob.pp_d0
+        p.wall_kind = int(getattr(prob, "wall_kind", 0))
         self.p = p
         nm = len(prob.capsules)
         mps = (o_mesh_params * max(nm, 1))()
@@ -313,3 +315,68 @@ def threads():
 
 def set_threads(n):
     lib().o_set_threads(int(n))
+
+
+# ------------------------------------------------------------------------------------------------------
+# Membrane-only reference model of Sec. III.B (Eq. emulatetension): no fluid; the fluid-fluid interface is
+# emulated by a tensile force on the elements that lie in a band of width w around a fixed interface plane.
+# ------------------------------------------------------------------------------------------------------
+def _area_below(z, A, h):
+    """Area of each planar triangle (vertex heights z [T, 3], areas A [T]) below the plane z = h.  The
+    cross-section of a triangle at height t is a segment whose length is piecewise linear in t, so the area
+    below h is piecewise quadratic: with sorted heights z1 <= z2 <= z3 it is A (h - z1)^2 / ((z2 - z1)(z3 - z1))
+    up to z2 and A [1 - (z3 - h)^2 / ((z3 - z2)(z3 - z1))] above."""
+    zs = np.sort(z, axis=1)
+    z1, z2, z3 = zs[:, 0], zs[:, 1], zs[:, 2]
+    d31 = np.maximum(z3 - z1, 1e-300)
+    lo = A * np.clip(h - z1, 0, None) ** 2 / (np.maximum(z2 - z1, 1e-300) * d31)
+    hi = A * (1.0 - np.clip(z3 - h, 0, None) ** 2 / (np.maximum(z3 - z2, 1e-300) * d31))
+    out = np.where(h <= z1, 0.0, np.where(h >= z3, A, np.where(h <= z2, lo, hi)))
+    return out
+
+
+def emulated_tension(x, tri, z_int, gamma, w=1.0):
+    """Node forces of the emulated interface (Eq. emulatetension): an element whose area A lies within w/2 of
+    the plane z = z_int gets F = gamma A / w, spread evenly over its three nodes.  Reading (the paper states the
+    magnitude, not the direction): the interface pulls the membrane in its own plane, radially outward from the
+    capsule's vertical axis through its centre of mass, taken at the element's centroid."""
+    x = np.asarray(x, np.float64)
+    tri = np.asarray(tri)
+    p = x[tri]                                            # [T, 3 corners, 3]
+    A = 0.5 * np.linalg.norm(np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0]), axis=1)
+    z = p[:, :, 2]
+    band = _area_below(z, A, z_int + 0.5 * w) - _area_below(z, A, z_int - 0.5 * w)
+    axis = x[:, :2].mean(0)
+    radial = p.mean(1)[:, :2] - axis
+    rn = np.linalg.norm(radial, axis=1)
+    dirn = np.zeros((len(tri), 3))
+    ok = rn > 0
+    dirn[ok, :2] = radial[ok] / rn[ok, None]
+    Fe = (gamma * band / w)[:, None] * dirn
+    F = np.zeros_like(x)
+    for k in range(3):
+        np.add.at(F, tri[:, k], Fe / 3.0)
+    return F
+
+
+def reference_model(ref, tri, kS, C_, kB, kV, z_int, gamma, w=1.0, mass=5.0, damping=0.05, steps=4000,
+                    x0=None):
+    """The membrane-only reference model of Sec. III.B: the same elastic laws (Skalak, volume, bending; Sec.
+    II.B) and the same symplectic node update as the coupled method (V += F / m, X += V), with the emulated
+    interface tension in place of the fluid.  Reading: the fluid's dissipation is replaced by a velocity damping
+    (V *= 1 - damping each step), which does not change the static equilibrium the model is used for.
+    Returns the final positions and the largest node force of the last step (the equilibrium residual)."""
+    ref = np.asarray(ref, np.float64)
+    tri = np.asarray(tri, np.int32)
+    X = (ref if x0 is None else np.asarray(x0, np.float64)).copy()
+    V = np.zeros_like(X)
+    V0 = volume(ref, tri)
+    F = np.zeros_like(X)
+    for _ in range(steps):
+        F = skalak(X, tri, ref, kS, C_)[1] + volume_force(X, tri, kV, V0)[1] + emulated_tension(X, tri, z_int,
+                                                                                                  gamma, w)
+        if kB:
+            F += bending(X, tri, kB)["F"]
+        V = (1.0 - damping) * V + F / mass
+        X = X + V
+    return X, np.abs(F).max()

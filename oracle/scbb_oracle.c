@@ -79,6 +79,8 @@ typedef struct {
     double rho_maj, rho_min, C0;
     int mass_correction;
     double pp_eps, pp_d0;
+    int wall_kind;          /* 0: walls moving at u_lo / u_hi (half-way bounce-back, Eq. 11); 1: resting walls and
+                               on-site velocity boundaries u_lo / u_hi on the planes z = 1 and z = nz-2 */
 } o_params;
 
 typedef struct {
@@ -131,6 +133,12 @@ static inline long IDX(const osim* s, int x, int y, int z) {
 }
 static inline int wrap(int a, int n) { a %= n; return a < 0 ? a + n : a; }
 static inline int is_wall_z(const osim* s, int z) { return s->p.walls && (z == 0 || z == s->p.nz - 1); }
+
+/* velocity of the wall plane z (zero for resting walls next to on-site velocity planes) */
+static double wall_u(const osim* s, int z, int k) {
+    if (s->p.wall_kind == 1) return 0.0;
+    return z == 0 ? s->p.u_lo[k] : s->p.u_hi[k];
+}
 
 /* neighbour of (x,y,z) along direction i; returns -1 if it leaves a non-periodic z range */
 static long nbr(const osim* s, int x, int y, int z, int i, int* zz_out) {
@@ -647,7 +655,7 @@ void o_ibm_interp(const osim* s, const double* ufield, double* Ub) {
                 double uk;
                 if (s->owner[nd[q]] == OWNER_WALL) {
                     int z = (int)(nd[q] / ((long)s->p.nx * s->p.ny));
-                    uk = (z == 0) ? s->p.u_lo[k] : s->p.u_hi[k];
+                    uk = wall_u(s, z, k);
                 } else {
                     uk = ufield[k * s->N + nd[q]];
                 }
@@ -711,6 +719,46 @@ void o_capsule_diag(const osim* s, int m, double* vol, double* com3) {
 /* Fluid: Shan-Chen force (Eq. 13), forcing by equilibrium-velocity shift (Sec. II.A), BGK collision      */
 /* (Eq. 1), push streaming with half-way bounce-back (Eq. 11) on wall links and on membrane-cut links.    */
 /* ---------------------------------------------------------------------------------------------------- */
+
+/* On-site velocity boundaries (Zou and He, in the D3Q19 form of Hecht and Harting; Sec. III.A and III.C use
+   them to impose the shear): on the fluid planes next to the walls (z = 1 with U = u_lo, z = nz-2 with
+   U = u_hi) the populations that arrived from the wall are replaced, component by component, so that the
+   node's velocity is U.  With n the inward normal (+z at the bottom, -z at the top): rho = (sum of the
+   populations with c.n = 0 + 2 x those with c.n < 0) / (1 - U.n); each unknown f_i (c_i.n > 0) is
+   f_opp(i) + 6 w_i rho c_i.U - c_i,t . N_t, with the tangential correction
+   N_t = 1/2 sum_{c.n = 0} f c_t - rho U_t / 3, which makes sum_i f_i c_i = rho U exactly. */
+static void onsite_velocity(osim* s) {
+    const long N = s->N;
+    for (int side = 0; side < 2; side++) {
+        const int z = side == 0 ? 1 : s->p.nz - 2;
+        const int nrm = side == 0 ? 1 : -1;
+        const double* U = side == 0 ? s->p.u_lo : s->p.u_hi;
+        for (int y = 0; y < s->p.ny; y++)
+            for (int x = 0; x < s->p.nx; x++) {
+                const long n = IDX(s, x, y, z);
+                if (s->owner[n] == OWNER_WALL) continue;
+                for (int c = 0; c < 2; c++) {
+                    double* f = s->f + (c * N + n) * 19;
+                    double s0 = 0, sin = 0, tx = 0, ty = 0;
+                    for (int i = 0; i < 19; i++) {
+                        if (CZ[i] == 0) {
+                            s0 += f[i];
+                            tx += f[i] * CX[i];
+                            ty += f[i] * CY[i];
+                        } else if (CZ[i] == -nrm) {
+                            sin += f[i];
+                        }
+                    }
+                    const double rho = (s0 + 2.0 * sin) / (1.0 - nrm * U[2]);
+                    const double Nx = 0.5 * tx - rho * U[0] / 3.0, Ny = 0.5 * ty - rho * U[1] / 3.0;
+                    for (int i = 0; i < 19; i++)
+                        if (CZ[i] == nrm)
+                            f[i] = f[OPP(i)] + 6.0 * W[i] * rho * (CX[i] * U[0] + CY[i] * U[1] + CZ[i] * U[2]) -
+                                   (CX[i] * Nx + CY[i] * Ny);
+                }
+            }
+    }
+}
 
 /* virtual density seen across a wall link: mean of rho over the fluid neighbours of the wall node */
 static double wall_virtual_rho(const osim* s, long wn, int c) {
@@ -800,8 +848,7 @@ static void fluid_step(osim* s) {
                 } else if (s->owner[m] == OWNER_WALL) {
                     /* half-way bounce-back on a moving wall (Eq. 11, v0 = wall velocity); c_i points into the
                        wall, the population returns to n in the opposite direction */
-                    const double* U = (zz == 0) ? s->p.u_lo : s->p.u_hi;
-                    double cu = CX[i] * U[0] + CY[i] * U[1] + CZ[i] * U[2];
+                    double cu = CX[i] * wall_u(s, zz, 0) + CY[i] * wall_u(s, zz, 1) + CZ[i] * wall_u(s, zz, 2);
                     s->fn[(c * N + n) * 19 + OPP(i)] = fs - 2.0 * W[i] * rho[c] * cu / CS2;
                 } else if (s->owner[m] != s->owner[n]) {
                     bb_link(s, n, x, y, z, i, m, c, fs, rho[c]);
@@ -812,6 +859,7 @@ static void fluid_step(osim* s) {
         }
     }
     double* t = s->f; s->f = s->fn; s->fn = t;
+    if (s->p.walls && s->p.wall_kind == 1) onsite_velocity(s);
 }
 
 /* ---------------------------------------------------------------------------------------------------- */

@@ -130,6 +130,8 @@ class Problem:
     walls: int = 1                  # 1: solid wall planes at z=0 and z=nz-1 (half-way bounce-back)
     u_lo: tuple = (0.0, 0.0, 0.0)   # velocity of the z=0 wall
     u_hi: tuple = (0.0, 0.0, 0.0)   # velocity of the z=nz-1 wall
+    wall_kind: int = 0              # 0: walls moving at u_lo / u_hi; 1: resting walls, on-site velocity u_lo / u_hi
+                                    #    on the planes z = 1 and z = nz-2
     tau: float = 1.0
     G: float = 3.6
     psi_kind: int = 0               # 0: psi = 1-exp(-rho) (paper), 1: psi = rho
@@ -148,6 +150,7 @@ class Problem:
     seed: int = 1
     steps: int = 200
     storage: int = 0                # populations on the GPU: 0 FP32, 1 FP16, 2 BF16 (the oracle is FP64 always)
+    max_boundary: int = 0           # GPU boundary-list capacity (0: sized from the membrane areas)
 
     @property
     def n_nodes(self):
@@ -279,8 +282,8 @@ def cfg_adjoint(n: int = 32, R_drop: float = 8.0, seed: int = 9, G: float = 3.6)
 
 
 def cfg_batch48(n_boxes: int = 48, seed: int = 3) -> List[Problem]:
-    """A sweep of independent boxes of uneven size: cubes with edges drawn from PCG64(seed) among the multiples
-    of 4 in [40, 72], walls at both z ends, a flat interface at mid height, one s = 3 capsule of radius 6 (642
+    """A sweep of independent boxes of uneven size: cubes with edges drawn from PCG64(seed) uniformly among the
+    integers in [40, 72], walls at both z ends, a flat interface at mid height, one s = 3 capsule of radius 6 (642
     vertices) penetrating it by 1; box k takes colour index k mod 11 over [-0.1, 0.1] and shear modulus index
     (k div 11) mod 4 over {0.001, 0.003, 0.01, 0.03}, kB = 0.01 kS R^2, kV = 2 (coarse mesh), exponential psi."""
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -289,7 +292,7 @@ def cfg_batch48(n_boxes: int = 48, seed: int = 3) -> List[Problem]:
     R = 6.0
     out = []
     for k in range(n_boxes):
-        L = 4 * int(rng.integers(10, 19))
+        L = int(rng.integers(40, 73))
         kS = moduli[(k // 11) % 4]
         cap = Capsule(centre=(L / 2 + 0.3, L / 2 - 0.2, L / 2 - R + 1.0), radius=R, subdiv=3, kS=kS,
                       kB=0.01 * kS * R * R, kV=2.0, colour=float(colours[k % 11]))

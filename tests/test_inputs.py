@@ -39,11 +39,13 @@ def test_janus_colours_split_at_the_centre():
 
 
 def test_batch_sweep_boxes():
-    """48 cubes with edges among the multiples of 4 in [40, 72] (the row-vectorised kernel's four-node rows),
-    11 colours over [-0.1, 0.1] and 4 shear moduli, seeds 100 + k."""
+    """48 cubes with integer edges drawn uniformly from [40, 72] (both multiples of 4 and others occur, so the
+    sweep exercises both forms of the bulk kernels), 11 colours over [-0.1, 0.1] and 4 shear moduli, seeds
+    100 + k."""
     probs = inputs.cfg_batch48()
     assert len(probs) == 48
-    assert all(p.nx == p.ny == p.nz and p.nx % 4 == 0 and 40 <= p.nx <= 72 for p in probs)
+    assert all(p.nx == p.ny == p.nz and 40 <= p.nx <= 72 for p in probs)
+    assert any(p.nx % 4 for p in probs) and any(p.nx % 4 == 0 for p in probs)
     assert sorted({round(p.capsules[0].colour, 12) for p in probs}) == sorted(
         {round(v, 12) for v in np.linspace(-0.1, 0.1, 11)})
     assert {p.capsules[0].kS for p in probs} == {0.001, 0.003, 0.01, 0.03}

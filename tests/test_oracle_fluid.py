@@ -234,3 +234,43 @@ def test_laplace_law_surface_tension():
     gamma_m = (p_n - p_xx).sum() / 2             # two interfaces in the periodic column
     assert abs(gamma_l - gamma_m) < 0.1 * gamma_m, (gamma_l, gamma_m)
     assert 0.03 < gamma_m < 0.07
+
+
+def test_onsite_velocity_couette_exact():
+    """On-site velocity boundaries (Zou and He, D3Q19 form of Hecht and Harting; Sec. III.A and III.C impose
+    their shear with them): resting walls at z = 0 and nz - 1, the planes z = 1 and nz - 2 held at u_lo and
+    u_hi.  A single-component fluid (two non-interacting components, G = 0) relaxes to plane Couette flow,
+    u(z) = u_lo + (u_hi - u_lo) (z - 1) / (nz - 3), exactly linear between the two planes (the lattice
+    Boltzmann method reproduces a linear profile exactly), with the velocities imposed on the planes themselves
+    and the density uniform."""
+    nz = 20
+    p = _prob(nx=2, ny=2, nz=nz, walls=1, G=0.0, u_lo=(-0.02, 0.0, 0.0), u_hi=(0.02, 0.005, 0.0), wall_kind=1)
+    s = O.OracleSim(p, np.full((nz, 2, 2), 0.5), np.full((nz, 2, 2), 0.5))
+    s.step(6000)
+    a, b, u = s.fields()
+    z = np.arange(1, nz - 1)
+    lin = (z - 1) / (nz - 3)
+    assert np.abs(u[0, 1:nz - 1, 0, 0] - (-0.02 + 0.04 * lin)).max() < 1e-12
+    assert np.abs(u[1, 1:nz - 1, 0, 0] - 0.005 * lin).max() < 1e-12
+    assert np.abs(u[2, 1:nz - 1]).max() < 1e-12
+    assert np.abs((a + b)[1:nz - 1] - 1.0).max() < 1e-9
+
+
+def test_onsite_velocity_imposed_each_component():
+    """With the Shan-Chen coupling on (G = 3.6, a flat A|B interface between the two on-site planes), every step
+    leaves each component's velocity on the two planes exactly at the plane's velocity (the reconstruction makes
+    sum_i f_i^c c_i = rho^c U for each c), while the interior evolves."""
+    nz = 16
+    p = _prob(nx=4, ny=3, nz=nz, walls=1, G=3.6, psi_kind=0, z_interface=8, noise=1e-3,
+              u_lo=(0.01, -0.003, 0.0), u_hi=(-0.01, 0.0, 0.0), wall_kind=1)
+    s = O.OracleSim(p)
+    c, _, _ = O.d3q19()
+    for _ in range(3):
+        s.step(7)
+        f = s.populations().reshape(2, nz, 3, 4, 19)
+        for zp, U in ((1, p.u_lo), (nz - 2, p.u_hi)):
+            for comp in range(2):
+                fz = f[comp, zp]
+                rho = fz.sum(-1)
+                j = fz @ c
+                assert np.abs(j - rho[..., None] * np.array(U)).max() < 1e-14

@@ -196,3 +196,57 @@ def test_bending_force_density_spheroid():
                     band_num = (num[m] * A[m]).sum() / A[m].sum()
                     band_an = (an[m] * A[m]).sum() / A[m].sum()
                     assert abs(band_num - band_an) < 0.1 * np.abs(an).max(), (k, band_num, band_an)
+
+
+def test_reference_model_band_area_and_hat_box():
+    """The band area of the reference model (Sec. III.B, Eq. emulatetension).  (1) A right triangle in the x-z
+    plane with legs 1 along x and z: the area below height h is h - h^2 / 2, by hand.  (2) Archimedes' hat-box
+    theorem: the area of a spherical zone of height w is 2 pi R w wherever the zone sits, so the band areas of a
+    fine icosphere (s = 4) summed over its elements give 2 pi R w for a band at the equator and one halfway to
+    the pole alike (the inscribed polyhedron is a few 1e-3 smaller)."""
+    z = np.array([[0.0, 0.0, 1.0]])
+    A = np.array([0.5])
+    for h in (0.0, 0.3, 0.7, 1.0):
+        assert abs(O._area_below(z, A, h)[0] - (h - h * h / 2)) < 1e-15
+    R, w = 9.0, 1.0
+    cap = inputs.Capsule(centre=(0.0, 0.0, 0.0), radius=R, subdiv=4)
+    ref, tri, _ = cap.mesh()
+    p = ref[tri]
+    Atri = 0.5 * np.linalg.norm(np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0]), axis=1)
+    for zc in (0.0, 0.5 * R):
+        band = (O._area_below(p[:, :, 2], Atri, zc + w / 2) - O._area_below(p[:, :, 2], Atri, zc - w / 2)).sum()
+        assert abs(band / (2 * np.pi * R * w) - 1) < 1e-2, (zc, band / (2 * np.pi * R * w))
+
+
+def test_reference_model_tension_balance_and_equilibrium():
+    """The emulated tension on a sphere centred at the interface pulls radially in the interface plane: its
+    net force vanishes and its total magnitude is gamma x (band area / w) = 2 pi R gamma (the hat-box theorem).
+    Relaxed with the elastic laws (Skalak with C = 1, volume penalty, no bending), the capsule reaches an
+    equilibrium (residual node force below 1e-6 of the tension on a node's share) with its equator stretched
+    and its poles drawn in, r_i > R > r_p, and for small tension (gamma / kS = 0.08 and 0.04) the polar
+    contraction is linear in gamma (the largest equatorial radius is not: it sits at the local bulge under the
+    line load of the band)."""
+    R, kS = 8.0, 0.05
+    cap = inputs.Capsule(centre=(0.0, 0.0, 0.0), radius=R, subdiv=3)
+    ref, tri, _ = cap.mesh()
+    gamma = 0.0388
+    F = O.emulated_tension(ref, tri, 0.0, gamma)
+    assert np.abs(F.sum(0)).max() < 1e-12
+    assert abs(np.linalg.norm(F[:, :2], axis=1).sum() / (2 * np.pi * R * gamma) - 1) < 3e-2
+    assert np.abs(F[:, 2]).max() == 0.0
+
+    def strain(g):
+        X, res = O.reference_model(ref, tri, kS, 1.0, 0.0, 20.0, 0.0, g, steps=3000)
+        c = X.mean(0)
+        r_i = np.linalg.norm((X - c)[:, :2], axis=1).max()
+        r_p = np.abs((X - c)[:, 2]).max()
+        return r_i, r_p, res
+
+    r_i, r_p, res = strain(gamma)
+    assert res < 1e-6 * gamma
+    assert r_i > R * 1.01 and r_p < R * 0.99, (r_i, r_p)
+    _, p1, res1 = strain(0.004)
+    _, p2, _ = strain(0.002)
+    assert res1 < 1e-6 * 0.004
+    lin = (p1 - R) / (p2 - R)
+    assert 1.9 < lin < 2.2, lin
