@@ -59,7 +59,7 @@ def workload(name: str):
     if name == "parity32":
         return inputs.cfg_parity(coupling=1), "parity32-ibm2: 32^3, psi=rho, s=3 capsule R=6"
     if name == "batch48":
-        return inputs.cfg_batch48(), ("batch48: 48 independent cubes with edges 40-72 (multiples of 4), each a flat "
+        return inputs.cfg_batch48(), ("batch48: 48 independent cubes with integer edges 40-72, each a flat "
                                       "interface with one s=3 capsule R=6 (642 vertices), colours over [-0.1, 0.1] "
                                       "x shear moduli {0.001, 0.003, 0.01, 0.03}, half-way bounce-back")
     if name == "droplet256":
@@ -236,11 +236,52 @@ def storage_beside(prob, args, ws, local, n_upd, peak, storage):
             "error_vs_fp64_oracle": STORAGE_ERROR[storage]}
 
 
+def _timed_batch(probs, args, dev, shared, clocks=None):
+    """Steps a batch of fresh contexts of probs (warm-up, then args.steps timed on the batch stream); returns
+    (ms, launches, shared bulk phase or not, clock record)."""
+    import torch
+
+    from paper_1904_11386_gb300 import scbb
+
+    old = os.environ.get("SCBB_BATCH_PERSISTENT")
+    os.environ["SCBB_BATCH_PERSISTENT"] = "1" if shared else "0"
+    try:
+        sims = [scbb.Sim(p, device=dev) for p in probs]
+        batch = scbb.Batch(sims)
+    finally:
+        if old is None:
+            del os.environ["SCBB_BATCH_PERSISTENT"]
+        else:
+            os.environ["SCBB_BATCH_PERSISTENT"] = old
+    bst = batch.stream
+    batch.scbb_batch_step(args.warmup)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    l0 = sum(s.scbb_launch_count() for s in sims)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(bst)
+    batch.scbb_batch_step(args.steps)
+    e1.record(bst)
+    torch.cuda.synchronize()
+    launches = sum(s.scbb_launch_count() for s in sims) - l0
+    clk = clocks.stop() if clocks else None
+    for s in sims:
+        s.scbb_sync()
+    mode = batch.scbb_batch_shared_bulk()
+    batch.close()
+    for s in sims:
+        s.close()
+    return e0.elapsed_time(e1), launches, mode, clk
+
+
 def run_batch(args, probs, label, ws, rank, local):
-    """The sweep of independent boxes: steps of all boxes together (one CUDA graph with a branch per box),
-    against the same boxes stepped one after another on one stream, kernel by kernel (looping single
-    launches).  value = lattice updates of all boxes per second of the batched run."""
-    import numpy as np
+    """The sweep of independent boxes: steps of all boxes together, pairs of steps replayed from one CUDA graph
+    with a branch per box (the library's default for bounce-back boxes), against the same batch with the bulk
+    phase of every box in one persistent cooperative launch per step (the rest of each box's step on its own
+    stream), and against the boxes stepped one after another on one stream, kernel by kernel (looping single
+    launches).  value = lattice updates of all boxes per second of the default batched run."""
     import torch
 
     from paper_1904_11386_gb300 import scbb
@@ -249,26 +290,11 @@ def run_batch(args, probs, label, ws, rank, local):
     dev = f"cuda:{local}"
     nodes = sum(p.n_nodes for p in probs)
     n_upd = sum(p.nx * p.ny * (p.nz - 2 * p.walls) for p in probs)
-    sims = [scbb.Sim(p, device=dev) for p in probs]
-    batch = scbb.Batch(sims)
-    bst = batch.stream
-    batch.scbb_batch_step(args.warmup)
-    torch.cuda.synchronize()
     clocks = Clocks()
-    clocks.start()
-    time.sleep(0.3)
-    l0 = sum(s.scbb_launch_count() for s in sims)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(bst)
-    batch.scbb_batch_step(args.steps)
-    e1.record(bst)
-    torch.cuda.synchronize()
-    launches = sum(s.scbb_launch_count() for s in sims) - l0
-    ms = replica_max(e0.elapsed_time(e1), ws, dev)
-    clk = clocks.stop()
-    for s in sims:
-        s.scbb_sync()
-    batch.close()
+    ms, launches, _, clk = _timed_batch(probs, args, dev, False, clocks)
+    ms = replica_max(ms, ws, dev)
+    ms_sh, launches_sh, shared, _ = _timed_batch(probs, args, dev, True)
+    ms_sh = replica_max(ms_sh, ws, dev)
     # looping single launches: all boxes on one stream, one box after another, one step per call
     one = torch.cuda.Stream(device=dev)
     loop_sims = [scbb.Sim(p, device=dev, stream=one) for p in probs]
@@ -276,6 +302,7 @@ def run_batch(args, probs, label, ws, rank, local):
         s.scbb_step(args.warmup)
     torch.cuda.synchronize()
     k_loop = min(args.steps, 20)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(one)
     for _ in range(k_loop):
         for s in loop_sims:
@@ -285,8 +312,6 @@ def run_batch(args, probs, label, ws, rank, local):
     ms_loop = replica_max(e0.elapsed_time(e1), ws, dev)
     for s in loop_sims:
         s.scbb_sync()
-        s.close()
-    for s in sims:
         s.close()
     peak, src = peak_hbm()
     # the boxes' bulk kernels overlap each other and the other kernels of the step, so per-launch events do not
@@ -299,20 +324,23 @@ def run_batch(args, probs, label, ws, rank, local):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": label, "boxes": len(probs), "nodes": nodes, "parallelism": f"replicas x{ws}",
                       "l2": f"inputs larger than L2 (populations 2 x {2 * 19 * 4 * nodes / 1e6:.0f} MB)"},
+           "shared_bulk_launch": {"value": aggregate_glups(nodes, args.steps, ws, ms_sh / 1e3), "unit": "GLUPS",
+                                  "gpu_launches": launches_sh, "active": bool(shared),
+                                  "how": "the bulk phase of all boxes in one persistent cooperative launch per "
+                                         "step (kernel A, bounded grid barrier, kernel B), the rest per box"},
            "looped_single_launches": {"value": aggregate_glups(nodes, k_loop, ws, ms_loop / 1e3), "unit": "GLUPS",
                                       "steps": k_loop,
                                       "how": "all boxes on one stream, box after box, one step per call"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "traffic": None,
-                        "kernel": "k_bulk4 of all boxes: algorithmic bytes per batched step / whole step time "
+                        "kernel": "bulk phase of all boxes: algorithmic bytes per batched step / whole step time "
                                   "(a lower bound; the step also runs the bookkeeping kernels)",
                         "bytes_per_lu": BYTES_PER_LU, "units_per_step": n_upd, "peak_source": src},
            "gpu_launches": launches, "clocks": clk}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(probs[0], args.cpu_seconds)
         out["cpu_baseline"]["sample"] += " (box 0 of the sweep)"
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+    return out
 
 
 def cpu_baseline(prob, seconds=15.0):
@@ -422,8 +450,7 @@ def run_adjoint(args, prob, label, ws, rank, local, n_steps=2000, every=100):
            "gpu_launches": launches}
     adj.close()
     sim.close()
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+    return out
 
 
 def run_reference(args, prob, label, ws, rank):
@@ -459,6 +486,8 @@ def main():
     ap.add_argument("--workload", default="adsorb128")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="adsorb128: skip the batch48 and adjoint64 summaries of the default line")
     ap.add_argument("--no-fp16", action="store_true",
                     help="skip the 16-bit storage figures (FP16, BF16) beside the FP32 ones")
     ap.add_argument("--adj-steps", type=int, default=2000, help="adjoint64: steps differentiated")
@@ -471,7 +500,9 @@ def main():
     ws, rank, local = dist_setup()
     prob, label = workload(args.workload)
     if args.workload == "adjoint64" and args.impl == "ours":
-        run_adjoint(args, prob, label, ws, rank, local, n_steps=args.adj_steps, every=args.adj_every)
+        out = run_adjoint(args, prob, label, ws, rank, local, n_steps=args.adj_steps, every=args.adj_every)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
         if ws > 1:
             import torch.distributed as dist
 
@@ -481,7 +512,9 @@ def main():
         if args.impl == "reference":
             run_reference_batch(args, prob, label, rank)
         else:
-            run_batch(args, prob, label, ws, rank, local)
+            out = run_batch(args, prob, label, ws, rank, local)
+            if rank == 0:
+                print(json.dumps(out), flush=True)
         if ws > 1:
             import torch.distributed as dist
 
@@ -588,6 +621,20 @@ def main():
     if args.storage == "fp32" and not args.no_fp16:
         for st16 in ("fp16", "bf16"):
             out[f"{st16}_storage"] = storage_beside(prob, args, ws, local, n_upd, peak, st16)
+    if args.workload == "adsorb128" and args.storage == "fp32" and not args.no_extras:
+        # the batched and differentiated forms, measured in the same run (their own workloads)
+        bprobs, blabel = workload("batch48")
+        bargs = argparse.Namespace(**{**vars(args), "no_cpu_baseline": True})
+        b = run_batch(bargs, bprobs, blabel, ws, rank, local)
+        out["batch48"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "steps", "shared_bulk_launch",
+                                            "looped_single_launches", "gpu_launches")}
+        out["batch48"]["workload"] = blabel
+        aprob, alabel = workload("adjoint64")
+        a = run_adjoint(args, aprob, alabel, ws, rank, local, n_steps=args.adj_steps, every=args.adj_every)
+        out["adjoint64"] = {k: a[k] for k in ("value", "unit", "forward_ms", "backward_ms", "forward_glups",
+                                              "adjoint_workspace_bytes", "gpu_launches")}
+        out["adjoint64"]["metric"] = a["metric"]
+        out["adjoint64"]["workload"] = alabel
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
     if rank == 0:

@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define SCBB_ABI_VERSION 1
+#define SCBB_ABI_VERSION 2
 
 typedef struct scbb_ctx scbb_ctx;
 
@@ -49,12 +49,19 @@ typedef enum {
     SCBB_E_UNSUPPORTED = 8   /* a mode the library does not provide for these arguments */
 } scbb_status;
 
-/* Lattice (Sec. II.A).  walls: 1 = solid planes z=0 and z=nz-1 with half-way bounce-back (Eq. 11, with the
- * wall velocity as v0), 0 = periodic in z.  u_lo / u_hi: velocities of the z=0 / z=nz-1 walls. */
+/* Lattice (Sec. II.A).  walls: 1 = solid planes z=0 and z=nz-1 with half-way bounce-back (Eq. 11), 0 = periodic
+ * in z.  wall_kind (with walls = 1): 0 = the walls move at u_lo / u_hi (the bounce-back's v0); 1 = the walls rest
+ * and on-site velocity boundaries (Zou and He, in the D3Q19 form of Hecht and Harting, as Sec. III.A and III.C
+ * impose their shear) hold the planes of fluid nodes next to them, z = 1 and z = nz-2, at u_lo and u_hi: the
+ * populations those nodes receive from the wall are replaced so that each component moves at the plane's
+ * velocity.  wall_kind 1 needs walls = 1 and nz >= 5 (else SCBB_E_INVAL), tau = 1 and no bounce-back membranes
+ * (the fresh-node mass correction of Eq. 18 tracks the mass the lattice itself conserves; on-site planes
+ * exchange mass with the outside); otherwise scbb_create returns SCBB_E_UNSUPPORTED. */
 typedef struct {
     int nx, ny, nz;
     int walls;
     double u_lo[3], u_hi[3];
+    int wall_kind;
 } scbb_lattice;
 
 /* Fluid (Sec. II.A, II.D, II.E).
@@ -71,9 +78,13 @@ typedef struct {
  *   storage   0: FP32 populations; 1: populations stored as IEEE FP16, 2: as BF16 (arithmetic stays FP32;
  *             each stored value is rounded to nearest even, at most 2^-12 relative for FP16 and 2^-9 for
  *             BF16), half the population bytes.  Not in the paper.
- * 16-bit storage and the bounce-back coupling with meshes run on the row-vectorised bulk kernel, which needs nx
- * a multiple of 4 (and, for tau != 1, nx/4 a power of two up to 32 or a multiple of 32); otherwise
- * scbb_create returns SCBB_E_UNSUPPORTED. */
+ *   max_boundary  capacity of the bounce-back boundary-node list (nodes with a membrane-cut link); 0 sizes it
+ *             from the membrane areas (three node layers per unit area, 50 % margin, + 4096).  The fresh-node
+ *             list holds max_boundary / 2 + 1024.  A list that overflows keeps its first entries, skips the
+ *             rest and raises the device error word: the next synchronising call returns SCBB_E_UNSTABLE.
+ * 16-bit storage and the bounce-back coupling with meshes need a bulk kernel that stores every node whole: with
+ * tau = 1 (the paper's value) any nx up to 256, or nx a multiple of 4 up to 2048; with tau != 1 nx a multiple of
+ * 4 with nx/4 a power of two up to 32 or a multiple of 32.  Otherwise scbb_create returns SCBB_E_UNSUPPORTED. */
 typedef struct {
     double tau, G;
     int psi_kind;
@@ -83,6 +94,7 @@ typedef struct {
     int mass_correction;
     double pp_eps, pp_d0;
     int storage;
+    int max_boundary;
 } scbb_fluid;
 
 /* One capsule membrane (Sec. II.B): a closed triangulated surface, triangles counter-clockwise seen from
@@ -219,6 +231,26 @@ typedef struct scbb_batch scbb_batch;
 scbb_status scbb_batch_create(scbb_ctx* const* ctxs, int n, void* cuda_stream, scbb_batch** out);
 scbb_status scbb_batch_step(scbb_batch* batch, long long n);
 void scbb_batch_destroy(scbb_batch* batch);
+
+/* Shared bulk phase of a batch (not in the paper).  When every context runs the two-kernel bulk phase (tau = 1)
+ * with the same coupling mode and storage, and there are at most 64 of them, each step of the batch can run the
+ * bulk phase of all boxes as ONE persistent cooperative launch on the batch stream: the stream-and-moments
+ * kernel over every box's nodes, a grid barrier, then the force-and-collision kernel over every box's (tile,
+ * z-segment) work items; each context's other kernels run on its own stream before and after it.  A batch does
+ * so by default when none of its contexts has bounce-back membranes; with them, the per-box bookkeeping overlaps
+ * other boxes' bulk phases only when each box keeps its own (a graph branch per box), which is faster.  The
+ * environment variable SCBB_BATCH_PERSISTENT=1 shares the bulk phase whenever the boxes can, 0 never (read at
+ * scbb_batch_create).  Results equal those of stepping each context alone, to FP32 rounding.
+ * scbb_batch_shared_bulk: 1 if the batch shares the bulk phase, else 0 (also for NULL).
+ * scbb_batch_set_wait_limit: the number of polls (about 0.26 us each; default 2^22, about a second) that the
+ *   grid barrier's wait makes before it gives up.  A wait that gives up leaves the step incomplete and raises
+ *   bit 4 of every context's device error word, which the next synchronising call on a context reports as
+ *   SCBB_E_TIMEOUT (and SCBB_E_STATE afterwards, until scbb_load).  The barrier is bounded so that a launch
+ *   whose blocks cannot all run at once ends with an error instead of waiting forever; a small limit forces
+ *   that path.  SCBB_E_INVAL for polls < 0.  The grid barrier keeps its two counters in the first context's
+ *   workspace. */
+int scbb_batch_shared_bulk(const scbb_batch* batch);
+scbb_status scbb_batch_set_wait_limit(scbb_batch* batch, long long polls);
 
 /* Reverse-mode derivative of the fluid (not in the paper, which has no adjoint).  The gradient of a loss of
  * the densities after n steps, L(rho^A(T), rho^B(T)), with respect to the Shan-Chen coupling G (Eq. 13), the

@@ -98,6 +98,8 @@ bool valid_lattice(const scbb_lattice* l) {
     if (!l || l->nx < 1 || l->ny < 1 || l->nz < 1) return false;
     if (l->walls != 0 && l->walls != 1) return false;
     if (l->walls && l->nz < 3) return false;
+    if (l->wall_kind != 0 && l->wall_kind != 1) return false;
+    if (l->wall_kind == 1 && (!l->walls || l->nz < 5)) return false;
     double N = (double)l->nx * l->ny * l->nz;
     return N * 2.0 * Q < 4.0e9;     // 32-bit population indices
 }
@@ -135,6 +137,15 @@ LbmParams make_params(const scbb_lattice* lat, const scbb_fluid* fl) {
         p.g[k] = (float)fl->g[k];
         p.ulo[k] = (float)lat->u_lo[k];
         p.uhi[k] = (float)lat->u_hi[k];
+    }
+    if (lat->walls && lat->wall_kind == 1) {
+        // resting walls; the planes next to them move at u_lo / u_hi
+        p.onsite = 1;
+        for (int k = 0; k < 3; k++) {
+            p.vlo[k] = p.ulo[k];
+            p.vhi[k] = p.uhi[k];
+            p.ulo[k] = p.uhi[k] = 0.f;
+        }
     }
     // z-segment length of the scalar bulk kernels: several waves on 152 SMs, at least 8 planes
     int nzf = p.zf1 - p.zf0;
@@ -302,6 +313,11 @@ scbb_status check_device_error(scbb_ctx* c) {
     int h = 0;
     CUDA_TRY(c, cudaMemcpyAsync(&h, c->d.err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    if (h & 4) {
+        c->broken = 1;
+        return fail(c, SCBB_E_TIMEOUT, "device error word %d after %lld steps: a bounded wait of the batch's "
+                    "shared bulk phase gave up (its step is incomplete)", h, c->steps);
+    }
     if (h) {
         c->broken = 1;
         return fail(c, SCBB_E_UNSTABLE, "device error word %d after %lld steps (non-finite density or |u| > 0.3)",
@@ -327,9 +343,15 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
     std::string why;
     if (!valid_lattice(lat) || !valid_fluid(fl) || !dev_workspace) return SCBB_E_INVAL;
     if (!valid_meshes(n_mesh, meshes, why)) return SCBB_E_MESH;
+    if (lat->walls && lat->wall_kind == 1) {
+        // on-site velocity planes: the two-kernel bulk phase forms their moments; no fresh-node mass bookkeeping
+        LbmParams lp = make_params(lat, fl);
+        if (!bulk_split(lp) || (fl->coupling == 0 && n_mesh > 0)) return SCBB_E_UNSUPPORTED;
+    }
     if ((fl->coupling == 0 && n_mesh > 0) || fl->storage != 0) {
-        // bounce-back membranes and 16-bit storage run with the row-vectorised bulk kernel (nx a multiple of 4;
-        // for tau != 1 also nx/4 a power of two up to 32 or a multiple of 32)
+        // bounce-back membranes and 16-bit storage need a bulk kernel that stores every node whole: the two-kernel
+        // bulk phase (tau = 1; nx a multiple of 4 up to 2048, or any nx up to 256) or the fused row-vectorised
+        // kernel (nx a multiple of 4, and for tau != 1 nx/4 a power of two up to 32 or a multiple of 32)
         LbmParams lp = make_params(lat, fl);
         if (!bulk_vectorised(lp)) return SCBB_E_UNSUPPORTED;
     }
@@ -511,14 +533,22 @@ static bool overlap_enabled() {
     return v == 1;
 }
 
-// One time step on the context stream (kernel launches only), advancing cur, steps and the launch count.
+// One time step on the context stream (kernel launches only), advancing cur, steps and the launch count, in
+// three parts: what runs before the bulk phase, the bulk phase, and what runs after it (a batch launches the
+// bulk phase of all its contexts together, between the other two parts of each).
 // allow_side: false inside a batch, whose graph already runs the contexts side by side (a second stream per
 // context there cost more than it gained: 7.49 -> 7.36 GLUPS on the 48-box sweep).
-static void enqueue_step(scbb_ctx* c, bool allow_side = true) {
-    const bool ibm = c->fl.coupling == 1 && c->d.NV > 0;
-    const bool bb = c->d.owner != nullptr;
-    const int mode = ibm ? 1 : 0;
-    const int step = (int)(c->steps & 0x7fffffff);     // the kernels use its parity only
+struct StepPlan {
+    bool ibm, bb, side, side_walls, ghost_pass;
+    int mode, step;
+};
+
+static StepPlan plan_step(const scbb_ctx* c, bool allow_side) {
+    StepPlan s;
+    s.ibm = c->fl.coupling == 1 && c->d.NV > 0;
+    s.bb = c->d.owner != nullptr;
+    s.mode = s.ibm ? 1 : 0;
+    s.step = (int)(c->steps & 0x7fffffff);                 // the kernels use its parity only
     // Under bounce-back, kernels whose inputs are ready early run on the second stream (the bulk kernel
     // leaves SMs to them) and join where their results are needed; not while the phases are timed one after
     // another:
@@ -532,67 +562,78 @@ static void enqueue_step(scbb_ctx* c, bool allow_side = true) {
     //   write), joined at the end of the step.
     // With the immersed boundary, the wall ghosts (they read the populations alone) run there beside the
     // membrane forces and the spreading (they read the vertices alone), joined before the bulk kernel.
-    const bool side = allow_side && bb && c->side && overlap_enabled() && c->timing != 2;
-    // the two-kernel bulk phase computes the wall ghost densities itself
-    const bool ghost_pass = c->lp.walls && !bulk_writes_ghost(c->lp);
-    const bool side_walls = allow_side && ibm && ghost_pass && c->side && overlap_enabled() && c->timing != 2;
+    // The two-kernel bulk phase computes the wall ghost densities itself.
+    s.ghost_pass = c->lp.walls && !bulk_writes_ghost(c->lp);
+    s.side = allow_side && s.bb && c->side && overlap_enabled() && c->timing != 2;
+    s.side_walls = allow_side && s.ibm && s.ghost_pass && c->side && overlap_enabled() && c->timing != 2;
+    return s;
+}
+
+static void enqueue_pre(scbb_ctx* c, const StepPlan& s) {
     c->mark(0);
-    if (side_walls) {
+    if (s.side_walls) {
         cudaEventRecord(c->ev_fork, c->st);
         cudaStreamWaitEvent(c->side, c->ev_fork, 0);
         launch_wall_ghost(c->lp, c->d.S[c->cur], c->d.wall_rho, c->d.ghost, c->side);
         cudaEventRecord(c->ev_join, c->side);
     }
-    if (side) {
+    if (s.side) {
         cudaEventRecord(c->ev_fork, c->st);
         cudaStreamWaitEvent(c->side, c->ev_fork, 0);
         launch_bb_lists_reset(c->d, c->side);          // counted with the classification below
         c->launches += launch_membrane_elastic(c->lp, c->d, c->side);
         cudaEventRecord(c->ev_join, c->side);
     }
-    if (ibm) {
+    if (s.ibm) {
         // membrane forces at X(t), spread onto the lattice (2-point immersed boundary)
-        c->launches += launch_membrane_forces(c->lp, c->d, false, step, c->st);
+        c->launches += launch_membrane_forces(c->lp, c->d, false, s.step, c->st);
         launch_ibm_spread(c->lp, c->d, c->st);
         c->launches += 1;
     }
     c->mark(1);
-    if (ghost_pass) {
-        if (side_walls) cudaStreamWaitEvent(c->st, c->ev_join, 0);
+    if (s.ghost_pass) {
+        if (s.side_walls) cudaStreamWaitEvent(c->st, c->ev_join, 0);
         else launch_wall_ghost(c->lp, c->d.S[c->cur], c->d.wall_rho, c->d.ghost, c->st);
         c->launches += 2;
     }
     c->mark(2);
+}
+
+static void enqueue_bulk(scbb_ctx* c, const StepPlan& s) {
     const bool timed = c->timing && c->ev_used + 2 <= c->ev.size();
     if (timed) cudaEventRecord(c->ev[c->ev_used], c->st);
     launch_bulk(c->lp, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.rho, c->d.J, c->d.ghost, c->d.Fibm,
-                c->d.mask, c->d.u, c->d.err, mode, c->st);
+                c->d.mask, c->d.u, c->d.err, s.mode, c->st);
     if (timed) {
         cudaEventRecord(c->ev[c->ev_used + 1], c->st);
         c->ev_used += 2;
     }
     c->launches += bulk_split(c->lp) ? 2 : 1;
+}
+
+static void enqueue_post(scbb_ctx* c, const StepPlan& s) {
+    const int step = s.step;
     c->mark(3);
-    if (ibm) {
+    if (s.ibm) {
         launch_ibm_interp(c->lp, c->d, c->st);
         c->launches++;
     }
-    if (bb) {
+    if (s.bb) {
         // boundary nodes (bounce-back, wetting) -> membrane forces with coupling, node update ->
         // classification at X(t+1), boundary list -> fresh nodes
         launch_bb_boundary(c->lp, c->d, c->d.S[c->cur], c->d.S[1 - c->cur], c->d.ghost, step, c->d.err, c->st);
         c->launches += 2;
-        if (side) {
+        if (s.side) {
             cudaEventRecord(c->ev_fork2, c->st);
             cudaStreamWaitEvent(c->side, c->ev_fork2, 0);
             launch_bb_mass(c->lp, c->d, c->side);
         }
         c->mark(4);
-        if (side) cudaStreamWaitEvent(c->st, c->ev_join, 0);
+        if (s.side) cudaStreamWaitEvent(c->st, c->ev_join, 0);
         else c->launches += launch_membrane_elastic(c->lp, c->d, c->st);
         c->launches += launch_membrane_update(c->lp, c->d, true, step, c->st);
         c->mark(5);
-        if (side) {
+        if (s.side) {
             launch_bb_owner(c->lp, c->d, step, false, c->st);
             cudaEventRecord(c->ev_fork3, c->st);
             cudaStreamWaitEvent(c->side, c->ev_fork3, 0);
@@ -617,6 +658,13 @@ static void enqueue_step(scbb_ctx* c, bool allow_side = true) {
     if (c->timing == 2 && (c->pev_steps + 1) * (SCBB_PHASES + 1) <= c->pev.size()) c->pev_steps++;
     c->cur ^= 1;
     c->steps++;
+}
+
+static void enqueue_step(scbb_ctx* c, bool allow_side = true) {
+    const StepPlan s = plan_step(c, allow_side);
+    enqueue_pre(c, s);
+    enqueue_bulk(c, s);
+    enqueue_post(c, s);
 }
 
 static bool graphs_enabled() {
@@ -704,7 +752,31 @@ struct scbb_batch {
     std::vector<long long> pair_launches;
     std::vector<cudaEvent_t> ev;          // [0]: fork, [1 + k]: join of context k
     int graph_off = 0;
+    int persistent = 0;                   // the bulk phase of all contexts in one cooperative launch
+    long long spin_limit = 1LL << 22;     // polls of the grid barrier's wait before it gives up (about 1 s)
 };
+
+// The boxes of a batch can share one persistent launch of the bulk phase when every context runs the two-kernel
+// bulk phase with the same coupling mode and storage, and there are at most BATCH_MAX of them.  They do by
+// default when no context has bounce-back membranes: the shared launch makes every box's post-bulk kernels wait
+// for the bulk phase of all boxes, and the bounce-back bookkeeping (a chain of small latency-bound kernels per
+// box) then no longer overlaps other boxes' bulk phases as it does with a graph branch per box (48-box sweep:
+// 6.4 GLUPS shared against 7.5 GLUPS with branches).  SCBB_BATCH_PERSISTENT=1 shares whenever the boxes can,
+// SCBB_BATCH_PERSISTENT=0 never.
+static int batch_can_share(const scbb_batch* b) {
+    const char* e = getenv("SCBB_BATCH_PERSISTENT");
+    if (e && e[0] == '0') return 0;
+    const bool force = e && e[0] == '1';
+    if (b->ctx.empty() || b->ctx.size() > (size_t)BATCH_MAX) return 0;
+    const scbb_ctx* c0 = b->ctx[0];
+    const bool mode0 = c0->fl.coupling == 1 && c0->d.NV > 0;
+    for (const scbb_ctx* c : b->ctx) {
+        if (!bulk_split(c->lp) || c->lp.store != c0->lp.store) return 0;
+        if ((c->fl.coupling == 1 && c->d.NV > 0) != mode0) return 0;
+        if (c->d.owner && !force) return 0;
+    }
+    return 1;
+}
 
 static int ctx_key(const scbb_ctx* c) { return (c->cur << 1) | (int)(c->steps & 1); }
 
@@ -723,7 +795,47 @@ static cudaError_t batch_join(scbb_batch* b) {
     return e;
 }
 
-// One graph with a branch per context, each branch two steps of that context on its own stream.
+// One step of every context with a shared bulk phase: each context's pre-bulk kernels on its own stream, the
+// bulk phase of all of them in one cooperative launch on the batch stream, then each context's post-bulk kernels.
+static cudaError_t batch_step_shared(scbb_batch* b) {
+    const size_t n = b->ctx.size();
+    std::vector<StepPlan> plan(n);
+    cudaError_t e = batch_fork(b);
+    for (size_t k = 0; k < n && e == cudaSuccess; k++) {
+        plan[k] = plan_step(b->ctx[k], false);
+        enqueue_pre(b->ctx[k], plan[k]);
+    }
+    if (e == cudaSuccess) e = batch_join(b);
+    if (e != cudaSuccess) return e;
+    BatchDesc d;
+    memset(&d, 0, sizeof(d));
+    d.nbox = (int)n;
+    d.bar = b->ctx[0]->d.err + 2;
+    d.spin_limit = b->spin_limit;
+    for (size_t k = 0; k < n; k++) {
+        scbb_ctx* c = b->ctx[k];
+        BatchBox& x = d.box[k];
+        x.p = c->lp;
+        x.S = c->d.S[c->cur];
+        x.D = c->d.S[1 - c->cur];
+        x.rho = c->d.rho;
+        x.J = c->d.J;
+        x.ghost = c->d.ghost;
+        x.Fibm = c->d.Fibm;
+        x.mask = c->d.mask;
+        x.u = c->d.u;
+        x.err = c->d.err;
+    }
+    if (!launch_batch_bulk(d, plan[0].mode, b->ctx[0]->lp.store, b->st)) return cudaErrorLaunchFailure;
+    b->ctx[0]->launches++;
+    e = batch_fork(b);
+    for (size_t k = 0; k < n && e == cudaSuccess; k++) enqueue_post(b->ctx[k], plan[k]);
+    if (e == cudaSuccess) e = batch_join(b);
+    return e;
+}
+
+// One graph with a branch per context, each branch two steps of that context on its own stream (or, with a
+// shared bulk phase, two shared steps).
 static void batch_capture(scbb_batch* b) {
     const size_t n = b->ctx.size();
     std::vector<int> cur0(n);
@@ -738,12 +850,18 @@ static void batch_capture(scbb_batch* b) {
         b->graph_off = 1;
         return;
     }
-    cudaError_t e = batch_fork(b);
-    for (size_t k = 0; k < n && e == cudaSuccess; k++) {
-        enqueue_step(b->ctx[k], false);
-        enqueue_step(b->ctx[k], false);
+    cudaError_t e = cudaSuccess;
+    if (b->persistent) {
+        e = batch_step_shared(b);
+        if (e == cudaSuccess) e = batch_step_shared(b);
+    } else {
+        e = batch_fork(b);
+        for (size_t k = 0; k < n && e == cudaSuccess; k++) {
+            enqueue_step(b->ctx[k], false);
+            enqueue_step(b->ctx[k], false);
+        }
+        if (e == cudaSuccess) e = batch_join(b);
     }
-    if (e == cudaSuccess) e = batch_join(b);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
     b->keys.assign(n, 0);
@@ -1015,7 +1133,29 @@ scbb_status scbb_batch_create(scbb_ctx* const* ctxs, int n, void* cuda_stream, s
             delete b;
             return SCBB_E_CUDA;
         }
+    b->persistent = batch_can_share(b);
+    if (b->persistent) {
+        // the grid barrier's words start at rest (arrivals 0)
+        if (cudaMemsetAsync(b->ctx[0]->d.err + 2, 0, 2 * sizeof(int), b->ctx[0]->st) != cudaSuccess ||
+            cudaStreamSynchronize(b->ctx[0]->st) != cudaSuccess) {
+            cudaGetLastError();
+            for (auto& f : b->ev) cudaEventDestroy(f);
+            delete b;
+            return SCBB_E_CUDA;
+        }
+    }
     *out = b;
+    return SCBB_OK;
+}
+
+int scbb_batch_shared_bulk(const scbb_batch* b) { return b ? b->persistent : 0; }
+
+scbb_status scbb_batch_set_wait_limit(scbb_batch* b, long long polls) {
+    if (!b || polls < 0) return SCBB_E_INVAL;
+    b->spin_limit = polls;
+    // captured steps hold the old limit
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
     return SCBB_OK;
 }
 
@@ -1051,12 +1191,14 @@ scbb_status scbb_batch_step(scbb_batch* b, long long n) {
             }
         }
         // one step of every context, launched kernel by kernel on the contexts' own streams
-        if (batch_fork(b) != cudaSuccess) return SCBB_E_CUDA;
-        for (auto* c : b->ctx) {
-            enqueue_step(c, false);
-            c->eager_steps++;
+        if (b->persistent) {
+            if (batch_step_shared(b) != cudaSuccess) return SCBB_E_CUDA;
+        } else {
+            if (batch_fork(b) != cudaSuccess) return SCBB_E_CUDA;
+            for (auto* c : b->ctx) enqueue_step(c, false);
+            if (batch_join(b) != cudaSuccess) return SCBB_E_CUDA;
         }
-        if (batch_join(b) != cudaSuccess) return SCBB_E_CUDA;
+        for (auto* c : b->ctx) c->eager_steps++;
         left--;
     }
     if (batch_fork(b) != cudaSuccess) return SCBB_E_CUDA;      // later calls on a context wait for the batch
@@ -1096,7 +1238,7 @@ struct scbb_adjoint {
 namespace {
 
 bool adjoint_supported(const scbb_ctx* c) {
-    return c && c->d.NV == 0 && c->d.NM == 0 && c->lp.store == 0;
+    return c && c->d.NV == 0 && c->d.NM == 0 && c->lp.store == 0 && !c->lp.onsite;
 }
 
 // Carves the adjoint's buffers (base == nullptr: measures only).
@@ -1135,7 +1277,7 @@ scbb_status scbb_adjoint_create(scbb_ctx* c, long long n, int K, void* ws, scbb_
     if (!c || !ws || n < 1 || K < 1 || ((uintptr_t)ws % ALIGN)) return SCBB_E_INVAL;
     if (c->broken) return SCBB_E_STATE;
     if (!adjoint_supported(c))
-        return fail(c, SCBB_E_UNSUPPORTED, "adjoint: boxes without meshes and FP32 storage only");
+        return fail(c, SCBB_E_UNSUPPORTED, "adjoint: boxes without meshes, FP32 storage, no on-site planes only");
     scbb_adjoint* a = new scbb_adjoint;
     a->c = c;
     a->n = n;

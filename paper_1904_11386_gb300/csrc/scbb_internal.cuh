@@ -52,6 +52,8 @@ struct LbmParams {
     int store;              // population storage: 0 FP32, 1 FP16 (__half), 2 BF16 (__nv_bfloat16); the S
                             // pointers point to that type
     int b4cfg;              // shape of the row-vectorised bulk kernel, 0 .. B4_CONFIGS - 1 (scbb_autotune)
+    int onsite;             // 1: resting walls (ulo = uhi = 0) and on-site velocity planes z = 1 (vlo), nz-2 (vhi)
+    float vlo[3], vhi[3];
 };
 
 // Shapes of the row-vectorised bulk kernel: (threads per CTA, CTAs per SM, fewest planes per z-segment) =
@@ -163,7 +165,9 @@ struct DevState {
     float* wall_rho;        // [2 walls][2 comp][nxy] densities of the planes next to the walls
     float* ghost;           // [2 walls][2 comp][nxy] virtual densities of the wall planes
     double* red;            // reduction scratch
-    int* err;               // sticky device error word
+    int* err;               // [4] sticky device error word (bits: 1 Mach guard or non-positive density, 2 boundary
+                            //     list out of step, 4 a bounded wait gave up); [2..3] the grid barrier of a batch
+                            //     whose first context this is
     // membranes
     int NV, NT, NM;
     float4* X;              // [NV] positions
@@ -270,17 +274,91 @@ __device__ __forceinline__ void pull(const LbmParams& p, const T* __restrict__ S
     }
 }
 
+// On-site velocity boundary (Zou and He, in the D3Q19 form of Hecht and Harting; Sec. III.A and III.C impose the
+// shear with it).  f: the 2 x 19 populations pulled at a node of plane z = 1 (velocity vlo) or z = nz-2 (vhi),
+// the ones that arrived from the wall included.  Those are replaced, component by component, so that the
+// node's velocity is the plane's velocity U: with n the inward normal, rho = (sum of the populations with
+// c.n = 0 + 2 x those with c.n < 0) / (1 - U.n) and, for c_i.n > 0,
+// f_i = f_opp(i) + 6 w_i rho c_i.U - c_i,t . N_t with N_t = 1/2 sum_{c.n = 0} f c_t - rho U_t / 3.
+__device__ __forceinline__ bool is_onsite_plane(const LbmParams& p, int z) {
+    return p.onsite && (z == 1 || z == p.nz - 2);
+}
+__device__ __forceinline__ void onsite_fix(const LbmParams& p, int z, float (&f)[2 * Q]) {
+    const int nrm = z == 1 ? 1 : -1;
+    const float* U = nrm > 0 ? p.vlo : p.vhi;
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        float s0 = 0.f, sin = 0.f, tx = 0.f, ty = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const float v = f[c * Q + i];
+            if (dir_z(i) == 0) {
+                s0 += v;
+                if (dir_x(i)) tx += dir_x(i) * v;
+                if (dir_y(i)) ty += dir_y(i) * v;
+            } else if (dir_z(i) == -nrm) {
+                sin += v;
+            }
+        }
+        const float rho = (s0 + 2.f * sin) / (1.f - nrm * U[2]);
+        const float Nx = 0.5f * tx - rho * U[0] * (1.f / 3.f), Ny = 0.5f * ty - rho * U[1] * (1.f / 3.f);
+#pragma unroll
+        for (int i = 1; i < Q; i++)
+            if (dir_z(i) == nrm)
+                f[c * Q + i] = f[c * Q + dir_opp(i)] +
+                               6.f * dir_w(i) * rho * (dir_x(i) * U[0] + dir_y(i) * U[1] + dir_z(i) * U[2]) -
+                               (dir_x(i) * Nx + dir_y(i) * Ny);
+    }
+}
+
 // ---- launches (lbm_kernels.cu) ----
 void launch_init_state(const LbmParams& p, float* S, const float* rho_st, const float* u_st, cudaStream_t st);
 void launch_wall_ghost(const LbmParams& p, const float* S, float* wall_rho, float* ghost, cudaStream_t st);
 // mode 0: fluid only (also with bounce-back membranes), 1: immersed boundary (mask = IBM stencil bits)
-// J: [3][N] momentum scratch of the two-kernel bulk phase (tau = 1, nx a multiple of 4), which also writes the
-// wall ghost densities itself (bulk_writes_ghost); with J null the fused kernels run
+// J: [3][N] momentum scratch of the two-kernel bulk phase (tau = 1), which also writes the wall ghost
+// densities itself (bulk_writes_ghost); with J null the fused kernels run
 void launch_bulk(const LbmParams& p, const float* S, float* D, float* rho, float* J, float* ghost,
                  const float* Fibm, const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st);
+// true when the bounce-back coupling can run on this lattice: the two-kernel bulk phase or the fused
+// row-vectorised kernel (both store every node of the lattice whole)
 bool bulk_vectorised(const LbmParams& p);
-bool bulk_split(const LbmParams& p);
 bool bulk_writes_ghost(const LbmParams& p);
+int bulk_variant();
+
+// ---- the two-kernel bulk phase (bulk_split.cu)
+bool bulk_split(const LbmParams& p);
+int split_grid_blocks(const LbmParams& p);
+void launch_split(const LbmParams& p, const float* S, float* D, float* rho, float* J, float* ghost,
+                  const float* Fibm, const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st);
+
+// Bulk phase of a batch of boxes in one cooperative launch (kernel parameters carry every box).
+constexpr int BATCH_MAX = 64;
+constexpr int BATCH_THREADS = 256;
+struct BatchBox {
+    LbmParams p;
+    const void* S;          // populations read (storage type of p.store)
+    void* D;                // populations written
+    float* rho;
+    float* J;
+    float* ghost;
+    const float* Fibm;
+    const uint32_t* mask;
+    float* u;
+    int* err;
+    unsigned int a_begin;   // first thread of kernel A (a multiple of 32)
+    unsigned int a_count;   // its work units: quads (vec) or nodes
+    int b_begin;            // first (tile, z-segment) item of kernel B
+    int cols, nseg, TY, vec;
+};
+struct BatchDesc {
+    int nbox;
+    unsigned int a_total;
+    int b_total;
+    int* bar;               // [2] grid barrier: arrivals, generation
+    long long spin_limit;   // polls of a barrier wait before it gives up
+    BatchBox box[BATCH_MAX];
+};
+bool launch_batch_bulk(BatchDesc& d, int mode, int store, cudaStream_t st);
 void launch_export(const LbmParams& p, const float* S, float* out, int what, cudaStream_t st);
 void launch_moments_reduce(const LbmParams& p, const float* S, double* red, cudaStream_t st);
 int bulk_grid_blocks(const LbmParams& p);

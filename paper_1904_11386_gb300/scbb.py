@@ -21,20 +21,21 @@ EXPORTS = ["scbb_workspace_bytes", "scbb_create", "scbb_set_density", "scbb_step
            "scbb_get_fields", "scbb_get_populations", "scbb_get_vertices", "scbb_get_diag", "scbb_get_owner",
            "scbb_launch_count", "scbb_enable_timing", "scbb_kernel_time", "scbb_phase_times", "scbb_autotune",
            "scbb_population_moments_noalloc", "scbb_batch_create", "scbb_batch_step", "scbb_batch_destroy",
+           "scbb_batch_shared_bulk", "scbb_batch_set_wait_limit",
            "scbb_adjoint_workspace_bytes", "scbb_adjoint_create", "scbb_adjoint_forward", "scbb_adjoint_backward",
            "scbb_adjoint_destroy", "scbb_state_bytes", "scbb_save", "scbb_load", "scbb_last_error", "scbb_destroy"]
 
 
 class scbb_lattice(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("walls", C.c_int),
-                ("u_lo", C.c_double * 3), ("u_hi", C.c_double * 3)]
+                ("u_lo", C.c_double * 3), ("u_hi", C.c_double * 3), ("wall_kind", C.c_int)]
 
 
 class scbb_fluid(C.Structure):
     _fields_ = [("tau", C.c_double), ("G", C.c_double), ("psi_kind", C.c_int), ("g", C.c_double * 3),
                 ("coupling", C.c_int), ("rho_maj", C.c_double), ("rho_min", C.c_double), ("C0", C.c_double),
                 ("mass_correction", C.c_int), ("pp_eps", C.c_double), ("pp_d0", C.c_double),
-                ("storage", C.c_int)]
+                ("storage", C.c_int), ("max_boundary", C.c_int)]
 
 
 class scbb_mesh(C.Structure):
@@ -107,6 +108,10 @@ def load(path: str = LIB_PATH):
     L.scbb_batch_step.argtypes = [vp, C.c_longlong]
     L.scbb_batch_destroy.restype = None
     L.scbb_batch_destroy.argtypes = [vp]
+    L.scbb_batch_shared_bulk.restype = C.c_int
+    L.scbb_batch_shared_bulk.argtypes = [vp]
+    L.scbb_batch_set_wait_limit.restype = C.c_int
+    L.scbb_batch_set_wait_limit.argtypes = [vp, C.c_longlong]
     L.scbb_adjoint_workspace_bytes.restype = C.c_size_t
     L.scbb_adjoint_workspace_bytes.argtypes = [vp, C.c_longlong, C.c_int]
     L.scbb_adjoint_create.restype = C.c_int
@@ -130,6 +135,7 @@ def lattice_of(prob) -> scbb_lattice:
     lat.nx, lat.ny, lat.nz, lat.walls = prob.nx, prob.ny, prob.nz, int(prob.walls)
     lat.u_lo = (C.c_double * 3)(*prob.u_lo)
     lat.u_hi = (C.c_double * 3)(*prob.u_hi)
+    lat.wall_kind = int(getattr(prob, "wall_kind", 0))
     return lat
 
 
@@ -142,6 +148,7 @@ def fluid_of(prob) -> scbb_fluid:
     fl.mass_correction = int(prob.mass_correction)
     fl.pp_eps, fl.pp_d0 = prob.pp_eps, prob.pp_d0
     fl.storage = int(getattr(prob, "storage", 0))
+    fl.max_boundary = int(getattr(prob, "max_boundary", 0))
     return fl
 
 
@@ -325,7 +332,8 @@ class Sim:
 
 class Batch:
     """Several independent Sim contexts stepped together (scbb_batch_*): each context keeps its own stream, the
-    batch runs on a stream of its own, and pairs of steps of all contexts replay from one CUDA graph."""
+    batch runs on a stream of its own, pairs of steps of all contexts replay from one CUDA graph, and the bulk
+    phase of all boxes runs as one persistent cooperative launch where they can share it."""
 
     def __init__(self, sims, stream=None, autotune=False):
         import torch
@@ -354,6 +362,15 @@ class Batch:
         st = self.L.scbb_batch_step(self.h, int(n))
         if st != SCBB_OK:
             raise ScbbError(f"scbb_batch_step: {STATUS.get(st, st)}")
+
+    def scbb_batch_shared_bulk(self):
+        """True when the bulk phase of all boxes runs as one persistent cooperative launch."""
+        return bool(self.L.scbb_batch_shared_bulk(self.h))
+
+    def scbb_batch_set_wait_limit(self, polls):
+        st = self.L.scbb_batch_set_wait_limit(self.h, C.c_longlong(int(polls)))
+        if st != SCBB_OK:
+            raise ScbbError(f"scbb_batch_set_wait_limit: {STATUS.get(st, st)}")
 
     def close(self):
         if getattr(self, "h", None):

@@ -45,6 +45,9 @@ def test_bounce_back_results_do_not_depend_on_the_shape():
 def test_general_kernel_has_no_shapes():
     from paper_1904_11386_gb300 import scbb
 
-    s = scbb.Sim(inputs.small_problem(n=16, nx=37, walls=1, coupling=1, capsule=False))
+    import dataclasses
+
+    # tau != 1 with nx not a multiple of 4 runs the general fused kernel
+    s = scbb.Sim(dataclasses.replace(inputs.small_problem(n=16, nx=37, walls=1, coupling=1, capsule=False), tau=0.8))
     assert s.scbb_autotune(2) == -1
     s.scbb_step(2)

@@ -106,3 +106,28 @@ def test_pp_repulsion_two_capsules():
     # the repulsion is active: compare with the elastic-only force of the same shapes
     assert np.abs(Fo).max() > 0.05
     assert np.abs(Fg - Fo).max() < 1e-4 * np.abs(Fo).max()
+
+
+def test_ibm_capsule_in_onsite_shear():
+    """A capsule in shear imposed by on-site velocity planes (Zou and He), the setup of Sec. III.A: a single
+    component mixture (G = 0, rho^A = rho^B = 0.5), resting walls, planes z = 1 and nz - 2 at -+U along x, a
+    soft capsule (kappa_V = 1) at the centre coupled by the 2-point immersed boundary; 100 steps against the
+    oracle: densities within 1e-5 relative, vertex positions within 1e-4, velocities within 1e-4 of max|u| (the
+    immersed-boundary velocities carry the FP32 rounding of the vertex positions through the stencil weights,
+    a few 1e-5 of max|u|, as in the 1000-step case)."""
+    nz = 24
+    cap = inputs.Capsule(centre=(12.3, 11.8, 11.6), radius=5.0, subdiv=3, kS=0.01, kB=1e-3, kV=1.0)
+    p = inputs.Problem(name="shear", nx=24, ny=24, nz=nz, walls=1, coupling=1, psi_kind=0, G=0.0,
+                       capsules=[cap], noise=0.0, seed=3, u_lo=(-0.01, 0.0, 0.0), u_hi=(0.01, 0.0, 0.0),
+                       wall_kind=1)
+    A = np.full((nz, 24, 24), 0.5)
+    g = _sim(p, rhoA=A, rhoB=A)
+    o = O.OracleSim(p, A, A)
+    g.scbb_step(100)
+    o.step(100)
+    (ga, gb, gu), (oa, ob, ou) = g.scbb_get_fields(), o.fields()
+    fl = oa + ob > 0
+    assert (np.abs(ga - oa)[fl] / oa[fl]).max() < 1e-5
+    assert (np.abs(gb - ob)[fl] / ob[fl]).max() < 1e-5
+    assert np.abs(gu - ou).max() < 1e-4 * np.abs(ou).max()
+    assert np.abs(g.scbb_get_vertices()[0] - o.vertices()[0]).max() < 1e-4
