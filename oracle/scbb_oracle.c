@@ -245,6 +245,11 @@ void o_set_elem_colour(osim* s, const double* col) {
 }
 
 /* populations f = f_eq(rho^c, u) on every node (wall nodes included; they are never used as fluid) */
+static void onsite_velocity(osim* s);
+
+/* Initial state: f = f_eq(rho, u) at every node; with on-site velocity planes the state satisfies their
+   boundary condition from the start (the populations they would receive from the walls are reconstructed, as
+   after every streaming step). */
 void o_set_state(osim* s, const double* rhoA, const double* rhoB, const double* u /* [3][N] or NULL */) {
     for (long n = 0; n < s->N; n++) {
         double uu[3] = {0, 0, 0};
@@ -256,6 +261,7 @@ void o_set_state(osim* s, const double* rhoA, const double* rhoB, const double* 
         s->rho[n] = rhoA[n];
         s->rho[s->N + n] = rhoB[n];
     }
+    if (s->p.walls && s->p.wall_kind == 1) onsite_velocity(s);
 }
 
 void o_get_f(const osim* s, double* out) { memcpy(out, s->f, sizeof(double) * 2 * 19 * s->N); }
