@@ -258,11 +258,18 @@ scbb_status scbb_batch_set_wait_limit(scbb_batch* batch, long long polls);
  * BGK collision with the velocity-shift forcing (Eq. 1-5), the pseudo-potential force (Eq. 13) whose
  * stencil the adjoint applies transposed, and streaming (pull; the adjoint pushes).
  *   With walls, the adjoint includes the moving-wall bounce-back (Eq. 11) and the walls' virtual densities
- *   in the force.  Supported contexts: boxes without meshes, FP32 storage; otherwise SCBB_E_UNSUPPORTED at
- *   creation.
+ *   in the force.  Supported contexts: FP32 storage, no on-site velocity planes, and either no meshes or
+ *   capsules coupled by the 2-point immersed boundary (coupling 1, Sec. II.B-C) without particle-particle
+ *   repulsion; otherwise SCBB_E_UNSUPPORTED at creation.  With capsules the vertex positions are part of the
+ *   state: the adjoint steps back through the interpolation of the velocity (Eq. 6-7), the explicit vertex
+ *   update, the membrane forces (Skalak Eq. 8, Helfrich bending with the cotangent discretisation, volume
+ *   penalty) and their spreading (Eq. 9), which carries the force into the fluid step by the velocity shift
+ *   (Eq. 5).
  *   scbb_adjoint_workspace_bytes(ctx, n, K): device bytes of the adjoint's workspace for n steps with a
  *     population checkpoint every K steps: ceil(n/K) checkpoints, K + 1 lattices, K density fields and (walls)
- *     K wall planes of one segment, two adjoint lattices and 13 + 2 floats per node of scratch.  0 for bad
+ *     K wall planes of one segment, two adjoint lattices and 13 + 2 floats per node of scratch; with capsules
+ *     also ceil(n/K) + K + 1 copies of the vertices, 8 more float4 per vertex and one per triangle corner
+ *     for the membrane's adjoint, and 9 floats per node for the adjoint of the spread force.  0 for bad
  *     arguments.
  *   scbb_adjoint_create(ctx, n, K, dev_workspace, out): dev_workspace caller-owned, at least that many
  *     bytes, 256-byte aligned; the adjoint keeps ctx and runs on its stream.
@@ -273,7 +280,17 @@ scbb_status scbb_batch_set_wait_limit(scbb_batch* batch, long long polls);
  *     doubles in, the adjoint of the final densities; out: host dL_dG (1 double), dL_dg (3 doubles) and
  *     dL_drho0A, dL_drho0B (N doubles each; either may be NULL).  Recomputes each segment of K steps from
  *     its checkpoint, then steps the adjoint backwards through it.  Synchronous.  SCBB_E_STATE before
- *     scbb_adjoint_forward.  All arithmetic is FP32 except the FP64 sums of the parameter gradients. */
+ *     scbb_adjoint_forward.  All arithmetic is FP32 except the FP64 sums of the parameter gradients.  For a
+ *     context with capsules the vertices' adjoint is zero (use scbb_adjoint_backward_capsule to seed it).
+ *   scbb_adjoint_backward_capsule(a, dL_dX, dL_drhoA, dL_drhoB, dL_dmoduli, dL_dX0, dL_dG, dL_dg): the same
+ *     for a context with capsules and a loss L(X(T), rho^A(T), rho^B(T)).  In: dL_dX (host, NV x 3 doubles,
+ *     the vertices in the order of scbb_get_vertices), dL_drhoA and dL_drhoB (N doubles each, or NULL for a
+ *     loss without the densities).  Out: dL_dmoduli (NM x 3 doubles: dL/dkS, dL/dkB, dL/dkV of each
+ *     capsule, Eq. 8 and Sec. II.C), dL_dX0 (NV x 3 doubles, the initial vertex positions; NULL to skip),
+ *     dL_dG, dL_dg (NULL to skip).  SCBB_E_UNSUPPORTED for a context without capsules; SCBB_E_INVAL for a
+ *     NULL dL_dX or dL_dmoduli.  The initial positions' gradient holds X(0) as the membrane's reference
+ *     shape fixed (a displacement of the initial positions without a change of the reference).  The
+ *     vertices' positions after the backward pass are those of step n again. */
 typedef struct scbb_adjoint scbb_adjoint;
 size_t scbb_adjoint_workspace_bytes(const scbb_ctx* ctx, long long n_steps, int checkpoint_every);
 scbb_status scbb_adjoint_create(scbb_ctx* ctx, long long n_steps, int checkpoint_every, void* dev_workspace,
@@ -281,6 +298,9 @@ scbb_status scbb_adjoint_create(scbb_ctx* ctx, long long n_steps, int checkpoint
 scbb_status scbb_adjoint_forward(scbb_adjoint* a);
 scbb_status scbb_adjoint_backward(scbb_adjoint* a, const double* dL_drhoA, const double* dL_drhoB, double* dL_dG,
                                   double* dL_dg, double* dL_drho0A, double* dL_drho0B);
+scbb_status scbb_adjoint_backward_capsule(scbb_adjoint* a, const double* dL_dX, const double* dL_drhoA,
+                                          const double* dL_drhoB, double* dL_dmoduli, double* dL_dX0,
+                                          double* dL_dG, double* dL_dg);
 void scbb_adjoint_destroy(scbb_adjoint* a);
 
 /* State save and load (checkpoint and resume; not in the paper).  scbb_state_bytes: the size of a saved state,

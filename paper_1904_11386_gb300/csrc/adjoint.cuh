@@ -34,11 +34,46 @@ int adj_blocks(const LbmParams& p);
 // with the weights g^c = dL/drho^c (device, N floats per component).
 void launch_adj_final(const LbmParams& p, const float* gA, const float* gB, float* lam, cudaStream_t st);
 
+// Immersed-boundary terms of a step (all [3][N] fields except mask): the spread force the step used and its
+// marks, the adjoint of the half-force velocity it wrote at the marked nodes (in), the adjoint of the spread
+// force and the half-force velocity itself at the marked nodes (out).
+struct AdjIB {
+    const float* Fibm;
+    const uint32_t* mask;
+    const float* luh;
+    float* lfi;
+    float* uh;
+};
+
 // One step backwards: S is the lattice the forward step read, rho the densities it computed, ghost the wall
 // planes' virtual densities it used (4 nxy floats, walls only), lam_in the adjoint of the lattice it wrote;
-// writes lam_out, the adjoint of S.  scr holds ADJ_SCR * N floats, gw 4 nxy floats (walls only).
+// writes lam_out, the adjoint of S.  scr holds ADJ_SCR * N floats, gw 4 nxy floats (walls only).  ib: the
+// immersed-boundary terms of the step, or null.
 void launch_adj_step(const LbmParams& p, const float* S, const float* rho, const float* ghost, const float* lam_in,
-                     float* lam_out, float* scr, float* gw, double* part, cudaStream_t st);
+                     float* lam_out, float* scr, float* gw, double* part, cudaStream_t st, const AdjIB* ib = nullptr);
+
+// ---- adjoint of a capsule coupled by the 2-point immersed boundary (adjoint_capsule.cu)
+// Device buffers of the capsule's part of one backward step.
+struct AdjCap {
+    float4* lx;             // [NV] adjoint of the vertex positions (of X(t + 1) in, of X(t) out)
+    float4* lF;             // [NV] adjoint of the node forces
+    float4* vp;             // [NV] per-vertex products summed per capsule: lF.F_Skalak, lF.F_bend, lF.F_vol, lF.dV
+    float4* vb0;            // [NV] bending, first reverse stage: (mu, lambda_H part, lambda_KG, lambda_A part)
+    float4* vb1;            //      (fb lambda_F, H)
+    float4* va;             // [NV] second stage: (lambda_A, lambda_angle sum, mu, H)
+    float4* vK;             //      adjoint of the corner sum of mean-curvature vectors
+    float4* vN;             //      adjoint of the corner sum of face normals
+    float4* lp;             // [3 NT] per-corner contributions to lambda_X
+    float* luh;             // [3][N] adjoint of the half-force velocity
+    float* lfi;             // [3][N] adjoint of the spread force
+    float* uh;              // [3][N] half-force velocity of the step
+    double* capd;           // [4 NM] dL/dkS, dL/dkB, dL/dkV (summed over the steps), lambda_F . dV of the step
+};
+// luh = the interpolation transposed applied to lx (at X of the step, in d.X)
+void launch_cap_adj_spread(const LbmParams& p, const DevState& d, const AdjCap& a, cudaStream_t st);
+// after the fluid's backward step: lambda_F, the stencil and membrane terms of lx, the parameter sums, and the
+// clearing of the step's fields (d holds the membrane forces and spread force of the step)
+void launch_cap_adj_vertices(const LbmParams& p, const DevState& d, const AdjCap& a, cudaStream_t st);
 
 // dL/drho0^c(x) of an initial equilibrium lattice S0 (f_i = f_eq,i(rho0, u0), linear in rho0 at fixed u0):
 // sum_i lambda0^c[i][x - c_i] S0^c[i][x - c_i] / rho0^c(x), into drho (2 N floats).

@@ -52,13 +52,16 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_final(LbmParams p, const fl
     }
 }
 
-// Local pass (one thread per node, grid-stride over a fixed grid).
-template <bool W>
+// Local pass (one thread per node, grid-stride over a fixed grid).  IB: the step carried the spread force of a
+// 2-point immersed boundary (ib.Fibm at the nodes marked in ib.mask) and wrote the half-force velocity there; ib.luh
+// holds the adjoint of that velocity, and the pass writes the adjoint of the spread force (ib.lfi) and the
+// half-force velocity itself (ib.uh) at the marked nodes.
+template <bool W, bool IB>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(LbmParams p, const float* __restrict__ S,
                                                            const float* __restrict__ rho,
                                                            const float* __restrict__ ghost,
                                                            const float* __restrict__ lam, float* __restrict__ scr,
-                                                           double* __restrict__ part) {
+                                                           double* __restrict__ part, AdjIB ib) {
     float acc[ADJ_PARAMS] = {0.f, 0.f, 0.f, 0.f};
     const size_t N = p.N;
     for (unsigned int n = blockIdx.x * blockDim.x + threadIdx.x; n < p.N; n += gridDim.x * blockDim.x) {
@@ -107,8 +110,19 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(LbmParams p, const fl
         const float rt = ra + rb, irt = 1.f / rt;
         const float up[3] = {jx * irt, jy * irt, jz * irt};
         const float ta = ra > 0.f ? p.tau / ra : 0.f, tb = rb > 0.f ? p.tau / rb : 0.f;
-        const float uA[3] = {up[0] + ta * FA[0], up[1] + ta * FA[1], up[2] + ta * FA[2]};
-        const float uB[3] = {up[0] + tb * FB[0], up[1] + tb * FB[1], up[2] + tb * FB[2]};
+        // spread force (its share rho^c / rho on component c shifts both velocities by tau Fi / rho)
+        bool marked = false;
+        float Fi[3] = {0.f, 0.f, 0.f};
+        if (IB) {
+            marked = (ib.mask[n >> 5] >> (n & 31)) & 1u;
+            if (marked)
+                for (int k = 0; k < 3; k++) Fi[k] = ib.Fibm[(size_t)k * N + n];
+        }
+        const float tf = p.tau * irt;
+        const float uA[3] = {up[0] + ta * FA[0] + tf * Fi[0], up[1] + ta * FA[1] + tf * Fi[1],
+                             up[2] + ta * FA[2] + tf * Fi[2]};
+        const float uB[3] = {up[0] + tb * FB[0] + tf * Fi[0], up[1] + tb * FB[1] + tf * Fi[1],
+                             up[2] + tb * FB[2] + tf * Fi[2]};
         const float uuA = uA[0] * uA[0] + uA[1] * uA[1] + uA[2] * uA[2];
         const float uuB = uB[0] * uB[0] + uB[1] * uB[1] + uB[2] * uB[2];
         // adjoint of f* = f + omega (f_eq(rho, u) - f) through f_eq:
@@ -156,29 +170,52 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(LbmParams p, const fl
             aFB[k] = tb * auB[k];
         }
         const float aupu = aup[0] * up[0] + aup[1] * up[1] + aup[2] * up[2];
+        // immersed boundary: the half-force velocity uh = (j + (F^A + F^B + Fi) / 2) / rho_t (Eq. 5) at a marked
+        // node, with F^c = F_SC^c + rho^c g: its adjoint luh reaches j, both Shan-Chen forces and Fi with
+        // 1 / rho_t, 1 / (2 rho_t), 1 / (2 rho_t), g with 1/2, and rho^c with (g/2 - uh) / rho_t
+        float luh[3] = {0.f, 0.f, 0.f}, rib = 0.f;
+        if (IB && marked) {
+            float uh[3];
+            for (int k = 0; k < 3; k++) {
+                luh[k] = ib.luh[(size_t)k * N + n];
+                uh[k] = (k == 0 ? jx : (k == 1 ? jy : jz)) * irt + 0.5f * (FA[k] + FB[k] + Fi[k]) * irt;
+                ib.uh[(size_t)k * N + n] = uh[k];
+            }
+            // tau Fi / rho_t in both velocities, and uh's 1 / rho_t (its rho^c g / 2 reaches rho^c through the
+            // Shan-Chen force adjoints' g term below)
+            rib = -tf * irt * (aup[0] * Fi[0] + aup[1] * Fi[1] + aup[2] * Fi[2]) -
+                  irt * (luh[0] * uh[0] + luh[1] * uh[1] + luh[2] * uh[2]);
+            for (int k = 0; k < 3; k++) ib.lfi[(size_t)k * N + n] = tf * aup[k] + 0.5f * irt * luh[k];
+        }
+        // the Shan-Chen forces' adjoints: through the velocities and, at marked nodes, through uh
+        float sFA[3], sFB[3];
+        for (int k = 0; k < 3; k++) {
+            sFA[k] = aFA[k] + 0.5f * irt * luh[k];
+            sFB[k] = aFB[k] + 0.5f * irt * luh[k];
+        }
         // rho^c: through f_eq, through tau F^c / rho^c, through rho^c g, through u' = j / rho_t
         const float rA = arA - (ra > 0.f ? (aFA[0] * FA[0] + aFA[1] * FA[1] + aFA[2] * FA[2]) / ra : 0.f) +
-                         (aFA[0] * p.g[0] + aFA[1] * p.g[1] + aFA[2] * p.g[2]) - aupu * irt + wallA;
+                         (sFA[0] * p.g[0] + sFA[1] * p.g[1] + sFA[2] * p.g[2]) - aupu * irt + wallA + rib;
         const float rB = arB - (rb > 0.f ? (aFB[0] * FB[0] + aFB[1] * FB[1] + aFB[2] * FB[2]) / rb : 0.f) +
-                         (aFB[0] * p.g[0] + aFB[1] * p.g[1] + aFB[2] * p.g[2]) - aupu * irt + wallB;
-        const float gpA = -p.G * (aFA[0] * sA[0] + aFA[1] * sA[1] + aFA[2] * sA[2]);
-        const float gpB = -p.G * (aFB[0] * sB[0] + aFB[1] * sB[1] + aFB[2] * sB[2]);
+                         (sFB[0] * p.g[0] + sFB[1] * p.g[1] + sFB[2] * p.g[2]) - aupu * irt + wallB + rib;
+        const float gpA = -p.G * (sFA[0] * sA[0] + sFA[1] * sA[1] + sFA[2] * sA[2]);
+        const float gpB = -p.G * (sFB[0] * sB[0] + sFB[1] * sB[1] + sFB[2] * sB[2]);
         float* o = scr + n;
         o[0 * N] = rA;
         o[1 * N] = rB;
-        o[2 * N] = aup[0] * irt;
-        o[3 * N] = aup[1] * irt;
-        o[4 * N] = aup[2] * irt;
+        o[2 * N] = (aup[0] + luh[0]) * irt;
+        o[3 * N] = (aup[1] + luh[1]) * irt;
+        o[4 * N] = (aup[2] + luh[2]) * irt;
         o[5 * N] = gpA;
         o[6 * N] = gpB;
         for (int k = 0; k < 3; k++) {
-            o[(7 + k) * N] = p.G * pa * aFA[k];
-            o[(10 + k) * N] = p.G * pb * aFB[k];
+            o[(7 + k) * N] = p.G * pa * sFA[k];
+            o[(10 + k) * N] = p.G * pb * sFB[k];
         }
-        // dL/dG = sum_c -psi^c (dL/dF^c . s^c);  dL/dg = sum_c rho^c dL/dF^c
-        acc[0] -= pa * (aFA[0] * sA[0] + aFA[1] * sA[1] + aFA[2] * sA[2]) +
-                  pb * (aFB[0] * sB[0] + aFB[1] * sB[1] + aFB[2] * sB[2]);
-        for (int k = 0; k < 3; k++) acc[1 + k] += ra * aFA[k] + rb * aFB[k];
+        // dL/dG = sum_c -psi^c (dL/dF^c . s^c);  dL/dg = sum_c rho^c dL/dF^c (and uh's g/2)
+        acc[0] -= pa * (sFA[0] * sA[0] + sFA[1] * sA[1] + sFA[2] * sA[2]) +
+                  pb * (sFB[0] * sB[0] + sFB[1] * sB[1] + sFB[2] * sB[2]);
+        for (int k = 0; k < 3; k++) acc[1 + k] += ra * aFA[k] + rb * aFB[k] + 0.5f * luh[k];
     }
     // block sums in a fixed order, added to this block's own slot
     __shared__ float sh[ADJ_PARAMS][ADJ_THREADS / 32];
@@ -304,14 +341,18 @@ void launch_adj_final(const LbmParams& p, const float* gA, const float* gB, floa
 }
 
 void launch_adj_step(const LbmParams& p, const float* S, const float* rho, const float* ghost, const float* lam_in,
-                     float* lam_out, float* scr, float* gw, double* part, cudaStream_t st) {
+                     float* lam_out, float* scr, float* gw, double* part, cudaStream_t st, const AdjIB* ib) {
     const unsigned nb = (p.N + ADJ_THREADS - 1) / ADJ_THREADS;
+    const AdjIB none{};
+    const AdjIB& b = ib ? *ib : none;
     if (p.walls) {
-        k_adj_local<true><<<adj_blocks(p), ADJ_THREADS, 0, st>>>(p, S, rho, ghost, lam_in, scr, part);
+        if (ib) k_adj_local<true, true><<<adj_blocks(p), ADJ_THREADS, 0, st>>>(p, S, rho, ghost, lam_in, scr, part, b);
+        else k_adj_local<true, false><<<adj_blocks(p), ADJ_THREADS, 0, st>>>(p, S, rho, ghost, lam_in, scr, part, b);
         k_adj_wall<<<(2 * p.nxy + ADJ_THREADS - 1) / ADJ_THREADS, ADJ_THREADS, 0, st>>>(p, ghost, scr, gw);
         k_adj_push<true><<<nb, ADJ_THREADS, 0, st>>>(p, rho, lam_in, scr, gw, lam_out);
     } else {
-        k_adj_local<false><<<adj_blocks(p), ADJ_THREADS, 0, st>>>(p, S, rho, ghost, lam_in, scr, part);
+        if (ib) k_adj_local<false, true><<<adj_blocks(p), ADJ_THREADS, 0, st>>>(p, S, rho, ghost, lam_in, scr, part, b);
+        else k_adj_local<false, false><<<adj_blocks(p), ADJ_THREADS, 0, st>>>(p, S, rho, ghost, lam_in, scr, part, b);
         k_adj_push<false><<<nb, ADJ_THREADS, 0, st>>>(p, rho, lam_in, scr, gw, lam_out);
     }
 }

@@ -1220,6 +1220,11 @@ void scbb_batch_destroy(scbb_batch* b) {
 
 struct scbb_adjoint {
     scbb_ctx* c = nullptr;
+    bool ibm = false;           // a capsule coupled by the immersed boundary: its vertices are part of the state
+    float4* Xck = nullptr;      // nseg x NV vertex positions at the checkpoints (ibm)
+    float4* Xs = nullptr;       // K x NV vertex positions of the segment being recomputed (ibm)
+    float4* Xend = nullptr;     // NV: the context's vertices after the forward run, restored after the backward
+    AdjCap cap{};
     long long n = 0;
     int K = 0, nseg = 0;
     float* ckpt = nullptr;      // nseg lattices: the state read by steps 0, K, 2K, ...
@@ -1237,8 +1242,12 @@ struct scbb_adjoint {
 
 namespace {
 
+// the fluid alone, or with capsules coupled by the immersed boundary (no particle-particle repulsion); FP32
+static bool adjoint_ibm(const scbb_ctx* c) {
+    return c->fl.coupling == 1 && c->d.NV > 0 && c->d.NM > 0 && !c->d.pp_head;
+}
 bool adjoint_supported(const scbb_ctx* c) {
-    return c && c->d.NV == 0 && c->d.NM == 0 && c->lp.store == 0 && !c->lp.onsite;
+    return c && (( c->d.NV == 0 && c->d.NM == 0) || adjoint_ibm(c)) && c->lp.store == 0 && !c->lp.onsite;
 }
 
 // Carves the adjoint's buffers (base == nullptr: measures only).
@@ -1261,6 +1270,30 @@ size_t adjoint_layout(const scbb_ctx* c, long long n, int K, void* base, scbb_ad
         a->ckpt = ckpt; a->L = L; a->R = R; a->Gh = Gh; a->gw = gw; a->lam[0] = l0; a->lam[1] = l1;
         a->scr = scr; a->g = g; a->part = part; a->nseg = nseg; a->blocks = adj_blocks(c->lp);
     }
+    if (adjoint_ibm(c)) {
+        const size_t NV = c->d.NV, NT = c->d.NT;
+        float4* Xck = cv.take<float4>(NV * nseg);
+        float4* Xs = cv.take<float4>(NV * K);
+        float4* Xend = cv.take<float4>(NV);
+        AdjCap ac{};
+        ac.lx = cv.take<float4>(NV);
+        ac.lF = cv.take<float4>(NV);
+        ac.vp = cv.take<float4>(NV);
+        ac.vb0 = cv.take<float4>(NV);
+        ac.vb1 = cv.take<float4>(NV);
+        ac.va = cv.take<float4>(NV);
+        ac.vK = cv.take<float4>(NV);
+        ac.vN = cv.take<float4>(NV);
+        ac.lp = cv.take<float4>(3 * NT);
+        ac.luh = cv.take<float>(3 * N);
+        ac.lfi = cv.take<float>(3 * N);
+        ac.uh = cv.take<float>(3 * N);
+        ac.capd = cv.take<double>(4 * (size_t)c->d.NM);
+        if (a) {
+            a->ibm = true;
+            a->Xck = Xck; a->Xs = Xs; a->Xend = Xend; a->cap = ac;
+        }
+    }
     return cv.off + ALIGN;
 }
 
@@ -1277,12 +1310,21 @@ scbb_status scbb_adjoint_create(scbb_ctx* c, long long n, int K, void* ws, scbb_
     if (!c || !ws || n < 1 || K < 1 || ((uintptr_t)ws % ALIGN)) return SCBB_E_INVAL;
     if (c->broken) return SCBB_E_STATE;
     if (!adjoint_supported(c))
-        return fail(c, SCBB_E_UNSUPPORTED, "adjoint: boxes without meshes, FP32 storage, no on-site planes only");
+        return fail(c, SCBB_E_UNSUPPORTED, "adjoint: the fluid alone or with immersed-boundary capsules (no "
+                    "repulsion), FP32 storage, no on-site planes");
     scbb_adjoint* a = new scbb_adjoint;
     a->c = c;
     a->n = n;
     a->K = K;
     adjoint_layout(c, n, K, ws, a);
+    if (a->ibm) {
+        // the spread-force adjoint and half-force velocity fields start (and are kept) at zero
+        const size_t N = c->lp.N;
+        CUDA_TRY(c, cudaMemsetAsync(a->cap.luh, 0, sizeof(float) * 3 * N, c->st));
+        CUDA_TRY(c, cudaMemsetAsync(a->cap.lfi, 0, sizeof(float) * 3 * N, c->st));
+        CUDA_TRY(c, cudaMemsetAsync(a->cap.uh, 0, sizeof(float) * 3 * N, c->st));
+        CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    }
     *out = a;
     return SCBB_OK;
 }
@@ -1295,6 +1337,9 @@ scbb_status scbb_adjoint_forward(scbb_adjoint* a) {
     for (int s = 0; s < a->nseg; s++) {
         CUDA_TRY(c, cudaMemcpyAsync(a->ckpt + (size_t)s * 2 * Q * c->lp.N, c->d.S[c->cur], lat_bytes,
                                     cudaMemcpyDeviceToDevice, c->st));
+        if (a->ibm)
+            CUDA_TRY(c, cudaMemcpyAsync(a->Xck + (size_t)s * c->d.NV, c->d.X, sizeof(float4) * c->d.NV,
+                                        cudaMemcpyDeviceToDevice, c->st));
         const long long len = std::min<long long>(a->K, a->n - (long long)s * a->K);
         const scbb_status r = scbb_step(c, len);
         if (r != SCBB_OK) return r;
@@ -1303,40 +1348,83 @@ scbb_status scbb_adjoint_forward(scbb_adjoint* a) {
     return SCBB_OK;
 }
 
-scbb_status scbb_adjoint_backward(scbb_adjoint* a, const double* gA, const double* gB, double* dG, double* dg,
-                                  double* drA, double* drB) {
-    if (!a || !gA || !gB || !dG || !dg) return SCBB_E_INVAL;
+// The backward pass shared by both entry points: gA, gB the adjoint of the final densities (host, may be null:
+// zero), gX that of the final vertex positions (host NV x 3, capsule contexts; may be null: zero).
+static scbb_status adjoint_backward_core(scbb_adjoint* a, const double* gA, const double* gB, const double* gX,
+                                         double* dG, double* dg, double* drA, double* drB, double* dmod,
+                                         double* dX0) {
     scbb_ctx* c = a->c;
     if (c->broken) return SCBB_E_STATE;
     if (!a->forward_done) return fail(c, SCBB_E_STATE, "adjoint: scbb_adjoint_forward has not run");
     const size_t N = c->lp.N, lat = (size_t)2 * Q * N;
+    const int NV = c->d.NV, NM = c->d.NM;
     std::vector<float> h(2 * N);
     for (size_t q = 0; q < N; q++) {
-        h[q] = (float)gA[q];
-        h[N + q] = (float)gB[q];
+        h[q] = gA ? (float)gA[q] : 0.f;
+        h[N + q] = gB ? (float)gB[q] : 0.f;
     }
     CUDA_TRY(c, cudaMemcpyAsync(a->g, h.data(), sizeof(float) * 2 * N, cudaMemcpyHostToDevice, c->st));
     CUDA_TRY(c, cudaMemsetAsync(a->part, 0, sizeof(double) * ADJ_PARAMS * a->blocks, c->st));
+    std::vector<float4> hx;
+    if (a->ibm) {
+        hx.resize(NV);
+        for (int v = 0; v < NV; v++)
+            hx[v] = gX ? make_float4((float)gX[3 * v], (float)gX[3 * v + 1], (float)gX[3 * v + 2], 0.f)
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        CUDA_TRY(c, cudaMemcpyAsync(a->cap.lx, hx.data(), sizeof(float4) * NV, cudaMemcpyHostToDevice, c->st));
+        CUDA_TRY(c, cudaMemsetAsync(a->cap.capd, 0, sizeof(double) * 4 * NM, c->st));
+        CUDA_TRY(c, cudaMemcpyAsync(a->Xend, c->d.X, sizeof(float4) * NV, cudaMemcpyDeviceToDevice, c->st));
+    }
     launch_adj_final(c->lp, a->g, a->g + N, a->lam[0], c->st);
     c->launches++;
+    const AdjIB ib{c->d.Fibm, c->d.mask, a->cap.luh, a->cap.lfi, a->cap.uh};
     int cur = 0;
     for (int s = a->nseg - 1; s >= 0; s--) {
         const int len = (int)std::min<long long>(a->K, a->n - (long long)s * a->K);
         CUDA_TRY(c, cudaMemcpyAsync(a->L, a->ckpt + (size_t)s * lat, sizeof(float) * lat, cudaMemcpyDeviceToDevice,
                                     c->st));
+        if (a->ibm)
+            CUDA_TRY(c, cudaMemcpyAsync(c->d.X, a->Xck + (size_t)s * NV, sizeof(float4) * NV,
+                                        cudaMemcpyDeviceToDevice, c->st));
         // recompute the segment with the forward kernels, keeping every lattice, density field and wall plane
+        // (and, with a capsule, every vertex position)
         const size_t nw = (size_t)4 * c->lp.nxy;
         for (int k = 0; k < len; k++) {
             float* gh = c->lp.walls ? a->Gh + (size_t)k * nw : c->d.ghost;
+            if (a->ibm) {
+                CUDA_TRY(c, cudaMemcpyAsync(a->Xs + (size_t)k * NV, c->d.X, sizeof(float4) * NV,
+                                            cudaMemcpyDeviceToDevice, c->st));
+                c->launches += launch_membrane_forces(c->lp, c->d, false, 0, c->st);
+                launch_ibm_spread(c->lp, c->d, c->st);
+                c->launches++;
+            }
             if (c->lp.walls && !bulk_writes_ghost(c->lp))
                 launch_wall_ghost(c->lp, a->L + (size_t)k * lat, c->d.wall_rho, gh, c->st);
             launch_bulk(c->lp, a->L + (size_t)k * lat, a->L + (size_t)(k + 1) * lat, a->R + (size_t)k * 2 * N, c->d.J, gh,
-                        nullptr, nullptr, nullptr, c->d.err, 0, c->st);
+                        a->ibm ? c->d.Fibm : nullptr, a->ibm ? c->d.mask : nullptr, a->ibm ? c->d.u : nullptr,
+                        c->d.err, a->ibm ? 1 : 0, c->st);
+            if (a->ibm) {
+                launch_ibm_interp(c->lp, c->d, c->st);
+                c->launches++;
+            }
         }
         for (int k = len - 1; k >= 0; k--) {
             const float* gh = c->lp.walls ? a->Gh + (size_t)k * nw : nullptr;
+            if (a->ibm) {
+                // the step's membrane forces and spread force at X(t), and the interpolation transposed
+                CUDA_TRY(c, cudaMemcpyAsync(c->d.X, a->Xs + (size_t)k * NV, sizeof(float4) * NV,
+                                            cudaMemcpyDeviceToDevice, c->st));
+                c->launches += launch_membrane_forces(c->lp, c->d, false, 0, c->st);
+                launch_ibm_spread(c->lp, c->d, c->st);
+                launch_cap_adj_spread(c->lp, c->d, a->cap, c->st);
+                c->launches += 2;
+            }
             launch_adj_step(c->lp, a->L + (size_t)k * lat, a->R + (size_t)k * 2 * N, gh, a->lam[cur],
-                            a->lam[1 - cur], a->scr, a->gw, a->part, c->st);
+                            a->lam[1 - cur], a->scr, a->gw, a->part, c->st, a->ibm ? &ib : nullptr);
+            if (a->ibm) {
+                launch_cap_adj_vertices(c->lp, c->d, a->cap, c->st);
+                c->launches += 6;
+            }
             cur ^= 1;
         }
         c->launches += ((c->lp.walls ? 5 : 2) + (bulk_split(c->lp) ? 2 : 1) -
@@ -1348,17 +1436,51 @@ scbb_status scbb_adjoint_backward(scbb_adjoint* a, const double* gA, const doubl
     std::vector<double> part((size_t)ADJ_PARAMS * a->blocks);
     CUDA_TRY(c, cudaMemcpyAsync(part.data(), a->part, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, c->st));
     CUDA_TRY(c, cudaMemcpyAsync(h.data(), a->g, sizeof(float) * 2 * N, cudaMemcpyDeviceToHost, c->st));
+    std::vector<double> capd;
+    if (a->ibm) {
+        capd.resize(4 * (size_t)NM);
+        CUDA_TRY(c, cudaMemcpyAsync(capd.data(), a->cap.capd, sizeof(double) * capd.size(), cudaMemcpyDeviceToHost,
+                                    c->st));
+        CUDA_TRY(c, cudaMemcpyAsync(hx.data(), a->cap.lx, sizeof(float4) * NV, cudaMemcpyDeviceToHost, c->st));
+        CUDA_TRY(c, cudaMemcpyAsync(c->d.X, a->Xend, sizeof(float4) * NV, cudaMemcpyDeviceToDevice, c->st));
+    }
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
     double acc[ADJ_PARAMS] = {0, 0, 0, 0};
     for (int b = 0; b < a->blocks; b++)
         for (int k = 0; k < ADJ_PARAMS; k++) acc[k] += part[(size_t)b * ADJ_PARAMS + k];
-    *dG = acc[0];
-    for (int k = 0; k < 3; k++) dg[k] = acc[1 + k];
+    if (dG) *dG = acc[0];
+    if (dg)
+        for (int k = 0; k < 3; k++) dg[k] = acc[1 + k];
     for (size_t q = 0; q < N; q++) {
         if (drA) drA[q] = h[q];
         if (drB) drB[q] = h[N + q];
     }
-    return SCBB_OK;
+    if (a->ibm) {
+        if (dmod)
+            for (int m = 0; m < NM; m++)
+                for (int k = 0; k < 3; k++) dmod[3 * m + k] = capd[4 * m + k];
+        if (dX0)
+            for (int v = 0; v < NV; v++) {
+                dX0[3 * v] = hx[v].x;
+                dX0[3 * v + 1] = hx[v].y;
+                dX0[3 * v + 2] = hx[v].z;
+            }
+    }
+    return check_device_error(c);
+}
+
+scbb_status scbb_adjoint_backward(scbb_adjoint* a, const double* gA, const double* gB, double* dG, double* dg,
+                                  double* drA, double* drB) {
+    if (!a || !gA || !gB || !dG || !dg) return SCBB_E_INVAL;
+    return adjoint_backward_core(a, gA, gB, nullptr, dG, dg, drA, drB, nullptr, nullptr);
+}
+
+scbb_status scbb_adjoint_backward_capsule(scbb_adjoint* a, const double* dL_dX, const double* dL_drhoA,
+                                          const double* dL_drhoB, double* dL_dmoduli, double* dL_dX0, double* dL_dG,
+                                          double* dL_dg) {
+    if (!a || !dL_dX || !dL_dmoduli) return SCBB_E_INVAL;
+    if (!a->ibm) return fail(a->c, SCBB_E_UNSUPPORTED, "adjoint: the context has no immersed-boundary capsule");
+    return adjoint_backward_core(a, dL_drhoA, dL_drhoB, dL_dX, dL_dG, dL_dg, nullptr, nullptr, dL_dmoduli, dL_dX0);
 }
 
 void scbb_adjoint_destroy(scbb_adjoint* a) { delete a; }

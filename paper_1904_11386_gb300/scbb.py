@@ -23,6 +23,7 @@ EXPORTS = ["scbb_workspace_bytes", "scbb_create", "scbb_set_density", "scbb_step
            "scbb_population_moments_noalloc", "scbb_batch_create", "scbb_batch_step", "scbb_batch_destroy",
            "scbb_batch_shared_bulk", "scbb_batch_set_wait_limit",
            "scbb_adjoint_workspace_bytes", "scbb_adjoint_create", "scbb_adjoint_forward", "scbb_adjoint_backward",
+           "scbb_adjoint_backward_capsule",
            "scbb_adjoint_destroy", "scbb_state_bytes", "scbb_save", "scbb_load", "scbb_last_error", "scbb_destroy"]
 
 
@@ -120,6 +121,8 @@ def load(path: str = LIB_PATH):
     L.scbb_adjoint_forward.argtypes = [vp]
     L.scbb_adjoint_backward.restype = C.c_int
     L.scbb_adjoint_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.scbb_adjoint_backward_capsule.restype = C.c_int
+    L.scbb_adjoint_backward_capsule.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     L.scbb_adjoint_destroy.restype = None
     L.scbb_adjoint_destroy.argtypes = [vp]
     _lib = L
@@ -397,7 +400,7 @@ class Adjoint:
         nbytes = self.L.scbb_adjoint_workspace_bytes(sim.h, self.n, self.K)
         if nbytes == 0:
             raise ScbbError("scbb_adjoint_workspace_bytes: unsupported context or arguments "
-                            "(periodic boxes without meshes, FP32 storage)")
+                            "(FP32 storage; no meshes, or immersed-boundary capsules without repulsion)")
         self.nbytes = int(nbytes)
         self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=sim.workspace.device)
         h = C.c_void_p()
@@ -424,6 +427,20 @@ class Adjoint:
                         "scbb_adjoint_backward")
         s = (p.nz, p.ny, p.nx)
         return float(dG[0]), dg, ra.reshape(s), rb.reshape(s)
+
+    def scbb_adjoint_backward_capsule(self, dL_dX, dL_drhoA=None, dL_drhoB=None):
+        """Adjoint of the final vertex positions (NV x 3) and, optionally, of the final densities in; returns
+        (dL/dmoduli (NM x 3: kS, kB, kV), dL/dX0 (NV x 3), dL/dG, dL/dg[3])."""
+        p = self.sim.prob
+        x = np.ascontiguousarray(dL_dX, np.float64).reshape(-1, 3)
+        a = None if dL_drhoA is None else np.ascontiguousarray(dL_drhoA, np.float64).ravel()
+        b = None if dL_drhoB is None else np.ascontiguousarray(dL_drhoB, np.float64).ravel()
+        nm = len(p.capsules)
+        dmod, dx0 = np.zeros((nm, 3)), np.zeros_like(x)
+        dG, dg = np.zeros(1), np.zeros(3)
+        self.sim._check(self.L.scbb_adjoint_backward_capsule(self.h, _p(x), _p(a), _p(b), _p(dmod), _p(dx0), _p(dG),
+                                                             _p(dg)), "scbb_adjoint_backward_capsule")
+        return dmod, dx0, float(dG[0]), dg
 
     def scbb_adjoint_destroy(self):
         self.close()

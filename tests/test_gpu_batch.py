@@ -95,14 +95,16 @@ def test_batch_against_oracle():
     """Three boxes of the sweep's kind (edges 41, 44 and 50: one quad-form and two node-form lattices), each
     with a capsule of its own colour and shear modulus at the interface, 10 steps of the batch with its shared
     bulk phase and 10 of the same batch with one bulk phase per box, each against the FP64 oracle: owner fields
-    identical, vertices within 1e-4, densities within 1e-5 relative except next to the membrane (boundary
+    identical, densities within 1e-5 relative except next to the membrane (boundary
     nodes, nodes that turned fresh during the run, and their neighbours), which are held to 2e-3.  Two discrete
     decisions there can come out differently in FP32 and FP64 without changing the owner field: a fresh node's
     density carries Eq. 18, which multiplies the global mass error by C0 sum(rho_init) / rho_init^c / V_sys
     (about 0.6 per unit of mass here for the minority component), so the FP32 state's total mass, one rounding
     of about 2e-8 of itself away from the oracle's, moves it by a few 1e-4; and a link that crosses the
     membrane next to a shared edge can be given the neighbouring element, whose velocity enters its bounce-back
-    (the 44-wide box meets one at step 9: 8e-4 at that node)."""
+    (the 44-wide box meets one at step 9: 8e-4 at that node, and 3.5e-4 on the vertices of the two elements).
+    Either element belongs to the same capsule, which therefore receives the same momentum: the mean of each
+    capsule's vertices is held to 1e-5, single vertices to 1e-3."""
     from oracle import oracle as O
     from paper_1904_11386_gb300 import scbb
 
@@ -139,7 +141,11 @@ def test_batch_against_oracle():
             err[~fl] = 0.0
             assert err[~near_fresh].max() < 1e-5, (p.name, shared, err[~near_fresh].max())
             assert err.max() < 2e-3, (p.name, shared, err.max())
-            assert np.abs(g.scbb_get_vertices()[0] - o.vertices()[0]).max() < 1e-4
+            # the crossed-element event moves one element's momentum to its neighbour: vertices there differ by
+            # a few 1e-4, while the capsule's momentum, and so the mean of its vertices, is the same either way
+            gx, ox = g.scbb_get_vertices()[0], o.vertices()[0]
+            assert np.abs(gx - ox).max() < 1e-3
+            assert np.abs(gx.mean(0) - ox.mean(0)).max() < 1e-5
         batch.close()
 
 
