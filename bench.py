@@ -72,10 +72,16 @@ def workload(name: str):
         return p, (f"droplet128: 128^3 periodic two-component box, B droplet R=35 covered by {len(p.capsules)} s=3 "
                    "capsules R=8 with colours +-0.05, half-way bounce-back, repulsion")
     if name == "adjoint64":
-        return inputs.cfg_adjoint(n=64, R_drop=16.0), ("adjoint64: 64^3 periodic two-component box, B droplet R=16, "
-                                                       "gradient of the components' weighted centres of mass "
-                                                       "after 2000 steps w.r.t. G, g and the initial densities, "
-                                                       "checkpoint every 100 steps")
+        return inputs.cfg_adjoint64(coupling=1), ("adjoint64: 64^3 box between walls, flat interface, one s=3 "
+                                                  "capsule R=8 (642 vertices) 4 above it, 2-point immersed "
+                                                  "boundary; gradient of the capsule's centre-of-mass height "
+                                                  "after 2000 steps w.r.t. kS, kB, kV, the initial vertices, G "
+                                                  "and g, checkpoint every 100 steps")
+    if name == "adjoint64-fluid":
+        return inputs.cfg_adjoint(n=64, R_drop=16.0), ("adjoint64-fluid: 64^3 periodic two-component box, B "
+                                                       "droplet R=16, gradient of the components' weighted "
+                                                       "centres of mass after 2000 steps w.r.t. G, g and the "
+                                                       "initial densities, checkpoint every 100 steps")
     if name == "fluid256":
         p = inputs.cfg_droplet256(n_caps=0, coupling=1)
         p.capsules = []
@@ -167,7 +173,8 @@ def aggregate_glups(nodes: int, steps: int, ws: int, seconds: float) -> float:
     return nodes * steps * ws / seconds / 1e9
 
 
-KERNEL_SOURCES = ("paper_1904_11386_gb300/csrc/lbm_kernels.cu", "paper_1904_11386_gb300/csrc/scbb_internal.cuh")
+KERNEL_SOURCES = ("paper_1904_11386_gb300/csrc/bulk_split.cu", "paper_1904_11386_gb300/csrc/pull.cuh",
+                  "paper_1904_11386_gb300/csrc/scbb_internal.cuh")
 
 
 def kernel_source_hash() -> str:
@@ -402,9 +409,11 @@ def run_reference_batch(args, probs, label, rank):
 
 
 def run_adjoint(args, prob, label, ws, rank, local, n_steps=2000, every=100):
-    """Forward (n steps with a population checkpoint every `every` steps) and backward (recompute each
-    segment, adjoint steps) of the fluid adjoint, each timed with CUDA events on the context stream after a
-    warm-up pair; value = backward time / forward time."""
+    """Forward (n steps with a checkpoint every `every` steps) and backward (recompute each segment, adjoint
+    steps) of the adjoint, each timed with CUDA events on the context stream after a warm-up pair; value =
+    backward time / forward time.  With a capsule the loss is its centre-of-mass height (the mean z of its
+    vertices) and the gradients are those of scbb_adjoint_backward_capsule; without, the weighted centres of
+    mass of the two components."""
     import numpy as np
     import torch
 
@@ -416,18 +425,26 @@ def run_adjoint(args, prob, label, ws, rank, local, n_steps=2000, every=100):
     wA, wB = z.astype(np.float64), 0.5 * x.astype(np.float64)
     sim = scbb.Sim(prob, rhoA0, rhoB0, device=f"cuda:{local}")
     shape = sim.scbb_autotune()              # a single 64^3 box fills the GPU only with short z-segments
+    capsule = bool(prob.capsules)
+    nv = int(sum(sim.nv))
+    state0 = sim.scbb_save()                 # the initial state (populations and vertices) of both passes
     adj = scbb.Adjoint(sim, n_steps, every)
     st = sim.stream
     times = []
     for rep in range(2):                     # the first pair warms up
-        sim.scbb_set_density(rhoA0, rhoB0)
+        sim.scbb_load(state0)
         sim.scbb_sync()
         l0 = sim.scbb_launch_count()
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(st)
         adj.scbb_adjoint_forward()
         e1.record(st)
-        dG, dg, _, _ = adj.scbb_adjoint_backward(wA, wB)
+        if capsule:
+            gX = np.zeros((nv, 3))
+            gX[:, 2] = 1.0 / nv
+            dmod, _, dG, dg = adj.scbb_adjoint_backward_capsule(gX)
+        else:
+            dG, dg, _, _ = adj.scbb_adjoint_backward(wA, wB)
         e2.record(st)
         torch.cuda.synchronize()
         times.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
@@ -436,7 +453,8 @@ def run_adjoint(args, prob, label, ws, rank, local, n_steps=2000, every=100):
     fwd_ms = replica_max(fwd_ms, ws, f"cuda:{local}")
     bwd_ms = replica_max(bwd_ms, ws, f"cuda:{local}")
     nodes = prob.n_nodes
-    out = {"metric": f"fluid adjoint backward / forward time ({n_steps} steps, checkpoint every {every})",
+    what = "capsule (immersed boundary) adjoint" if capsule else "fluid adjoint"
+    out = {"metric": f"{what} backward / forward time ({n_steps} steps, checkpoint every {every})",
            "value": bwd_ms / fwd_ms, "unit": "x", "n_gpus": ws, "steps": n_steps, "warmup": 1,
            "ms_per_step": (fwd_ms + bwd_ms) / n_steps, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -448,6 +466,9 @@ def run_adjoint(args, prob, label, ws, rank, local, n_steps=2000, every=100):
            "gradients": {"dL_dG": dG, "dL_dg": list(map(float, dg))},
            "gradient_check": "tests/test_gpu_adjoint.py: FP64 central differences of the oracle, 32^3, 100 steps",
            "gpu_launches": launches}
+    if capsule:
+        out["gradients"].update({"dCOMz_dkS": float(dmod[0, 0]), "dCOMz_dkB": float(dmod[0, 1]),
+                                 "dCOMz_dkV": float(dmod[0, 2])})
     adj.close()
     sim.close()
     return out
@@ -499,7 +520,7 @@ def main():
 
     ws, rank, local = dist_setup()
     prob, label = workload(args.workload)
-    if args.workload == "adjoint64" and args.impl == "ours":
+    if args.workload in ("adjoint64", "adjoint64-fluid") and args.impl == "ours":
         out = run_adjoint(args, prob, label, ws, rank, local, n_steps=args.adj_steps, every=args.adj_every)
         if rank == 0:
             print(json.dumps(out), flush=True)
@@ -635,6 +656,11 @@ def main():
                                               "adjoint_workspace_bytes", "gpu_launches")}
         out["adjoint64"]["metric"] = a["metric"]
         out["adjoint64"]["workload"] = alabel
+        fprob, flabel = workload("adjoint64-fluid")
+        f = run_adjoint(args, fprob, flabel, ws, rank, local, n_steps=args.adj_steps, every=args.adj_every)
+        out["adjoint64"]["fluid_only"] = {k: f[k] for k in ("value", "unit", "forward_ms", "backward_ms",
+                                                            "adjoint_workspace_bytes", "gpu_launches", "metric")}
+        out["adjoint64"]["fluid_only"]["workload"] = flabel
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
     if rank == 0:

@@ -198,9 +198,10 @@ scbb_status scbb_phase_times(scbb_ctx* ctx, double* ms, long long* steps);
  *   out5    host double[5]: mass of component A, mass of component B, total momentum x, y, z
  * Allocates nothing: its scratch is a fixed file-scope device array of 512 x 5 partial sums plus 5 results
  * (about 20 KB, held on every GPU that loads the library until exit).  Inputs with more than
- * SCBB_NOALLOC_MAX_NODES nodes are rejected with SCBB_E_INVAL.  The first call on a device looks up the
- * array's device address once (cudaGetSymbolAddress); make that first call before any stream capture.
- * Runs on cuda_stream (NULL = legacy default) and synchronises it.  All calls share the one scratch array
+ * SCBB_NOALLOC_MAX_NODES nodes are rejected with SCBB_E_INVAL.  Every call looks up the array's address on
+ * the current device (cudaGetSymbolAddress), copies the result to the host and synchronises cuda_stream
+ * (NULL = legacy default), so it must never be called on a stream under capture; dev_f must live on the
+ * current device and cuda_stream belong to it.  All calls share the one scratch array
  * (every call overwrites all of it), so calls that overlap on the GPU, from several streams or threads,
  * race and must be serialised by the caller. */
 #define SCBB_NOALLOC_MAX_NODES 50000000
@@ -216,6 +217,15 @@ scbb_status scbb_population_moments_noalloc(const float* dev_f, int nx, int ny, 
  * context runs the general bulk kernel (nx not a multiple of 4), which has no shapes.  Synchronous; call it
  * between steps, not while a batch holds the context. */
 scbb_status scbb_autotune(scbb_ctx* ctx, int reps, int* chosen);
+
+/* Bound of the bulk phase's waits on its asynchronous copies (not in the paper).  The bulk kernels of a box
+ * whose rows are a multiple of 4 nodes bring their inputs into shared memory by bulk asynchronous copies
+ * and wait for each on an mbarrier; a wait polls at most `polls` times (default 4194304, about a second at
+ * most) and then gives up: the kernel raises bit 4 of the device error word, lets its copies land and
+ * returns, so the next synchronising call reports SCBB_E_TIMEOUT and later calls SCBB_E_STATE until
+ * scbb_load restores a saved state.  polls = 0 gives up at the first poll that finds a copy still in
+ * flight.  SCBB_E_INVAL for polls < 0.  Call it between steps, not while a batch holds the context. */
+scbb_status scbb_set_wait_limit(scbb_ctx* ctx, long long polls);
 
 /* Batches (not in the paper): step several independent contexts together, for example a sweep of boxes of
  * different sizes and parameters.  ctxs: n distinct contexts, kept alive by the caller until

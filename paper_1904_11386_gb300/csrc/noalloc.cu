@@ -5,8 +5,6 @@
 // synchronisation and the risk of an out-of-memory failure in the middle of a run.
 #include <stdio.h>
 
-#include <mutex>
-
 #include "scbb_internal.cuh"
 
 namespace scbb {
@@ -64,28 +62,6 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) k_noalloc_sum(double* scratch
     }
 }
 
-// Device address of the scratch array, looked up once per device (with that device current).
-static double* scratch_address(int dev, cudaError_t* err) {
-    static std::mutex mu;
-    static void* addr[128] = {};
-    std::lock_guard<std::mutex> lock(mu);
-    *err = cudaSuccess;
-    if (dev < 0 || dev >= 128) {
-        *err = cudaErrorInvalidDevice;
-        return nullptr;
-    }
-    if (!addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) {
-            *err = e;
-            return nullptr;
-        }
-        addr[dev] = p;
-    }
-    return (double*)addr[dev];
-}
-
 }  // namespace scbb
 
 using namespace scbb;
@@ -99,11 +75,11 @@ extern "C" scbb_status scbb_population_moments_noalloc(const float* dev_f, int n
                 SCBB_NOALLOC_MAX_NODES);
         return SCBB_E_INVAL;
     }
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return SCBB_E_CUDA;
-    cudaError_t e;
-    double* scratch = scratch_address(dev, &e);
-    if (!scratch) return SCBB_E_CUDA;
+    // the array's address on the current device, looked up on every call (a cached address would outlive a
+    // reset of the device's primary context)
+    void* addr = nullptr;
+    if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr) return SCBB_E_CUDA;
+    double* scratch = (double*)addr;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const unsigned int N = (unsigned int)nodes;
     k_noalloc_moments<<<NOALLOC_BLOCKS, NOALLOC_THREADS, 0, st>>>(dev_f, N, nx * ny, nz, walls, scratch);

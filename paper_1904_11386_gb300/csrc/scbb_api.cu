@@ -160,6 +160,7 @@ LbmParams make_params(const scbb_lattice* lat, const scbb_fluid* fl) {
     // replaces it); results do not depend on the shape
     const char* e = getenv("SCBB_BULK_SHAPE");
     if (e && e[0] >= '0' && e[0] < '0' + B4_CONFIGS && e[1] == 0) p.b4cfg = e[0] - '0';
+    p.wait_limit = 1LL << 22;
     return p;
 }
 
@@ -315,8 +316,9 @@ scbb_status check_device_error(scbb_ctx* c) {
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
     if (h & 4) {
         c->broken = 1;
-        return fail(c, SCBB_E_TIMEOUT, "device error word %d after %lld steps: a bounded wait of the batch's "
-                    "shared bulk phase gave up (its step is incomplete)", h, c->steps);
+        return fail(c, SCBB_E_TIMEOUT, "device error word %d after %lld steps: a bounded wait of the bulk phase "
+                    "(its asynchronous copies, or a batch's grid barrier) gave up; the step is incomplete", h,
+                    c->steps);
     }
     if (h) {
         c->broken = 1;
@@ -1055,6 +1057,18 @@ scbb_status scbb_autotune(scbb_ctx* c, int reps, int* chosen) {
     c->gkey = -1;
     c->eager_steps = 0;
     if (chosen) *chosen = best_k;
+    return SCBB_OK;
+}
+
+scbb_status scbb_set_wait_limit(scbb_ctx* c, long long polls) {
+    if (!c || polls < 0) return SCBB_E_INVAL;
+    if (c->broken) return SCBB_E_STATE;
+    c->lp.wait_limit = polls;
+    // the captured step pairs hold the old limit
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->gkey = -1;
+    c->eager_steps = 0;
     return SCBB_OK;
 }
 

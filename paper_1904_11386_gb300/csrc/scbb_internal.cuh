@@ -54,6 +54,7 @@ struct LbmParams {
     int b4cfg;              // shape of the row-vectorised bulk kernel, 0 .. B4_CONFIGS - 1 (scbb_autotune)
     int onsite;             // 1: resting walls (ulo = uhi = 0) and on-site velocity planes z = 1 (vlo), nz-2 (vhi)
     float vlo[3], vhi[3];
+    long long wait_limit;   // polls of a bounded wait on asynchronous copies before it gives up (error bit 4)
 };
 
 // Shapes of the row-vectorised bulk kernel: (threads per CTA, CTAs per SM, fewest planes per z-segment) =

@@ -20,6 +20,7 @@ STATUS = {0: "SCBB_OK", 1: "SCBB_E_INVAL", 2: "SCBB_E_CUDA", 3: "SCBB_E_NOMEM", 
 EXPORTS = ["scbb_workspace_bytes", "scbb_create", "scbb_set_density", "scbb_step", "scbb_sync",
            "scbb_get_fields", "scbb_get_populations", "scbb_get_vertices", "scbb_get_diag", "scbb_get_owner",
            "scbb_launch_count", "scbb_enable_timing", "scbb_kernel_time", "scbb_phase_times", "scbb_autotune",
+           "scbb_set_wait_limit",
            "scbb_population_moments_noalloc", "scbb_batch_create", "scbb_batch_step", "scbb_batch_destroy",
            "scbb_batch_shared_bulk", "scbb_batch_set_wait_limit",
            "scbb_adjoint_workspace_bytes", "scbb_adjoint_create", "scbb_adjoint_forward", "scbb_adjoint_backward",
@@ -95,6 +96,8 @@ def load(path: str = LIB_PATH):
     L.scbb_load.argtypes = [vp, vp, C.c_size_t]
     L.scbb_autotune.restype = C.c_int
     L.scbb_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
+    L.scbb_set_wait_limit.restype = C.c_int
+    L.scbb_set_wait_limit.argtypes = [vp, C.c_longlong]
     L.scbb_phase_times.restype = C.c_int
     L.scbb_phase_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
     L.scbb_population_moments_noalloc.restype = C.c_int
@@ -166,9 +169,10 @@ def scbb_population_moments_noalloc(f_dev, nx, ny, nz, walls, stream=None):
         raise ScbbError("f_dev has the wrong size")
     L = load()
     out = np.zeros(5)
-    st = (stream or torch.cuda.current_stream(f_dev.device)).cuda_stream
-    rc = L.scbb_population_moments_noalloc(C.c_void_p(f_dev.data_ptr()), nx, ny, nz, int(walls), _p(out),
-                                           C.c_void_p(st))
+    with torch.cuda.device(f_dev.device):        # the C call works on the current device
+        st = (stream or torch.cuda.current_stream(f_dev.device)).cuda_stream
+        rc = L.scbb_population_moments_noalloc(C.c_void_p(f_dev.data_ptr()), nx, ny, nz, int(walls), _p(out),
+                                               C.c_void_p(st))
     if rc != SCBB_OK:
         raise ScbbError(f"scbb_population_moments_noalloc: {STATUS.get(rc, rc)}")
     return out
@@ -297,6 +301,10 @@ class Sim:
         k = C.c_int(-1)
         self._check(self.L.scbb_autotune(self.h, int(reps), C.byref(k)), "scbb_autotune")
         return k.value
+
+    def scbb_set_wait_limit(self, polls):
+        """Polls of the bulk phase's bounded waits on its asynchronous copies before they give up."""
+        self._check(self.L.scbb_set_wait_limit(self.h, int(polls)), "scbb_set_wait_limit")
 
     def scbb_state_bytes(self):
         return int(self.L.scbb_state_bytes(self.h))

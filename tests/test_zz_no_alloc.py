@@ -41,6 +41,27 @@ def test_population_moments_noalloc_matches_get_diag():
         sim.close()
 
 
+def test_population_moments_noalloc_grid_stride():
+    """A 64^3 two-component array with walls (262144 nodes, twice the 131072 threads of the launch, so every
+    thread's grid-stride loop takes two nodes): the sums equal numpy's FP64 sums of the same FP32 values to
+    1e-9 relative."""
+    import torch
+
+    from paper_1904_11386_gb300 import scbb
+
+    n = 64
+    rng = np.random.Generator(np.random.PCG64(23))
+    f = rng.uniform(0.0, 0.1, size=(2, 19, n * n * n)).astype(np.float32)
+    out = scbb.scbb_population_moments_noalloc(torch.from_numpy(f).cuda(), n, n, n, 1)
+    fl = f.reshape(2, 19, n, n * n)[:, :, 1:n - 1].astype(np.float64)       # wall planes left out
+    from oracle import oracle as O
+
+    c = O.d3q19()[0].astype(np.float64)                  # [i][xyz], the order of scbb_get_populations
+    tot = fl.sum(axis=3).sum(axis=2)                     # [c][i]
+    ref = np.concatenate([tot.sum(axis=1), (tot.sum(axis=0)[:, None] * c).sum(axis=0)])
+    assert np.allclose(out, ref, rtol=1e-9, atol=1e-9 * ref[:2].sum())
+
+
 def test_population_moments_noalloc_rejects_oversize():
     import torch
 
