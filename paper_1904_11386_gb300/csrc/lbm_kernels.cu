@@ -14,6 +14,8 @@
 
 #include <type_traits>
 
+#include <algorithm>
+
 #include "pull.cuh"
 #include "scbb_internal.cuh"
 
@@ -825,6 +827,28 @@ __global__ void k_export(LbmParams p, const T* __restrict__ S, float* __restrict
     out[2 * (size_t)p.N + n] = (float)(jx * irt);
     out[3 * (size_t)p.N + n] = (float)(jy * irt);
     out[4 * (size_t)p.N + n] = (float)(jz * irt);
+}
+
+__global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+        dst[q] = (float)src[q];
+}
+
+__global__ void k_to_f64(const float* __restrict__ src, double* __restrict__ dst, size_t n) {
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+        dst[q] = (double)src[q];
+}
+
+void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t st) {
+    if (n == 0) return;
+    const size_t blocks = std::min<size_t>((n + 255) / 256, 152 * 16);
+    k_to_f32<<<(unsigned)blocks, 256, 0, st>>>(src, dst, n);
+}
+
+void launch_to_f64(const float* src, double* dst, size_t n, cudaStream_t st) {
+    if (n == 0) return;
+    const size_t blocks = std::min<size_t>((n + 255) / 256, 152 * 16);
+    k_to_f64<<<(unsigned)blocks, 256, 0, st>>>(src, dst, n);
 }
 
 void launch_export(const LbmParams& p, const float* S, float* out, int what, cudaStream_t st) {

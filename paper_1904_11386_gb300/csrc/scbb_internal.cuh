@@ -361,6 +361,9 @@ struct BatchDesc {
 };
 bool launch_batch_bulk(BatchDesc& d, int mode, int store, cudaStream_t st);
 void launch_export(const LbmParams& p, const float* S, float* out, int what, cudaStream_t st);
+// element-wise FP64 -> FP32 (round to nearest) and FP32 -> FP64 conversions of n values on the device
+void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t st);
+void launch_to_f64(const float* src, double* dst, size_t n, cudaStream_t st);
 void launch_moments_reduce(const LbmParams& p, const float* S, double* red, cudaStream_t st);
 int bulk_grid_blocks(const LbmParams& p);
 

@@ -251,10 +251,18 @@ class Sim:
     def scbb_sync(self):
         self._check(self.L.scbb_sync(self.h), "scbb_sync")
 
-    def scbb_get_fields(self):
+    def scbb_get_fields(self, out=None):
+        """(rho^A, rho^B, u) as FP64 arrays shaped (nz, ny, nx) and (3, nz, ny, nx); out: optional caller
+        arrays (contiguous float64, for example views of pinned host memory) to fill instead."""
         N = self.prob.n_nodes
         s = (self.prob.nz, self.prob.ny, self.prob.nx)
-        a, b, u = np.empty(N), np.empty(N), np.empty(3 * N)
+        if out is None:
+            a, b, u = np.empty(N), np.empty(N), np.empty(3 * N)
+        else:
+            a, b, u = out
+            for arr, n in ((a, N), (b, N), (u, 3 * N)):
+                if arr.dtype != np.float64 or not arr.flags.c_contiguous or arr.size != n:
+                    raise ScbbError("scbb_get_fields: out arrays must be contiguous float64 of N, N and 3 N values")
         self._check(self.L.scbb_get_fields(self.h, _p(a), _p(b), _p(u)), "scbb_get_fields")
         return a.reshape(s), b.reshape(s), u.reshape((3,) + s)
 
