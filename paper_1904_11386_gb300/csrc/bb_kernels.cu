@@ -20,6 +20,7 @@
 #include <type_traits>
 
 #include "bb.cuh"
+#include "pdl.cuh"
 #include "scbb_internal.cuh"
 
 namespace scbb {
@@ -205,6 +206,8 @@ __device__ __forceinline__ void for_candidates(const DevState& d, const CellScan
 // Per triangle: clear the element accumulators the next step will fill, and append the heights where the
 // triangle crosses the +z rays of the columns inside its xy projection.
 __global__ void k_class_tri(LbmParams p, DevState d, int step) {
+    pdl_wait();
+    pdl_trigger();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) { d.cnt[0] = 0; d.cnt[1] = 0; }
     if (t >= d.NT) return;
@@ -268,6 +271,8 @@ __global__ void k_class_tri(LbmParams p, DevState d, int step) {
 // One thread per node of a capsule's box: parity of the column's crossings above the node; owner updated in
 // place, changed nodes recorded as fresh.
 __global__ void k_class_col(LbmParams p, DevState d, int init) {
+    pdl_wait();
+    pdl_trigger();
     const int k = blockIdx.y;
     const int4 lo = d.cbox[2 * k], hi = d.cbox[2 * k + 1];
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -305,6 +310,8 @@ __global__ void k_class_col(LbmParams p, DevState d, int init) {
 
 // Clears the boundary and fresh bits of the previous step's lists and the per-column counters.
 __global__ void k_lists_reset(DevState d) {
+    pdl_wait();
+    pdl_trigger();
     const int nb = d.cnt[0], nf = d.cnt[1];
     if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt[4] = nf;     // fresh nodes replaced at the end of the previous step
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < d.NM * d.CW * d.CW; q += gridDim.x * blockDim.x) {
@@ -325,6 +332,8 @@ __global__ void k_lists_reset(DevState d) {
 
 // Nodes of each capsule's box (one node wider) with a cut membrane link join the boundary list.
 __global__ void k_boundary_mark(LbmParams p, DevState d) {
+    pdl_wait();
+    pdl_trigger();
     const int k = blockIdx.y;
     const int4 lo = d.cbox[2 * k], hi = d.cbox[2 * k + 1];
     const int wx = hi.x - lo.x + 3, wy = hi.y - lo.y + 3, wz = hi.z - lo.z + 3;
@@ -495,6 +504,8 @@ __device__ __forceinline__ void node_elements(const LbmParams& p, const DevState
 }
 
 __global__ void __launch_bounds__(BE_WARPS * 32, 4) k_boundary_elements(LbmParams p, DevState d) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ unsigned long long best[BE_WARPS][Q - 1];
     __shared__ float4 segP[BE_WARPS][Q - 1];          // canonical start point of each link's segment
     __shared__ float4 segD[BE_WARPS][Q - 1];          // and its direction
@@ -509,7 +520,7 @@ __global__ void __launch_bounds__(BE_WARPS * 32, 4) k_boundary_elements(LbmParam
 
 void launch_bb_lists_reset(const DevState& d, cudaStream_t st) {
     if (d.NM == 0) return;
-    k_lists_reset<<<64, 256, 0, st>>>(d);
+    launch_k(k_lists_reset, dim3(64), dim3(256), 0, st, d);
 }
 
 void launch_bb_classify(const LbmParams& p, const DevState& d, int step, bool init, cudaStream_t st) {
@@ -524,9 +535,9 @@ void launch_bb_classify_lists(const LbmParams& p, const DevState& d, int step, b
 
 void launch_bb_owner(const LbmParams& p, const DevState& d, int step, bool init, cudaStream_t st) {
     if (d.NM == 0) return;
-    k_class_tri<<<(d.NT + 127) / 128, 128, 0, st>>>(p, d, step);
+    launch_k(k_class_tri, dim3((d.NT + 127) / 128), dim3(128), 0, st, p, d, step);
     dim3 gc((d.CW * d.CW * d.CW + 127) / 128, d.NM);
-    k_class_col<<<gc, 128, 0, st>>>(p, d, init ? 1 : 0);
+    launch_k(k_class_col, dim3(gc), dim3(128), 0, st, p, d, init ? 1 : 0);
 }
 
 void launch_bb_boundary_list(const LbmParams& p, const DevState& d, cudaStream_t st) {
@@ -534,9 +545,9 @@ void launch_bb_boundary_list(const LbmParams& p, const DevState& d, cudaStream_t
     // boxes are at most CW wide; one node of margin on each side
     const int w = d.CW + 2;
     dim3 gm((w * w * w + 127) / 128, d.NM);
-    k_boundary_mark<<<gm, 128, 0, st>>>(p, d);
+    launch_k(k_boundary_mark, dim3(gm), dim3(128), 0, st, p, d);
     static const int per_sm = occupancy((const void*)k_boundary_elements, BE_WARPS * 32);
-    k_boundary_elements<<<fill_grid(per_sm, ((size_t)d.maxB + BE_WARPS - 1) / BE_WARPS), BE_WARPS * 32, 0, st>>>(p,
+    launch_k(k_boundary_elements, dim3(fill_grid(per_sm, ((size_t)d.maxB + BE_WARPS - 1) / BE_WARPS)), dim3(BE_WARPS * 32), 0, st, p,
                                                                                                              d);
 }
 
@@ -586,6 +597,8 @@ __device__ __forceinline__ void node_vrho(const LbmParams& p, const DevState& d,
 }
 
 __global__ void __launch_bounds__(256) k_bb_vrho(LbmParams p, DevState d) {
+    pdl_wait();
+    pdl_trigger();
     const int nb = min(d.cnt[0], d.maxB);
     for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += (gridDim.x * blockDim.x) >> 5)
         node_vrho(p, d, b, threadIdx.x & 31);
@@ -746,6 +759,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_boundary(LbmParams p, DevState d, const T* __restrict__ S,
                                                   T* __restrict__ D, const float* __restrict__ ghost,
                                                   int step, int* err) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float2 part[8];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nb = min(d.cnt[0], d.maxB);
@@ -770,11 +785,11 @@ void launch_bb_boundary(const LbmParams& p, const DevState& d, const float* S, f
     if (d.NM == 0) return;
     const size_t need = ((size_t)d.maxB + 7) / 8;   // 8 warps per block; the partials fit in bdm[maxB]
     static const int per_v = occupancy((const void*)k_bb_vrho, 256);
-    k_bb_vrho<<<fill_grid(per_v, need), 256, 0, st>>>(p, d);
+    launch_k(k_bb_vrho, dim3(fill_grid(per_v, need)), dim3(256), 0, st, p, d);
     with_storage(p.store, [&](auto* tag) {
         using T = std::remove_pointer_t<decltype(tag)>;
         static const int per_b = occupancy((const void*)k_boundary<T>, 256);
-        k_boundary<T><<<fill_grid(per_b, need), 256, 0, st>>>(p, d, reinterpret_cast<const T*>(S),
+        launch_k(k_boundary<T>, dim3(fill_grid(per_b, need)), dim3(256), 0, st, p, d, reinterpret_cast<const T*>(S),
                                                               reinterpret_cast<T*>(D), ghost, step, err);
     });
 }
@@ -789,6 +804,8 @@ void launch_bb_boundary(const LbmParams& p, const DevState& d, const float* S, f
 // replacements of the previous step (Eq. 16).  Summing M(t) over the FP32 lattice instead would carry its
 // rounding (systematic over uniform regions), which Eq. 18 multiplies by C0 sum(rho_init)/rho_init^c.
 __global__ void __launch_bounds__(1024) k_mass_finalize(DevState d, double vsys) {
+    pdl_wait();
+    pdl_trigger();
     // the changes are small: FP32 partials per thread and per warp, FP64 only in warp 0
     __shared__ float shf[2][32];
     float fa = 0.f, fb = 0.f;
@@ -963,6 +980,8 @@ __device__ __forceinline__ void fresh_node(const LbmParams& p, const DevState& d
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_fresh_compute(LbmParams p, DevState d, const T* __restrict__ S) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int queue[8][CAND_Q];
     const int nf = min(d.cnt[1], d.maxF);
     for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nf; q += (gridDim.x * blockDim.x) >> 5) {
@@ -1018,6 +1037,8 @@ __device__ __forceinline__ void fresh_apply_node(const LbmParams& p, const DevSt
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_fresh_apply(LbmParams p, DevState d, T* __restrict__ S, int step) {
+    pdl_wait();
+    pdl_trigger();
     const int nf = min(d.cnt[1], d.maxF);
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nf; q += gridDim.x * blockDim.x)
         fresh_apply_node<T>(p, d, S, step, q);
@@ -1050,7 +1071,7 @@ void launch_bb_init(const LbmParams& p, const DevState& d, cudaStream_t st) {
 void launch_bb_mass(const LbmParams& p, const DevState& d, cudaStream_t st) {
     if (d.NM == 0) return;
     const double vsys = (double)p.nxy * (p.zf1 - p.zf0);
-    k_mass_finalize<<<1, 1024, 0, st>>>(d, vsys);
+    launch_k(k_mass_finalize, dim3(1), dim3(1024), 0, st, d, vsys);
 }
 
 void launch_bb_fresh(const LbmParams& p, const DevState& d, float* Snew, int step, cudaStream_t st) {
@@ -1066,8 +1087,8 @@ void launch_bb_fresh_nodes(const LbmParams& p, const DevState& d, float* Snew, i
         T* Sn = reinterpret_cast<T*>(Snew);
         static const int per_c = occupancy((const void*)k_fresh_compute<T>, 256);
         static const int per_a = occupancy((const void*)k_fresh_apply<T>, 128);
-        k_fresh_compute<T><<<fill_grid(per_c, need_c), 256, 0, st>>>(p, d, Sn);
-        k_fresh_apply<T><<<fill_grid(per_a, need_a), 128, 0, st>>>(p, d, Sn, step);
+        launch_k(k_fresh_compute<T>, dim3(fill_grid(per_c, need_c)), dim3(256), 0, st, p, d, Sn);
+        launch_k(k_fresh_apply<T>, dim3(fill_grid(per_a, need_a)), dim3(128), 0, st, p, d, Sn, step);
     });
 }
 

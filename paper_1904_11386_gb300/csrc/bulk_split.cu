@@ -20,6 +20,7 @@
 
 #include "async_copy.cuh"
 #include "pull.cuh"
+#include "pdl.cuh"
 #include "scbb_internal.cuh"
 
 namespace scbb {
@@ -649,6 +650,7 @@ constexpr long long DRAIN_POLLS = 1LL << 22;     // bounded wait for the copies 
 template <typename T>
 __global__ void __launch_bounds__(256) k_moments_staged(LbmParams p, const T* __restrict__ S, float* __restrict__ rho,
                                                         float* __restrict__ J, int* __restrict__ err) {
+    pdl_wait();
     extern __shared__ __align__(128) unsigned char msm[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     const int nx = p.nx;
@@ -911,6 +913,7 @@ __device__ __forceinline__ void collide4_staged(const LbmParams& p, T* __restric
 template <typename T>
 __global__ void __launch_bounds__(256) k_moments4(LbmParams p, const T* __restrict__ S, float* __restrict__ rho,
                                                   float* __restrict__ J) {
+    pdl_wait();
     const unsigned int total = (unsigned)(p.nx >> 2) * (unsigned)p.ny * (unsigned)(p.zf1 - p.zf0);
     // a warp wholly past the end has nothing to do (it is never a shuffle partner of a live lane)
     if (blockIdx.x * blockDim.x + (threadIdx.x & ~31u) >= total) return;
@@ -920,6 +923,7 @@ __global__ void __launch_bounds__(256) k_moments4(LbmParams p, const T* __restri
 template <typename T>
 __global__ void __launch_bounds__(256) k_moments1(LbmParams p, const T* __restrict__ S, float* __restrict__ rho,
                                                   float* __restrict__ J) {
+    pdl_wait();
     const unsigned int total = (unsigned)p.nx * (unsigned)p.ny * (unsigned)(p.zf1 - p.zf0);
     moments1_node<T>(p, S, rho, J, blockIdx.x * blockDim.x + threadIdx.x, total);
 }
@@ -931,6 +935,7 @@ __global__ void __launch_bounds__(512, 1)
 k_collide(LbmParams p, T* __restrict__ D, const float* __restrict__ rho, const float* __restrict__ J,
           float* __restrict__ ghost, const float* __restrict__ Fibm, const uint32_t* __restrict__ mask,
           float* __restrict__ u_out, int* __restrict__ err, int TY) {
+    pdl_wait();
     extern __shared__ float ring[];                      // psi [4 planes][2 components][TY + 2 rows][nx]
     if (VEC)
         collide4_tile<MODE, T>(p, D, rho, J, ghost, Fibm, mask, u_out, err, TY, blockIdx.x, blockIdx.y, gridDim.y,
@@ -1261,6 +1266,7 @@ __global__ void __launch_bounds__(256, 3)
 k_collide_pair(LbmParams p, T* __restrict__ D, const float* __restrict__ rho, const float* __restrict__ J,
                float* __restrict__ ghost, const float* __restrict__ Fibm, const uint32_t* __restrict__ mask,
                float* __restrict__ u_out, int* __restrict__ err, int TY) {
+    pdl_wait();
     extern __shared__ __align__(128) unsigned char psm[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(psm);
     float* ring = reinterpret_cast<float*>(psm + 128);
@@ -1274,6 +1280,7 @@ __global__ void __launch_bounds__(512, 1)
 k_collide_staged(LbmParams p, T* __restrict__ D, const float* __restrict__ rho, const float* __restrict__ J,
                  float* __restrict__ ghost, const float* __restrict__ Fibm, const uint32_t* __restrict__ mask,
                  float* __restrict__ u_out, int* __restrict__ err, int TY) {
+    pdl_wait();
     // [2 barriers, padded to 128 bytes][psi ring: 4 planes x 2 components x (TY + 2) rows x nx][2 stage buffers]
     extern __shared__ __align__(128) unsigned char csm[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(csm);
@@ -1360,7 +1367,7 @@ static void launch_collide(const LbmParams& p, dim3 grid, int threads, size_t sm
         cudaFuncSetAttribute(k_collide<MODE, T, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = smem;
     }
-    k_collide<MODE, T, VEC><<<grid, threads, smem, st>>>(p, D, rho, J, ghost, Fibm, mask, u, err, TY);
+    launch_k(k_collide<MODE, T, VEC>, dim3(grid), dim3(threads), smem, st, p, D, rho, J, ghost, Fibm, mask, u, err, TY);
 }
 
 // The staged forms (bulk asynchronous copies into shared memory) serve quad rows; SCBB_BULK_STAGED=0 turns
@@ -1437,7 +1444,7 @@ static void launch_collide_pair(const LbmParams& p, dim3 grid, size_t smem, int 
         cudaFuncSetAttribute(k_collide_pair<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = smem;
     }
-    k_collide_pair<MODE, T><<<grid, PAIR_THREADS, smem, st>>>(p, D, rho, J, ghost, Fibm, mask, u, err, TY);
+    launch_k(k_collide_pair<MODE, T>, dim3(grid), dim3(PAIR_THREADS), smem, st, p, D, rho, J, ghost, Fibm, mask, u, err, TY);
 }
 
 template <typename T>
@@ -1456,7 +1463,7 @@ static void launch_moments_staged(const LbmParams& p, int wpb, size_t smem, cons
     const unsigned int rows = (unsigned)p.ny * (unsigned)(p.zf1 - p.zf0);
     const unsigned int need = (rows + wpb - 1) / wpb;
     const unsigned int blocks = std::min<unsigned int>(need, (unsigned)(sm_count() * per_sm));
-    k_moments_staged<T><<<blocks, 32 * wpb, smem, st>>>(p, S, rho, J, err);
+    launch_k(k_moments_staged<T>, dim3(blocks), dim3(32 * wpb), smem, st, p, S, rho, J, err);
 }
 
 template <int MODE, typename T>
@@ -1468,7 +1475,7 @@ static void launch_collide_staged(const LbmParams& p, dim3 grid, int threads, si
         cudaFuncSetAttribute(k_collide_staged<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = smem;
     }
-    k_collide_staged<MODE, T><<<grid, threads, smem, st>>>(p, D, rho, J, ghost, Fibm, mask, u, err, TY);
+    launch_k(k_collide_staged<MODE, T>, dim3(grid), dim3(threads), smem, st, p, D, rho, J, ghost, Fibm, mask, u, err, TY);
 }
 
 void launch_split(const LbmParams& p, const float* S, float* D, float* rho, float* J, float* ghost,
@@ -1493,7 +1500,7 @@ void launch_split(const LbmParams& p, const float* S, float* D, float* rho, floa
         T* Dt = reinterpret_cast<T*>(D);
         if (vec) {
             if (a_staged) launch_moments_staged<T>(p, wpb, msmem, reinterpret_cast<const T*>(S), rho, J, err, st);
-            else k_moments4<T><<<(units + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<const T*>(S), rho, J);
+            else launch_k(k_moments4<T>, dim3((units + 255) / 256), dim3(256), 0, st, p, reinterpret_cast<const T*>(S), rho, J);
             if (b_pair) {
                 if (mode == 1) launch_collide_pair<1, T>(p, pgrid, psmem, pTY, Dt, rho, J, ghost, Fibm, mask, u, err, st);
                 else launch_collide_pair<0, T>(p, pgrid, psmem, pTY, Dt, rho, J, ghost, Fibm, mask, u, err, st);
@@ -1506,7 +1513,7 @@ void launch_split(const LbmParams& p, const float* S, float* D, float* rho, floa
                 launch_collide<0, T, true>(p, grid, threads, smem, TY, Dt, rho, J, ghost, Fibm, mask, u, err, st);
             }
         } else {
-            k_moments1<T><<<(units + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<const T*>(S), rho, J);
+            launch_k(k_moments1<T>, dim3((units + 255) / 256), dim3(256), 0, st, p, reinterpret_cast<const T*>(S), rho, J);
             if (mode == 1) launch_collide<1, T, false>(p, grid, threads, smem, TY, Dt, rho, J, ghost, Fibm, mask, u, err, st);
             else launch_collide<0, T, false>(p, grid, threads, smem, TY, Dt, rho, J, ghost, Fibm, mask, u, err, st);
         }

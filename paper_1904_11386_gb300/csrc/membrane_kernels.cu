@@ -8,6 +8,7 @@
 #include <math.h>
 
 #include "membrane.cuh"
+#include "pdl.cuh"
 #include "scbb_internal.cuh"
 
 namespace scbb {
@@ -36,6 +37,8 @@ constexpr int CAP_THREADS = 1024;
 
 // Volume terms come from the triangle pass (tvol), so the reduction is a plain FP64 sum.
 __global__ void __launch_bounds__(CAP_THREADS) k_capsule_reduce(DevState d, int use_tvol) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double sh[4 * 32];
     const int m = blockIdx.x;
     const CapDev c = d.cap[m];
@@ -117,7 +120,7 @@ __global__ void __launch_bounds__(CAP_THREADS) k_capsule_reduce(DevState d, int 
 }
 
 void launch_capsule_reduce(const DevState& d, cudaStream_t st) {
-    if (d.NM > 0) k_capsule_reduce<<<d.NM, CAP_THREADS, 0, st>>>(d, 0);
+    if (d.NM > 0) launch_k(k_capsule_reduce, dim3(d.NM), dim3(CAP_THREADS), 0, st, d, 0);
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -136,6 +139,8 @@ void launch_capsule_reduce(const DevState& d, cudaStream_t st) {
 // Corner c = 3 t + k of triangle t; cnb[c] holds the global ids of the two other corners (j, l).
 // ------------------------------------------------------------------------------------------------------
 __global__ void k_mem_tri(DevState d) {
+    pdl_wait();
+    pdl_trigger();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= d.NT) return;
     const int4 T = d.tri[t];
@@ -192,6 +197,8 @@ __global__ void k_mem_tri(DevState d) {
 constexpr int GATHER = 8;      // corners fetched per round of a vertex gather
 
 __global__ void k_mem_vert1(DevState d) {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.NV) return;
     float3 Fs = make_float3(0.f, 0.f, 0.f), dv = make_float3(0.f, 0.f, 0.f), K = make_float3(0.f, 0.f, 0.f);
@@ -229,6 +236,8 @@ __global__ void k_mem_vert1(DevState d) {
 // fresh-node momenta of the crossed elements, one third to each corner) and advance the node
 // (V += F/m, then X += V).
 __global__ void k_mem_vert2(DevState d, int bb, int step) {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.NV) return;
     const int m = d.vcap[i];
@@ -286,16 +295,16 @@ int launch_membrane_elastic(const LbmParams& p, const DevState& d, cudaStream_t 
     if (d.NM == 0) return 0;
     const int b = 128;
     const int npp = launch_pp_forces(p, d, d.pp_eps, d.pp_d0, st);
-    k_mem_tri<<<(d.NT + b - 1) / b, b, 0, st>>>(d);
-    k_mem_vert1<<<(d.NV + b - 1) / b, b, 0, st>>>(d);
-    k_capsule_reduce<<<d.NM, CAP_THREADS, 0, st>>>(d, 1);
+    launch_k(k_mem_tri, dim3((d.NT + b - 1) / b), dim3(b), 0, st, d);
+    launch_k(k_mem_vert1, dim3((d.NV + b - 1) / b), dim3(b), 0, st, d);
+    launch_k(k_capsule_reduce, dim3(d.NM), dim3(CAP_THREADS), 0, st, d, 1);
     return 3 + npp;
 }
 
 int launch_membrane_update(const LbmParams& p, const DevState& d, bool bb, int step, cudaStream_t st) {
     if (d.NM == 0) return 0;
     const int b = 128;
-    k_mem_vert2<<<(d.NV + b - 1) / b, b, 0, st>>>(d, bb ? 1 : 0, step);
+    launch_k(k_mem_vert2, dim3((d.NV + b - 1) / b), dim3(b), 0, st, d, bb ? 1 : 0, step);
     return 1;
 }
 
@@ -343,6 +352,8 @@ __device__ __forceinline__ Stencil hat_stencil(const LbmParams& p, float4 X) {
 }
 
 __global__ void k_ibm_spread(LbmParams p, DevState d) {
+    pdl_wait();
+    pdl_trigger();
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= d.NV) return;
     const Stencil s = hat_stencil(p, d.X[v]);
@@ -362,6 +373,8 @@ __global__ void k_ibm_spread(LbmParams p, DevState d) {
 // stencil (nothing else reads them in this kernel), then moves the vertex.  Wall nodes contribute the wall
 // velocity.
 __global__ void k_ibm_interp(LbmParams p, DevState d) {
+    pdl_wait();
+    pdl_trigger();
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= d.NV) return;
     float4 X = d.X[v];
@@ -390,12 +403,12 @@ __global__ void k_ibm_interp(LbmParams p, DevState d) {
 
 void launch_ibm_spread(const LbmParams& p, const DevState& d, cudaStream_t st) {
     if (d.NV == 0) return;
-    k_ibm_spread<<<(d.NV + 127) / 128, 128, 0, st>>>(p, d);
+    launch_k(k_ibm_spread, dim3((d.NV + 127) / 128), dim3(128), 0, st, p, d);
 }
 
 void launch_ibm_interp(const LbmParams& p, const DevState& d, cudaStream_t st) {
     if (d.NV == 0) return;
-    k_ibm_interp<<<(d.NV + 127) / 128, 128, 0, st>>>(p, d);
+    launch_k(k_ibm_interp, dim3((d.NV + 127) / 128), dim3(128), 0, st, p, d);
 }
 
 // ------------------------------------------------------------------------------------------------------
