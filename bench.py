@@ -174,6 +174,7 @@ def aggregate_glups(nodes: int, steps: int, ws: int, seconds: float) -> float:
 
 
 KERNEL_SOURCES = ("paper_1904_11386_gb300/csrc/bulk_split.cu", "paper_1904_11386_gb300/csrc/pull.cuh",
+                  "paper_1904_11386_gb300/csrc/async_copy.cuh", "paper_1904_11386_gb300/csrc/pdl.cuh",
                   "paper_1904_11386_gb300/csrc/scbb_internal.cuh")
 
 
@@ -631,7 +632,7 @@ def main():
     achieved = bpl * n_upd / bulk_avg_s / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": recorded_traffic(args.workload + ("" if args.storage == "fp32" else "-" + args.storage)),
-            "kernel": "bulk phase: k_moments4 (stream, moments) + k_collide4 (Shan-Chen force, collide)",
+            "kernel": "bulk phase: k_moments_staged (stream, moments) + k_collide_pair (Shan-Chen force, collide)",
             "bytes_per_lu": bpl, "units_per_launch": n_upd, "peak_source": src,
             "kernel_ms": bulk_avg_s * 1e3, "kernel_share": bulk_avg_s * 1e3 / (ms / args.steps) if ms > 0 else None,
             "kernel_timing": f"{bulk_n} bulk launches bracketed by CUDA events (second region of {args.steps} steps)"}
