@@ -278,8 +278,10 @@ scbb_status scbb_batch_set_wait_limit(scbb_batch* batch, long long polls);
  *   scbb_adjoint_workspace_bytes(ctx, n, K): device bytes of the adjoint's workspace for n steps with a
  *     population checkpoint every K steps: ceil(n/K) checkpoints, K + 1 lattices, K density fields and (walls)
  *     K wall planes of one segment, two adjoint lattices and 13 + 2 floats per node of scratch; with capsules
- *     also ceil(n/K) + K + 1 copies of the vertices, 8 more float4 per vertex and one per triangle corner
- *     for the membrane's adjoint, and 9 floats per node for the adjoint of the spread force.  0 for bad
+ *     also ceil(n/K) + K + 1 copies of the vertices, K copies of the membrane state of a step (12 float4 and 3
+ *     float2 and a float per triangle, 4 float4 and a float2 per vertex, 4 doubles per capsule), 7 more float4
+ *     per vertex and one per triangle corner for the membrane's adjoint, and 9 floats per node for the adjoint
+ *     of the spread force.  0 for bad
  *     arguments.
  *   scbb_adjoint_create(ctx, n, K, dev_workspace, out): dev_workspace caller-owned, at least that many
  *     bytes, 256-byte aligned; the adjoint keeps ctx and runs on its stream.

@@ -22,6 +22,10 @@
  *    the mean of rho over the neighbours of y that lie on x's side (not walls); the particle colour adds
  *    rho_virtual = 2 |colour| (rho_maj - rho_min) (Eq. 15) to component A if colour > 0, to B if < 0.
  *    The reaction +psi^c(x) G w_i psi^{c'}(virtual) c_i goes to the crossed element (momentum balance).
+ *    Parity unpinned: the magnitude of the colour's effect.  Its sign and its neutrality at colour 0 are
+ *    pinned by tests; with this normalisation a near-rigid capsule's equilibrium contact angle follows
+ *    cos theta = 4.3 .. 4.6 colour (R = 6, colours 0.03 .. 0.1), where Sec. III.D reports cos theta close to
+ *    the colour itself, so no measured value pins the magnitude.
  *  - Fresh nodes (Sec. II.E): nodes whose owner changed.  rho^c = mean over the non-fresh neighbours on
  *    the new side (Eq. 16), times the mass correction of Eq. 18 with Delta rho^c read as the global mass
  *    error M^c(t) - M^c(0), V_sys = number of fluid nodes, rho_init^c = M^c(0)/V_sys, clamped to the

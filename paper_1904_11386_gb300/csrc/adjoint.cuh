@@ -57,7 +57,6 @@ void launch_adj_step(const LbmParams& p, const float* S, const float* rho, const
 struct AdjCap {
     float4* lx;             // [NV] adjoint of the vertex positions (of X(t + 1) in, of X(t) out)
     float4* lF;             // [NV] adjoint of the node forces
-    float4* vp;             // [NV] per-vertex products summed per capsule: lF.F_Skalak, lF.F_bend, lF.F_vol, lF.dV
     float4* vb0;            // [NV] bending, first reverse stage: (mu, lambda_H part, lambda_KG, lambda_A part)
     float4* vb1;            //      (fb lambda_F, H)
     float4* va;             // [NV] second stage: (lambda_A, lambda_angle sum, mu, H)
@@ -68,11 +67,12 @@ struct AdjCap {
     float* lfi;             // [3][N] adjoint of the spread force
     float* uh;              // [3][N] half-force velocity of the step
     double* capd;           // [4 NM] dL/dkS, dL/dkB, dL/dkV (summed over the steps), lambda_F . dV of the step
+                            // (FP64 atomic sums of the vertex products)
 };
 // luh = the interpolation transposed applied to lx (at X of the step, in d.X)
 void launch_cap_adj_spread(const LbmParams& p, const DevState& d, const AdjCap& a, cudaStream_t st);
 // after the fluid's backward step: lambda_F, the stencil and membrane terms of lx, the parameter sums, and the
-// clearing of the step's fields (d holds the membrane forces and spread force of the step)
+// clearing of the step's fields (d holds the membrane forces and spread force of the step); four kernels
 void launch_cap_adj_vertices(const LbmParams& p, const DevState& d, const AdjCap& a, cudaStream_t st);
 
 // dL/drho0^c(x) of an initial equilibrium lattice S0 (f_i = f_eq,i(rho0, u0), linear in rho0 at fixed u0):

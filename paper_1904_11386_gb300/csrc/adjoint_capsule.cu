@@ -19,6 +19,7 @@
 
 #include "adjoint.cuh"
 #include "scbb_internal.cuh"
+#include "pdl.cuh"
 
 namespace scbb {
 
@@ -160,7 +161,10 @@ __device__ __forceinline__ float volume_factor(const DevState& d, int m) {
 
 // luh(x) += phi(x - X_b) lambda_X,b over the fluid nodes of each vertex's stencil (the interpolation transposed)
 __global__ void k_cap_adj_spread(LbmParams p, DevState d, AdjCap a) {
+    pdl_wait();
+    pdl_trigger();
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < d.NM) a.capd[4 * v + 3] = 0.0;             // the step's lambda_F . dV, summed by k_cap_adj_vert
     if (v >= d.NV) return;
     const AdjStencil s = adj_stencil(p, d.X[v]);
     const float4 l = a.lx[v];
@@ -177,6 +181,8 @@ __global__ void k_cap_adj_spread(LbmParams p, DevState d, AdjCap a) {
 // Per vertex: the adjoint of its node force (the spreading transposed), the stencil terms of lambda_X, and the
 // first reverse stage of bending; the per-vertex products that the capsule reduction sums.
 __global__ void k_cap_adj_vert(LbmParams p, DevState d, AdjCap a) {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.NV) return;
     const float4 X = d.X[i];
@@ -213,10 +219,16 @@ __global__ void k_cap_adj_vert(LbmParams p, DevState d, AdjCap a) {
     const float kv = volume_factor(d, m);
     const float4 fs = d.Fsk[i], dv = d.dV[i];
     const float Fb[3] = {F.x - fs.x - kv * dv.x, F.y - fs.y - kv * dv.y, F.z - fs.z - kv * dv.z};
-    a.vp[i] = make_float4(lF[0] * fs.x + lF[1] * fs.y + lF[2] * fs.z,
-                          lF[0] * Fb[0] + lF[1] * Fb[1] + lF[2] * Fb[2],
-                          kv * (lF[0] * dv.x + lF[1] * dv.y + lF[2] * dv.z),
-                          lF[0] * dv.x + lF[1] * dv.y + lF[2] * dv.z);
+    // per-capsule FP64 sums (atomic: their order, and so their last bits, vary from run to run): lambda_F . dV
+    // of the step for the volume transpose, and the parameter gradients, added over the steps (dF/dkS = F_Skalak
+    // / kS, and likewise for bending and volume)
+    const float ps = lF[0] * fs.x + lF[1] * fs.y + lF[2] * fs.z;
+    const float pb = lF[0] * Fb[0] + lF[1] * Fb[1] + lF[2] * Fb[2];
+    const float pd = lF[0] * dv.x + lF[1] * dv.y + lF[2] * dv.z;
+    atomicAdd(a.capd + 4 * m + 3, (double)pd);
+    if (cp.kS != 0.f) atomicAdd(a.capd + 4 * m + 0, (double)ps / cp.kS);
+    if (cp.kB != 0.f) atomicAdd(a.capd + 4 * m + 1, (double)pb / cp.kB);
+    if (cp.kV != 0.f) atomicAdd(a.capd + 4 * m + 2, (double)(kv * pd) / cp.kV);
     // bending, reversed from the force F_b = fb n with fb = 2 kB [2H(H^2 - K_G) + lap] A (Eq. 10)
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
     if (cp.kB != 0.f) {
@@ -245,35 +257,11 @@ __global__ void k_cap_adj_vert(LbmParams p, DevState d, AdjCap a) {
     a.vb1[i] = r1;
 }
 
-// Per capsule (one block each): FP64 sums of the per-vertex products: lambda_F . dV for the volume transpose, and
-// the parameter gradients, added over the steps.
-__global__ void __launch_bounds__(256) k_cap_adj_reduce(DevState d, AdjCap a) {
-    const int m = blockIdx.x;
-    const CapDev c = d.cap[m];
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int v = threadIdx.x; v < c.nv; v += blockDim.x) {
-        const float4 q = a.vp[c.v0 + v];
-        acc[0] += q.x; acc[1] += q.y; acc[2] += q.z; acc[3] += q.w;
-    }
-    __shared__ double sh[4][256];
-    for (int k = 0; k < 4; k++) sh[k][threadIdx.x] = acc[k];
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int k = 0; k < 4; k++) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        a.capd[4 * m + 3] = sh[3][0];                                  // lambda_F . dV of this step
-        if (c.kS != 0.f) a.capd[4 * m + 0] += sh[0][0] / c.kS;
-        if (c.kB != 0.f) a.capd[4 * m + 1] += sh[1][0] / c.kB;
-        if (c.kV != 0.f) a.capd[4 * m + 2] += sh[2][0] / c.kV;
-    }
-}
-
 // Per vertex: the second reverse stage of bending -- H's adjoint gathers the neighbours' Laplace-Beltrami terms,
 // then the chain rule through H = K . n / 2, K = Ksum / (2A), n = Nsum / |Nsum|, K_G = (2 pi - angles) / A.
 __global__ void k_cap_adj_vert2(DevState d, AdjCap a) {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.NV) return;
     const CapDev cp = d.cap[d.vcap[i]];
@@ -320,6 +308,8 @@ __global__ void k_cap_adj_vert2(DevState d, AdjCap a) {
 // forces, kv lambda_F of the volume records, and the bending stages' adjoints of the mixed-area shares, angles,
 // mean-curvature vectors, face normal and cotangents.  Writes lambda . d/dP per corner.
 __global__ void k_cap_adj_tri(DevState d, AdjCap a) {
+    pdl_wait();
+    pdl_trigger();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= d.NT) return;
     const int4 T = d.tri[t];
@@ -417,8 +407,12 @@ __global__ void k_cap_adj_tri(DevState d, AdjCap a) {
     for (int k = 0; k < 3; k++) a.lp[3 * t + k] = make_float4(gacc[3 * k], gacc[3 * k + 1], gacc[3 * k + 2], 0.f);
 }
 
-// Per vertex: lambda_X += its corners' contributions and the volume factor's (d kv / dX = -kV / V0 dV).
-__global__ void k_cap_adj_gather(DevState d, AdjCap a) {
+// Per vertex: lambda_X += its corners' contributions and the volume factor's (d kv / dX = -kV / V0 dV); then the
+// fields of the step are cleared at its stencil's fluid nodes (spread force and marks, luh, lfi, uh), which no
+// vertex's gather reads.
+__global__ void k_cap_adj_gather(LbmParams p, DevState d, AdjCap a) {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.NV) return;
     float4 l = a.lx[i];
@@ -432,17 +426,11 @@ __global__ void k_cap_adj_gather(DevState d, AdjCap a) {
     const float4 dv = d.dV[i];
     l.x += s * dv.x; l.y += s * dv.y; l.z += s * dv.z;
     a.lx[i] = l;
-}
-
-// Per vertex: clears the fields of the step at its stencil's fluid nodes (spread force and marks, luh, lfi, uh).
-__global__ void k_cap_adj_clear(LbmParams p, DevState d, AdjCap a) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= d.NV) return;
-    const AdjStencil s = adj_stencil(p, d.X[v]);
+    const AdjStencil st = adj_stencil(p, d.X[i]);
 #pragma unroll
     for (int q = 0; q < 8; q++) {
-        if (!s.fluid[q]) continue;
-        const unsigned int n = s.node[q];
+        if (!st.fluid[q]) continue;
+        const unsigned int n = st.node[q];
         for (int k = 0; k < 3; k++) {
             d.Fibm[(size_t)k * p.N + n] = 0.f;
             a.luh[(size_t)k * p.N + n] = 0.f;
@@ -454,17 +442,15 @@ __global__ void k_cap_adj_clear(LbmParams p, DevState d, AdjCap a) {
 }
 
 void launch_cap_adj_spread(const LbmParams& p, const DevState& d, const AdjCap& a, cudaStream_t st) {
-    k_cap_adj_spread<<<(d.NV + 127) / 128, 128, 0, st>>>(p, d, a);
+    launch_k(k_cap_adj_spread, dim3((d.NV + 127) / 128), dim3(128), 0, st, p, d, a);
 }
 
 void launch_cap_adj_vertices(const LbmParams& p, const DevState& d, const AdjCap& a, cudaStream_t st) {
     const int b = 128;
-    k_cap_adj_vert<<<(d.NV + b - 1) / b, b, 0, st>>>(p, d, a);
-    k_cap_adj_reduce<<<d.NM, 256, 0, st>>>(d, a);
-    k_cap_adj_vert2<<<(d.NV + b - 1) / b, b, 0, st>>>(d, a);
-    k_cap_adj_tri<<<(d.NT + 63) / 64, 64, 0, st>>>(d, a);
-    k_cap_adj_gather<<<(d.NV + b - 1) / b, b, 0, st>>>(d, a);
-    k_cap_adj_clear<<<(d.NV + b - 1) / b, b, 0, st>>>(p, d, a);
+    launch_k(k_cap_adj_vert, dim3((d.NV + b - 1) / b), dim3(b), 0, st, p, d, a);
+    launch_k(k_cap_adj_vert2, dim3((d.NV + b - 1) / b), dim3(b), 0, st, d, a);
+    launch_k(k_cap_adj_tri, dim3((d.NT + 63) / 64), dim3(64), 0, st, d, a);
+    launch_k(k_cap_adj_gather, dim3((d.NV + b - 1) / b), dim3(b), 0, st, p, d, a);
 }
 
 }  // namespace scbb

@@ -2,6 +2,7 @@
 #include <math.h>
 
 #include "adjoint.cuh"
+#include "pdl.cuh"
 
 namespace scbb {
 
@@ -57,11 +58,12 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_final(LbmParams p, const fl
 // holds the adjoint of that velocity, and the pass writes the adjoint of the spread force (ib.lfi) and the
 // half-force velocity itself (ib.uh) at the marked nodes.
 template <bool W, bool IB>
-__global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(LbmParams p, const float* __restrict__ S,
+__global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_local(LbmParams p, const float* __restrict__ S,
                                                            const float* __restrict__ rho,
                                                            const float* __restrict__ ghost,
                                                            const float* __restrict__ lam, float* __restrict__ scr,
                                                            double* __restrict__ part, AdjIB ib) {
+    pdl_wait();
     float acc[ADJ_PARAMS] = {0.f, 0.f, 0.f, 0.f};
     const size_t N = p.N;
     for (unsigned int n = blockIdx.x * blockDim.x + threadIdx.x; n < p.N; n += gridDim.x * blockDim.x) {
@@ -239,6 +241,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(LbmParams p, const fl
 // dL/d(virtual density) = psi'(ghost) dL/dpsi, per wall and component.
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_wall(LbmParams p, const float* __restrict__ ghost,
                                                           const float* __restrict__ scr, float* __restrict__ gw) {
+    pdl_wait();
+    pdl_trigger();
     const unsigned int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= 2u * p.nxy) return;
     const size_t N = p.N;
@@ -263,6 +267,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_push(LbmParams p, const flo
                                                           const float* __restrict__ scr,
                                                           const float* __restrict__ gw,
                                                           float* __restrict__ lam_out) {
+    pdl_wait();
     const unsigned int y = blockIdx.x * blockDim.x + threadIdx.x;
     if (y >= p.N) return;
     const size_t N = p.N;
@@ -346,14 +351,14 @@ void launch_adj_step(const LbmParams& p, const float* S, const float* rho, const
     const AdjIB none{};
     const AdjIB& b = ib ? *ib : none;
     if (p.walls) {
-        if (ib) k_adj_local<true, true><<<adj_blocks(p), ADJ_THREADS, 0, st>>>(p, S, rho, ghost, lam_in, scr, part, b);
-        else k_adj_local<true, false><<<adj_blocks(p), ADJ_THREADS, 0, st>>>(p, S, rho, ghost, lam_in, scr, part, b);
-        k_adj_wall<<<(2 * p.nxy + ADJ_THREADS - 1) / ADJ_THREADS, ADJ_THREADS, 0, st>>>(p, ghost, scr, gw);
-        k_adj_push<true><<<nb, ADJ_THREADS, 0, st>>>(p, rho, lam_in, scr, gw, lam_out);
+        if (ib) launch_k(k_adj_local<true, true>, dim3(adj_blocks(p)), dim3(ADJ_THREADS), 0, st, p, S, rho, ghost, lam_in, scr, part, b);
+        else launch_k(k_adj_local<true, false>, dim3(adj_blocks(p)), dim3(ADJ_THREADS), 0, st, p, S, rho, ghost, lam_in, scr, part, b);
+        launch_k(k_adj_wall, dim3((2 * p.nxy + ADJ_THREADS - 1) / ADJ_THREADS), dim3(ADJ_THREADS), 0, st, p, ghost, scr, gw);
+        launch_k(k_adj_push<true>, dim3(nb), dim3(ADJ_THREADS), 0, st, p, rho, lam_in, scr, gw, lam_out);
     } else {
-        if (ib) k_adj_local<false, true><<<adj_blocks(p), ADJ_THREADS, 0, st>>>(p, S, rho, ghost, lam_in, scr, part, b);
-        else k_adj_local<false, false><<<adj_blocks(p), ADJ_THREADS, 0, st>>>(p, S, rho, ghost, lam_in, scr, part, b);
-        k_adj_push<false><<<nb, ADJ_THREADS, 0, st>>>(p, rho, lam_in, scr, gw, lam_out);
+        if (ib) launch_k(k_adj_local<false, true>, dim3(adj_blocks(p)), dim3(ADJ_THREADS), 0, st, p, S, rho, ghost, lam_in, scr, part, b);
+        else launch_k(k_adj_local<false, false>, dim3(adj_blocks(p)), dim3(ADJ_THREADS), 0, st, p, S, rho, ghost, lam_in, scr, part, b);
+        launch_k(k_adj_push<false>, dim3(nb), dim3(ADJ_THREADS), 0, st, p, rho, lam_in, scr, gw, lam_out);
     }
 }
 

@@ -1284,6 +1284,12 @@ struct scbb_adjoint {
     float4* Xs = nullptr;       // K x NV vertex positions of the segment being recomputed (ibm)
     float4* Xend = nullptr;     // NV: the context's vertices after the forward run, restored after the backward
     AdjCap cap{};
+    // K slots of the membrane state of each step of the segment being recomputed (ibm): the forward kernels write
+    // slot k during the recomputation and the adjoint kernels of step k read it
+    float4 *s_corner = nullptr, *s_Fsk = nullptr, *s_dV = nullptr, *s_nrm = nullptr, *s_F = nullptr;
+    float2 *s_ccot = nullptr, *s_AK = nullptr;
+    float* s_tvol = nullptr;
+    double* s_cap = nullptr;
     long long n = 0;
     int K = 0, nseg = 0;
     float* ckpt = nullptr;      // nseg lattices: the state read by steps 0, K, 2K, ...
@@ -1337,7 +1343,6 @@ size_t adjoint_layout(const scbb_ctx* c, long long n, int K, void* base, scbb_ad
         AdjCap ac{};
         ac.lx = cv.take<float4>(NV);
         ac.lF = cv.take<float4>(NV);
-        ac.vp = cv.take<float4>(NV);
         ac.vb0 = cv.take<float4>(NV);
         ac.vb1 = cv.take<float4>(NV);
         ac.va = cv.take<float4>(NV);
@@ -1348,9 +1353,21 @@ size_t adjoint_layout(const scbb_ctx* c, long long n, int K, void* base, scbb_ad
         ac.lfi = cv.take<float>(3 * N);
         ac.uh = cv.take<float>(3 * N);
         ac.capd = cv.take<double>(4 * (size_t)c->d.NM);
+        const size_t NM = c->d.NM;
+        float4* s_corner = cv.take<float4>(K * 12 * NT);
+        float2* s_ccot = cv.take<float2>(K * 3 * NT);
+        float* s_tvol = cv.take<float>(K * NT);
+        float4* s_Fsk = cv.take<float4>(K * NV);
+        float4* s_dV = cv.take<float4>(K * NV);
+        float4* s_nrm = cv.take<float4>(K * NV);
+        float4* s_F = cv.take<float4>(K * NV);
+        float2* s_AK = cv.take<float2>(K * NV);
+        double* s_cap = cv.take<double>(K * 4 * NM);
         if (a) {
             a->ibm = true;
             a->Xck = Xck; a->Xs = Xs; a->Xend = Xend; a->cap = ac;
+            a->s_corner = s_corner; a->s_ccot = s_ccot; a->s_tvol = s_tvol; a->s_Fsk = s_Fsk; a->s_dV = s_dV;
+            a->s_nrm = s_nrm; a->s_F = s_F; a->s_AK = s_AK; a->s_cap = s_cap;
         }
     }
     return cv.off + ALIGN;
@@ -1437,24 +1454,40 @@ static scbb_status adjoint_backward_core(scbb_adjoint* a, const double* gA, cons
     launch_adj_final(c->lp, a->g, a->g + N, a->lam[0], c->st);
     c->launches++;
     const AdjIB ib{c->d.Fibm, c->d.mask, a->cap.luh, a->cap.lfi, a->cap.uh};
-    int cur = 0;
-    for (int s = a->nseg - 1; s >= 0; s--) {
-        const int len = (int)std::min<long long>(a->K, a->n - (long long)s * a->K);
-        CUDA_TRY(c, cudaMemcpyAsync(a->L, a->ckpt + (size_t)s * lat, sizeof(float) * lat, cudaMemcpyDeviceToDevice,
-                                    c->st));
-        if (a->ibm)
-            CUDA_TRY(c, cudaMemcpyAsync(c->d.X, a->Xck + (size_t)s * NV, sizeof(float4) * NV,
-                                        cudaMemcpyDeviceToDevice, c->st));
-        // recompute the segment with the forward kernels, keeping every lattice, density field and wall plane
-        // (and, with a capsule, every vertex position)
-        const size_t nw = (size_t)4 * c->lp.nxy;
+    // One segment of `len` steps from its checkpoint (already in a->L[0] and d.X): recompute it with the forward
+    // kernels, keeping every lattice, density field and wall plane (and, with a capsule, every vertex position),
+    // then step the adjoint back through it.  Every pointer depends on the step within the segment only, so a
+    // full segment is the same stream of work whichever segment it is: it is captured once per call (and per
+    // parity of the adjoint lattices) and replayed.
+    const size_t nw = (size_t)4 * c->lp.nxy;
+    // the context's device state with the membrane arrays of step k's slot
+    auto slot = [&](int k) {
+        DevState d = c->d;
+        if (!a->ibm) return d;
+        const size_t NT = c->d.NT;
+        d.corner = a->s_corner + (size_t)k * 12 * NT;
+        d.ccot = a->s_ccot + (size_t)k * 3 * NT;
+        d.tvol = a->s_tvol + (size_t)k * NT;
+        d.Fsk = a->s_Fsk + (size_t)k * NV;
+        d.dV = a->s_dV + (size_t)k * NV;
+        d.nrm = a->s_nrm + (size_t)k * NV;
+        d.F = a->s_F + (size_t)k * NV;
+        d.AK = a->s_AK + (size_t)k * NV;
+        d.cap_red = a->s_cap + (size_t)k * 4 * NM;
+        return d;
+    };
+    auto enqueue_segment = [&](int len, int cur0) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+        int cu = cur0;
         for (int k = 0; k < len; k++) {
             float* gh = c->lp.walls ? a->Gh + (size_t)k * nw : c->d.ghost;
             if (a->ibm) {
-                CUDA_TRY(c, cudaMemcpyAsync(a->Xs + (size_t)k * NV, c->d.X, sizeof(float4) * NV,
-                                            cudaMemcpyDeviceToDevice, c->st));
-                c->launches += launch_membrane_forces(c->lp, c->d, false, 0, c->st);
-                launch_ibm_spread(c->lp, c->d, c->st);
+                chk(cudaMemcpyAsync(a->Xs + (size_t)k * NV, c->d.X, sizeof(float4) * NV, cudaMemcpyDeviceToDevice,
+                                    c->st));
+                const DevState dk = slot(k);
+                c->launches += launch_membrane_forces(c->lp, dk, false, 0, c->st);
+                launch_ibm_spread(c->lp, dk, c->st);
                 c->launches++;
             }
             if (c->lp.walls && !bulk_writes_ghost(c->lp))
@@ -1469,27 +1502,74 @@ static scbb_status adjoint_backward_core(scbb_adjoint* a, const double* gA, cons
         }
         for (int k = len - 1; k >= 0; k--) {
             const float* gh = c->lp.walls ? a->Gh + (size_t)k * nw : nullptr;
+            const DevState dk = slot(k);
             if (a->ibm) {
-                // the step's membrane forces and spread force at X(t), and the interpolation transposed
-                CUDA_TRY(c, cudaMemcpyAsync(c->d.X, a->Xs + (size_t)k * NV, sizeof(float4) * NV,
-                                            cudaMemcpyDeviceToDevice, c->st));
-                c->launches += launch_membrane_forces(c->lp, c->d, false, 0, c->st);
-                launch_ibm_spread(c->lp, c->d, c->st);
-                launch_cap_adj_spread(c->lp, c->d, a->cap, c->st);
+                // the step's spread force at X(t) from its stored node forces, and the interpolation transposed
+                chk(cudaMemcpyAsync(c->d.X, a->Xs + (size_t)k * NV, sizeof(float4) * NV, cudaMemcpyDeviceToDevice,
+                                    c->st));
+                launch_ibm_spread(c->lp, dk, c->st);
+                launch_cap_adj_spread(c->lp, dk, a->cap, c->st);
                 c->launches += 2;
             }
-            launch_adj_step(c->lp, a->L + (size_t)k * lat, a->R + (size_t)k * 2 * N, gh, a->lam[cur],
-                            a->lam[1 - cur], a->scr, a->gw, a->part, c->st, a->ibm ? &ib : nullptr);
+            launch_adj_step(c->lp, a->L + (size_t)k * lat, a->R + (size_t)k * 2 * N, gh, a->lam[cu], a->lam[1 - cu],
+                            a->scr, a->gw, a->part, c->st, a->ibm ? &ib : nullptr);
             if (a->ibm) {
-                launch_cap_adj_vertices(c->lp, c->d, a->cap, c->st);
-                c->launches += 6;
+                launch_cap_adj_vertices(c->lp, dk, a->cap, c->st);
+                c->launches += 4;
             }
-            cur ^= 1;
+            cu ^= 1;
         }
         c->launches += ((c->lp.walls ? 5 : 2) + (bulk_split(c->lp) ? 2 : 1) -
                         (c->lp.walls && bulk_writes_ghost(c->lp) ? 2 : 0)) * len;
-        CUDA_TRY(c, cudaGetLastError());
+        chk(cudaGetLastError());
+        return e;
+    };
+    cudaGraphExec_t seg_graph[2] = {nullptr, nullptr};   // full segments, by the parity of the adjoint lattices
+    long long seg_launches[2] = {0, 0};
+    auto release = [&]() {
+        for (auto& g : seg_graph)
+            if (g) cudaGraphExecDestroy(g);
+    };
+    int cur = 0;
+    for (int s = a->nseg - 1; s >= 0; s--) {
+        const int len = (int)std::min<long long>(a->K, a->n - (long long)s * a->K);
+        cudaError_t e = cudaMemcpyAsync(a->L, a->ckpt + (size_t)s * lat, sizeof(float) * lat, cudaMemcpyDeviceToDevice,
+                                        c->st);
+        if (e == cudaSuccess && a->ibm)
+            e = cudaMemcpyAsync(c->d.X, a->Xck + (size_t)s * NV, sizeof(float4) * NV, cudaMemcpyDeviceToDevice, c->st);
+        if (e != cudaSuccess) {
+            release();
+            CUDA_TRY(c, e);
+        }
+        if (len == a->K && graphs_enabled() && !seg_graph[cur]) {
+            const long long l0 = c->launches;
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                const cudaError_t ce = enqueue_segment(len, cur);
+                const cudaError_t ee = cudaStreamEndCapture(c->st, &g);
+                if (ce == cudaSuccess && ee == cudaSuccess && g &&
+                    cudaGraphInstantiate(&seg_graph[cur], g, 0) != cudaSuccess)
+                    seg_graph[cur] = nullptr;
+                if (g) cudaGraphDestroy(g);
+            }
+            cudaGetLastError();
+            seg_launches[cur] = c->launches - l0;
+            c->launches = l0;
+        }
+        if (len == a->K && seg_graph[cur]) {
+            e = cudaGraphLaunch(seg_graph[cur], c->st);
+            c->launches += seg_launches[cur];
+            if (len & 1) cur ^= 1;
+        } else {
+            e = enqueue_segment(len, cur);
+            if (len & 1) cur ^= 1;
+        }
+        if (e != cudaSuccess) {
+            release();
+            CUDA_TRY(c, e);
+        }
     }
+    release();
     launch_adj_initial(c->lp, a->ckpt, a->lam[cur], a->g, c->st);
     c->launches++;
     std::vector<double> part((size_t)ADJ_PARAMS * a->blocks);
