@@ -112,7 +112,11 @@ typedef struct {
     const double* elem_colour;  /* [nt] or NULL */
 } scbb_mesh;
 
-/* Bytes of device workspace a context with this description needs (0 on invalid input). */
+/* Bytes of device workspace a context with this description needs (0 on invalid input).  The populations take
+ * one lattice of 2 * 19 * N values (FP32, or 16-bit with storage 1 or 2), updated in place by the two-kernel
+ * bulk phase, plus 5 N doubles of staging for the host's fields; a context with bounce-back membranes, or one
+ * whose bulk phase is a fused kernel (tau != 1, or rows too long for the two-kernel phase), takes two lattices
+ * (read one, write the other), the spare one staging the fields. */
 size_t scbb_workspace_bytes(const scbb_lattice* lat, const scbb_fluid* fl, int n_mesh, const scbb_mesh* meshes);
 
 /* Create a context.  dev_workspace: device pointer, 256-byte aligned, of at least `bytes` bytes, owned by
@@ -214,7 +218,9 @@ scbb_status scbb_population_moments_noalloc(const float* dev_f, int nx, int ny, 
  * state in every shape that fits the box (one untimed launch, then reps launches between CUDA events, into the
  * spare lattice, which the next step rewrites) and keeps the fastest for the context's later steps.  The
  * results of a step do not depend on the shape.  chosen (may be NULL): the shape kept, 0 .. 3, or -1 when the
- * context runs the general bulk kernel (nx not a multiple of 4), which has no shapes.  Synchronous; call it
+ * context runs the general bulk kernel (nx not a multiple of 4), which has no shapes, or keeps one lattice
+ * updated in place (every context without bounce-back membranes on the two-kernel bulk phase: a timing launch
+ * would advance its state; its kernel B runs the pair form, which has one shape).  Synchronous; call it
  * between steps, not while a batch holds the context. */
 scbb_status scbb_autotune(scbb_ctx* ctx, int reps, int* chosen);
 

@@ -1402,7 +1402,9 @@ static bool moments_staged_geometry(const LbmParams& p, int& wpb, size_t& smem) 
     if (!staged_enabled() || p.onsite || p.nx < 64 || p.nx > 512 || (p.nx * es) % 16 != 0) return false;
     const size_t two = 2 * (size_t)2 * Q * p.nx * es;
     wpb = (int)std::min<size_t>(8, (MOMENTS_SMEM_BUDGET - 128) / two);
-    if (wpb < 1) return false;
+    // fewer than four streaming warps per SM cannot keep the loads in flight (256-wide FP32 rows: two warps,
+    // slower than the register form)
+    if (wpb < 4) return false;
     smem = 128 + (size_t)wpb * two;
     return true;
 }
@@ -1420,6 +1422,8 @@ static bool pair_geometry(const LbmParams& p, dim3& grid, int& TY, size_t& smem)
     if (4 * NQ > PAIR_THREADS) return false;
     TY = std::max(2, std::min(PAIR_THREADS / (2 * NQ), p.ny));
     if (2 * NQ * TY > PAIR_THREADS) return false;
+    // tiles under four rows re-read their two halo rows for every one or two rows collided (nx > 128)
+    if (TY < 4 && TY < p.ny) return false;
     const int cols = (p.ny + TY - 1) / TY;
     grid = dim3(cols, split_segments(p, cols, sm_count() * 3, 4), 1);
     smem = collide_staged_smem(p, TY);
@@ -1490,7 +1494,8 @@ void launch_split(const LbmParams& p, const float* S, float* D, float* rho, floa
     size_t msmem = 0;
     const bool a_staged = vec && moments_staged_geometry(p, wpb, msmem);
     const size_t csmem = collide_staged_smem(p, TY);
-    const bool b_staged = vec && staged_enabled() && csmem <= STAGED_SMEM_MAX;
+    // the staged quad form, like the pair form, where tiles hold at least four rows of at most 128 nodes
+    const bool b_staged = vec && staged_enabled() && csmem <= STAGED_SMEM_MAX && p.nx <= 128;
     dim3 pgrid;
     int pTY = 0;
     size_t psmem = 0;

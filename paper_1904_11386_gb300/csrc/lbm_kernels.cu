@@ -26,17 +26,18 @@ namespace scbb {
 // (c, i, x - c_i); the rest population closes the node's mass over the values as stored.  The lattice is
 // zeroed beforehand (slots only wall nodes would pull from stay 0).
 // ------------------------------------------------------------------------------------------------------
-template <typename T>
-__global__ void k_init_state(LbmParams p, T* __restrict__ S, const float* __restrict__ rho_st,
-                             const float* __restrict__ u_st) {
+template <typename T, typename TI>
+__global__ void k_init_state(LbmParams p, T* __restrict__ S, const TI* __restrict__ rho_st,
+                             const TI* __restrict__ u_st) {
     const unsigned int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
     const int z = n / p.nxy;
     if (is_wall_plane(p, z)) return;
     const int r = n - z * p.nxy;
     const int y = r / p.nx, x = r - y * p.nx;
-    const float ux = u_st[n], uy = u_st[p.N + n], uz = u_st[2 * p.N + n];
-    const float a = rho_st[n], b = rho_st[p.N + n];
+    // the fields in FP32 (rounded to nearest when they come in FP64)
+    const float ux = (float)u_st[n], uy = (float)u_st[p.N + n], uz = (float)u_st[2 * p.N + n];
+    const float a = (float)rho_st[n], b = (float)rho_st[p.N + n];
     const float uu = ux * ux + uy * uy + uz * uz;
     float sa = 0.f, sb = 0.f;
 #pragma unroll
@@ -762,7 +763,14 @@ void launch_bulk(const LbmParams& p, const float* S, float* D, float* rho, float
 void launch_init_state(const LbmParams& p, float* S, const float* rho_st, const float* u_st, cudaStream_t st) {
     with_storage(p.store, [&](auto* tag) {
         using T = std::remove_pointer_t<decltype(tag)>;
-        k_init_state<T><<<(p.N + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<T*>(S), rho_st, u_st);
+        k_init_state<T, float><<<(p.N + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<T*>(S), rho_st, u_st);
+    });
+}
+
+void launch_init_state(const LbmParams& p, float* S, const double* rho_st, const double* u_st, cudaStream_t st) {
+    with_storage(p.store, [&](auto* tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        k_init_state<T, double><<<(p.N + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<T*>(S), rho_st, u_st);
     });
 }
 
@@ -780,7 +788,8 @@ void launch_wall_ghost(const LbmParams& p, const float* S, float* wall_rho, floa
 // ------------------------------------------------------------------------------------------------------
 // what = 2, 3: the populations of component A or B only, [node][i] (19 N floats)
 template <typename T>
-__global__ void k_export(LbmParams p, const T* __restrict__ S, float* __restrict__ out, int what) {
+__global__ void k_export(LbmParams p, const T* __restrict__ S, float* __restrict__ out, int what,
+                         double* __restrict__ out64) {
     unsigned int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
     int z = n / p.nxy;
@@ -811,6 +820,15 @@ __global__ void k_export(LbmParams p, const T* __restrict__ S, float* __restrict
         for (int i = 0; i < Q; i++) out[(size_t)n * Q + i] = f[c * Q + i];
         return;
     }
+    if (what >= 16) {                                  // one direction of one component: f[c Q + i], c Q + i = what - 16
+        const int ci = what - 16;
+        float v = 0.f;
+#pragma unroll
+        for (int k = 0; k < 2 * Q; k++)
+            if (k == ci) v = f[k];
+        out[n] = v;
+        return;
+    }
     // read-out in FP64: the momentum is a sum of populations with +- cancellations, whose FP32 rounding
     // (about 19 * 2^-24 of the largest population) would otherwise show in the exported velocity
     double ra = 0.0, rb = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
@@ -822,6 +840,14 @@ __global__ void k_export(LbmParams p, const T* __restrict__ S, float* __restrict
     }
     const double rt = ra + rb;
     const double irt = rt > 0.0 ? 1.0 / rt : 0.0;
+    if (what == 4) {                                   // the same FP32 values, widened to FP64
+        out64[n] = (double)(float)ra;
+        out64[p.N + n] = (double)(float)rb;
+        out64[2 * (size_t)p.N + n] = (double)(float)(jx * irt);
+        out64[3 * (size_t)p.N + n] = (double)(float)(jy * irt);
+        out64[4 * (size_t)p.N + n] = (double)(float)(jz * irt);
+        return;
+    }
     out[n] = (float)ra;
     out[p.N + n] = (float)rb;
     out[2 * (size_t)p.N + n] = (float)(jx * irt);
@@ -829,32 +855,10 @@ __global__ void k_export(LbmParams p, const T* __restrict__ S, float* __restrict
     out[4 * (size_t)p.N + n] = (float)(jz * irt);
 }
 
-__global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
-    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
-        dst[q] = (float)src[q];
-}
-
-__global__ void k_to_f64(const float* __restrict__ src, double* __restrict__ dst, size_t n) {
-    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
-        dst[q] = (double)src[q];
-}
-
-void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t st) {
-    if (n == 0) return;
-    const size_t blocks = std::min<size_t>((n + 255) / 256, 152 * 16);
-    k_to_f32<<<(unsigned)blocks, 256, 0, st>>>(src, dst, n);
-}
-
-void launch_to_f64(const float* src, double* dst, size_t n, cudaStream_t st) {
-    if (n == 0) return;
-    const size_t blocks = std::min<size_t>((n + 255) / 256, 152 * 16);
-    k_to_f64<<<(unsigned)blocks, 256, 0, st>>>(src, dst, n);
-}
-
-void launch_export(const LbmParams& p, const float* S, float* out, int what, cudaStream_t st) {
+void launch_export(const LbmParams& p, const float* S, float* out, int what, cudaStream_t st, double* out64) {
     with_storage(p.store, [&](auto* tag) {
         using T = std::remove_pointer_t<decltype(tag)>;
-        k_export<T><<<(p.N + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<const T*>(S), out, what);
+        k_export<T><<<(p.N + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<const T*>(S), out, what, out64);
     });
 }
 

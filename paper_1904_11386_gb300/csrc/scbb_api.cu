@@ -200,6 +200,13 @@ BBSizes bb_sizes(int nm, const scbb_mesh* ms, int max_boundary) {
     return z;
 }
 
+// One lattice, updated in place by the two-kernel bulk phase: every context but those with bounce-back membranes,
+// when the bulk phase is the two-kernel one (tau = 1 and a box it fits).
+static bool lattice_in_place(const scbb_lattice* lat, const scbb_fluid* fl, int nm) {
+    if (nm > 0 && fl->coupling == 0) return false;
+    return bulk_split(make_params(lat, fl));
+}
+
 // Lays out every device buffer; returns total bytes.
 size_t layout(const scbb_lattice* lat, const scbb_fluid* fl, int nm, const scbb_mesh* ms, void* base, DevState* d) {
     Carve c(base);
@@ -207,10 +214,15 @@ size_t layout(const scbb_lattice* lat, const scbb_fluid* fl, int nm, const scbb_
     const size_t nxy = (size_t)lat->nx * lat->ny;
     const int NV = total(ms, nm, false), NT = total(ms, nm, true);
     DevState t{};
-    // FP16 and BF16 storage halve the lattices; each still holds the 5 N floats staged through it by set_density
+    // FP16 and BF16 storage halve the lattices.  The two-kernel bulk phase reads the whole lattice (kernel A)
+    // before it writes any of it (kernel B), so it updates one lattice in place; the bounce-back coupling keeps
+    // two, because its boundary kernel pulls the step's populations after kernel B has run.  One lattice comes
+    // with a staging area of 5 N doubles for the host's fields; with two, the spare lattice stages them.
     const size_t pop_floats = fl->storage != 0 ? (size_t)Q * N : (size_t)2 * Q * N;
+    const bool inplace = lattice_in_place(lat, fl, nm);
     t.S[0] = c.take<float>(pop_floats);
-    t.S[1] = c.take<float>(pop_floats);
+    t.S[1] = inplace ? t.S[0] : c.take<float>(pop_floats);
+    t.stage = inplace ? c.take<double>(5 * N) : nullptr;
     t.rho = c.take<float>(2 * N);
     t.J = c.take<float>(3 * N);
     const bool ibm = fl->coupling == 1 && NV > 0;
@@ -486,6 +498,7 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
 // FP64 staging area in the spare lattice (dead between steps: the next step overwrites all of it), after
 // 5 N floats; null when the lattice is too small for 5 N floats and 5 N doubles (tiny boxes).
 static double* stage64(scbb_ctx* c) {
+    if (c->d.stage) return c->d.stage;
     const size_t N = c->lp.N;
     const size_t lat_bytes = (c->lp.store ? sizeof(uint16_t) : sizeof(float)) * 2 * Q * N;
     const size_t off = (sizeof(float) * 5 * N + 255) / 256 * 256;
@@ -498,8 +511,8 @@ scbb_status scbb_set_density(scbb_ctx* c, const double* rhoA, const double* rhoB
     if (c->broken) return SCBB_E_STATE;
     const size_t N = c->lp.N;
     c->cur = 0;                       // state in lattice 0 at step 0 (the captured step pairs stay valid)
-    // the FP64 fields go to the device as they are (pinned host memory moves at full link speed) and are
-    // rounded to FP32 there, in the spare lattice: [5 N floats][5 N doubles]
+    // the FP64 fields go to the device as they are (pinned host memory moves at full link speed) and the initial
+    // state is built from them there, in FP32 (the staging area, or the spare lattice after 5 N floats)
     float* stage = c->d.S[1 - c->cur];
     double* s64 = stage64(c);
     if (s64) {
@@ -507,8 +520,6 @@ scbb_status scbb_set_density(scbb_ctx* c, const double* rhoA, const double* rhoB
         CUDA_TRY(c, cudaMemcpyAsync(s64 + N, rhoB, sizeof(double) * N, cudaMemcpyHostToDevice, c->st));
         if (u) CUDA_TRY(c, cudaMemcpyAsync(s64 + 2 * N, u, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->st));
         else CUDA_TRY(c, cudaMemsetAsync(s64 + 2 * N, 0, sizeof(double) * 3 * N, c->st));
-        launch_to_f32(s64, stage, 5 * N, c->st);
-        c->launches++;
     } else {
         std::vector<float> h(5 * N);
         for (size_t n = 0; n < N; n++) {
@@ -523,7 +534,8 @@ scbb_status scbb_set_density(scbb_ctx* c, const double* rhoA, const double* rhoB
     }
     CUDA_TRY(c, cudaMemsetAsync(c->d.S[c->cur], 0,
                                 (c->lp.store ? sizeof(uint16_t) : sizeof(float)) * 2 * Q * N, c->st));
-    launch_init_state(c->lp, c->d.S[c->cur], stage, stage + 2 * N, c->st);
+    if (s64) launch_init_state(c->lp, c->d.S[c->cur], s64, s64 + 2 * N, c->st);
+    else launch_init_state(c->lp, c->d.S[c->cur], stage, stage + 2 * N, c->st);
     c->launches++;
     if (c->d.NV > 0) {
         CUDA_TRY(c, cudaMemcpyAsync(c->d.X, c->d.X0, sizeof(float4) * c->d.NV, cudaMemcpyDeviceToDevice, c->st));
@@ -932,9 +944,30 @@ scbb_status scbb_sync(scbb_ctx* c) {
 
 static scbb_status export_state(scbb_ctx* c, int what, std::vector<float>& h) {
     const size_t N = c->lp.N;
-    float* stage = c->d.S[1 - c->cur];
     const size_t cnt = what == 1 ? 2 * Q * N : 5 * N;
     h.resize(cnt);
+    if (c->d.stage) {
+        // one lattice: export one direction of one component at a time through the staging area
+        float* stage = reinterpret_cast<float*>(c->d.stage);
+        std::vector<float> one(N);
+        const int parts = what == 1 ? 2 * Q : 1;
+        for (int k = 0; k < parts; k++) {
+            launch_export(c->lp, c->d.S[c->cur], stage, what == 1 ? 16 + k : what, c->st);
+            c->launches++;
+            CUDA_TRY(c, cudaGetLastError());
+            if (what != 1) {
+                CUDA_TRY(c, cudaMemcpyAsync(h.data(), stage, sizeof(float) * cnt, cudaMemcpyDeviceToHost, c->st));
+                CUDA_TRY(c, cudaStreamSynchronize(c->st));
+                break;
+            }
+            CUDA_TRY(c, cudaMemcpyAsync(one.data(), stage, sizeof(float) * N, cudaMemcpyDeviceToHost, c->st));
+            CUDA_TRY(c, cudaStreamSynchronize(c->st));
+            const int comp = k / Q, i = k % Q;
+            for (size_t n = 0; n < N; n++) h[((size_t)comp * N + n) * Q + i] = one[n];
+        }
+        return SCBB_OK;
+    }
+    float* stage = c->d.S[1 - c->cur];
     if (what == 1 && c->lp.store) {
         // a 16-bit lattice holds 19 N floats: export the components one after the other
         for (int comp = 0; comp < 2; comp++) {
@@ -962,10 +995,8 @@ scbb_status scbb_get_fields(scbb_ctx* c, double* rhoA, double* rhoB, double* u) 
     if (s64) {
         // fields in FP32, widened to FP64 on the device, copied straight into the caller's arrays
         const size_t N = c->lp.N;
-        float* stage = c->d.S[1 - c->cur];
-        launch_export(c->lp, c->d.S[c->cur], stage, 0, c->st);
-        launch_to_f64(stage, s64, 5 * N, c->st);
-        c->launches += 2;
+        launch_export(c->lp, c->d.S[c->cur], nullptr, 4, c->st, s64);
+        c->launches++;
         CUDA_TRY(c, cudaGetLastError());
         if (rhoA) CUDA_TRY(c, cudaMemcpyAsync(rhoA, s64, sizeof(double) * N, cudaMemcpyDeviceToHost, c->st));
         if (rhoB) CUDA_TRY(c, cudaMemcpyAsync(rhoB, s64 + N, sizeof(double) * N, cudaMemcpyDeviceToHost, c->st));
@@ -1057,6 +1088,9 @@ scbb_status scbb_autotune(scbb_ctx* c, int reps, int* chosen) {
     if (!c || reps < 1) return SCBB_E_INVAL;
     if (c->broken) return SCBB_E_STATE;
     if (chosen) *chosen = -1;
+    // one lattice updated in place: a timing launch would advance the state, and kernel B's pair form has one
+    // shape; the context keeps its shape
+    if (c->d.S[0] == c->d.S[1]) return SCBB_OK;
     LbmParams q = c->lp;
     q.b4cfg = 0;
     if (!bulk_vectorised(q)) return SCBB_OK;      // the general bulk kernel has no shapes to choose from

@@ -157,7 +157,9 @@ struct CapDev {
 
 // Device-side buffers of a context (all carved from the caller's workspace).
 struct DevState {
-    float* S[2];            // populations, 2 * 19 * N values each, of the type LbmParams::store names
+    float* S[2];            // populations, 2 * 19 * N values each, of the type LbmParams::store names; one
+                            // lattice (S[1] == S[0]) when the two-kernel bulk phase updates it in place
+    double* stage;          // with one lattice: host-I/O staging, 5 N doubles; else null (the spare lattice serves)
     float* rho;             // [2][N] densities of the last collision
     float* J;               // [3][N] momentum of the last stream (two-kernel bulk phase)
     float* u;               // [3][N] velocity incl. half force, written where the IBM mask is set
@@ -314,6 +316,7 @@ __device__ __forceinline__ void onsite_fix(const LbmParams& p, int z, float (&f)
 
 // ---- launches (lbm_kernels.cu) ----
 void launch_init_state(const LbmParams& p, float* S, const float* rho_st, const float* u_st, cudaStream_t st);
+void launch_init_state(const LbmParams& p, float* S, const double* rho_st, const double* u_st, cudaStream_t st);
 void launch_wall_ghost(const LbmParams& p, const float* S, float* wall_rho, float* ghost, cudaStream_t st);
 // mode 0: fluid only (also with bounce-back membranes), 1: immersed boundary (mask = IBM stencil bits)
 // J: [3][N] momentum scratch of the two-kernel bulk phase (tau = 1), which also writes the wall ghost
@@ -360,10 +363,9 @@ struct BatchDesc {
     BatchBox box[BATCH_MAX];
 };
 bool launch_batch_bulk(BatchDesc& d, int mode, int store, cudaStream_t st);
-void launch_export(const LbmParams& p, const float* S, float* out, int what, cudaStream_t st);
-// element-wise FP64 -> FP32 (round to nearest) and FP32 -> FP64 conversions of n values on the device
-void launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t st);
-void launch_to_f64(const float* src, double* dst, size_t n, cudaStream_t st);
+// what: 0 fields (rho^A, rho^B, u: 5 N floats), 1 populations [c][n][i], 2 / 3 one component's [n][i],
+// 4 fields in FP64 into out64 (5 N doubles), 16 + c Q + i one direction of one component (N floats)
+void launch_export(const LbmParams& p, const float* S, float* out, int what, cudaStream_t st, double* out64 = nullptr);
 void launch_moments_reduce(const LbmParams& p, const float* S, double* red, cudaStream_t st);
 int bulk_grid_blocks(const LbmParams& p);
 

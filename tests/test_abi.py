@@ -56,7 +56,12 @@ def test_workspace_sizing_and_argument_checks():
     p = inputs.small_problem(n=16, capsule=False)
     lat, fl = scbb.lattice_of(p), scbb.fluid_of(p)
     nb = L.scbb_workspace_bytes(ctypes.byref(lat), ctypes.byref(fl), 0, None)
-    assert nb >= 2 * 2 * 19 * p.n_nodes * 4
+    # tau = 1: one lattice updated in place by the two-kernel bulk phase, and 5 N doubles of staging
+    assert 2 * 19 * p.n_nodes * 4 + 5 * p.n_nodes * 8 <= nb < 2 * (2 * 19 * p.n_nodes * 4)
+    slow = scbb.fluid_of(p)
+    slow.tau = 0.8
+    # tau != 1: the fused bulk kernel reads one lattice and writes the other
+    assert L.scbb_workspace_bytes(ctypes.byref(lat), ctypes.byref(slow), 0, None) >= 2 * (2 * 19 * p.n_nodes * 4)
     bad = scbb.fluid_of(p)
     bad.tau = 0.4
     assert L.scbb_workspace_bytes(ctypes.byref(lat), ctypes.byref(bad), 0, None) == 0

@@ -14,12 +14,13 @@ def _pair(p):
     return scbb.Sim(p), scbb.Sim(p)
 
 
-def test_fluid_results_do_not_depend_on_the_shape():
-    """64^3 periodic droplet: the autotuned context and the default one agree bit for bit after 20 steps (the
-    per-node arithmetic of the bulk kernel does not depend on the tiling)."""
+def test_one_lattice_contexts_keep_their_shape():
+    """64^3 periodic droplet: its one lattice is updated in place, so the autotuner times nothing (a timing
+    launch would advance the state), reports no shape, and leaves the state as it was: the context then agrees
+    bit for bit with an untouched one after 20 steps.  (The quad form's shapes are compared bit for bit in
+    test_gpu_staged.py.)"""
     a, b = _pair(inputs.cfg_adjoint(n=64, R_drop=16.0))
-    k = a.scbb_autotune(3)
-    assert 0 <= k <= 3
+    assert a.scbb_autotune(3) == -1
     a.scbb_step(20)
     b.scbb_step(20)
     fa, fb = a.scbb_get_fields(), b.scbb_get_fields()
