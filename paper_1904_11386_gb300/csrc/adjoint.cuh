@@ -38,7 +38,7 @@ void launch_adj_final(const LbmParams& p, const float* gA, const float* gB, floa
 // marks, the adjoint of the half-force velocity it wrote at the marked nodes (in), the adjoint of the spread
 // force and the half-force velocity itself at the marked nodes (out).
 struct AdjIB {
-    const float* Fibm;
+    const IbmF* Fibm;
     const uint32_t* mask;
     const float* luh;
     float* lfi;

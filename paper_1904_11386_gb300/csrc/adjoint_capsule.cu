@@ -432,7 +432,7 @@ __global__ void k_cap_adj_gather(LbmParams p, DevState d, AdjCap a) {
         if (!st.fluid[q]) continue;
         const unsigned int n = st.node[q];
         for (int k = 0; k < 3; k++) {
-            d.Fibm[(size_t)k * p.N + n] = 0.f;
+            d.Fibm[(size_t)k * p.N + n] = 0ull;
             a.luh[(size_t)k * p.N + n] = 0.f;
             a.lfi[(size_t)k * p.N + n] = 0.f;
             a.uh[(size_t)k * p.N + n] = 0.f;

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_local(LbmParams p, const
         if (IB) {
             marked = (ib.mask[n >> 5] >> (n & 31)) & 1u;
             if (marked)
-                for (int k = 0; k < 3; k++) Fi[k] = ib.Fibm[(size_t)k * N + n];
+                for (int k = 0; k < 3; k++) Fi[k] = ibm_unfix(ib.Fibm[(size_t)k * N + n]);
         }
         const float tf = p.tau * irt;
         const float uA[3] = {up[0] + ta * FA[0] + tf * Fi[0], up[1] + ta * FA[1] + tf * Fi[1],

@@ -124,7 +124,7 @@ __device__ __forceinline__ float wall_ghost1(const LbmParams& p, const float* __
 template <int MODE, typename T>
 __device__ __forceinline__ void collide1_tile(const LbmParams& p, T* __restrict__ D, const float* __restrict__ rho,
                                               const float* __restrict__ J, float* __restrict__ ghost,
-                                              const float* __restrict__ Fibm, const uint32_t* __restrict__ mask,
+                                              const IbmF* __restrict__ Fibm, const uint32_t* __restrict__ mask,
                                               float* __restrict__ u_out, int* __restrict__ err, int TY, int tile,
                                               int seg, int nseg, float* ring) {
     constexpr bool IBM = MODE == 1;
@@ -250,7 +250,7 @@ __device__ __forceinline__ void collide1_tile(const LbmParams& p, T* __restrict_
             if (ibm_node) {
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
-                    const float fi = Fibm[(size_t)d * p.N + n0];
+                    const float fi = ibm_unfix(Fibm[(size_t)d * p.N + n0]);
                     FA[d] += ra * irt * fi;
                     FB[d] += rb * irt * fi;
                 }
@@ -326,7 +326,7 @@ template <int MODE, typename T>
 __device__ __forceinline__ void collide4_plane(const LbmParams& p, T* __restrict__ D, const float* ring, int plane_sz,
                                                int rel, int dz, int r, int x, const int ry[3], int z, float4 a4,
                                                float4 b4, float4 jx4, float4 jy4, float4 jz4,
-                                               const float* __restrict__ Fibm, const uint32_t* __restrict__ mask,
+                                               const IbmF* __restrict__ Fibm, const uint32_t* __restrict__ mask,
                                                float* __restrict__ u_out, int* __restrict__ err) {
     constexpr bool IBM = MODE == 1;
     const int nx = p.nx;
@@ -393,7 +393,7 @@ __device__ __forceinline__ void collide4_plane(const LbmParams& p, T* __restrict
         if (IBM && ((bits >> k) & 1u)) {
 #pragma unroll
             for (int d = 0; d < 3; d++) {
-                const float fi = Fibm[(size_t)d * p.N + n0 + k];
+                const float fi = ibm_unfix(Fibm[(size_t)d * p.N + n0 + k]);
                 FA[d] += ra[k] * irt * fi;
                 FB[d] += rb[k] * irt * fi;
             }
@@ -487,7 +487,7 @@ __device__ __forceinline__ void collide4_plane(const LbmParams& p, T* __restrict
 template <int MODE, typename T>
 __device__ __forceinline__ void collide4_tile(const LbmParams& p, T* __restrict__ D, const float* __restrict__ rho,
                                               const float* __restrict__ J, float* __restrict__ ghost,
-                                              const float* __restrict__ Fibm, const uint32_t* __restrict__ mask,
+                                              const IbmF* __restrict__ Fibm, const uint32_t* __restrict__ mask,
                                               float* __restrict__ u_out, int* __restrict__ err, int TY, int tile,
                                               int seg, int nseg, float* ring) {
     constexpr bool IBM = MODE == 1;
@@ -735,7 +735,7 @@ __global__ void __launch_bounds__(256) k_moments_staged(LbmParams p, const T* __
 template <int MODE, typename T>
 __device__ __forceinline__ void collide4_staged(const LbmParams& p, T* __restrict__ D, const float* __restrict__ rho,
                                                 const float* __restrict__ J, float* __restrict__ ghost,
-                                                const float* __restrict__ Fibm, const uint32_t* __restrict__ mask,
+                                                const IbmF* __restrict__ Fibm, const uint32_t* __restrict__ mask,
                                                 float* __restrict__ u_out, int* __restrict__ err, int TY, int tile,
                                                 int seg, int nseg, float* ring, float* stage, uint64_t* bar) {
     const int nx = p.nx;
@@ -933,7 +933,7 @@ __global__ void __launch_bounds__(256) k_moments1(LbmParams p, const T* __restri
 template <int MODE, typename T, bool VEC>
 __global__ void __launch_bounds__(512, 1)
 k_collide(LbmParams p, T* __restrict__ D, const float* __restrict__ rho, const float* __restrict__ J,
-          float* __restrict__ ghost, const float* __restrict__ Fibm, const uint32_t* __restrict__ mask,
+          float* __restrict__ ghost, const IbmF* __restrict__ Fibm, const uint32_t* __restrict__ mask,
           float* __restrict__ u_out, int* __restrict__ err, int TY) {
     pdl_wait();
     extern __shared__ float ring[];                      // psi [4 planes][2 components][TY + 2 rows][nx]
@@ -954,7 +954,7 @@ template <int MODE, typename T>
 __device__ __forceinline__ void collide4_half(const LbmParams& p, T* __restrict__ D, const float* ring, int plane_sz,
                                               int rel, int dz, int r, int x, int c, const int ry[3], int z,
                                               float4 a4, float4 b4, float4 jx4, float4 jy4, float4 jz4,
-                                              const float* __restrict__ Fibm, const uint32_t* __restrict__ mask,
+                                              const IbmF* __restrict__ Fibm, const uint32_t* __restrict__ mask,
                                               float* __restrict__ u_out, int* __restrict__ err, unsigned int pairs) {
     constexpr bool IBM = MODE == 1;
     const int nx = p.nx;
@@ -1011,7 +1011,7 @@ __device__ __forceinline__ void collide4_half(const LbmParams& p, T* __restrict_
         if (IBM && ((bits >> k) & 1u)) {
 #pragma unroll
             for (int d = 0; d < 3; d++) {
-                const float fi = Fibm[(size_t)d * p.N + n0 + k];
+                const float fi = ibm_unfix(Fibm[(size_t)d * p.N + n0 + k]);
                 F[d] += rc[k] * irt * fi;
             }
         }
@@ -1095,7 +1095,7 @@ __device__ __forceinline__ void collide4_half(const LbmParams& p, T* __restrict_
 template <int MODE, typename T>
 __device__ __forceinline__ void collide_pair_staged(const LbmParams& p, T* __restrict__ D, const float* __restrict__ rho,
                                                     const float* __restrict__ J, float* __restrict__ ghost,
-                                                    const float* __restrict__ Fibm, const uint32_t* __restrict__ mask,
+                                                    const IbmF* __restrict__ Fibm, const uint32_t* __restrict__ mask,
                                                     float* __restrict__ u_out, int* __restrict__ err, int TY, int tile,
                                                     int seg, int nseg, float* ring, float* stage, uint64_t* bar) {
     const int nx = p.nx;
@@ -1264,7 +1264,7 @@ __device__ __forceinline__ void collide_pair_staged(const LbmParams& p, T* __res
 template <int MODE, typename T>
 __global__ void __launch_bounds__(256, 3)
 k_collide_pair(LbmParams p, T* __restrict__ D, const float* __restrict__ rho, const float* __restrict__ J,
-               float* __restrict__ ghost, const float* __restrict__ Fibm, const uint32_t* __restrict__ mask,
+               float* __restrict__ ghost, const IbmF* __restrict__ Fibm, const uint32_t* __restrict__ mask,
                float* __restrict__ u_out, int* __restrict__ err, int TY) {
     pdl_wait();
     extern __shared__ __align__(128) unsigned char psm[];
@@ -1278,7 +1278,7 @@ k_collide_pair(LbmParams p, T* __restrict__ D, const float* __restrict__ rho, co
 template <int MODE, typename T>
 __global__ void __launch_bounds__(512, 1)
 k_collide_staged(LbmParams p, T* __restrict__ D, const float* __restrict__ rho, const float* __restrict__ J,
-                 float* __restrict__ ghost, const float* __restrict__ Fibm, const uint32_t* __restrict__ mask,
+                 float* __restrict__ ghost, const IbmF* __restrict__ Fibm, const uint32_t* __restrict__ mask,
                  float* __restrict__ u_out, int* __restrict__ err, int TY) {
     pdl_wait();
     // [2 barriers, padded to 128 bytes][psi ring: 4 planes x 2 components x (TY + 2) rows x nx][2 stage buffers]
@@ -1360,7 +1360,7 @@ int split_grid_blocks(const LbmParams& p) {
 
 template <int MODE, typename T, bool VEC>
 static void launch_collide(const LbmParams& p, dim3 grid, int threads, size_t smem, int TY, T* D, const float* rho,
-                           const float* J, float* ghost, const float* Fibm, const uint32_t* mask, float* u, int* err,
+                           const float* J, float* ghost, const IbmF* Fibm, const uint32_t* mask, float* u, int* err,
                            cudaStream_t st) {
     static size_t attr = 0;
     if (smem > attr) {
@@ -1441,7 +1441,7 @@ static bool pair_enabled() {
 
 template <int MODE, typename T>
 static void launch_collide_pair(const LbmParams& p, dim3 grid, size_t smem, int TY, T* D, const float* rho,
-                                const float* J, float* ghost, const float* Fibm, const uint32_t* mask, float* u,
+                                const float* J, float* ghost, const IbmF* Fibm, const uint32_t* mask, float* u,
                                 int* err, cudaStream_t st) {
     static size_t attr = 0;
     if (smem > attr) {
@@ -1472,7 +1472,7 @@ static void launch_moments_staged(const LbmParams& p, int wpb, size_t smem, cons
 
 template <int MODE, typename T>
 static void launch_collide_staged(const LbmParams& p, dim3 grid, int threads, size_t smem, int TY, T* D,
-                                  const float* rho, const float* J, float* ghost, const float* Fibm,
+                                  const float* rho, const float* J, float* ghost, const IbmF* Fibm,
                                   const uint32_t* mask, float* u, int* err, cudaStream_t st) {
     static size_t attr = 0;
     if (smem > attr) {
@@ -1483,7 +1483,7 @@ static void launch_collide_staged(const LbmParams& p, dim3 grid, int threads, si
 }
 
 void launch_split(const LbmParams& p, const float* S, float* D, float* rho, float* J, float* ghost,
-                  const float* Fibm, const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st) {
+                  const IbmF* Fibm, const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st) {
     dim3 grid;
     int threads, TY;
     size_t smem;

@@ -115,7 +115,7 @@ constexpr int bulk2_smem_bytes() {
 template <int TX, int TY, bool IBM>
 __global__ void __launch_bounds__(Tile<TX, TY>::HN, 2)
 k_bulk2(LbmParams p, const float* __restrict__ S, float* __restrict__ D, float* __restrict__ rho_out,
-        const float* __restrict__ ghost, const float* __restrict__ Fibm, const uint32_t* __restrict__ mask,
+        const float* __restrict__ ghost, const IbmF* __restrict__ Fibm, const uint32_t* __restrict__ mask,
         float* __restrict__ u_out, int* __restrict__ err) {
     using T = Tile<TX, TY>;
     extern __shared__ float smem[];
@@ -221,7 +221,7 @@ k_bulk2(LbmParams p, const float* __restrict__ S, float* __restrict__ D, float* 
             if (hit) {
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
-                    const float fi = Fibm[(size_t)d * p.N + n];
+                    const float fi = ibm_unfix(Fibm[(size_t)d * p.N + n]);
                     FA[d] += ra * irt * fi;
                     FB[d] += rb * irt * fi;
                 }
@@ -300,7 +300,7 @@ k_bulk2(LbmParams p, const float* __restrict__ S, float* __restrict__ D, float* 
 template <bool TAU1, int MODE, int NT, int MINB, typename T>
 __global__ void __launch_bounds__(NT, MINB)
 k_bulk4(LbmParams p, const T* __restrict__ S, T* __restrict__ D, float* __restrict__ rho_out,
-        const float* __restrict__ ghost, const float* __restrict__ Fibm, const uint32_t* __restrict__ mask,
+        const float* __restrict__ ghost, const IbmF* __restrict__ Fibm, const uint32_t* __restrict__ mask,
         float* __restrict__ u_out, int* __restrict__ err, int TY) {
     constexpr bool IBM = MODE == 1;
     extern __shared__ float ring[];                      // psi [4][2][RR][nx], then moments [2][5][RR][nx]
@@ -473,7 +473,7 @@ k_bulk4(LbmParams p, const T* __restrict__ S, T* __restrict__ D, float* __restri
                 if (IBM && ((bits >> k) & 1u)) {
 #pragma unroll
                     for (int d = 0; d < 3; d++) {
-                        const float fi = Fibm[(size_t)d * p.N + n0 + k];
+                        const float fi = ibm_unfix(Fibm[(size_t)d * p.N + n0 + k]);
                         FA[d] += ra[k] * irt * fi;
                         FB[d] += rb[k] * irt * fi;
                     }
@@ -655,7 +655,7 @@ static bool bulk4_geometry(const LbmParams& p, int nthreads, int cps, int min_pl
 
 template <bool TAU1, int MODE, int NT, int MINB, typename T>
 static void launch_b4t(const LbmParams& q, dim3 grid, int threads, size_t smem, int TY, const T* S, T* D,
-                       float* rho, const float* ghost, const float* Fibm, const uint32_t* mask, float* u, int* err,
+                       float* rho, const float* ghost, const IbmF* Fibm, const uint32_t* mask, float* u, int* err,
                        cudaStream_t st) {
     static size_t attr = 0;
     if (smem > attr) {
@@ -669,7 +669,7 @@ static void launch_b4t(const LbmParams& q, dim3 grid, int threads, size_t smem, 
 // S, D point to populations of the type q.store names
 template <bool TAU1, int MODE, int NT, int MINB>
 static void launch_b4(const LbmParams& q, dim3 grid, int threads, size_t smem, int TY, const float* S, float* D,
-                      float* rho, const float* ghost, const float* Fibm, const uint32_t* mask, float* u, int* err,
+                      float* rho, const float* ghost, const IbmF* Fibm, const uint32_t* mask, float* u, int* err,
                       cudaStream_t st) {
     with_storage(q.store, [&](auto* tag) {
         using T = std::remove_pointer_t<decltype(tag)>;
@@ -680,7 +680,7 @@ static void launch_b4(const LbmParams& q, dim3 grid, int threads, size_t smem, i
 
 template <int NT, int MINB>
 static bool try_b4(const LbmParams& p, int min_planes, const float* S, float* D, float* rho, const float* ghost,
-                   const float* Fibm, const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st,
+                   const IbmF* Fibm, const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st,
                    int* blocks) {
     LbmParams q;
     dim3 grid;
@@ -705,7 +705,7 @@ static bool try_b4(const LbmParams& p, int min_planes, const float* S, float* D,
 }
 
 static bool dispatch_b4(const LbmParams& p, const float* S, float* D, float* rho, const float* ghost,
-                        const float* Fibm, const uint32_t* mask, float* u, int* err, int mode,
+                        const IbmF* Fibm, const uint32_t* mask, float* u, int* err, int mode,
                         cudaStream_t st, int* blocks) {
     switch (p.b4cfg) {
         case 1: return try_b4<256, 2>(p, 6, S, D, rho, ghost, Fibm, mask, u, err, mode, st, blocks);
@@ -736,7 +736,7 @@ int bulk_grid_blocks(const LbmParams& p) {
     return (int)(g.x * g.y * g.z);
 }
 
-void launch_bulk(const LbmParams& p, const float* S, float* D, float* rho, float* J, float* ghost, const float* Fibm,
+void launch_bulk(const LbmParams& p, const float* S, float* D, float* rho, float* J, float* ghost, const IbmF* Fibm,
                  const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st) {
     const bool ibm = mode == 1;
     if (J && bulk_split(p)) {

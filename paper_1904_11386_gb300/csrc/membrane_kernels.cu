@@ -351,6 +351,9 @@ __device__ __forceinline__ Stencil hat_stencil(const LbmParams& p, float4 X) {
     return s;
 }
 
+// Spreading (Eq. 9 forces onto the lattice): the vertices' contributions w F are summed into the fixed-point
+// force field (ibm_fix: integer atomics, so the sums do not depend on the order the atomics land in), and the
+// nodes they reach are marked.
 __global__ void k_ibm_spread(LbmParams p, DevState d) {
     pdl_wait();
     pdl_trigger();
@@ -362,9 +365,9 @@ __global__ void k_ibm_spread(LbmParams p, DevState d) {
     for (int q = 0; q < 8; q++) {
         if (!s.fluid[q]) continue;
         const unsigned int n = s.node[q];
-        atomicAdd(d.Fibm + n, s.w[q] * F.x);
-        atomicAdd(d.Fibm + (size_t)p.N + n, s.w[q] * F.y);
-        atomicAdd(d.Fibm + 2 * (size_t)p.N + n, s.w[q] * F.z);
+        atomicAdd(d.Fibm + n, ibm_fix(s.w[q] * F.x));
+        atomicAdd(d.Fibm + (size_t)p.N + n, ibm_fix(s.w[q] * F.y));
+        atomicAdd(d.Fibm + 2 * (size_t)p.N + n, ibm_fix(s.w[q] * F.z));
         atomicOr(d.mask + (n >> 5), 1u << (n & 31));
     }
 }
@@ -387,9 +390,7 @@ __global__ void k_ibm_interp(LbmParams p, DevState d) {
             U[0] += s.w[q] * d.u[n];
             U[1] += s.w[q] * d.u[(size_t)p.N + n];
             U[2] += s.w[q] * d.u[2 * (size_t)p.N + n];
-            d.Fibm[n] = 0.f;
-            d.Fibm[(size_t)p.N + n] = 0.f;
-            d.Fibm[2 * (size_t)p.N + n] = 0.f;
+            for (int k = 0; k < 3; k++) d.Fibm[(size_t)k * p.N + n] = 0ull;
             d.mask[n >> 5] = 0u;
         } else if (p.walls && (s.zc[q] == 0 || s.zc[q] == p.nz - 1)) {
             const float* Uw = s.zc[q] == 0 ? p.ulo : p.uhi;
@@ -401,9 +402,10 @@ __global__ void k_ibm_interp(LbmParams p, DevState d) {
     d.V[v] = make_float4(U[0], U[1], U[2], 0.f);
 }
 
-void launch_ibm_spread(const LbmParams& p, const DevState& d, cudaStream_t st) {
-    if (d.NV == 0) return;
+int launch_ibm_spread(const LbmParams& p, const DevState& d, cudaStream_t st) {
+    if (d.NV == 0) return 0;
     launch_k(k_ibm_spread, dim3((d.NV + 127) / 128), dim3(128), 0, st, p, d);
+    return 1;
 }
 
 void launch_ibm_interp(const LbmParams& p, const DevState& d, cudaStream_t st) {

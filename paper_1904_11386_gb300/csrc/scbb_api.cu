@@ -227,7 +227,7 @@ size_t layout(const scbb_lattice* lat, const scbb_fluid* fl, int nm, const scbb_
     t.J = c.take<float>(3 * N);
     const bool ibm = fl->coupling == 1 && NV > 0;
     t.u = ibm ? c.take<float>(3 * N) : nullptr;
-    t.Fibm = ibm ? c.take<float>(3 * N) : nullptr;
+    t.Fibm = ibm ? c.take<IbmF>(3 * N) : nullptr;
     t.mask = ibm ? c.take<uint32_t>((N + 31) / 32) : nullptr;
     t.wall_rho = c.take<float>(4 * nxy);
     t.ghost = c.take<float>(4 * nxy);
@@ -485,7 +485,7 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
     CUDA_TRY(c, cudaMemsetAsync(d.S[1], 0, pop_bytes, c->st));
     CUDA_TRY(c, cudaMemsetAsync(d.rho, 0, sizeof(float) * 2 * N, c->st));
     if (d.Fibm) {
-        CUDA_TRY(c, cudaMemsetAsync(d.Fibm, 0, sizeof(float) * 3 * N, c->st));
+        CUDA_TRY(c, cudaMemsetAsync(d.Fibm, 0, sizeof(IbmF) * 3 * N, c->st));
         CUDA_TRY(c, cudaMemsetAsync(d.u, 0, sizeof(float) * 3 * N, c->st));
         CUDA_TRY(c, cudaMemsetAsync(d.mask, 0, sizeof(uint32_t) * ((N + 31) / 32), c->st));
     }
@@ -543,7 +543,7 @@ scbb_status scbb_set_density(scbb_ctx* c, const double* rhoA, const double* rhoB
         CUDA_TRY(c, cudaMemsetAsync(c->d.F, 0, sizeof(float4) * c->d.NV, c->st));
     }
     if (c->d.Fibm) {
-        CUDA_TRY(c, cudaMemsetAsync(c->d.Fibm, 0, sizeof(float) * 3 * N, c->st));
+        CUDA_TRY(c, cudaMemsetAsync(c->d.Fibm, 0, sizeof(IbmF) * 3 * N, c->st));
         CUDA_TRY(c, cudaMemsetAsync(c->d.mask, 0, sizeof(uint32_t) * ((N + 31) / 32), c->st));
     }
     if (c->d.owner) {
@@ -627,8 +627,7 @@ static void enqueue_pre(scbb_ctx* c, const StepPlan& s) {
     if (s.ibm) {
         // membrane forces at X(t), spread onto the lattice (2-point immersed boundary)
         c->launches += launch_membrane_forces(c->lp, c->d, false, s.step, c->st);
-        launch_ibm_spread(c->lp, c->d, c->st);
-        c->launches += 1;
+        c->launches += launch_ibm_spread(c->lp, c->d, c->st);
     }
     c->mark(1);
     if (s.ghost_pass) {
@@ -1521,8 +1520,7 @@ static scbb_status adjoint_backward_core(scbb_adjoint* a, const double* gA, cons
                                     c->st));
                 const DevState dk = slot(k);
                 c->launches += launch_membrane_forces(c->lp, dk, false, 0, c->st);
-                launch_ibm_spread(c->lp, dk, c->st);
-                c->launches++;
+                c->launches += launch_ibm_spread(c->lp, dk, c->st);
             }
             if (c->lp.walls && !bulk_writes_ghost(c->lp))
                 launch_wall_ghost(c->lp, a->L + (size_t)k * lat, c->d.wall_rho, gh, c->st);
@@ -1541,9 +1539,9 @@ static scbb_status adjoint_backward_core(scbb_adjoint* a, const double* gA, cons
                 // the step's spread force at X(t) from its stored node forces, and the interpolation transposed
                 chk(cudaMemcpyAsync(c->d.X, a->Xs + (size_t)k * NV, sizeof(float4) * NV, cudaMemcpyDeviceToDevice,
                                     c->st));
-                launch_ibm_spread(c->lp, dk, c->st);
+                c->launches += launch_ibm_spread(c->lp, dk, c->st);
                 launch_cap_adj_spread(c->lp, dk, a->cap, c->st);
-                c->launches += 2;
+                c->launches += 1;
             }
             launch_adj_step(c->lp, a->L + (size_t)k * lat, a->R + (size_t)k * 2 * N, gh, a->lam[cu], a->lam[1 - cu],
                             a->scr, a->gw, a->part, c->st, a->ibm ? &ib : nullptr);

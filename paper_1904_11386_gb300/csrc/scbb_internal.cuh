@@ -38,6 +38,15 @@ __host__ __device__ constexpr float dir_w(int i) {
     return i == 0 ? (1.0f / 3.0f) : (i <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f));
 }
 
+// Spread force of the immersed boundary: 64-bit fixed point in units of 2^-40.  The spreading sums the vertices'
+// contributions with integer atomics, which are associative, so the sums (and the step) are the same bits in
+// whatever order the atomics land; |values| < 2^23.
+// (Both conversions stay in FP32: scaling by a power of two is exact, and the integer <-> float conversions
+// round once.)
+typedef unsigned long long IbmF;
+__device__ __forceinline__ IbmF ibm_fix(float v) { return (IbmF)__float2ll_rn(v * 0x1p40f); }
+__device__ __forceinline__ float ibm_unfix(IbmF v) { return __ll2float_rn((long long)v) * 0x1p-40f; }
+
 // Lattice / fluid parameters passed by value to the fluid kernels.
 struct LbmParams {
     int nx, ny, nz, nxy;
@@ -163,7 +172,7 @@ struct DevState {
     float* rho;             // [2][N] densities of the last collision
     float* J;               // [3][N] momentum of the last stream (two-kernel bulk phase)
     float* u;               // [3][N] velocity incl. half force, written where the IBM mask is set
-    float* Fibm;            // [3][N] spread immersed-boundary force density
+    IbmF* Fibm;             // [3][N] immersed boundary: spread force, fixed-point sums (ibm_fix)
     uint32_t* mask;         // [ceil(N/32)] IBM stencil bits
     float* wall_rho;        // [2 walls][2 comp][nxy] densities of the planes next to the walls
     float* ghost;           // [2 walls][2 comp][nxy] virtual densities of the wall planes
@@ -322,7 +331,7 @@ void launch_wall_ghost(const LbmParams& p, const float* S, float* wall_rho, floa
 // J: [3][N] momentum scratch of the two-kernel bulk phase (tau = 1), which also writes the wall ghost
 // densities itself (bulk_writes_ghost); with J null the fused kernels run
 void launch_bulk(const LbmParams& p, const float* S, float* D, float* rho, float* J, float* ghost,
-                 const float* Fibm, const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st);
+                 const IbmF* Fibm, const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st);
 // true when the bounce-back coupling can run on this lattice: the two-kernel bulk phase or the fused
 // row-vectorised kernel (both store every node of the lattice whole)
 bool bulk_vectorised(const LbmParams& p);
@@ -333,7 +342,7 @@ int bulk_variant();
 bool bulk_split(const LbmParams& p);
 int split_grid_blocks(const LbmParams& p);
 void launch_split(const LbmParams& p, const float* S, float* D, float* rho, float* J, float* ghost,
-                  const float* Fibm, const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st);
+                  const IbmF* Fibm, const uint32_t* mask, float* u, int* err, int mode, cudaStream_t st);
 
 // Bulk phase of a batch of boxes in one cooperative launch (kernel parameters carry every box).
 constexpr int BATCH_MAX = 64;
@@ -345,7 +354,7 @@ struct BatchBox {
     float* rho;
     float* J;
     float* ghost;
-    const float* Fibm;
+    const IbmF* Fibm;
     const uint32_t* mask;
     float* u;
     int* err;
@@ -373,7 +382,7 @@ int bulk_grid_blocks(const LbmParams& p);
 void launch_capsule_reduce(const DevState& d, cudaStream_t st);
 // returns the number of kernels launched
 int launch_membrane_forces(const LbmParams& p, const DevState& d, bool bb, int step, cudaStream_t st);
-void launch_ibm_spread(const LbmParams& p, const DevState& d, cudaStream_t st);
+int launch_ibm_spread(const LbmParams& p, const DevState& d, cudaStream_t st);
 void launch_ibm_interp(const LbmParams& p, const DevState& d, cudaStream_t st);
 int launch_pp_forces(const LbmParams& p, const DevState& d, float eps, float d0, cudaStream_t st);
 
