@@ -5,7 +5,10 @@ The staged kernels move the same values through shared memory and run the same c
 run with them equals a run without them (SCBB_BULK_STAGED=0, in a child process: the switches are read once per
 process) bit for bit: FP32 and FP16 storage, walls and periodic z, the immersed-boundary mode.  So does kernel
 B's pair form (two threads per quad, one per component; the default) against its quad form (SCBB_BULK_PAIR=0)
-in every block shape of the quad form (the ring and stage layout depend on it).  A wait limit of 0 makes the
+in every block shape of the quad form (the ring and stage layout depend on it).  The single fused kernels
+(SCBB_BULK_VARIANT=4: the first build's row-vectorised kernel; 2: the general kernel, two lattices) give the
+same step to FP32 rounding (1e-5 of the largest population; the immersed boundary's coupled steps carry a few ulps
+of the different summation orders).  A wait limit of 0 makes the
 waits give up: the next synchronising call reports SCBB_E_TIMEOUT, later calls SCBB_E_STATE, and a saved
 state restores the context, which then steps like a fresh one."""
 import os
@@ -82,6 +85,16 @@ def test_pair_form_equals_quad_form_in_every_shape(name, tmp_path):
     for shape in ("0", "1", "2", "3"):
         ref = _run_child(src, steps, tmp_path, SCBB_BULK_PAIR="0", SCBB_BULK_SHAPE=shape)
         assert np.array_equal(f, ref), (shape, np.abs(f - ref).max())
+
+
+@pytest.mark.parametrize("name", ["walls64", "ibm64"])
+def test_fused_kernels_agree(name, tmp_path):
+    src, steps = CASES[name]
+    f = _run_here(src, steps)
+    scale = np.abs(f).max()
+    for variant in ("4", "2"):
+        ref = _run_child(src, steps, tmp_path, SCBB_BULK_VARIANT=variant)
+        assert np.abs(f - ref).max() < 1e-5 * scale, (variant, np.abs(f - ref).max())
 
 
 def test_staged_wait_timeout_and_recovery():
