@@ -28,7 +28,7 @@ from paper_1904_11386_gb300 import inputs  # noqa: E402
 # the neighbours' densities of the same time level): 320 B, or 168 B with 16-bit populations.
 BYTES_PER_LU = 2 * 19 * 4 * 2 + 2 * 4 + 2 * 4
 BYTES_PER_LU_16 = 2 * 19 * 2 * 2 + 2 * 4 + 2 * 4
-STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
+STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2, "fp16dev": 3, "bf16dev": 4}
 # error against the FP64 oracle of each 16-bit storage, as the tests bound it
 STORAGE_ERROR = {
     "fp16": ("densities 1.3e-3, velocities 2.2e-3 of max|u|, vertices 2.5e-3 after 200 steps (32^3); mass offset "
@@ -644,7 +644,7 @@ def main():
            "config": {"workload": label, "lattice": [prob.nx, prob.ny, prob.nz], "nodes": N,
                       "vertices": int(sum(sim.nv)), "parallelism": f"replicas x{ws}",
                       "storage": args.storage,
-                      "l2": f"inputs larger than L2 (populations 2 x {2 * 19 * N * (4 if args.storage == 'fp32' else 2) / 1e6:.0f} MB)"},
+                      "l2": f"inputs larger than L2 (populations {2 * 19 * N * (4 if args.storage == 'fp32' else 2) / 1e6:.0f} MB a lattice)"},
            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
     nv = int(sum(sim.nv))
     if nv:

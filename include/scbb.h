@@ -77,7 +77,9 @@ typedef struct {
  *   pp_eps, pp_d0         particle-particle repulsion (Eq. 26, Sec. III.E), 0.5 and 1.25 in the paper
  *   storage   0: FP32 populations; 1: populations stored as IEEE FP16, 2: as BF16 (arithmetic stays FP32;
  *             each stored value is rounded to nearest even, at most 2^-12 relative for FP16 and 2^-9 for
- *             BF16), half the population bytes.  Not in the paper.
+ *             BF16), half the population bytes; 3 / 4: the deviations f_i^c - w_i rho_ref stored as FP16 / BF16,
+ *             with rho_ref = (rho_maj + rho_min) / 2 for both components (the rounding is then relative to the
+ *             deviation; two-kernel bulk phase only, tau = 1).  Not in the paper.
  *   max_boundary  capacity of the bounce-back boundary-node list (nodes with a membrane-cut link); 0 sizes it
  *             from the membrane areas (three node layers per unit area, 50 % margin, + 4096).  The fresh-node
  *             list holds max_boundary / 2 + 1024.  A list that overflows keeps its first entries, skips the
@@ -113,7 +115,7 @@ typedef struct {
 } scbb_mesh;
 
 /* Bytes of device workspace a context with this description needs (0 on invalid input).  The populations take
- * one lattice of 2 * 19 * N values (FP32, or 16-bit with storage 1 or 2), updated in place by the two-kernel
+ * one lattice of 2 * 19 * N values (FP32, or 16-bit with storage 1 to 4), updated in place by the two-kernel
  * bulk phase, plus 5 N doubles of staging for the host's fields; a context with bounce-back membranes, or one
  * whose bulk phase is a fused kernel (tau != 1, or rows too long for the two-kernel phase), takes two lattices
  * (read one, write the other), the spare one staging the fields. */

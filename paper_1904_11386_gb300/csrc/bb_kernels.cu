@@ -629,8 +629,8 @@ __device__ __forceinline__ float2 boundary_node(const LbmParams& p, const DevSta
         int zs = z - cz;
         if (!p.walls) zs = wrapf(zs, p.nz);
         const unsigned int src = (unsigned)wrapf(x - cx, p.nx) + (unsigned)wrapf(y - cy, p.ny) * p.nx + (unsigned)zs * p.nxy;
-        fa = pld(S + (size_t)i * p.N + src);
-        fb = pld(S + (size_t)(Q + i) * p.N + src);
+        fa = pld(S + (size_t)i * p.N + src) + wi * dev_ref<T>(p, 0);      // + the reference of a deviation storage
+        fb = pld(S + (size_t)(Q + i) * p.N + src) + wi * dev_ref<T>(p, 1);
     }
     const float ra = wsum(fa), rb = wsum(fb);
     const float jx = wsum(cx * (fa + fb)), jy = wsum(cy * (fa + fb)), jz = wsum(cz * (fa + fb));
@@ -719,21 +719,22 @@ __device__ __forceinline__ float2 boundary_node(const LbmParams& p, const DevSta
     const float sA = wsum(eA), sB = wsum(eB);
     if (lane == 0) { eA = ra - sA; eB = rb - sB; }
     const float oA = fa + p.omega * (eA - fa), oB = fb + p.omega * (eB - fb);
-    // ---- streaming
+    // ---- streaming (a deviation storage keeps f - w rref; opposite directions share their weight)
     float dm[2] = {0.f, 0.f};
+    const float gA = wi * dev_ref<T>(p, 0), gB = wi * dev_ref<T>(p, 1);
     if (dl) {
         if (lane == 0) {
-            pst(D + n, oA);
-            pst(D + (size_t)Q * p.N + n, oB);
+            pst(D + n, oA - gA);
+            pst(D + (size_t)Q * p.N + n, oB - gB);
         } else if (wall) {
             const float* U = zn == 0 ? p.ulo : p.uhi;
             const float cU = 6.f * wi * (cx * U[0] + cy * U[1] + cz * U[2]);
             const unsigned int tgt = (unsigned)(wrapf(x + cx, p.nx) + wrapf(y + cy, p.ny) * p.nx) + (unsigned)zn * p.nxy;
-            pst(D + (size_t)dir_opp(i) * p.N + tgt, oA - cU * ra);
-            pst(D + (size_t)(Q + dir_opp(i)) * p.N + tgt, oB - cU * rb);
+            pst(D + (size_t)dir_opp(i) * p.N + tgt, oA - cU * ra - gA);
+            pst(D + (size_t)(Q + dir_opp(i)) * p.N + tgt, oB - cU * rb - gB);
         } else if (om == me || e < 0) {
-            pst(D + (size_t)i * p.N + n, oA);
-            pst(D + (size_t)(Q + i) * p.N + n, oB);
+            pst(D + (size_t)i * p.N + n, oA - gA);
+            pst(D + (size_t)(Q + i) * p.N + n, oB - gB);
         } else {
             // moving half-way bounce-back (Eq. 11) with the element velocity; exchanged momentum (Eq. 12)
             const int4 T = d.tri[e];
@@ -742,8 +743,8 @@ __device__ __forceinline__ float2 boundary_node(const LbmParams& p, const DevSta
                         vz = (V0.z + V1.z + V2.z) * (1.f / 3.f);
             const float cv = 6.f * wi * (cx * vx + cy * vy + cz * vz);
             const float bA = oA - cv * ra, bB = oB - cv * rb;
-            pst(D + (size_t)dir_opp(i) * p.N + m, bA);
-            pst(D + (size_t)(Q + dir_opp(i)) * p.N + m, bB);
+            pst(D + (size_t)dir_opp(i) * p.N + m, bA - gA);
+            pst(D + (size_t)(Q + dir_opp(i)) * p.N + m, bB - gB);
             const float dp = oA + bA + oB + bB;
             atomicAdd(&d.emom[pr * d.NT + e], make_float4(dp * cx, dp * cy, dp * cz, 0.f));
             dm[0] = bA - oA;
@@ -1020,14 +1021,16 @@ __device__ __forceinline__ void fresh_apply_node(const LbmParams& p, const DevSt
         const float e0 = dir_w(i) * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
         T* sa = S + (size_t)i * p.N + m;
         T* sb = S + (size_t)(Q + i) * p.N + m;
-        const float oa = pldc(sa), ob = pldc(sb);
+        // a deviation storage keeps f - w_i rref^c: the reference is added on the load and taken off the store
+        const float ga = dir_w(i) * dev_ref<T>(p, 0), gb = dir_w(i) * dev_ref<T>(p, 1);
+        const float oa = pldc(sa) + ga, ob = pldc(sb) + gb;
         const float old = oa + ob;
         rem[0] += dir_x(i) * old; rem[1] += dir_y(i) * old; rem[2] += dir_z(i) * old;
-        const float na = pround(e0 * a.x, S), nb = pround(e0 * a.y, S);
-        dA += na - oa;
-        dB += nb - ob;
-        pst(sa, na);
-        pst(sb, nb);
+        const float sna = pround(e0 * a.x - ga, S), snb = pround(e0 * a.y - gb, S);
+        dA += (sna + ga) - oa;
+        dB += (snb + gb) - ob;
+        pst(sa, sna);
+        pst(sb, snb);
     }
     d.fdm[q] = make_float2(dA, dB);
     const float rt = a.x + a.y;

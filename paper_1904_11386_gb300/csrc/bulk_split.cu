@@ -293,8 +293,15 @@ __device__ __forceinline__ void collide1_tile(const LbmParams& p, T* __restrict_
                 const float qA = cdot<I>(vA[0], vA[1], vA[2]), qB = cdot<I>(vB[0], vB[1], vB[2]);
                 const float hA = fmaf(0.5f * qA, qA, aA), hB = fmaf(0.5f * qB, qB, aB);
                 const float wA = W * ra, wB = W * rb;
-                const float oA = pround(wA * (hA + qA), D), oB = pround(wB * (hB + qB), D);
-                const float pA = pround(wA * (hA - qA), D), pB = pround(wB * (hB - qB), D);
+                float oA, oB, pA, pB;
+                if constexpr (is_dev<T>::value) {      // deviations from W rref^c
+                    const float dA = W * p.rref[0], dB = W * p.rref[1];
+                    oA = pround(wA * (hA + qA) - dA, D); oB = pround(wB * (hB + qB) - dB, D);
+                    pA = pround(wA * (hA - qA) - dA, D); pB = pround(wB * (hB - qB) - dB, D);
+                } else {
+                    oA = pround(wA * (hA + qA), D); oB = pround(wB * (hB + qB), D);
+                    pA = pround(wA * (hA - qA), D); pB = pround(wB * (hB - qB), D);
+                }
                 sA += oA + pA;
                 sB += oB + pB;
                 store_dir(std::integral_constant<int, I>{}, oA, oB);
@@ -305,7 +312,7 @@ __device__ __forceinline__ void collide1_tile(const LbmParams& p, T* __restrict_
             emit_pair(std::integral_constant<int, 9>{});  emit_pair(std::integral_constant<int, 11>{});
             emit_pair(std::integral_constant<int, 13>{}); emit_pair(std::integral_constant<int, 15>{});
             emit_pair(std::integral_constant<int, 17>{});
-            float oA = ra - sA, oB = rb - sB;
+            float oA = (ra - dev_ref<T>(p, 0)) - sA, oB = (rb - dev_ref<T>(p, 1)) - sB;
             if (sizeof(T) == 2) {           // unbiased rounding of the mass-closing value
                 const uint32_t h = dither_bits(n0, ra, rb);
                 oA = pdither(oA, h >> 16, D);
@@ -448,10 +455,18 @@ __device__ __forceinline__ void collide4_plane(const LbmParams& p, T* __restrict
             const float qB = cdot<I>(vB[k][0], vB[k][1], vB[k][2]);
             const float hA = fmaf(0.5f * qA, qA, aA[k]), hB = fmaf(0.5f * qB, qB, aB[k]);
             const float wA = W * ra[k], wB = W * rb[k];
-            oA[k] = pround(wA * (hA + qA), D);
-            oB[k] = pround(wB * (hB + qB), D);
-            qA4[k] = pround(wA * (hA - qA), D);
-            qB4[k] = pround(wB * (hB - qB), D);
+            if constexpr (is_dev<T>::value) {          // deviations from W rref^c
+                const float dA = W * p.rref[0], dB = W * p.rref[1];
+                oA[k] = pround(wA * (hA + qA) - dA, D);
+                oB[k] = pround(wB * (hB + qB) - dB, D);
+                qA4[k] = pround(wA * (hA - qA) - dA, D);
+                qB4[k] = pround(wB * (hB - qB) - dB, D);
+            } else {
+                oA[k] = pround(wA * (hA + qA), D);
+                oB[k] = pround(wB * (hB + qB), D);
+                qA4[k] = pround(wA * (hA - qA), D);
+                qB4[k] = pround(wB * (hB - qB), D);
+            }
             sA[k] += oA[k] + qA4[k];
             sB[k] += oB[k] + qB4[k];
         }
@@ -468,8 +483,8 @@ __device__ __forceinline__ void collide4_plane(const LbmParams& p, T* __restrict
         float oA[4], oB[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            oA[k] = ra[k] - sA[k];
-            oB[k] = rb[k] - sB[k];
+            oA[k] = (ra[k] - dev_ref<T>(p, 0)) - sA[k];
+            oB[k] = (rb[k] - dev_ref<T>(p, 1)) - sB[k];
             if (sizeof(T) == 2) {       // unbiased rounding of the mass-closing value
                 const uint32_t h = dither_bits(n0 + k, ra[k], rb[k]);
                 oA[k] = pdither(oA[k], h >> 16, D);
@@ -624,6 +639,10 @@ __device__ __forceinline__ float4 sld4(const __nv_bfloat16* p) {
     const float2 a = __bfloat1622float2(h[0]), b = __bfloat1622float2(h[1]);
     return make_float4(a.x, a.y, b.x, b.y);
 }
+__device__ __forceinline__ float sld(const DevH* p) { return sld(raw16(p)); }
+__device__ __forceinline__ float sld(const DevB* p) { return sld(raw16(p)); }
+__device__ __forceinline__ float4 sld4(const DevH* p) { return sld4(raw16(p)); }
+__device__ __forceinline__ float4 sld4(const DevB* p) { return sld4(raw16(p)); }
 
 // the values direction I brings to the nodes x .. x+3 from a whole source row in shared memory (periodic in x)
 template <int I, typename T>
@@ -635,9 +654,16 @@ __device__ __forceinline__ float4 srow4(const T* row, int x, int nx) {
 }
 
 template <typename T, int I, int... Rest>
-__device__ __forceinline__ void srow_all(const T* stage, int x, int nx, Mom4& m, DirList<I, Rest...>) {
-    acc_dir<I>(m, srow4<I, T>(stage + (size_t)I * nx, x, nx), srow4<I, T>(stage + (size_t)(Q + I) * nx, x, nx));
-    if constexpr (sizeof...(Rest) > 0) srow_all<T>(stage, x, nx, m, DirList<Rest...>{});
+__device__ __forceinline__ void srow_all(const LbmParams& p, const T* stage, int x, int nx, Mom4& m,
+                                         DirList<I, Rest...>) {
+    float4 a = srow4<I, T>(stage + (size_t)I * nx, x, nx), b = srow4<I, T>(stage + (size_t)(Q + I) * nx, x, nx);
+    if constexpr (is_dev<T>::value) {                  // deviation storage: add the reference back
+        const float ra = dir_w(I) * p.rref[0], rb = dir_w(I) * p.rref[1];
+        a = make_float4(a.x + ra, a.y + ra, a.z + ra, a.w + ra);
+        b = make_float4(b.x + rb, b.y + rb, b.z + rb, b.w + rb);
+    }
+    acc_dir<I>(m, a, b);
+    if constexpr (sizeof...(Rest) > 0) srow_all<T>(p, stage, x, nx, m, DirList<Rest...>{});
 }
 
 constexpr long long DRAIN_POLLS = 1LL << 22;     // bounded wait for the copies in flight after a give-up
@@ -711,7 +737,7 @@ __global__ void __launch_bounds__(256) k_moments_staged(LbmParams p, const T* __
             Mom4 m;
 #pragma unroll
             for (int k = 0; k < 4; k++) m.ra[k] = m.rb[k] = m.jx[k] = m.jy[k] = m.jz[k] = 0.f;
-            srow_all<T>(sb, x, nx, m, AllDirs{});
+            srow_all<T>(p, sb, x, nx, m, AllDirs{});
             const unsigned int n0 = (unsigned)x + (unsigned)y * nx + (unsigned)z * p.nxy;
             *reinterpret_cast<float4*>(rho + n0) = make_float4(m.ra[0], m.ra[1], m.ra[2], m.ra[3]);
             *reinterpret_cast<float4*>(rho + p.N + n0) = make_float4(m.rb[0], m.rb[1], m.rb[2], m.rb[3]);
@@ -1066,8 +1092,14 @@ __device__ __forceinline__ void collide4_half(const LbmParams& p, T* __restrict_
             const float qv = cdot<I>(v[k][0], v[k][1], v[k][2]);
             const float h = fmaf(0.5f * qv, qv, a[k]);
             const float w = W * rc[k];
-            o[k] = pround(w * (h + qv), D);
-            om[k] = pround(w * (h - qv), D);
+            if constexpr (is_dev<T>::value) {          // deviations from W rref^c
+                const float dc = W * p.rref[c];
+                o[k] = pround(w * (h + qv) - dc, D);
+                om[k] = pround(w * (h - qv) - dc, D);
+            } else {
+                o[k] = pround(w * (h + qv), D);
+                om[k] = pround(w * (h - qv), D);
+            }
             sc[k] += o[k] + om[k];
         }
         store_dir(std::integral_constant<int, I>{}, o);
@@ -1081,7 +1113,7 @@ __device__ __forceinline__ void collide4_half(const LbmParams& p, T* __restrict_
     float o[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        o[k] = rc[k] - sc[k];
+        o[k] = (rc[k] - dev_ref<T>(p, c)) - sc[k];
         if (sizeof(T) == 2) {
             const uint32_t h = dither_bits(n0 + k, ra[k], rb[k]);
             o[k] = pdither(o[k], c == 0 ? h >> 16 : h & 0xffffu, D);

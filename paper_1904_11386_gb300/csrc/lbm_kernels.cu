@@ -44,7 +44,8 @@ __global__ void k_init_state(LbmParams p, T* __restrict__ S, const TI* __restric
     for (int i = 1; i < Q; i++) {
         const float cu = dir_x(i) * ux + dir_y(i) * uy + dir_z(i) * uz;
         const float e = dir_w(i) * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
-        const float va = pround(e * a, S), vb = pround(e * b, S);
+        // a deviation storage keeps e rho - w_i rref^c (e carries w_i)
+        const float va = pround(e * a - dir_w(i) * dev_ref<T>(p, 0), S), vb = pround(e * b - dir_w(i) * dev_ref<T>(p, 1), S);
         sa += va;
         sb += vb;
         int zs = z - dir_z(i);
@@ -54,8 +55,8 @@ __global__ void k_init_state(LbmParams p, T* __restrict__ S, const TI* __restric
         pst(S + (size_t)(Q + i) * p.N + m, vb);
     }
     const uint32_t h = dither_bits(n, a, b);
-    pst(S + n, pdither(a - sa, h >> 16, S));
-    pst(S + (size_t)Q * p.N + n, pdither(b - sb, h & 0xffffu, S));
+    pst(S + n, pdither((a - dev_ref<T>(p, 0)) - sa, h >> 16, S));
+    pst(S + (size_t)Q * p.N + n, pdither((b - dev_ref<T>(p, 1)) - sb, h & 0xffffu, S));
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -671,7 +672,7 @@ template <bool TAU1, int MODE, int NT, int MINB>
 static void launch_b4(const LbmParams& q, dim3 grid, int threads, size_t smem, int TY, const float* S, float* D,
                       float* rho, const float* ghost, const IbmF* Fibm, const uint32_t* mask, float* u, int* err,
                       cudaStream_t st) {
-    with_storage(q.store, [&](auto* tag) {
+    with_plain_storage(q.store, [&](auto* tag) {
         using T = std::remove_pointer_t<decltype(tag)>;
         launch_b4t<TAU1, MODE, NT, MINB, T>(q, grid, threads, smem, TY, reinterpret_cast<const T*>(S),
                                             reinterpret_cast<T*>(D), rho, ghost, Fibm, mask, u, err, st);
@@ -775,7 +776,7 @@ void launch_init_state(const LbmParams& p, float* S, const double* rho_st, const
 }
 
 void launch_wall_ghost(const LbmParams& p, const float* S, float* wall_rho, float* ghost, cudaStream_t st) {
-    with_storage(p.store, [&](auto* tag) {
+    with_plain_storage(p.store, [&](auto* tag) {
         using T = std::remove_pointer_t<decltype(tag)>;
         k_wall_planes_rho<T><<<(2 * p.nxy + 255) / 256, 256, 0, st>>>(p, reinterpret_cast<const T*>(S), wall_rho);
     });

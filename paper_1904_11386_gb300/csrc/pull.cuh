@@ -57,8 +57,13 @@ template <int I, typename T>
 __device__ __forceinline__ void pull_dir(const LbmParams& p, const T* __restrict__ S, const PullCtx& pc, int x,
                                          int segl, int W, int edge, Mom4& m) {
     const unsigned int srow = pc.rows[1 - dir_y(I)][1 - dir_z(I)];
-    const float4 a = pull4<I, T>(p, S, srow, x, segl, W, edge, 0xffffffffu);
-    const float4 b = pull4<I, T>(p, S + (size_t)Q * p.N, srow, x, segl, W, edge, 0xffffffffu);
+    float4 a = pull4<I, T>(p, S, srow, x, segl, W, edge, 0xffffffffu);
+    float4 b = pull4<I, T>(p, S + (size_t)Q * p.N, srow, x, segl, W, edge, 0xffffffffu);
+    if constexpr (is_dev<T>::value) {                  // deviation storage: add the reference back
+        const float ra = dir_w(I) * p.rref[0], rb = dir_w(I) * p.rref[1];
+        a = make_float4(a.x + ra, a.y + ra, a.z + ra, a.w + ra);
+        b = make_float4(b.x + rb, b.y + rb, b.z + rb, b.w + rb);
+    }
     acc_dir<I>(m, a, b);
 }
 

@@ -108,7 +108,7 @@ bool valid_fluid(const scbb_fluid* f) {
     if (!f || !(f->tau > 0.5) || !isfinite(f->G)) return false;
     if (f->psi_kind != 0 && f->psi_kind != 1) return false;
     if (f->coupling != 0 && f->coupling != 1) return false;
-    if (f->storage < 0 || f->storage > 2) return false;
+    if (f->storage < 0 || f->storage > 4) return false;
     if (f->max_boundary < 0) return false;
     if (f->pp_eps != 0.0 && !(f->pp_d0 > 0.0)) return false;
     return true;
@@ -133,6 +133,9 @@ LbmParams make_params(const scbb_lattice* lat, const scbb_fluid* fl) {
     p.G = (float)fl->G;
     p.psi_kind = fl->psi_kind;
     p.store = fl->storage;
+    // deviation storages: the reference of each component is the middle of its two phase densities
+    const float rref = fl->storage >= 3 ? (float)(0.5 * (fl->rho_maj + fl->rho_min)) : 0.f;
+    p.rref[0] = p.rref[1] = rref;
     for (int k = 0; k < 3; k++) {
         p.g[k] = (float)fl->g[k];
         p.ulo[k] = (float)lat->u_lo[k];
@@ -362,6 +365,8 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
         LbmParams lp = make_params(lat, fl);
         if (!bulk_split(lp) || (fl->coupling == 0 && n_mesh > 0)) return SCBB_E_UNSUPPORTED;
     }
+    if (fl->storage >= 3 && !bulk_split(make_params(lat, fl)))
+        return SCBB_E_UNSUPPORTED;            // the deviation storages run the two-kernel bulk phase only
     if ((fl->coupling == 0 && n_mesh > 0) || fl->storage != 0) {
         // bounce-back membranes and 16-bit storage need a bulk kernel that stores every node whole: the two-kernel
         // bulk phase (tau = 1; nx a multiple of 4 up to 2048, or any nx up to 256) or the fused row-vectorised

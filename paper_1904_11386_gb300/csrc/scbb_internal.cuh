@@ -58,8 +58,9 @@ struct LbmParams {
     int psi_kind;
     float g[3];
     float ulo[3], uhi[3];
-    int store;              // population storage: 0 FP32, 1 FP16 (__half), 2 BF16 (__nv_bfloat16); the S
-                            // pointers point to that type
+    int store;              // population storage: 0 FP32, 1 FP16 (__half), 2 BF16 (__nv_bfloat16), 3 / 4 FP16 /
+                            // BF16 deviations from w_i rref^c (DevH, DevB); the S pointers point to that type
+    float rref[2];          // reference densities of the deviation storages (0 otherwise)
     int b4cfg;              // shape of the row-vectorised bulk kernel, 0 .. B4_CONFIGS - 1 (scbb_autotune)
     int onsite;             // 1: resting walls (ulo = uhi = 0) and on-site velocity planes z = 1 (vlo), nz-2 (vhi)
     float vlo[3], vhi[3];
@@ -70,12 +71,53 @@ struct LbmParams {
 // 0: (512, 1, 6), 1: (256, 2, 6), 2: (512, 1, 3), 3: (256, 2, 3).
 constexpr int B4_CONFIGS = 4;
 
-// Calls f with a null pointer of the population storage type of `store` (float, __half or __nv_bfloat16), so a
-// launcher instantiates the kernel for that type: with_storage(p.store, [&](auto* tag) { using T = ...; }).
+// Deviation storages: a population f_i^c is stored as the 16-bit value of f_i^c - w_i rref^c.  The reference
+// adds nothing to the moments that the kernels cannot fold in (sum_i w_i = 1, sum_i w_i c_i = 0), and a
+// population near w_i rref^c keeps the 16-bit type's relative precision on its (small) deviation.  Every load
+// adds the reference back and every store takes it off; the rounding of the mass-closing rest population
+// works on the deviations: d_0 = (rho - rref) - sum_{i >= 1} d_i.
+struct DevH {
+    __half h;
+};
+struct DevB {
+    __nv_bfloat16 h;
+};
+template <typename T>
+struct is_dev {
+    static constexpr bool value = false;
+};
+template <>
+struct is_dev<DevH> {
+    static constexpr bool value = true;
+};
+template <>
+struct is_dev<DevB> {
+    static constexpr bool value = true;
+};
+// the reference density of component c for storage type T (0 for the plain storages, at compile time)
+template <typename T>
+__device__ __forceinline__ float dev_ref(const LbmParams& p, int c) {
+    if constexpr (is_dev<T>::value) return p.rref[c];
+    else return 0.f;
+}
+
+// Calls f with a null pointer of the population storage type of `store` (float, __half, __nv_bfloat16, DevH or
+// DevB), so a launcher instantiates the kernel for that type: with_storage(p.store, [&](auto* tag) { ... }).
 template <class F>
 inline void with_storage(int store, F&& f) {
     if (store == 1) f(static_cast<__half*>(nullptr));
     else if (store == 2) f(static_cast<__nv_bfloat16*>(nullptr));
+    else if (store == 3) f(static_cast<DevH*>(nullptr));
+    else if (store == 4) f(static_cast<DevB*>(nullptr));
+    else f(static_cast<float*>(nullptr));
+}
+// The same for kernels that have no deviation form (the fused bulk kernels and their wall pass, which a context
+// with a deviation storage never runs: it requires the two-kernel bulk phase); the deviation codes map to the
+// plain 16-bit types so that the launchers compile.
+template <class F>
+inline void with_plain_storage(int store, F&& f) {
+    if (store == 1 || store == 3) f(static_cast<__half*>(nullptr));
+    else if (store == 2 || store == 4) f(static_cast<__nv_bfloat16*>(nullptr));
     else f(static_cast<float*>(nullptr));
 }
 
@@ -156,6 +198,25 @@ __device__ __forceinline__ void pst4(__nv_bfloat16* p, float4 v) {
     memcpy(&u.y, &b, 4);
     *reinterpret_cast<uint2*>(p) = u;
 }
+// The deviation storages hold their deviations in the plain 16-bit types: the same access functions.
+__device__ __forceinline__ const __half* raw16(const DevH* p) { return reinterpret_cast<const __half*>(p); }
+__device__ __forceinline__ __half* raw16(DevH* p) { return reinterpret_cast<__half*>(p); }
+__device__ __forceinline__ const __nv_bfloat16* raw16(const DevB* p) { return reinterpret_cast<const __nv_bfloat16*>(p); }
+__device__ __forceinline__ __nv_bfloat16* raw16(DevB* p) { return reinterpret_cast<__nv_bfloat16*>(p); }
+__device__ __forceinline__ float pld(const DevH* p) { return pld(raw16(p)); }
+__device__ __forceinline__ float pld(const DevB* p) { return pld(raw16(p)); }
+__device__ __forceinline__ float pldc(const DevH* p) { return pldc(raw16(p)); }
+__device__ __forceinline__ float pldc(const DevB* p) { return pldc(raw16(p)); }
+__device__ __forceinline__ float pround(float v, const DevH* p) { return pround(v, raw16(p)); }
+__device__ __forceinline__ float pround(float v, const DevB* p) { return pround(v, raw16(p)); }
+__device__ __forceinline__ float pdither(float v, uint32_t u, const DevH* p) { return pdither(v, u, raw16(p)); }
+__device__ __forceinline__ float pdither(float v, uint32_t u, const DevB* p) { return pdither(v, u, raw16(p)); }
+__device__ __forceinline__ void pst(DevH* p, float v) { pst(raw16(p), v); }
+__device__ __forceinline__ void pst(DevB* p, float v) { pst(raw16(p), v); }
+__device__ __forceinline__ float4 pld4(const DevH* p) { return pld4(raw16(p)); }
+__device__ __forceinline__ float4 pld4(const DevB* p) { return pld4(raw16(p)); }
+__device__ __forceinline__ void pst4(DevH* p, float4 v) { pst4(raw16(p), v); }
+__device__ __forceinline__ void pst4(DevB* p, float4 v) { pst4(raw16(p), v); }
 
 // One capsule's constants on the device.
 struct CapDev {
@@ -283,6 +344,10 @@ __device__ __forceinline__ void pull(const LbmParams& p, const T* __restrict__ S
         unsigned int m = k.cx[1 - dir_x(i)] + k.ry[1 - dir_y(i)] + pz[1 - dir_z(i)];
         f[i] = pld(S + (size_t)i * p.N + m);
         f[Q + i] = pld(S + (size_t)(Q + i) * p.N + m);
+        if constexpr (is_dev<T>::value) {
+            f[i] += dir_w(i) * p.rref[0];
+            f[Q + i] += dir_w(i) * p.rref[1];
+        }
     }
 }
 

@@ -149,7 +149,8 @@ class Problem:
     noise: float = 1e-4
     seed: int = 1
     steps: int = 200
-    storage: int = 0                # populations on the GPU: 0 FP32, 1 FP16, 2 BF16 (the oracle is FP64 always)
+    storage: int = 0                # populations on the GPU: 0 FP32, 1 FP16, 2 BF16, 3 / 4 FP16 / BF16 deviations
+                                    # from w_i (rho_maj + rho_min) / 2 (the oracle is FP64 always)
     max_boundary: int = 0           # GPU boundary-list capacity (0: sized from the membrane areas)
 
     @property

@@ -33,6 +33,8 @@ CASES = {
     "ibm64": ("inputs.small_problem(n=64, walls=1, coupling=1, capsule=True, noise=1e-3, seed=43, radius=6.0)", 6),
     "fp16_64": ("dataclasses.replace(inputs.Problem(name='h', nx=64, ny=36, nz=26, walls=1, psi_kind=0, "
                 "coupling=1, z_interface=13, noise=1e-3, seed=44), storage=1)", 8),
+    "fp16dev_64": ("dataclasses.replace(inputs.Problem(name='d', nx=64, ny=36, nz=26, walls=1, psi_kind=0, "
+                   "coupling=1, z_interface=13, noise=1e-3, seed=45), storage=3)", 8),
 }
 
 _CHILD = r"""
