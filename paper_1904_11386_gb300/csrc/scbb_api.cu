@@ -28,6 +28,8 @@ struct scbb_ctx {
     // contexts with meshes: a second stream for kernels that run beside the critical path of the step
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_fork3 = nullptr, ev_join3 = nullptr;
+    cudaEvent_t ev_blist = nullptr;   // the next step's boundary list, built on the side stream (many capsules)
+    bool blist_pending = false;       // ev_blist recorded and not yet waited for on the context stream
     int nm = 0;
     std::vector<float4> X0;           // initial shape, host copy
     void* ws = nullptr;               // the caller's workspace: every piece of device state lives in it
@@ -399,6 +401,7 @@ scbb_status scbb_create(const scbb_lattice* lat, const scbb_fluid* fl, int n_mes
         CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork2, cudaEventDisableTiming));
         CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork3, cudaEventDisableTiming));
         CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join3, cudaEventDisableTiming));
+        CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_blist, cudaEventDisableTiming));
     }
     layout(lat, fl, n_mesh, meshes, dev_workspace, &c->d);
     c->ws = dev_workspace;
@@ -602,9 +605,12 @@ static StepPlan plan_step(const scbb_ctx* c, bool allow_side) {
     //   after the owner field, the fresh nodes (they need the owner field, the column lists, the vertex
     //   velocities and the mass factors, not the boundary list, and the boundary-list kernels read nothing they
     //   write), joined at the end of the step.
-    // (The boundary list of the next step could also wait on the side stream until the next step's boundary
-    // kernel, beside its bulk phase; measured at 128^3 that slows the bulk kernels more than it saves: 215.6
-    // against 209.9 us a step.)
+    // With many capsules the boundary list of the next step (boundary nodes and crossed elements at X(t+1))
+    // is built on the side stream too, beside the next step's bulk phase: nothing reads it before the next
+    // step's boundary kernel, where it is joined (and at the end of every call and captured graph:
+    // join_deferred).  Those list kernels are instruction-bound and the bulk kernels memory-bound, so they
+    // share the SMs well; with one capsule at 128^3 the list is small and the sharing slows the bulk kernels
+    // more than it saves (215.6 against 209.9 us a step), so it stays on the context stream there.
     // With the immersed boundary, the wall ghosts (they read the populations alone) run there beside the
     // membrane forces and the spreading (they read the vertices alone), joined before the bulk kernel.
     // The two-kernel bulk phase computes the wall ghost densities itself.
@@ -655,8 +661,28 @@ static void enqueue_bulk(scbb_ctx* c, const StepPlan& s) {
     c->launches += bulk_split(c->lp) ? 2 : 1;
 }
 
+// The boundary list moves beside the bulk phase from DEFER_CAPSULES capsules on (SCBB_DEFER=0/1 forces it).
+constexpr int DEFER_CAPSULES = 8;
+static bool defer_blist(const scbb_ctx* c) {
+    static int v = -2;
+    if (v == -2) {
+        const char* e = getenv("SCBB_DEFER");
+        v = (e && (e[0] == '0' || e[0] == '1') && e[1] == 0) ? e[0] - '0' : -1;
+    }
+    return v >= 0 ? v == 1 : c->d.NM >= DEFER_CAPSULES;
+}
+
+// The context stream waits for a boundary list still being built on the side stream.
+static void join_deferred(scbb_ctx* c) {
+    if (c->blist_pending) {
+        cudaStreamWaitEvent(c->st, c->ev_blist, 0);
+        c->blist_pending = false;
+    }
+}
+
 static void enqueue_post(scbb_ctx* c, const StepPlan& s) {
     const int step = s.step;
+    join_deferred(c);
     c->mark(3);
     if (s.ibm) {
         launch_ibm_interp(c->lp, c->d, c->st);
@@ -683,7 +709,13 @@ static void enqueue_post(scbb_ctx* c, const StepPlan& s) {
             cudaStreamWaitEvent(c->side, c->ev_fork3, 0);
             launch_bb_fresh_nodes(c->lp, c->d, c->d.S[1 - c->cur], step, c->side);
             cudaEventRecord(c->ev_join3, c->side);
-            launch_bb_boundary_list(c->lp, c->d, c->st);
+            if (defer_blist(c)) {
+                launch_bb_boundary_list(c->lp, c->d, c->side);
+                cudaEventRecord(c->ev_blist, c->side);
+                c->blist_pending = true;
+            } else {
+                launch_bb_boundary_list(c->lp, c->d, c->st);
+            }
             cudaStreamWaitEvent(c->st, c->ev_join3, 0);
         } else {
             launch_bb_lists_reset(c->d, c->st);
@@ -740,6 +772,7 @@ static void capture_pair(scbb_ctx* c) {
         return;
     }
     for (int k = 0; k < GRAPH_STEPS; k++) enqueue_step(c);
+    join_deferred(c);
     const cudaError_t e = cudaStreamEndCapture(c->st, &g);
     const long long per_pair = c->launches - launches0;
     c->cur = cur0;
@@ -771,6 +804,7 @@ scbb_status scbb_step(scbb_ctx* c, long long n) {
         // and not before one step has run eagerly, which sets the kernels' launch attributes)
         if (left >= GRAPH_STEPS && graphs_enabled() && !c->graph_off && c->timing == 0 && c->eager_steps > 0) {
             const int key = (c->cur << 1) | (int)(c->steps & 1);
+            join_deferred(c);       // a graph neither waits for nor leaves side-stream work outside it
             if (!c->gexec || ((key ^ c->gkey) != 0 && (key ^ c->gkey) != 3)) capture_pair(c);
             if (c->gexec && key == c->gkey) {
                 for (; left >= GRAPH_STEPS; left -= GRAPH_STEPS) {
@@ -785,6 +819,7 @@ scbb_status scbb_step(scbb_ctx* c, long long n) {
         c->eager_steps++;
         left--;
     }
+    join_deferred(c);
     CUDA_TRY(c, cudaGetLastError());
     return SCBB_OK;
 }
@@ -1740,6 +1775,7 @@ void scbb_destroy(scbb_ctx* c) {
     if (c->ev_fork2) cudaEventDestroy(c->ev_fork2);
     if (c->ev_fork3) cudaEventDestroy(c->ev_fork3);
     if (c->ev_join3) cudaEventDestroy(c->ev_join3);
+    if (c->ev_blist) cudaEventDestroy(c->ev_blist);
     for (auto& e : c->ev) cudaEventDestroy(e);
     for (auto& e : c->pev) cudaEventDestroy(e);
     delete c;
