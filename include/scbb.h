@@ -169,6 +169,21 @@ scbb_status scbb_get_diag(scbb_ctx* ctx, double* mass2, double* mom3, double* vo
  * SCBB_E_UNSUPPORTED for the immersed-boundary coupling. */
 scbb_status scbb_get_owner(scbb_ctx* ctx, unsigned short* owner, int* n_boundary, int* n_fresh);
 
+/* The boundary list the next step's boundary kernel will use (built at the current positions) and the element
+ * of each of its cut links (Sec. II.C): the triangle the link's segment crosses nearest to the link's node of
+ * lower linear index, lower triangle id on ties; a cut link with no crossing (round-off) takes the triangle
+ * of the searched capsule whose centroid is nearest the link's midpoint.  The searched capsule is the one
+ * the node lies in, else the one across the link.  Writes the first min(n, max_nodes) boundary nodes (linear
+ * node index, in the list's own order) to nodes[] and their elements to elems[max_nodes][18] (slot i-1 for
+ * direction i of the D3Q19 order of scbb_get_populations; -1 for a link that is not cut), the list's length n
+ * to *n_boundary (may be NULL; a list that overflowed its capacity holds its first maxB nodes and raises the
+ * error word at the next synchronising call) and the number of cut links resolved by the nearest-centroid rule to *n_fallback (may be
+ * NULL).  max_nodes = 0 with NULL arrays reads the counts alone.  Synchronous; it adds one kernel launch and
+ * leaves the state as it was.  SCBB_E_INVAL for max_nodes < 0 or missing arrays, SCBB_E_UNSUPPORTED for the
+ * immersed-boundary coupling. */
+scbb_status scbb_get_boundary(scbb_ctx* ctx, int max_nodes, int* nodes, int* elems, int* n_boundary,
+                              int* n_fallback);
+
 /* Number of kernel launches issued by this context since creation (for launch accounting). */
 long long scbb_launch_count(const scbb_ctx* ctx);
 

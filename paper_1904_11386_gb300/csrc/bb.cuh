@@ -14,6 +14,9 @@ void launch_bb_lists_reset(const DevState& d, cudaStream_t st);
 void launch_bb_classify_lists(const LbmParams& p, const DevState& d, int step, bool init, cudaStream_t st);
 void launch_bb_owner(const LbmParams& p, const DevState& d, int step, bool init, cudaStream_t st);
 void launch_bb_boundary_list(const LbmParams& p, const DevState& d, cudaStream_t st);
+// Settles the crossed element of every cut link of the current boundary list (and the virtual densities the
+// boundary kernel reads); the first kernel of the step's boundary phase.
+void launch_bb_vrho(const LbmParams& p, const DevState& d, cudaStream_t st);
 // Mass bookkeeping and correction factors of Eq. 18 (after this step's boundary kernel).
 void launch_bb_mass(const LbmParams& p, const DevState& d, cudaStream_t st);
 // New populations of the fresh nodes (after the classification and the mass bookkeeping).

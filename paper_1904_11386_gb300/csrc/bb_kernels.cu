@@ -16,6 +16,8 @@
 // link midpoint).
 #include <cuda_fp16.h>
 #include <math.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include <type_traits>
 
@@ -223,7 +225,7 @@ __global__ void k_class_tri(LbmParams p, DevState d, int step) {
     d.trec[4 * t + 1] = make_float4(b.x, b.y, b.z, 0.f);
     d.trec[4 * t + 2] = make_float4(c.x, c.y, c.z, 0.f);
     d.trec[4 * t + 3] = make_float4((a.x + b.x + c.x) * (1.f / 3.f), (a.y + b.y + c.y) * (1.f / 3.f),
-                                    (a.z + b.z + c.z) * (1.f / 3.f), 0.f);
+                                    (a.z + b.z + c.z) * (1.f / 3.f), __int_as_float(k));
     const float xmin = fminf(a.x, fminf(b.x, c.x)), xmax = fmaxf(a.x, fmaxf(b.x, c.x));
     const float ymin = fminf(a.y, fminf(b.y, c.y)), ymax = fmaxf(a.y, fmaxf(b.y, c.y));
     // a triangle wider than a column grid or outside its capsule's grid (a degenerate mesh, runaway or
@@ -308,7 +310,8 @@ __global__ void k_class_col(LbmParams p, DevState d, int init) {
     }
 }
 
-// Clears the boundary and fresh bits of the previous step's lists and the per-column counters.
+// Clears the boundary and fresh bits of the previous step's lists (and the boundary nodes' places, so that
+// bidx is -1 at every node not listed) and the per-column counters.
 __global__ void k_lists_reset(DevState d) {
     pdl_wait();
     pdl_trigger();
@@ -322,6 +325,7 @@ __global__ void k_lists_reset(DevState d) {
         if (q < nb && q < d.maxB) {
             const int n = d.blist[q];
             atomicAnd(d.bmask + (n >> 5), ~(1u << (n & 31)));
+            d.bidx[n] = -1;
         }
         if (q < nf && q < d.maxF) {
             const int n = d.flist[q];
@@ -330,7 +334,8 @@ __global__ void k_lists_reset(DevState d) {
     }
 }
 
-// Nodes of each capsule's box (one node wider) with a cut membrane link join the boundary list.
+// Nodes of each capsule's box (one node wider) with a cut membrane link join the boundary list; each one's
+// place in it goes to bidx, and the crossing keys of its links start at "none".
 __global__ void k_boundary_mark(LbmParams p, DevState d) {
     pdl_wait();
     pdl_trigger();
@@ -357,164 +362,193 @@ __global__ void k_boundary_mark(LbmParams p, DevState d) {
     const uint32_t prev = atomicOr(d.bmask + (n >> 5), bit);
     if (prev & bit) return;                           // already listed (boxes of two capsules overlap)
     const int b = atomicAdd(d.cnt + 0, 1);
-    if (b < d.maxB) d.blist[b] = (int)n;
-    else atomicOr(d.cnt + 2, 8);
+    d.bidx[n] = b < d.maxB ? b : -1;
+    if (b < d.maxB) {
+        d.blist[b] = (int)n;
+        // no crossing yet on any of its links (the element search lowers these keys)
+        ulonglong2* k2 = reinterpret_cast<ulonglong2*>(d.bkey + (size_t)b * (Q - 1));
+#pragma unroll
+        for (int j = 0; j < (Q - 1) / 2; j++) k2[j] = make_ulonglong2(~0ull, ~0ull);
+    } else {
+        atomicOr(d.cnt + 2, 8);
+    }
 }
 
-// One warp per boundary node: the element each cut link crosses.  Lane i-1 owns direction i.  Candidate
-// triangles come from the 3 x 3 column cells around the node, filtered by their z range; every lane tests
-// its candidates against all cut links of the node, and the nearest crossing per link is kept with a
-// shared-memory atomicMin on (crossing parameter, triangle id) -- the order-independent form of
-// "nearest crossing, lower triangle id on ties".
-constexpr int BE_WARPS = 8;
+// ------------------------------------------------------------------------------------------------------
+// Crossed elements of the cut links
+// ------------------------------------------------------------------------------------------------------
+// A cut link's element is the triangle its segment crosses nearest to the node of lower linear index (lower
+// triangle id on ties).  The search runs over the triangles: a thread per triangle and group of link
+// directions visits the lattice links whose segments can meet its bounding box and, for each cut link the
+// triangle crosses, records the key
+// (crossing parameter, triangle id) with a 64-bit atomicMin at every boundary node that searches this
+// triangle's capsule along that link: the minimum over all triangles is the nearest crossing whatever the
+// order.  Each node takes the link's segment as it would alone: from its own offset position in the periodic
+// image nearest the capsule's centre, along c_i, turned around to start at the node of lower linear index.
+// Links left without a crossing (round-off) are resolved when the list is read (k_bb_vrho).
 
-__device__ __forceinline__ void node_elements(const LbmParams& p, const DevState& d, const int warp, const int wl,
-                                              const int lane, unsigned long long (*best)[Q - 1],
-                                              float4 (*segP)[Q - 1], float4 (*segD)[Q - 1], int (*queue)[CAND_Q]) {
-    const int n = d.blist[warp];
-    const int z = n / p.nxy, r = n - z * p.nxy, y = r / p.nx, x = r - y * p.nx;
-    const uint16_t me = d.owner[n];
-    int my_cap = -1;
-    if (lane < Q - 1) {
-        const int i = lane + 1;
-        const long long m = node_of(p, x + dir_x(i), y + dir_y(i), z + dir_z(i));
-        if (m >= 0) {
-            const uint16_t o = d.owner[m];
-            if (o != 0xFFFF && o != me) my_cap = (me != 0 ? me : o) - 1;
-        }
-        best[wl][lane] = ~0ull;
-    }
-    __syncwarp();
-    const unsigned cutmask = __ballot_sync(0xffffffffu, my_cap >= 0);
-    unsigned todo = cutmask;
-    while (todo) {
-        const int src = __ffs(todo) - 1;
-        const int cap = __shfl_sync(0xffffffffu, my_cap, src);
-        const unsigned same = __ballot_sync(0xffffffffu, my_cap == cap) & cutmask;
-        todo &= ~same;
-        const double* cr = d.cap_red + 4 * cap;
-        const float px = near_image(x, (float)cr[1], p.nx, true) + BB_EPSX;
-        const float py = near_image(y, (float)cr[2], p.ny, true) + BB_EPSY;
-        const float pz = near_image(z, (float)cr[3], p.nz, !p.walls) + BB_EPSZ;
-        if (lane < Q - 1 && ((same >> lane) & 1u)) {
-            const int i = lane + 1;
-            const long long m = node_of(p, x + dir_x(i), y + dir_y(i), z + dir_z(i));
-            float3 P = make_float3(px, py, pz);
-            float3 Dv = make_float3((float)dir_x(i), (float)dir_y(i), (float)dir_z(i));
-            if (m < n) {                // canonical orientation: from the node of lower linear index
-                P = make_float3(px + Dv.x, py + Dv.y, pz + Dv.z);
-                Dv = make_float3(-Dv.x, -Dv.y, -Dv.z);
-            }
-            segP[wl][lane] = make_float4(P.x, P.y, P.z, 0.f);
-            segD[wl][lane] = make_float4(Dv.x, Dv.y, Dv.z, 0.f);
-        }
-        __syncwarp();
-        const int4 lo = d.cbox[2 * cap];
-        const int ccx = (int)floorf(px) - lo.x, ccy = (int)floorf(py) - lo.y;
-        // box around the cut links of this capsule: a triangle crossing one of them meets it
-        float b0x = 1e30f, b0y = 1e30f, b0z = 1e30f, b1x = -1e30f, b1y = -1e30f, b1z = -1e30f;
-        if (lane < Q - 1 && ((same >> lane) & 1u)) {
-            const float4 P4 = segP[wl][lane], D4 = segD[wl][lane];
-            b0x = fminf(P4.x, P4.x + D4.x); b1x = fmaxf(P4.x, P4.x + D4.x);
-            b0y = fminf(P4.y, P4.y + D4.y); b1y = fmaxf(P4.y, P4.y + D4.y);
-            b0z = fminf(P4.z, P4.z + D4.z); b1z = fmaxf(P4.z, P4.z + D4.z);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            b0x = fminf(b0x, __shfl_xor_sync(0xffffffffu, b0x, o));
-            b0y = fminf(b0y, __shfl_xor_sync(0xffffffffu, b0y, o));
-            b0z = fminf(b0z, __shfl_xor_sync(0xffffffffu, b0z, o));
-            b1x = fmaxf(b1x, __shfl_xor_sync(0xffffffffu, b1x, o));
-            b1y = fmaxf(b1y, __shfl_xor_sync(0xffffffffu, b1y, o));
-            b1z = fmaxf(b1z, __shfl_xor_sync(0xffffffffu, b1z, o));
-        }
-        const CellScan cs = cell_scan(d, cap, ccx - 1, ccy - 1, 3, lane);
-        for_candidates(d, cs, make_float3(b0x, b0y, b0z), make_float3(b1x, b1y, b1z), queue[wl], lane, [&](int t) {
-            if (t < 0) return;
-            const float3 v0 = f3(d.trec[4 * t]), v1 = f3(d.trec[4 * t + 1]), v2 = f3(d.trec[4 * t + 2]);
-            const float bx0 = fminf(v0.x, fminf(v1.x, v2.x)), bx1 = fmaxf(v0.x, fmaxf(v1.x, v2.x));
-            const float by0 = fminf(v0.y, fminf(v1.y, v2.y)), by1 = fmaxf(v0.y, fmaxf(v1.y, v2.y));
-            const float bz0 = fminf(v0.z, fminf(v1.z, v2.z)), bz1 = fmaxf(v0.z, fmaxf(v1.z, v2.z));
-            const float3 e1 = sub(v1, v0), e2 = sub(v2, v0);
-            unsigned links = same;
-            while (links) {
-                const int li = __ffs(links) - 1;
-                links &= links - 1;
-                const float4 P4 = segP[wl][li], D4 = segD[wl][li];
-                // the segment's bounding box must meet the triangle's
-                if (fmaxf(P4.x, P4.x + D4.x) < bx0 || fminf(P4.x, P4.x + D4.x) > bx1) continue;
-                if (fmaxf(P4.y, P4.y + D4.y) < by0 || fminf(P4.y, P4.y + D4.y) > by1) continue;
-                if (fmaxf(P4.z, P4.z + D4.z) < bz0 || fminf(P4.z, P4.z + D4.z) > bz1) continue;
-                const float3 P = make_float3(P4.x, P4.y, P4.z), Dv = make_float3(D4.x, D4.y, D4.z);
-                const float3 h = cross(Dv, e2);
-                const float det = dot(e1, h);
-                if (fabsf(det) < 1e-30f) continue;
-                const float inv = 1.f / det;
-                const float3 sv = sub(P, v0);
-                const float u = dot(sv, h) * inv;
-                if (u < 0.f || u > 1.f) continue;
-                const float3 qv = cross(sv, e1);
-                const float v = dot(Dv, qv) * inv;
-                if (v < 0.f || u + v > 1.f) continue;
-                const float tt = dot(e2, qv) * inv;
-                if (tt < 0.f || tt > 1.f) continue;
-                const unsigned long long key =
-                    ((unsigned long long)__float_as_uint(tt) << 32) | (unsigned long long)(unsigned)t;
-                atomicMin(&best[wl][li], key);
-            }
-        });
-        __syncwarp();
-    }
-    __syncwarp();
-    int best_e = -1;
-    if (lane < Q - 1 && ((cutmask >> lane) & 1u) && best[wl][lane] != ~0ull)
-        best_e = (int)(unsigned)(best[wl][lane] & 0xffffffffull);
-    // links without a crossing (round-off): nearest centroid to the link midpoint, whole capsule
-    const unsigned miss = __ballot_sync(0xffffffffu, lane < Q - 1 && ((cutmask >> lane) & 1u) && best_e < 0);
-    unsigned mm = miss;
-    while (mm) {
-        const int li = __ffs(mm) - 1;
-        mm &= mm - 1;
-        const int i = li + 1;
-        const int cap = __shfl_sync(0xffffffffu, my_cap, li);
-        const CapDev cp = d.cap[cap];
-        const double* cr = d.cap_red + 4 * cap;
-        const float px = near_image(x, (float)cr[1], p.nx, true) + BB_EPSX;
-        const float py = near_image(y, (float)cr[2], p.ny, true) + BB_EPSY;
-        const float pz = near_image(z, (float)cr[3], p.nz, !p.walls) + BB_EPSZ;
-        const float mx = px + 0.5f * dir_x(i), my = py + 0.5f * dir_y(i), mz = pz + 0.5f * dir_z(i);
-        float bd = 1e30f;
-        int be = -1;
-        for (int tl = lane; tl < cp.nt; tl += 32) {
-            const int t = cp.t0 + tl;
-            const float3 cc = f3(d.trec[4 * t + 3]);
-            const float3 dd = make_float3(cc.x - mx, cc.y - my, cc.z - mz);
-            const float d2 = dot(dd, dd);
-            if (d2 < bd || (d2 == bd && t < be)) { bd = d2; be = t; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float b2 = __shfl_xor_sync(0xffffffffu, bd, o);
-            const int e2 = __shfl_xor_sync(0xffffffffu, be, o);
-            if (e2 >= 0 && (be < 0 || b2 < bd || (b2 == bd && e2 < be))) { bd = b2; be = e2; }
-        }
-        if (lane == li) best_e = be;
-    }
-    if (lane < Q - 1) d.belem[(size_t)warp * (Q - 1) + lane] = ((cutmask >> lane) & 1u) ? best_e : -1;
+// The segment's bounding box meets the triangle's [b0, b1].
+__device__ __forceinline__ bool seg_meets_box(float3 P, float3 Dv, float3 b0, float3 b1) {
+    if (fmaxf(P.x, P.x + Dv.x) < b0.x || fminf(P.x, P.x + Dv.x) > b1.x) return false;
+    if (fmaxf(P.y, P.y + Dv.y) < b0.y || fminf(P.y, P.y + Dv.y) > b1.y) return false;
+    if (fmaxf(P.z, P.z + Dv.z) < b0.z || fminf(P.z, P.z + Dv.z) > b1.z) return false;
+    return true;
 }
 
-__global__ void __launch_bounds__(BE_WARPS * 32, 4) k_boundary_elements(LbmParams p, DevState d) {
+// Segment P + s Dv (s in [0, 1]) against the triangle (v0, v0 + e1, v0 + e2): Moller-Trumbore with closed
+// bounds; the crossing parameter in tt (a crossing at s = -0 counts as +0, so the key orders it first).
+__device__ __forceinline__ bool seg_tri(float3 P, float3 Dv, float3 v0, float3 e1, float3 e2, float& tt) {
+    const float3 h = cross(Dv, e2);
+    const float det = dot(e1, h);
+    if (fabsf(det) < 1e-30f) return false;
+    const float inv = 1.f / det;
+    const float3 sv = sub(P, v0);
+    const float u = dot(sv, h) * inv;
+    if (u < 0.f || u > 1.f) return false;
+    const float3 qv = cross(sv, e1);
+    const float v = dot(Dv, qv) * inv;
+    if (v < 0.f || u + v > 1.f) return false;
+    tt = dot(e2, qv) * inv;
+    if (tt < 0.f || tt > 1.f) return false;
+    tt = __fadd_rn(tt, 0.f);
+    return true;
+}
+
+struct TriGeom {
+    float3 v0, e1, e2, b0, b1, cr;   // vertex 0, edges, bounding box, capsule centre (image reference)
+    int t, k;
+};
+
+// Lattice coordinate X (unwrapped) is the periodic image of its node nearest the capsule's centre r, as
+// near_image takes it: at once when X lies well inside half a period of r, else by near_image itself.
+__device__ __forceinline__ bool own_image(int X, float r, int L, bool per) {
+    if (!per || fabsf((float)X - r) < 0.5f * (float)L - 1.f) return true;
+    return near_image(wrapf(X, L), r, L, true) == (float)X;
+}
+
+// The segment node n (unwrapped coordinates X, Y, Z, its own image) tests along direction i towards its
+// neighbour o: from its offset position, turned around to start at the node of lower linear index.
+__device__ __forceinline__ void end_segment(long long n, long long o, int X, int Y, int Z, int i, float3& P,
+                                            float3& Dv) {
+    P = make_float3((float)X + BB_EPSX, (float)Y + BB_EPSY, (float)Z + BB_EPSZ);
+    Dv = make_float3((float)dir_x(i), (float)dir_y(i), (float)dir_z(i));
+    if (o < n) {
+        P = make_float3(P.x + Dv.x, P.y + Dv.y, P.z + Dv.z);
+        Dv = make_float3(-Dv.x, -Dv.y, -Dv.z);
+    }
+}
+
+// Crossing parameter of the triangle on a segment, -1 when it misses.
+__device__ __forceinline__ float seg_cross(const TriGeom& g, float3 P, float3 Dv) {
+    float tt;
+    if (!seg_meets_box(P, Dv, g.b0, g.b1) || !seg_tri(P, Dv, g.v0, g.e1, g.e2, tt)) return -1.f;
+    return tt;
+}
+
+// Records the crossing (parameter tt >= 0) at node n's link along direction i, when n is listed.
+__device__ __forceinline__ void end_record(const DevState& d, const TriGeom& g, int b, int i, float tt) {
+    if (b < 0) return;              // not listed: the list is full (flagged by the list kernel)
+    const unsigned long long key = ((unsigned long long)__float_as_uint(tt) << 32) | (unsigned long long)(unsigned)g.t;
+    atomicMin(d.bkey + (size_t)b * (Q - 1) + (i - 1), key);
+}
+
+// One thread per (triangle, group of the nine directions c_i with odd i): G = 3 groups of an axis and two face
+// diagonals ({1,7,13} {3,9,15} {5,11,17}) for many triangles, G = 9 single directions for few (more threads,
+// shorter ones).  The nine odd directions and their opposites (i + 1, the same links seen from the other end)
+// are all eighteen.  The geometric tests of a link come first; the owner field and the list are read only for
+// the links the triangle crosses.
+template <int G>
+__global__ void __launch_bounds__(128, 6) k_link_cross(LbmParams p, DevState d) {
     pdl_wait();
     pdl_trigger();
-    __shared__ unsigned long long best[BE_WARPS][Q - 1];
-    __shared__ float4 segP[BE_WARPS][Q - 1];          // canonical start point of each link's segment
-    __shared__ float4 segD[BE_WARPS][Q - 1];          // and its direction
-    __shared__ int queue[BE_WARPS][CAND_Q];
-    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nb = min(d.cnt[0], d.maxB);
-    for (int w = blockIdx.x * BE_WARPS + wl; w < nb; w += gridDim.x * BE_WARPS) {
-        node_elements(p, d, w, wl, lane, best, segP, segD, queue);
-        __syncwarp();
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = q / G;
+    if (t >= d.NT) return;
+    const int grp = q - t * G;
+    TriGeom g;
+    g.t = t;
+    const float4 c3 = d.trec[4 * t + 3];
+    g.k = __float_as_int(c3.w);
+    const float3 v0 = f3(d.trec[4 * t]), v1 = f3(d.trec[4 * t + 1]), v2 = f3(d.trec[4 * t + 2]);
+    g.b0 = make_float3(fminf(v0.x, fminf(v1.x, v2.x)), fminf(v0.y, fminf(v1.y, v2.y)), fminf(v0.z, fminf(v1.z, v2.z)));
+    g.b1 = make_float3(fmaxf(v0.x, fmaxf(v1.x, v2.x)), fmaxf(v0.y, fmaxf(v1.y, v2.y)), fmaxf(v0.z, fmaxf(v1.z, v2.z)));
+    // the triangles the classification leaves out of its column lists (wider than a column grid, outside their
+    // capsule's grid, non-finite) are flagged there and cross nothing here; a triangle as tall as the grid is a
+    // broken mesh too.  What is left bounds the loops below to CW + 3 nodes per axis.
+    const int4 lo = d.cbox[2 * g.k];
+    if (!(g.b1.x - g.b0.x < (float)d.CW && g.b1.y - g.b0.y < (float)d.CW && g.b0.x >= (float)(lo.x - 2) &&
+          g.b1.x <= (float)(lo.x + d.CW + 2) && g.b0.y >= (float)(lo.y - 2) && g.b1.y <= (float)(lo.y + d.CW + 2)))
+        return;
+    if (!(g.b1.z - g.b0.z < (float)d.CW)) {
+        atomicOr(d.cnt + 2, 32);
+        return;
+    }
+    g.v0 = v0;
+    g.e1 = sub(v1, v0);
+    g.e2 = sub(v2, v0);
+    const double* cr = d.cap_red + 4 * g.k;
+    g.cr = make_float3((float)cr[1], (float)cr[2], (float)cr[3]);
+    // Plane test, conservative: a link whose two ends lie on the same side of the triangle's plane by more than
+    // tol (about 1e3 times the rounding of these products) cannot pass seg_tri.
+    const float3 nrm = cross(g.e1, g.e2);
+    const float tol = 1e-3f * (fabsf(g.e1.x) + fabsf(g.e1.y) + fabsf(g.e1.z)) *
+                      (fabsf(g.e2.x) + fabsf(g.e2.y) + fabsf(g.e2.z));
+    constexpr float DL = 1e-3f;     // margin of the node ranges over the exact box test
+#pragma unroll 1
+    for (int j = 0; j < 9 / G; j++) {
+        const int i = 2 * (grp + G * j) + 1;
+        const int cx = dir_x(i), cy = dir_y(i), cz = dir_z(i);
+        const float dn = nrm.x * cx + nrm.y * cy + nrm.z * cz;
+        // nodes u whose segment [u, u + c] (with the offsets) can meet the box
+        const int x0 = (int)ceilf(g.b0.x - DL - BB_EPSX - (float)max(cx, 0)), x1 = (int)floorf(g.b1.x + DL - BB_EPSX - (float)min(cx, 0));
+        const int y0 = (int)ceilf(g.b0.y - DL - BB_EPSY - (float)max(cy, 0)), y1 = (int)floorf(g.b1.y + DL - BB_EPSY - (float)min(cy, 0));
+        const int z0 = (int)ceilf(g.b0.z - DL - BB_EPSZ - (float)max(cz, 0)), z1 = (int)floorf(g.b1.z + DL - BB_EPSZ - (float)min(cz, 0));
+        for (int Z = z0; Z <= z1; Z++)
+            for (int Y = y0; Y <= y1; Y++) {
+                const float syz = nrm.y * (((float)Y + BB_EPSY) - v0.y) + nrm.z * (((float)Z + BB_EPSZ) - v0.z);
+                for (int X = x0; X <= x1; X++) {
+                    const float su = syz + nrm.x * (((float)X + BB_EPSX) - v0.x), sw = su + dn;
+                    if ((su > tol && sw > tol) || (su < -tol && sw < -tol)) continue;
+                    // where the link meets the plane must lie in the triangle's box, up to a margin far above
+                    // the rounding of that point (links almost parallel to the plane go on to the exact test)
+                    if (fabsf(dn) > tol) {
+                        const float s = -su / dn, m = 4.f * tol / fabsf(dn) + 1e-3f;
+                        const float px = ((float)X + BB_EPSX) + s * cx, py = ((float)Y + BB_EPSY) + s * cy,
+                                    pz = ((float)Z + BB_EPSZ) + s * cz;
+                        if (px < g.b0.x - m || px > g.b1.x + m || py < g.b0.y - m || py > g.b1.y + m ||
+                            pz < g.b0.z - m || pz > g.b1.z + m)
+                            continue;
+                    }
+                    const long long nu = node_of(p, X, Y, Z), nw = node_of(p, X + cx, Y + cy, Z + cz);
+                    if (nu < 0 || nw < 0) continue;
+                    // each end tests the segment as its own search takes it (only in its own image); the two
+                    // segments are the same bits unless rounding at a power of two parts them
+                    float tu = -1.f, tw = -1.f;
+                    float3 Pu, Du, Pw, Dw;
+                    const bool iu = own_image(X, g.cr.x, p.nx, true) && own_image(Y, g.cr.y, p.ny, true) &&
+                                    own_image(Z, g.cr.z, p.nz, !p.walls);
+                    const bool iw = own_image(X + cx, g.cr.x, p.nx, true) && own_image(Y + cy, g.cr.y, p.ny, true) &&
+                                    own_image(Z + cz, g.cr.z, p.nz, !p.walls);
+                    if (iu) {
+                        end_segment(nu, nw, X, Y, Z, i, Pu, Du);
+                        tu = seg_cross(g, Pu, Du);
+                    }
+                    if (iw) {
+                        end_segment(nw, nu, X + cx, Y + cy, Z + cz, i + 1, Pw, Dw);
+                        const bool same = iu && Pw.x == Pu.x && Pw.y == Pu.y && Pw.z == Pu.z && Dw.x == Du.x &&
+                                          Dw.y == Du.y && Dw.z == Du.z;
+                        tw = same ? tu : seg_cross(g, Pw, Dw);
+                    }
+                    if (tu < 0.f && tw < 0.f) continue;
+                    // the owners and the list places of both ends, loaded together
+                    const uint16_t ou = d.owner[nu], ow = d.owner[nw];
+                    const int bu = d.bidx[nu], bw = d.bidx[nw];
+                    if (ou == ow || ou == 0xFFFF || ow == 0xFFFF) continue;
+                    // each end searches the capsule it lies in, else the one across the link
+                    if (tu >= 0.f && (ou != 0 ? ou : ow) - 1 == g.k) end_record(d, g, bu, i, tu);
+                    if (tw >= 0.f && (ow != 0 ? ow : ou) - 1 == g.k) end_record(d, g, bw, i + 1, tw);
+                }
+            }
     }
 }
 
@@ -546,14 +580,357 @@ void launch_bb_boundary_list(const LbmParams& p, const DevState& d, cudaStream_t
     const int w = d.CW + 2;
     dim3 gm((w * w * w + 127) / 128, d.NM);
     launch_k(k_boundary_mark, dim3(gm), dim3(128), 0, st, p, d);
-    static const int per_sm = occupancy((const void*)k_boundary_elements, BE_WARPS * 32);
-    launch_k(k_boundary_elements, dim3(fill_grid(per_sm, ((size_t)d.maxB + BE_WARPS - 1) / BE_WARPS)), dim3(BE_WARPS * 32), 0, st, p,
-                                                                                                             d);
+    if (d.NT < 65536) launch_k(k_link_cross<9>, dim3(((size_t)d.NT * 9 + 127) / 128), dim3(128), 0, st, p, d);
+    else launch_k(k_link_cross<3>, dim3(((size_t)d.NT * 3 + 127) / 128), dim3(128), 0, st, p, d);
 }
 
 // ------------------------------------------------------------------------------------------------------
 // Boundary kernel: collision and streaming of the nodes with cut links
 // ------------------------------------------------------------------------------------------------------
+
+// Compile-time loop over the directions: f(std::integral_constant<int, I>) for I = A .. B-1.
+template <int A, int B, class F>
+__device__ __forceinline__ void for_dirs(F&& f) {
+    if constexpr (A < B) {
+        f(std::integral_constant<int, A>{});
+        for_dirs<A + 1, B>(f);
+    }
+}
+
+// c_i . v with only the nonzero terms of c_i, in x, y, z order (a product by a zero component is not folded
+// away under IEEE rules)
+template <int I>
+__device__ __forceinline__ float c_dot(float vx, float vy, float vz) {
+    float r = 0.f;
+    bool first = true;
+    auto add = [&](int c, float v) {
+        if (c == 0) return;
+        const float t = c > 0 ? v : -v;
+        r = first ? t : r + t;
+        first = false;
+    };
+    add(dir_x(I), vx);
+    add(dir_y(I), vy);
+    add(dir_z(I), vz);
+    return r;
+}
+
+// The lattice neighbourhood of a fluid node: its wrapped coordinates x, y, z and those of x +- 1, y +- 1,
+// z +- 1 (z unwrapped between walls, where a fluid node's z +- 1 is in range).
+struct Nbhd {
+    int x, y, z, xs[3], ys[3], zs[3];   // [1 + c]: coordinate of x + c
+    __device__ __forceinline__ Nbhd(const LbmParams& p, int n) {
+        z = n / p.nxy;
+        const int r = n - z * p.nxy;
+        y = r / p.nx;
+        x = r - y * p.nx;
+        xs[0] = wrapf(x - 1, p.nx); xs[1] = x; xs[2] = wrapf(x + 1, p.nx);
+        ys[0] = wrapf(y - 1, p.ny); ys[1] = y; ys[2] = wrapf(y + 1, p.ny);
+        zs[0] = p.walls ? z - 1 : wrapf(z - 1, p.nz); zs[1] = z; zs[2] = p.walls ? z + 1 : wrapf(z + 1, p.nz);
+    }
+    // linear index of x + (cx, cy, cz)
+    __device__ __forceinline__ unsigned at(const LbmParams& p, int cx, int cy, int cz) const {
+        return (unsigned)xs[1 + cx] + (unsigned)ys[1 + cy] * (unsigned)p.nx + (unsigned)zs[1 + cz] * p.nxy;
+    }
+};
+
+// The fallback element of a cut link (node x, y, z, direction i) with no crossing: the triangle of capsule cap
+// whose centroid is nearest the link's midpoint, lower id on ties; the whole warp searches (warp-convergent
+// call), every lane gets the result.
+__device__ __forceinline__ int nearest_centroid(const LbmParams& p, const DevState& d, int cap, int x, int y, int z,
+                                                int i, int lane) {
+    const CapDev cp = d.cap[cap];
+    const double* cr = d.cap_red + 4 * cap;
+    const float px = near_image(x, (float)cr[1], p.nx, true) + BB_EPSX;
+    const float py = near_image(y, (float)cr[2], p.ny, true) + BB_EPSY;
+    const float pz = near_image(z, (float)cr[3], p.nz, !p.walls) + BB_EPSZ;
+    const float mx = px + 0.5f * dir_x(i), my = py + 0.5f * dir_y(i), mz = pz + 0.5f * dir_z(i);
+    float bd = 1e30f;
+    int be = -1;
+    for (int tl = lane; tl < cp.nt; tl += 32) {
+        const int t = cp.t0 + tl;
+        const float3 cc = f3(d.trec[4 * t + 3]);
+        const float3 dd = make_float3(cc.x - mx, cc.y - my, cc.z - mz);
+        const float d2 = dot(dd, dd);
+        if (d2 < bd || (d2 == bd && t < be)) { bd = d2; be = t; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float b2 = __shfl_xor_sync(0xffffffffu, bd, o);
+        const int e2 = __shfl_xor_sync(0xffffffffu, be, o);
+        if (e2 >= 0 && (be < 0 || b2 < bd || (b2 == bd && e2 < be))) { bd = b2; be = e2; }
+    }
+    return be;
+}
+
+// Every boundary node m, one thread each: mean density of its neighbours on the other side of the membrane.
+// A node x that sees m across a cut link needs the mean over m's neighbours on x's side (Eq. 14); when m
+// borders a single other side that is the same set, so it is computed once per m (otherwise flagged, and
+// recomputed per link).
+// The same pass settles the element of each of m's cut links for the boundary kernel: the nearest crossing
+// the element search recorded, else (no crossing, by round-off) the triangle of the searched capsule whose
+// centroid is nearest the link's midpoint, lower id on ties, found by the whole warp.
+__global__ void __launch_bounds__(256) k_bb_vrho(LbmParams p, DevState d) {
+    pdl_wait();
+    pdl_trigger();
+    const int nb = min(d.cnt[0], d.maxB);
+    const int lane = threadIdx.x & 31;
+    // whole warps go round the loop together (the fallback search below takes every lane)
+    for (int b0 = blockIdx.x * blockDim.x + threadIdx.x - lane; b0 < nb; b0 += gridDim.x * blockDim.x) {
+        const int b = b0 + lane;
+        unsigned miss = 0;
+        int x = 0, y = 0, z = 0;
+        uint16_t me = 0;
+        if (b < nb) {
+            const int m = d.blist[b];
+            const Nbhd nh(p, m);
+            x = nh.x; y = nh.y; z = nh.z;
+            me = d.owner[m];
+            float a = 0.f, c = 0.f, cnt = 0.f;
+            int omin = 0x10000, omax = -1;
+            for_dirs<1, Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                int e = -1;
+                if (!wall_z(p, z + dir_z(i))) {
+                    const unsigned q = nh.at(p, dir_x(i), dir_y(i), dir_z(i));
+                    const uint16_t oq = d.owner[q];
+                    if (oq != 0xFFFF && oq != me) {
+                        a += d.rho[q];
+                        c += d.rho[p.N + q];
+                        cnt += 1.f;
+                        omin = min(omin, (int)oq);
+                        omax = max(omax, (int)oq);
+                        const unsigned long long key = d.bkey[(size_t)b * (Q - 1) + (i - 1)];
+                        if (key != ~0ull) e = (int)(unsigned)(key & 0xffffffffull);
+                        else miss |= 1u << i;
+                    }
+                }
+                d.belem[(size_t)b * (Q - 1) + (i - 1)] = e;
+            });
+            d.vrho[m] = make_float4(cnt > 0.f ? a / cnt : 0.f, cnt > 0.f ? c / cnt : 0.f, cnt, omin != omax ? 1.f : 0.f);
+        }
+        unsigned who = __ballot_sync(0xffffffffu, miss != 0);
+        while (who) {
+            const int src = __ffs(who) - 1;
+            who &= who - 1;
+            unsigned mm = __shfl_sync(0xffffffffu, miss, src);
+            const int sx = __shfl_sync(0xffffffffu, x, src), sy = __shfl_sync(0xffffffffu, y, src),
+                      sz = __shfl_sync(0xffffffffu, z, src), sb = __shfl_sync(0xffffffffu, b, src);
+            const int sme = __shfl_sync(0xffffffffu, (int)me, src);
+            while (mm) {
+                const int i = __ffs(mm) - 1;
+                mm &= mm - 1;
+                const long long q = node_of(p, sx + dir_x(i), sy + dir_y(i), sz + dir_z(i));
+                const int cap = (sme != 0 ? sme : (int)d.owner[q]) - 1;
+                const int be = nearest_centroid(p, d, cap, sx, sy, sz, i, lane);
+                if (lane == src) {
+                    d.belem[(size_t)sb * (Q - 1) + (i - 1)] = be;
+                    atomicAdd(d.cnt + 6, 1);
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Boundary kernel, one thread per boundary node: pull, moments, Shan-Chen force with virtual densities
+// across cut links and the wetting offset (Eq. 13-15; reactions to the crossed element), BGK collision,
+// streaming with moving half-way bounce-back on walls and cut links (Eq. 11) and the exchanged momentum
+// (Eq. 12).
+// ------------------------------------------------------------------------------------------------------
+// Returns the mass change (A, B) of the node's moving bounce-back links (Eq. 11).
+template <typename T>
+__device__ __forceinline__ float2 boundary_node(const LbmParams& p, const DevState& d, const T* __restrict__ S,
+                                                T* __restrict__ D, const float* __restrict__ ghost, const int step,
+                                                int* err, const int b) {
+    const int n = d.blist[b];
+    const Nbhd nh(p, n);
+    const int z = nh.z;
+    const uint16_t me = d.owner[n];
+    const int pr = step & 1;
+    // ---- pull (a deviation storage keeps f - w rref: the reference is added back)
+    float fa[Q], fb[Q];
+    float ra = 0.f, rb = 0.f;
+    for_dirs<0, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        const unsigned src = nh.at(p, -dir_x(i), -dir_y(i), -dir_z(i));
+        fa[i] = pld(S + (size_t)i * p.N + src) + dir_w(i) * dev_ref<T>(p, 0);
+        fb[i] = pld(S + (size_t)(Q + i) * p.N + src) + dir_w(i) * dev_ref<T>(p, 1);
+        ra += fa[i];
+        rb += fb[i];
+    });
+    float jx = 0.f, jy = 0.f, jz = 0.f;
+    for_dirs<1, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        const float s = fa[i] + fb[i];
+        if constexpr (dir_x(i) != 0) jx += dir_x(i) > 0 ? s : -s;
+        if constexpr (dir_y(i) != 0) jy += dir_y(i) > 0 ? s : -s;
+        if constexpr (dir_z(i) != 0) jz += dir_z(i) > 0 ? s : -s;
+    });
+    const float pa = psi_fn(ra, p.psi_kind), pb = psi_fn(rb, p.psi_kind);
+    // ---- neighbour along c_i: wall (ghost density), same side, or across a cut link (virtual density with the
+    // crossed element's colour); the links that bounce back are the cut ones with an element
+    const float drho = (float)(d.rho_maj - d.rho_min);
+    float sa0 = 0.f, sa1 = 0.f, sa2 = 0.f, sb0 = 0.f, sb1 = 0.f, sb2 = 0.f;
+    unsigned bounce = 0;
+    for_dirs<1, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr float wi = dir_w(i);
+        const int zn = z + dir_z(i);
+        float psA = 0.f, psB = 0.f;
+        if (wall_z(p, zn)) {
+            const int w = zn == 0 ? 0 : 1;
+            const int rr = nh.xs[1 + dir_x(i)] + nh.ys[1 + dir_y(i)] * p.nx;
+            psA = psi_fn(ghost[(w * 2 + 0) * p.nxy + rr], p.psi_kind);
+            psB = psi_fn(ghost[(w * 2 + 1) * p.nxy + rr], p.psi_kind);
+        } else {
+            const unsigned m = nh.at(p, dir_x(i), dir_y(i), dir_z(i));
+            const uint16_t om = d.owner[m];
+            if (om == me) {
+                psA = psi_fn(d.rho[m], p.psi_kind);
+                psB = psi_fn(d.rho[p.N + m], p.psi_kind);
+            } else {
+                const int e = d.belem[(size_t)b * (Q - 1) + (i - 1)];
+                float vA, vB;
+                const float4 vr = d.vrho[m];
+                if (vr.w == 0.f) {
+                    vA = vr.x;
+                    vB = vr.y;
+                } else {
+                    // m borders more than one other side: mean over its neighbours on this node's side
+                    const Nbhd mh(p, (int)m);
+                    float sA = 0.f, sB = 0.f;
+                    int cnt = 0;
+                    for (int q = 1; q < Q; q++) {
+                        if (wall_z(p, mh.z + dir_z(q))) continue;
+                        const unsigned qq = mh.at(p, dir_x(q), dir_y(q), dir_z(q));
+                        if (d.owner[qq] != me) continue;
+                        sA += d.rho[qq];
+                        sB += d.rho[p.N + qq];
+                        cnt++;
+                    }
+                    vA = cnt ? sA / cnt : ra;
+                    vB = cnt ? sB / cnt : rb;
+                }
+                if (e >= 0) {
+                    const float col = d.tcol[e];     // the crossed element's colour (per capsule or per element)
+                    const float rv = 2.f * fabsf(col) * drho;
+                    if (col > 0.f) vA += rv;
+                    else if (col < 0.f) vB += rv;
+                    psA = psi_fn(vA, p.psi_kind);
+                    psB = psi_fn(vB, p.psi_kind);
+                    // reaction of both components on the element: + psi^c(x) G w_i psi^{c'}(virtual) c_i
+                    const float a = p.G * wi * (pa * psB + pb * psA);
+                    atomicAdd(&d.epend[pr * d.NT + e], make_float4(a * dir_x(i), a * dir_y(i), a * dir_z(i), 0.f));
+                    bounce |= 1u << i;
+                } else {
+                    atomicOr(err, 2);      // list out of step with the owner field: never expected
+                }
+            }
+        }
+        const float qa = wi * psA, qb = wi * psB;
+        if constexpr (dir_x(i) != 0) { sa0 += dir_x(i) > 0 ? qa : -qa; sb0 += dir_x(i) > 0 ? qb : -qb; }
+        if constexpr (dir_y(i) != 0) { sa1 += dir_y(i) > 0 ? qa : -qa; sb1 += dir_y(i) > 0 ? qb : -qb; }
+        if constexpr (dir_z(i) != 0) { sa2 += dir_z(i) > 0 ? qa : -qa; sb2 += dir_z(i) > 0 ? qb : -qb; }
+    });
+    const float FA[3] = {-pa * p.G * sb0 + ra * p.g[0], -pa * p.G * sb1 + ra * p.g[1], -pa * p.G * sb2 + ra * p.g[2]};
+    const float FB[3] = {-pb * p.G * sa0 + rb * p.g[0], -pb * p.G * sa1 + rb * p.g[1], -pb * p.G * sa2 + rb * p.g[2]};
+    const float rt = ra + rb, irt = 1.f / rt;
+    const float ux = jx * irt, uy = jy * irt, uz = jz * irt;
+    if (!(rt > 0.f) || !(ux * ux + uy * uy + uz * uz <= 0.09f)) atomicOr(err, 1);
+    const float ta = ra > 0.f ? p.tau / ra : 0.f, tb = rb > 0.f ? p.tau / rb : 0.f;
+    const float uA[3] = {ux + ta * FA[0], uy + ta * FA[1], uz + ta * FA[2]};
+    const float uB[3] = {ux + tb * FB[0], uy + tb * FB[1], uz + tb * FB[2]};
+    const float uuA = uA[0] * uA[0] + uA[1] * uA[1] + uA[2] * uA[2];
+    const float uuB = uB[0] * uB[0] + uB[1] * uB[1] + uB[2] * uB[2];
+    // ---- equilibrium (Eq. 2) and collision; the rest population closes the mass
+    float sA = 0.f, sB = 0.f;
+    for_dirs<1, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr float wi = dir_w(i);
+        const float cuA = c_dot<i>(uA[0], uA[1], uA[2]), cuB = c_dot<i>(uB[0], uB[1], uB[2]);
+        const float eA = wi * ra * (1.f + 3.f * cuA + 4.5f * cuA * cuA - 1.5f * uuA);
+        const float eB = wi * rb * (1.f + 3.f * cuB + 4.5f * cuB * cuB - 1.5f * uuB);
+        sA += eA;
+        sB += eB;
+        fa[i] = fa[i] + p.omega * (eA - fa[i]);
+        fb[i] = fb[i] + p.omega * (eB - fb[i]);
+    });
+    fa[0] = fa[0] + p.omega * ((ra - sA) - fa[0]);
+    fb[0] = fb[0] + p.omega * ((rb - sB) - fb[0]);
+    // ---- streaming (a deviation storage keeps f - w rref; opposite directions share their weight)
+    float dmA = 0.f, dmB = 0.f;
+    pst(D + n, fa[0] - dir_w(0) * dev_ref<T>(p, 0));
+    pst(D + (size_t)Q * p.N + n, fb[0] - dir_w(0) * dev_ref<T>(p, 1));
+    for_dirs<1, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int io = dir_opp(i);
+        const float gA = dir_w(i) * dev_ref<T>(p, 0), gB = dir_w(i) * dev_ref<T>(p, 1);
+        const float oA = fa[i], oB = fb[i];
+        const int zn = z + dir_z(i);
+        if (wall_z(p, zn)) {
+            const float* U = zn == 0 ? p.ulo : p.uhi;
+            const float cU = 6.f * dir_w(i) * (dir_x(i) * U[0] + dir_y(i) * U[1] + dir_z(i) * U[2]);
+            const unsigned tgt = (unsigned)(nh.xs[1 + dir_x(i)] + nh.ys[1 + dir_y(i)] * p.nx) + (unsigned)zn * p.nxy;
+            pst(D + (size_t)io * p.N + tgt, oA - cU * ra - gA);
+            pst(D + (size_t)(Q + io) * p.N + tgt, oB - cU * rb - gB);
+        } else if (!((bounce >> i) & 1u)) {
+            pst(D + (size_t)i * p.N + n, oA - gA);
+            pst(D + (size_t)(Q + i) * p.N + n, oB - gB);
+        } else {
+            // moving half-way bounce-back (Eq. 11) with the element velocity; exchanged momentum (Eq. 12)
+            const unsigned m = nh.at(p, dir_x(i), dir_y(i), dir_z(i));
+            const int e = d.belem[(size_t)b * (Q - 1) + (i - 1)];
+            const int4 Te = d.tri[e];
+            const float4 V0 = d.V[Te.x], V1 = d.V[Te.y], V2 = d.V[Te.z];
+            const float vx = (V0.x + V1.x + V2.x) * (1.f / 3.f), vy = (V0.y + V1.y + V2.y) * (1.f / 3.f),
+                        vz = (V0.z + V1.z + V2.z) * (1.f / 3.f);
+            const float cv = 6.f * dir_w(i) * (dir_x(i) * vx + dir_y(i) * vy + dir_z(i) * vz);
+            const float bA = oA - cv * ra, bB = oB - cv * rb;
+            pst(D + (size_t)io * p.N + m, bA - gA);
+            pst(D + (size_t)(Q + io) * p.N + m, bB - gB);
+            const float dp = oA + bA + oB + bB;
+            atomicAdd(&d.emom[pr * d.NT + e], make_float4(dp * dir_x(i), dp * dir_y(i), dp * dir_z(i), 0.f));
+            dmA += bA - oA;
+            dmB += bB - oB;
+        }
+    });
+    return make_float2(dmA, dmB);
+}
+
+// Grid-stride over the boundary list, a thread per node; each block writes the sum of its nodes' mass changes,
+// in a fixed order, to bdm[blockIdx.x] and block 0 records the number of partials.
+constexpr int BT_THREADS = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(BT_THREADS) k_boundary(LbmParams p, DevState d, const T* __restrict__ S,
+                                                         T* __restrict__ D, const float* __restrict__ ghost,
+                                                         int step, int* err) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ float2 part[BT_THREADS / 32];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nb = min(d.cnt[0], d.maxB);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int b = blockIdx.x * BT_THREADS + threadIdx.x; b < nb; b += gridDim.x * BT_THREADS) {
+        const float2 v = boundary_node<T>(p, d, S, D, ghost, step, err, b);
+        acc.x += v.x;
+        acc.y += v.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) part[wl] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float2 t = part[0];
+        for (int w = 1; w < BT_THREADS / 32; w++) { t.x += part[w].x; t.y += part[w].y; }
+        d.bdm[blockIdx.x] = t;
+        if (blockIdx.x == 0) d.cnt[5] = (int)gridDim.x;
+    }
+}
 
 __device__ __forceinline__ float wsum(float v) {
 #pragma unroll
@@ -561,58 +938,68 @@ __device__ __forceinline__ float wsum(float v) {
     return v;
 }
 
-// Every boundary node m: mean density of its neighbours on the other side of the membrane (one warp per
-// node, lane i-1 looks at direction i).  A node x that sees m across a cut link needs the mean over m's
-// neighbours on x's side (Eq. 14); when m borders a single other side that is the same set, so it is
-// computed once per m (otherwise flagged, and recomputed per link).
-__device__ __forceinline__ void node_vrho(const LbmParams& p, const DevState& d, const int b, const int lane) {
-    const int m = d.blist[b];
-    const int z = m / p.nxy, r = m - z * p.nxy, y = r / p.nx, x = r - y * p.nx;
-    const uint16_t me = d.owner[m];
-    float a = 0.f, c = 0.f, cnt = 0.f;
-    int omin = 0x10000, omax = -1;
-    if (lane < Q - 1) {
-        const int i = lane + 1;
-        const long long q = node_of(p, x + dir_x(i), y + dir_y(i), z + dir_z(i));
-        if (q >= 0) {
-            const uint16_t oq = d.owner[q];
-            if (oq != 0xFFFF && oq != me) {
-                a = d.rho[q];
-                c = d.rho[p.N + q];
-                cnt = 1.f;
-                omin = omax = oq;
-            }
-        }
-    }
-    a = wsum(a);
-    c = wsum(c);
-    cnt = wsum(cnt);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        omin = min(omin, __shfl_xor_sync(0xffffffffu, omin, o));
-        omax = max(omax, __shfl_xor_sync(0xffffffffu, omax, o));
-    }
-    if (lane == 0)
-        d.vrho[m] = make_float4(cnt > 0.f ? a / cnt : 0.f, cnt > 0.f ? c / cnt : 0.f, cnt, omin != omax ? 1.f : 0.f);
-}
-
-__global__ void __launch_bounds__(256) k_bb_vrho(LbmParams p, DevState d) {
+// k_bb_vrho with one warp per node, lane i-1 looking at direction i (the short-list form, beside
+// k_boundary_warp).
+__global__ void __launch_bounds__(256) k_bb_vrho_warp(LbmParams p, DevState d) {
     pdl_wait();
     pdl_trigger();
     const int nb = min(d.cnt[0], d.maxB);
-    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += (gridDim.x * blockDim.x) >> 5)
-        node_vrho(p, d, b, threadIdx.x & 31);
+    const int lane = threadIdx.x & 31;
+    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += (gridDim.x * blockDim.x) >> 5) {
+        const int m = d.blist[b];
+        const int z = m / p.nxy, r = m - z * p.nxy, y = r / p.nx, x = r - y * p.nx;
+        const uint16_t me = d.owner[m];
+        float a = 0.f, c = 0.f, cnt = 0.f;
+        int omin = 0x10000, omax = -1;
+        int e = -1, my_cap = -1;
+        if (lane < Q - 1) {
+            const int i = lane + 1;
+            const long long q = node_of(p, x + dir_x(i), y + dir_y(i), z + dir_z(i));
+            if (q >= 0) {
+                const uint16_t oq = d.owner[q];
+                if (oq != 0xFFFF && oq != me) {
+                    a = d.rho[q];
+                    c = d.rho[p.N + q];
+                    cnt = 1.f;
+                    omin = omax = oq;
+                    my_cap = (me != 0 ? me : oq) - 1;
+                    const unsigned long long key = d.bkey[(size_t)b * (Q - 1) + lane];
+                    if (key != ~0ull) e = (int)(unsigned)(key & 0xffffffffull);
+                }
+            }
+        }
+        a = wsum(a);
+        c = wsum(c);
+        cnt = wsum(cnt);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            omin = min(omin, __shfl_xor_sync(0xffffffffu, omin, o));
+            omax = max(omax, __shfl_xor_sync(0xffffffffu, omax, o));
+        }
+        if (lane == 0)
+            d.vrho[m] = make_float4(cnt > 0.f ? a / cnt : 0.f, cnt > 0.f ? c / cnt : 0.f, cnt, omin != omax ? 1.f : 0.f);
+        unsigned mm = __ballot_sync(0xffffffffu, my_cap >= 0 && e < 0);
+        while (mm) {
+            const int li = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const int i = li + 1;
+            const int cap = __shfl_sync(0xffffffffu, my_cap, li);
+            const int be = nearest_centroid(p, d, cap, x, y, z, i, lane);
+            if (lane == li) {
+                e = be;
+                atomicAdd(d.cnt + 6, 1);
+            }
+        }
+        if (lane < Q - 1) d.belem[(size_t)b * (Q - 1) + lane] = e;
+    }
 }
 
-// ------------------------------------------------------------------------------------------------------
-// Boundary kernel: one warp per boundary node, lane i owns direction i (i = 0..18).  Pull, moments by warp
-// reductions, Shan-Chen force with virtual densities across cut links and the wetting offset
-// (Eq. 13-15; reactions to the crossed element), BGK collision, streaming with moving half-way
-// bounce-back on walls and cut links (Eq. 11) and the exchanged momentum (Eq. 12).
-// ------------------------------------------------------------------------------------------------------
+// The same boundary update with one warp per node, lane i owning direction i (i = 0..18), moments and force sums
+// by warp reductions: each node's links run side by side, which suits short lists (a few capsules), where the
+// thread-per-node form leaves most SMs idle and each thread waits through its links one after another.
 // Returns the mass change (A, B) of the node's moving bounce-back links (Eq. 11), in every lane.
 template <typename T>
-__device__ __forceinline__ float2 boundary_node(const LbmParams& p, const DevState& d, const T* __restrict__ S,
+__device__ __forceinline__ float2 boundary_node_warp(const LbmParams& p, const DevState& d, const T* __restrict__ S,
                                                 T* __restrict__ D, const float* __restrict__ ghost, const int step,
                                                 int* err, const int b, const int lane) {
     const int n = d.blist[b];
@@ -757,7 +1144,7 @@ __device__ __forceinline__ float2 boundary_node(const LbmParams& p, const DevSta
 // Grid-stride over the boundary list, 8 warps per block; each block writes the sum of its nodes' mass
 // changes, in a fixed order, to bdm[blockIdx.x] and block 0 records the number of partials.
 template <typename T>
-__global__ void __launch_bounds__(256) k_boundary(LbmParams p, DevState d, const T* __restrict__ S,
+__global__ void __launch_bounds__(256) k_boundary_warp(LbmParams p, DevState d, const T* __restrict__ S,
                                                   T* __restrict__ D, const float* __restrict__ ghost,
                                                   int step, int* err) {
     pdl_wait();
@@ -767,7 +1154,7 @@ __global__ void __launch_bounds__(256) k_boundary(LbmParams p, DevState d, const
     const int nb = min(d.cnt[0], d.maxB);
     float2 acc = make_float2(0.f, 0.f);
     for (int b = blockIdx.x * 8 + wl; b < nb; b += gridDim.x * 8) {
-        const float2 v = boundary_node<T>(p, d, S, D, ghost, step, err, b, lane);
+        const float2 v = boundary_node_warp<T>(p, d, S, D, ghost, step, err, b, lane);
         acc.x += v.x;
         acc.y += v.y;
     }
@@ -781,17 +1168,49 @@ __global__ void __launch_bounds__(256) k_boundary(LbmParams p, DevState d, const
     }
 }
 
+// A list of this capacity or more takes the thread-per-node forms, a shorter one the warp-per-node forms
+// (SCBB_BOUNDARY_FORM=warp or thread forces one).
+constexpr int THREAD_FORM_NODES = 65536;
+static bool thread_form(const DevState& d) {
+    static const int force = [] {
+        const char* e = getenv("SCBB_BOUNDARY_FORM");
+        if (e && !strcmp(e, "warp")) return 0;
+        if (e && !strcmp(e, "thread")) return 1;
+        return -1;
+    }();
+    return force >= 0 ? force == 1 : d.maxB >= THREAD_FORM_NODES;
+}
+
+void launch_bb_vrho(const LbmParams& p, const DevState& d, cudaStream_t st) {
+    if (d.NM == 0) return;
+    if (thread_form(d)) {
+        const size_t need = ((size_t)d.maxB + 255) / 256;
+        static const int per_v = occupancy((const void*)k_bb_vrho, 256);
+        launch_k(k_bb_vrho, dim3(fill_grid(per_v, need)), dim3(256), 0, st, p, d);
+    } else {
+        const size_t need = ((size_t)d.maxB + 7) / 8;
+        static const int per_v = occupancy((const void*)k_bb_vrho_warp, 256);
+        launch_k(k_bb_vrho_warp, dim3(fill_grid(per_v, need)), dim3(256), 0, st, p, d);
+    }
+}
+
 void launch_bb_boundary(const LbmParams& p, const DevState& d, const float* S, float* D, const float* ghost,
                         int step, int* err, cudaStream_t st) {
     if (d.NM == 0) return;
-    const size_t need = ((size_t)d.maxB + 7) / 8;   // 8 warps per block; the partials fit in bdm[maxB]
-    static const int per_v = occupancy((const void*)k_bb_vrho, 256);
-    launch_k(k_bb_vrho, dim3(fill_grid(per_v, need)), dim3(256), 0, st, p, d);
+    launch_bb_vrho(p, d, st);
     with_storage(p.store, [&](auto* tag) {
         using T = std::remove_pointer_t<decltype(tag)>;
-        static const int per_b = occupancy((const void*)k_boundary<T>, 256);
-        launch_k(k_boundary<T>, dim3(fill_grid(per_b, need)), dim3(256), 0, st, p, d, reinterpret_cast<const T*>(S),
-                                                              reinterpret_cast<T*>(D), ghost, step, err);
+        if (thread_form(d)) {
+            const size_t need = ((size_t)d.maxB + BT_THREADS - 1) / BT_THREADS;   // the partials fit in bdm[maxB]
+            static const int per_b = occupancy((const void*)k_boundary<T>, BT_THREADS);
+            launch_k(k_boundary<T>, dim3(fill_grid(per_b, need)), dim3(BT_THREADS), 0, st, p, d,
+                     reinterpret_cast<const T*>(S), reinterpret_cast<T*>(D), ghost, step, err);
+        } else {
+            const size_t need = ((size_t)d.maxB + 7) / 8;   // 8 warps per block; the partials fit in bdm[maxB]
+            static const int per_b = occupancy((const void*)k_boundary_warp<T>, 256);
+            launch_k(k_boundary_warp<T>, dim3(fill_grid(per_b, need)), dim3(256), 0, st, p, d,
+                     reinterpret_cast<const T*>(S), reinterpret_cast<T*>(D), ghost, step, err);
+        }
     });
 }
 
@@ -1053,6 +1472,7 @@ __global__ void k_bb_init(LbmParams p, DevState d) {
     if (n < p.N) {
         const int z = n / p.nxy;
         d.owner[n] = wall_z(p, z) ? (uint16_t)0xFFFF : (uint16_t)0;
+        d.bidx[n] = -1;
         if ((n & 31) == 0) { d.bmask[n >> 5] = 0u; d.fmask[n >> 5] = 0u; }
     }
     if (n < 2u * d.NT) {

@@ -280,6 +280,8 @@ size_t layout(const scbb_lattice* lat, const scbb_fluid* fl, int nm, const scbb_
         t.blist = c.take<int>(z.maxB);
         t.bdm = c.take<float2>(z.maxB);
         t.belem = c.take<int>((size_t)z.maxB * (Q - 1));
+        t.bkey = c.take<unsigned long long>((size_t)z.maxB * (Q - 1));
+        t.bidx = c.take<int>(N);
         t.flist = c.take<int>(z.maxF);
         t.fold = c.take<int>(z.maxF);
         t.fnew = c.take<float4>((size_t)2 * z.maxF);
@@ -1118,6 +1120,32 @@ scbb_status scbb_get_owner(scbb_ctx* c, unsigned short* owner, int* n_boundary, 
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
     if (n_boundary) *n_boundary = h[0];
     if (n_fresh) *n_fresh = h[1];
+    return check_device_error(c);
+}
+
+scbb_status scbb_get_boundary(scbb_ctx* c, int max_nodes, int* nodes, int* elems, int* n_boundary,
+                              int* n_fallback) {
+    if (!c || max_nodes < 0 || (max_nodes > 0 && (!nodes || !elems))) return SCBB_E_INVAL;
+    if (c->broken) return SCBB_E_STATE;
+    if (!c->d.owner) return SCBB_E_UNSUPPORTED;
+    // the elements are settled by the first pass of the next step's boundary phase; run that pass now (the
+    // virtual densities it also writes are recomputed by that step)
+    CUDA_TRY(c, cudaMemsetAsync(c->d.cnt + 6, 0, sizeof(int), c->st));
+    launch_bb_vrho(c->lp, c->d, c->st);
+    c->launches++;
+    int h[7] = {0, 0, 0, 0, 0, 0, 0};
+    CUDA_TRY(c, cudaMemcpyAsync(h, c->d.cnt, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    const int nb = std::min(h[0], c->d.maxB);
+    const int k = std::min(nb, max_nodes);
+    if (k > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(nodes, c->d.blist, sizeof(int) * k, cudaMemcpyDeviceToHost, c->st));
+        CUDA_TRY(c, cudaMemcpyAsync(elems, c->d.belem, sizeof(int) * (size_t)k * (Q - 1), cudaMemcpyDeviceToHost,
+                                    c->st));
+        CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    }
+    if (n_boundary) *n_boundary = nb;
+    if (n_fallback) *n_fallback = h[6];
     return check_device_error(c);
 }
 

@@ -271,18 +271,23 @@ struct DevState {
     float2* bdm;            // [maxB] mass change (A, B) of the bounce-back links, one partial per block of the
                             //     boundary kernel (cnt[5] partials)
     int* belem;             // [maxB][18] element crossed by the link along direction i (slot i-1), -1 if uncut
+    unsigned long long* bkey;   // [maxB][18] nearest crossing found so far: (parameter bits << 32) | triangle
+    int* bidx;              // [N] place in the boundary list of each node listed by the last list build (-1: the
+                            //     list was full); stale for the other nodes
     int* flist;             // [maxF] fresh nodes
     int* fold;              // [maxF] their owner before the change
     float4* fnew;           // [maxF][2] new (rhoA, rhoB, ok, -) and (vx, vy, vz, element)
     int* cnt;               // [8] 0: boundary nodes, 1: fresh nodes, 2: overflow flags, 4: fresh nodes of the
-                            //     previous step (saved before re-listing), 5: partials in bdm
+                            //     previous step (saved before re-listing), 5: partials in bdm, 6: cut links
+                            //     whose element came from the nearest-centroid rule (running count)
     float4* emom;           // [2][NT] exchanged momentum (Eq. 12) by step parity
     float4* epend;          // [2][NT] Shan-Chen reactions and fresh-node momenta by step parity
     int4* cbox;             // [NM][2] classification box (lo, hi), unwrapped lattice coordinates
     int* ccnt;              // [NM][CW*CW] crossings per column
     float* czs;             // [NM][CW*CW][MAXC] crossing heights
     float2* fdm;            // [maxF] mass change (A, B) of each fresh node's replacement
-    float4* trec;           // [NT][4] vertex positions and centroid of every triangle at X(t+1)
+    float4* trec;           // [NT][4] vertex positions and centroid of every triangle at X(t+1); the centroid's w
+                            //     holds the triangle's capsule (int bits)
     int* tcnt;              // [NM][CW*CW] triangles whose xy bounding box overlaps each column cell
     int4* tlst;             // [NM][CW*CW][BB_MAXT] their ids and z ranges (t, zmin bits, zmax bits, 0)
     float4* vrho;           // [N] at boundary nodes: mean rho^A, rho^B over neighbours on the other side,

@@ -19,6 +19,7 @@ STATUS = {0: "SCBB_OK", 1: "SCBB_E_INVAL", 2: "SCBB_E_CUDA", 3: "SCBB_E_NOMEM", 
 
 EXPORTS = ["scbb_workspace_bytes", "scbb_create", "scbb_set_density", "scbb_step", "scbb_sync",
            "scbb_get_fields", "scbb_get_populations", "scbb_get_vertices", "scbb_get_diag", "scbb_get_owner",
+           "scbb_get_boundary",
            "scbb_launch_count", "scbb_enable_timing", "scbb_kernel_time", "scbb_phase_times", "scbb_autotune",
            "scbb_set_wait_limit",
            "scbb_population_moments_noalloc", "scbb_batch_create", "scbb_batch_step", "scbb_batch_destroy",
@@ -82,6 +83,8 @@ def load(path: str = LIB_PATH):
     L.scbb_get_diag.argtypes = [vp, vp, vp, vp, vp]
     L.scbb_get_owner.restype = C.c_int
     L.scbb_get_owner.argtypes = [vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.scbb_get_boundary.restype = C.c_int
+    L.scbb_get_boundary.argtypes = [vp, C.c_int, vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.scbb_launch_count.restype = C.c_longlong
     L.scbb_launch_count.argtypes = [vp]
     L.scbb_enable_timing.restype = C.c_int
@@ -290,6 +293,18 @@ class Sim:
         nb, nf = C.c_int(0), C.c_int(0)
         self._check(self.L.scbb_get_owner(self.h, _p(o), C.byref(nb), C.byref(nf)), "scbb_get_owner")
         return o.reshape(self.prob.nz, self.prob.ny, self.prob.nx), nb.value, nf.value
+
+    def scbb_get_boundary(self):
+        """(boundary nodes int32[n] in the list's order, their links' crossed elements int32[n, 18] (-1: not
+        cut), cut links resolved by the nearest-centroid rule)."""
+        nb, nfb = C.c_int(0), C.c_int(0)
+        self._check(self.L.scbb_get_boundary(self.h, 0, None, None, C.byref(nb), C.byref(nfb)), "scbb_get_boundary")
+        n = nb.value
+        nodes = np.empty(max(n, 1), np.int32)
+        elems = np.empty((max(n, 1), 18), np.int32)
+        self._check(self.L.scbb_get_boundary(self.h, n, _p(nodes), _p(elems), C.byref(nb), C.byref(nfb)),
+                    "scbb_get_boundary")
+        return nodes[:n], elems[:n], nfb.value
 
     def scbb_launch_count(self):
         return int(self.L.scbb_launch_count(self.h))

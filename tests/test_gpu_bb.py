@@ -95,15 +95,177 @@ def test_bb_adsorb128_full_size():
     assert np.abs(Xg - Xo).max() < 1e-4
 
 
+def _three():
+    caps = [inputs.Capsule(centre=(9.7, 10.2, 12.1), radius=5.0, subdiv=3, kS=0.02, kB=1e-3, kV=2.0, colour=0.05),
+            inputs.Capsule(centre=(21.1, 10.6, 11.8), radius=5.0, subdiv=3, kS=0.02, kB=1e-3, kV=2.0, colour=-0.05),
+            inputs.Capsule(centre=(15.6, 21.3, 12.4), radius=5.0, subdiv=3, kS=0.02, kB=1e-3, kV=2.0, colour=0.05)]
+    return inputs.Problem(name="bb3", nx=32, ny=32, nz=24, walls=0, coupling=0, psi_kind=0,
+                          droplet=(16.0, 16.0, 12.0, 7.0), capsules=caps, noise=1e-4, seed=15)
+
+
+def _wrapping():
+    """One capsule across the periodic x and y edges and a second one beside it."""
+    caps = [inputs.Capsule(centre=(0.7, 27.4, 11.9), radius=5.0, subdiv=3, kS=0.02, kB=1e-3, kV=2.0, colour=0.05),
+            inputs.Capsule(centre=(14.3, 13.8, 12.3), radius=6.0, subdiv=3, kS=0.02, kB=1e-3, kV=2.0, colour=-0.05)]
+    return inputs.Problem(name="bbw", nx=32, ny=28, nz=24, walls=0, coupling=0, psi_kind=0, z_interface=12,
+                          capsules=caps, noise=1e-4, seed=21)
+
+
+# D3Q19 directions in the library's order (rest, +x, -x, +y, -y, +z, -z, then the face diagonals in pairs)
+_C = np.array([(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1), (1, 1, 0), (-1, -1, 0),
+               (1, -1, 0), (-1, 1, 0), (1, 0, 1), (-1, 0, -1), (1, 0, -1), (-1, 0, 1), (0, 1, 1), (0, -1, -1),
+               (0, 1, -1), (0, -1, 1)])
+
+
+def _cut_links(prob, own, n):
+    """(direction, neighbour, searched capsule) of every cut link of node n, from an owner field."""
+    nx, ny, nz = prob.nx, prob.ny, prob.nz
+    o = own.ravel()
+    z, r = divmod(int(n), nx * ny)
+    y, x = divmod(r, nx)
+    out = []
+    for i in range(1, 19):
+        zz = z + _C[i, 2]
+        if prob.walls and not 0 <= zz < nz:
+            continue
+        m = (x + _C[i, 0]) % nx + nx * ((y + _C[i, 1]) % ny + ny * (zz % nz))
+        if o[m] == 0xFFFF or o[m] == o[n]:
+            continue
+        out.append((i, m, int(o[n] if o[n] != 0 else o[m]) - 1))
+    return out
+
+
+def _check_elements(prob, g, o, exact):
+    """Every cut link's element from the GPU list against the oracle's search on its own state (Sec. II.C: the
+    crossing nearest the lower-index node).  exact: the two states are the same shapes (no steps yet), so every
+    element must agree; after steps the FP32 and FP64 vertices differ by round-off and a link that meets a shared
+    edge or vertex within it may pick the neighbouring triangle: then the two must share a vertex."""
+    own = o.owner()
+    nodes, elems, n_fb = g.scbb_get_boundary()
+    assert len(nodes) == o.boundary_count()[0] and len(set(nodes.tolist())) == len(nodes)
+    voff = np.cumsum([0] + list(o.nv))[:-1]
+    tri = np.concatenate([np.asarray(t) + off for t, off in zip(o.tris, voff)])     # global vertex ids
+    links = mismatch = 0
+    fb0 = o.boundary_count()[1]
+    for r, n in enumerate(nodes):
+        cut = _cut_links(prob, own, n)
+        assert cut, n
+        want = -np.ones(18, np.int64)
+        for i, m, cap in cut:
+            want[i - 1] = o.crossed_element(cap, int(n), i)
+        assert np.array_equal(want < 0, elems[r] < 0), (n, want, elems[r])
+        for j in np.nonzero(want >= 0)[0]:
+            links += 1
+            if elems[r, j] != want[j]:
+                mismatch += 1
+                assert not exact, (n, j + 1, elems[r, j], want[j])
+                assert set(tri[elems[r, j]]) & set(tri[want[j]]), (n, j + 1)
+    fb = o.boundary_count()[1] - fb0
+    assert links > 0
+    assert mismatch <= 0.01 * links, (mismatch, links)
+    assert n_fb <= fb + 2, (n_fb, fb)
+    return links, mismatch
+
+
+def test_bb_crossed_elements_match_oracle():
+    """The crossed element of every cut link (the triangle-wise search with its atomic minimum over
+    (crossing parameter, triangle id)) equals the oracle's node-wise search: one capsule between walls, the
+    first configuration's capsule, three capsules in a periodic box, a capsule across the periodic edges; then
+    again after 20 coupled steps (not the first configuration's: with bounce-back its A-filled capsule in the
+    B-rich phase drives the flow past the Mach guard)."""
+    for prob, steps in ((_small(), 20), (inputs.cfg_parity(coupling=0), 0), (_three(), 20), (_wrapping(), 20)):
+        g = _sim(prob)
+        o = O.OracleSim(prob)
+        assert np.array_equal(g.scbb_get_owner()[0], o.owner())
+        _check_elements(prob, g, o, exact=True)
+        if not steps:
+            g.close()
+            continue
+        g.scbb_step(steps)
+        o.step(steps)
+        assert np.array_equal(g.scbb_get_owner()[0], o.owner())
+        _check_elements(prob, g, o, exact=False)
+        g.close()
+
+
+def _many():
+    """64 capsules (81,920 triangles) on a 4 x 4 x 4 grid in a periodic 64^3 box across a flat interface: a list
+    long enough for the thread-per-node boundary forms and the three-direction groups of the crossing search."""
+    caps = []
+    for k in range(64):
+        i, j, l = k % 4, (k // 4) % 4, k // 16
+        caps.append(inputs.Capsule(centre=(8.3 + 16 * i, 8.6 + 16 * j, 8.2 + 16 * l), radius=5.0, subdiv=3, kS=0.02,
+                                   kB=1e-3, kV=2.0, colour=0.05 if k % 2 else -0.05))
+    return inputs.Problem(name="bb64", nx=64, ny=64, nz=64, walls=0, coupling=0, psi_kind=0, z_interface=32,
+                          capsules=caps, noise=1e-4, seed=23)
+
+
+def test_bb_thread_forms_against_oracle():
+    """The thread-per-node forms of the boundary pass (virtual densities, elements, boundary update), which
+    lists of 65,536 nodes or more take, against the oracle: forced onto the small problems through a large
+    list capacity (one step node by node, then 20 steps), and on 64 capsules, whose list takes them by itself
+    (the crossing search then runs three directions a thread): one step node by node, then 4 more with the
+    owner field, the elements and each capsule's centre of mass.  (With 230,000 cut links a step, a few links
+    that meet a shared edge within the FP32 / FP64 difference of the vertices pick the neighbouring triangle
+    within those steps; the momentum they exchange then lands on other vertices, which moves single vertices by
+    up to 3e-4 and single boundary densities by 1e-4 relative, in the warp-per-node forms alike.)"""
+    import dataclasses
+    for prob in (_small(), _three()):
+        big = dataclasses.replace(prob, max_boundary=100000)
+        g, o = _sim(big), O.OracleSim(prob)
+        _check_elements(prob, g, o, exact=True)
+        g.scbb_step(1)
+        o.step(1)
+        assert np.array_equal(g.scbb_get_owner()[0], o.owner())
+        assert _cmp_rho(g.scbb_get_fields(), o.fields()) < 1e-5
+        g.scbb_step(19)
+        o.step(19)
+        assert np.array_equal(g.scbb_get_owner()[0], o.owner())
+        assert _cmp_rho(g.scbb_get_fields(), o.fields()) < 1e-5
+        assert np.abs(g.scbb_get_vertices()[0] - o.vertices()[0]).max() < 1e-4
+        _check_elements(prob, g, o, exact=False)
+        g.close()
+    prob = _many()
+    g, o = _sim(prob), O.OracleSim(prob)
+    assert np.array_equal(g.scbb_get_owner()[0], o.owner())
+    _check_elements(prob, g, o, exact=True)
+    g.scbb_step(1)
+    o.step(1)
+    assert np.array_equal(g.scbb_get_owner()[0], o.owner())
+    assert _cmp_rho(g.scbb_get_fields(), o.fields()) < 1e-5
+    assert np.abs(g.scbb_get_vertices()[0] - o.vertices()[0]).max() < 1e-4
+    g.scbb_step(4)
+    o.step(4)
+    assert np.array_equal(g.scbb_get_owner()[0], o.owner())
+    com = np.asarray(g.scbb_get_diag()["com"])
+    assert max(np.abs(com[k] - o.capsule(k)[1]).max() for k in range(len(prob.capsules))) < 1e-5
+    _check_elements(prob, g, o, exact=False)
+    g.close()
+
+
+def test_bb_boundary_readout_leaves_the_run_unchanged():
+    """Reading the boundary list between steps runs the first pass of the next boundary phase early; the
+    continued run matches one that never read it (to the FP32 atomics' summation order: the element momenta
+    are sums of atomics in whatever order they land)."""
+    p = _three()
+    a, b = _sim(p), _sim(p)
+    a.scbb_step(6)
+    b.scbb_step(6)
+    b.scbb_get_boundary()
+    a.scbb_step(6)
+    b.scbb_step(6)
+    assert np.array_equal(a.scbb_get_owner()[0], b.scbb_get_owner()[0])
+    assert np.abs(a.scbb_get_populations() - b.scbb_get_populations()).max() < 1e-6
+    assert np.abs(a.scbb_get_vertices()[0] - b.scbb_get_vertices()[0]).max() < 2e-5     # a few ulp at |x| ~ 30
+    a.close()
+    b.close()
+
+
 def test_bb_three_capsules_periodic():
     """Three capsules with colours +-0.05 and the particle-particle repulsion in a periodic box (a reduced
     stand-in for the droplet-covering workload): 10 steps, owner fields identical, densities within 1e-5,
     vertices within 1e-4."""
-    caps = [inputs.Capsule(centre=(9.7, 10.2, 12.1), radius=5.0, subdiv=3, kS=0.02, kB=1e-3, kV=2.0, colour=0.05),
-            inputs.Capsule(centre=(21.1, 10.6, 11.8), radius=5.0, subdiv=3, kS=0.02, kB=1e-3, kV=2.0, colour=-0.05),
-            inputs.Capsule(centre=(15.6, 21.3, 12.4), radius=5.0, subdiv=3, kS=0.02, kB=1e-3, kV=2.0, colour=0.05)]
-    p = inputs.Problem(name="bb3", nx=32, ny=32, nz=24, walls=0, coupling=0, psi_kind=0,
-                       droplet=(16.0, 16.0, 12.0, 7.0), capsules=caps, noise=1e-4, seed=15)
+    p = _three()
     g = _sim(p)
     o = O.OracleSim(p)
     og, _, _ = g.scbb_get_owner()
