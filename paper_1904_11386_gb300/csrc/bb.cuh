@@ -14,6 +14,7 @@ void launch_bb_lists_reset(const DevState& d, cudaStream_t st);
 void launch_bb_classify_lists(const LbmParams& p, const DevState& d, int step, bool init, cudaStream_t st);
 void launch_bb_owner(const LbmParams& p, const DevState& d, int step, bool init, cudaStream_t st);
 void launch_bb_boundary_list(const LbmParams& p, const DevState& d, cudaStream_t st);
+constexpr int BB_LIST_LAUNCHES = 3;     // kernels of launch_bb_boundary_list
 // Settles the crossed element of every cut link of the current boundary list (and the virtual densities the
 // boundary kernel reads); the first kernel of the step's boundary phase.
 void launch_bb_vrho(const LbmParams& p, const DevState& d, cudaStream_t st);

@@ -211,7 +211,7 @@ __global__ void k_class_tri(LbmParams p, DevState d, int step) {
     pdl_wait();
     pdl_trigger();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t == 0) { d.cnt[0] = 0; d.cnt[1] = 0; }
+    if (t == 0) { d.cnt[0] = 0; d.cnt[1] = 0; d.cnt[7] = 0; }
     if (t >= d.NT) return;
     const int nxt = (step + 1) & 1;
     d.emom[nxt * d.NT + t] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -452,103 +452,157 @@ __device__ __forceinline__ void end_record(const DevState& d, const TriGeom& g, 
     atomicMin(d.bkey + (size_t)b * (Q - 1) + (i - 1), key);
 }
 
-// One thread per (triangle, group of the nine directions c_i with odd i): G = 3 groups of an axis and two face
-// diagonals ({1,7,13} {3,9,15} {5,11,17}) for many triangles, G = 9 single directions for few (more threads,
-// shorter ones).  The nine odd directions and their opposites (i + 1, the same links seen from the other end)
-// are all eighteen.  The geometric tests of a link come first; the owner field and the list are read only for
-// the links the triangle crosses.
+// Crossing candidates, one thread per (triangle, group of the nine directions c_i with odd i): G = 3 groups of an
+// axis and two face diagonals ({1,7,13} {3,9,15} {5,11,17}) for many triangles, G = 9 single directions for few
+// (more threads, shorter ones).  The nine odd directions and their opposites (i + 1, the same links seen from
+// the other end) are all eighteen.  A link whose segment can meet the triangle's box goes through two cheap
+// conservative tests (its ends straddle the triangle's plane; where it meets the plane lies in the box) and,
+// if it passes, onto the candidate list (t, X, Y, Z << 5 | i) that k_link_test takes a thread per entry: the
+// enumeration's uneven loops and the few survivors would otherwise leave most lanes idle in the exact tests.
+// The enumeration runs twice, to count and to write, so that a warp takes its places with one atomic.
+constexpr int LC_CAP = BB_CAND_PER_TRI;     // candidate capacity per triangle (a few survive on average)
+
+// The links of direction c_i (odd i) whose segment can meet the triangle's box (v0, e1, e2; box b0, b1) and that
+// pass the two cheap tests: f(X, Y, Z) for each.
+template <class F>
+__device__ __forceinline__ void link_candidates(int i, float3 v0, float3 b0, float3 b1, float3 nrm, float tol, F&& f) {
+    constexpr float DL = 1e-3f;     // margin of the node ranges over the exact box test
+    const int cx = dir_x(i), cy = dir_y(i), cz = dir_z(i);
+    const float dn = nrm.x * cx + nrm.y * cy + nrm.z * cz;
+    // nodes u whose segment [u, u + c] (with the offsets) can meet the box
+    const int x0 = (int)ceilf(b0.x - DL - BB_EPSX - (float)max(cx, 0)), x1 = (int)floorf(b1.x + DL - BB_EPSX - (float)min(cx, 0));
+    const int y0 = (int)ceilf(b0.y - DL - BB_EPSY - (float)max(cy, 0)), y1 = (int)floorf(b1.y + DL - BB_EPSY - (float)min(cy, 0));
+    const int z0 = (int)ceilf(b0.z - DL - BB_EPSZ - (float)max(cz, 0)), z1 = (int)floorf(b1.z + DL - BB_EPSZ - (float)min(cz, 0));
+    for (int Z = z0; Z <= z1; Z++)
+        for (int Y = y0; Y <= y1; Y++) {
+            const float syz = nrm.y * (((float)Y + BB_EPSY) - v0.y) + nrm.z * (((float)Z + BB_EPSZ) - v0.z);
+            for (int X = x0; X <= x1; X++) {
+                const float su = syz + nrm.x * (((float)X + BB_EPSX) - v0.x), sw = su + dn;
+                if ((su > tol && sw > tol) || (su < -tol && sw < -tol)) continue;
+                // where the link meets the plane must lie in the triangle's box, up to a margin far above the
+                // rounding of that point (links almost parallel to the plane go on to the exact test)
+                if (fabsf(dn) > tol) {
+                    const float s = -su / dn, m = 4.f * tol / fabsf(dn) + 1e-3f;
+                    const float px = ((float)X + BB_EPSX) + s * cx, py = ((float)Y + BB_EPSY) + s * cy,
+                                pz = ((float)Z + BB_EPSZ) + s * cz;
+                    if (px < b0.x - m || px > b1.x + m || py < b0.y - m || py > b1.y + m || pz < b0.z - m ||
+                        pz > b1.z + m)
+                        continue;
+                }
+                f(X, Y, Z);
+            }
+        }
+}
+
 template <int G>
-__global__ void __launch_bounds__(128, 6) k_link_cross(LbmParams p, DevState d) {
+__global__ void __launch_bounds__(128) k_link_cand(LbmParams p, DevState d) {
     pdl_wait();
     pdl_trigger();
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
     const int t = q / G;
-    if (t >= d.NT) return;
     const int grp = q - t * G;
-    TriGeom g;
-    g.t = t;
-    const float4 c3 = d.trec[4 * t + 3];
-    g.k = __float_as_int(c3.w);
-    const float3 v0 = f3(d.trec[4 * t]), v1 = f3(d.trec[4 * t + 1]), v2 = f3(d.trec[4 * t + 2]);
-    g.b0 = make_float3(fminf(v0.x, fminf(v1.x, v2.x)), fminf(v0.y, fminf(v1.y, v2.y)), fminf(v0.z, fminf(v1.z, v2.z)));
-    g.b1 = make_float3(fmaxf(v0.x, fmaxf(v1.x, v2.x)), fmaxf(v0.y, fmaxf(v1.y, v2.y)), fmaxf(v0.z, fmaxf(v1.z, v2.z)));
-    // the triangles the classification leaves out of its column lists (wider than a column grid, outside their
-    // capsule's grid, non-finite) are flagged there and cross nothing here; a triangle as tall as the grid is a
-    // broken mesh too.  What is left bounds the loops below to CW + 3 nodes per axis.
-    const int4 lo = d.cbox[2 * g.k];
-    if (!(g.b1.x - g.b0.x < (float)d.CW && g.b1.y - g.b0.y < (float)d.CW && g.b0.x >= (float)(lo.x - 2) &&
-          g.b1.x <= (float)(lo.x + d.CW + 2) && g.b0.y >= (float)(lo.y - 2) && g.b1.y <= (float)(lo.y + d.CW + 2)))
-        return;
-    if (!(g.b1.z - g.b0.z < (float)d.CW)) {
-        atomicOr(d.cnt + 2, 32);
-        return;
+    bool live = t < d.NT;           // every lane stays for the warp's scan below
+    float3 v0 = make_float3(0.f, 0.f, 0.f), b0 = v0, b1 = v0, nrm = v0;
+    float tol = 0.f;
+    if (live) {
+        const int k = __float_as_int(d.trec[4 * t + 3].w);
+        v0 = f3(d.trec[4 * t]);
+        const float3 v1 = f3(d.trec[4 * t + 1]), v2 = f3(d.trec[4 * t + 2]);
+        b0 = make_float3(fminf(v0.x, fminf(v1.x, v2.x)), fminf(v0.y, fminf(v1.y, v2.y)), fminf(v0.z, fminf(v1.z, v2.z)));
+        b1 = make_float3(fmaxf(v0.x, fmaxf(v1.x, v2.x)), fmaxf(v0.y, fmaxf(v1.y, v2.y)), fmaxf(v0.z, fmaxf(v1.z, v2.z)));
+        // the triangles the classification leaves out of its column lists (wider than a column grid, outside
+        // their capsule's grid, non-finite) are flagged there and cross nothing here; a triangle as tall as the
+        // grid is a broken mesh too.  What is left bounds the loops to CW + 3 nodes per axis.
+        const int4 lo = d.cbox[2 * k];
+        if (!(b1.x - b0.x < (float)d.CW && b1.y - b0.y < (float)d.CW && b0.x >= (float)(lo.x - 2) &&
+              b1.x <= (float)(lo.x + d.CW + 2) && b0.y >= (float)(lo.y - 2) && b1.y <= (float)(lo.y + d.CW + 2))) {
+            live = false;
+        } else if (!(b1.z - b0.z < (float)d.CW)) {
+            atomicOr(d.cnt + 2, 32);
+            live = false;
+        } else {
+            const float3 e1 = sub(v1, v0), e2 = sub(v2, v0);
+            // Plane test, conservative: a link whose two ends lie on the same side of the triangle's plane by
+            // more than tol (about 1e3 times the rounding of these products) cannot pass seg_tri.
+            nrm = cross(e1, e2);
+            tol = 1e-3f * (fabsf(e1.x) + fabsf(e1.y) + fabsf(e1.z)) * (fabsf(e2.x) + fabsf(e2.y) + fabsf(e2.z));
+        }
     }
-    g.v0 = v0;
-    g.e1 = sub(v1, v0);
-    g.e2 = sub(v2, v0);
-    const double* cr = d.cap_red + 4 * g.k;
-    g.cr = make_float3((float)cr[1], (float)cr[2], (float)cr[3]);
-    // Plane test, conservative: a link whose two ends lie on the same side of the triangle's plane by more than
-    // tol (about 1e3 times the rounding of these products) cannot pass seg_tri.
-    const float3 nrm = cross(g.e1, g.e2);
-    const float tol = 1e-3f * (fabsf(g.e1.x) + fabsf(g.e1.y) + fabsf(g.e1.z)) *
-                      (fabsf(g.e2.x) + fabsf(g.e2.y) + fabsf(g.e2.z));
-    constexpr float DL = 1e-3f;     // margin of the node ranges over the exact box test
-#pragma unroll 1
-    for (int j = 0; j < 9 / G; j++) {
-        const int i = 2 * (grp + G * j) + 1;
+    // count, take the warp's places with one atomic, then write (a single counter taking every lane's appends
+    // serialises them)
+    int n = 0;
+    if (live)
+        for (int j = 0; j < 9 / G; j++)
+            link_candidates(2 * (grp + G * j) + 1, v0, b0, b1, nrm, tol, [&](int, int, int) { n++; });
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    int base = 0;
+    if (lane == 31 && incl > 0) base = atomicAdd(d.cnt + 7, incl);
+    base = __shfl_sync(0xffffffffu, base, 31) + incl - n;
+    const int cap = min(d.NT, 1 << 26) * LC_CAP;
+    if (live && n > 0)
+        for (int j = 0; j < 9 / G; j++) {
+            const int i = 2 * (grp + G * j) + 1;
+            link_candidates(i, v0, b0, b1, nrm, tol, [&](int X, int Y, int Z) {
+                if (base < cap) d.lcand[base] = make_int4(t, X, Y, (Z << 5) | i);
+                else atomicOr(d.cnt + 2, 256);
+                base++;
+            });
+        }
+}
+
+// One thread per crossing candidate: each end of the link tests the segment as its own search takes it (only in
+// its own periodic image; the two segments are the same bits unless rounding at a power of two parts them), and
+// the owner field and the list decide which ends record the crossing.
+__global__ void __launch_bounds__(128) k_link_test(LbmParams p, DevState d) {
+    pdl_wait();
+    pdl_trigger();
+    const int nc = min(d.cnt[7], min(d.NT, 1 << 26) * LC_CAP);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
+        const int4 c = d.lcand[q];
+        const int t = c.x, X = c.y, Y = c.z, Z = c.w >> 5, i = c.w & 31;
+        TriGeom g;
+        g.t = t;
+        g.k = __float_as_int(d.trec[4 * t + 3].w);
+        const float3 v0 = f3(d.trec[4 * t]), v1 = f3(d.trec[4 * t + 1]), v2 = f3(d.trec[4 * t + 2]);
+        g.b0 = make_float3(fminf(v0.x, fminf(v1.x, v2.x)), fminf(v0.y, fminf(v1.y, v2.y)), fminf(v0.z, fminf(v1.z, v2.z)));
+        g.b1 = make_float3(fmaxf(v0.x, fmaxf(v1.x, v2.x)), fmaxf(v0.y, fmaxf(v1.y, v2.y)), fmaxf(v0.z, fmaxf(v1.z, v2.z)));
+        g.v0 = v0;
+        g.e1 = sub(v1, v0);
+        g.e2 = sub(v2, v0);
+        const double* cr = d.cap_red + 4 * g.k;
+        g.cr = make_float3((float)cr[1], (float)cr[2], (float)cr[3]);
         const int cx = dir_x(i), cy = dir_y(i), cz = dir_z(i);
-        const float dn = nrm.x * cx + nrm.y * cy + nrm.z * cz;
-        // nodes u whose segment [u, u + c] (with the offsets) can meet the box
-        const int x0 = (int)ceilf(g.b0.x - DL - BB_EPSX - (float)max(cx, 0)), x1 = (int)floorf(g.b1.x + DL - BB_EPSX - (float)min(cx, 0));
-        const int y0 = (int)ceilf(g.b0.y - DL - BB_EPSY - (float)max(cy, 0)), y1 = (int)floorf(g.b1.y + DL - BB_EPSY - (float)min(cy, 0));
-        const int z0 = (int)ceilf(g.b0.z - DL - BB_EPSZ - (float)max(cz, 0)), z1 = (int)floorf(g.b1.z + DL - BB_EPSZ - (float)min(cz, 0));
-        for (int Z = z0; Z <= z1; Z++)
-            for (int Y = y0; Y <= y1; Y++) {
-                const float syz = nrm.y * (((float)Y + BB_EPSY) - v0.y) + nrm.z * (((float)Z + BB_EPSZ) - v0.z);
-                for (int X = x0; X <= x1; X++) {
-                    const float su = syz + nrm.x * (((float)X + BB_EPSX) - v0.x), sw = su + dn;
-                    if ((su > tol && sw > tol) || (su < -tol && sw < -tol)) continue;
-                    // where the link meets the plane must lie in the triangle's box, up to a margin far above
-                    // the rounding of that point (links almost parallel to the plane go on to the exact test)
-                    if (fabsf(dn) > tol) {
-                        const float s = -su / dn, m = 4.f * tol / fabsf(dn) + 1e-3f;
-                        const float px = ((float)X + BB_EPSX) + s * cx, py = ((float)Y + BB_EPSY) + s * cy,
-                                    pz = ((float)Z + BB_EPSZ) + s * cz;
-                        if (px < g.b0.x - m || px > g.b1.x + m || py < g.b0.y - m || py > g.b1.y + m ||
-                            pz < g.b0.z - m || pz > g.b1.z + m)
-                            continue;
-                    }
-                    const long long nu = node_of(p, X, Y, Z), nw = node_of(p, X + cx, Y + cy, Z + cz);
-                    if (nu < 0 || nw < 0) continue;
-                    // each end tests the segment as its own search takes it (only in its own image); the two
-                    // segments are the same bits unless rounding at a power of two parts them
-                    float tu = -1.f, tw = -1.f;
-                    float3 Pu, Du, Pw, Dw;
-                    const bool iu = own_image(X, g.cr.x, p.nx, true) && own_image(Y, g.cr.y, p.ny, true) &&
-                                    own_image(Z, g.cr.z, p.nz, !p.walls);
-                    const bool iw = own_image(X + cx, g.cr.x, p.nx, true) && own_image(Y + cy, g.cr.y, p.ny, true) &&
-                                    own_image(Z + cz, g.cr.z, p.nz, !p.walls);
-                    if (iu) {
-                        end_segment(nu, nw, X, Y, Z, i, Pu, Du);
-                        tu = seg_cross(g, Pu, Du);
-                    }
-                    if (iw) {
-                        end_segment(nw, nu, X + cx, Y + cy, Z + cz, i + 1, Pw, Dw);
-                        const bool same = iu && Pw.x == Pu.x && Pw.y == Pu.y && Pw.z == Pu.z && Dw.x == Du.x &&
-                                          Dw.y == Du.y && Dw.z == Du.z;
-                        tw = same ? tu : seg_cross(g, Pw, Dw);
-                    }
-                    if (tu < 0.f && tw < 0.f) continue;
-                    // the owners and the list places of both ends, loaded together
-                    const uint16_t ou = d.owner[nu], ow = d.owner[nw];
-                    const int bu = d.bidx[nu], bw = d.bidx[nw];
-                    if (ou == ow || ou == 0xFFFF || ow == 0xFFFF) continue;
-                    // each end searches the capsule it lies in, else the one across the link
-                    if (tu >= 0.f && (ou != 0 ? ou : ow) - 1 == g.k) end_record(d, g, bu, i, tu);
-                    if (tw >= 0.f && (ow != 0 ? ow : ou) - 1 == g.k) end_record(d, g, bw, i + 1, tw);
-                }
-            }
+        const long long nu = node_of(p, X, Y, Z), nw = node_of(p, X + cx, Y + cy, Z + cz);
+        if (nu < 0 || nw < 0) continue;
+        float tu = -1.f, tw = -1.f;
+        float3 Pu, Du, Pw, Dw;
+        const bool iu = own_image(X, g.cr.x, p.nx, true) && own_image(Y, g.cr.y, p.ny, true) &&
+                        own_image(Z, g.cr.z, p.nz, !p.walls);
+        const bool iw = own_image(X + cx, g.cr.x, p.nx, true) && own_image(Y + cy, g.cr.y, p.ny, true) &&
+                        own_image(Z + cz, g.cr.z, p.nz, !p.walls);
+        if (iu) {
+            end_segment(nu, nw, X, Y, Z, i, Pu, Du);
+            tu = seg_cross(g, Pu, Du);
+        }
+        if (iw) {
+            end_segment(nw, nu, X + cx, Y + cy, Z + cz, i + 1, Pw, Dw);
+            const bool same = iu && Pw.x == Pu.x && Pw.y == Pu.y && Pw.z == Pu.z && Dw.x == Du.x && Dw.y == Du.y &&
+                              Dw.z == Du.z;
+            tw = same ? tu : seg_cross(g, Pw, Dw);
+        }
+        if (tu < 0.f && tw < 0.f) continue;
+        // the owners and the list places of both ends, loaded together
+        const uint16_t ou = d.owner[nu], ow = d.owner[nw];
+        const int bu = d.bidx[nu], bw = d.bidx[nw];
+        if (ou == ow || ou == 0xFFFF || ow == 0xFFFF) continue;
+        // each end searches the capsule it lies in, else the one across the link
+        if (tu >= 0.f && (ou != 0 ? ou : ow) - 1 == g.k) end_record(d, g, bu, i, tu);
+        if (tw >= 0.f && (ow != 0 ? ow : ou) - 1 == g.k) end_record(d, g, bw, i + 1, tw);
     }
 }
 
@@ -580,8 +634,10 @@ void launch_bb_boundary_list(const LbmParams& p, const DevState& d, cudaStream_t
     const int w = d.CW + 2;
     dim3 gm((w * w * w + 127) / 128, d.NM);
     launch_k(k_boundary_mark, dim3(gm), dim3(128), 0, st, p, d);
-    if (d.NT < 65536) launch_k(k_link_cross<9>, dim3(((size_t)d.NT * 9 + 127) / 128), dim3(128), 0, st, p, d);
-    else launch_k(k_link_cross<3>, dim3(((size_t)d.NT * 3 + 127) / 128), dim3(128), 0, st, p, d);
+    if (d.NT < 65536) launch_k(k_link_cand<9>, dim3(((size_t)d.NT * 9 + 127) / 128), dim3(128), 0, st, p, d);
+    else launch_k(k_link_cand<3>, dim3(((size_t)d.NT * 3 + 127) / 128), dim3(128), 0, st, p, d);
+    static const int per_t = occupancy((const void*)k_link_test, 128);
+    launch_k(k_link_test, dim3(fill_grid(per_t, ((size_t)d.NT * LC_CAP + 127) / 128)), dim3(128), 0, st, p, d);
 }
 
 // ------------------------------------------------------------------------------------------------------

@@ -442,17 +442,84 @@ __device__ __forceinline__ int pp_cell(float v, int k, const PPGrid& g) {
     return c;
 }
 
+// Empty hash table; each capsule's reference point for this step (its centre, as the last reduction left it)
+// and a zero bounding radius.
 __global__ void k_pp_clear(DevState d, unsigned size) {
     for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < size; q += gridDim.x * blockDim.x) d.pp_head[q] = -1;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < d.NM; k += gridDim.x * blockDim.x) {
+        const double* cr = d.cap_red + 4 * k;
+        d.pp_ref[k] = make_float4((float)cr[1], (float)cr[2], (float)cr[3], 0.f);
+        d.pp_rmax[k] = 0;
+    }
+}
+
+// minimum-image separation a - b
+__device__ __forceinline__ float3 pp_sep(float3 a, float3 b, const PPGrid& g) {
+    float r[3] = {a.x - b.x, a.y - b.y, a.z - b.z};
+    for (int k = 0; k < 3; k++)
+        if (g.per[k]) r[k] -= g.L[k] * floorf(r[k] / g.L[k] + 0.5f);
+    return make_float3(r[0], r[1], r[2]);
+}
+
+// Margin of the sphere tests over the rounding of these FP32 distances.
+constexpr float PP_MARGIN = 1e-3f;
+
+// Per capsule: the other capsules whose bounding spheres (reference point, largest vertex distance) come within
+// the repulsion range d0 of its own.  A vertex farther than radius + d0 from every such capsule's reference
+// point has no vertex of another capsule within d0 (triangle inequality of the minimum-image distance).
+// One warp per capsule i, its lanes over the other capsules j.
+__global__ void k_pp_pairs(DevState d, PPGrid g, float d0) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (i >= d.NM) return;                          // warp-uniform
+    const float4 ci = d.pp_ref[i];
+    const float ri = __int_as_float(d.pp_rmax[i]);
+    int n = 0;
+    for (int j0 = 0; j0 < d.NM; j0 += 32) {
+        const int j = j0 + lane;
+        bool hit = false;
+        if (j < d.NM && j != i) {
+            const float4 cj = d.pp_ref[j];
+            const float3 r = pp_sep(make_float3(ci.x, ci.y, ci.z), make_float3(cj.x, cj.y, cj.z), g);
+            const float reach = ri + __int_as_float(d.pp_rmax[j]) + d0 + PP_MARGIN;
+            hit = !(r.x * r.x + r.y * r.y + r.z * r.z > reach * reach);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        const int at = n + __popc(bal & ((1u << lane) - 1u));
+        if (hit && at < PP_NBR) d.pp_nbr[i * PP_NBR + at] = j;
+        n += __popc(bal);
+    }
+    // too many: the vertices of capsule i search without the filter
+    if (lane == 0) d.pp_ncnt[i] = n > PP_NBR ? -1 : n;
 }
 
 __global__ void k_pp_insert(DevState d, PPGrid g) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= d.NV) return;
-    const float4 X = d.X[v];
-    if (!(fabsf(X.x) < 1e6f && fabsf(X.y) < 1e6f && fabsf(X.z) < 1e6f)) { d.pp_next[v] = -1; return; }
-    const unsigned h = pp_hash(pp_cell(X.x, 0, g), pp_cell(X.y, 1, g), pp_cell(X.z, 2, g), g.mask);
-    d.pp_next[v] = atomicExch(d.pp_head + h, v);
+    const int lane = threadIdx.x & 31;
+    int k = -1;
+    float dist = 0.f;
+    if (v < d.NV) {
+        const float4 X = d.X[v];
+        if (!(fabsf(X.x) < 1e6f && fabsf(X.y) < 1e6f && fabsf(X.z) < 1e6f)) {
+            d.pp_next[v] = -1;
+        } else {
+            const unsigned h = pp_hash(pp_cell(X.x, 0, g), pp_cell(X.y, 1, g), pp_cell(X.z, 2, g), g.mask);
+            d.pp_next[v] = atomicExch(d.pp_head + h, v);
+            k = d.vcap[v];
+            const float4 c = d.pp_ref[k];
+            const float3 r = pp_sep(make_float3(X.x, X.y, X.z), make_float3(c.x, c.y, c.z), g);
+            dist = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
+        }
+    }
+    // the capsule's bounding radius: one atomic per warp when the warp's vertices share a capsule (they are
+    // stored capsule by capsule), else one per vertex; distances are >= 0, so their bits order as ints
+    const int k0 = __shfl_sync(0xffffffffu, k, 0);
+    if (__all_sync(0xffffffffu, k == k0)) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dist = fmaxf(dist, __shfl_xor_sync(0xffffffffu, dist, o));
+        if (lane == 0 && k0 >= 0) atomicMax(d.pp_rmax + k0, __float_as_int(dist));
+    } else if (k >= 0) {
+        atomicMax(d.pp_rmax + k, __float_as_int(dist));
+    }
 }
 
 __global__ void k_pp_force(DevState d, PPGrid g, float eps, float d0) {
@@ -461,7 +528,17 @@ __global__ void k_pp_force(DevState d, PPGrid g, float eps, float d0) {
     const float4 X = d.X[v];
     const int cap = d.vcap[v];
     float3 F = make_float3(0.f, 0.f, 0.f);
-    if (fabsf(X.x) < 1e6f && fabsf(X.y) < 1e6f && fabsf(X.z) < 1e6f) {
+    // the cell search only where another capsule's bounding sphere comes within d0 (else no term is nonzero)
+    const int nn = d.pp_ncnt[cap];
+    bool near = nn < 0;
+    for (int q = 0; q < nn && !near; q++) {
+        const int j = d.pp_nbr[cap * PP_NBR + q];
+        const float4 c = d.pp_ref[j];
+        const float3 r = pp_sep(make_float3(X.x, X.y, X.z), make_float3(c.x, c.y, c.z), g);
+        const float reach = __int_as_float(d.pp_rmax[j]) + d0 + PP_MARGIN;
+        near = !(r.x * r.x + r.y * r.y + r.z * r.z > reach * reach);     // a non-finite distance searches
+    }
+    if (near && fabsf(X.x) < 1e6f && fabsf(X.y) < 1e6f && fabsf(X.z) < 1e6f) {
         const int c0[3] = {pp_cell(X.x, 0, g), pp_cell(X.y, 1, g), pp_cell(X.z, 2, g)};
         for (int dz = -1; dz <= 1; dz++)
             for (int dy = -1; dy <= 1; dy++)
@@ -514,8 +591,9 @@ int launch_pp_forces(const LbmParams& p, const DevState& d, float eps, float d0,
     g.mask = (unsigned)d.pp_size - 1u;
     k_pp_clear<<<(d.pp_size + 255) / 256, 256, 0, st>>>(d, (unsigned)d.pp_size);
     k_pp_insert<<<(d.NV + 127) / 128, 128, 0, st>>>(d, g);
+    k_pp_pairs<<<(d.NM * 32 + 127) / 128, 128, 0, st>>>(d, g, d0);
     k_pp_force<<<(d.NV + 127) / 128, 128, 0, st>>>(d, g, eps, d0);
-    return 3;
+    return 4;
 }
 
 }  // namespace scbb

@@ -267,6 +267,10 @@ size_t layout(const scbb_lattice* lat, const scbb_fluid* fl, int nm, const scbb_
         t.pp_head = c.take<int>(sz);
         t.pp_next = c.take<int>(nv1);
         t.Fpp = c.take<float4>(nv1);
+        t.pp_ref = c.take<float4>(nm);
+        t.pp_rmax = c.take<int>(nm);
+        t.pp_nbr = c.take<int>((size_t)nm * PP_NBR);
+        t.pp_ncnt = c.take<int>(nm);
     }
     t.pp_eps = (float)fl->pp_eps;
     t.pp_d0 = (float)fl->pp_d0;
@@ -282,6 +286,7 @@ size_t layout(const scbb_lattice* lat, const scbb_fluid* fl, int nm, const scbb_
         t.belem = c.take<int>((size_t)z.maxB * (Q - 1));
         t.bkey = c.take<unsigned long long>((size_t)z.maxB * (Q - 1));
         t.bidx = c.take<int>(N);
+        t.lcand = c.take<int4>((size_t)nt1 * BB_CAND_PER_TRI);
         t.flist = c.take<int>(z.maxF);
         t.fold = c.take<int>(z.maxF);
         t.fnew = c.take<float4>((size_t)2 * z.maxF);
@@ -324,7 +329,7 @@ scbb_status check_bb_flags(scbb_ctx* c) {
         return fail(c, SCBB_E_UNSTABLE,
                     "bounce-back geometry or list overflow (flags %d: 1/16 capsule box, 2 column crossings, "
                     "4 fresh list, 8 boundary list, 32 triangle outside its column grid, 64 column triangle list, "
-                    "128 fresh node without a finite nearest element)", h[2]);
+                    "128 fresh node without a finite nearest element, 256 crossing candidate list)", h[2]);
     }
     return SCBB_OK;
 }
@@ -563,7 +568,7 @@ scbb_status scbb_set_density(scbb_ctx* c, const double* rhoA, const double* rhoB
         launch_bb_classify(c->lp, c->d, -1, true, c->st);
         launch_moments_reduce(c->lp, c->d.S[c->cur], c->d.red, c->st);
         CUDA_TRY(c, cudaMemcpyAsync(c->d.mass, c->d.red, 2 * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
-        c->launches += 9;
+        c->launches += 7 + BB_LIST_LAUNCHES;
     }
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
@@ -726,7 +731,7 @@ static void enqueue_post(scbb_ctx* c, const StepPlan& s) {
             launch_bb_mass(c->lp, c->d, c->st);
             launch_bb_fresh_nodes(c->lp, c->d, c->d.S[1 - c->cur], step, c->st);
         }
-        c->launches += 5 + 3;
+        c->launches += 3 + BB_LIST_LAUNCHES + 3;      // reset, owner (2), list; mass, fresh (2)
     } else {
         c->mark(4);
         c->mark(5);

@@ -226,6 +226,9 @@ struct CapDev {
 };
 
 // Device-side buffers of a context (all carved from the caller's workspace).
+constexpr int BB_CAND_PER_TRI = 16;   // capacity of the element search's candidate list, per triangle
+constexpr int PP_NBR = 16;     // neighbour capsules listed per capsule for the repulsion
+
 struct DevState {
     float* S[2];            // populations, 2 * 19 * N values each, of the type LbmParams::store names; one
                             // lattice (S[1] == S[0]) when the two-kernel bulk phase updates it in place
@@ -272,6 +275,7 @@ struct DevState {
                             //     boundary kernel (cnt[5] partials)
     int* belem;             // [maxB][18] element crossed by the link along direction i (slot i-1), -1 if uncut
     unsigned long long* bkey;   // [maxB][18] nearest crossing found so far: (parameter bits << 32) | triangle
+    int4* lcand;            // [NT * BB_CAND_PER_TRI] crossing candidates of the element search: (t, X, Y, Z << 5 | i)
     int* bidx;              // [N] place in the boundary list of each node listed by the last list build (-1: the
                             //     list was full); stale for the other nodes
     int* flist;             // [maxF] fresh nodes
@@ -279,7 +283,8 @@ struct DevState {
     float4* fnew;           // [maxF][2] new (rhoA, rhoB, ok, -) and (vx, vy, vz, element)
     int* cnt;               // [8] 0: boundary nodes, 1: fresh nodes, 2: overflow flags, 4: fresh nodes of the
                             //     previous step (saved before re-listing), 5: partials in bdm, 6: cut links
-                            //     whose element came from the nearest-centroid rule (running count)
+                            //     whose element came from the nearest-centroid rule (running count),
+                            //     7: crossing candidates of the element search
     float4* emom;           // [2][NT] exchanged momentum (Eq. 12) by step parity
     float4* epend;          // [2][NT] Shan-Chen reactions and fresh-node momenta by step parity
     int4* cbox;             // [NM][2] classification box (lo, hi), unwrapped lattice coordinates
@@ -299,6 +304,10 @@ struct DevState {
     int* pp_head;           // [pp_size] hashed cell heads, nullptr when unused
     int* pp_next;           // [NV] linked lists
     float4* Fpp;            // [NV] repulsion force of the step
+    float4* pp_ref;         // [NM] reference point of each capsule for the step's repulsion (its centre)
+    int* pp_rmax;           // [NM] largest distance of the capsule's vertices from pp_ref (float bits)
+    int* pp_nbr;            // [NM][PP_NBR] capsules whose bounding spheres come within the repulsion range
+    int* pp_ncnt;           // [NM] their number, -1 when more than PP_NBR
     int pp_size;
     float pp_eps, pp_d0;
     double rho_maj, rho_min, C0;

@@ -108,6 +108,25 @@ def test_pp_repulsion_two_capsules():
     assert np.abs(Fg - Fo).max() < 1e-4 * np.abs(Fo).max()
 
 
+def test_pp_repulsion_across_the_periodic_edge_and_far_capsules():
+    """The repulsion's capsule filter (bounding spheres within d0) keeps every nonzero term: two capsules 0.5
+    apart across the periodic x edge repel as the oracle has it, while a third one far from both gets no
+    repulsion (its node forces are the elastic ones, as in the oracle)."""
+    caps = [inputs.Capsule(centre=(4.1, 12.1, 12.2), radius=4.0, subdiv=3, kS=0.01, kB=1e-3, kV=1.0),
+            inputs.Capsule(centre=(32 - 4.4, 12.0, 12.3), radius=4.0, subdiv=3, kS=0.01, kB=1e-3, kV=1.0),
+            inputs.Capsule(centre=(16.2, 12.3, 12.1), radius=3.0, subdiv=3, kS=0.01, kB=1e-3, kV=1.0)]
+    p = inputs.Problem(name="pp2", nx=32, ny=24, nz=24, walls=0, coupling=1, psi_kind=0, capsules=caps,
+                       noise=1e-4, seed=6)
+    g = _sim(p)
+    o = O.OracleSim(p)
+    g.scbb_step(1)
+    o.step(1)
+    _, _, Fg = g.scbb_get_vertices()
+    _, _, Fo = o.vertices()
+    assert np.abs(Fo).max() > 0.05
+    assert np.abs(Fg - Fo).max() < 1e-4 * np.abs(Fo).max()
+
+
 def test_ibm_capsule_in_onsite_shear():
     """A capsule in shear imposed by on-site velocity planes (Zou and He), the setup of Sec. III.A: a single
     component mixture (G = 0, rho^A = rho^B = 0.5), resting walls, planes z = 1 and nz - 2 at -+U along x, a
