@@ -825,64 +825,89 @@ __device__ __forceinline__ float2 boundary_node(const LbmParams& p, const DevSta
     });
     const float pa = psi_fn(ra, p.psi_kind), pb = psi_fn(rb, p.psi_kind);
     // ---- neighbour along c_i: wall (ghost density), same side, or across a cut link (virtual density with the
-    // crossed element's colour); the links that bounce back are the cut ones with an element
+    // crossed element's colour); the links that bounce back are the cut ones with an element.  In phases, so
+    // that each phase's loads are in flight together: the owners; the densities (or, across a cut link, its
+    // element and the virtual densities); the elements' colours; then the sums and the reactions.
+    uint16_t om[Q];                 // 0xFFFF: a wall plane
+    for_dirs<1, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        om[i] = wall_z(p, z + dir_z(i)) ? (uint16_t)0xFFFF : d.owner[nh.at(p, dir_x(i), dir_y(i), dir_z(i))];
+    });
+    float va[Q], vb[Q];
+    int el[Q];
+    unsigned cut = 0, multi = 0;
+    for_dirs<1, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        el[i] = -1;
+        if (om[i] == 0xFFFF) {
+            const int zn = z + dir_z(i);
+            const int w = zn == 0 ? 0 : 1;
+            const int rr = nh.xs[1 + dir_x(i)] + nh.ys[1 + dir_y(i)] * p.nx;
+            va[i] = ghost[(w * 2 + 0) * p.nxy + rr];
+            vb[i] = ghost[(w * 2 + 1) * p.nxy + rr];
+        } else {
+            const unsigned m = nh.at(p, dir_x(i), dir_y(i), dir_z(i));
+            if (om[i] == me) {
+                va[i] = d.rho[m];
+                vb[i] = d.rho[p.N + m];
+            } else {
+                el[i] = d.belem[(size_t)b * (Q - 1) + (i - 1)];
+                const float4 vr = d.vrho[m];
+                va[i] = vr.x;
+                vb[i] = vr.y;
+                cut |= 1u << i;
+                if (vr.w != 0.f) multi |= 1u << i;
+            }
+        }
+    });
+    if (multi) {
+        // m borders more than one other side: mean over its neighbours on this node's side
+        for_dirs<1, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            if (!((multi >> i) & 1u)) return;
+            const Nbhd mh(p, (int)nh.at(p, dir_x(i), dir_y(i), dir_z(i)));
+            float sA = 0.f, sB = 0.f;
+            int cnt = 0;
+            for (int q = 1; q < Q; q++) {
+                if (wall_z(p, mh.z + dir_z(q))) continue;
+                const unsigned qq = mh.at(p, dir_x(q), dir_y(q), dir_z(q));
+                if (d.owner[qq] != me) continue;
+                sA += d.rho[qq];
+                sB += d.rho[p.N + qq];
+                cnt++;
+            }
+            va[i] = cnt ? sA / cnt : ra;
+            vb[i] = cnt ? sB / cnt : rb;
+        });
+    }
+    // the crossed element's colour (per capsule or per element) on the virtual density of Eq. 15
     const float drho = (float)(d.rho_maj - d.rho_min);
+    for_dirs<1, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        if (!((cut >> i) & 1u) || el[i] < 0) return;
+        const float col = d.tcol[el[i]];
+        const float rv = 2.f * fabsf(col) * drho;
+        if (col > 0.f) va[i] += rv;
+        else if (col < 0.f) vb[i] += rv;
+    });
     float sa0 = 0.f, sa1 = 0.f, sa2 = 0.f, sb0 = 0.f, sb1 = 0.f, sb2 = 0.f;
     unsigned bounce = 0;
     for_dirs<1, Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr float wi = dir_w(i);
-        const int zn = z + dir_z(i);
         float psA = 0.f, psB = 0.f;
-        if (wall_z(p, zn)) {
-            const int w = zn == 0 ? 0 : 1;
-            const int rr = nh.xs[1 + dir_x(i)] + nh.ys[1 + dir_y(i)] * p.nx;
-            psA = psi_fn(ghost[(w * 2 + 0) * p.nxy + rr], p.psi_kind);
-            psB = psi_fn(ghost[(w * 2 + 1) * p.nxy + rr], p.psi_kind);
+        if (!((cut >> i) & 1u)) {
+            psA = psi_fn(va[i], p.psi_kind);
+            psB = psi_fn(vb[i], p.psi_kind);
+        } else if (el[i] >= 0) {
+            psA = psi_fn(va[i], p.psi_kind);
+            psB = psi_fn(vb[i], p.psi_kind);
+            // reaction of both components on the element: + psi^c(x) G w_i psi^{c'}(virtual) c_i
+            const float a = p.G * wi * (pa * psB + pb * psA);
+            atomicAdd(&d.epend[pr * d.NT + el[i]], make_float4(a * dir_x(i), a * dir_y(i), a * dir_z(i), 0.f));
+            bounce |= 1u << i;
         } else {
-            const unsigned m = nh.at(p, dir_x(i), dir_y(i), dir_z(i));
-            const uint16_t om = d.owner[m];
-            if (om == me) {
-                psA = psi_fn(d.rho[m], p.psi_kind);
-                psB = psi_fn(d.rho[p.N + m], p.psi_kind);
-            } else {
-                const int e = d.belem[(size_t)b * (Q - 1) + (i - 1)];
-                float vA, vB;
-                const float4 vr = d.vrho[m];
-                if (vr.w == 0.f) {
-                    vA = vr.x;
-                    vB = vr.y;
-                } else {
-                    // m borders more than one other side: mean over its neighbours on this node's side
-                    const Nbhd mh(p, (int)m);
-                    float sA = 0.f, sB = 0.f;
-                    int cnt = 0;
-                    for (int q = 1; q < Q; q++) {
-                        if (wall_z(p, mh.z + dir_z(q))) continue;
-                        const unsigned qq = mh.at(p, dir_x(q), dir_y(q), dir_z(q));
-                        if (d.owner[qq] != me) continue;
-                        sA += d.rho[qq];
-                        sB += d.rho[p.N + qq];
-                        cnt++;
-                    }
-                    vA = cnt ? sA / cnt : ra;
-                    vB = cnt ? sB / cnt : rb;
-                }
-                if (e >= 0) {
-                    const float col = d.tcol[e];     // the crossed element's colour (per capsule or per element)
-                    const float rv = 2.f * fabsf(col) * drho;
-                    if (col > 0.f) vA += rv;
-                    else if (col < 0.f) vB += rv;
-                    psA = psi_fn(vA, p.psi_kind);
-                    psB = psi_fn(vB, p.psi_kind);
-                    // reaction of both components on the element: + psi^c(x) G w_i psi^{c'}(virtual) c_i
-                    const float a = p.G * wi * (pa * psB + pb * psA);
-                    atomicAdd(&d.epend[pr * d.NT + e], make_float4(a * dir_x(i), a * dir_y(i), a * dir_z(i), 0.f));
-                    bounce |= 1u << i;
-                } else {
-                    atomicOr(err, 2);      // list out of step with the owner field: never expected
-                }
-            }
+            atomicOr(err, 2);      // list out of step with the owner field: never expected
         }
         const float qa = wi * psA, qb = wi * psB;
         if constexpr (dir_x(i) != 0) { sa0 += dir_x(i) > 0 ? qa : -qa; sb0 += dir_x(i) > 0 ? qb : -qb; }
@@ -936,7 +961,7 @@ __device__ __forceinline__ float2 boundary_node(const LbmParams& p, const DevSta
         } else {
             // moving half-way bounce-back (Eq. 11) with the element velocity; exchanged momentum (Eq. 12)
             const unsigned m = nh.at(p, dir_x(i), dir_y(i), dir_z(i));
-            const int e = d.belem[(size_t)b * (Q - 1) + (i - 1)];
+            const int e = el[i];
             const int4 Te = d.tri[e];
             const float4 V0 = d.V[Te.x], V1 = d.V[Te.y], V2 = d.V[Te.z];
             const float vx = (V0.x + V1.x + V2.x) * (1.f / 3.f), vy = (V0.y + V1.y + V2.y) * (1.f / 3.f),
