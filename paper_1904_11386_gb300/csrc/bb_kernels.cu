@@ -345,6 +345,18 @@ __global__ void k_boundary_mark(LbmParams p, DevState d) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= wx * wy * wz) return;
     const int xx = lo.x - 1 + q % wx, yy = lo.y - 1 + (q / wx) % wy, zz = lo.z - 1 + q / (wx * wy);
+    // A node can have a link to capsule k's inside only if its column or a neighbouring one crosses capsule k's
+    // surface (elsewhere no node is k's: the ray parity is even); links between other sides are listed by the
+    // passes of the capsules whose insides they touch.
+    const int ccx = xx - lo.x, ccy = yy - lo.y;
+    bool crossed = false;
+    for (int dy = -1; dy <= 1; dy++)
+        for (int dx = -1; dx <= 1; dx++) {
+            const int cx = ccx + dx, cy = ccy + dy;
+            if (cx >= 0 && cy >= 0 && cx < d.CW && cy < d.CW && d.ccnt[k * d.CW * d.CW + cy * d.CW + cx] > 0)
+                crossed = true;
+        }
+    if (!crossed) return;
     const long long n = node_of(p, xx, yy, zz);
     if (n < 0) return;
     const uint16_t me = d.owner[n];
