@@ -69,6 +69,15 @@ static int occupancy(const void* kernel, int threads) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, 0) != cudaSuccess || v < 1) v = 1;
     return v;
 }
+// Blocks of 128 threads per capsule for a pass over each capsule's box of `nodes` nodes: about 16 blocks per SM
+// in all, at most one per 128 nodes.
+static unsigned box_blocks(const DevState& d, size_t nodes) {
+    const size_t per_cap = ((size_t)16 * sm_count() + d.NM - 1) / (d.NM > 0 ? d.NM : 1);
+    const size_t full = (nodes + 127) / 128;
+    const size_t g = per_cap < full ? per_cap : full;
+    return (unsigned)(g > 0 ? g : 1);
+}
+
 static unsigned fill_grid(int per_sm, size_t need) {
     size_t g = (size_t)per_sm * sm_count();
     if (need < g) g = need;
@@ -272,12 +281,8 @@ __global__ void k_class_tri(LbmParams p, DevState d, int step) {
 
 // One thread per node of a capsule's box: parity of the column's crossings above the node; owner updated in
 // place, changed nodes recorded as fresh.
-__global__ void k_class_col(LbmParams p, DevState d, int init) {
-    pdl_wait();
-    pdl_trigger();
-    const int k = blockIdx.y;
-    const int4 lo = d.cbox[2 * k], hi = d.cbox[2 * k + 1];
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void class_col_node(const LbmParams& p, const DevState& d, int init, int k, int4 lo,
+                                               int4 hi, int q) {
     const int c = q % (d.CW * d.CW), zo = q / (d.CW * d.CW);
     if (zo >= d.CW) return;
     const int cx = c % d.CW, cy = c / d.CW;
@@ -310,6 +315,17 @@ __global__ void k_class_col(LbmParams p, DevState d, int init) {
     }
 }
 
+// Grid-stride over each capsule's box (blockIdx.y: the capsule): a few blocks per capsule rather than a block
+// per 128 nodes, whose launch and drain cost more than their work with hundreds of capsules.
+__global__ void k_class_col(LbmParams p, DevState d, int init) {
+    pdl_wait();
+    pdl_trigger();
+    const int k = blockIdx.y;
+    const int4 lo = d.cbox[2 * k], hi = d.cbox[2 * k + 1];
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < d.CW * d.CW * d.CW; q += gridDim.x * blockDim.x)
+        class_col_node(p, d, init, k, lo, hi, q);
+}
+
 // Clears the boundary and fresh bits of the previous step's lists (and the boundary nodes' places, so that
 // bidx is -1 at every node not listed) and the per-column counters.
 __global__ void k_lists_reset(DevState d) {
@@ -336,14 +352,8 @@ __global__ void k_lists_reset(DevState d) {
 
 // Nodes of each capsule's box (one node wider) with a cut membrane link join the boundary list; each one's
 // place in it goes to bidx, and the crossing keys of its links start at "none".
-__global__ void k_boundary_mark(LbmParams p, DevState d) {
-    pdl_wait();
-    pdl_trigger();
-    const int k = blockIdx.y;
-    const int4 lo = d.cbox[2 * k], hi = d.cbox[2 * k + 1];
-    const int wx = hi.x - lo.x + 3, wy = hi.y - lo.y + 3, wz = hi.z - lo.z + 3;
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= wx * wy * wz) return;
+__device__ __forceinline__ void mark_node(const LbmParams& p, const DevState& d, int k, int4 lo, int wx, int wy,
+                                          int q) {
     const int xx = lo.x - 1 + q % wx, yy = lo.y - 1 + (q / wx) % wy, zz = lo.z - 1 + q / (wx * wy);
     // A node can have a link to capsule k's inside only if its column or a neighbouring one crosses capsule k's
     // surface (elsewhere no node is k's: the ray parity is even); links between other sides are listed by the
@@ -384,6 +394,17 @@ __global__ void k_boundary_mark(LbmParams p, DevState d) {
     } else {
         atomicOr(d.cnt + 2, 8);
     }
+}
+
+// Grid-stride over each capsule's box, one node wider (blockIdx.y: the capsule).
+__global__ void k_boundary_mark(LbmParams p, DevState d) {
+    pdl_wait();
+    pdl_trigger();
+    const int k = blockIdx.y;
+    const int4 lo = d.cbox[2 * k], hi = d.cbox[2 * k + 1];
+    const int wx = hi.x - lo.x + 3, wy = hi.y - lo.y + 3, wz = hi.z - lo.z + 3;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < wx * wy * wz; q += gridDim.x * blockDim.x)
+        mark_node(p, d, k, lo, wx, wy, q);
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -636,16 +657,14 @@ void launch_bb_classify_lists(const LbmParams& p, const DevState& d, int step, b
 void launch_bb_owner(const LbmParams& p, const DevState& d, int step, bool init, cudaStream_t st) {
     if (d.NM == 0) return;
     launch_k(k_class_tri, dim3((d.NT + 127) / 128), dim3(128), 0, st, p, d, step);
-    dim3 gc((d.CW * d.CW * d.CW + 127) / 128, d.NM);
-    launch_k(k_class_col, dim3(gc), dim3(128), 0, st, p, d, init ? 1 : 0);
+    launch_k(k_class_col, dim3(box_blocks(d, (size_t)d.CW * d.CW * d.CW), d.NM), dim3(128), 0, st, p, d, init ? 1 : 0);
 }
 
 void launch_bb_boundary_list(const LbmParams& p, const DevState& d, cudaStream_t st) {
     if (d.NM == 0) return;
     // boxes are at most CW wide; one node of margin on each side
     const int w = d.CW + 2;
-    dim3 gm((w * w * w + 127) / 128, d.NM);
-    launch_k(k_boundary_mark, dim3(gm), dim3(128), 0, st, p, d);
+    launch_k(k_boundary_mark, dim3(box_blocks(d, (size_t)w * w * w), d.NM), dim3(128), 0, st, p, d);
     if (d.NT < 65536) launch_k(k_link_cand<9>, dim3(((size_t)d.NT * 9 + 127) / 128), dim3(128), 0, st, p, d);
     else launch_k(k_link_cand<3>, dim3(((size_t)d.NT * 3 + 127) / 128), dim3(128), 0, st, p, d);
     static const int per_t = occupancy((const void*)k_link_test, 128);
