@@ -1236,8 +1236,8 @@ __device__ __forceinline__ float2 boundary_node_warp(const LbmParams& p, const D
             pst(D + (size_t)(Q + i) * p.N + n, oB - gB);
         } else {
             // moving half-way bounce-back (Eq. 11) with the element velocity; exchanged momentum (Eq. 12)
-            const int4 T = d.tri[e];
-            const float4 V0 = d.V[T.x], V1 = d.V[T.y], V2 = d.V[T.z];
+            const int4 tv = d.tri[e];
+            const float4 V0 = d.V[tv.x], V1 = d.V[tv.y], V2 = d.V[tv.z];
             const float vx = (V0.x + V1.x + V2.x) * (1.f / 3.f), vy = (V0.y + V1.y + V2.y) * (1.f / 3.f),
                         vz = (V0.z + V1.z + V2.z) * (1.f / 3.f);
             const float cv = 6.f * wi * (cx * vx + cy * vy + cz * vz);
@@ -1501,10 +1501,10 @@ __device__ __forceinline__ void fresh_node(const LbmParams& p, const DevState& d
         return;
     }
     if (lane == 0) {
-        const int4 T = d.tri[be];
-        const float3 v = make_float3((d.V[T.x].x + d.V[T.y].x + d.V[T.z].x) * (1.f / 3.f),
-                                     (d.V[T.x].y + d.V[T.y].y + d.V[T.z].y) * (1.f / 3.f),
-                                     (d.V[T.x].z + d.V[T.y].z + d.V[T.z].z) * (1.f / 3.f));
+        const int4 tv = d.tri[be];
+        const float3 v = make_float3((d.V[tv.x].x + d.V[tv.y].x + d.V[tv.z].x) * (1.f / 3.f),
+                                     (d.V[tv.x].y + d.V[tv.y].y + d.V[tv.z].y) * (1.f / 3.f),
+                                     (d.V[tv.x].z + d.V[tv.y].z + d.V[tv.z].z) * (1.f / 3.f));
         d.fnew[2 * q] = make_float4(rf[0], rf[1], 1.f, 0.f);
         d.fnew[2 * q + 1] = make_float4(v.x, v.y, v.z, __int_as_float(be));
     }
