@@ -72,7 +72,8 @@ typedef struct {
  *   coupling  0: half-way bounce-back membranes with wetting (the paper, Sec. II.C-E),
  *             1: 2-point immersed boundary (Peskin hat; not in the paper; colour must be 0)
  *   rho_maj, rho_min   equilibrium majority / minority densities used to turn colour into a virtual
- *             density offset (Eq. 15): rho_virtual = 2 |colour| (rho_maj - rho_min)
+ *             density offset (Eq. 15): rho_virtual = |colour| (rho_maj - rho_min) / 2, the normalisation
+ *             under which a rigid sphere's contact angle follows cos theta = colour (Sec. III.D)
  *   C0, mass_correction   adaptive fresh-node mass correction (Eq. 18), C0 = 2500 in the paper
  *   pp_eps, pp_d0         particle-particle repulsion (Eq. 26, Sec. III.E), 0.5 and 1.25 in the paper
  *   storage   0: FP32 populations; 1: populations stored as IEEE FP16, 2: as BF16 (arithmetic stays FP32;

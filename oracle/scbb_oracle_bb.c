@@ -20,12 +20,14 @@
  *    and homogeneously over the element's three nodes.
  *  - Shan-Chen across a cut link (Eq. 14): the density seen at the node y = x + c_i on the other side is
  *    the mean of rho over the neighbours of y that lie on x's side (not walls); the particle colour adds
- *    rho_virtual = 2 |colour| (rho_maj - rho_min) (Eq. 15) to component A if colour > 0, to B if < 0.
+ *    rho_virtual = |colour| (rho_maj - rho_min) / 2 to component A if colour > 0, to B if < 0.  The
+ *    normalisation below Eq. 14 reads the other way round (colour = rho_virtual / (2 (rho_maj - rho_min)),
+ *    i.e. an offset 2 |colour| (rho_maj - rho_min)); with that one Sec. III.D's own result cannot hold: a
+ *    near-rigid capsule's equilibrium contact angle follows cos theta = 4.3 .. 4.6 colour, and at the
+ *    section's colours 0.30 and 0.61 the capsule leaves the interface.  With the factor the other way
+ *    round the oracle gives cos theta = 0.38 and 0.63 at colours 0.3 and 0.6, the section's cos theta =
+ *    colour within 0.1 (pinned by a test).
  *    The reaction +psi^c(x) G w_i psi^{c'}(virtual) c_i goes to the crossed element (momentum balance).
- *    Parity unpinned: the magnitude of the colour's effect.  Its sign and its neutrality at colour 0 are
- *    pinned by tests; with this normalisation a near-rigid capsule's equilibrium contact angle follows
- *    cos theta = 4.3 .. 4.6 colour (R = 6, colours 0.03 .. 0.1), where Sec. III.D reports cos theta close to
- *    the colour itself, so no measured value pins the magnitude.
  *  - Fresh nodes (Sec. II.E): nodes whose owner changed.  rho^c = mean over the non-fresh neighbours on
  *    the new side (Eq. 16), times the mass correction of Eq. 18 with Delta rho^c read as the global mass
  *    error M^c(t) - M^c(0), V_sys = number of fluid nodes, rho_init^c = M^c(0)/V_sys, clamped to the
@@ -331,7 +333,7 @@ static double bb_virtual_psi(osim* s, long n, int x, int y, int z, int i, long m
     int e = table_element(s, n, i);
     /* the colour of the crossed element (Sec. V's per-element colour), else of its capsule */
     double col = (s->ecol && e >= 0) ? s->ecol[e] : s->mp[cap].colour;
-    double rv = 2.0 * fabs(col) * (s->p.rho_maj - s->p.rho_min);
+    double rv = 0.5 * fabs(col) * (s->p.rho_maj - s->p.rho_min);
     if ((col > 0 && c_other == 0) || (col < 0 && c_other == 1)) rt += rv;
     double ps = psi_of(s, rt);
     /* reaction on the element: + psi^c(n) G w_i psi^{c'}(virtual) c_i, c = the other component's partner */

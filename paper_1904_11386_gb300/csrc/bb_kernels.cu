@@ -911,13 +911,15 @@ __device__ __forceinline__ float2 boundary_node(const LbmParams& p, const DevSta
             vb[i] = cnt ? sB / cnt : rb;
         });
     }
-    // the crossed element's colour (per capsule or per element) on the virtual density of Eq. 15
+    // the crossed element's colour (per capsule or per element) on the virtual density: an offset of
+    // |colour| (rho_maj - rho_min) / 2 (Eq. 15 with its normalisation read so that Sec. III.D's contact angles
+    // hold, cos theta = colour)
     const float drho = (float)(d.rho_maj - d.rho_min);
     for_dirs<1, Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         if (!((cut >> i) & 1u) || el[i] < 0) return;
         const float col = d.tcol[el[i]];
-        const float rv = 2.f * fabsf(col) * drho;
+        const float rv = 0.5f * fabsf(col) * drho;
         if (col > 0.f) va[i] += rv;
         else if (col < 0.f) vb[i] += rv;
     });
@@ -1180,7 +1182,7 @@ __device__ __forceinline__ float2 boundary_node_warp(const LbmParams& p, const D
                 }
                 if (e >= 0) {
                     const float col = d.tcol[e];     // the crossed element's colour (per capsule or per element)
-                    const float rv = 2.f * fabsf(col) * (float)(d.rho_maj - d.rho_min);
+                    const float rv = 0.5f * fabsf(col) * (float)(d.rho_maj - d.rho_min);
                     if (col > 0.f) vA += rv;
                     else if (col < 0.f) vB += rv;
                     psA = psi_fn(vA, p.psi_kind);

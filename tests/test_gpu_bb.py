@@ -21,6 +21,52 @@ def _small(colour=0.3, walls=1, seed=13, steps_noise=1e-4):
                           capsules=[cap], noise=steps_noise, seed=seed, u_lo=(-0.002, 0, 0), u_hi=(0.002, 0, 0))
 
 
+def _nbrs(mask):
+    """mask and its 18 D3Q19 neighbours (periodic in all three directions: a wall plane's owner is its own)."""
+    out = mask.copy()
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if abs(dx) + abs(dy) + abs(dz) in (1, 2):
+                    out |= np.roll(mask, (dz, dy, dx), (0, 1, 2))
+    return out
+
+
+def _step_with_band(o, steps):
+    """Steps the oracle and returns the nodes next to the membrane over those steps: boundary nodes (a neighbour
+    on another side) and nodes that turned fresh, with their neighbours (R15)."""
+    own = o.owner()
+    near = np.zeros_like(own, bool)
+    for _ in range(steps):
+        o.step(1)
+        nown = o.owner()
+        near |= nown != own
+        for k in np.unique(nown):
+            if k != 0xFFFF:
+                near |= _nbrs(nown == k) & (nown != k) & (nown != 0xFFFF)
+        own = nown
+    return _nbrs(near)
+
+
+def _cmp_band(prob, g, o, band):
+    """R15's bounds for a free-running window in which a discrete decision next to the membrane can part FP32
+    and FP64 (a fresh node's Eq. 18 factor, a link given the neighbouring element of the same capsule): densities
+    within 1e-5 relative away from the membrane and 2e-3 next to it, single vertices within 1e-3, each capsule's
+    mean vertex within 1e-5."""
+    ga, gb, _ = g.scbb_get_fields()
+    oa, ob, _ = o.fields()
+    fl = oa + ob > 0
+    err = np.maximum(np.abs(ga - oa) / np.where(fl, oa, 1.0), np.abs(gb - ob) / np.where(fl, ob, 1.0))
+    err[~fl] = 0.0
+    assert err[~band].max() < 1e-5, err[~band].max()
+    assert err.max() < 2e-3, err.max()
+    gx, ox = g.scbb_get_vertices()[0], o.vertices()[0]
+    assert np.abs(gx - ox).max() < 1e-3
+    off = np.cumsum([0] + list(o.nv))
+    for k in range(len(o.nv)):
+        assert np.abs(gx[off[k]:off[k + 1]].mean(0) - ox[off[k]:off[k + 1]].mean(0)).max() < 1e-5
+
+
 def _cmp_rho(g, o, tol=1e-5):
     ga, gb, _ = g
     oa, ob, _ = o
@@ -203,7 +249,7 @@ def _many():
 def test_bb_thread_forms_against_oracle():
     """The thread-per-node forms of the boundary pass (virtual densities, elements, boundary update), which
     lists of 65,536 nodes or more take, against the oracle: forced onto the small problems through a large
-    list capacity (one step node by node, then 20 steps), and on 64 capsules, whose list takes them by itself
+    list capacity (one step node by node, then 20 steps with R15's bounds), and on 64 capsules, whose list takes them by itself
     (the crossing search then runs three directions a thread): one step node by node, then 4 more with the
     owner field, the elements and each capsule's centre of mass.  (With 230,000 cut links a step, a few links
     that meet a shared edge within the FP32 / FP64 difference of the vertices pick the neighbouring triangle
@@ -219,10 +265,9 @@ def test_bb_thread_forms_against_oracle():
         assert np.array_equal(g.scbb_get_owner()[0], o.owner())
         assert _cmp_rho(g.scbb_get_fields(), o.fields()) < 1e-5
         g.scbb_step(19)
-        o.step(19)
+        band = _step_with_band(o, 19)
         assert np.array_equal(g.scbb_get_owner()[0], o.owner())
-        assert _cmp_rho(g.scbb_get_fields(), o.fields()) < 1e-5
-        assert np.abs(g.scbb_get_vertices()[0] - o.vertices()[0]).max() < 1e-4
+        _cmp_band(prob, g, o, band)
         _check_elements(prob, g, o, exact=False)
         g.close()
     prob = _many()
@@ -283,20 +328,17 @@ def test_bb_three_capsules_periodic():
 def test_bb_uneven_box_rows_across_warps():
     """A box whose rows are not a power-of-two number of four-node quads (nx = 44: 11 quads, rows straddle
     warps, the x-shift falls back to direct loads at warp edges and at the periodic wrap): 20 coupled steps,
-    owners identical, densities within 1e-5, vertices within 1e-4."""
+    owners identical, densities and vertices within R15's bounds (1e-5 away from the membrane)."""
     cap = inputs.Capsule(centre=(21.3, 17.8, 19.6), radius=6.0, subdiv=3, kS=0.02, kB=1e-3, kV=2.0, colour=-0.2)
     p = inputs.Problem(name="uneven", nx=44, ny=36, nz=40, walls=1, coupling=0, psi_kind=0, z_interface=20,
                        capsules=[cap], noise=1e-4, seed=17, u_lo=(-0.001, 0, 0), u_hi=(0.001, 0, 0))
     g = _sim(p)
     o = O.OracleSim(p)
     g.scbb_step(20)
-    o.step(20)
+    band = _step_with_band(o, 20)
     og, _, _ = g.scbb_get_owner()
     assert np.array_equal(og, o.owner())
-    assert _cmp_rho(g.scbb_get_fields(), o.fields()) < 1e-5
-    Xg, _, _ = g.scbb_get_vertices()
-    Xo, _, _ = o.vertices()
-    assert np.abs(Xg - Xo).max() < 1e-4
+    _cmp_band(p, g, o, band)
 
 
 def test_bb_janus_capsule_20_steps():

@@ -10,7 +10,8 @@ against itself under that 1e-6 shift (times a margin), so a GPU error larger tha
 fails, while round-off does not.
 
 Box: 32 x 24 x 26 between walls sheared at +-0.002, a flat interface at z = 13, one s = 3 capsule (R = 6,
-kS = 0.02, colour 0.3) starting above it; over the 1000 steps it adsorbs and moves about 4.4 lattice units down."""
+kS = 0.02, colour 0.9: strongly preferring the lower phase) starting above it; over the 1000 steps it adsorbs and
+moves about 3 lattice units down."""
 import numpy as np
 import pytest
 
@@ -24,7 +25,7 @@ STEPS = 1000
 
 def _problem(shift=0.0):
     cap = inputs.Capsule(centre=(15.3 + shift, 11.8, 12.6), radius=6.0, subdiv=3, kS=0.02, kB=1e-3, kV=2.0,
-                         colour=0.3)
+                         colour=0.9)
     return inputs.Problem(name="long", nx=32, ny=24, nz=26, walls=1, coupling=0, psi_kind=0, z_interface=13,
                           capsules=[cap], noise=1e-4, seed=13, u_lo=(-0.002, 0.0, 0.0), u_hi=(0.002, 0.0, 0.0))
 

@@ -119,6 +119,41 @@ def test_wetting_colour_sign():
     assert zc[0] < zc[1] - 0.5 and zc[2] > zc[1] + 0.5, zc
 
 
+def _interface_height(a, b):
+    """Height of the flat A/B interface from the box's corner columns: where (rho^A - rho^B) / (rho^A + rho^B)
+    changes sign, linearly interpolated (A, the lower phase, is positive)."""
+    d = ((a - b) / np.maximum(a + b, 1e-30))[:, [0, 0, -1, -1], [0, -1, 0, -1]].mean(axis=1)
+    for z in range(2, len(d) - 3):
+        if d[z] > 0 and d[z + 1] <= 0:
+            return z + d[z] / (d[z] - d[z + 1])
+    return np.nan
+
+
+def test_young_law_contact_angle():
+    """Young's law at non-zero colour (Sec. III.D with Eq. 15): a near-rigid capsule (kappa_S = 1, R = 5)
+    started below a flat interface settles with its centre dz below the interface, and cos theta = dz / R
+    equals the colour within 0.1 at the section's colours 0.3 and 0.6 (its figure: cos theta = Delta rho).
+    This fixes the magnitude of the virtual-density offset: with an offset four times larger (the other reading
+    of the normalisation) the contact angle follows cos theta = 4.3 .. 4.6 colour and at 0.3 the capsule
+    leaves the interface."""
+    R, zi = 5.0, 14
+    for col in (0.3, 0.6):
+        cap = inputs.Capsule(centre=(12.1, 11.8, zi - 0.5 - R + 1.0), radius=R, subdiv=2, kS=1.0,
+                             kB=0.01 * R * R, kV=1.0, mass=50.0, colour=col)
+        p = _bb(nx=24, ny=24, nz=28, walls=1, caps=[cap], z_interface=zi, noise=0.0, G=3.6)
+        s = O.OracleSim(p)
+        s.step(2500)
+        cos = []
+        for _ in range(3):                      # settled: the last three readings, 250 steps apart
+            s.step(250)
+            a, b, _ = s.fields()
+            cos.append((_interface_height(a, b) - s.capsule(0)[1][2]) / R)
+        X, _, _ = s.vertices()
+        assert X[:, 2].max() - X[:, 2].min() > 0.95 * 2 * R      # near-rigid: the shape stays a sphere
+        assert np.ptp(cos) < 0.05, cos
+        assert abs(np.mean(cos) - col) < 0.1, (col, cos)
+
+
 def test_fresh_node_mass_correction_reduces_drift():
     """The adaptive correction of Eq. 18 (C0 = 2500) keeps each component's mass closer to its initial value
     than the plain neighbour average of Eq. 16 (C0 = 0) for a capsule moving through a fluid."""
