@@ -65,7 +65,9 @@ def test_bounce_back_1000_steps_within_the_methods_own_sensitivity():
     # volume (the penalty holds it near V0) and the owner field's composition
     assert abs(float(diag["volume"][0]) - a["vol"]) / a["vol"] < max(10.0 * d_vol, 1e-4)
     assert np.mean(own != a["owner"]) < max(10.0 * d_own, 1e-3)
-    assert abs(np.sum(own == 1) - np.sum(a["owner"] == 1)) < 0.01 * np.sum(a["owner"] == 1)
+    # the capsule's inside, in nodes: the oracle pair differ by a couple of nodes (893 and 895 at colour 0.9)
+    n_o, n_o2 = np.sum(a["owner"] == 1), np.sum(b["owner"] == 1)
+    assert abs(np.sum(own == 1) - n_o) <= max(10 * abs(n_o - n_o2), 0.01 * n_o), (np.sum(own == 1), n_o, n_o2)
     # each component's mass: the GPU's drift over 1000 steps matches the oracle's (Eq. 18's correction)
     drift_o = (a["mass"] - m0) / m0
     drift_g = (np.asarray(diag["mass"]) - m0) / m0
