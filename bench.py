@@ -32,9 +32,11 @@ STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2, "fp16dev": 3, "bf16dev": 4}
 # error against the FP64 oracle of each 16-bit storage, as the tests bound it
 STORAGE_ERROR = {
     "fp16": ("densities 1.3e-3, velocities 2.2e-3 of max|u|, vertices 2.5e-3 after 200 steps (32^3); mass offset "
-             "4.7e-6, drift 2.0e-4 over 2000 steps (128^3, FP32 2.3e-4); tests/test_gpu_storage16.py"),
+             "4.7e-6, drift 2.0e-4 over 2000 steps (128^3, FP32 2.3e-4; measured with a colour offset four times "
+             "the present one); tests/test_gpu_storage16.py"),
     "bf16": ("densities 2.0e-2, velocities 2.6e-2 of max|u|, vertices 2.0e-2 after 200 steps (32^3); mass offset "
-             "1.5e-4, drift 1.5e-4 over 2000 steps (128^3, FP32 2.3e-4); tests/test_gpu_storage16.py"),
+             "1.5e-4, drift 1.5e-4 over 2000 steps (128^3, FP32 2.3e-4; measured with a colour offset four times "
+             "the present one); tests/test_gpu_storage16.py"),
 }
 
 
