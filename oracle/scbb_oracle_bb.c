@@ -20,8 +20,8 @@
  *    and homogeneously over the element's three nodes.
  *  - Shan-Chen across a cut link (Eq. 14): the density seen at the node y = x + c_i on the other side is
  *    the mean of rho over the neighbours of y that lie on x's side (not walls); the particle colour adds
- *    rho_virtual = |colour| (rho_maj - rho_min) / 2 to component A if colour > 0, to B if < 0.  The
- *    normalisation below Eq. 14 reads the other way round (colour = rho_virtual / (2 (rho_maj - rho_min)),
+ *    rho_virtual = |colour| (rho_maj - rho_min) / 2 to component A if colour > 0, to B if < 0.  Eq. 15 as
+ *    printed reads the other way round (colour = rho_virtual / (2 (rho_maj - rho_min)),
  *    i.e. an offset 2 |colour| (rho_maj - rho_min)); with that one Sec. III.D's own result cannot hold: a
  *    near-rigid capsule's equilibrium contact angle follows cos theta = 4.3 .. 4.6 colour, and at the
  *    section's colours 0.30 and 0.61 the capsule leaves the interface.  With the factor the other way
