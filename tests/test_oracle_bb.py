@@ -271,3 +271,28 @@ def test_fresh_node_density_eq18_closed_form(eta, regime):
     assert checked >= 0.9 * fresh.sum()
     if regime == "inside":
         assert clamped < 0.5 * 2 * checked, (clamped, checked)
+
+
+def test_fresh_node_velocity_of_a_translating_capsule():
+    """Eq. 17 with Eq. 16's equilibrium: a fresh node takes the velocity of its nearest element, the mean of the
+    element's node velocities.  A capsule translating as a whole (every node at U, no elastic moduli, a node
+    mass so large that the fluid's forces do not change U within the step) has the same velocity on every
+    element, so every fresh node's populations carry exactly U: each component's momentum over its density is U,
+    whichever element is nearest."""
+    U = np.array([0.04, -0.025, 0.03])
+    cap = inputs.Capsule(centre=(10.3, 9.8, 10.6), radius=5.0, subdiv=3, kS=0.0, kB=0.0, kV=0.0, mass=1e12)
+    p = _bb(nx=20, ny=20, nz=22, walls=0, caps=[cap], z_interface=11, noise=0.0, G=3.6)
+    s = O.OracleSim(p)
+    X, _, _ = s.vertices()
+    s.set_vertices(X, np.tile(U, (len(X), 1)))
+    own0 = s.owner().ravel().copy()
+    s.step(1)
+    fresh = np.nonzero(s.owner().ravel() != own0)[0]
+    assert len(fresh) >= 5
+    f = s.populations()                                  # [component][node][direction]
+    c = O.d3q19()[0].astype(float)                       # [19][3]
+    for comp in (0, 1):
+        fn = f[comp, fresh]                              # [fresh][19]
+        rho = fn.sum(axis=1)
+        j = fn @ c
+        assert np.abs(j / rho[:, None] - U).max() < 1e-12, (comp, np.abs(j / rho[:, None] - U).max())
